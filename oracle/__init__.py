@@ -1,0 +1,382 @@
+"""CPU oracle for the AFC path: ctypes wrapper around ``afc_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline leg (and its ``--impl reference`` arm) may import this package.  It shares no
+code with the CUDA path and never imports it.  Everything it computes is FP64 (or exact
+integers) and follows the paper's definitions; see the header of ``afc_oracle.c`` for what
+pins each routine.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "afc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_EOVERFLOW, ORC_ESINGULAR = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, single-threaded code) if stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+P = ctypes.c_void_p
+i32, i64, u32, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+
+
+def _declare(L):
+    L.orc_philox4x32_10.argtypes = [P, P, P]
+    L.orc_philox4x64_10.argtypes = [P, P, P]
+    L.orc_build_csr.argtypes = [i32, i64, P, P, P, P, P]
+    L.orc_survival_threshold.argtypes = [f64]
+    L.orc_survival_threshold.restype = u64
+    L.orc_realize.argtypes = [i64, u64, u32, u32, P, u64, P, P, u32, u32, P, P]
+    L.orc_components.argtypes = [i32, P, P, P, P, P, P]
+    L.orc_sssp.argtypes = [i32, P, P, P, P, P, i32, P, P, P, P]
+    L.orc_brandes.argtypes = [i32, P, P, P, P, P, P, P]
+    L.orc_select.argtypes = [i32, P, P, P, u32, P, u32, f64, P]
+    L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
+                                        u32, u32, u32, P, u32, f64, P, P]
+    L.orc_gauss_solve.argtypes = [i32, P, P, i32]
+    L.orc_assemble_q.argtypes = [i32, P, u32, f64, f64, P, P]
+    L.orc_afc_from_q.argtypes = [i32, P, P, P, P, P, P, P]
+    L.orc_solve_full.argtypes = [i32, P, u32, f64, f64, P, P, P, P, P, P]
+    L.orc_solve_reduced.argtypes = [i32, P, u32, f64, f64, P, P, P, P, P, P, P]
+    L.orc_rank.argtypes = [i32, P, f64, P]
+    L.orc_certificates.argtypes = [i32, P, P, f64, f64, i32, P, P, P, P, P]
+    L.orc_perturb_row.argtypes = [i32, P, f64, u64, u32, u32, f64, f64, P, P]
+    L.orc_perturb_sweep.argtypes = [i32, P, P, P, u32, u32, f64, f64, u64, i32, i32, i32, f64,
+                                    P, P, P, P, P, P]
+    for name in ("orc_build_csr", "orc_components", "orc_sssp", "orc_brandes",
+                 "orc_count_transitions", "orc_gauss_solve", "orc_afc_from_q", "orc_solve_full",
+                 "orc_solve_reduced", "orc_certificates", "orc_perturb_sweep"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(st, what):
+    if st != ORC_OK:
+        raise OracleError(f"{what} failed with status {st}")
+
+
+# ---------------------------------------------------------------- Philox ----
+
+def philox4x32(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- graphs ----
+
+@dataclass
+class Graph:
+    n: int
+    m: int
+    row_ptr: np.ndarray   # int64 [n+1]
+    col: np.ndarray       # int32 [2m]
+    eid: np.ndarray       # int32 [2m]
+
+
+def build_graph(n: int, eu, ev) -> Graph:
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    m = int(eu.shape[0])
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(2 * m, 1), np.int32)
+    eid = np.zeros(max(2 * m, 1), np.int32)
+    _check(lib().orc_build_csr(n, m, _p(eu), _p(ev), _p(rp), _p(col), _p(eid)), "build_csr")
+    return Graph(n, m, rp, col, eid)
+
+
+def survival_threshold(p: float) -> int:
+    return int(lib().orc_survival_threshold(float(p)))
+
+
+def thresholds(p_survive, m: int):
+    """(per-edge array or None, scalar) survival thresholds floor(p 2^32)."""
+    if np.ndim(p_survive) == 0:
+        return None, survival_threshold(float(p_survive))
+    arr = np.array([survival_threshold(float(x)) for x in np.asarray(p_survive)], dtype=np.uint64)
+    assert arr.shape[0] == m
+    return arr, 0
+
+
+def realize(g: Graph, seed: int, graph_tag: int, r: int, p_survive, w_lo, w_hi):
+    th, th_all = thresholds(p_survive, g.m)
+    lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
+    hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
+    alive = np.zeros(max(g.m, 1), np.uint8)
+    w = np.zeros(max(g.m, 1), np.uint32)
+    lib().orc_realize(g.m, seed, graph_tag, r, _p(th), th_all, _p(lo_arr), _p(hi_arr),
+                      0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
+                      _p(alive), _p(w))
+    return alive[:g.m], w[:g.m]
+
+
+def components(g: Graph, alive):
+    alive = np.ascontiguousarray(alive, dtype=np.uint8)
+    comp = np.zeros(max(g.n, 1), np.int32)
+    csize = np.zeros(max(g.n, 1), np.int32)
+    _check(lib().orc_components(g.n, _p(g.row_ptr), _p(g.col), _p(g.eid), _p(alive), _p(comp),
+                                _p(csize)), "components")
+    return comp[:g.n], csize[:g.n]
+
+
+INF = np.iinfo(np.uint64).max
+
+
+def sssp(g: Graph, alive, w, s: int):
+    """Returns (dist u64 [INF if unreachable], sigma u64, settle order, overflowed)."""
+    alive = np.ascontiguousarray(alive, dtype=np.uint8)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    dist = np.zeros(g.n, np.uint64)
+    sigma = np.zeros(g.n, np.uint64)
+    order = np.zeros(g.n, np.int32)
+    ns = ctypes.c_int32(0)
+    st = lib().orc_sssp(g.n, _p(g.row_ptr), _p(g.col), _p(g.eid), _p(alive), _p(w), s,
+                        _p(dist), _p(sigma), _p(order), ctypes.byref(ns))
+    if st not in (ORC_OK, ORC_EOVERFLOW):
+        _check(st, "sssp")
+    return dist, sigma, order[:ns.value], st == ORC_EOVERFLOW
+
+
+def brandes(g: Graph, alive, w, src_mask=None):
+    alive = np.ascontiguousarray(alive, dtype=np.uint8)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    mask = None if src_mask is None else np.ascontiguousarray(src_mask, dtype=np.uint8)
+    bc = np.zeros(max(g.n, 1), np.float64)
+    st = lib().orc_brandes(g.n, _p(g.row_ptr), _p(g.col), _p(g.eid), _p(alive), _p(w), _p(mask),
+                           _p(bc))
+    if st not in (ORC_OK, ORC_EOVERFLOW):
+        _check(st, "brandes")
+    return bc[:g.n]
+
+
+def select(n, comp, csize, bc, k_min, in_w=None, top_k=0, tie_rel=1e-9):
+    comp = np.ascontiguousarray(comp, dtype=np.int32)
+    csize = np.ascontiguousarray(csize, dtype=np.int32)
+    bc = np.ascontiguousarray(bc, dtype=np.float64)
+    inw = None if in_w is None else np.ascontiguousarray(in_w, dtype=np.uint8)
+    centre = np.zeros(max(n, 1), np.int32)
+    lib().orc_select(n, _p(comp), _p(csize), _p(bc), k_min, _p(inw), top_k, tie_rel, _p(centre))
+    return centre[:n]
+
+
+def candidate_mask(n, candidates):
+    if candidates is None:
+        return None
+    m = np.zeros(n, np.uint8)
+    m[np.asarray(candidates, dtype=np.int64)] = 1
+    return m
+
+
+def count_transitions(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi,
+                      k_min, candidates=None, top_k=0, tie_rel=1e-9, counts=None):
+    """Transition counts [n, n+1] (uint32, last column = absorption) for realizations
+    r_begin .. r_begin + r_count - 1.  Returns (counts, n_sigma_overflow_realizations)."""
+    th, th_all = thresholds(p_survive, g.m)
+    lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
+    hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
+    inw = candidate_mask(g.n, candidates)
+    if counts is None:
+        counts = np.zeros((g.n, g.n + 1), np.uint32)
+    stats = np.zeros(1, np.uint64)
+    st = lib().orc_count_transitions(
+        g.n, g.m, _p(g.row_ptr), _p(g.col), _p(g.eid), seed, graph_tag, r_begin, r_count,
+        _p(th), th_all, _p(lo_arr), _p(hi_arr),
+        0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
+        k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats))
+    if st not in (ORC_OK, ORC_EOVERFLOW):
+        _check(st, "count_transitions")
+    return counts, int(stats[0])
+
+
+def count_transitions_parallel(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo,
+                               w_hi, k_min, candidates=None, top_k=0, tie_rel=1e-9, threads=None):
+    """Same result as count_transitions, split over threads on disjoint realization ranges
+    (the C routine is re-entrant and ctypes releases the GIL).  Returns (counts, overflows,
+    threads used)."""
+    threads = threads or os.cpu_count() or 1
+    threads = max(1, min(threads, r_count))
+    bounds = [r_begin + (r_count * t) // threads for t in range(threads + 1)]
+    parts = [None] * threads
+
+    def work(t):
+        parts[t] = count_transitions(g, seed, graph_tag, bounds[t], bounds[t + 1] - bounds[t],
+                                     p_survive, w_lo, w_hi, k_min, candidates, top_k, tie_rel)
+
+    ts = [threading.Thread(target=work, args=(t,)) for t in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    counts = np.zeros((g.n, g.n + 1), np.uint64)
+    ovf = 0
+    for c, o in parts:
+        counts += c
+        ovf += o
+    return counts.astype(np.uint32), ovf, threads
+
+
+# ---------------------------------------------------------------- linear algebra ----
+
+def gauss_solve(A, b):
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    b = np.array(b, dtype=np.float64, order="C", copy=True)
+    n = A.shape[0]
+    nrhs = 1 if b.ndim == 1 else b.shape[1]
+    _check(lib().orc_gauss_solve(n, _p(A), _p(b), nrhs), "gauss_solve")
+    return b
+
+
+def assemble_q(counts, R, alpha, eta=1e-6):
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    n = counts.shape[0]
+    Q = np.zeros((n, n), np.float64)
+    r = np.zeros(n, np.float64)
+    lib().orc_assemble_q(n, _p(counts), R, alpha, eta, _p(Q), _p(r))
+    return Q, r
+
+
+def afc_from_q(Q, s=None, f=None):
+    """Returns (mu, b, E_s[T], b_f)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    n = Q.shape[0]
+    s_ = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+    f_ = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
+    mu = np.zeros(n)
+    b = np.zeros(n)
+    T = ctypes.c_double(0)
+    bf = ctypes.c_double(0)
+    _check(lib().orc_afc_from_q(n, _p(Q), _p(s_), _p(f_), _p(mu), _p(b), ctypes.byref(T),
+                                ctypes.byref(bf)), "afc_from_q")
+    return mu, b, T.value, bf.value
+
+
+def solve_counts(counts, R, alpha, eta=1e-6, s=None, f=None, reduced=False):
+    """counts -> (mu, b, E_s[T], b_f[, |C|]).  Full n x n solve unless reduced=True."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    n = counts.shape[0]
+    s_ = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+    f_ = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
+    mu = np.zeros(n)
+    b = np.zeros(n)
+    T = ctypes.c_double(0)
+    bf = ctypes.c_double(0)
+    if reduced:
+        c = ctypes.c_int32(0)
+        _check(lib().orc_solve_reduced(n, _p(counts), R, alpha, eta, _p(s_), _p(f_), _p(mu), _p(b),
+                                       ctypes.byref(T), ctypes.byref(bf), ctypes.byref(c)),
+               "solve_reduced")
+        return mu, b, T.value, bf.value, c.value
+    _check(lib().orc_solve_full(n, _p(counts), R, alpha, eta, _p(s_), _p(f_), _p(mu), _p(b),
+                                ctypes.byref(T), ctypes.byref(bf)), "solve_full")
+    return mu, b, T.value, bf.value
+
+
+def rank(b, tie_rel=1e-9):
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(b.shape[0], np.int32)
+    lib().orc_rank(b.shape[0], _p(b), tie_rel, _p(out))
+    return out
+
+
+def certificates(Q, s, eps_bar, r_min, pairs):
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    n = Q.shape[0]
+    s_ = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+    pu = np.ascontiguousarray([p[0] for p in pairs], dtype=np.int32)
+    pv = np.ascontiguousarray([p[1] for p in pairs], dtype=np.int32)
+    gap = np.zeros(len(pairs))
+    sharp = np.zeros(len(pairs))
+    crude = ctypes.c_double(0)
+    _check(lib().orc_certificates(n, _p(Q), _p(s_), eps_bar, r_min, len(pairs), _p(pu), _p(pv),
+                                  _p(gap), ctypes.byref(crude), _p(sharp)), "certificates")
+    return gap, crude.value, sharp
+
+
+def perturb_row(q0, r0, seed, i, p, radius, r_min):
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    n = q0.shape[0]
+    q = np.zeros(n)
+    r = ctypes.c_double(0)
+    lib().orc_perturb_row(n, _p(q0), r0, seed, i, p, radius, r_min, _p(q), ctypes.byref(r))
+    return q, r.value
+
+
+@dataclass
+class PerturbStats:
+    top1_changes: int
+    topk_set_changes: int
+    topk_order_changes: int
+    pair_flips: np.ndarray     # [K2, K2], upper triangle
+    shift_hist: np.ndarray     # [H]
+    max_db: float
+    max_lin_err: float
+    max_rowsum_N: float
+    b: Optional[np.ndarray] = None       # [p_count, n] if requested
+    ranks: Optional[np.ndarray] = None   # [p_count, n] if requested
+
+
+def perturb_sweep(Q0, r0, s, p_begin, p_count, radius, r_min, seed, top_k=5, K2=10, H=16,
+                  tie_rel=1e-9, keep=False) -> PerturbStats:
+    Q0 = np.ascontiguousarray(Q0, dtype=np.float64)
+    r0 = np.ascontiguousarray(r0, dtype=np.float64)
+    n = Q0.shape[0]
+    s_ = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+    oc = np.zeros(3, np.uint64)
+    pf = np.zeros(K2 * K2, np.uint64)
+    sh = np.zeros(H, np.uint64)
+    of = np.zeros(3, np.float64)
+    b_out = np.zeros((p_count, n)) if keep else None
+    r_out = np.zeros((p_count, n), np.int32) if keep else None
+    _check(lib().orc_perturb_sweep(n, _p(Q0), _p(r0), _p(s_), p_begin, p_count, radius, r_min,
+                                   seed, top_k, K2, H, tie_rel, _p(oc), _p(pf), _p(sh), _p(of),
+                                   _p(b_out), _p(r_out)), "perturb_sweep")
+    return PerturbStats(int(oc[0]), int(oc[1]), int(oc[2]), pf.reshape(K2, K2), sh,
+                        float(of[0]), float(of[1]), float(of[2]), b_out, r_out)

@@ -1,0 +1,804 @@
+/*
+ * afc_oracle.c -- plain, single-threaded CPU oracle for the absorbing-frequency-centrality
+ * (AFC) path of "Betweenness-Central Nodes Under Uncertainty: An Absorbing Markov Chain
+ * Approach" (Bao, Kontou, Vogiatzis).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline leg load this file's library.  It shares no code, header, table or helper with
+ * the CUDA path.  Every routine is the plain definition (or the paper's algorithm in the
+ * paper's order); nothing is blocked, fused or reordered for speed.  Floating point is FP64.
+ *
+ * Parity status of each routine (what pins it in the not-gpu tests):
+ *   orc_philox4x32_10 / orc_philox4x64_10 : 4x64 checked against numpy.random.Philox;
+ *                                           4x32 shares the round structure; uniformity tests.
+ *   orc_realize                           : survival frequency / weight histogram tests.
+ *   orc_components                        : brute-force BFS comparison, invariants.
+ *   orc_sssp / orc_brandes                : closed-form betweenness (path, star, cycle,
+ *                                           complete, clique-bridge), brute-force shortest
+ *                                           path enumeration, networkx cross-check.
+ *   orc_select / orc_count_transitions    : crossroads example (Sec. 2.1) by exhaustive
+ *                                           enumeration of failure patterns; row sums.
+ *   orc_gauss_solve / orc_solve_*         : crossroads AFC and E[T]; Appendix B; canonical
+ *                                           chain closed form (Prop. in App. A); constant-
+ *                                           hazard discounted occupancy (Sec. 5.3).
+ *   orc_certificates                      : Appendix B printed thresholds.
+ *   orc_perturb_sweep                     : parity unpinned beyond invariants (no printed
+ *                                           values exist for this statistic).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+#define ORC_EOVERFLOW 3
+#define ORC_ESINGULAR 4
+
+#define ORC_INF UINT64_MAX
+
+/* ------------------------------------------------------------------------------------ */
+/* Philox counter-based generator (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:  */
+/* as easy as 1, 2, 3", SC'11): 10 rounds of a multiply-hi/lo Feistel-like bijection on    */
+/* a 4-word counter, with a Weyl-sequence key schedule.                                   */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    unsigned __int128 p0 = (unsigned __int128)0xD2E7470EE14C6C93ull * x0;
+    unsigned __int128 p1 = (unsigned __int128)0xCA5A826395121157ull * x2;
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t y0 = hi1 ^ x1 ^ k0;
+    uint64_t y1 = lo1;
+    uint64_t y2 = hi0 ^ x3 ^ k1;
+    uint64_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Base graph: symmetric CSR built from an undirected simple edge list (Sec. 3.1: base    */
+/* topology G(V, E)).  Arc a of row v goes to col[a] and belongs to undirected edge eid[a].*/
+/* ------------------------------------------------------------------------------------ */
+
+int orc_build_csr(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                  int64_t *row_ptr, int32_t *col, int32_t *eid) {
+  if (n < 0 || m < 0) return ORC_EINVAL;
+  for (int64_t e = 0; e < m; ++e) {
+    if (eu[e] < 0 || eu[e] >= n || ev[e] < 0 || ev[e] >= n || eu[e] == ev[e]) return ORC_EINVAL;
+  }
+  for (int32_t v = 0; v <= n; ++v) row_ptr[v] = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    row_ptr[eu[e] + 1]++;
+    row_ptr[ev[e] + 1]++;
+  }
+  for (int32_t v = 0; v < n; ++v) row_ptr[v + 1] += row_ptr[v];
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!fill) return ORC_ENOMEM;
+  for (int32_t v = 0; v < n; ++v) fill[v] = row_ptr[v];
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t a = eu[e], b = ev[e];
+    col[fill[a]] = b; eid[fill[a]] = (int32_t)e; fill[a]++;
+    col[fill[b]] = a; eid[fill[b]] = (int32_t)e; fill[b]++;
+  }
+  free(fill);
+  /* reject duplicate edges: sort each row by neighbour (insertion sort; rows are short) */
+  for (int32_t v = 0; v < n; ++v) {
+    for (int64_t i = row_ptr[v] + 1; i < row_ptr[v + 1]; ++i) {
+      int32_t c = col[i], d = eid[i];
+      int64_t j = i - 1;
+      while (j >= row_ptr[v] && col[j] > c) {
+        col[j + 1] = col[j]; eid[j + 1] = eid[j]; --j;
+      }
+      col[j + 1] = c; eid[j + 1] = d;
+    }
+    for (int64_t i = row_ptr[v] + 1; i < row_ptr[v + 1]; ++i)
+      if (col[i] == col[i - 1]) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* One network realization (Sec. 3.1: network state Y -> working graph H).  Edge e of      */
+/* realization r of graph g draws (u0, u1, -, -) = Philox4x32-10(ctr = (e, r, g, 0),       */
+/* key = seed); it survives iff u0 < T_e with T_e = floor(p_e 2^32) (T_e = 2^32 for p=1),  */
+/* and its length is w_e = lo_e + floor(u1 (hi_e - lo_e + 1) / 2^32).                     */
+/* ------------------------------------------------------------------------------------ */
+
+uint64_t orc_survival_threshold(double p) {
+  if (!(p > 0.0)) return 0;
+  if (p >= 1.0) return (uint64_t)1 << 32;
+  return (uint64_t)floor(p * 4294967296.0);
+}
+
+void orc_realize(int64_t m, uint64_t seed, uint32_t graph_tag, uint32_t r,
+                 const uint64_t *thresh, uint64_t thresh_all,
+                 const uint32_t *w_lo, const uint32_t *w_hi, uint32_t w_lo_all, uint32_t w_hi_all,
+                 uint8_t *alive, uint32_t *w) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t e = 0; e < m; ++e) {
+    uint32_t ctr[4] = {(uint32_t)e, r, graph_tag, 0u};
+    uint32_t u[4];
+    orc_philox4x32_10(ctr, key, u);
+    uint64_t T = thresh ? thresh[e] : thresh_all;
+    uint32_t lo = w_lo ? w_lo[e] : w_lo_all;
+    uint32_t hi = w_hi ? w_hi[e] : w_hi_all;
+    alive[e] = ((uint64_t)u[0] < T) ? 1 : 0;
+    uint64_t span = (uint64_t)hi - (uint64_t)lo + 1u;
+    w[e] = lo + (uint32_t)(((uint64_t)u[1] * span) >> 32);
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Components K(i; H) of the realized graph (Sec. 3.2).  comp[v] = smallest vertex id of  */
+/* v's component; csize[v] = |K(v; H)|.  Plain BFS started from each unvisited vertex in  */
+/* increasing id order.                                                                   */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_components(int32_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *eid,
+                   const uint8_t *alive, int32_t *comp, int32_t *csize) {
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!queue) return ORC_ENOMEM;
+  for (int32_t v = 0; v < n; ++v) comp[v] = -1;
+  for (int32_t s = 0; s < n; ++s) {
+    if (comp[s] >= 0) continue;
+    int32_t head = 0, tail = 0;
+    queue[tail++] = s;
+    comp[s] = s;
+    while (head < tail) {
+      int32_t v = queue[head++];
+      for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+        if (!alive[eid[a]]) continue;
+        int32_t u = col[a];
+        if (comp[u] < 0) { comp[u] = s; queue[tail++] = u; }
+      }
+    }
+    for (int32_t i = 0; i < tail; ++i) csize[queue[i]] = tail;
+  }
+  free(queue);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Weighted single-source shortest paths with path counting (Sec. 3.1: d_H(s,t) and       */
+/* sigma_st(H)).  Textbook Dijkstra with a binary heap (lazy deletion).  sigma is counted  */
+/* exactly in 64-bit integers; an overflow makes the call return ORC_EOVERFLOW.           */
+/* order[] receives the settled vertices in non-decreasing distance; *n_settled its size.  */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct { uint64_t d; int32_t v; } heap_item;
+
+static void heap_push(heap_item *h, int64_t *size, uint64_t d, int32_t v) {
+  int64_t i = (*size)++;
+  h[i].d = d; h[i].v = v;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d < h[i].d || (h[p].d == h[i].d && h[p].v <= h[i].v)) break;
+    heap_item t = h[p]; h[p] = h[i]; h[i] = t;
+    i = p;
+  }
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *size) {
+  heap_item top = h[0];
+  h[0] = h[--(*size)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, b = i;
+    if (l < *size && (h[l].d < h[b].d || (h[l].d == h[b].d && h[l].v < h[b].v))) b = l;
+    if (r < *size && (h[r].d < h[b].d || (h[r].d == h[b].d && h[r].v < h[b].v))) b = r;
+    if (b == i) break;
+    heap_item t = h[b]; h[b] = h[i]; h[i] = t;
+    i = b;
+  }
+  return top;
+}
+
+int orc_sssp(int32_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *eid,
+             const uint8_t *alive, const uint32_t *w, int32_t s,
+             uint64_t *dist, uint64_t *sigma, int32_t *order, int32_t *n_settled) {
+  int64_t arcs = row_ptr[n];
+  heap_item *heap = (heap_item *)malloc(sizeof(heap_item) * (size_t)(arcs + 2));
+  uint8_t *done = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!heap || !done) { free(heap); free(done); return ORC_ENOMEM; }
+  int status = ORC_OK;
+  for (int32_t v = 0; v < n; ++v) { dist[v] = ORC_INF; sigma[v] = 0; }
+  dist[s] = 0; sigma[s] = 1;
+  int64_t hs = 0;
+  int32_t ns = 0;
+  heap_push(heap, &hs, 0, s);
+  while (hs > 0) {
+    heap_item it = heap_pop(heap, &hs);
+    int32_t v = it.v;
+    if (done[v] || it.d != dist[v]) continue;
+    done[v] = 1;
+    order[ns++] = v;
+    for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+      int32_t e = eid[a];
+      if (!alive[e]) continue;
+      int32_t u = col[a];
+      uint64_t nd = dist[v] + (uint64_t)w[e];
+      if (nd < dist[u]) {
+        dist[u] = nd;
+        sigma[u] = sigma[v];
+        heap_push(heap, &hs, nd, u);
+      } else if (nd == dist[u]) {
+        uint64_t t;
+        if (__builtin_add_overflow(sigma[u], sigma[v], &t)) status = ORC_EOVERFLOW;
+        sigma[u] = t;
+      }
+    }
+  }
+  *n_settled = ns;
+  free(heap); free(done);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Weighted betweenness B_v(H) over ordered pairs (Sec. 3.1, the non-normalised           */
+/* definition: sum over s != t, s != v != t with t reachable of sigma_st(v) / sigma_st).   */
+/* Computed with Brandes' dependency recursion: for each source s, in non-increasing       */
+/* distance, delta_s(v) = sum over successors w of (sigma_v / sigma_w)(1 + delta_s(w)),    */
+/* where w is a successor of v iff d(s,v) + len(v,w) = d(s,w); then B_v += delta_s(v).     */
+/* Only sources with src_mask[s] != 0 are used (src_mask NULL = every source).            */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_brandes(int32_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *eid,
+                const uint8_t *alive, const uint32_t *w, const uint8_t *src_mask, double *bc) {
+  uint64_t *dist = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  double *delta = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!dist || !sigma || !order || !delta) {
+    free(dist); free(sigma); free(order); free(delta);
+    return ORC_ENOMEM;
+  }
+  int status = ORC_OK;
+  for (int32_t v = 0; v < n; ++v) bc[v] = 0.0;
+  for (int32_t s = 0; s < n; ++s) {
+    if (src_mask && !src_mask[s]) continue;
+    int32_t ns = 0;
+    int st = orc_sssp(n, row_ptr, col, eid, alive, w, s, dist, sigma, order, &ns);
+    if (st == ORC_ENOMEM) { status = st; break; }
+    if (st != ORC_OK) status = st;
+    for (int32_t i = 0; i < ns; ++i) delta[order[i]] = 0.0;
+    for (int32_t i = ns - 1; i >= 0; --i) {
+      int32_t v = order[i];
+      double acc = 0.0;
+      for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) {
+        int32_t e = eid[a];
+        if (!alive[e]) continue;
+        int32_t x = col[a];
+        if (dist[x] != ORC_INF && dist[v] + (uint64_t)w[e] == dist[x])
+          acc += ((double)sigma[v] / (double)sigma[x]) * (1.0 + delta[x]);
+      }
+      delta[v] = acc;
+      if (v != s) bc[v] += delta[v];
+    }
+  }
+  free(dist); free(sigma); free(order); free(delta);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Tie-broken local centre per component (Sec. 3.2 eq. local-center; Cor. on             */
+/* deterministic tie-breaking; Sec. 7.1 constrained selector Sel_W).                      */
+/*   valid component K: |K| >= k_min.  Candidate set X = K intersect W (W = V if absent).  */
+/*   B* = max_X B, tau = tie_rel * B*, ties = {v in X : B_v >= B* - tau}, centre = min id. */
+/*   With top_k > 0 the centre must also rank within the first top_k of K:                */
+/*   rank = 1 + #{u in K : B_u > B_c + tauK, or |B_u - B_c| <= tauK and u < c},             */
+/*   tauK = tie_rel * max_K B.  centre[root] = -1 encodes "no valid continuation".         */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_select(int32_t n, const int32_t *comp, const int32_t *csize, const double *bc,
+                uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
+                int32_t *centre) {
+  for (int32_t v = 0; v < n; ++v) centre[v] = -1;
+  for (int32_t root = 0; root < n; ++root) {
+    if (comp[root] != root) continue;
+    if ((uint32_t)csize[root] < k_min) continue;
+    double bstar = -1.0, bmaxK = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      if (comp[v] != root) continue;
+      if (bc[v] > bmaxK) bmaxK = bc[v];
+      if (in_w && !in_w[v]) continue;
+      if (bc[v] > bstar) bstar = bc[v];
+    }
+    if (bstar < 0.0) continue; /* K has no candidate */
+    double tau = tie_rel * bstar;
+    int32_t c = -1;
+    for (int32_t v = 0; v < n && c < 0; ++v) {
+      if (comp[v] != root || (in_w && !in_w[v])) continue;
+      if (bc[v] >= bstar - tau) c = v;
+    }
+    if (top_k > 0) {
+      double tauK = tie_rel * bmaxK;
+      uint32_t rank = 1;
+      for (int32_t u = 0; u < n; ++u) {
+        if (comp[u] != root || u == c) continue;
+        double diff = bc[u] - bc[c];
+        if (diff > tauK || (fabs(diff) <= tauK && u < c)) rank++;
+      }
+      if (rank > top_k) continue;
+    }
+    centre[root] = c;
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Monte Carlo transition counts (Alg. 1 SampleNext and Alg. 2 row-wise construction).    */
+/* Realization r in [r_begin, r_begin + r_count) serves every anchor i at once (the row   */
+/* law depends only on the law of H, Prop. on order/branch invariance):                   */
+/*   next(i) = bottom if |K(i;H)| < k_min or K(i;H) has no admissible centre,             */
+/*   next(i) = centre of K(i;H) otherwise;  counts[i*(n+1) + next(i)] += 1 (bottom = n).  */
+/* Only sources inside valid components enter the betweenness (a vertex's betweenness     */
+/* only depends on sources of its own component).                                         */
+/* stats[0] += realizations whose sigma overflowed 64 bits.                               */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                          const int32_t *eid, uint64_t seed, uint32_t graph_tag,
+                          uint32_t r_begin, uint32_t r_count,
+                          const uint64_t *thresh, uint64_t thresh_all,
+                          const uint32_t *w_lo, const uint32_t *w_hi,
+                          uint32_t w_lo_all, uint32_t w_hi_all,
+                          uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
+                          uint32_t *counts, uint64_t *stats) {
+  size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
+  uint8_t *alive = (uint8_t *)malloc(mm);
+  uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
+  int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *csize = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *centre = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint8_t *src = (uint8_t *)malloc(nn);
+  double *bc = (double *)malloc(sizeof(double) * nn);
+  int status = ORC_OK;
+  if (!alive || !w || !comp || !csize || !centre || !src || !bc) { status = ORC_ENOMEM; goto out; }
+  for (uint32_t k = 0; k < r_count; ++k) {
+    uint32_t r = r_begin + k;
+    orc_realize(m, seed, graph_tag, r, thresh, thresh_all, w_lo, w_hi, w_lo_all, w_hi_all, alive, w);
+    int st = orc_components(n, row_ptr, col, eid, alive, comp, csize);
+    if (st != ORC_OK) { status = st; goto out; }
+    /* sources: members of valid components that contain at least one candidate */
+    for (int32_t v = 0; v < n; ++v) src[v] = 0;
+    for (int32_t v = 0; v < n; ++v) {
+      if ((uint32_t)csize[v] >= k_min && (!in_w || in_w[v])) src[comp[v]] = 1; /* mark root */
+    }
+    for (int32_t v = 0; v < n; ++v) src[v] = src[comp[v]];
+    st = orc_brandes(n, row_ptr, col, eid, alive, w, src, bc);
+    if (st == ORC_ENOMEM) { status = st; goto out; }
+    if (st == ORC_EOVERFLOW) { if (stats) stats[0]++; status = ORC_EOVERFLOW; }
+    orc_select(n, comp, csize, bc, k_min, in_w, top_k, tie_rel, centre);
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t c = centre[comp[i]];
+      size_t col_idx = (c < 0) ? (size_t)n : (size_t)c;
+      counts[(size_t)i * (size_t)(n + 1) + col_idx] += 1u;
+    }
+  }
+out:
+  free(alive); free(w); free(comp); free(csize); free(centre); free(src); free(bc);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Dense Gaussian elimination with partial pivoting: solves A x = b in place (A is n x n  */
+/* row-major and is destroyed; b is overwritten by x).                                    */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_gauss_solve(int32_t n, double *A, double *b, int32_t nrhs) {
+  for (int32_t k = 0; k < n; ++k) {
+    int32_t piv = k;
+    double best = fabs(A[(size_t)k * n + k]);
+    for (int32_t i = k + 1; i < n; ++i) {
+      double a = fabs(A[(size_t)i * n + k]);
+      if (a > best) { best = a; piv = i; }
+    }
+    if (best == 0.0) return ORC_ESINGULAR;
+    if (piv != k) {
+      for (int32_t j = 0; j < n; ++j) {
+        double t = A[(size_t)k * n + j]; A[(size_t)k * n + j] = A[(size_t)piv * n + j]; A[(size_t)piv * n + j] = t;
+      }
+      for (int32_t q = 0; q < nrhs; ++q) {
+        double t = b[(size_t)k * nrhs + q]; b[(size_t)k * nrhs + q] = b[(size_t)piv * nrhs + q]; b[(size_t)piv * nrhs + q] = t;
+      }
+    }
+    for (int32_t i = k + 1; i < n; ++i) {
+      double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (f == 0.0) continue;
+      for (int32_t j = k; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+      for (int32_t q = 0; q < nrhs; ++q) b[(size_t)i * nrhs + q] -= f * b[(size_t)k * nrhs + q];
+    }
+  }
+  for (int32_t i = n - 1; i >= 0; --i) {
+    for (int32_t q = 0; q < nrhs; ++q) {
+      double acc = b[(size_t)i * nrhs + q];
+      for (int32_t j = i + 1; j < n; ++j) acc -= A[(size_t)i * n + j] * b[(size_t)j * nrhs + q];
+      b[(size_t)i * nrhs + q] = acc / A[(size_t)i * n + i];
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Kernel assembly from counts (Alg. 2 plus stabilisation, Sec. 8.2, and the analytic     */
+/* exogenous stop alpha, Sec. 4):                                                         */
+/*   Q_ij = (1 - alpha) counts_ij / R,   r_i = alpha + (1 - alpha) counts_i,bottom / R.   */
+/*   If r_i == 0 (possible only for alpha = 0): r_i = eta and row i's transient part is   */
+/*   rescaled to sum 1 - eta.                                                              */
+/* Q is written densely (n x n row-major), r as a vector.                                 */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_assemble_q(int32_t n, const uint32_t *counts, uint32_t R, double alpha, double eta,
+                    double *Q, double *r) {
+  for (int32_t i = 0; i < n; ++i) {
+    const uint32_t *row = counts + (size_t)i * (size_t)(n + 1);
+    double tsum = 0.0;
+    for (int32_t j = 0; j < n; ++j) {
+      Q[(size_t)i * n + j] = (1.0 - alpha) * (double)row[j] / (double)R;
+      tsum += Q[(size_t)i * n + j];
+    }
+    r[i] = alpha + (1.0 - alpha) * (double)row[n] / (double)R;
+    if (r[i] == 0.0) {
+      r[i] = eta;
+      if (tsum > 0.0)
+        for (int32_t j = 0; j < n; ++j) Q[(size_t)i * n + j] *= (1.0 - eta) / tsum;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* AFC from a transient block (Sec. 4 eqs. fundamental, visits, expected-length, afc-def, */
+/* Sec. 6.4 eq. mr-inner-product):  mu = s N with N = (I - Q)^-1, i.e. (I - Q)^T mu^T =    */
+/* s^T;  E_s[T] = mu 1;  b = mu / E_s[T];  b_f = b . f.  Full n x n solve.                */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_afc_from_q(int32_t n, const double *Q, const double *s, const double *f,
+                   double *mu, double *b, double *expected_T, double *b_f) {
+  double *A = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  if (!A) return ORC_ENOMEM;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < n; ++j)
+      A[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - Q[(size_t)j * n + i]; /* (I - Q)^T */
+  for (int32_t i = 0; i < n; ++i) mu[i] = s ? s[i] : 1.0 / (double)n;
+  int st = orc_gauss_solve(n, A, mu, 1);
+  free(A);
+  if (st != ORC_OK) return st;
+  double T = 0.0;
+  for (int32_t i = 0; i < n; ++i) T += mu[i];
+  *expected_T = T;
+  double bf = 0.0;
+  for (int32_t i = 0; i < n; ++i) {
+    b[i] = mu[i] / T;
+    if (f) bf += b[i] * f[i];
+  }
+  if (b_f) *b_f = f ? bf : 0.0;
+  return ORC_OK;
+}
+
+/* counts -> Q -> AFC, full solve.  Also returns r (absorption probabilities). */
+int orc_solve_full(int32_t n, const uint32_t *counts, uint32_t R, double alpha, double eta,
+                   const double *s, const double *f, double *mu, double *b, double *expected_T,
+                   double *b_f) {
+  double *Q = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!Q || !r) { free(Q); free(r); return ORC_ENOMEM; }
+  orc_assemble_q(n, counts, R, alpha, eta, Q, r);
+  int st = orc_afc_from_q(n, Q, s, f, mu, b, expected_T, b_f);
+  free(Q); free(r);
+  return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Reduced solve on the observed centre states.  C = {j : some count_ij > 0, j in V},     */
+/* U = V \ C.  The columns of Q on U are zero, so with (U, C) block order                 */
+/*   mu_U = s_U,   mu_C (I - Q_CC) = s_C + s_U Q_UC.                                       */
+/* This is an exact rewriting of mu = s N, used where the full n x n system is too large. */
+/* c_out receives |C|.                                                                     */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_solve_reduced(int32_t n, const uint32_t *counts, uint32_t R, double alpha, double eta,
+                      const double *s, const double *f, double *mu, double *b,
+                      double *expected_T, double *b_f, int32_t *c_out) {
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * nn);
+  double *qrow = (double *)malloc(sizeof(double) * nn);
+  if (!pos || !cl || !qrow) { free(pos); free(cl); free(qrow); return ORC_ENOMEM; }
+  int32_t c = 0;
+  for (int32_t j = 0; j < n; ++j) {
+    pos[j] = -1;
+    for (int32_t i = 0; i < n; ++i)
+      if (counts[(size_t)i * (size_t)(n + 1) + j] > 0) { pos[j] = c; cl[c++] = j; break; }
+  }
+  *c_out = c;
+  double *A = (double *)calloc((size_t)(c > 0 ? c : 1) * (size_t)(c > 0 ? c : 1), sizeof(double));
+  double *y = (double *)calloc((size_t)(c > 0 ? c : 1), sizeof(double));
+  if (!A || !y) { free(pos); free(cl); free(qrow); free(A); free(y); return ORC_ENOMEM; }
+  for (int32_t k = 0; k < c; ++k) A[(size_t)k * c + k] = 1.0; /* A = (I - Q_CC)^T */
+  for (int32_t i = 0; i < n; ++i) {
+    const uint32_t *row = counts + (size_t)i * (size_t)(n + 1);
+    double tsum = 0.0;
+    for (int32_t j = 0; j < n; ++j) { qrow[j] = (1.0 - alpha) * (double)row[j] / (double)R; tsum += qrow[j]; }
+    double ri = alpha + (1.0 - alpha) * (double)row[n] / (double)R;
+    if (ri == 0.0 && tsum > 0.0)
+      for (int32_t j = 0; j < n; ++j) qrow[j] *= (1.0 - eta) / tsum;
+    double si = s ? s[i] : 1.0 / (double)n;
+    if (pos[i] >= 0) {
+      for (int32_t k = 0; k < c; ++k) A[(size_t)k * c + pos[i]] -= qrow[cl[k]];
+      y[pos[i]] += si;
+    } else {
+      for (int32_t k = 0; k < c; ++k) y[k] += si * qrow[cl[k]];
+    }
+  }
+  int st = orc_gauss_solve(c, A, y, 1);
+  if (st == ORC_OK) {
+    for (int32_t i = 0; i < n; ++i) mu[i] = (pos[i] >= 0) ? y[pos[i]] : (s ? s[i] : 1.0 / (double)n);
+    double T = 0.0;
+    for (int32_t i = 0; i < n; ++i) T += mu[i];
+    *expected_T = T;
+    double bf = 0.0;
+    for (int32_t i = 0; i < n; ++i) { b[i] = mu[i] / T; if (f) bf += b[i] * f[i]; }
+    if (b_f) *b_f = f ? bf : 0.0;
+  }
+  free(pos); free(cl); free(qrow); free(A); free(y);
+  return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Ranking of AFC scores: u precedes v iff b_u - b_v > tau, or |b_u - b_v| <= tau and     */
+/* u < v, with tau = tie_rel * max b.  rank[v] = #{u : u precedes v} (0 = first).          */
+/* ------------------------------------------------------------------------------------ */
+
+static int precedes(const double *b, int32_t u, int32_t v, double tau) {
+  double d = b[u] - b[v];
+  return d > tau || (fabs(d) <= tau && u < v);
+}
+
+void orc_rank(int32_t n, const double *b, double tie_rel, int32_t *rank) {
+  double bmax = 0.0;
+  for (int32_t v = 0; v < n; ++v) if (b[v] > bmax) bmax = b[v];
+  double tau = tie_rel * bmax;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t r = 0;
+    for (int32_t u = 0; u < n; ++u) if (u != v && precedes(b, u, v, tau)) r++;
+    rank[v] = r;
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Ranking certificates (Sec. 5.5): visit gap G_uv = mu_u - mu_v (eq. pm-gap); crude     */
+/* threshold 2 eps / r^2; sharpened threshold (eps / r) max_i |N_iu - N_iv| (eq.          */
+/* sharp-gap).  Q is the dense n x n nominal transient block; pairs (u[k], v[k]).         */
+/* Outputs per pair: gap[k], crude (same for all pairs), sharp[k].                        */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_certificates(int32_t n, const double *Q, const double *s, double eps_bar, double r_min,
+                     int32_t npairs, const int32_t *pu, const int32_t *pv,
+                     double *gap, double *crude, double *sharp) {
+  double *mu = (double *)malloc(sizeof(double) * (size_t)n);
+  double *b = (double *)malloc(sizeof(double) * (size_t)n);
+  double *A = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  double *Nm = (double *)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  if (!mu || !b || !A || !Nm) { free(mu); free(b); free(A); free(Nm); return ORC_ENOMEM; }
+  double T = 0.0;
+  int st = orc_afc_from_q(n, Q, s, NULL, mu, b, &T, NULL);
+  if (st == ORC_OK) {
+    /* N = (I - Q)^-1: solve (I - Q) N = I */
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t j = 0; j < n; ++j) {
+        A[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - Q[(size_t)i * n + j];
+        Nm[(size_t)i * n + j] = (i == j ? 1.0 : 0.0);
+      }
+    st = orc_gauss_solve(n, A, Nm, n);
+  }
+  if (st == ORC_OK) {
+    *crude = 2.0 * eps_bar / (r_min * r_min);
+    for (int32_t k = 0; k < npairs; ++k) {
+      int32_t u = pu[k], v = pv[k];
+      gap[k] = mu[u] - mu[v];
+      double mx = 0.0;
+      for (int32_t i = 0; i < n; ++i) {
+        double d = fabs(Nm[(size_t)i * n + u] - Nm[(size_t)i * n + v]);
+        if (d > mx) mx = d;
+      }
+      sharp[k] = eps_bar / r_min * mx;
+    }
+  }
+  free(mu); free(b); free(A); free(Nm);
+  return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Row-wise perturbation sweep (Sec. 5.1 row-wise uncertainty; Sec. 5.4 first-order      */
+/* sensitivity; Sec. 5.5 ranking reversals).  For p = 0..P-1 every row i of the nominal   */
+/* kernel is perturbed on its support J_i = {j : Q_ij > 0} plus the absorbing column:      */
+/*   z_j = 2 u_j - 1, u_j = Philox4x32-10(ctr = (j, i, p, 1), key = seed)[0] / 2^32       */
+/*   (j = n for the absorbing column);  d = z - mean(z);  d <- radius d / ||d||_1;         */
+/*   q' = max(q + d, 0);  q' <- q' / sum(q');  if q'_abs < r_min the transient part is     */
+/*   rescaled to 1 - r_min and q'_abs = r_min.                                             */
+/* Then mu' = s N', b' = mu' / mu' 1 (full solve), ranked with orc_rank.  Against the      */
+/* nominal ranking the sweep counts:                                                       */
+/*   out_counts[0] top-1 changes; [1] top-k set changes; [2] top-k order changes.          */
+/*   pair_flips[a*K2+b] (a<b<K2): perturbations where nominal ranks a and b swap order.     */
+/*   shift_hist[h]: |rank' - rank0| over the nominal top-K2 nodes, h clipped to H-1.       */
+/*   out_f64[0] = max ||b' - b0||_inf; [1] = max ||b' - (b0 + db_lin)||_inf with the       */
+/*   first-order prediction db_lin = x/T0 - b0 (x 1)/T0, x = mu0 E N0, E = Q' - Q0;         */
+/*   [2] = max over p of max_i (N' 1)_i (uniform transience bound, eq. pm-N-bound).        */
+/* Q0 is dense n x n; r0 its absorption vector.                                             */
+/* ------------------------------------------------------------------------------------ */
+
+static double perturb_uniform(uint64_t seed, uint32_t j, uint32_t i, uint32_t p) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {j, i, p, 1u};
+  uint32_t u[4];
+  orc_philox4x32_10(ctr, key, u);
+  return (double)u[0] / 4294967296.0;
+}
+
+void orc_perturb_row(int32_t n, const double *q0, double r0, uint64_t seed, uint32_t i,
+                     uint32_t p, double radius, double r_min, double *q, double *r) {
+  int32_t supp = 1;
+  for (int32_t j = 0; j < n; ++j) if (q0[j] > 0.0) supp++;
+  double zsum = 0.0;
+  for (int32_t j = 0; j < n; ++j) if (q0[j] > 0.0) zsum += 2.0 * perturb_uniform(seed, (uint32_t)j, i, p) - 1.0;
+  double zabs = 2.0 * perturb_uniform(seed, (uint32_t)n, i, p) - 1.0;
+  zsum += zabs;
+  double mean = zsum / (double)supp;
+  double l1 = 0.0;
+  for (int32_t j = 0; j < n; ++j)
+    if (q0[j] > 0.0) l1 += fabs((2.0 * perturb_uniform(seed, (uint32_t)j, i, p) - 1.0) - mean);
+  l1 += fabs(zabs - mean);
+  double scale = (l1 > 0.0) ? radius / l1 : 0.0;
+  double tot = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (q0[j] > 0.0) {
+      double d = ((2.0 * perturb_uniform(seed, (uint32_t)j, i, p) - 1.0) - mean) * scale;
+      q[j] = q0[j] + d;
+      if (q[j] < 0.0) q[j] = 0.0;
+      tot += q[j];
+    } else {
+      q[j] = 0.0;
+    }
+  }
+  double ra = r0 + (zabs - mean) * scale;
+  if (ra < 0.0) ra = 0.0;
+  tot += ra;
+  double ts = 0.0;
+  for (int32_t j = 0; j < n; ++j) { q[j] /= tot; ts += q[j]; }
+  ra /= tot;
+  if (ra < r_min) {
+    double f = (ts > 0.0) ? (1.0 - r_min) / ts : 0.0;
+    for (int32_t j = 0; j < n; ++j) q[j] *= f;
+    ra = r_min;
+  }
+  *r = ra;
+}
+
+int orc_perturb_sweep(int32_t n, const double *Q0, const double *r0, const double *s,
+                      uint32_t p_begin, uint32_t p_count, double radius, double r_min,
+                      uint64_t seed, int32_t top_k, int32_t K2, int32_t H, double tie_rel,
+                      uint64_t *out_counts, uint64_t *pair_flips, uint64_t *shift_hist,
+                      double *out_f64, double *b_out, int32_t *rank_out) {
+  size_t nn = (size_t)n;
+  double *Qp = (double *)malloc(sizeof(double) * nn * nn);
+  double *rp = (double *)malloc(sizeof(double) * nn);
+  double *mu0 = (double *)malloc(sizeof(double) * nn);
+  double *b0 = (double *)malloc(sizeof(double) * nn);
+  double *mu = (double *)malloc(sizeof(double) * nn);
+  double *b = (double *)malloc(sizeof(double) * nn);
+  double *x = (double *)malloc(sizeof(double) * nn);
+  double *A = (double *)malloc(sizeof(double) * nn * nn);
+  double *ones = (double *)malloc(sizeof(double) * nn);
+  int32_t *rank0 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *rank = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *byrank0 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int st = ORC_OK;
+  if (!Qp || !rp || !mu0 || !b0 || !mu || !b || !x || !A || !ones || !rank0 || !rank || !byrank0) {
+    st = ORC_ENOMEM; goto out;
+  }
+  double T0 = 0.0;
+  st = orc_afc_from_q(n, Q0, s, NULL, mu0, b0, &T0, NULL);
+  if (st != ORC_OK) goto out;
+  orc_rank(n, b0, tie_rel, rank0);
+  for (int32_t v = 0; v < n; ++v) byrank0[rank0[v]] = v;
+  out_counts[0] = out_counts[1] = out_counts[2] = 0;
+  out_f64[0] = out_f64[1] = out_f64[2] = 0.0;
+  for (int32_t a = 0; a < K2 * K2; ++a) pair_flips[a] = 0;
+  for (int32_t h = 0; h < H; ++h) shift_hist[h] = 0;
+  for (uint32_t k = 0; k < p_count; ++k) {
+    uint32_t p = p_begin + k;
+    for (int32_t i = 0; i < n; ++i)
+      orc_perturb_row(n, Q0 + (size_t)i * nn, r0[i], seed, (uint32_t)i, p, radius, r_min,
+                      Qp + (size_t)i * nn, rp + i);
+    double T = 0.0;
+    st = orc_afc_from_q(n, Qp, s, NULL, mu, b, &T, NULL);
+    if (st != ORC_OK) goto out;
+    /* first-order prediction: x = mu0 E, then y = x N0 (solve (I - Q0)^T y^T = x^T) */
+    for (int32_t j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int32_t i = 0; i < n; ++i) acc += mu0[i] * (Qp[(size_t)i * nn + j] - Q0[(size_t)i * nn + j]);
+      x[j] = acc;
+    }
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t j = 0; j < n; ++j)
+        A[(size_t)i * nn + j] = (i == j ? 1.0 : 0.0) - Q0[(size_t)j * nn + i];
+    st = orc_gauss_solve(n, A, x, 1);
+    if (st != ORC_OK) goto out;
+    double y1 = 0.0;
+    for (int32_t j = 0; j < n; ++j) y1 += x[j];
+    double dmax = 0.0, lmax = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+      double lin = b0[v] + x[v] / T0 - b0[v] * y1 / T0;
+      if (fabs(b[v] - b0[v]) > dmax) dmax = fabs(b[v] - b0[v]);
+      if (fabs(b[v] - lin) > lmax) lmax = fabs(b[v] - lin);
+    }
+    if (dmax > out_f64[0]) out_f64[0] = dmax;
+    if (lmax > out_f64[1]) out_f64[1] = lmax;
+    /* uniform transience: max_i (N' 1)_i, solve (I - Q') t = 1 */
+    for (int32_t i = 0; i < n; ++i) {
+      ones[i] = 1.0;
+      for (int32_t j = 0; j < n; ++j) A[(size_t)i * nn + j] = (i == j ? 1.0 : 0.0) - Qp[(size_t)i * nn + j];
+    }
+    st = orc_gauss_solve(n, A, ones, 1);
+    if (st != ORC_OK) goto out;
+    for (int32_t i = 0; i < n; ++i) if (ones[i] > out_f64[2]) out_f64[2] = ones[i];
+    /* ranking statistics against the nominal ranking */
+    orc_rank(n, b, tie_rel, rank);
+    if (b_out) for (int32_t v = 0; v < n; ++v) b_out[(size_t)k * nn + v] = b[v];
+    if (rank_out) for (int32_t v = 0; v < n; ++v) rank_out[(size_t)k * nn + v] = rank[v];
+    int32_t kk = top_k < n ? top_k : n;
+    int top1 = (rank[byrank0[0]] != 0);
+    int set_changed = 0, order_changed = 0;
+    for (int32_t a = 0; a < kk; ++a) {
+      int32_t v = byrank0[a];
+      if (rank[v] >= kk) set_changed = 1;
+      if (rank[v] != a) order_changed = 1;
+    }
+    out_counts[0] += (uint64_t)top1;
+    out_counts[1] += (uint64_t)set_changed;
+    out_counts[2] += (uint64_t)order_changed;
+    int32_t k2 = K2 < n ? K2 : n;
+    for (int32_t a = 0; a < k2; ++a)
+      for (int32_t c = a + 1; c < k2; ++c)
+        if (rank[byrank0[a]] > rank[byrank0[c]]) pair_flips[a * K2 + c]++;
+    for (int32_t a = 0; a < k2; ++a) {
+      int32_t sh = abs(rank[byrank0[a]] - a);
+      if (sh > H - 1) sh = H - 1;
+      shift_hist[sh]++;
+    }
+  }
+out:
+  free(Qp); free(rp); free(mu0); free(b0); free(mu); free(b); free(x); free(A); free(ones);
+  free(rank0); free(rank); free(byrank0);
+  return st;
+}
