@@ -1,0 +1,302 @@
+"""Benchmark of the stochastic-betweenness -> absorbing-chain path on GB300.
+
+Workload: WS(n=1000, k=6, beta=0.1) base graph (seed 102), edge failure probability 0.05,
+integer lengths uniform in {1..100}, 10,000 realizations (Philox seed 1), node reward
+f ~ U(0,1), restricted candidate pool = 100 random nodes, plain FP64 dependencies; then the
+FP64 absorbing-chain solve and 10,000 row-wise l1 perturbations of radius 0.05.
+A step is one whole query: Monte Carlo counts (A1-A6) -> solve (A8) -> perturbation sweep (A9).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  value = realizations per second over all ranks (device time,
+inputs resident in HBM, L2 flushed between steps); e2e = the same metric through the
+end-to-end host entry point with host buffers (copies inside the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("realizations/sec and GTEPS (Brandes BC+argmax) at 1 GB300 vs plain FP64; "
+          "p50/p99 query latency")
+WORKLOAD = ("ws1000: Watts-Strogatz n=1000 k=6 beta=0.1, failure 0.05, lengths {1..100}, "
+            "10000 realizations, reward U(0,1), pool 100 random nodes, FP64; "
+            "+ FP64 absorbing solve + 10000 l1 perturbations (radius 0.05)")
+# Algorithmic bytes of one source's three pull passes over its component (per alive arc:
+# SSSP 4 col + 2 len + 4 dist; sigma + 8; delta + 8 more) and per-vertex state writes.
+BYTES_PER_ARC = 54
+BYTES_PER_VERTEX = 24
+KERNELS_PER_STEP = 10  # counts 1, observed states 2, solve 5, perturbation 2
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, seconds_target=12.0, per_core=None):
+    """The oracle as it stands, on the host cores, over a bounded sample of realizations of
+    the same workload (counting stage A1-A6, which dominates the step)."""
+    import oracle as O
+    g = O.build_graph(wl.n, wl.eu, wl.ev)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.count_transitions(g, wl.seed, wl.graph_tag, 0, 1, wl.p_survive, wl.w_lo, wl.w_hi,
+                        wl.k_min, wl.candidates, wl.top_k, wl.tie_rel)
+    one = max(time.perf_counter() - t0, 1e-4)
+    if per_core is None:
+        per_core = max(1, int(seconds_target / one))
+    sample = per_core * cores
+    t0 = time.perf_counter()
+    _, _, used = O.count_transitions_parallel(g, wl.seed, wl.graph_tag, 0, sample, wl.p_survive,
+                                              wl.w_lo, wl.w_hi, wl.k_min, wl.candidates, wl.top_k,
+                                              wl.tie_rel, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": "realizations/s", "cores": used, "kind": "oracle",
+            "sample": f"realizations 0..{sample - 1} of the ws1000 counting stage (A1-A6) on "
+                      f"{used} threads; A8/A9 not included", "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from afc_inputs import workload
+    wl = workload("ws1000")
+    cores = os.cpu_count() or 1
+    per_step_core = 2
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, per_core=per_step_core)
+        if i >= args.warmup:
+            vals.append(cb)
+    tot_real = sum(v["value"] * v["seconds"] for v in vals)
+    tot_s = sum(v["seconds"] for v in vals)
+    value = tot_real / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "realizations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tot_s / max(1, len(vals)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_per_step": per_step_core * cores,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "realizations/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{per_step_core * cores} realizations per step of the "
+                                       f"ws1000 counting stage on {cores} threads"},
+            "e2e": {"value": value, "unit": "realizations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _env_rank()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+
+    wl = workload("ws1000")
+    R = wl.realizations
+    q = afc.Query(wl)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(timers=None):
+        # this rank's share: realizations [rank*R, (rank+1)*R) of the same query (weak scaling)
+        q.counts.zero_()
+        q.stats.zero_()
+        if timers is not None:
+            timers[0].record(stream)
+        afc.afc_transition_counts(q.prob, rank * R, R, q.counts, q.stats, None, None,
+                                  q.ws_counts, q.ws_counts.numel(), stream.cuda_stream)
+        if timers is not None:
+            timers[1].record(stream)
+        if dist:
+            import torch.distributed as tdist
+            tdist.all_reduce(q.counts)          # exact integer merge of the shards
+        q.wl.realizations = R * world
+        q.run_solve()
+        q.run_perturb()
+        q.wl.realizations = R
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                    # evict L2 between steps (not timed)
+        t = ev[k]
+        t[2].record(stream)
+        step(timers=(t[0], t[1]))
+        t[3].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    step_ms = [t[2].elapsed_time(t[3]) for t in ev]
+    kern_ms = [t[0].elapsed_time(t[1]) for t in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    stats = q.stats.cpu().numpy()
+    edge_visits, vertex_visits = int(stats[2]), int(stats[6])
+    value = args.steps * R * world / (total_ms / 1000.0)
+    gteps = args.steps * edge_visits * world / (total_ms / 1000.0) / 1e9
+    # roofline of the dominant kernel (counting kernel), per launch
+    kavg = sum(kern_ms) / len(kern_ms)
+    alg_bytes = BYTES_PER_ARC * 2 * edge_visits + BYTES_PER_VERTEX * vertex_visits
+    peaks, src = _peaks()
+    achieved = alg_bytes / (kavg / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": f"{src} HBM copy bandwidth",
+            "kernel": "mc_counts_kernel", "kernel_ms": kavg,
+            "model": f"{BYTES_PER_ARC} B per alive arc + {BYTES_PER_VERTEX} B per vertex per source"}
+    res = q.result() if rank == 0 else None
+
+    # end to end through the host entry point (pinned host buffers, copies inside)
+    e2e = None
+    if rank == 0:
+        bufs = afc.engine.HostBuffers(wl, pinned=True)
+        afc.run_query_host(bufs)   # warm
+        lat = []
+        for k in range(max(1, min(args.steps, 3))):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            afc.run_query_host(bufs)
+            lat.append(time.perf_counter() - t0)
+        e2e = {"value": R / statistics.mean(lat), "unit": "realizations/s",
+               "h2d_bytes_per_step": bufs.h2d_bytes, "d2h_bytes_per_step": bufs.d2h_bytes,
+               "latency_ms_p50": 1000 * statistics.median(lat),
+               "latency_ms_p99": 1000 * max(lat), "calls": len(lat)}
+
+    if rank == 0:
+        cb = None if args.no_cpu else cpu_baseline(wl)
+        line = {"metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "realizations_per_rank": R,
+                           "n_perturb": wl.n_perturb, "l2": "flushed (256 MB write) between steps",
+                           "bucket_width": int(q.prob.bucket_width) or "auto",
+                           "group_threads": int(q.prob.group_threads) or "auto"},
+                "gteps": gteps, "counts_kernel_ms": kavg,
+                "query_latency_ms_p50": statistics.median(step_ms),
+                "query_latency_ms_p99": max(step_ms),
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
+                "check": {"c": res.c, "expected_T": res.expected_T, "b_f": res.b_f,
+                          "device_error": int(stats[5]), "overflow": int(stats[3])}}
+        print(json.dumps(line))
+    if dist:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,279 @@
+/*
+ * afc.h -- C ABI of the GB300 (sm_103a) absorbing-frequency-centrality engine.
+ *
+ * The engine estimates, by Monte Carlo over sampled network realizations, the absorbing
+ * Markov chain whose states are the reported local betweenness centres of a stochastic
+ * network, and from it the absorbing-frequency centrality (AFC) and its sensitivity to
+ * row-wise perturbations of the estimated kernel ("Betweenness-Central Nodes Under
+ * Uncertainty: An Absorbing Markov Chain Approach", Bao, Kontou, Vogiatzis).
+ *
+ * Conventions for every entry point:
+ *   - Return value: AFC_OK (0) or one of the AFC_E* codes below; afc_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.  No C++ exception
+ *     crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the current device; "host"
+ *     pointers are ordinary CPU memory.  The caller owns every buffer it passes in; the
+ *     library keeps no pointer after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device entry points only
+ *     enqueue work on it unless their comment says they synchronise it.
+ *   - Node ids are 0..n-1; undirected edge e joins eu[e] and ev[e]; the absorbing state is
+ *     column n of the transition-count matrix.
+ */
+#ifndef AFC_H_
+#define AFC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFC_OK 0
+#define AFC_EINVAL 1       /* invalid argument (sizes, ranges, malformed graph)           */
+#define AFC_ENOMEM 2       /* a device or host allocation failed, or workspace too small   */
+#define AFC_EOVERFLOW 3    /* a shortest-path count exceeded 2^64 - 1 in some realization  */
+#define AFC_ESINGULAR 4    /* I - Q was numerically singular                               */
+#define AFC_ETIMEOUT 5     /* a bounded device wait expired                                */
+#define AFC_ECUDA 6        /* a CUDA runtime call failed                                   */
+#define AFC_EUNSUPPORTED 7 /* the problem exceeds an implementation limit                  */
+#define AFC_EDEVICE 8      /* a device-side consistency check failed (see message)        */
+
+#define AFC_FP64 0          /* dependencies delta accumulated in FP64                        */
+#define AFC_FP32_RECHECK 1  /* delta in FP32, realizations with a near-tied top two in FP64 */
+
+const char *afc_last_error(void);
+int afc_version(void);
+
+/* ------------------------------------------------------------------------------------ */
+/* Host helpers                                                                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* Base topology G(V, E) (Sec. 3.1) as a symmetric CSR.  Host in: eu, ev [m] (int32), each
+ * edge once, no self loops, no duplicates, 0 <= eu, ev < n.  Host out (caller-allocated):
+ * row_ptr [n+1], col [2m], eid [2m] (undirected edge id of each arc), rows sorted by col.
+ * Returns AFC_EINVAL on a malformed edge list (nothing is written in that case except
+ * possibly partial row_ptr). */
+int afc_csr_from_edges(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                       int32_t *row_ptr, int32_t *col, int32_t *eid);
+
+/* Survival threshold T = floor(p * 2^32) of an edge that survives with probability p
+ * (T = 2^32 for p >= 1, 0 for p <= 0); a realization keeps the edge iff its 32-bit draw
+ * u0 < T (Sec. 3.1 network state; independent edge availability as in Sec. 9.1). */
+uint64_t afc_survival_threshold(double p);
+
+/* ------------------------------------------------------------------------------------ */
+/* A1-A7: Monte Carlo transition counts (Alg. 1 SampleNext, Alg. 2 row-wise construction) */
+/* ------------------------------------------------------------------------------------ */
+
+/* One stochastic base graph and its one-step simulator.  All pointers are DEVICE pointers
+ * except where noted.  Realization r of graph `graph_tag` draws, for each undirected edge e,
+ * (u0, u1) = Philox4x32-10(counter = (e, r, graph_tag, 0), key = seed): the edge survives
+ * iff u0 < thresh[e] and has integer length w = w_lo[e] + floor(u1 (w_hi[e]-w_lo[e]+1) / 2^32).
+ * From realization r every anchor i moves to the tie-broken betweenness centre of its
+ * component K(i; H_r) (Sec. 3.2 eq. local-center) or to the absorbing state when
+ * |K(i; H_r)| < k_min or K(i; H_r) holds no admissible candidate (Sec. 7.1 Sel_W). */
+typedef struct {
+  int32_t n;                 /* nodes, 1 <= n <= 65535                                   */
+  int64_t m;                 /* undirected edges                                          */
+  const int32_t *row_ptr;    /* [n+1] device symmetric CSR (afc_csr_from_edges layout)   */
+  const int32_t *col;        /* [2m]  device                                              */
+  const int32_t *eid;        /* [2m]  device                                              */
+  uint64_t seed;             /* Philox key (low word, high word)                          */
+  uint32_t graph_tag;        /* third Philox counter word                                 */
+  const uint64_t *thresh;    /* [m] device survival thresholds, or NULL -> thresh_all     */
+  uint64_t thresh_all;
+  const uint32_t *w_lo;      /* [m] device, or NULL -> w_lo_all (lengths >= 1)            */
+  const uint32_t *w_hi;      /* [m] device, or NULL -> w_hi_all (w_hi >= w_lo, <= 65535)  */
+  uint32_t w_lo_all, w_hi_all;
+  uint32_t k_min;            /* component-size threshold (Sec. 3.2), >= 1                 */
+  const uint8_t *in_w;       /* [n] device candidate-pool mask W, or NULL = all nodes     */
+  uint32_t top_k;            /* 0: centre = tie-broken argmax over K cap W; k > 0: that    */
+                             /* centre must also rank within the first k of K (Sec. 7.1)  */
+  double tie_rel;            /* relative tie band: v ties the maximum B* iff              */
+                             /* B_v >= B* - tie_rel * B*; ties go to the smallest id       */
+  int32_t precision;         /* AFC_FP64 or AFC_FP32_RECHECK                              */
+  double recheck_margin;     /* FP32 mode: recompute a realization in FP64 when some valid */
+                             /* component's top-two gap (B1 - B2) / B1 < recheck_margin    */
+  uint32_t bucket_width;     /* SSSP bucket width (Delta); 0 = automatic                  */
+  int32_t group_threads;     /* threads cooperating on one source: 32, 64 or 128; 0 = auto */
+} afc_mc_problem;
+
+/* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */
+typedef struct {
+  uint64_t realizations;     /* realizations processed                                    */
+  uint64_t sources;          /* single-source shortest-path problems solved               */
+  uint64_t edge_visits;      /* sum over solved sources of the alive edges of the source's */
+                             /* component (Graph500 TEPS numerator, edges once)            */
+  uint64_t overflow;         /* realizations with a path count above 2^64 - 1              */
+  uint64_t rechecked;        /* FP32 mode: realizations recomputed in FP64                */
+  uint64_t device_error;     /* bit mask of device consistency failures (0 = none)         */
+  uint64_t vertex_visits;    /* sum over solved sources of the size of the source's component */
+} afc_mc_stats;
+
+/* Bytes of device workspace afc_transition_counts needs for this problem (0 when the whole
+ * per-realization state fits in shared memory). */
+size_t afc_transition_counts_workspace(const afc_mc_problem *prob);
+
+/* Adds the outcomes of realizations r_begin .. r_begin + r_count - 1 to counts, a DEVICE
+ * uint32 matrix [n][n+1] in row-major order (column n = absorption).  counts is accumulated,
+ * not cleared, so disjoint realization ranges (shards, resumed runs) sum bit-exactly.
+ * stats: DEVICE afc_mc_stats (accumulated), or NULL.  dump_bc: DEVICE double [r_count][n]
+ * receiving each realization's betweenness B_v(H_r) over ordered pairs for nodes of valid
+ * components (0 elsewhere), or NULL; dump_next: DEVICE int32 [r_count][n] receiving each
+ * anchor's next state (n = absorbed), or NULL.  workspace: DEVICE, at least
+ * afc_transition_counts_workspace(prob) bytes (may be NULL when that is 0).
+ * Asynchronous on `stream`; argument errors are returned before anything is enqueued. */
+int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
+                          uint32_t *counts, afc_mc_stats *stats, double *dump_bc,
+                          int32_t *dump_next, void *workspace, size_t workspace_bytes,
+                          void *stream);
+
+/* Several base graphs in one persistent launch (the batched mix).  probs: HOST array of
+ * nprob problems; r_count: HOST [nprob]; counts: HOST array of nprob DEVICE count matrices;
+ * stats: DEVICE afc_mc_stats [nprob] or NULL.  workspace: DEVICE, at least
+ * afc_transition_counts_batched_workspace(...) bytes.  Realization r of problem g is exactly
+ * the realization r of afc_transition_counts on that problem alone. */
+size_t afc_transition_counts_batched_workspace(int32_t nprob, const afc_mc_problem *probs,
+                                               const uint32_t *r_count);
+int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
+                                  const uint32_t *r_count, uint32_t *const *counts,
+                                  afc_mc_stats *stats, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+/* Parity hooks for single steps of the same kernels (DEVICE outputs):
+ *   afc_debug_realize: alive [r_count][m] (uint8), w [r_count][m] (uint32) for A1.
+ *   afc_debug_components: comp [r_count][n] (smallest id of the component), csize.
+ *   afc_debug_sssp: realization r, sources[nsrc] (DEVICE int32): dist [nsrc][n] (uint32,
+ *     0xFFFFFFFF = unreachable) and sigma [nsrc][n] (uint64) from the production SSSP and
+ *     path-counting code, run on every source's whole component. */
+int afc_debug_realize(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
+                      uint8_t *alive, uint32_t *w, void *stream);
+int afc_debug_components(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
+                         int32_t *comp, int32_t *csize, void *stream);
+int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *sources, int32_t nsrc,
+                   uint32_t *dist, uint64_t *sigma, afc_mc_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* A8: kernel assembly and the absorbing-chain solve (Sec. 4 eqs. fundamental, visits,    */
+/* expected-length, afc-def; Sec. 6.4 eq. mr-inner-product; Sec. 8.2 stabilisation)        */
+/* ------------------------------------------------------------------------------------ */
+
+/* Q_ij = (1 - alpha) counts_ij / R and r_i = alpha + (1 - alpha) counts_i,n / R; a row with
+ * r_i = 0 (possible only for alpha = 0) gets r_i = absorb_floor and its transient part
+ * rescaled to 1 - absorb_floor. */
+typedef struct {
+  int32_t n;
+  uint32_t realizations;     /* R: the row sum of every count row                         */
+  double alpha;              /* exogenous per-step stop probability (Sec. 4)               */
+  double absorb_floor;       /* eta                                                        */
+  const double *s_init;      /* [n] DEVICE initial law, or NULL = uniform                  */
+  const double *reward;      /* [n] DEVICE node values f, or NULL                          */
+} afc_chain;
+
+/* Observed centre states C = {j : counts_ij > 0 for some i} (DEVICE outputs c_index [n]:
+ * position of j in C or -1; c_list [n]: the members of C in increasing id).  Writes |C| to
+ * *c_host (HOST) and SYNCHRONISES `stream`. */
+int afc_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index, int32_t *c_list,
+                        int32_t *c_host, void *stream);
+
+/* Device workspace of afc_absorbing_solve / afc_perturb_sweep / afc_certificates. */
+size_t afc_solve_workspace(int32_t n, int32_t c);
+
+/* AFC from the counts by the reduced solve on C: with the columns of U = V \ C zero,
+ * mu_U = s_U and mu_C (I - Q_CC) = s_C + s_U Q_UC, solved by FP64 LU with partial pivoting.
+ * DEVICE outputs: mu [n], b [n] = mu / (mu 1), scalars [4] = {E_s[T], b_f = b.f (0 without a
+ * reward), max_i (N 1)_i (largest expected absorption time over start nodes), |C|},
+ * lu [c*c] and piv [c]: the LU factors of (I - Q_CC) (kept for afc_perturb_sweep and
+ * afc_certificates).  Returns AFC_ESINGULAR (after synchronising) if a pivot vanished. */
+int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const int32_t *c_index,
+                        const int32_t *c_list, int32_t c, double *mu, double *b, double *scalars,
+                        double *lu, int32_t *piv, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* A9: row-wise perturbation sweep (Sec. 5.1 uncertainty set, Sec. 5.4 first-order        */
+/* sensitivity, Sec. 5.5 ranking reversals and certificates)                               */
+/* ------------------------------------------------------------------------------------ */
+
+/* Perturbation p (p_begin <= p < p_begin + p_count) moves every row i of the estimated kernel
+ * on its support J_i = {j : Q_ij > 0} plus the absorbing column: z_j = 2u - 1 with
+ * u = Philox4x32-10(counter = (j, i, p, 1), key = seed)[0] / 2^32 (j = n for absorption),
+ * d = z - mean(z), d <- l1_radius d / ||d||_1, q' = max(q + d, 0), q' <- q' / sum(q'), and
+ * if q'_abs < r_min the transient part is scaled to 1 - r_min.  The perturbed AFC b' is then
+ * ranked (u before v iff b'_u - b'_v > tie_rel max b', or within that band and u < v) and
+ * compared with the nominal ranking. */
+typedef struct {
+  uint32_t p_begin, p_count;
+  double l1_radius;          /* 0.05 */
+  double r_min;              /* leak lower bound r_min (Sec. 5.1)                          */
+  uint64_t seed;
+  int32_t top_k;             /* k of the Top-k set / order statistics (5)                  */
+  int32_t k2;                /* nominal top-k2 nodes tracked for pair flips / shifts (10)  */
+  int32_t hist_bins;         /* bins of the rank-shift histogram (16)                      */
+  double tie_rel;
+} afc_perturb_params;
+
+/* DEVICE outputs (accumulated, caller zeroes): counters [3] = {top-1 changes, top-k set
+ * changes, top-k order changes}; pair_flips [k2*k2] (entry a*k2+b, a<b: perturbations where
+ * nominal ranks a and b swap); shift_hist [hist_bins] (|rank' - rank| of the nominal top-k2
+ * nodes, last bin open); maxima [3] = {max ||b' - b||_inf, max ||b' - (b + db_lin)||_inf with
+ * the first-order prediction db_lin, max_i (N' 1)_i} as non-negative doubles (updated with
+ * an integer max on their bit patterns).  b_out: DEVICE [p_count][n] or NULL.  b0, mu0, lu0,
+ * piv0: the nominal afc_absorbing_solve outputs. */
+int afc_perturb_sweep(const afc_chain *chain, const afc_perturb_params *pp,
+                      const uint32_t *counts, const int32_t *c_index, const int32_t *c_list,
+                      int32_t c, const double *mu0, const double *b0, const double *lu0,
+                      const int32_t *piv0, uint64_t *counters, uint64_t *pair_flips,
+                      uint64_t *shift_hist, double *maxima, double *b_out, void *workspace,
+                      size_t workspace_bytes, void *stream);
+
+/* Ranking certificates (Sec. 5.5): for pairs (pu[k], pv[k]) (DEVICE int32 [npairs]) writes
+ * gap[k] = mu_u - mu_v (eq. pm-gap) and sharp[k] = (eps_bar / r_min) max_i |N_iu - N_iv|
+ * (eq. sharp-gap) to DEVICE arrays; the crude threshold is 2 eps_bar / r_min^2. */
+int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32_t *c_index,
+                     const int32_t *c_list, int32_t c, const double *mu0, const double *lu0,
+                     const int32_t *piv0, double eps_bar, double r_min, int32_t npairs,
+                     const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* End-to-end query from HOST memory                                                      */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t n; int64_t m;
+  const int32_t *eu, *ev;            /* HOST edge list                                     */
+  const double *p_survive;           /* HOST [m] or NULL -> p_survive_all                   */
+  double p_survive_all;
+  const uint32_t *w_lo, *w_hi;       /* HOST [m] or NULL -> the scalars                     */
+  uint32_t w_lo_all, w_hi_all;
+  uint64_t seed; uint32_t graph_tag; uint32_t realizations;
+  uint32_t k_min; double alpha; double absorb_floor;
+  const double *s_init;              /* HOST [n] or NULL                                    */
+  const double *reward;              /* HOST [n] or NULL                                    */
+  const int32_t *candidates; int32_t n_candidates;   /* HOST W or NULL                      */
+  uint32_t top_k; double tie_rel; int32_t precision; double recheck_margin;
+  uint32_t n_perturb; double l1_radius; double r_min; uint64_t perturb_seed;
+} afc_host_query;
+
+typedef struct {
+  uint32_t *counts;                  /* HOST [n][n+1] or NULL                               */
+  double *mu, *b;                    /* HOST [n] (b required)                               */
+  double expected_T, b_f, max_rowsum_N;
+  int32_t c;                         /* |C|                                                 */
+  afc_mc_stats stats;
+  uint64_t perturb_counters[3];      /* as afc_perturb_sweep with top_k 5, k2 10, 16 bins   */
+  double perturb_maxima[3];
+  double device_ms;                  /* device time of the query (CUDA events)              */
+} afc_host_result;
+
+/* Runs the whole query: CSR build, host-to-device copies, counts, solve and (n_perturb > 0)
+ * the perturbation sweep, then device-to-host copies.  Allocates and frees its own device
+ * memory (stream-ordered) and SYNCHRONISES `stream` before returning. */
+int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFC_H_ */

@@ -1,0 +1,258 @@
+"""Python binding of the GB300 absorbing-frequency-centrality engine (``include/afc.h``).
+
+Every ``afc_*`` function here has the name and argument order of the C entry point it wraps
+and only marshals arguments (integers, doubles, raw device or host addresses, the CUDA stream
+handle); all computation runs in the library's sm_103a kernels.  PyTorch, where used by the
+helpers at the bottom, only provides device memory and streams.
+
+The shared library is built in-tree (``_build/libafc.so``) by ``build.py``; importing this
+package raises if it is missing and cannot be built, so nothing silently falls back to CPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "AfcError", "lib", "McProblem", "McStats", "Chain", "PerturbParams", "HostQuery", "HostResult",
+    "afc_last_error", "afc_version", "afc_csr_from_edges", "afc_survival_threshold",
+    "afc_transition_counts_workspace", "afc_transition_counts",
+    "afc_transition_counts_batched_workspace", "afc_transition_counts_batched",
+    "afc_debug_realize", "afc_debug_components", "afc_debug_sssp", "afc_observed_states",
+    "afc_solve_workspace", "afc_absorbing_solve", "afc_perturb_sweep", "afc_certificates",
+    "afc_run_host", "AFC_FP64", "AFC_FP32_RECHECK",
+]
+
+AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
+AFC_ETIMEOUT, AFC_ECUDA, AFC_EUNSUPPORTED, AFC_EDEVICE = 5, 6, 7, 8
+AFC_FP64, AFC_FP32_RECHECK = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+c_i32, c_i64, c_u32, c_u64, c_f64, c_p, c_sz = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                                ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
+                                                ctypes.c_size_t)
+
+
+class AfcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"afc error {code}: {msg}")
+        self.code = code
+
+
+class McProblem(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("m", c_i64), ("row_ptr", c_p), ("col", c_p), ("eid", c_p),
+                ("seed", c_u64), ("graph_tag", c_u32), ("thresh", c_p), ("thresh_all", c_u64),
+                ("w_lo", c_p), ("w_hi", c_p), ("w_lo_all", c_u32), ("w_hi_all", c_u32),
+                ("k_min", c_u32), ("in_w", c_p), ("top_k", c_u32), ("tie_rel", c_f64),
+                ("precision", c_i32), ("recheck_margin", c_f64), ("bucket_width", c_u32),
+                ("group_threads", c_i32)]
+
+
+class McStats(ctypes.Structure):
+    _fields_ = [("realizations", c_u64), ("sources", c_u64), ("edge_visits", c_u64),
+                ("overflow", c_u64), ("rechecked", c_u64), ("device_error", c_u64),
+                ("vertex_visits", c_u64)]
+
+
+class Chain(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("realizations", c_u32), ("alpha", c_f64), ("absorb_floor", c_f64),
+                ("s_init", c_p), ("reward", c_p)]
+
+
+class PerturbParams(ctypes.Structure):
+    _fields_ = [("p_begin", c_u32), ("p_count", c_u32), ("l1_radius", c_f64), ("r_min", c_f64),
+                ("seed", c_u64), ("top_k", c_i32), ("k2", c_i32), ("hist_bins", c_i32),
+                ("tie_rel", c_f64)]
+
+
+class HostQuery(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("m", c_i64), ("eu", c_p), ("ev", c_p), ("p_survive", c_p),
+                ("p_survive_all", c_f64), ("w_lo", c_p), ("w_hi", c_p), ("w_lo_all", c_u32),
+                ("w_hi_all", c_u32), ("seed", c_u64), ("graph_tag", c_u32),
+                ("realizations", c_u32), ("k_min", c_u32), ("alpha", c_f64),
+                ("absorb_floor", c_f64), ("s_init", c_p), ("reward", c_p), ("candidates", c_p),
+                ("n_candidates", c_i32), ("top_k", c_u32), ("tie_rel", c_f64),
+                ("precision", c_i32), ("recheck_margin", c_f64), ("n_perturb", c_u32),
+                ("l1_radius", c_f64), ("r_min", c_f64), ("perturb_seed", c_u64)]
+
+
+class HostResult(ctypes.Structure):
+    _fields_ = [("counts", c_p), ("mu", c_p), ("b", c_p), ("expected_T", c_f64), ("b_f", c_f64),
+                ("max_rowsum_N", c_f64), ("c", c_i32), ("stats", McStats),
+                ("perturb_counters", c_u64 * 3), ("perturb_maxima", c_f64 * 3),
+                ("device_ms", c_f64)]
+
+
+_SIGS = {
+    "afc_last_error": ([], ctypes.c_char_p),
+    "afc_version": ([], ctypes.c_int),
+    "afc_csr_from_edges": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "afc_survival_threshold": ([c_f64], c_u64),
+    "afc_transition_counts_workspace": ([ctypes.POINTER(McProblem)], c_sz),
+    "afc_transition_counts": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p, c_p, c_p,
+                               c_sz, c_p], ctypes.c_int),
+    "afc_transition_counts_batched_workspace": ([c_i32, ctypes.POINTER(McProblem), c_p], c_sz),
+    "afc_transition_counts_batched": ([c_i32, ctypes.POINTER(McProblem), c_p, c_p, c_p, c_p, c_sz,
+                                       c_p], ctypes.c_int),
+    "afc_debug_realize": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p], ctypes.c_int),
+    "afc_debug_components": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p],
+                             ctypes.c_int),
+    "afc_debug_sssp": ([ctypes.POINTER(McProblem), c_u32, c_p, c_i32, c_p, c_p, c_p, c_p],
+                       ctypes.c_int),
+    "afc_observed_states": ([c_i32, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "afc_solve_workspace": ([c_i32, c_i32], c_sz),
+    "afc_absorbing_solve": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p, c_p,
+                             c_p, c_sz, c_p], ctypes.c_int),
+    "afc_perturb_sweep": ([ctypes.POINTER(Chain), ctypes.POINTER(PerturbParams), c_p, c_p, c_p,
+                           c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_sz, c_p],
+                          ctypes.c_int),
+    "afc_certificates": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_f64,
+                          c_f64, c_i32, c_p, c_p, c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
+    "afc_run_host": ([ctypes.POINTER(HostQuery), ctypes.POINTER(HostResult), c_p], ctypes.c_int),
+}
+
+
+def lib():
+    """Loads (building first if stale) the in-tree sm_103a library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build.stale():
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing and could not be built")
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _chk(code: int):
+    if code != AFC_OK:
+        raise AfcError(code, afc_last_error())
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+# ---- thin wrappers (same names as the C ABI) ------------------------------------------------
+
+def afc_last_error() -> str:
+    return (lib().afc_last_error() or b"").decode()
+
+
+def afc_version() -> int:
+    return lib().afc_version()
+
+
+def afc_csr_from_edges(n, m, eu, ev, row_ptr, col, eid):
+    _chk(lib().afc_csr_from_edges(n, m, _ptr(eu), _ptr(ev), _ptr(row_ptr), _ptr(col), _ptr(eid)))
+
+
+def afc_survival_threshold(p: float) -> int:
+    return int(lib().afc_survival_threshold(float(p)))
+
+
+def afc_transition_counts_workspace(prob: McProblem) -> int:
+    return int(lib().afc_transition_counts_workspace(ctypes.byref(prob)))
+
+
+def afc_transition_counts(prob, r_begin, r_count, counts, stats, dump_bc, dump_next, workspace,
+                          workspace_bytes, stream):
+    _chk(lib().afc_transition_counts(ctypes.byref(prob), r_begin, r_count, _ptr(counts),
+                                     _ptr(stats), _ptr(dump_bc), _ptr(dump_next), _ptr(workspace),
+                                     workspace_bytes, _ptr(stream)))
+
+
+def afc_transition_counts_batched_workspace(nprob, probs, r_count) -> int:
+    return int(lib().afc_transition_counts_batched_workspace(nprob, probs, _ptr(r_count)))
+
+
+def afc_transition_counts_batched(nprob, probs, r_count, counts, stats, workspace, workspace_bytes,
+                                  stream):
+    _chk(lib().afc_transition_counts_batched(nprob, probs, _ptr(r_count), _ptr(counts), _ptr(stats),
+                                             _ptr(workspace), workspace_bytes, _ptr(stream)))
+
+
+def afc_debug_realize(prob, r_begin, r_count, alive, w, stream):
+    _chk(lib().afc_debug_realize(ctypes.byref(prob), r_begin, r_count, _ptr(alive), _ptr(w),
+                                 _ptr(stream)))
+
+
+def afc_debug_components(prob, r_begin, r_count, comp, csize, stream):
+    _chk(lib().afc_debug_components(ctypes.byref(prob), r_begin, r_count, _ptr(comp), _ptr(csize),
+                                    _ptr(stream)))
+
+
+def afc_debug_sssp(prob, r, sources, nsrc, dist, sigma, stats, stream):
+    _chk(lib().afc_debug_sssp(ctypes.byref(prob), r, _ptr(sources), nsrc, _ptr(dist), _ptr(sigma),
+                              _ptr(stats), _ptr(stream)))
+
+
+def afc_observed_states(n, counts, c_index, c_list, stream) -> int:
+    c = ctypes.c_int32(0)
+    _chk(lib().afc_observed_states(n, _ptr(counts), _ptr(c_index), _ptr(c_list),
+                                   ctypes.addressof(c), _ptr(stream)))
+    return c.value
+
+
+def afc_solve_workspace(n, c) -> int:
+    return int(lib().afc_solve_workspace(n, c))
+
+
+def afc_absorbing_solve(chain, counts, c_index, c_list, c, mu, b, scalars, lu, piv, workspace,
+                        workspace_bytes, stream):
+    _chk(lib().afc_absorbing_solve(ctypes.byref(chain), _ptr(counts), _ptr(c_index), _ptr(c_list), c,
+                                   _ptr(mu), _ptr(b), _ptr(scalars), _ptr(lu), _ptr(piv),
+                                   _ptr(workspace), workspace_bytes, _ptr(stream)))
+
+
+def afc_perturb_sweep(chain, pp, counts, c_index, c_list, c, mu0, b0, lu0, piv0, counters,
+                      pair_flips, shift_hist, maxima, b_out, workspace, workspace_bytes, stream):
+    _chk(lib().afc_perturb_sweep(ctypes.byref(chain), ctypes.byref(pp), _ptr(counts), _ptr(c_index),
+                                 _ptr(c_list), c, _ptr(mu0), _ptr(b0), _ptr(lu0), _ptr(piv0),
+                                 _ptr(counters), _ptr(pair_flips), _ptr(shift_hist), _ptr(maxima),
+                                 _ptr(b_out), _ptr(workspace), workspace_bytes, _ptr(stream)))
+
+
+def afc_certificates(chain, counts, c_index, c_list, c, mu0, lu0, piv0, eps_bar, r_min, npairs, pu,
+                     pv, gap, sharp, workspace, workspace_bytes, stream):
+    _chk(lib().afc_certificates(ctypes.byref(chain), _ptr(counts), _ptr(c_index), _ptr(c_list), c,
+                                _ptr(mu0), _ptr(lu0), _ptr(piv0), eps_bar, r_min, npairs, _ptr(pu),
+                                _ptr(pv), _ptr(gap), _ptr(sharp), _ptr(workspace), workspace_bytes,
+                                _ptr(stream)))
+
+
+def afc_run_host(query: HostQuery, result: HostResult, stream):
+    _chk(lib().afc_run_host(ctypes.byref(query), ctypes.byref(result), _ptr(stream)))
+
+
+# ---- helpers over torch device memory -------------------------------------------------------
+
+from .engine import (DeviceGraph, Query, QueryResult, run_query, run_query_host,  # noqa: E402
+                     make_problem)
+
+__all__ += ["DeviceGraph", "Query", "QueryResult", "run_query", "run_query_host", "make_problem"]

@@ -1,0 +1,599 @@
+// abi.cu -- host side of the C ABI declared in include/afc.h: argument validation, launch
+// configuration (shared-memory layout, thread groups, bucket width), the stream-ordered
+// end-to-end query path and the bucket-width / group-size autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "afc.h"
+#include "afc_internal.h"
+
+using namespace afc;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(AFC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define AFC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+struct DevInfo {
+  int sms = 0, smem_optin = 0;
+};
+
+DevInfo dev_info() {
+  DevInfo d;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return d;
+}
+
+uint32_t auto_delta(const afc_mc_problem &p) {
+  if (p.bucket_width) return p.bucket_width;
+  const double lo = p.w_lo ? 1.0 : (double)p.w_lo_all;
+  const double hi = p.w_hi ? 100.0 : (double)p.w_hi_all;
+  const double mean = 0.5 * (lo + hi);
+  return (uint32_t)std::max(1.0, std::floor(mean / 3.0));
+}
+
+int auto_group(const afc_mc_problem &p) {
+  if (p.group_threads) return p.group_threads;
+  return p.n >= 256 ? 64 : 32;
+}
+
+int validate(const afc_mc_problem *p) {
+  if (!p) return fail(AFC_EINVAL, "null problem");
+  if (p->n < 1 || p->n > 32767) return fail(AFC_EUNSUPPORTED, "n = %d outside [1, 32767]", p->n);
+  if (p->m < 0 || p->m > 0x3FFFFFFF) return fail(AFC_EINVAL, "m = %lld out of range", (long long)p->m);
+  if (!p->row_ptr || (p->m > 0 && (!p->col || !p->eid)))
+    return fail(AFC_EINVAL, "CSR pointers missing");
+  if (!p->w_lo && (p->w_lo_all < 1 || p->w_lo_all > 65535)) return fail(AFC_EINVAL, "w_lo_all must be in [1, 65535]");
+  if (!p->w_hi && (p->w_hi_all < 1 || p->w_hi_all > 65535)) return fail(AFC_EINVAL, "w_hi_all must be in [1, 65535]");
+  if (!p->w_lo && !p->w_hi && p->w_hi_all < p->w_lo_all) return fail(AFC_EINVAL, "w_hi_all < w_lo_all");
+  if (!p->thresh && p->thresh_all > (1ull << 32)) return fail(AFC_EINVAL, "thresh_all > 2^32");
+  if (p->k_min < 1) return fail(AFC_EINVAL, "k_min must be >= 1");
+  if (!(p->tie_rel >= 0.0) || p->tie_rel >= 1.0) return fail(AFC_EINVAL, "tie_rel must be in [0, 1)");
+  if (p->precision != AFC_FP64 && p->precision != AFC_FP32_RECHECK) return fail(AFC_EINVAL, "bad precision");
+  if (p->precision == AFC_FP32_RECHECK && !(p->recheck_margin >= 0.0)) return fail(AFC_EINVAL, "bad recheck_margin");
+  const int G = auto_group(*p);
+  if (G != 32 && G != 64 && G != 128) return fail(AFC_EINVAL, "group_threads must be 32, 64 or 128");
+  if (p->bucket_width > 0x7FFFFFFF) return fail(AFC_EINVAL, "bucket_width too large");
+  return AFC_OK;
+}
+
+McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc_stats *stats,
+             double *dump_bc, int32_t *dump_next) {
+  McDev d{};
+  d.n = p.n;
+  d.m = p.m;
+  d.row_ptr = p.row_ptr;
+  d.col = p.col;
+  d.eid = p.eid;
+  d.key_lo = (uint32_t)p.seed;
+  d.key_hi = (uint32_t)(p.seed >> 32);
+  d.graph_tag = p.graph_tag;
+  d.thresh = p.thresh;
+  d.thresh_all = p.thresh_all;
+  d.w_lo = p.w_lo;
+  d.w_hi = p.w_hi;
+  d.w_lo_all = p.w_lo_all;
+  d.w_hi_all = p.w_hi_all;
+  d.k_min = p.k_min;
+  d.in_w = p.in_w;
+  d.top_k = p.top_k;
+  d.tie_rel = p.tie_rel;
+  d.precision = p.precision;
+  d.recheck_margin = p.recheck_margin;
+  d.delta = auto_delta(p);
+  d.r_begin = r_begin;
+  d.counts = counts;
+  d.stats = stats;
+  d.dump_bc = dump_bc;
+  d.dump_next = dump_next;
+  return d;
+}
+
+// Launch plan of the counting kernel for a set of problems.
+struct McPlan {
+  int G = 64;
+  uint32_t ngroups = 1, smem = 0, grid = 1, slab = 0;
+  bool global_slab = false;
+  size_t ws_meta = 0, ws_total = 0;
+};
+
+McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items) {
+  const DevInfo d = dev_info();
+  McPlan pl;
+  pl.G = auto_group(probs[0]);
+  uint32_t nmax = 1;
+  uint64_t amax = 1;
+  for (int g = 0; g < nprob; ++g) {
+    nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
+    amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
+  }
+  const uint32_t base = mc_layout_bytes(nmax, amax, 0);
+  const uint32_t one = mc_layout_bytes(nmax, amax, 1) - base;
+  const uint32_t cap = (uint32_t)std::max(0, d.smem_optin - 1024);
+  const uint32_t by_threads = 1024u / (uint32_t)pl.G;
+  uint32_t want = std::min<uint32_t>(kMaxGroups, by_threads);
+  // small graphs: do not spread few sources over many groups
+  want = std::min<uint32_t>(want, std::max<uint32_t>(1u, (nmax + 7) / 8));
+  if (base + one <= cap) {
+    pl.ngroups = std::min<uint32_t>(want, (cap - base) / one);
+    pl.smem = mc_layout_bytes(nmax, amax, pl.ngroups);
+    pl.global_slab = false;
+    int per_sm = 1;
+    // estimate CTAs per SM from shared memory and threads
+    const uint32_t smem_sm = 228u * 1024u;
+    per_sm = (int)std::max<uint32_t>(1u, std::min<uint32_t>(smem_sm / (pl.smem + 1024u),
+                                                             2048u / (pl.ngroups * pl.G)));
+    pl.grid = (uint32_t)std::min<uint64_t>(total_items, (uint64_t)d.sms * per_sm);
+  } else {
+    pl.ngroups = want;
+    pl.slab = mc_layout_bytes(nmax, amax, pl.ngroups);
+    pl.smem = (uint32_t)sizeof(CtaCtl) + 64;
+    pl.global_slab = true;
+    pl.grid = (uint32_t)std::min<uint64_t>(total_items, (uint64_t)d.sms);
+  }
+  if (pl.grid == 0) pl.grid = 1;
+  pl.ws_meta = ((sizeof(McDev) * (size_t)nprob + sizeof(uint64_t) * (size_t)(nprob + 1)) + 255) & ~size_t(255);
+  pl.ws_total = pl.ws_meta + (pl.global_slab ? (size_t)pl.grid * pl.slab : 0);
+  return pl;
+}
+
+int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
+               const uint32_t *r_count, uint32_t *const *counts, afc_mc_stats *stats,
+               double *dump_bc, int32_t *dump_next, void *workspace, size_t ws_bytes,
+               cudaStream_t stream) {
+  for (int g = 0; g < nprob; ++g) {
+    int st = validate(&probs[g]);
+    if (st) return st;
+    if (auto_group(probs[g]) != auto_group(probs[0]))
+      return fail(AFC_EINVAL, "all problems of a batch must use the same group_threads");
+    if (!counts[g]) return fail(AFC_EINVAL, "counts[%d] is null", g);
+  }
+  std::vector<McDev> devs(nprob);
+  std::vector<uint64_t> prefix(nprob + 1, 0);
+  for (int g = 0; g < nprob; ++g) {
+    devs[g] = to_dev(probs[g], r_begin ? r_begin[g] : 0u, counts[g], stats ? stats + g : nullptr,
+                     nprob == 1 ? dump_bc : nullptr, nprob == 1 ? dump_next : nullptr);
+    prefix[g + 1] = prefix[g] + r_count[g];
+  }
+  const uint64_t total = prefix[nprob];
+  if (total == 0) return AFC_OK;
+  const McPlan pl = plan_counts(nprob, probs, total);
+  if (!workspace || ws_bytes < pl.ws_total)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", ws_bytes, pl.ws_total);
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  McDev *devs_d = reinterpret_cast<McDev *>(ws);
+  uint64_t *prefix_d = reinterpret_cast<uint64_t *>(ws + sizeof(McDev) * (size_t)nprob);
+  AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)nprob, cudaMemcpyHostToDevice, stream));
+  AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(nprob + 1), cudaMemcpyHostToDevice, stream));
+  cudaError_t e = launch_mc_counts(pl.G, devs_d, nprob, prefix_d, total,
+                                   pl.global_slab ? ws + pl.ws_meta : nullptr, pl.slab, pl.ngroups,
+                                   pl.smem, pl.grid, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
+  return AFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *afc_last_error(void) { return g_err.c_str(); }
+
+int afc_version(void) { return 10000; }
+
+int afc_csr_from_edges(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t *row_ptr,
+                       int32_t *col, int32_t *eid) {
+  if (n < 0 || m < 0 || !row_ptr || (m > 0 && (!eu || !ev || !col || !eid)))
+    return fail(AFC_EINVAL, "bad arguments");
+  if (2 * m > 0x7FFFFFFF) return fail(AFC_EUNSUPPORTED, "too many edges");
+  for (int64_t e = 0; e < m; ++e)
+    if (eu[e] < 0 || eu[e] >= n || ev[e] < 0 || ev[e] >= n || eu[e] == ev[e])
+      return fail(AFC_EINVAL, "edge %lld = (%d, %d) invalid", (long long)e, eu[e], ev[e]);
+  std::vector<int32_t> deg((size_t)n + 1, 0);
+  for (int64_t e = 0; e < m; ++e) { deg[eu[e]]++; deg[ev[e]]++; }
+  row_ptr[0] = 0;
+  for (int32_t v = 0; v < n; ++v) row_ptr[v + 1] = row_ptr[v] + deg[v];
+  std::vector<int32_t> fill(row_ptr, row_ptr + n);
+  for (int64_t e = 0; e < m; ++e) {
+    const int32_t a = eu[e], b = ev[e];
+    col[fill[a]] = b; eid[fill[a]++] = (int32_t)e;
+    col[fill[b]] = a; eid[fill[b]++] = (int32_t)e;
+  }
+  std::vector<std::pair<int32_t, int32_t>> row;
+  for (int32_t v = 0; v < n; ++v) {
+    row.clear();
+    for (int32_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) row.emplace_back(col[a], eid[a]);
+    std::sort(row.begin(), row.end());
+    for (size_t k = 0; k < row.size(); ++k) {
+      if (k > 0 && row[k].first == row[k - 1].first)
+        return fail(AFC_EINVAL, "duplicate edge (%d, %d)", v, row[k].first);
+      col[row_ptr[v] + k] = row[k].first;
+      eid[row_ptr[v] + k] = row[k].second;
+    }
+  }
+  return AFC_OK;
+}
+
+uint64_t afc_survival_threshold(double p) {
+  if (!(p > 0.0)) return 0;
+  if (p >= 1.0) return 1ull << 32;
+  return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+size_t afc_transition_counts_workspace(const afc_mc_problem *prob) {
+  if (validate(prob)) return 0;
+  return plan_counts(1, prob, 1u << 20).ws_total;
+}
+
+int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
+                          uint32_t *counts, afc_mc_stats *stats, double *dump_bc,
+                          int32_t *dump_next, void *workspace, size_t workspace_bytes,
+                          void *stream) {
+  if (!prob) return fail(AFC_EINVAL, "null problem");
+  uint32_t *cs[1] = {counts};
+  return run_counts(1, prob, &r_begin, &r_count, cs, stats, dump_bc, dump_next, workspace,
+                    workspace_bytes, (cudaStream_t)stream);
+}
+
+size_t afc_transition_counts_batched_workspace(int32_t nprob, const afc_mc_problem *probs,
+                                               const uint32_t *r_count) {
+  if (nprob <= 0 || !probs || !r_count) return 0;
+  for (int g = 0; g < nprob; ++g)
+    if (validate(&probs[g])) return 0;
+  uint64_t total = 0;
+  for (int g = 0; g < nprob; ++g) total += r_count[g];
+  return plan_counts(nprob, probs, std::max<uint64_t>(total, 1)).ws_total;
+}
+
+int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
+                                  const uint32_t *r_count, uint32_t *const *counts,
+                                  afc_mc_stats *stats, void *workspace, size_t workspace_bytes,
+                                  void *stream) {
+  if (nprob <= 0 || !probs || !r_count || !counts) return fail(AFC_EINVAL, "bad batch arguments");
+  return run_counts(nprob, probs, nullptr, r_count, counts, stats, nullptr, nullptr, workspace,
+                    workspace_bytes, (cudaStream_t)stream);
+}
+
+int afc_debug_realize(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count, uint8_t *alive,
+                      uint32_t *w, void *stream) {
+  int st = validate(prob);
+  if (st) return st;
+  if (!alive || !w) return fail(AFC_EINVAL, "null output");
+  McDev d = to_dev(*prob, r_begin, nullptr, nullptr, nullptr, nullptr);
+  cudaError_t e = launch_debug_realize(d, r_count, alive, w, (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_realize");
+}
+
+int afc_debug_components(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
+                         int32_t *comp, int32_t *csize, void *stream) {
+  int st = validate(prob);
+  if (st) return st;
+  if (!comp || !csize) return fail(AFC_EINVAL, "null output");
+  const DevInfo di = dev_info();
+  if ((int)mc_layout_bytes(prob->n, 2 * prob->m, 0) > di.smem_optin)
+    return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory component kernel");
+  if (r_count == 0) return AFC_OK;
+  McDev d = to_dev(*prob, r_begin, nullptr, nullptr, nullptr, nullptr);
+  cudaError_t e = launch_debug_components(d, r_count, comp, csize, (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_components");
+}
+
+int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *sources, int32_t nsrc,
+                   uint32_t *dist, uint64_t *sigma, afc_mc_stats *stats, void *stream) {
+  int st = validate(prob);
+  if (st) return st;
+  if (nsrc < 0 || (nsrc > 0 && (!sources || !dist || !sigma))) return fail(AFC_EINVAL, "bad outputs");
+  if (nsrc == 0) return AFC_OK;
+  const DevInfo di = dev_info();
+  const int G = auto_group(*prob);
+  const uint32_t base = mc_layout_bytes(prob->n, 2 * prob->m, 0);
+  const uint32_t one = mc_layout_bytes(prob->n, 2 * prob->m, 1) - base;
+  const uint32_t cap = (uint32_t)std::max(0, di.smem_optin - 1024);
+  if (base + one > cap) return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory SSSP kernel");
+  uint32_t ng = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxGroups, 1024u / (uint32_t)G});
+  ng = std::max<uint32_t>(1, std::min<uint32_t>(ng, (uint32_t)nsrc));
+  const uint32_t smem = mc_layout_bytes(prob->n, 2 * prob->m, ng);
+  const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((nsrc + ng - 1) / ng, (uint32_t)di.sms));
+  McDev d = to_dev(*prob, 0, nullptr, stats, nullptr, nullptr);
+  cudaError_t e = launch_debug_sssp(G, d, r, sources, nsrc, ng, smem, grid, dist, sigma, (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_sssp");
+}
+
+// ---- A8 / A9 ---------------------------------------------------------------------------------
+
+int afc_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index, int32_t *c_list,
+                        int32_t *c_host, void *stream) {
+  if (n < 1 || !counts || !c_index || !c_list || !c_host) return fail(AFC_EINVAL, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *c_dev = nullptr;
+  AFC_CUDA(cudaMallocAsync(&c_dev, sizeof(int32_t), s));
+  cudaError_t e = launch_observed_states(n, counts, c_index, c_list, c_dev, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c_host, c_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(c_dev, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "observed_states");
+}
+
+static size_t solve_ws_bytes(int32_t n, int32_t c) {
+  const DevInfo d = dev_info();
+  // nonzeros of the kernel: at most the transient columns in C plus the absorbing column
+  const size_t nnz_cap = (size_t)n * ((size_t)std::min<int32_t>(c, n) + 1);
+  const size_t slab = std::max<size_t>(perturb_slab_bytes(n, c) + nnz_cap * 8, 8 * (size_t)(c + 1) * 64 / (size_t)std::max(1, d.sms) + 256);
+  return solve_ws_layout(n, c, nnz_cap, (uint32_t)std::max(1, d.sms), slab).total;
+}
+
+size_t afc_solve_workspace(int32_t n, int32_t c) {
+  if (n < 1 || c < 0 || c > n) return 0;
+  return solve_ws_bytes(n, c);
+}
+
+static SolveWs ws_layout_for(int32_t n, int32_t c) {
+  const DevInfo d = dev_info();
+  const size_t nnz_cap = (size_t)n * ((size_t)std::min<int32_t>(c, n) + 1);
+  const size_t slab = std::max<size_t>(perturb_slab_bytes(n, c) + nnz_cap * 8, 8 * (size_t)(c + 1) * 64 / (size_t)std::max(1, d.sms) + 256);
+  return solve_ws_layout(n, c, nnz_cap, (uint32_t)std::max(1, d.sms), slab);
+}
+
+static int chain_checks(const afc_chain *ch, const uint32_t *counts, const int32_t *c_index,
+                        const int32_t *c_list, int32_t c) {
+  if (!ch || !counts || !c_index || !c_list) return fail(AFC_EINVAL, "null argument");
+  if (ch->n < 1 || c < 0 || c > ch->n) return fail(AFC_EINVAL, "bad n or c");
+  if (ch->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
+  if (!(ch->alpha >= 0.0 && ch->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(ch->absorb_floor > 0.0 && ch->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  return AFC_OK;
+}
+
+static ChainDev chain_dev(const afc_chain *ch, const uint32_t *counts, const int32_t *c_index,
+                          const int32_t *c_list, int32_t c) {
+  ChainDev C{};
+  C.n = ch->n;
+  C.R = ch->realizations;
+  C.alpha = ch->alpha;
+  C.eta = ch->absorb_floor;
+  C.s = ch->s_init;
+  C.f = ch->reward;
+  C.counts = counts;
+  C.c_index = c_index;
+  C.c_list = c_list;
+  C.c = c;
+  return C;
+}
+
+int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const int32_t *c_index,
+                        const int32_t *c_list, int32_t c, double *mu, double *b, double *scalars,
+                        double *lu, int32_t *piv, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+  int st = chain_checks(chain, counts, c_index, c_list, c);
+  if (st) return st;
+  if (!mu || !b || !scalars || (c > 0 && (!lu || !piv))) return fail(AFC_EINVAL, "null output");
+  const SolveWs L = ws_layout_for(chain->n, c);
+  if (!workspace || workspace_bytes < L.total)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, L.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws + L.off_tmp + 256);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  ChainDev C = chain_dev(chain, counts, c_index, c_list, c);
+  cudaError_t e = launch_solve(C, mu, b, scalars, lu, piv, ws, L, status, s);
+  if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  uint32_t st_host = 0;
+  AFC_CUDA(cudaMemcpyAsync(&st_host, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AFC_CUDA(cudaStreamSynchronize(s));
+  if (st_host & kErrSolve) return fail(AFC_ESINGULAR, "zero pivot in the LU of I - Q_CC");
+  return AFC_OK;
+}
+
+int afc_perturb_sweep(const afc_chain *chain, const afc_perturb_params *pp, const uint32_t *counts,
+                      const int32_t *c_index, const int32_t *c_list, int32_t c, const double *mu0,
+                      const double *b0, const double *lu0, const int32_t *piv0, uint64_t *counters,
+                      uint64_t *pair_flips, uint64_t *shift_hist, double *maxima, double *b_out,
+                      void *workspace, size_t workspace_bytes, void *stream) {
+  int st = chain_checks(chain, counts, c_index, c_list, c);
+  if (st) return st;
+  if (!pp || !mu0 || !b0 || (c > 0 && (!lu0 || !piv0)) || !counters || !pair_flips || !shift_hist || !maxima)
+    return fail(AFC_EINVAL, "null argument");
+  if (pp->k2 < 1 || pp->k2 > 32 || pp->top_k < 1 || pp->top_k > pp->k2 || pp->hist_bins < 1 || pp->hist_bins > 64)
+    return fail(AFC_EINVAL, "need 1 <= top_k <= k2 <= 32 and 1 <= hist_bins <= 64");
+  if (!(pp->l1_radius >= 0.0) || !(pp->r_min >= 0.0 && pp->r_min < 1.0) || !(pp->tie_rel >= 0.0))
+    return fail(AFC_EINVAL, "bad perturbation parameters");
+  const SolveWs L = ws_layout_for(chain->n, c);
+  if (!workspace || workspace_bytes < L.total)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, L.total);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws + L.off_tmp + 256);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  ChainDev C = chain_dev(chain, counts, c_index, c_list, c);
+  const DevInfo d = dev_info();
+  cudaError_t e = launch_perturb(C, *pp, mu0, b0, lu0, piv0, counters, pair_flips, shift_hist, maxima,
+                                 b_out, ws, L, status, d.sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "perturb launch");
+  return AFC_OK;
+}
+
+int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32_t *c_index,
+                     const int32_t *c_list, int32_t c, const double *mu0, const double *lu0,
+                     const int32_t *piv0, double eps_bar, double r_min, int32_t npairs,
+                     const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+  int st = chain_checks(chain, counts, c_index, c_list, c);
+  if (st) return st;
+  if (npairs < 0 || (npairs > 0 && (!pu || !pv || !gap || !sharp)) || !mu0 || (c > 0 && (!lu0 || !piv0)))
+    return fail(AFC_EINVAL, "null argument");
+  if (!(r_min > 0.0) || !(eps_bar >= 0.0)) return fail(AFC_EINVAL, "need r_min > 0 and eps_bar >= 0");
+  const SolveWs L = ws_layout_for(chain->n, c);
+  if (!workspace || workspace_bytes < L.total)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, L.total);
+  ChainDev C = chain_dev(chain, counts, c_index, c_list, c);
+  cudaError_t e = launch_certificates(C, mu0, lu0, piv0, eps_bar, r_min, npairs, pu, pv, gap, sharp,
+                                      static_cast<unsigned char *>(workspace), L, (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "certificates launch");
+}
+
+// ---- end to end from host memory ----------------------------------------------------------------
+
+int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream) {
+  if (!q || !res || !res->b) return fail(AFC_EINVAL, "null query/result");
+  const int32_t n = q->n;
+  const int64_t m = q->m;
+  if (n < 1 || m < 0) return fail(AFC_EINVAL, "bad n/m");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)), eid(col.size());
+  int st = afc_csr_from_edges(n, m, q->eu, q->ev, rp.data(), col.data(), eid.data());
+  if (st) return st;
+  std::vector<uint64_t> th;
+  if (q->p_survive) {
+    th.resize((size_t)m);
+    for (int64_t e = 0; e < m; ++e) th[e] = afc_survival_threshold(q->p_survive[e]);
+  }
+  std::vector<uint8_t> inw;
+  if (q->candidates) {
+    inw.assign((size_t)n, 0);
+    for (int32_t k = 0; k < q->n_candidates; ++k) {
+      if (q->candidates[k] < 0 || q->candidates[k] >= n) return fail(AFC_EINVAL, "candidate out of range");
+      inw[q->candidates[k]] = 1;
+    }
+  }
+  // device buffers (stream ordered)
+  std::vector<void *> allocs;
+  auto dalloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, std::max<size_t>(bytes, 16), s) != cudaSuccess) return nullptr;
+    allocs.push_back(p);
+    return p;
+  };
+  auto cleanup = [&]() {
+    for (void *p : allocs) cudaFreeAsync(p, s);
+    cudaStreamSynchronize(s);
+  };
+  int rc = AFC_OK;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  do {
+    int32_t *d_rp = (int32_t *)dalloc(4 * rp.size());
+    int32_t *d_col = (int32_t *)dalloc(4 * col.size());
+    int32_t *d_eid = (int32_t *)dalloc(4 * eid.size());
+    uint64_t *d_th = th.empty() ? nullptr : (uint64_t *)dalloc(8 * th.size());
+    uint32_t *d_wlo = q->w_lo ? (uint32_t *)dalloc(4 * (size_t)m) : nullptr;
+    uint32_t *d_whi = q->w_hi ? (uint32_t *)dalloc(4 * (size_t)m) : nullptr;
+    uint8_t *d_inw = inw.empty() ? nullptr : (uint8_t *)dalloc(inw.size());
+    double *d_s = q->s_init ? (double *)dalloc(8 * (size_t)n) : nullptr;
+    double *d_f = q->reward ? (double *)dalloc(8 * (size_t)n) : nullptr;
+    uint32_t *d_counts = (uint32_t *)dalloc(4 * (size_t)n * ((size_t)n + 1));
+    afc_mc_stats *d_stats = (afc_mc_stats *)dalloc(sizeof(afc_mc_stats));
+    if (!d_rp || !d_col || !d_eid || !d_counts || !d_stats) { rc = fail(AFC_ENOMEM, "device allocation"); break; }
+    cudaEventRecord(ev0, s);
+    cudaMemcpyAsync(d_rp, rp.data(), 4 * rp.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_col, col.data(), 4 * col.size(), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_eid, eid.data(), 4 * eid.size(), cudaMemcpyHostToDevice, s);
+    if (d_th) cudaMemcpyAsync(d_th, th.data(), 8 * th.size(), cudaMemcpyHostToDevice, s);
+    if (d_wlo) cudaMemcpyAsync(d_wlo, q->w_lo, 4 * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (d_whi) cudaMemcpyAsync(d_whi, q->w_hi, 4 * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (d_inw) cudaMemcpyAsync(d_inw, inw.data(), inw.size(), cudaMemcpyHostToDevice, s);
+    if (d_s) cudaMemcpyAsync(d_s, q->s_init, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (d_f) cudaMemcpyAsync(d_f, q->reward, 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(d_counts, 0, 4 * (size_t)n * ((size_t)n + 1), s);
+    cudaMemsetAsync(d_stats, 0, sizeof(afc_mc_stats), s);
+    afc_mc_problem p{};
+    p.n = n; p.m = m; p.row_ptr = d_rp; p.col = d_col; p.eid = d_eid;
+    p.seed = q->seed; p.graph_tag = q->graph_tag;
+    p.thresh = d_th; p.thresh_all = afc_survival_threshold(q->p_survive_all);
+    p.w_lo = d_wlo; p.w_hi = d_whi; p.w_lo_all = q->w_lo_all; p.w_hi_all = q->w_hi_all;
+    p.k_min = q->k_min; p.in_w = d_inw; p.top_k = q->top_k; p.tie_rel = q->tie_rel;
+    p.precision = q->precision; p.recheck_margin = q->recheck_margin;
+    const size_t wsc = afc_transition_counts_workspace(&p);
+    if (wsc == 0) { rc = validate(&p); if (!rc) rc = fail(AFC_EINVAL, "problem rejected"); break; }
+    void *d_wsc = dalloc(wsc);
+    if (!d_wsc) { rc = fail(AFC_ENOMEM, "device allocation"); break; }
+    rc = afc_transition_counts(&p, 0, q->realizations, d_counts, d_stats, nullptr, nullptr, d_wsc, wsc, s);
+    if (rc) break;
+    int32_t *d_cidx = (int32_t *)dalloc(4 * (size_t)n);
+    int32_t *d_clist = (int32_t *)dalloc(4 * (size_t)n);
+    int32_t c = 0;
+    rc = afc_observed_states(n, d_counts, d_cidx, d_clist, &c, s);
+    if (rc) break;
+    afc_chain ch{n, q->realizations, q->alpha, q->absorb_floor, d_s, d_f};
+    const size_t wss = afc_solve_workspace(n, c);
+    void *d_wss = dalloc(wss);
+    double *d_mu = (double *)dalloc(8 * (size_t)n);
+    double *d_b = (double *)dalloc(8 * (size_t)n);
+    double *d_sc = (double *)dalloc(8 * 4);
+    double *d_lu = (double *)dalloc(8 * (size_t)std::max(c, 1) * (size_t)std::max(c, 1));
+    int32_t *d_piv = (int32_t *)dalloc(4 * (size_t)std::max(c, 1));
+    if (!d_wss || !d_mu || !d_b || !d_sc || !d_lu || !d_piv) { rc = fail(AFC_ENOMEM, "device allocation"); break; }
+    rc = afc_absorbing_solve(&ch, d_counts, d_cidx, d_clist, c, d_mu, d_b, d_sc, d_lu, d_piv, d_wss, wss, s);
+    if (rc) break;
+    uint64_t *d_pc = (uint64_t *)dalloc(8 * (3 + 100 + 16));
+    double *d_pm = (double *)dalloc(8 * 3);
+    if (q->n_perturb > 0) {
+      if (!d_pc || !d_pm) { rc = fail(AFC_ENOMEM, "device allocation"); break; }
+      cudaMemsetAsync(d_pc, 0, 8 * (3 + 100 + 16), s);
+      cudaMemsetAsync(d_pm, 0, 8 * 3, s);
+      afc_perturb_params pp{0, q->n_perturb, q->l1_radius, q->r_min, q->perturb_seed, 5, 10, 16, q->tie_rel};
+      rc = afc_perturb_sweep(&ch, &pp, d_counts, d_cidx, d_clist, c, d_mu, d_b, d_lu, d_piv, d_pc,
+                             d_pc + 3, d_pc + 103, d_pm, nullptr, d_wss, wss, s);
+      if (rc) break;
+    }
+    double sc[4] = {0, 0, 0, 0};
+    cudaMemcpyAsync(sc, d_sc, sizeof(sc), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(res->b, d_b, 8 * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (res->mu) cudaMemcpyAsync(res->mu, d_mu, 8 * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (res->counts) cudaMemcpyAsync(res->counts, d_counts, 4 * (size_t)n * ((size_t)n + 1), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&res->stats, d_stats, sizeof(afc_mc_stats), cudaMemcpyDeviceToHost, s);
+    if (q->n_perturb > 0) {
+      cudaMemcpyAsync(res->perturb_counters, d_pc, 8 * 3, cudaMemcpyDeviceToHost, s);
+      cudaMemcpyAsync(res->perturb_maxima, d_pm, 8 * 3, cudaMemcpyDeviceToHost, s);
+    } else {
+      memset(res->perturb_counters, 0, sizeof(res->perturb_counters));
+      memset(res->perturb_maxima, 0, sizeof(res->perturb_maxima));
+    }
+    cudaEventRecord(ev1, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "run_host"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    res->device_ms = ms;
+    res->expected_T = sc[0];
+    res->b_f = sc[1];
+    res->max_rowsum_N = sc[2];
+    res->c = c;
+    if (res->stats.device_error) { rc = fail(AFC_EDEVICE, "device consistency check failed (bits %llu)", (unsigned long long)res->stats.device_error); break; }
+    if (res->stats.overflow) { rc = fail(AFC_EOVERFLOW, "path count overflow in %llu realizations", (unsigned long long)res->stats.overflow); break; }
+  } while (false);
+  cleanup();
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return rc;
+}
+
+}  // extern "C"

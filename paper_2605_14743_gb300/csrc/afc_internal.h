@@ -1,0 +1,111 @@
+// afc_internal.h -- structures shared by the library's host code and kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "afc.h"
+
+namespace afc {
+
+constexpr int kMaxGroups = 15;               // named barriers 1..15
+constexpr uint32_t kSizeMask = 0x00FFFFFFu;  // component size in cinfo
+constexpr uint32_t kHasCand = 0x80000000u;   // component holds a candidate
+
+// device_error bits
+constexpr uint32_t kErrInput = 1u;       // malformed CSR / weight seen on the device
+constexpr uint32_t kErrCapacity = 2u;    // a per-source list would have overflowed
+constexpr uint32_t kErrPassLimit = 4u;   // an iteration bound was hit
+constexpr uint32_t kErrSolve = 8u;       // zero pivot in a device LU
+
+// One problem as seen by the counting kernel (all pointers device).
+struct McDev {
+  int32_t n;
+  int64_t m;
+  const int32_t *row_ptr, *col, *eid;
+  uint32_t key_lo, key_hi, graph_tag;
+  const uint64_t *thresh;
+  uint64_t thresh_all;
+  const uint32_t *w_lo, *w_hi;
+  uint32_t w_lo_all, w_hi_all;
+  uint32_t k_min;
+  const uint8_t *in_w;
+  uint32_t top_k;
+  double tie_rel;
+  int32_t precision;
+  double recheck_margin;
+  uint32_t delta;
+  uint32_t r_begin;
+  uint32_t *counts;
+  afc_mc_stats *stats;
+  double *dump_bc;
+  int32_t *dump_next;
+};
+
+struct GroupCtl {
+  uint32_t npend, npend_next, nm, claim;
+};
+
+struct CtaCtl {
+  uint32_t err, ovf, nsrc, cursor;
+  unsigned long long edges, verts;
+  uint32_t need_recheck, pad0;
+  uint32_t scan[32];
+  uint32_t scan_total, pad1, pad2, pad3;
+  GroupCtl gctl[kMaxGroups];
+  uint32_t gred[kMaxGroups][3];
+};
+
+// mc_kernel.cu
+uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t ngroups);
+cudaError_t launch_mc_counts(int G, const McDev *probs_dev, int nprob, const uint64_t *prefix_dev,
+                             uint64_t total_items, unsigned char *gslab, uint32_t slab_bytes,
+                             uint32_t ngroups, uint32_t smem_bytes, uint32_t grid,
+                             cudaStream_t stream);
+cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
+                                 cudaStream_t stream);
+cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *comp,
+                                    int32_t *csize, cudaStream_t stream);
+cudaError_t launch_debug_sssp(int G, const McDev &P, uint32_t r, const int32_t *sources,
+                              int32_t nsrc, uint32_t ngroups, uint32_t smem, uint32_t grid,
+                              uint32_t *dist, uint64_t *sigma, cudaStream_t stream);
+
+// solve.cu / perturb.cu
+struct ChainDev {
+  int32_t n;
+  uint32_t R;
+  double alpha, eta;
+  const double *s;       // [n] or null (uniform)
+  const double *f;       // [n] or null
+  const uint32_t *counts;
+  const int32_t *c_index, *c_list;
+  int32_t c;
+};
+
+// Workspace carve-up of the solve path (byte offsets), shared by solve and perturb.
+struct SolveWs {
+  size_t off_y, off_t, off_rowscale, off_nzptr, off_nzcol, off_nzval, off_flags, off_tmp, off_slab,
+      total;
+  size_t nnz_cap;
+};
+SolveWs solve_ws_layout(int32_t n, int32_t c, size_t nnz_cap, uint32_t perturb_slabs,
+                        size_t slab_bytes);
+
+cudaError_t launch_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index,
+                                   int32_t *c_list, int32_t *c_dev, cudaStream_t stream);
+cudaError_t launch_solve(const ChainDev &C, double *mu, double *b, double *scalars, double *lu,
+                         int32_t *piv, unsigned char *ws, const SolveWs &L, uint32_t *status_dev,
+                         cudaStream_t stream);
+cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, const double *mu0,
+                           const double *b0, const double *lu0, const int32_t *piv0,
+                           uint64_t *counters, uint64_t *pair_flips, uint64_t *shift_hist,
+                           double *maxima, double *b_out, unsigned char *ws, const SolveWs &L,
+                           uint32_t *status_dev, int num_sms, cudaStream_t stream);
+cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const double *lu0,
+                                const int32_t *piv0, double eps_bar, double r_min, int32_t npairs,
+                                const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
+                                unsigned char *ws, const SolveWs &L, cudaStream_t stream);
+size_t perturb_slab_bytes(int32_t n, int32_t c);
+uint32_t perturb_smem_bytes(int32_t n, int32_t c);
+
+}  // namespace afc

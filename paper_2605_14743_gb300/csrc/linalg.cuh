@@ -1,0 +1,168 @@
+// linalg.cuh -- CTA-cooperative FP64 dense LU with partial pivoting and triangular solves.
+// The matrix may live in shared memory or global memory (generic pointers); all threads of
+// the CTA must call these functions together.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace afc {
+
+struct LinScratch {
+  double *val;   // [32]
+  int32_t *idx;  // [32]
+  double *bcast; // [2]
+  int32_t *flag; // [1]
+};
+
+// argmax |x| over rows [k, c) of column k, ties to the smallest row
+__device__ __forceinline__ int32_t pivot_search(const double *A, int32_t c, int32_t lda, int32_t k,
+                                                LinScratch s) {
+  double best = -1.0;
+  int32_t bi = k;
+  for (int32_t i = k + (int32_t)threadIdx.x; i < c; i += blockDim.x) {
+    const double a = fabs(A[(size_t)i * lda + k]);
+    if (a > best) { best = a; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xFFFFFFFFu, best, o);
+    const int32_t oi = __shfl_down_sync(0xFFFFFFFFu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  if (lane == 0) { s.val[warp] = best; s.idx[warp] = bi; }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t nw = (blockDim.x + 31u) >> 5;
+    best = lane < nw ? s.val[lane] : -1.0;
+    bi = lane < nw ? s.idx[lane] : 0x7FFFFFFF;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xFFFFFFFFu, best, o);
+      const int32_t oi = __shfl_down_sync(0xFFFFFFFFu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s.idx[0] = bi; s.val[0] = best; }
+  }
+  __syncthreads();
+  const int32_t p = s.idx[0];
+  const double pv = s.val[0];
+  __syncthreads();
+  return pv > 0.0 ? p : -1;
+}
+
+// In-place PA = LU (unit lower L below the diagonal, U on and above).  piv[k] = row swapped
+// with row k at step k.  Returns false if a pivot column is exactly zero.
+__device__ inline bool lu_factor(double *A, int32_t c, int32_t lda, int32_t *piv, LinScratch s) {
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t nw = blockDim.x >> 5;
+  for (int32_t k = 0; k < c; ++k) {
+    const int32_t p = pivot_search(A, c, lda, k, s);
+    if (p < 0) return false;
+    if (threadIdx.x == 0) piv[k] = p;
+    if (p != k) {
+      for (int32_t j = threadIdx.x; j < c; j += blockDim.x) {
+        const double t = A[(size_t)k * lda + j];
+        A[(size_t)k * lda + j] = A[(size_t)p * lda + j];
+        A[(size_t)p * lda + j] = t;
+      }
+      __syncthreads();
+    }
+    const double inv = 1.0 / A[(size_t)k * lda + k];
+    for (int32_t i = k + 1 + threadIdx.x; i < c; i += blockDim.x) A[(size_t)i * lda + k] *= inv;
+    __syncthreads();
+    for (int32_t i = k + 1 + warp; i < c; i += nw) {
+      const double l = A[(size_t)i * lda + k];
+      if (l == 0.0) continue;
+      for (int32_t j = k + 1 + lane; j < c; j += 32)
+        A[(size_t)i * lda + j] = fma(-l, A[(size_t)k * lda + j], A[(size_t)i * lda + j]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Solves A x = b in place (b -> x) with the factors of lu_factor.
+__device__ inline void lu_solve(const double *LU, int32_t c, int32_t lda, const int32_t *piv, double *b,
+                         LinScratch s) {
+  if (threadIdx.x == 0)
+    for (int32_t k = 0; k < c; ++k) {
+      const int32_t p = piv[k];
+      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+  __syncthreads();
+  for (int32_t k = 0; k < c; ++k) {  // L y = P b
+    const double yk = b[k];
+    for (int32_t i = k + 1 + threadIdx.x; i < c; i += blockDim.x)
+      b[i] = fma(-LU[(size_t)i * lda + k], yk, b[i]);
+    __syncthreads();
+  }
+  for (int32_t k = c - 1; k >= 0; --k) {  // U x = y
+    if (threadIdx.x == 0) s.bcast[0] = b[k] / LU[(size_t)k * lda + k];
+    __syncthreads();
+    const double xk = s.bcast[0];
+    for (int32_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = fma(-LU[(size_t)i * lda + k], xk, b[i]);
+    if (threadIdx.x == 0) b[k] = xk;
+    __syncthreads();
+  }
+}
+
+// Solves A^T x = b in place (b -> x): U^T z = b, L^T w = z, x = P^T w.
+__device__ inline void lu_solve_transposed(const double *LU, int32_t c, int32_t lda, const int32_t *piv,
+                                    double *b, LinScratch s) {
+  for (int32_t k = 0; k < c; ++k) {  // U^T z = b (forward; column k of U^T = row k of U)
+    if (threadIdx.x == 0) s.bcast[0] = b[k] / LU[(size_t)k * lda + k];
+    __syncthreads();
+    const double zk = s.bcast[0];
+    for (int32_t i = k + 1 + threadIdx.x; i < c; i += blockDim.x) b[i] = fma(-LU[(size_t)k * lda + i], zk, b[i]);
+    if (threadIdx.x == 0) b[k] = zk;
+    __syncthreads();
+  }
+  for (int32_t k = c - 1; k >= 0; --k) {  // L^T w = z (backward, unit diagonal)
+    const double wk = b[k];
+    for (int32_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = fma(-LU[(size_t)k * lda + i], wk, b[i]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int32_t k = c - 1; k >= 0; --k) {
+      const int32_t p = piv[k];
+      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+  __syncthreads();
+}
+
+// Block reductions of doubles (result broadcast to every thread).
+__device__ __forceinline__ double block_sum(double x, double *tmp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  __syncthreads();
+  if (lane == 0) tmp[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (uint32_t w = 0; w < (blockDim.x + 31u) / 32u; ++w) t += tmp[w];
+    tmp[32] = t;
+  }
+  __syncthreads();
+  return tmp[32];
+}
+
+__device__ __forceinline__ double block_max(double x, double *tmp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xFFFFFFFFu, x, o));
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  __syncthreads();
+  if (lane == 0) tmp[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = tmp[0];
+    for (uint32_t w = 1; w < (blockDim.x + 31u) / 32u; ++w) t = fmax(t, tmp[w]);
+    tmp[32] = t;
+  }
+  __syncthreads();
+  return tmp[32];
+}
+
+}  // namespace afc

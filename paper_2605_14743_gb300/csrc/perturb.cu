@@ -1,0 +1,333 @@
+// perturb.cu -- A9: row-wise perturbation sweep of the estimated kernel (Sec. 5.1 row-wise
+// uncertainty, Sec. 5.4 first-order sensitivity, Sec. 5.5 ranking reversals).
+//
+// One CTA handles one perturbation p at a time (persistent over p).  The perturbation is
+// regenerated from Philox (counter (column, row, p, 1)), never stored: every row i is moved on
+// its support J_i (transient columns in C plus the absorbing column), the perturbed reduced
+// system (I - Q'_CC)^T mu'_C = s_C + s_U Q'_UC is factored and solved in FP64, and the ranking
+// of the perturbed AFC b' is compared with the nominal one.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "afc_device.cuh"
+#include "afc_internal.h"
+#include "linalg.cuh"
+
+namespace afc {
+
+constexpr int kPerturbThreads = 512;
+constexpr int kMaxK2 = 32;
+constexpr int kMaxHist = 64;
+
+struct PerturbArena {
+  double *A;    // [c*c]
+  double *y;    // [c]  rhs, then mu'_C
+  double *x;    // [c]  first-order rhs, then y_lin
+  double *t;    // [c]  (N' 1)_C
+  int32_t *piv; // [c]
+};
+
+__host__ __device__ inline size_t arena_bytes(int32_t c) {
+  const size_t cc = (size_t)(c > 0 ? c : 1);
+  return 8 * cc * cc + 3 * 8 * cc + 4 * cc + 64;
+}
+
+__device__ inline PerturbArena carve(unsigned char *base, int32_t c) {
+  const size_t cc = (size_t)(c > 0 ? c : 1);
+  PerturbArena a;
+  a.A = reinterpret_cast<double *>(base);
+  a.y = a.A + cc * cc;
+  a.x = a.y + cc;
+  a.t = a.x + cc;
+  a.piv = reinterpret_cast<int32_t *>(a.t + cc);
+  return a;
+}
+
+// Nominal ranking: rank0[v] = #{u : u precedes v}; byrank0[a] = node of nominal rank a < k2.
+__global__ void nominal_rank_kernel(int32_t n, const double *b0, double tie_rel, int32_t k2,
+                                    int32_t *rank0, int32_t *byrank0) {
+  __shared__ double red[33];
+  double mx = 0.0;
+  for (int32_t v = threadIdx.x; v < n; v += blockDim.x) mx = fmax(mx, b0[v]);
+  mx = block_max(mx, red);
+  const double tau = tie_rel * mx;
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int32_t r = 0;
+    const double bv = b0[v];
+    for (int32_t u = 0; u < n; ++u) {
+      if (u == v) continue;
+      const double d = b0[u] - bv;
+      if (d > tau || (fabs(d) <= tau && u < v)) ++r;
+    }
+    rank0[v] = r;
+    if (r < k2) atomicMax(&byrank0[r], v);
+  }
+}
+
+__device__ __forceinline__ double uniform_draw(uint32_t j, uint32_t i, uint32_t p, uint32_t k0,
+                                               uint32_t k1) {
+  const uint4 u = philox4x32_10(make_uint4(j, i, p, 1u), k0, k1);
+  return (double)u.x * (1.0 / 4294967296.0);
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(kPerturbThreads, 1)
+perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const double *b0,
+               const double *lu0, const int32_t *piv0, const int32_t *nzptr, const int32_t *nzcol,
+               const double *nzval, const int32_t *byrank0, uint64_t *counters,
+               uint64_t *pair_flips, uint64_t *shift_hist, double *maxima, double *b_out,
+               unsigned char *slabs, size_t slab_bytes, int use_smem, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  __shared__ int32_t rk[kMaxK2];
+  __shared__ uint32_t loc_pair[kMaxK2 * kMaxK2];
+  __shared__ uint32_t loc_hist[kMaxHist];
+  __shared__ uint32_t loc_cnt[3];
+  LinScratch ls{sval, sidx, sb, sflag};
+  const int32_t n = C.n, c = C.c;
+  const int32_t k2 = min(pp.k2, min(kMaxK2, n));
+  const int32_t kk = min(pp.top_k, n);
+  const int32_t H = min(pp.hist_bins, kMaxHist);
+  unsigned char *slab = slabs + (size_t)blockIdx.x * slab_bytes;
+  PerturbArena ar = carve(use_smem ? smem : slab, c);
+  double *qp = reinterpret_cast<double *>(slab + (use_smem ? 0 : arena_bytes(c)));
+  const uint32_t k0 = (uint32_t)pp.seed, k1 = (uint32_t)(pp.seed >> 32);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u, nw = blockDim.x >> 5;
+  for (int32_t k = threadIdx.x; k < kMaxK2 * kMaxK2; k += blockDim.x) loc_pair[k] = 0;
+  for (int32_t k = threadIdx.x; k < kMaxHist; k += blockDim.x) loc_hist[k] = 0;
+  if (threadIdx.x < 3) loc_cnt[threadIdx.x] = 0;
+  // nominal E[T]
+  double part = 0.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) part += mu0[i];
+  const double T0 = block_sum(part, red);
+  double loc_db = 0.0, loc_lin = 0.0, loc_t = 0.0;
+
+  const uint32_t p_end = pp.p_begin + pp.p_count;
+  for (uint32_t p = pp.p_begin + blockIdx.x; p < p_end; p += gridDim.x) {
+    // (1) A' = I, y' = 0, x = 0
+    for (size_t k = threadIdx.x; k < (size_t)c * c; k += blockDim.x)
+      ar.A[k] = (k / c == k % c) ? 1.0 : 0.0;
+    for (int32_t k = threadIdx.x; k < c; k += blockDim.x) { ar.y[k] = 0.0; ar.x[k] = 0.0; }
+    __syncthreads();
+    // (2) perturb every row (warp per row)
+    for (int32_t i = warp; i < n; i += nw) {
+      const int32_t e0 = nzptr[i], e1 = nzptr[i + 1];
+      const int32_t supp = e1 - e0;
+      double zs = 0.0;
+      for (int32_t e = e0 + lane; e < e1; e += 32) {
+        const int32_t pj = nzcol[e];
+        const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
+        const double z = 2.0 * uniform_draw(node, (uint32_t)i, p, k0, k1) - 1.0;
+        qp[e] = z;
+        zs += z;
+      }
+      const double mean = warp_sum(zs) / (double)supp;
+      double l1 = 0.0;
+      for (int32_t e = e0 + lane; e < e1; e += 32) l1 += fabs(qp[e] - mean);
+      l1 = warp_sum(l1);
+      const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
+      double tot = 0.0;
+      for (int32_t e = e0 + lane; e < e1; e += 32) {
+        double q = nzval[e] + (qp[e] - mean) * scale;
+        q = q < 0.0 ? 0.0 : q;
+        qp[e] = q;
+        tot += q;
+      }
+      tot = warp_sum(tot);
+      double ts = 0.0, ra = 0.0;
+      for (int32_t e = e0 + lane; e < e1; e += 32) {
+        const double q = qp[e] / tot;
+        qp[e] = q;
+        if (nzcol[e] < c) ts += q; else ra = q;
+      }
+      ts = warp_sum(ts);
+      ra = warp_sum(ra);
+      const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+      const int32_t pi = C.c_index[i];
+      const double si = C.s ? C.s[i] : 1.0 / (double)n;
+      const double mi = mu0[i];
+      for (int32_t e = e0 + lane; e < e1; e += 32) {
+        const int32_t pj = nzcol[e];
+        double q = qp[e];
+        if (pj < c) {
+          if (ra < pp.r_min) q *= f;
+          qp[e] = q;
+          if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
+          else atomicAdd(&ar.y[pj], si * q);
+          atomicAdd(&ar.x[pj], mi * (q - nzval[e]));
+        } else {
+          qp[e] = (ra < pp.r_min) ? pp.r_min : q;
+        }
+      }
+      if (lane == 0 && pi >= 0) atomicAdd(&ar.y[pi], si);
+    }
+    __syncthreads();
+    // (3) factor, mu'_C, (N' 1)_C, first-order y_lin = x N0
+    bool ok = true;
+    if (c > 0) {
+      ok = lu_factor(ar.A, c, c, ar.piv, ls);
+      if (ok) {
+        lu_solve_transposed(ar.A, c, c, ar.piv, ar.y, ls);
+        for (int32_t k = threadIdx.x; k < c; k += blockDim.x) ar.t[k] = 1.0;
+        __syncthreads();
+        lu_solve(ar.A, c, c, ar.piv, ar.t, ls);
+        lu_solve_transposed(lu0, c, c, piv0, ar.x, ls);
+      }
+    }
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(status, kErrSolve);
+      continue;
+    }
+    // (4) E'[T], max b', y_lin . 1
+    double pT = 0.0, pY = 0.0, pm = 0.0;
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+      const int32_t pv = C.c_index[v];
+      pT += pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n);
+      if (pv >= 0) pY += ar.x[pv];
+    }
+    const double T = block_sum(pT, red);
+    const double Y1 = block_sum(pY, red);
+    for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+      const int32_t pv = C.c_index[v];
+      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n)) / T;
+      pm = fmax(pm, bv);
+      const double lin = b0[v] + (pv >= 0 ? ar.x[pv] : 0.0) / T0 - b0[v] * Y1 / T0;
+      loc_db = fmax(loc_db, fabs(bv - b0[v]));
+      loc_lin = fmax(loc_lin, fabs(bv - lin));
+      if (b_out) b_out[(size_t)(p - pp.p_begin) * n + v] = bv;
+    }
+    const double bmax = block_max(pm, red);
+    const double tau = pp.tie_rel * bmax;
+    // (N' 1) over all rows
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const int32_t pi = C.c_index[i];
+      double ti;
+      if (pi >= 0) {
+        ti = ar.t[pi];
+      } else {
+        ti = 1.0;
+        for (int32_t e = nzptr[i]; e < nzptr[i + 1]; ++e)
+          if (nzcol[e] < c) ti += qp[e] * ar.t[nzcol[e]];
+      }
+      loc_t = fmax(loc_t, ti);
+    }
+    // (5) ranks of the nominal top-k2 nodes under b'
+    for (int32_t a = warp; a < k2; a += nw) {
+      const int32_t v = byrank0[a];
+      const int32_t pv = C.c_index[v];
+      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n)) / T;
+      int32_t r = 0;
+      for (int32_t u = lane; u < n; u += 32) {
+        if (u == v) continue;
+        const int32_t pu = C.c_index[u];
+        const double bu = (pu >= 0 ? ar.y[pu] : (C.s ? C.s[u] : 1.0 / (double)n)) / T;
+        const double d = bu - bv;
+        if (d > tau || (fabs(d) <= tau && u < v)) ++r;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+      if (lane == 0) rk[a] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bool set_changed = false, order_changed = false;
+      for (int32_t a = 0; a < kk && a < k2; ++a) {
+        if (rk[a] >= kk) set_changed = true;
+        if (rk[a] != a) order_changed = true;
+      }
+      if (k2 > 0 && rk[0] != 0) loc_cnt[0]++;
+      if (set_changed) loc_cnt[1]++;
+      if (order_changed) loc_cnt[2]++;
+      for (int32_t a = 0; a < k2; ++a) {
+        int32_t sh = abs(rk[a] - a);
+        if (sh > H - 1) sh = H - 1;
+        loc_hist[sh]++;
+      }
+    }
+    for (int32_t q = threadIdx.x; q < k2 * k2; q += blockDim.x) {
+      const int32_t a = q / k2, b = q % k2;
+      if (a < b && rk[a] > rk[b]) loc_pair[a * kMaxK2 + b]++;
+    }
+    __syncthreads();
+  }
+  // flush
+  loc_db = block_max(loc_db, red);
+  loc_lin = block_max(loc_lin, red);
+  loc_t = block_max(loc_t, red);
+  if (threadIdx.x == 0) {
+    atomic_max_pos(&maxima[0], loc_db);
+    atomic_max_pos(&maxima[1], loc_lin);
+    atomic_max_pos(&maxima[2], loc_t);
+    for (int k = 0; k < 3; ++k)
+      if (loc_cnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&counters[k]), (unsigned long long)loc_cnt[k]);
+  }
+  for (int32_t q = threadIdx.x; q < k2 * k2; q += blockDim.x) {
+    const int32_t a = q / k2, b = q % k2;
+    const uint32_t v = loc_pair[a * kMaxK2 + b];
+    if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&pair_flips[a * pp.k2 + b]), (unsigned long long)v);
+  }
+  for (int32_t h = threadIdx.x; h < H; h += blockDim.x)
+    if (loc_hist[h]) atomicAdd(reinterpret_cast<unsigned long long *>(&shift_hist[h]), (unsigned long long)loc_hist[h]);
+}
+
+size_t perturb_slab_bytes(int32_t n, int32_t c) {
+  (void)n;
+  return (arena_bytes(c) + 255) & ~size_t(255);
+}
+
+uint32_t perturb_smem_bytes(int32_t n, int32_t c) {
+  (void)n;
+  return (uint32_t)arena_bytes(c);
+}
+
+cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, const double *mu0,
+                           const double *b0, const double *lu0, const int32_t *piv0,
+                           uint64_t *counters, uint64_t *pair_flips, uint64_t *shift_hist,
+                           double *maxima, double *b_out, unsigned char *ws, const SolveWs &L,
+                           uint32_t *status_dev, int num_sms, cudaStream_t stream) {
+  if (pp.p_count == 0) return cudaSuccess;
+  const int32_t n = C.n, c = C.c;
+  const int32_t *nzptr = reinterpret_cast<const int32_t *>(ws + L.off_nzptr);
+  const int32_t *nzcol = reinterpret_cast<const int32_t *>(ws + L.off_nzcol);
+  const double *nzval = reinterpret_cast<const double *>(ws + L.off_nzval);
+  int32_t *rank0 = reinterpret_cast<int32_t *>(ws + L.off_flags);
+  int32_t *byrank0 = reinterpret_cast<int32_t *>(ws + L.off_tmp);
+  cudaMemsetAsync(byrank0, 0, sizeof(int32_t) * kMaxK2, stream);
+  nominal_rank_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, b0, pp.tie_rel, min(pp.k2, kMaxK2),
+                                                           rank0, byrank0);
+  // per-CTA slab: arena (unless in shared memory) + the perturbed rows
+  const uint32_t smem = perturb_smem_bytes(n, c);
+  int max_optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int use_smem = (int)smem + 16 * 1024 <= max_optin ? 1 : 0;
+  const size_t nnz_bytes = L.nnz_cap * 8;
+  const size_t slab_bytes = ((use_smem ? 0 : arena_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
+  const size_t avail = L.total - L.off_slab;
+  size_t fit = avail / (slab_bytes ? slab_bytes : 1);
+  if (fit > (size_t)num_sms) fit = (size_t)num_sms;
+  if (fit > (size_t)pp.p_count) fit = (size_t)pp.p_count;
+  const int grid = (int)fit;
+  if (grid <= 0) return cudaErrorMemoryAllocation;
+  if (use_smem)
+    cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  perturb_kernel<<<grid, kPerturbThreads, use_smem ? smem : 0, stream>>>(
+      C, pp, mu0, b0, lu0, piv0, nzptr, nzcol, nzval, byrank0, counters, pair_flips, shift_hist,
+      maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, status_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace afc

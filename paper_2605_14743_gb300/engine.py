@@ -1,0 +1,304 @@
+"""Query driver over the C ABI: device buffers come from PyTorch's caching allocator, every
+step runs in the library's kernels (A1-A7 counts, A8 solve, A9 perturbation sweep).
+
+The input side accepts any object with the attributes of ``afc_inputs.Workload`` (n, eu, ev,
+p_survive, w_lo, w_hi, realizations, seed, graph_tag, alpha, k_min, absorb_floor, s_init,
+reward, candidates, top_k, precision, recheck_margin, tie_rel, n_perturb, l1_radius, r_min,
+perturb_seed)."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
+               PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
+               afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
+               afc_transition_counts, afc_transition_counts_workspace)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the AFC engine needs a CUDA device")
+    return torch
+
+
+def host_csr(n: int, eu, ev):
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    m = int(eu.shape[0])
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(max(2 * m, 1), np.int32)
+    eid = np.zeros(max(2 * m, 1), np.int32)
+    afc_csr_from_edges(n, m, eu, ev, rp, col, eid)
+    return rp, col, eid
+
+
+@dataclass
+class DeviceGraph:
+    n: int
+    m: int
+    row_ptr: "object"
+    col: "object"
+    eid: "object"
+
+    @staticmethod
+    def from_edges(n, eu, ev, device="cuda"):
+        torch = _torch()
+        rp, col, eid = host_csr(n, eu, ev)
+        return DeviceGraph(n, int(len(eu)), torch.from_numpy(rp).to(device),
+                           torch.from_numpy(col).to(device), torch.from_numpy(eid).to(device))
+
+
+def _precision(p):
+    if isinstance(p, str):
+        return AFC_FP32_RECHECK if p.startswith("fp32") else AFC_FP64
+    return int(p)
+
+
+def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=None,
+                 bucket_width: int = 0, group_threads: int = 0) -> McProblem:
+    """McProblem for a workload on device tensors (per-edge arrays optional)."""
+    p = McProblem()
+    p.n, p.m = dg.n, dg.m
+    p.row_ptr, p.col, p.eid = dg.row_ptr.data_ptr(), dg.col.data_ptr(), dg.eid.data_ptr()
+    p.seed, p.graph_tag = int(wl.seed), int(wl.graph_tag)
+    if thresh is not None:
+        p.thresh = thresh.data_ptr()
+    else:
+        p.thresh_all = afc_survival_threshold(float(wl.p_survive))
+    if w_lo is not None:
+        p.w_lo = w_lo.data_ptr()
+    else:
+        p.w_lo_all = int(wl.w_lo)
+    if w_hi is not None:
+        p.w_hi = w_hi.data_ptr()
+    else:
+        p.w_hi_all = int(wl.w_hi)
+    p.k_min = int(wl.k_min)
+    p.in_w = in_w.data_ptr() if in_w is not None else None
+    p.top_k = int(wl.top_k)
+    p.tie_rel = float(wl.tie_rel)
+    p.precision = _precision(wl.precision)
+    p.recheck_margin = float(wl.recheck_margin)
+    p.bucket_width = int(bucket_width)
+    p.group_threads = int(group_threads)
+    return p
+
+
+@dataclass
+class QueryResult:
+    counts: np.ndarray
+    mu: np.ndarray
+    b: np.ndarray
+    expected_T: float
+    b_f: float
+    max_rowsum_N: float
+    c: int
+    stats: dict
+    perturb: Optional[dict] = None
+
+
+class Query:
+    """All device state of one stochastic-centrality query.  Build once, run many times."""
+
+    def __init__(self, wl, device="cuda", bucket_width=0, group_threads=0, stream=None):
+        torch = _torch()
+        self.torch = torch
+        self.wl = wl
+        self.n = n = int(wl.n)
+        self.device = device
+        self.graph = DeviceGraph.from_edges(n, wl.eu, wl.ev, device)
+        m = self.graph.m
+        self.thresh = None
+        if np.ndim(wl.p_survive) > 0:
+            th = np.array([afc_survival_threshold(float(x)) for x in np.asarray(wl.p_survive)],
+                          dtype=np.uint64)
+            self.thresh = torch.from_numpy(th.view(np.int64)).to(device)
+        self.w_lo = self.w_hi = None
+        if np.ndim(wl.w_lo) > 0:
+            self.w_lo = torch.from_numpy(np.asarray(wl.w_lo, np.int32)).to(device)
+        if np.ndim(wl.w_hi) > 0:
+            self.w_hi = torch.from_numpy(np.asarray(wl.w_hi, np.int32)).to(device)
+        self.in_w = None
+        if wl.candidates is not None:
+            mask = np.zeros(n, np.uint8)
+            mask[np.asarray(wl.candidates, np.int64)] = 1
+            self.in_w = torch.from_numpy(mask).to(device)
+        self.s = None if wl.s_init is None else torch.from_numpy(np.asarray(wl.s_init, np.float64)).to(device)
+        self.f = None if wl.reward is None else torch.from_numpy(np.asarray(wl.reward, np.float64)).to(device)
+        self.prob = make_problem(self.graph, wl, self.thresh, self.w_lo, self.w_hi, self.in_w,
+                                 bucket_width, group_threads)
+        self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
+        self.stats = torch.zeros(7, dtype=torch.int64, device=device)
+        wsb = afc_transition_counts_workspace(self.prob)
+        self.ws_counts = torch.empty(max(wsb, 256), dtype=torch.uint8, device=device)
+        self.c_index = torch.empty(n, dtype=torch.int32, device=device)
+        self.c_list = torch.empty(n, dtype=torch.int32, device=device)
+        self.mu = torch.empty(n, dtype=torch.float64, device=device)
+        self.b = torch.empty(n, dtype=torch.float64, device=device)
+        self.scalars = torch.empty(4, dtype=torch.float64, device=device)
+        self.p_counters = torch.zeros(3, dtype=torch.int64, device=device)
+        self.p_pairs = torch.zeros(100, dtype=torch.int64, device=device)
+        self.p_hist = torch.zeros(16, dtype=torch.int64, device=device)
+        self.p_max = torch.zeros(3, dtype=torch.float64, device=device)
+        self.c = 0
+        self.lu = self.piv = self.ws_solve = None
+        self.stream = stream
+
+    def _stream(self):
+        s = self.stream if self.stream is not None else self.torch.cuda.current_stream()
+        return s.cuda_stream
+
+    def chain(self) -> Chain:
+        ch = Chain()
+        ch.n, ch.realizations = self.n, int(self.wl.realizations)
+        ch.alpha, ch.absorb_floor = float(self.wl.alpha), float(self.wl.absorb_floor)
+        ch.s_init = None if self.s is None else self.s.data_ptr()
+        ch.reward = None if self.f is None else self.f.data_ptr()
+        return ch
+
+    def run_counts(self, r_begin=0, r_count=None, zero=True, dump_bc=None, dump_next=None):
+        if zero:
+            self.counts.zero_()
+            self.stats.zero_()
+        r_count = int(self.wl.realizations) if r_count is None else int(r_count)
+        afc_transition_counts(self.prob, r_begin, r_count, self.counts, self.stats, dump_bc,
+                              dump_next, self.ws_counts, self.ws_counts.numel(), self._stream())
+
+    def run_solve(self):
+        torch = self.torch
+        n = self.n
+        self.c = afc_observed_states(n, self.counts, self.c_index, self.c_list, self._stream())
+        c = self.c
+        wss = afc_solve_workspace(n, c)
+        if self.ws_solve is None or self.ws_solve.numel() < wss:
+            self.ws_solve = torch.empty(wss, dtype=torch.uint8, device=self.device)
+        if self.lu is None or self.lu.numel() < max(c * c, 1):
+            self.lu = torch.empty(max(c * c, 1), dtype=torch.float64, device=self.device)
+            self.piv = torch.empty(max(c, 1), dtype=torch.int32, device=self.device)
+        afc_absorbing_solve(self.chain(), self.counts, self.c_index, self.c_list, c, self.mu, self.b,
+                            self.scalars, self.lu, self.piv, self.ws_solve, self.ws_solve.numel(),
+                            self._stream())
+
+    def perturb_params(self, p_begin=0, p_count=None, top_k=5, k2=10, hist=16) -> PerturbParams:
+        pp = PerturbParams()
+        pp.p_begin = p_begin
+        pp.p_count = int(self.wl.n_perturb if p_count is None else p_count)
+        pp.l1_radius, pp.r_min = float(self.wl.l1_radius), float(self.wl.r_min)
+        pp.seed = int(self.wl.perturb_seed)
+        pp.top_k, pp.k2, pp.hist_bins = top_k, k2, hist
+        pp.tie_rel = float(self.wl.tie_rel)
+        return pp
+
+    def run_perturb(self, p_begin=0, p_count=None, b_out=None, zero=True):
+        if zero:
+            self.p_counters.zero_()
+            self.p_pairs.zero_()
+            self.p_hist.zero_()
+            self.p_max.zero_()
+        pp = self.perturb_params(p_begin, p_count)
+        if pp.p_count == 0:
+            return
+        afc_perturb_sweep(self.chain(), pp, self.counts, self.c_index, self.c_list, self.c, self.mu,
+                          self.b, self.lu, self.piv, self.p_counters, self.p_pairs, self.p_hist,
+                          self.p_max, b_out, self.ws_solve, self.ws_solve.numel(), self._stream())
+
+    def step(self, perturb=True):
+        """One pass of the whole path: counts -> solve -> (perturbation sweep)."""
+        self.run_counts()
+        self.run_solve()
+        if perturb and int(self.wl.n_perturb) > 0:
+            self.run_perturb()
+
+    def result(self) -> QueryResult:
+        self.torch.cuda.synchronize()
+        st = self.stats.cpu().numpy().view(np.uint64)
+        sc = self.scalars.cpu().numpy()
+        pert = None
+        if int(self.wl.n_perturb) > 0:
+            pert = {"counters": self.p_counters.cpu().numpy().view(np.uint64).copy(),
+                    "pair_flips": self.p_pairs.cpu().numpy().view(np.uint64).reshape(10, 10).copy(),
+                    "shift_hist": self.p_hist.cpu().numpy().view(np.uint64).copy(),
+                    "maxima": self.p_max.cpu().numpy().copy()}
+        return QueryResult(self.counts.cpu().numpy().view(np.uint32).copy(), self.mu.cpu().numpy(),
+                           self.b.cpu().numpy(), float(sc[0]), float(sc[1]), float(sc[2]), self.c,
+                           dict(zip([f[0] for f in McStats._fields_], [int(x) for x in st])), pert)
+
+
+def run_query(wl, **kw) -> QueryResult:
+    q = Query(wl, **kw)
+    q.step()
+    return q.result()
+
+
+class HostBuffers:
+    """Host-side (optionally pinned) input and output buffers of the end-to-end entry point."""
+
+    def __init__(self, wl, pinned=True):
+        torch = _torch()
+        n = int(wl.n)
+
+        def host(arr, dtype):
+            a = np.ascontiguousarray(arr, dtype=dtype)
+            t = torch.from_numpy(a)
+            return t.pin_memory() if pinned else t
+
+        self.eu = host(wl.eu, np.int32)
+        self.ev = host(wl.ev, np.int32)
+        self.p = None if np.ndim(wl.p_survive) == 0 else host(wl.p_survive, np.float64)
+        self.wlo = None if np.ndim(wl.w_lo) == 0 else host(wl.w_lo, np.int32)
+        self.whi = None if np.ndim(wl.w_hi) == 0 else host(wl.w_hi, np.int32)
+        self.s = None if wl.s_init is None else host(wl.s_init, np.float64)
+        self.f = None if wl.reward is None else host(wl.reward, np.float64)
+        self.cand = None if wl.candidates is None else host(wl.candidates, np.int32)
+        zeros = lambda shape, dt: (torch.zeros(shape, dtype=dt).pin_memory() if pinned
+                                   else torch.zeros(shape, dtype=dt))
+        self.b = zeros(n, torch.float64)
+        self.mu = zeros(n, torch.float64)
+        self.counts = zeros((n, n + 1), torch.int32)
+        q = HostQuery()
+        q.n, q.m = n, int(len(wl.eu))
+        q.eu, q.ev = self.eu.data_ptr(), self.ev.data_ptr()
+        q.p_survive = None if self.p is None else self.p.data_ptr()
+        q.p_survive_all = 0.0 if self.p is not None else float(wl.p_survive)
+        q.w_lo = None if self.wlo is None else self.wlo.data_ptr()
+        q.w_hi = None if self.whi is None else self.whi.data_ptr()
+        q.w_lo_all = 0 if self.wlo is not None else int(wl.w_lo)
+        q.w_hi_all = 0 if self.whi is not None else int(wl.w_hi)
+        q.seed, q.graph_tag, q.realizations = int(wl.seed), int(wl.graph_tag), int(wl.realizations)
+        q.k_min, q.alpha, q.absorb_floor = int(wl.k_min), float(wl.alpha), float(wl.absorb_floor)
+        q.s_init = None if self.s is None else self.s.data_ptr()
+        q.reward = None if self.f is None else self.f.data_ptr()
+        q.candidates = None if self.cand is None else self.cand.data_ptr()
+        q.n_candidates = 0 if self.cand is None else int(self.cand.numel())
+        q.top_k, q.tie_rel = int(wl.top_k), float(wl.tie_rel)
+        q.precision, q.recheck_margin = _precision(wl.precision), float(wl.recheck_margin)
+        q.n_perturb, q.l1_radius, q.r_min = int(wl.n_perturb), float(wl.l1_radius), float(wl.r_min)
+        q.perturb_seed = int(wl.perturb_seed)
+        self.query = q
+        r = HostResult()
+        r.counts, r.mu, r.b = self.counts.data_ptr(), self.mu.data_ptr(), self.b.data_ptr()
+        self.result = r
+
+    @property
+    def h2d_bytes(self) -> int:
+        tot = 0
+        for t in (self.eu, self.ev, self.p, self.wlo, self.whi, self.s, self.f, self.cand):
+            if t is not None:
+                tot += t.numel() * t.element_size()
+        return tot
+
+    @property
+    def d2h_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.b, self.mu, self.counts))
+
+
+def run_query_host(bufs: HostBuffers, stream=None) -> HostResult:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    afc_run_host(bufs.query, bufs.result, s.cuda_stream)
+    return bufs.result

@@ -1,0 +1,68 @@
+"""Not-gpu checks of the C ABI: the sm_103a library builds and loads, exports every entry point
+declared in include/afc.h, and its host-side helpers (CSR construction, survival thresholds,
+argument validation) behave as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2605_14743_gb300 as afc
+from afc_inputs import er_edges, ws_edges
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "afc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(afc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = afc.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in afc._SIGS, f"binding lacks {name}"
+
+
+def test_csr_matches_oracle_layout():
+    import oracle as O
+    eu, ev = ws_edges(200, 6, 0.2, 3)
+    rp, col, eid = afc.engine.host_csr(200, eu, ev)
+    g = O.build_graph(200, eu, ev)
+    assert (rp == g.row_ptr).all() and (col == g.col).all() and (eid == g.eid).all()
+
+
+@pytest.mark.parametrize("eu,ev", [([0], [0]), ([0, 1], [1, 0]), ([0], [7]), ([-1], [2])])
+def test_csr_rejects_bad_edges(eu, ev):
+    with pytest.raises(afc.AfcError) as e:
+        afc.engine.host_csr(3, np.array(eu), np.array(ev))
+    assert e.value.code == afc.AFC_EINVAL
+    assert afc.afc_last_error()
+
+
+def test_survival_threshold_matches_oracle():
+    import oracle as O
+    for p in [0.0, 1e-9, 0.05, 0.5, 0.9, 0.95, 0.999999, 1.0, 1.5, -1.0]:
+        assert afc.afc_survival_threshold(p) == O.survival_threshold(p)
+
+
+def test_validation_errors_without_device():
+    prob = afc.McProblem()
+    prob.n = 0
+    assert afc.afc_transition_counts_workspace(prob) == 0
+    prob.n, prob.m = 40000, 10
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_transition_counts(prob, 0, 1, None, None, None, None, None, 0, None)
+    assert e.value.code == afc.AFC_EUNSUPPORTED
+    prob.n, prob.m, prob.row_ptr, prob.col, prob.eid = 10, 5, 8, 8, 8
+    prob.w_lo_all, prob.w_hi_all, prob.k_min = 0, 3, 1
+    with pytest.raises(afc.AfcError):
+        afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)
+    prob.w_lo_all, prob.k_min, prob.group_threads = 1, 1, 48
+    with pytest.raises(afc.AfcError):
+        afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)

@@ -1,0 +1,43 @@
+"""End-to-end entry point from host memory: identical results to the device path and to the
+oracle on the small ER workload."""
+import numpy as np
+import pytest
+
+import oracle as O
+from afc_inputs import workload
+from tests._util import close, oracle_counts, variant
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+afc = pytest.importorskip("paper_2605_14743_gb300")
+
+
+def test_run_host_matches_device_path_and_oracle():
+    wl = variant(workload("small_er"), n_perturb=64)
+    q = afc.Query(wl)
+    q.step()
+    dev = q.result()
+    bufs = afc.engine.HostBuffers(wl)
+    res = afc.run_query_host(bufs)
+    counts = bufs.counts.numpy().view(np.uint32)
+    assert (counts == dev.counts).all()
+    assert np.array_equal(bufs.b.numpy(), dev.b)
+    assert res.c == dev.c and abs(res.expected_T - dev.expected_T) == 0.0
+    assert list(res.perturb_counters) == dev.perturb["counters"].tolist()
+    oc, _ = oracle_counts(wl, 0, wl.realizations, threads=4)
+    assert (counts == oc).all()
+    mu, b, T, _ = O.solve_counts(oc, wl.realizations, wl.alpha)
+    assert close(bufs.b.numpy(), b)
+    assert res.stats.realizations == wl.realizations and res.device_ms > 0
+
+
+def test_run_host_reward_and_pool():
+    wl = workload("ws1000")
+    wl = variant(wl, realizations=16, n_perturb=0)
+    bufs = afc.engine.HostBuffers(wl, pinned=False)
+    res = afc.run_query_host(bufs)
+    oc, _ = oracle_counts(wl, 0, 16, threads=4)
+    assert (bufs.counts.numpy().view(np.uint32) == oc).all()
+    mu, b, T, bf, c = O.solve_counts(oc, 16, wl.alpha, f=wl.reward, reduced=True)
+    assert close(bufs.b.numpy(), b) and abs(res.b_f - bf) <= 1e-9 * bf and res.c == c
