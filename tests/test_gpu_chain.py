@@ -78,10 +78,10 @@ def er_counts():
 
 def _random_counts(n, R, seed, support_frac=0.3, alpha_bias=0.2):
     rng = np.random.default_rng(seed)
-    C = rng.choice(n, size=max(2, int(n * support_frac)), replace=False)
+    C = rng.choice(n, size=max(4, int(n * support_frac)), replace=False)
     counts = np.zeros((n, n + 1), np.uint32)
     for i in range(n):
-        k = int(rng.integers(1, 5))
+        k = int(rng.integers(1, min(5, len(C) + 1)))
         t = rng.choice(C, size=k, replace=False)
         p = rng.dirichlet(np.ones(k + 1))
         p[-1] += alpha_bias
