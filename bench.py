@@ -271,7 +271,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "realizations_per_rank": R,
                            "n_perturb": wl.n_perturb, "l2": "flushed (256 MB write) between steps",
                            "bucket_width": int(q.prob.bucket_width) or "auto",
-                           "group_threads": int(q.prob.group_threads) or "auto"},
+                           "block_threads": int(q.prob.block_threads) or "auto"},
                 "gteps": gteps, "counts_kernel_ms": kavg,
                 "query_latency_ms_p50": statistics.median(step_ms),
                 "query_latency_ms_p99": max(step_ms),

@@ -95,8 +95,10 @@ typedef struct {
   int32_t precision;         /* AFC_FP64 or AFC_FP32_RECHECK                              */
   double recheck_margin;     /* FP32 mode: recompute a realization in FP64 when some valid */
                              /* component's top-two gap (B1 - B2) / B1 < recheck_margin    */
-  uint32_t bucket_width;     /* SSSP bucket width (Delta); 0 = automatic                  */
-  int32_t group_threads;     /* threads cooperating on one source: 32, 64 or 128; 0 = auto */
+  uint32_t bucket_width;     /* SSSP bucket width Delta (raised, per realization, to at     */
+                             /* least ceil(max length / 10)); 0 = automatic                */
+  int32_t block_threads;     /* threads per CTA of the counting kernel: 256, 512 or 1024;  */
+                             /* 0 = automatic                                              */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */

@@ -61,9 +61,9 @@ uint32_t auto_delta(const afc_mc_problem &p) {
   return (uint32_t)std::max(1.0, std::floor(mean / 3.0));
 }
 
-int auto_group(const afc_mc_problem &p) {
-  if (p.group_threads) return p.group_threads;
-  return p.n >= 256 ? 64 : 32;
+int auto_block(const afc_mc_problem &p) {
+  if (p.block_threads) return p.block_threads;
+  return p.n >= 128 ? 512 : 256;
 }
 
 int validate(const afc_mc_problem *p) {
@@ -80,8 +80,8 @@ int validate(const afc_mc_problem *p) {
   if (!(p->tie_rel >= 0.0) || p->tie_rel >= 1.0) return fail(AFC_EINVAL, "tie_rel must be in [0, 1)");
   if (p->precision != AFC_FP64 && p->precision != AFC_FP32_RECHECK) return fail(AFC_EINVAL, "bad precision");
   if (p->precision == AFC_FP32_RECHECK && !(p->recheck_margin >= 0.0)) return fail(AFC_EINVAL, "bad recheck_margin");
-  const int G = auto_group(*p);
-  if (G != 32 && G != 64 && G != 128) return fail(AFC_EINVAL, "group_threads must be 32, 64 or 128");
+  const int B = auto_block(*p);
+  if (B != 256 && B != 512 && B != 1024) return fail(AFC_EINVAL, "block_threads must be 256, 512 or 1024");
   if (p->bucket_width > 0x7FFFFFFF) return fail(AFC_EINVAL, "bucket_width too large");
   return AFC_OK;
 }
@@ -120,16 +120,16 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
 
 // Launch plan of the counting kernel for a set of problems.
 struct McPlan {
-  int G = 64;
-  uint32_t ngroups = 1, smem = 0, grid = 1, slab = 0;
-  bool global_slab = false;
+  int block = 512;
+  uint32_t nslots = 1, smem = 0, grid = 1;
   size_t ws_meta = 0, ws_total = 0;
+  bool fits = true;
 };
 
 McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items) {
   const DevInfo d = dev_info();
   McPlan pl;
-  pl.G = auto_group(probs[0]);
+  pl.block = auto_block(probs[0]);
   uint32_t nmax = 1;
   uint64_t amax = 1;
   for (int g = 0; g < nprob; ++g) {
@@ -139,30 +139,18 @@ McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items)
   const uint32_t base = mc_layout_bytes(nmax, amax, 0);
   const uint32_t one = mc_layout_bytes(nmax, amax, 1) - base;
   const uint32_t cap = (uint32_t)std::max(0, d.smem_optin - 1024);
-  const uint32_t by_threads = 1024u / (uint32_t)pl.G;
-  uint32_t want = std::min<uint32_t>(kMaxGroups, by_threads);
-  // small graphs: do not spread few sources over many groups
-  want = std::min<uint32_t>(want, std::max<uint32_t>(1u, (nmax + 7) / 8));
-  if (base + one <= cap) {
-    pl.ngroups = std::min<uint32_t>(want, (cap - base) / one);
-    pl.smem = mc_layout_bytes(nmax, amax, pl.ngroups);
-    pl.global_slab = false;
-    int per_sm = 1;
-    // estimate CTAs per SM from shared memory and threads
+  pl.fits = base + one <= cap;
+  if (pl.fits) {
+    pl.nslots = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxSlots, nmax});
+    pl.smem = mc_layout_bytes(nmax, amax, pl.nslots);
     const uint32_t smem_sm = 228u * 1024u;
-    per_sm = (int)std::max<uint32_t>(1u, std::min<uint32_t>(smem_sm / (pl.smem + 1024u),
-                                                             2048u / (pl.ngroups * pl.G)));
+    const uint32_t per_sm = std::max<uint32_t>(1u, std::min<uint32_t>(smem_sm / (pl.smem + 1024u),
+                                                                      2048u / (uint32_t)pl.block));
     pl.grid = (uint32_t)std::min<uint64_t>(total_items, (uint64_t)d.sms * per_sm);
-  } else {
-    pl.ngroups = want;
-    pl.slab = mc_layout_bytes(nmax, amax, pl.ngroups);
-    pl.smem = (uint32_t)sizeof(CtaCtl) + 64;
-    pl.global_slab = true;
-    pl.grid = (uint32_t)std::min<uint64_t>(total_items, (uint64_t)d.sms);
   }
   if (pl.grid == 0) pl.grid = 1;
   pl.ws_meta = ((sizeof(McDev) * (size_t)nprob + sizeof(uint64_t) * (size_t)(nprob + 1)) + 255) & ~size_t(255);
-  pl.ws_total = pl.ws_meta + (pl.global_slab ? (size_t)pl.grid * pl.slab : 0);
+  pl.ws_total = pl.ws_meta;
   return pl;
 }
 
@@ -173,8 +161,8 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   for (int g = 0; g < nprob; ++g) {
     int st = validate(&probs[g]);
     if (st) return st;
-    if (auto_group(probs[g]) != auto_group(probs[0]))
-      return fail(AFC_EINVAL, "all problems of a batch must use the same group_threads");
+    if (auto_block(probs[g]) != auto_block(probs[0]))
+      return fail(AFC_EINVAL, "all problems of a batch must use the same block_threads");
     if (!counts[g]) return fail(AFC_EINVAL, "counts[%d] is null", g);
   }
   std::vector<McDev> devs(nprob);
@@ -187,6 +175,8 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   const uint64_t total = prefix[nprob];
   if (total == 0) return AFC_OK;
   const McPlan pl = plan_counts(nprob, probs, total);
+  if (!pl.fits)
+    return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory counting kernel");
   if (!workspace || ws_bytes < pl.ws_total)
     return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", ws_bytes, pl.ws_total);
   unsigned char *ws = static_cast<unsigned char *>(workspace);
@@ -194,9 +184,8 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   uint64_t *prefix_d = reinterpret_cast<uint64_t *>(ws + sizeof(McDev) * (size_t)nprob);
   AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)nprob, cudaMemcpyHostToDevice, stream));
   AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(nprob + 1), cudaMemcpyHostToDevice, stream));
-  cudaError_t e = launch_mc_counts(pl.G, devs_d, nprob, prefix_d, total,
-                                   pl.global_slab ? ws + pl.ws_meta : nullptr, pl.slab, pl.ngroups,
-                                   pl.smem, pl.grid, stream);
+  cudaError_t e = launch_mc_counts(pl.block, devs_d, nprob, prefix_d, total, pl.nslots, pl.smem,
+                                   pl.grid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
   return AFC_OK;
 }
@@ -313,17 +302,16 @@ int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *source
   if (nsrc < 0 || (nsrc > 0 && (!sources || !dist || !sigma))) return fail(AFC_EINVAL, "bad outputs");
   if (nsrc == 0) return AFC_OK;
   const DevInfo di = dev_info();
-  const int G = auto_group(*prob);
   const uint32_t base = mc_layout_bytes(prob->n, 2 * prob->m, 0);
   const uint32_t one = mc_layout_bytes(prob->n, 2 * prob->m, 1) - base;
   const uint32_t cap = (uint32_t)std::max(0, di.smem_optin - 1024);
   if (base + one > cap) return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory SSSP kernel");
-  uint32_t ng = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxGroups, 1024u / (uint32_t)G});
-  ng = std::max<uint32_t>(1, std::min<uint32_t>(ng, (uint32_t)nsrc));
-  const uint32_t smem = mc_layout_bytes(prob->n, 2 * prob->m, ng);
-  const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((nsrc + ng - 1) / ng, (uint32_t)di.sms));
+  uint32_t ns = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxSlots, (uint32_t)nsrc});
+  ns = std::max<uint32_t>(1, ns);
+  const uint32_t smem = mc_layout_bytes(prob->n, 2 * prob->m, ns);
   McDev d = to_dev(*prob, 0, nullptr, stats, nullptr, nullptr);
-  cudaError_t e = launch_debug_sssp(G, d, r, sources, nsrc, ng, smem, grid, dist, sigma, (cudaStream_t)stream);
+  cudaError_t e = launch_debug_sssp(auto_block(*prob), d, r, sources, nsrc, ns, smem, dist, sigma,
+                                    (cudaStream_t)stream);
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_sssp");
 }
 

@@ -8,7 +8,6 @@
 
 namespace afc {
 
-constexpr int kMaxGroups = 15;               // named barriers 1..15
 constexpr uint32_t kSizeMask = 0x00FFFFFFu;  // component size in cinfo
 constexpr uint32_t kHasCand = 0x80000000u;   // component holds a candidate
 
@@ -42,33 +41,37 @@ struct McDev {
   int32_t *dump_next;
 };
 
-struct GroupCtl {
-  uint32_t npend, npend_next, nm, claim;
+constexpr int kMaxSlots = 64;   // sources advanced together by one CTA
+constexpr int kRing = 12;       // bucket bitmaps per source (ring over pending distances)
+
+struct SlotCtl {
+  uint32_t s, nm, mstart, hi, lo;
+  uint32_t ring_cnt[kRing];
 };
 
 struct CtaCtl {
-  uint32_t err, ovf, nsrc, cursor;
+  uint32_t err, ovf, nsrc, bucket;
   unsigned long long edges, verts;
-  uint32_t need_recheck, pad0;
+  uint32_t need_recheck, delta, ring_b, wmax;
   uint32_t scan[32];
   uint32_t scan_total, pad1, pad2, pad3;
-  GroupCtl gctl[kMaxGroups];
-  uint32_t gred[kMaxGroups][3];
+  uint32_t pref[kMaxSlots + 1];
+  uint32_t pad4[3];
+  SlotCtl slot[kMaxSlots];
 };
 
 // mc_kernel.cu
-uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t ngroups);
-cudaError_t launch_mc_counts(int G, const McDev *probs_dev, int nprob, const uint64_t *prefix_dev,
-                             uint64_t total_items, unsigned char *gslab, uint32_t slab_bytes,
-                             uint32_t ngroups, uint32_t smem_bytes, uint32_t grid,
-                             cudaStream_t stream);
+uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots);
+cudaError_t launch_mc_counts(int block, const McDev *probs_dev, int nprob,
+                             const uint64_t *prefix_dev, uint64_t total_items, uint32_t nslots,
+                             uint32_t smem_bytes, uint32_t grid, cudaStream_t stream);
 cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
                                  cudaStream_t stream);
 cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *comp,
                                     int32_t *csize, cudaStream_t stream);
-cudaError_t launch_debug_sssp(int G, const McDev &P, uint32_t r, const int32_t *sources,
-                              int32_t nsrc, uint32_t ngroups, uint32_t smem, uint32_t grid,
-                              uint32_t *dist, uint64_t *sigma, cudaStream_t stream);
+cudaError_t launch_debug_sssp(int block, const McDev &P, uint32_t r, const int32_t *sources,
+                              int32_t nsrc, uint32_t nslots, uint32_t smem, uint32_t *dist,
+                              uint64_t *sigma, cudaStream_t stream);
 
 // solve.cu / perturb.cu
 struct ChainDev {

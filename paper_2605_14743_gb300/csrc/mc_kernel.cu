@@ -1,17 +1,22 @@
 // mc_kernel.cu -- Monte Carlo transition counts on GB300 (sm_103a).
 //
 // One CTA owns one network realization at a time (persistent over realizations) and keeps
-// the whole realization in shared memory:
+// it in shared memory:
 //   A1  Philox4x32-10 edge draws -> alive-compacted CSR with packed (neighbour, length) arcs
 //   A2  components by lock-free union-find (root = smallest id), sizes, candidate flags
-//   A3  per source: bucketed (Delta-stepping) integer SSSP over a shared-memory frontier
-//   A4  shortest-path counts sigma (exact 64-bit) resolved bucket by bucket
-//   A5  dependencies delta in reverse bucket order, betweenness accumulated in FP64
+//   A3  bucketed (Delta-stepping) integer SSSP for a batch of S sources advanced in lockstep:
+//       all S sources work on the same bucket [b*Delta, (b+1)*Delta) at once, so one set of
+//       CTA barriers serves S sources and the bucket members of all sources fill the threads
+//   A4  shortest-path counts sigma (exact 64-bit), resolved bucket by bucket
+//   A5  dependencies delta in reverse bucket order; betweenness accumulated in FP64
 //   A6  tie-ruled argmax per valid component (Sec. 3.2 eq. local-center, Sec. 7.1 Sel_W)
 //       and the transition-count update of every anchor (Alg. 1 / Alg. 2)
 //   A7  FP32 mode: a realization whose top-two gap is under the margin is redone in FP64
-// Several thread groups of G threads each process different sources of the realization
-// concurrently; each group owns its per-source state (dist, sigma, delta, bucket lists).
+//
+// Per source ("slot") state: dist[n] (u32 distance | flag), sig[n] (u64: last relaxed
+// distance while tentative, then sigma, then rho = (1 + delta) / sigma in the same slot),
+// ord[n] (u16 settled vertices grouped by bucket) and a ring of kRing bucket bitmaps that
+// holds the discovered-but-unsettled vertices by bucket.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -27,14 +32,16 @@ __device__ __forceinline__ unsigned long long *u64p(uint64_t *p) {
 constexpr uint32_t kInf = 0x7FFFFFFFu;    // unreached distance
 constexpr uint32_t kFlag = 0x80000000u;   // "sigma final" (forward) / "delta pending" (backward)
 constexpr uint32_t kMask = 0x7FFFFFFFu;
-constexpr uint16_t kMark = 0x8000u;       // finalise-this-member mark in the bucket lists
+constexpr uint16_t kMark = 0x8000u;       // finalise-this-member mark in ord
 constexpr uint64_t kNoRelax = ~0ull;
 
-// Shared-memory (or global-slab) layout of one CTA for a graph of n nodes and 2m arcs.
+// Shared-memory layout of one CTA for a graph of n nodes, `arcs` arcs and S source slots.
 struct Layout {
-  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_src, off_groups, group_bytes, total;
+  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_src, off_sel, off_slots;
+  uint32_t slot_bytes, words, total;
   __host__ __device__ static uint32_t al(uint32_t x) { return (x + 15u) & ~15u; }
-  __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t ngroups) {
+  __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t nslots) {
+    words = (n + 31u) / 32u;
     uint32_t o = al(sizeof(CtaCtl));
     off_rp = o;     o = al(o + 4u * (n + 1));
     off_arc = o;    o = al(o + 4u * (arcs > 0 ? arcs : 1));
@@ -42,29 +49,28 @@ struct Layout {
     off_cinfo = o;  o = al(o + 4u * n);
     off_bc = o;     o = al(o + 8u * n);
     off_src = o;    o = al(o + 2u * n);
-    off_groups = o;
-    group_bytes = al(4u * n) + al(8u * n) + al(8u * n) + al(2u * n) + al(2u * n);
-    total = o + ngroups * group_bytes;
+    off_sel = o;    o = al(o + 4u * n);
+    off_slots = o;
+    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n) + al(4u * kRing * words);
+    total = o + nslots * slot_bytes;
   }
 };
 
-struct GroupArrays {
-  uint32_t *dist;   // [n] distance | flag
-  uint64_t *sig;    // [n] last relaxed distance during SSSP, then sigma
-  double *dlt;      // [n] rho = (1 + delta) / sigma (FP64) or float pairs (FP32)
-  uint16_t *ord;    // [n] settled vertices in bucket order (+ current bucket)
-  uint16_t *pend;   // [n] discovered vertices beyond the current bucket
+struct SlotArrays {
+  uint32_t *dist;
+  uint64_t *sig;
+  uint16_t *ord;
+  uint32_t *ring;   // [kRing][words]
 };
 
-__device__ __forceinline__ GroupArrays group_arrays(unsigned char *base, const Layout &L,
-                                                    uint32_t n, uint32_t g) {
-  unsigned char *p = base + L.off_groups + g * L.group_bytes;
-  GroupArrays a;
+__device__ __forceinline__ SlotArrays slot_arrays(unsigned char *smem, const Layout &L, uint32_t n,
+                                                  uint32_t i) {
+  unsigned char *p = smem + L.off_slots + i * L.slot_bytes;
+  SlotArrays a;
   a.dist = reinterpret_cast<uint32_t *>(p);  p += Layout::al(4u * n);
   a.sig = reinterpret_cast<uint64_t *>(p);   p += Layout::al(8u * n);
-  a.dlt = reinterpret_cast<double *>(p);     p += Layout::al(8u * n);
   a.ord = reinterpret_cast<uint16_t *>(p);   p += Layout::al(2u * n);
-  a.pend = reinterpret_cast<uint16_t *>(p);
+  a.ring = reinterpret_cast<uint32_t *>(p);
   return a;
 }
 
@@ -74,77 +80,129 @@ struct Realized {
   const uint32_t *arc;   // packed: neighbour (low 16 bits) | length << 16
 };
 
-// ---------------------------------------------------------------------------------------
-// One source: distances, path counts, dependencies; adds delta_s(v) to bc[v] (v != s).
-// Returns false on a detected consistency failure (error bits are OR-ed into *err).
-// ---------------------------------------------------------------------------------------
-template <int G, typename DT>
-__device__ bool brandes_one_source(Group<G> &grp, const Realized &H, GroupArrays a,
-                                   GroupCtl *gc, uint32_t s, uint32_t delta, double *bc,
-                                   bool want_delta, uint32_t *err, uint32_t *ovf) {
-  const uint32_t n = H.n;
-  const uint32_t t = grp.rank;
-  for (uint32_t v = t; v < n; v += G) a.dist[v] = kInf;
-  grp.sync();
-  if (t == 0) {
-    a.dist[s] = 0;
-    a.pend[0] = (uint16_t)s;
-    gc->npend = 1;
-    gc->nm = 0;
-  }
-  grp.sync();
-
-  uint32_t nset = 0;
-  uint32_t my_err = 0, my_ovf = 0;
-  bool ok = true;
-  for (uint32_t guard = 0;; ++guard) {
-    if (guard > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-    // (1) smallest live tentative distance among the pending vertices
-    const uint32_t np = gc->npend;
-    uint32_t local = kInf;
-    for (uint32_t i = t; i < np; i += G) {
-      const uint32_t d = a.dist[a.pend[i]];
-      if (!(d & kFlag) && d < local) local = d;   // flagged entries are settled (stale)
+// Exclusive prefix of per-slot counts into ctl->pref[0..S]; executed by warp 0.
+template <typename F>
+__device__ __forceinline__ void slot_prefix(CtaCtl *ctl, uint32_t S, F count) {
+  if (threadIdx.x >= 32) return;
+  const uint32_t lane = threadIdx.x;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < S; base += 32) {
+    const uint32_t i = base + lane;
+    const uint32_t x = i < S ? count(i) : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, o);
+      if (lane >= (uint32_t)o) inc += y;
     }
-    const uint32_t dmin = grp.reduce_min(local);
-    if (dmin >= kInf) break;
-    const uint32_t dstart = (dmin / delta) * delta;
-    const uint32_t dend = dstart + delta;
-    // (2) move pending vertices of [dstart, dend) into the bucket, drop stale entries,
-    //     compact the rest in place (chunk reads complete before any chunk write)
-    if (t == 0) gc->npend_next = 0;
-    grp.sync();
-    for (uint32_t base = 0; base < np; base += G) {
-      const uint32_t i = base + t;
-      uint32_t v = 0, d = kInf;
-      if (i < np) { v = a.pend[i]; d = a.dist[v]; }
-      grp.sync();
-      if (i < np && !(d & kFlag)) {
-        if (d < dend) {
-          const uint32_t pos = warp_append(&gc->nm);
-          if (pos < n) { a.ord[pos] = (uint16_t)v; a.sig[v] = kNoRelax; }
-          else my_err |= kErrCapacity;
-        } else {
-          const uint32_t pos = warp_append(&gc->npend_next);
-          a.pend[pos] = (uint16_t)v;
-        }
+    if (i < S) ctl->pref[i] = carry + inc - x;
+    carry += __shfl_sync(kFull, inc, 31);
+  }
+  if (lane == 0) ctl->pref[S] = carry;
+}
+
+// Largest slot i with pref[i] <= k (pref ascending, pref[S] = total > k).
+__device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, uint32_t k) {
+  uint32_t lo = 0, hi = S;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pref[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------
+// A batch of S sources (srcs[0..S)) in lockstep.  Adds delta_s(v) to bc[v] for v != s.
+// With want_delta = false it stops after distances and path counts (parity hook).
+// Every thread of the CTA must call it.  Returns false on a consistency failure.
+// ---------------------------------------------------------------------------------------
+template <typename DT>
+__device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layout &L, uint32_t S,
+                              const uint16_t *srcs, uint32_t delta, uint32_t ringB, double *bc,
+                              bool want_delta, CtaCtl *ctl) {
+  const uint32_t n = H.n, W = L.words;
+  const uint32_t T = blockDim.x, tid = threadIdx.x;
+  uint32_t my_err = 0, my_ovf = 0;
+
+  // ---- init
+  for (uint32_t t = tid; t < S * n; t += T) {
+    const uint32_t i = t / n;
+    slot_arrays(smem, L, n, i).dist[t - i * n] = kInf;
+  }
+  for (uint32_t t = tid; t < S * kRing * W; t += T) {
+    const uint32_t i = t / (kRing * W);
+    slot_arrays(smem, L, n, i).ring[t - i * kRing * W] = 0u;
+  }
+  for (uint32_t i = tid; i < S; i += T) {
+    SlotCtl &sc = ctl->slot[i];
+    sc.s = srcs[i];
+    sc.nm = 0; sc.mstart = 0; sc.hi = 0; sc.lo = 0;
+    for (int k = 0; k < kRing; ++k) sc.ring_cnt[k] = 0;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < S; i += T) {
+    SlotArrays a = slot_arrays(smem, L, n, i);
+    const uint32_t s = ctl->slot[i].s;
+    a.dist[s] = 0;
+    a.ring[s >> 5] = 1u << (s & 31u);
+    ctl->slot[i].ring_cnt[0] = 1;
+  }
+  __syncthreads();
+
+  // ---- forward: buckets in increasing order
+  bool ok = true;
+  uint32_t b = 0;
+  for (uint32_t guard = 0;; ++guard) {
+    if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
+    if (tid < 32) {
+      // first ring offset k (bucket b + k) holding discovered vertices in any slot
+      bool here = false;
+      if (tid < ringB) {
+        const uint32_t rs = (b + tid) % ringB;
+        for (uint32_t i = 0; i < S && !here; ++i) here = ctl->slot[i].ring_cnt[rs] != 0;
+      }
+      const uint32_t ball = __ballot_sync(kFull, here);
+      if (tid == 0) ctl->bucket = ball ? b + (uint32_t)(__ffs(ball) - 1) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    if (ctl->bucket == 0xFFFFFFFFu) break;
+    b = ctl->bucket;
+    const uint32_t rs = b % ringB;
+    const uint32_t dend = (b + 1u) * delta;
+    // extraction of bucket b into the member lists
+    for (uint32_t t = tid; t < S * W; t += T) {
+      const uint32_t i = t / W, w = t - i * W;
+      SlotArrays a = slot_arrays(smem, L, n, i);
+      uint32_t word = a.ring[rs * W + w];
+      if (!word) continue;
+      a.ring[rs * W + w] = 0u;
+      while (word) {
+        const uint32_t j = __ffs(word) - 1;
+        word &= word - 1u;
+        const uint32_t v = w * 32u + j;
+        const uint32_t d = a.dist[v];
+        if ((d & kFlag) || d >= dend) continue;   // settled (stale bit)
+        const uint32_t pos = atomicAdd(&ctl->slot[i].nm, 1u);
+        if (pos < n) { a.ord[pos] = (uint16_t)v; a.sig[v] = kNoRelax; }
+        else my_err |= kErrCapacity;
       }
     }
-    grp.sync();
-    if (t == 0) gc->npend = gc->npend_next;
-    // (3) relaxation passes inside the bucket until no member improves
-    const uint32_t mstart = nset;
+    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].ring_cnt[rs] = 0;
+    __syncthreads();
+    // relaxation passes until no member of the bucket improves
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-      const uint32_t nm = gc->nm;
-      grp.sync();  // everyone holds the same member count before anyone appends
-      bool relaxed = false;
-      for (uint32_t idx = mstart + t; idx < nm; idx += G) {
-        const uint32_t v = a.ord[idx];
+      slot_prefix(ctl, S, [&](uint32_t i) { return min(ctl->slot[i].nm, n) - ctl->slot[i].mstart; });
+      __syncthreads();
+      const uint32_t total = ctl->pref[S];
+      bool improved = false;
+      for (uint32_t k = tid; k < total; k += T) {
+        const uint32_t i = find_slot(ctl->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, i);
+        const uint32_t v = a.ord[ctl->slot[i].mstart + k - ctl->pref[i]];
         const uint32_t d = a.dist[v];
         if ((uint64_t)d == a.sig[v]) continue;
         a.sig[v] = d;
-        relaxed = true;
         const uint32_t e1 = H.rp[v + 1];
         for (uint32_t e = H.rp[v]; e < e1; ++e) {
           const uint32_t pk = H.arc[e];
@@ -155,36 +213,45 @@ __device__ bool brandes_one_source(Group<G> &grp, const Realized &H, GroupArrays
           const uint32_t old = atomicMin(&a.dist[u], nd);
           if (nd >= old) continue;
           if (nd < dend) {
+            improved = true;
             if (old >= dend) {
-              const uint32_t pos = warp_append(&gc->nm);
+              const uint32_t pos = atomicAdd(&ctl->slot[i].nm, 1u);
               if (pos < n) { a.ord[pos] = (uint16_t)u; a.sig[u] = kNoRelax; }
               else my_err |= kErrCapacity;
             }
-          } else if (old == kInf) {
-            const uint32_t pos = warp_append(&gc->npend);
-            if (pos < n) a.pend[pos] = (uint16_t)u;
-            else my_err |= kErrCapacity;
+          } else {
+            const uint32_t r2 = (nd / delta) % ringB;
+            const uint32_t bit = 1u << (u & 31u);
+            const uint32_t prev = atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
+            if (!(prev & bit)) atomicAdd(&ctl->slot[i].ring_cnt[r2], 1u);
           }
         }
       }
-      if (!grp.any(relaxed)) break;
+      if (!__syncthreads_or(improved)) break;
     }
     if (!ok) break;
-    // (4) path counts of the bucket: a member is final once all its same-bucket
-    //     predecessors are final (earlier buckets are final already)
-    const uint32_t mend = min(gc->nm, n);
-    for (uint32_t idx = mstart + t; idx < mend; idx += G) {
-      const uint32_t v = a.ord[idx];
-      a.sig[v] = (v == s) ? 1ull : 0ull;
+    // path counts of the bucket: a member is final once its same-bucket predecessors are
+    slot_prefix(ctl, S, [&](uint32_t i) { return min(ctl->slot[i].nm, n) - ctl->slot[i].mstart; });
+    __syncthreads();
+    const uint32_t total = ctl->pref[S];
+    for (uint32_t k = tid; k < total; k += T) {
+      const uint32_t i = find_slot(ctl->pref, S, k);
+      SlotArrays a = slot_arrays(smem, L, n, i);
+      const uint32_t v = a.ord[ctl->slot[i].mstart + k - ctl->pref[i]];
+      a.sig[v] = (v == ctl->slot[i].s) ? 1ull : 0ull;
     }
-    grp.sync();
+    __syncthreads();
     for (uint32_t pass = 0;; ++pass) {
-      if (pass > mend - mstart + 1) { my_err |= kErrPassLimit; ok = false; break; }
+      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
       bool open = false;
-      for (uint32_t idx = mstart + t; idx < mend; idx += G) {
+      for (uint32_t k = tid; k < total; k += T) {
+        const uint32_t i = find_slot(ctl->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, i);
+        const uint32_t idx = ctl->slot[i].mstart + k - ctl->pref[i];
         const uint32_t v = a.ord[idx];
         const uint32_t dv = a.dist[v];
         if (dv & kFlag) continue;
+        const uint32_t s = ctl->slot[i].s;
         uint64_t acc = (v == s) ? 1ull : 0ull;
         bool all_final = true;
         if (v != s) {
@@ -194,8 +261,7 @@ __device__ bool brandes_one_source(Group<G> &grp, const Realized &H, GroupArrays
             const uint32_t u = pk & 0xFFFFu;
             const uint32_t du = a.dist[u];
             if ((du & kMask) + (pk >> 16) != dv) continue;
-            const uint64_t su = a.sig[u];
-            const uint64_t nx = acc + su;
+            const uint64_t nx = acc + a.sig[u];
             if (nx < acc) my_ovf = 1;
             acc = nx;
             if (!(du & kFlag)) all_final = false;
@@ -205,43 +271,84 @@ __device__ bool brandes_one_source(Group<G> &grp, const Realized &H, GroupArrays
         if (all_final) a.ord[idx] = (uint16_t)(v | kMark);
         else open = true;
       }
-      grp.sync();
-      for (uint32_t idx = mstart + t; idx < mend; idx += G) {
+      __syncthreads();
+      for (uint32_t k = tid; k < total; k += T) {
+        const uint32_t i = find_slot(ctl->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, i);
+        const uint32_t idx = ctl->slot[i].mstart + k - ctl->pref[i];
         const uint32_t e = a.ord[idx];
         if (e & kMark) {
           a.ord[idx] = (uint16_t)(e & ~kMark);
           a.dist[e & ~kMark] |= kFlag;
         }
       }
-      if (!grp.any(open)) break;
+      if (!__syncthreads_or(open)) break;
     }
     if (!ok) break;
-    nset = mend;
+    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].mstart = min(ctl->slot[i].nm, n);
+    __syncthreads();
+    b += 1;
   }
   if (!ok) {
-    atomicOr(err, my_err);
+    if (my_err) atomicOr(&ctl->err, my_err);
+    __syncthreads();
     return false;
   }
 
-  // (5) dependencies, buckets in reverse order; kFlag now means "delta still pending"
+  // ---- backward: dependencies, buckets in decreasing order; kFlag = "delta pending"
   if (want_delta) {
-    uint32_t hi = nset;
-    while (hi > 0) {
-      const uint32_t bid = (a.dist[a.ord[hi - 1]] & kMask) / delta;
-      uint32_t lo = 0;
-      for (uint32_t top = hi; top > 0;) {
-        const uint32_t base = top > G ? top - G : 0;
-        const uint32_t i = base + t;
-        uint32_t cand = 0;
-        if (i < top && (a.dist[a.ord[i]] & kMask) / delta != bid) cand = i + 1;
-        const uint32_t found = grp.reduce_max(cand);
-        if (found > 0) { lo = found; break; }
-        top = base;
+    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].hi = ctl->slot[i].mstart;
+    __syncthreads();
+    const uint32_t warp = tid >> 5, lane = tid & 31u, nw = T >> 5;
+    for (uint32_t guard = 0;; ++guard) {
+      if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
+      if (tid < 32) {
+        uint32_t best = 0;  // 1 + bucket id of the last unprocessed member, 0 if none
+        for (uint32_t i = lane; i < S; i += 32) {
+          const uint32_t hi = ctl->slot[i].hi;
+          if (hi > 0) {
+            SlotArrays a = slot_arrays(smem, L, n, i);
+            const uint32_t bb = (a.dist[a.ord[hi - 1]] & kMask) / delta + 1u;
+            best = max(best, bb);
+          }
+        }
+        best = __reduce_max_sync(kFull, best);
+        if (lane == 0) ctl->bucket = best;
       }
+      __syncthreads();
+      const uint32_t bb = ctl->bucket;
+      if (bb == 0) break;
+      const uint32_t bcur = bb - 1u;
+      // per slot: start of the run of bucket bcur at the end of its settled list
+      for (uint32_t i = warp; i < S; i += nw) {
+        SlotArrays a = slot_arrays(smem, L, n, i);
+        const uint32_t hi = ctl->slot[i].hi;
+        uint32_t lo = hi;
+        if (hi > 0 && (a.dist[a.ord[hi - 1]] & kMask) / delta == bcur) {
+          lo = 0;
+          for (uint32_t top = hi; top > 0;) {
+            const uint32_t base = top > 32u ? top - 32u : 0u;
+            const uint32_t p = base + lane;
+            uint32_t cand = 0;
+            if (p < top && (a.dist[a.ord[p]] & kMask) / delta != bcur) cand = p + 1u;
+            const uint32_t found = __reduce_max_sync(kFull, cand);
+            if (found > 0) { lo = found; break; }
+            top = base;
+          }
+        }
+        if (lane == 0) ctl->slot[i].lo = lo;
+      }
+      __syncthreads();
+      slot_prefix(ctl, S, [&](uint32_t i) { return ctl->slot[i].hi - ctl->slot[i].lo; });
+      __syncthreads();
+      const uint32_t total = ctl->pref[S];
       for (uint32_t pass = 0;; ++pass) {
-        if (pass > hi - lo + 1) { my_err |= kErrPassLimit; ok = false; break; }
+        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
         bool open = false;
-        for (uint32_t idx = lo + t; idx < hi; idx += G) {
+        for (uint32_t k = tid; k < total; k += T) {
+          const uint32_t i = find_slot(ctl->pref, S, k);
+          SlotArrays a = slot_arrays(smem, L, n, i);
+          const uint32_t idx = ctl->slot[i].lo + k - ctl->pref[i];
           const uint32_t v = a.ord[idx];
           const uint32_t dv = a.dist[v];
           if (!(dv & kFlag)) continue;
@@ -254,36 +361,48 @@ __device__ bool brandes_one_source(Group<G> &grp, const Realized &H, GroupArrays
             const uint32_t w = pk & 0xFFFFu;
             const uint32_t dw = a.dist[w];
             if ((dw & kMask) != dvm + (pk >> 16)) continue;
-            acc += reinterpret_cast<const DT *>(a.dlt)[w];
+            acc += *reinterpret_cast<const DT *>(&a.sig[w]);   // rho(w) once w is final
             if (dw & kFlag) all_final = false;
           }
           if (all_final) {
-            const DT sv = (DT)a.sig[v];
-            const DT dep = sv * acc;
-            reinterpret_cast<DT *>(a.dlt)[v] = ((DT)1 + dep) / sv;
-            if (v != s) atomicAdd(&bc[v], (double)dep);
+            const uint64_t sg = a.sig[v];
+            DT dep, rho;
+            if (sg == 1ull) {           // unique shortest path: no division needed
+              dep = acc;
+              rho = (DT)1 + dep;
+            } else {
+              const DT sv = (DT)sg;
+              dep = sv * acc;
+              rho = ((DT)1 + dep) / sv;
+            }
+            *reinterpret_cast<DT *>(&a.sig[v]) = rho;
+            if (v != ctl->slot[i].s) atomicAdd(&bc[v], (double)dep);
             a.ord[idx] = (uint16_t)(v | kMark);
           } else {
             open = true;
           }
         }
-        grp.sync();
-        for (uint32_t idx = lo + t; idx < hi; idx += G) {
+        __syncthreads();
+        for (uint32_t k = tid; k < total; k += T) {
+          const uint32_t i = find_slot(ctl->pref, S, k);
+          SlotArrays a = slot_arrays(smem, L, n, i);
+          const uint32_t idx = ctl->slot[i].lo + k - ctl->pref[i];
           const uint32_t e = a.ord[idx];
           if (e & kMark) {
             a.ord[idx] = (uint16_t)(e & ~kMark);
             a.dist[e & ~kMark] &= kMask;
           }
         }
-        if (!grp.any(open)) break;
+        if (!__syncthreads_or(open)) break;
       }
       if (!ok) break;
-      hi = lo;
+      for (uint32_t i = tid; i < S; i += T) ctl->slot[i].hi = ctl->slot[i].lo;
+      __syncthreads();
     }
   }
-  if (my_err) atomicOr(err, my_err);
-  if (my_ovf) atomicOr(ovf, 1u);
-  grp.sync();
+  if (my_err) atomicOr(&ctl->err, my_err);
+  if (my_ovf) atomicOr(&ctl->ovf, 1u);
+  __syncthreads();
   return ok;
 }
 
@@ -329,10 +448,10 @@ __device__ __forceinline__ void edge_draw(const McDev &P, uint32_t r, uint32_t e
   w = lo + (uint32_t)(((uint64_t)u.y * ((uint64_t)hi - lo + 1u)) >> 32);
 }
 
-// Builds the alive-compacted CSR of realization r into rp/arc.  Thread-per-vertex over
-// contiguous vertex ranges so that the offsets come from one block scan.
+// Builds the alive-compacted CSR of realization r into rp/arc (thread per contiguous vertex
+// range, offsets from one block scan) and the largest alive length into ctl->wmax.
 __device__ void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uint32_t *arc,
-                            CtaCtl *ctl, uint32_t *err) {
+                            CtaCtl *ctl) {
   const uint32_t n = P.n;
   const uint32_t cap = (uint32_t)(2 * P.m);   // arc slots reserved in the layout
   const uint32_t T = blockDim.x;
@@ -350,20 +469,25 @@ __device__ void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uint32_t *
     }
   }
   uint32_t off = block_exclusive_scan(cnt, ctl->scan, &ctl->scan_total);
+  uint32_t wmax = 1, err = 0;
   for (uint32_t v = v0; v < v1; ++v) {
     rp[v] = off;
     const int32_t a0 = P.row_ptr[v], a1 = P.row_ptr[v + 1];
     for (int32_t a = a0; a < a1; ++a) {
       const uint32_t e = (uint32_t)P.eid[a];
       const uint32_t u = (uint32_t)P.col[a];
-      if (e >= (uint64_t)P.m || u >= n) { atomicOr(err, kErrInput); continue; }
+      if (e >= (uint64_t)P.m || u >= n) { err = kErrInput; continue; }
       bool alive; uint32_t w;
       edge_draw(P, r, e, alive, w);
       if (!alive) continue;
-      if (w == 0 || w > 0xFFFFu || off >= cap) { atomicOr(err, kErrInput); continue; }
+      if (w == 0 || w > 0xFFFFu || off >= cap) { err = kErrInput; continue; }
       arc[off++] = u | (w << 16);
+      wmax = max(wmax, w);
     }
   }
+  if (err) atomicOr(&ctl->err, err);
+  wmax = __reduce_max_sync(kFull, wmax);
+  if ((threadIdx.x & 31u) == 0) atomicMax(&ctl->wmax, wmax);
   const uint32_t total = ctl->scan_total;
   if (threadIdx.x == 0) rp[n] = total < cap ? total : cap;
   __syncthreads();
@@ -413,30 +537,40 @@ __device__ __forceinline__ bool comp_valid(uint32_t info, uint32_t k_min) {
   return (info & kHasCand) && (info & kSizeMask) >= k_min;
 }
 
+// Effective bucket width: at least ceil(wmax / (kRing - 2)) so that all discovered distances
+// beyond the current bucket fit into the ring of bucket bitmaps.
+__device__ __forceinline__ void bucket_setup(CtaCtl *ctl, uint32_t delta_req) {
+  if (threadIdx.x == 0) {
+    const uint32_t wmax = ctl->wmax;
+    const uint32_t dmin = (wmax + (kRing - 2) - 1) / (kRing - 2);
+    const uint32_t delta = max(max(delta_req, 1u), dmin);
+    ctl->delta = delta;
+    ctl->ring_b = min((uint32_t)kRing, (wmax + delta - 1) / delta + 2u);
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------
-// Select (A6) and count.  Per-root scratch borrows group 0's arrays.
-// Returns true when the FP32 gap test asks for an FP64 recheck.
+// Select (A6) and count.  Scratch: slot 0's sig (u64 per root), slot 0's dist (centre per
+// root), the layout's sel array (rank per root).  Returns true when the FP32 gap test asks
+// for an FP64 recheck (then nothing is committed).
 // ---------------------------------------------------------------------------------------
 __device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_t *comp,
-                                 const uint32_t *cinfo, const double *bc, GroupArrays s0,
-                                 bool gap_test, bool commit, CtaCtl *ctl) {
+                                 const uint32_t *cinfo, const double *bc, SlotArrays s0,
+                                 uint32_t *rank, bool gap_test, CtaCtl *ctl) {
   const uint32_t n = P.n;
-  unsigned long long *best = reinterpret_cast<unsigned long long *>(s0.sig);   // max over X
-  unsigned long long *bestK = reinterpret_cast<unsigned long long *>(s0.dlt);  // max over K
+  unsigned long long *best = reinterpret_cast<unsigned long long *>(s0.sig);
   uint32_t *centre = s0.dist;
-  uint32_t *rank = reinterpret_cast<uint32_t *>(s0.ord);  // 2n bytes + 2n bytes of pend: 4n
-  uint32_t &need_recheck = ctl->need_recheck;
-  if (threadIdx.x == 0) need_recheck = 0;
+  if (threadIdx.x == 0) ctl->need_recheck = 0;
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    best[v] = 0ull; bestK[v] = 0ull; centre[v] = 0xFFFFFFFFu; rank[v] = 1u;
+    best[v] = 0ull; centre[v] = 0xFFFFFFFFu; rank[v] = 1u;
   }
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
     const uint32_t root = comp[v];
     if (!comp_valid(cinfo[root], P.k_min)) continue;
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(bc[v]);
-    if (P.top_k) atomicMax(&bestK[root], bits);
-    if (P.in_w == nullptr || P.in_w[v]) atomicMax(&best[root], bits);
+    if (P.in_w == nullptr || P.in_w[v])
+      atomicMax(&best[root], (unsigned long long)__double_as_longlong(bc[v]));
   }
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -448,13 +582,23 @@ __device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_
   }
   __syncthreads();
   if (P.top_k || gap_test) {
+    if (P.top_k) {   // best now becomes the maximum over the whole component
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) best[v] = 0ull;
+      __syncthreads();
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+        const uint32_t root = comp[v];
+        if (comp_valid(cinfo[root], P.k_min))
+          atomicMax(&best[root], (unsigned long long)__double_as_longlong(bc[v]));
+      }
+      __syncthreads();
+    }
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
       const uint32_t root = comp[v];
       if (!comp_valid(cinfo[root], P.k_min)) continue;
       const uint32_t c = centre[root];
       if (c == v || c >= n) continue;
       if (P.top_k) {
-        const double tauK = P.tie_rel * __longlong_as_double((long long)bestK[root]);
+        const double tauK = P.tie_rel * __longlong_as_double((long long)best[root]);
         const double diff = bc[v] - bc[c];
         if (diff > tauK || (fabs(diff) <= tauK && v < c)) atomicAdd(&rank[root], 1u);
       }
@@ -462,13 +606,12 @@ __device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_
         // top-two gap of the candidate set (of the whole component when a rank cutoff is
         // active): another node within the margin of B1 sends the realization to FP64
         const double b1 = bc[c];
-        if (b1 > 0.0 && fabs(b1 - bc[v]) < P.recheck_margin * b1) need_recheck = 1;
+        if (b1 > 0.0 && fabs(b1 - bc[v]) < P.recheck_margin * b1) ctl->need_recheck = 1;
       }
     }
     __syncthreads();
   }
-  const bool recheck = gap_test && need_recheck;
-  if (recheck || !commit) return recheck;
+  if (gap_test && ctl->need_recheck) return true;
   uint32_t *counts = P.counts;
   const size_t stride = (size_t)n + 1;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -491,22 +634,12 @@ __device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_
 // The persistent kernel.  Work item w enumerates (problem, realization) pairs of all
 // problems; items are visited in strided order by the CTAs.
 // ---------------------------------------------------------------------------------------
-template <int G>
-__global__ void __launch_bounds__(1024, 1)
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1)
 mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *item_prefix,
-                 uint64_t total_items, unsigned char *gslab, uint32_t slab_bytes,
-                 uint32_t ngroups) {
+                 uint64_t total_items, uint32_t nslots) {
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char *base = gslab ? gslab + (size_t)blockIdx.x * slab_bytes : smem;
-  CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);  // control block always in shared memory
-  const uint32_t gidx = threadIdx.x / G;
-  const bool in_group = gidx < ngroups;
-  Group<G> grp;
-  grp.idx = gidx;
-  grp.rank = threadIdx.x % G;
-  grp.red = ctl->gred[gidx < kMaxGroups ? gidx : 0];
-  grp.turn = 0;
-
+  CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
   for (uint64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     int g = 0;
     while (g + 1 < nprob && item_prefix[g + 1] <= item) ++g;
@@ -515,33 +648,46 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     const uint32_t r = P.r_begin + r_local;
     const uint32_t n = P.n;
     Layout L;
-    L.make(n, (uint32_t)(2 * P.m), ngroups);
-    uint32_t *rp = reinterpret_cast<uint32_t *>(base + L.off_rp);
-    uint32_t *arc = reinterpret_cast<uint32_t *>(base + L.off_arc);
-    uint32_t *comp = reinterpret_cast<uint32_t *>(base + L.off_comp);
-    uint32_t *cinfo = reinterpret_cast<uint32_t *>(base + L.off_cinfo);
-    double *bc = reinterpret_cast<double *>(base + L.off_bc);
-    uint16_t *src = reinterpret_cast<uint16_t *>(base + L.off_src);
-    if (threadIdx.x < kMaxGroups * 3) (&ctl->gred[0][0])[threadIdx.x] = 0xFFFFFFFFu;
-    if (threadIdx.x == 0) { ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->cursor = 0; ctl->edges = 0; ctl->verts = 0; }
+    L.make(n, (uint32_t)(2 * P.m), nslots);
+    uint32_t *rp = reinterpret_cast<uint32_t *>(smem + L.off_rp);
+    uint32_t *arc = reinterpret_cast<uint32_t *>(smem + L.off_arc);
+    uint32_t *comp = reinterpret_cast<uint32_t *>(smem + L.off_comp);
+    uint32_t *cinfo = reinterpret_cast<uint32_t *>(smem + L.off_cinfo);
+    double *bc = reinterpret_cast<double *>(smem + L.off_bc);
+    uint16_t *src = reinterpret_cast<uint16_t *>(smem + L.off_src);
+    uint32_t *sel = reinterpret_cast<uint32_t *>(smem + L.off_sel);
+    if (threadIdx.x == 0) {
+      ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->edges = 0; ctl->verts = 0; ctl->wmax = 1;
+    }
     __syncthreads();
 
-    realize_csr(P, r, rp, arc, ctl, &ctl->err);
+    realize_csr(P, r, rp, arc, ctl);
     Realized H{n, rp, arc};
     components(P, H, comp, cinfo);
+    bucket_setup(ctl, P.delta);
+    const uint32_t delta = ctl->delta, ringB = ctl->ring_b;
 
-    // sources: every node of a valid component; alive edges per root for the TEPS count
-    GroupArrays g0 = group_arrays(base, L, n, 0);
-    uint32_t *cedges = g0.dist;
+    // sources: every node of a valid component (ascending), alive edges per root for TEPS
+    uint32_t *cedges = sel;
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { cedges[v] = 0; bc[v] = 0.0; }
     __syncthreads();
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
       const uint32_t root = comp[v];
       if (!comp_valid(cinfo[root], P.k_min)) continue;
-      src[atomicAdd(&ctl->nsrc, 1u)] = (uint16_t)v;
       uint32_t up = 0;
       for (uint32_t e = rp[v]; e < rp[v + 1]; ++e) up += ((arc[e] & 0xFFFFu) > v) ? 1u : 0u;
       if (up) atomicAdd(&cedges[root], up);
+    }
+    {
+      // ordered compaction of the sources (keeps the batches deterministic)
+      const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+      const uint32_t v0 = min(n, threadIdx.x * per), v1 = min(n, v0 + per);
+      uint32_t cnt = 0;
+      for (uint32_t v = v0; v < v1; ++v) cnt += comp_valid(cinfo[comp[v]], P.k_min) ? 1u : 0u;
+      uint32_t off = block_exclusive_scan(cnt, ctl->scan, &ctl->scan_total);
+      for (uint32_t v = v0; v < v1; ++v)
+        if (comp_valid(cinfo[comp[v]], P.k_min)) src[off++] = (uint16_t)v;
+      if (threadIdx.x == 0) ctl->nsrc = ctl->scan_total;
     }
     __syncthreads();
     {
@@ -563,40 +709,28 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
       const bool use32 = fp32 && attempt == 0;
       if (attempt == 1) {
         for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] = 0.0;
-        if (threadIdx.x == 0) ctl->cursor = 0;
         __syncthreads();
       }
-      if (in_group) {
-        GroupArrays ga = group_arrays(base, L, n, gidx);
-        GroupCtl *gc = &ctl->gctl[gidx];
-        for (;;) {
-          if (grp.rank == 0) gc->claim = atomicAdd(&ctl->cursor, 1u);
-          grp.sync();
-          const uint32_t k = gc->claim;
-          grp.sync();
-          if (k >= nsrc) break;
-          const uint32_t s = src[k];
-          if (use32)
-            brandes_one_source<G, float>(grp, H, ga, gc, s, P.delta, bc, true, &ctl->err, &ctl->ovf);
-          else
-            brandes_one_source<G, double>(grp, H, ga, gc, s, P.delta, bc, true, &ctl->err, &ctl->ovf);
-        }
+      for (uint32_t k0 = 0; k0 < nsrc; k0 += nslots) {
+        const uint32_t S = min(nslots, nsrc - k0);
+        if (use32)
+          brandes_batch<float>(H, smem, L, S, src + k0, delta, ringB, bc, true, ctl);
+        else
+          brandes_batch<double>(H, smem, L, S, src + k0, delta, ringB, bc, true, ctl);
       }
-      __syncthreads();
-      const bool recheck = select_and_count(P, r_local, comp, cinfo, bc, g0, use32, true, ctl);
+      const bool recheck = select_and_count(P, r_local, comp, cinfo, bc,
+                                            slot_arrays(smem, L, n, 0), sel, use32, ctl);
       __syncthreads();
       if (!recheck) break;
       if (threadIdx.x == 0 && P.stats) atomicAdd(u64p(&P.stats->rechecked), 1ull);
     }
-    if (threadIdx.x == 0) {
-      if (ctl->err && P.stats) atomicOr(u64p(&P.stats->device_error), (unsigned long long)ctl->err);
-      if (P.stats) {
-        atomicAdd(u64p(&P.stats->realizations), 1ull);
-        atomicAdd(u64p(&P.stats->sources), (unsigned long long)nsrc);
-        atomicAdd(u64p(&P.stats->edge_visits), (unsigned long long)ctl->edges);
-        atomicAdd(u64p(&P.stats->vertex_visits), (unsigned long long)ctl->verts);
-        if (ctl->ovf) atomicAdd(u64p(&P.stats->overflow), 1ull);
-      }
+    if (threadIdx.x == 0 && P.stats) {
+      if (ctl->err) atomicOr(u64p(&P.stats->device_error), (unsigned long long)ctl->err);
+      atomicAdd(u64p(&P.stats->realizations), 1ull);
+      atomicAdd(u64p(&P.stats->sources), (unsigned long long)nsrc);
+      atomicAdd(u64p(&P.stats->edge_visits), (unsigned long long)ctl->edges);
+      atomicAdd(u64p(&P.stats->vertex_visits), (unsigned long long)ctl->verts);
+      if (ctl->ovf) atomicAdd(u64p(&P.stats->overflow), 1ull);
     }
     __syncthreads();
   }
@@ -617,8 +751,7 @@ __global__ void debug_realize_kernel(McDev P, uint32_t r_count, uint8_t *alive, 
   }
 }
 
-__global__ void debug_components_kernel(McDev P, uint32_t ngroups, int32_t *comp_out,
-                                        int32_t *csize_out) {
+__global__ void debug_components_kernel(McDev P, int32_t *comp_out, int32_t *csize_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
   Layout L;
@@ -628,55 +761,53 @@ __global__ void debug_components_kernel(McDev P, uint32_t ngroups, int32_t *comp
   uint32_t *comp = reinterpret_cast<uint32_t *>(smem + L.off_comp);
   uint32_t *cinfo = reinterpret_cast<uint32_t *>(smem + L.off_cinfo);
   const uint32_t k = blockIdx.x;
-  if (threadIdx.x == 0) ctl->err = 0;
+  if (threadIdx.x == 0) { ctl->err = 0; ctl->wmax = 1; }
   __syncthreads();
-  realize_csr(P, P.r_begin + k, rp, arc, ctl, &ctl->err);
+  realize_csr(P, P.r_begin + k, rp, arc, ctl);
   Realized H{(uint32_t)P.n, rp, arc};
   components(P, H, comp, cinfo);
   for (uint32_t v = threadIdx.x; v < (uint32_t)P.n; v += blockDim.x) {
     comp_out[(size_t)k * P.n + v] = (int32_t)comp[v];
     csize_out[(size_t)k * P.n + v] = (int32_t)(cinfo[comp[v]] & kSizeMask);
   }
-  (void)ngroups;
 }
 
-template <int G>
-__global__ void __launch_bounds__(1024, 1)
-debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t ngroups,
+// Distances and path counts of given sources from the production batch routine: CTA b
+// handles sources [b*S, (b+1)*S) of the list on realization r.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1)
+debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t nslots,
                   uint32_t *dist_out, uint64_t *sigma_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
   const uint32_t n = P.n;
   Layout L;
-  L.make(n, (uint32_t)(2 * P.m), ngroups);
+  L.make(n, (uint32_t)(2 * P.m), nslots);
   uint32_t *rp = reinterpret_cast<uint32_t *>(smem + L.off_rp);
   uint32_t *arc = reinterpret_cast<uint32_t *>(smem + L.off_arc);
   double *bc = reinterpret_cast<double *>(smem + L.off_bc);
-  if (threadIdx.x < kMaxGroups * 3) (&ctl->gred[0][0])[threadIdx.x] = 0xFFFFFFFFu;
-  if (threadIdx.x == 0) { ctl->err = 0; ctl->ovf = 0; }
+  uint16_t *src = reinterpret_cast<uint16_t *>(smem + L.off_src);
+  if (threadIdx.x == 0) { ctl->err = 0; ctl->ovf = 0; ctl->wmax = 1; }
   __syncthreads();
-  realize_csr(P, r, rp, arc, ctl, &ctl->err);
+  realize_csr(P, r, rp, arc, ctl);
   Realized H{n, rp, arc};
-  const uint32_t gidx = threadIdx.x / G;
-  if (gidx < ngroups) {
-    Group<G> grp;
-    grp.idx = gidx;
-    grp.rank = threadIdx.x % G;
-    grp.red = ctl->gred[gidx];
-    grp.turn = 0;
-    GroupArrays ga = group_arrays(smem, L, n, gidx);
-    GroupCtl *gc = &ctl->gctl[gidx];
-    for (int32_t k = blockIdx.x * ngroups + gidx; k < nsrc; k += gridDim.x * ngroups) {
-      const uint32_t s = (uint32_t)sources[k];
-      if (s >= n) continue;
-      brandes_one_source<G, double>(grp, H, ga, gc, s, P.delta, bc, false, &ctl->err, &ctl->ovf);
-      for (uint32_t v = grp.rank; v < n; v += G) {
-        const uint32_t d = ga.dist[v] & kMask;
-        const bool reached = d < kInf;
-        dist_out[(size_t)k * n + v] = reached ? d : 0xFFFFFFFFu;
-        sigma_out[(size_t)k * n + v] = reached ? ga.sig[v] : 0ull;
-      }
-      grp.sync();
+  bucket_setup(ctl, P.delta);
+  const uint32_t k0 = blockIdx.x * nslots;
+  if (k0 < (uint32_t)nsrc) {
+    const uint32_t S = min(nslots, (uint32_t)nsrc - k0);
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+      const int32_t s = sources[k0 + i];
+      src[i] = (uint16_t)((s >= 0 && (uint32_t)s < n) ? s : 0);
+    }
+    __syncthreads();
+    brandes_batch<double>(H, smem, L, S, src, ctl->delta, ctl->ring_b, bc, false, ctl);
+    for (uint32_t t = threadIdx.x; t < S * n; t += blockDim.x) {
+      const uint32_t i = t / n, v = t - i * n;
+      SlotArrays a = slot_arrays(smem, L, n, i);
+      const uint32_t d = a.dist[v] & kMask;
+      const bool reached = d < kInf;
+      dist_out[(size_t)(k0 + i) * n + v] = reached ? d : 0xFFFFFFFFu;
+      sigma_out[(size_t)(k0 + i) * n + v] = reached ? a.sig[v] : 0ull;
     }
   }
   __syncthreads();
@@ -689,41 +820,39 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
 // ---------------------------------------------------------------------------------------
 // Host-side launch helpers (called from the C ABI)
 // ---------------------------------------------------------------------------------------
-uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t ngroups) {
+uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots) {
   Layout L;
-  L.make(n, (uint32_t)arcs, ngroups);
+  L.make(n, (uint32_t)arcs, nslots);
   return L.total;
 }
 
-cudaError_t launch_mc_counts(int G, const McDev *probs_dev, int nprob, const uint64_t *prefix_dev,
-                             uint64_t total_items, unsigned char *gslab, uint32_t slab_bytes,
-                             uint32_t ngroups, uint32_t smem_bytes, uint32_t grid,
-                             cudaStream_t stream) {
-  const uint32_t threads = ngroups * (uint32_t)G;
-  switch (G) {
-    case 32:
-      cudaFuncSetAttribute(mc_counts_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-      mc_counts_kernel<32><<<grid, threads, smem_bytes, stream>>>(probs_dev, nprob, prefix_dev, total_items, gslab, slab_bytes, ngroups);
-      break;
-    case 64:
-      cudaFuncSetAttribute(mc_counts_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-      mc_counts_kernel<64><<<grid, threads, smem_bytes, stream>>>(probs_dev, nprob, prefix_dev, total_items, gslab, slab_bytes, ngroups);
-      break;
-    case 128:
-      cudaFuncSetAttribute(mc_counts_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-      mc_counts_kernel<128><<<grid, threads, smem_bytes, stream>>>(probs_dev, nprob, prefix_dev, total_items, gslab, slab_bytes, ngroups);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+template <int BLOCK>
+static cudaError_t launch_counts_t(const McDev *probs_dev, int nprob, const uint64_t *prefix_dev,
+                                   uint64_t total_items, uint32_t nslots, uint32_t smem,
+                                   uint32_t grid, cudaStream_t stream) {
+  cudaFuncSetAttribute(mc_counts_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  mc_counts_kernel<BLOCK><<<grid, BLOCK, smem, stream>>>(probs_dev, nprob, prefix_dev,
+                                                         total_items, nslots);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mc_counts(int block, const McDev *probs_dev, int nprob,
+                             const uint64_t *prefix_dev, uint64_t total_items, uint32_t nslots,
+                             uint32_t smem_bytes, uint32_t grid, cudaStream_t stream) {
+  switch (block) {
+    case 256: return launch_counts_t<256>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
+    case 512: return launch_counts_t<512>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
+    case 1024: return launch_counts_t<1024>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
                                  cudaStream_t stream) {
   const uint64_t total = (uint64_t)r_count * P.m;
-  const uint32_t grid = (uint32_t)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   if (total == 0) return cudaSuccess;
+  const uint64_t want = (total + 255) / 256;
+  const uint32_t grid = (uint32_t)(want < 4096 ? want : 4096);
   debug_realize_kernel<<<grid, 256, 0, stream>>>(P, r_count, alive, w);
   return cudaGetLastError();
 }
@@ -732,31 +861,29 @@ cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *c
                                     cudaStream_t stream) {
   const uint32_t smem = mc_layout_bytes(P.n, 2 * P.m, 0);
   cudaFuncSetAttribute(debug_components_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  debug_components_kernel<<<r_count, 256, smem, stream>>>(P, 0, comp, csize);
+  debug_components_kernel<<<r_count, 256, smem, stream>>>(P, comp, csize);
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_sssp(int G, const McDev &P, uint32_t r, const int32_t *sources, int32_t nsrc,
-                              uint32_t ngroups, uint32_t smem, uint32_t grid, uint32_t *dist,
-                              uint64_t *sigma, cudaStream_t stream) {
-  const uint32_t threads = ngroups * (uint32_t)G;
-  switch (G) {
-    case 32:
-      cudaFuncSetAttribute(debug_sssp_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      debug_sssp_kernel<32><<<grid, threads, smem, stream>>>(P, r, sources, nsrc, ngroups, dist, sigma);
-      break;
-    case 64:
-      cudaFuncSetAttribute(debug_sssp_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      debug_sssp_kernel<64><<<grid, threads, smem, stream>>>(P, r, sources, nsrc, ngroups, dist, sigma);
-      break;
-    case 128:
-      cudaFuncSetAttribute(debug_sssp_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      debug_sssp_kernel<128><<<grid, threads, smem, stream>>>(P, r, sources, nsrc, ngroups, dist, sigma);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+template <int BLOCK>
+static cudaError_t launch_sssp_t(const McDev &P, uint32_t r, const int32_t *sources, int32_t nsrc,
+                                 uint32_t nslots, uint32_t smem, uint32_t *dist, uint64_t *sigma,
+                                 cudaStream_t stream) {
+  const uint32_t grid = (uint32_t)((nsrc + (int32_t)nslots - 1) / (int32_t)nslots);
+  cudaFuncSetAttribute(debug_sssp_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  debug_sssp_kernel<BLOCK><<<grid, BLOCK, smem, stream>>>(P, r, sources, nsrc, nslots, dist, sigma);
   return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sssp(int block, const McDev &P, uint32_t r, const int32_t *sources,
+                              int32_t nsrc, uint32_t nslots, uint32_t smem, uint32_t *dist,
+                              uint64_t *sigma, cudaStream_t stream) {
+  switch (block) {
+    case 256: return launch_sssp_t<256>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
+    case 512: return launch_sssp_t<512>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
+    case 1024: return launch_sssp_t<1024>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace afc

@@ -63,6 +63,6 @@ def test_validation_errors_without_device():
     prob.w_lo_all, prob.w_hi_all, prob.k_min = 0, 3, 1
     with pytest.raises(afc.AfcError):
         afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)
-    prob.w_lo_all, prob.k_min, prob.group_threads = 1, 1, 48
+    prob.w_lo_all, prob.k_min, prob.block_threads = 1, 1, 48
     with pytest.raises(afc.AfcError):
         afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)

@@ -115,25 +115,26 @@ def _sssp_check(wl, r, sources, **kw):
     return any_ovf, int(st[3])
 
 
-@pytest.mark.parametrize("G", [32, 64, 128])
+@pytest.mark.parametrize("B", [256, 512, 1024])
 @pytest.mark.parametrize("delta", [0, 1, 4, 1000])
-def test_sssp_sigma_small_er_all_sources(G, delta):
+def test_sssp_sigma_small_er_all_sources(B, delta):
     wl = _small_er()
-    _sssp_check(wl, 2, list(range(wl.n)), group_threads=G, bucket_width=delta)
+    _sssp_check(wl, 2, list(range(wl.n)), block_threads=B, bucket_width=delta)
 
 
-@pytest.mark.parametrize("G,delta", [(32, 0), (64, 0), (128, 0), (64, 1), (64, 7), (64, 200)])
-def test_sssp_sigma_ws1000_sampled(G, delta):
+@pytest.mark.parametrize("B,delta", [(256, 0), (512, 0), (1024, 0), (512, 1), (512, 7),
+                                     (512, 200)])
+def test_sssp_sigma_ws1000_sampled(B, delta):
     wl = _ws1000()
-    rng = np.random.default_rng(G + delta)
+    rng = np.random.default_rng(B + delta)
     sources = sorted(rng.choice(wl.n, 48, replace=False).tolist())
-    _sssp_check(wl, 1, sources, group_threads=G, bucket_width=delta)
+    _sssp_check(wl, 1, sources, block_threads=B, bucket_width=delta)
 
 
 def test_sssp_unweighted_grid_large_sigma():
     eu, ev = grid_edges(30, 30)
     wl = Workload("grid", 900, eu, ev, 1.0, 1, 1, 1, seed=1)
-    _sssp_check(wl, 0, [0, 29, 435, 899], group_threads=64)
+    _sssp_check(wl, 0, [0, 29, 435, 899], block_threads=512)
 
 
 def test_sigma_overflow_reported():
@@ -147,7 +148,7 @@ def test_sigma_overflow_reported():
     ev = np.array([max(p) for p in pairs], np.int32)
     order = np.lexsort((ev, eu))
     wl = Workload("diamonds", nxt, eu[order], ev[order], 1.0, 1, 1, 1, seed=1)
-    ovf, dev_ovf = _sssp_check(wl, 0, [0, 3], group_threads=32)
+    ovf, dev_ovf = _sssp_check(wl, 0, [0, 3], block_threads=256)
     assert ovf and dev_ovf >= 1
 
 
@@ -175,11 +176,11 @@ def _mc_check(wl, r_begin, r_count, **kw):
     return worst
 
 
-@pytest.mark.parametrize("G", [32, 64])
-def test_small_er_full_counts_bit_exact(G):
+@pytest.mark.parametrize("B", [256, 1024])
+def test_small_er_full_counts_bit_exact(B):
     """The small ER workload end to end: all 1000 realizations, counts bit-exact."""
     wl = _small_er()
-    q = _dev(wl, group_threads=G)
+    q = _dev(wl, block_threads=B)
     q.run_counts()
     oc, _ = oracle_counts(wl, 0, wl.realizations, threads=4)
     assert (q.counts.cpu().numpy().view(np.uint32) == oc).all()
@@ -239,7 +240,7 @@ def test_shards_sum_bit_exact():
 
 def test_batched_equals_individual():
     wls = [_small_er(), variant(_crossroads(), graph_tag=3), workload("paper_ws100")]
-    qs = [_dev(w, group_threads=32) for w in wls]
+    qs = [_dev(w, block_threads=256) for w in wls]
     probs = (afc.McProblem * len(wls))(*[q.prob for q in qs])
     rc = np.array([w.realizations for w in wls], np.uint32)
     counts_ptrs = np.array([q.counts.data_ptr() for q in qs], np.uint64)
