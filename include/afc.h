@@ -99,6 +99,10 @@ typedef struct {
                              /* least ceil(max length / 10)); 0 = automatic                */
   int32_t block_threads;     /* threads per CTA of the counting kernel: 256, 512 or 1024;  */
                              /* 0 = automatic                                              */
+  int32_t team_threads;      /* threads of one team (32 .. block_threads, a power of two); */
+                             /* each team advances its own batch of sources; 0 = auto      */
+  int32_t slots_per_team;    /* sources a team advances in lockstep (1..16); 0 = as many   */
+                             /* as shared memory holds                                     */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */

@@ -54,7 +54,8 @@ class McProblem(ctypes.Structure):
                 ("w_lo", c_p), ("w_hi", c_p), ("w_lo_all", c_u32), ("w_hi_all", c_u32),
                 ("k_min", c_u32), ("in_w", c_p), ("top_k", c_u32), ("tie_rel", c_f64),
                 ("precision", c_i32), ("recheck_margin", c_f64), ("bucket_width", c_u32),
-                ("block_threads", c_i32)]
+                ("block_threads", c_i32), ("team_threads", c_i32),
+                ("slots_per_team", c_i32)]
 
 
 class McStats(ctypes.Structure):

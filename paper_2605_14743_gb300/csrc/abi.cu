@@ -63,7 +63,7 @@ uint32_t auto_delta(const afc_mc_problem &p) {
 
 int auto_block(const afc_mc_problem &p) {
   if (p.block_threads) return p.block_threads;
-  return p.n >= 128 ? 512 : 256;
+  return p.n >= 128 ? 1024 : 256;
 }
 
 int validate(const afc_mc_problem *p) {
@@ -82,6 +82,10 @@ int validate(const afc_mc_problem *p) {
   if (p->precision == AFC_FP32_RECHECK && !(p->recheck_margin >= 0.0)) return fail(AFC_EINVAL, "bad recheck_margin");
   const int B = auto_block(*p);
   if (B != 256 && B != 512 && B != 1024) return fail(AFC_EINVAL, "block_threads must be 256, 512 or 1024");
+  if (p->team_threads && !mc_config_supported(B, p->team_threads))
+    return fail(AFC_EINVAL, "team_threads %d not supported with block_threads %d", p->team_threads, B);
+  if (p->slots_per_team < 0 || p->slots_per_team > kMaxSlotsPerTeam)
+    return fail(AFC_EINVAL, "slots_per_team must be in [0, %d]", kMaxSlotsPerTeam);
   if (p->bucket_width > 0x7FFFFFFF) return fail(AFC_EINVAL, "bucket_width too large");
   return AFC_OK;
 }
@@ -118,37 +122,61 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   return d;
 }
 
-// Launch plan of the counting kernel for a set of problems.
+// Launch plan of the counting kernel for a set of problems: block size, team size, slots
+// per team (sources a team advances together) and grid.
 struct McPlan {
-  int block = 512;
-  uint32_t nslots = 1, smem = 0, grid = 1;
+  int block = 1024, team = 256;
+  uint32_t spt = 1, smem = 0, grid = 1;
   size_t ws_meta = 0, ws_total = 0;
   bool fits = true;
 };
 
-McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items) {
+McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t total_items,
+                int req_team, int req_spt) {
   const DevInfo d = dev_info();
   McPlan pl;
-  pl.block = auto_block(probs[0]);
-  uint32_t nmax = 1;
-  uint64_t amax = 1;
-  for (int g = 0; g < nprob; ++g) {
-    nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
-    amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
-  }
+  pl.block = auto_block(p0);
   const uint32_t base = mc_layout_bytes(nmax, amax, 0);
   const uint32_t one = mc_layout_bytes(nmax, amax, 1) - base;
   const uint32_t cap = (uint32_t)std::max(0, d.smem_optin - 1024);
-  pl.fits = base + one <= cap;
+  const uint32_t fit = base <= cap ? (cap - base) / one : 0u;
+  // preferred team sizes, largest team last so that small graphs / small shared memory work
+  std::vector<int> prefs;
+  if (req_team) prefs.push_back(req_team);
+  else prefs = {256, 128, 512, 1024, 64, 32};
+  pl.fits = false;
+  for (int t : prefs) {
+    if (t > pl.block || !mc_config_supported(pl.block, t)) continue;
+    const uint32_t nt = (uint32_t)(pl.block / t);
+    if (fit < nt) continue;
+    uint32_t spt = std::min<uint32_t>(fit / nt, (uint32_t)kMaxSlotsPerTeam);
+    spt = std::min<uint32_t>(spt, std::max<uint32_t>(1u, (nmax + nt - 1) / nt));
+    if (req_spt) spt = std::min<uint32_t>(spt, (uint32_t)req_spt);
+    pl.team = t;
+    pl.spt = std::max<uint32_t>(1u, spt);
+    pl.fits = true;
+    break;
+  }
   if (pl.fits) {
-    pl.nslots = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxSlots, nmax});
-    pl.smem = mc_layout_bytes(nmax, amax, pl.nslots);
+    pl.smem = mc_layout_bytes(nmax, amax, (uint32_t)(pl.block / pl.team) * pl.spt);
     const uint32_t smem_sm = 228u * 1024u;
     const uint32_t per_sm = std::max<uint32_t>(1u, std::min<uint32_t>(smem_sm / (pl.smem + 1024u),
                                                                       2048u / (uint32_t)pl.block));
     pl.grid = (uint32_t)std::min<uint64_t>(total_items, (uint64_t)d.sms * per_sm);
   }
   if (pl.grid == 0) pl.grid = 1;
+  return pl;
+}
+
+McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items) {
+  uint32_t nmax = 1;
+  uint64_t amax = 1;
+  for (int g = 0; g < nprob; ++g) {
+    nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
+    amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
+  }
+  McPlan pl = plan_for(probs[0], nmax, amax, total_items, probs[0].team_threads,
+                       probs[0].slots_per_team);
   pl.ws_meta = ((sizeof(McDev) * (size_t)nprob + sizeof(uint64_t) * (size_t)(nprob + 1)) + 255) & ~size_t(255);
   pl.ws_total = pl.ws_meta;
   return pl;
@@ -184,8 +212,8 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   uint64_t *prefix_d = reinterpret_cast<uint64_t *>(ws + sizeof(McDev) * (size_t)nprob);
   AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)nprob, cudaMemcpyHostToDevice, stream));
   AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(nprob + 1), cudaMemcpyHostToDevice, stream));
-  cudaError_t e = launch_mc_counts(pl.block, devs_d, nprob, prefix_d, total, pl.nslots, pl.smem,
-                                   pl.grid, stream);
+  cudaError_t e = launch_mc_counts(pl.block, pl.team, devs_d, nprob, prefix_d, total, pl.spt,
+                                   pl.smem, pl.grid, stream);
   if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
   return AFC_OK;
 }
@@ -301,17 +329,12 @@ int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *source
   if (st) return st;
   if (nsrc < 0 || (nsrc > 0 && (!sources || !dist || !sigma))) return fail(AFC_EINVAL, "bad outputs");
   if (nsrc == 0) return AFC_OK;
-  const DevInfo di = dev_info();
-  const uint32_t base = mc_layout_bytes(prob->n, 2 * prob->m, 0);
-  const uint32_t one = mc_layout_bytes(prob->n, 2 * prob->m, 1) - base;
-  const uint32_t cap = (uint32_t)std::max(0, di.smem_optin - 1024);
-  if (base + one > cap) return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory SSSP kernel");
-  uint32_t ns = std::min<uint32_t>({(cap - base) / one, (uint32_t)kMaxSlots, (uint32_t)nsrc});
-  ns = std::max<uint32_t>(1, ns);
-  const uint32_t smem = mc_layout_bytes(prob->n, 2 * prob->m, ns);
+  const McPlan pl = plan_for(*prob, (uint32_t)prob->n, 2ull * (uint64_t)prob->m, (uint64_t)nsrc,
+                             prob->team_threads, prob->slots_per_team);
+  if (!pl.fits) return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory SSSP kernel");
   McDev d = to_dev(*prob, 0, nullptr, stats, nullptr, nullptr);
-  cudaError_t e = launch_debug_sssp(auto_block(*prob), d, r, sources, nsrc, ns, smem, dist, sigma,
-                                    (cudaStream_t)stream);
+  cudaError_t e = launch_debug_sssp(pl.block, pl.team, d, r, sources, nsrc, pl.spt, pl.smem, dist,
+                                    sigma, (cudaStream_t)stream);
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_sssp");
 }
 

@@ -41,37 +41,48 @@ struct McDev {
   int32_t *dump_next;
 };
 
-constexpr int kMaxSlots = 64;   // sources advanced together by one CTA
-constexpr int kRing = 12;       // bucket bitmaps per source (ring over pending distances)
+constexpr int kMaxSlots = 64;          // sources in flight per CTA
+constexpr int kMaxTeams = 32;          // independent thread teams per CTA
+constexpr int kMaxSlotsPerTeam = 16;   // sources a team advances in lockstep
+constexpr int kRing = 12;              // bucket bitmaps per source (ring over pending distances)
 
 struct SlotCtl {
-  uint32_t s, nm, mstart, hi, lo;
-  uint32_t ring_cnt[kRing];
+  uint32_t s, nm, mstart, hi, lo, ring_mask, pad[2];
+};
+
+struct TeamCtl {
+  uint32_t bucket, claim, nslots, base;
+  uint32_t red[4];
+  uint32_t pref[kMaxSlotsPerTeam + 1];
+  uint32_t pad[3];
 };
 
 struct CtaCtl {
-  uint32_t err, ovf, nsrc, bucket;
+  uint32_t err, ovf, nsrc, cursor;
   unsigned long long edges, verts;
   uint32_t need_recheck, delta, ring_b, wmax;
   uint32_t scan[32];
   uint32_t scan_total, pad1, pad2, pad3;
-  uint32_t pref[kMaxSlots + 1];
-  uint32_t pad4[3];
   SlotCtl slot[kMaxSlots];
+  TeamCtl team[kMaxTeams];
 };
 
 // mc_kernel.cu
 uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots);
-cudaError_t launch_mc_counts(int block, const McDev *probs_dev, int nprob,
-                             const uint64_t *prefix_dev, uint64_t total_items, uint32_t nslots,
-                             uint32_t smem_bytes, uint32_t grid, cudaStream_t stream);
+// team sizes with a kernel instantiation for a given block size
+bool mc_config_supported(int block, int team);
+cudaError_t launch_mc_counts(int block, int team, const McDev *probs_dev, int nprob,
+                             const uint64_t *prefix_dev, uint64_t total_items,
+                             uint32_t slots_per_team, uint32_t smem_bytes, uint32_t grid,
+                             cudaStream_t stream);
 cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
                                  cudaStream_t stream);
 cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *comp,
                                     int32_t *csize, cudaStream_t stream);
-cudaError_t launch_debug_sssp(int block, const McDev &P, uint32_t r, const int32_t *sources,
-                              int32_t nsrc, uint32_t nslots, uint32_t smem, uint32_t *dist,
-                              uint64_t *sigma, cudaStream_t stream);
+cudaError_t launch_debug_sssp(int block, int team, const McDev &P, uint32_t r,
+                              const int32_t *sources, int32_t nsrc, uint32_t slots_per_team,
+                              uint32_t smem, uint32_t *dist, uint64_t *sigma,
+                              cudaStream_t stream);
 
 // solve.cu / perturb.cu
 struct ChainDev {

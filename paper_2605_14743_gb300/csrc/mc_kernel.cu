@@ -48,7 +48,7 @@ struct Layout {
     off_comp = o;   o = al(o + 4u * n);
     off_cinfo = o;  o = al(o + 4u * n);
     off_bc = o;     o = al(o + 8u * n);
-    off_src = o;    o = al(o + 2u * n);
+    off_src = o;    o = al(o + 2u * (n > nslots ? n : nslots));
     off_sel = o;    o = al(o + 4u * n);
     off_slots = o;
     slot_bytes = al(4u * n) + al(8u * n) + al(2u * n) + al(4u * kRing * words);
@@ -80,25 +80,55 @@ struct Realized {
   const uint32_t *arc;   // packed: neighbour (low 16 bits) | length << 16
 };
 
-// Exclusive prefix of per-slot counts into ctl->pref[0..S]; executed by warp 0.
-template <typename F>
-__device__ __forceinline__ void slot_prefix(CtaCtl *ctl, uint32_t S, F count) {
-  if (threadIdx.x >= 32) return;
-  const uint32_t lane = threadIdx.x;
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < S; base += 32) {
-    const uint32_t i = base + lane;
-    const uint32_t x = i < S ? count(i) : 0u;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, inc, o);
-      if (lane >= (uint32_t)o) inc += y;
+// A team of TS threads (whole warps) of a BLOCK-thread CTA that advances its own subset of
+// source slots in lockstep.  TS == 32: warp-synchronous; TS == BLOCK: CTA barriers; otherwise
+// named barrier (team + 1) with bar.red for the OR reductions.
+template <int TS, int BLOCK>
+struct Team {
+  uint32_t id, rank;
+  TeamCtl *tc;
+  __device__ __forceinline__ void sync() const {
+    if constexpr (TS == 32) {
+      __syncwarp();
+    } else if constexpr (TS == BLOCK) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "n"(TS) : "memory");
     }
-    if (i < S) ctl->pref[i] = carry + inc - x;
-    carry += __shfl_sync(kFull, inc, 31);
   }
-  if (lane == 0) ctl->pref[S] = carry;
+  __device__ __forceinline__ bool any(bool p) const {
+    if constexpr (TS == 32) {
+      return __any_sync(kFull, p);
+    } else if constexpr (TS == BLOCK) {
+      return __syncthreads_or(p) != 0;
+    } else {
+      uint32_t r;
+      asm volatile(
+          "{ .reg .pred pa, pb;\n"
+          "  setp.ne.u32 pa, %1, 0;\n"
+          "  bar.red.or.pred pb, %2, %3, pa;\n"
+          "  selp.u32 %0, 1, 0, pb; }"
+          : "=r"(r)
+          : "r"((uint32_t)p), "r"(id + 1), "n"(TS)
+          : "memory");
+      return r != 0;
+    }
+  }
+};
+
+// Exclusive prefix of per-slot counts into tc->pref[0..S] (S <= 32); team's first warp only.
+template <typename F>
+__device__ __forceinline__ void slot_prefix(TeamCtl *tc, uint32_t rank, uint32_t S, F count) {
+  if (rank >= 32) return;
+  const uint32_t x = rank < S ? count(rank) : 0u;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, inc, o);
+    if (rank >= (uint32_t)o) inc += y;
+  }
+  if (rank < S) tc->pref[rank] = inc - x;
+  if (rank == 31) tc->pref[S] = inc;
 }
 
 // Largest slot i with pref[i] <= k (pref ascending, pref[S] = total > k).
@@ -112,42 +142,44 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, 
 }
 
 // ---------------------------------------------------------------------------------------
-// A batch of S sources (srcs[0..S)) in lockstep.  Adds delta_s(v) to bc[v] for v != s.
-// With want_delta = false it stops after distances and path counts (parity hook).
-// Every thread of the CTA must call it.  Returns false on a consistency failure.
+// A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) advanced in lockstep by
+// one team.  Adds delta_s(v) to bc[v] for v != s.  With want_delta = false it stops after
+// distances and path counts (parity hook).  Every thread of the team must call it.
 // ---------------------------------------------------------------------------------------
-template <typename DT>
-__device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layout &L, uint32_t S,
-                              const uint16_t *srcs, uint32_t delta, uint32_t ringB, double *bc,
-                              bool want_delta, CtaCtl *ctl) {
+template <int TS, int BLOCK, typename DT>
+__device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, unsigned char *smem,
+                              const Layout &L, uint32_t slot0, uint32_t S, const uint16_t *srcs,
+                              uint32_t delta, uint32_t ringB, double *bc, bool want_delta,
+                              CtaCtl *ctl) {
   const uint32_t n = H.n, W = L.words;
-  const uint32_t T = blockDim.x, tid = threadIdx.x;
+  const uint32_t tid = team.rank;
+  TeamCtl *tc = team.tc;
+  SlotCtl *sl = ctl->slot + slot0;
   uint32_t my_err = 0, my_ovf = 0;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t NW = TS / 32;
 
   // ---- init
-  for (uint32_t t = tid; t < S * n; t += T) {
+  for (uint32_t t = tid; t < S * n; t += TS) {
     const uint32_t i = t / n;
-    slot_arrays(smem, L, n, i).dist[t - i * n] = kInf;
+    slot_arrays(smem, L, n, slot0 + i).dist[t - i * n] = kInf;
   }
-  for (uint32_t t = tid; t < S * kRing * W; t += T) {
+  for (uint32_t t = tid; t < S * kRing * W; t += TS) {
     const uint32_t i = t / (kRing * W);
-    slot_arrays(smem, L, n, i).ring[t - i * kRing * W] = 0u;
+    slot_arrays(smem, L, n, slot0 + i).ring[t - i * kRing * W] = 0u;
   }
-  for (uint32_t i = tid; i < S; i += T) {
-    SlotCtl &sc = ctl->slot[i];
-    sc.s = srcs[i];
+  team.sync();
+  for (uint32_t i = tid; i < S; i += TS) {
+    SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+    const uint32_t s = srcs[i];
+    SlotCtl &sc = sl[i];
+    sc.s = s;
     sc.nm = 0; sc.mstart = 0; sc.hi = 0; sc.lo = 0;
-    for (int k = 0; k < kRing; ++k) sc.ring_cnt[k] = 0;
-  }
-  __syncthreads();
-  for (uint32_t i = tid; i < S; i += T) {
-    SlotArrays a = slot_arrays(smem, L, n, i);
-    const uint32_t s = ctl->slot[i].s;
+    sc.ring_mask = 1u;            // ring_mask: bucket 0 holds the source
     a.dist[s] = 0;
     a.ring[s >> 5] = 1u << (s & 31u);
-    ctl->slot[i].ring_cnt[0] = 1;
   }
-  __syncthreads();
+  team.sync();
 
   // ---- forward: buckets in increasing order
   bool ok = true;
@@ -156,50 +188,79 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
     if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
     if (tid < 32) {
       // first ring offset k (bucket b + k) holding discovered vertices in any slot
-      bool here = false;
-      if (tid < ringB) {
-        const uint32_t rs = (b + tid) % ringB;
-        for (uint32_t i = 0; i < S && !here; ++i) here = ctl->slot[i].ring_cnt[rs] != 0;
-      }
-      const uint32_t ball = __ballot_sync(kFull, here);
-      if (tid == 0) ctl->bucket = ball ? b + (uint32_t)(__ffs(ball) - 1) : 0xFFFFFFFFu;
+      uint32_t m = tid < S ? sl[tid].ring_mask : 0u;
+      m = __reduce_or_sync(kFull, m);
+      uint32_t rot = 0;   // bit k <-> ring slot (b + k) % ringB
+      for (uint32_t k = 0; k < ringB; ++k) rot |= ((m >> ((b + k) % ringB)) & 1u) << k;
+      if (tid == 0) tc->bucket = rot ? b + (uint32_t)(__ffs(rot) - 1) : 0xFFFFFFFFu;
     }
-    __syncthreads();
-    if (ctl->bucket == 0xFFFFFFFFu) break;
-    b = ctl->bucket;
+    team.sync();
+    if (tc->bucket == 0xFFFFFFFFu) break;
+    b = tc->bucket;
     const uint32_t rs = b % ringB;
     const uint32_t dend = (b + 1u) * delta;
-    // extraction of bucket b into the member lists
-    for (uint32_t t = tid; t < S * W; t += T) {
-      const uint32_t i = t / W, w = t - i * W;
-      SlotArrays a = slot_arrays(smem, L, n, i);
-      uint32_t word = a.ring[rs * W + w];
-      if (!word) continue;
-      a.ring[rs * W + w] = 0u;
-      while (word) {
-        const uint32_t j = __ffs(word) - 1;
-        word &= word - 1u;
-        const uint32_t v = w * 32u + j;
-        const uint32_t d = a.dist[v];
-        if ((d & kFlag) || d >= dend) continue;   // settled (stale bit)
-        const uint32_t pos = atomicAdd(&ctl->slot[i].nm, 1u);
-        if (pos < n) { a.ord[pos] = (uint16_t)v; a.sig[v] = kNoRelax; }
-        else my_err |= kErrCapacity;
+    // extraction of bucket b into the member lists, appends aggregated per warp and slot
+    for (uint32_t base = warp * 32u; base < S * W; base += TS) {
+      const uint32_t item = base + lane;
+      uint32_t i = 0xFFFFu, live = 0;
+      uint16_t vb = 0;
+      if (item < S * W) {
+        i = item / W;
+        const uint32_t w = item - i * W;
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        uint32_t word = a.ring[rs * W + w];
+        if (word) {
+          a.ring[rs * W + w] = 0u;
+          while (word) {
+            const uint32_t j = __ffs(word) - 1;
+            word &= word - 1u;
+            const uint32_t d = a.dist[w * 32u + j];
+            if (!(d & kFlag) && d < dend) live |= 1u << j;   // else settled (stale bit)
+          }
+        }
+        vb = (uint16_t)(w * 32u);
+      }
+      const uint32_t cnt = __popc(live);
+      uint32_t inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
+      }
+      const uint32_t peers = __match_any_sync(kFull, i);
+      const uint32_t leader = __ffs(peers) - 1, last = 31 - __clz(peers);
+      const uint32_t before = __shfl_sync(kFull, inc, leader == 0 ? 0 : leader - 1);
+      const uint32_t gbase = leader == 0 ? 0u : before;
+      const uint32_t gtotal = __shfl_sync(kFull, inc, last) - gbase;
+      uint32_t pos0 = 0;
+      if (lane == leader && i != 0xFFFFu && gtotal) pos0 = atomicAdd(&sl[i].nm, gtotal);
+      pos0 = __shfl_sync(kFull, pos0, leader);
+      if (live) {
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        uint32_t pos = pos0 + inc - cnt - gbase;
+        while (live) {
+          const uint32_t j = __ffs(live) - 1;
+          live &= live - 1u;
+          const uint32_t v = (uint32_t)vb + j;
+          if (pos < n) { a.ord[pos] = (uint16_t)v; a.sig[v] = kNoRelax; }
+          else my_err |= kErrCapacity;
+          ++pos;
+        }
       }
     }
-    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].ring_cnt[rs] = 0;
-    __syncthreads();
+    for (uint32_t i = tid; i < S; i += TS) sl[i].ring_mask &= ~(1u << rs);
+    team.sync();
     // relaxation passes until no member of the bucket improves
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-      slot_prefix(ctl, S, [&](uint32_t i) { return min(ctl->slot[i].nm, n) - ctl->slot[i].mstart; });
-      __syncthreads();
-      const uint32_t total = ctl->pref[S];
+      slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
+      team.sync();
+      const uint32_t total = tc->pref[S];
       bool improved = false;
-      for (uint32_t k = tid; k < total; k += T) {
-        const uint32_t i = find_slot(ctl->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, i);
-        const uint32_t v = a.ord[ctl->slot[i].mstart + k - ctl->pref[i]];
+      for (uint32_t k = tid; k < total; k += TS) {
+        const uint32_t i = find_slot(tc->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
         const uint32_t d = a.dist[v];
         if ((uint64_t)d == a.sig[v]) continue;
         a.sig[v] = d;
@@ -215,7 +276,7 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
           if (nd < dend) {
             improved = true;
             if (old >= dend) {
-              const uint32_t pos = atomicAdd(&ctl->slot[i].nm, 1u);
+              const uint32_t pos = warp_append(&sl[i].nm);
               if (pos < n) { a.ord[pos] = (uint16_t)u; a.sig[u] = kNoRelax; }
               else my_err |= kErrCapacity;
             }
@@ -223,35 +284,35 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
             const uint32_t r2 = (nd / delta) % ringB;
             const uint32_t bit = 1u << (u & 31u);
             const uint32_t prev = atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
-            if (!(prev & bit)) atomicAdd(&ctl->slot[i].ring_cnt[r2], 1u);
+            if (!(prev & bit) && !(sl[i].ring_mask & (1u << r2))) atomicOr(&sl[i].ring_mask, 1u << r2);
           }
         }
       }
-      if (!__syncthreads_or(improved)) break;
+      if (!team.any(improved)) break;
     }
     if (!ok) break;
     // path counts of the bucket: a member is final once its same-bucket predecessors are
-    slot_prefix(ctl, S, [&](uint32_t i) { return min(ctl->slot[i].nm, n) - ctl->slot[i].mstart; });
-    __syncthreads();
-    const uint32_t total = ctl->pref[S];
-    for (uint32_t k = tid; k < total; k += T) {
-      const uint32_t i = find_slot(ctl->pref, S, k);
-      SlotArrays a = slot_arrays(smem, L, n, i);
-      const uint32_t v = a.ord[ctl->slot[i].mstart + k - ctl->pref[i]];
-      a.sig[v] = (v == ctl->slot[i].s) ? 1ull : 0ull;
+    slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
+    team.sync();
+    const uint32_t total = tc->pref[S];
+    for (uint32_t k = tid; k < total; k += TS) {
+      const uint32_t i = find_slot(tc->pref, S, k);
+      SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+      const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
+      a.sig[v] = (v == sl[i].s) ? 1ull : 0ull;
     }
-    __syncthreads();
+    team.sync();
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
       bool open = false;
-      for (uint32_t k = tid; k < total; k += T) {
-        const uint32_t i = find_slot(ctl->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, i);
-        const uint32_t idx = ctl->slot[i].mstart + k - ctl->pref[i];
+      for (uint32_t k = tid; k < total; k += TS) {
+        const uint32_t i = find_slot(tc->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        const uint32_t idx = sl[i].mstart + k - tc->pref[i];
         const uint32_t v = a.ord[idx];
         const uint32_t dv = a.dist[v];
         if (dv & kFlag) continue;
-        const uint32_t s = ctl->slot[i].s;
+        const uint32_t s = sl[i].s;
         uint64_t acc = (v == s) ? 1ull : 0ull;
         bool all_final = true;
         if (v != s) {
@@ -271,58 +332,56 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
         if (all_final) a.ord[idx] = (uint16_t)(v | kMark);
         else open = true;
       }
-      __syncthreads();
-      for (uint32_t k = tid; k < total; k += T) {
-        const uint32_t i = find_slot(ctl->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, i);
-        const uint32_t idx = ctl->slot[i].mstart + k - ctl->pref[i];
+      team.sync();
+      for (uint32_t k = tid; k < total; k += TS) {
+        const uint32_t i = find_slot(tc->pref, S, k);
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        const uint32_t idx = sl[i].mstart + k - tc->pref[i];
         const uint32_t e = a.ord[idx];
         if (e & kMark) {
           a.ord[idx] = (uint16_t)(e & ~kMark);
           a.dist[e & ~kMark] |= kFlag;
         }
       }
-      if (!__syncthreads_or(open)) break;
+      if (!team.any(open)) break;
     }
     if (!ok) break;
-    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].mstart = min(ctl->slot[i].nm, n);
-    __syncthreads();
+    for (uint32_t i = tid; i < S; i += TS) sl[i].mstart = min(sl[i].nm, n);
+    team.sync();
     b += 1;
   }
   if (!ok) {
     if (my_err) atomicOr(&ctl->err, my_err);
-    __syncthreads();
+    team.sync();
     return false;
   }
 
   // ---- backward: dependencies, buckets in decreasing order; kFlag = "delta pending"
   if (want_delta) {
-    for (uint32_t i = tid; i < S; i += T) ctl->slot[i].hi = ctl->slot[i].mstart;
-    __syncthreads();
-    const uint32_t warp = tid >> 5, lane = tid & 31u, nw = T >> 5;
+    for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].mstart;
+    team.sync();
     for (uint32_t guard = 0;; ++guard) {
       if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
       if (tid < 32) {
         uint32_t best = 0;  // 1 + bucket id of the last unprocessed member, 0 if none
-        for (uint32_t i = lane; i < S; i += 32) {
-          const uint32_t hi = ctl->slot[i].hi;
+        if (lane < S) {
+          const uint32_t hi = sl[lane].hi;
           if (hi > 0) {
-            SlotArrays a = slot_arrays(smem, L, n, i);
-            const uint32_t bb = (a.dist[a.ord[hi - 1]] & kMask) / delta + 1u;
-            best = max(best, bb);
+            SlotArrays a = slot_arrays(smem, L, n, slot0 + lane);
+            best = (a.dist[a.ord[hi - 1]] & kMask) / delta + 1u;
           }
         }
         best = __reduce_max_sync(kFull, best);
-        if (lane == 0) ctl->bucket = best;
+        if (lane == 0) tc->bucket = best;
       }
-      __syncthreads();
-      const uint32_t bb = ctl->bucket;
+      team.sync();
+      const uint32_t bb = tc->bucket;
       if (bb == 0) break;
       const uint32_t bcur = bb - 1u;
       // per slot: start of the run of bucket bcur at the end of its settled list
-      for (uint32_t i = warp; i < S; i += nw) {
-        SlotArrays a = slot_arrays(smem, L, n, i);
-        const uint32_t hi = ctl->slot[i].hi;
+      for (uint32_t i = warp; i < S; i += NW) {
+        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+        const uint32_t hi = sl[i].hi;
         uint32_t lo = hi;
         if (hi > 0 && (a.dist[a.ord[hi - 1]] & kMask) / delta == bcur) {
           lo = 0;
@@ -336,19 +395,19 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
             top = base;
           }
         }
-        if (lane == 0) ctl->slot[i].lo = lo;
+        if (lane == 0) sl[i].lo = lo;
       }
-      __syncthreads();
-      slot_prefix(ctl, S, [&](uint32_t i) { return ctl->slot[i].hi - ctl->slot[i].lo; });
-      __syncthreads();
-      const uint32_t total = ctl->pref[S];
+      team.sync();
+      slot_prefix(tc, tid, S, [&](uint32_t i) { return sl[i].hi - sl[i].lo; });
+      team.sync();
+      const uint32_t total = tc->pref[S];
       for (uint32_t pass = 0;; ++pass) {
         if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
         bool open = false;
-        for (uint32_t k = tid; k < total; k += T) {
-          const uint32_t i = find_slot(ctl->pref, S, k);
-          SlotArrays a = slot_arrays(smem, L, n, i);
-          const uint32_t idx = ctl->slot[i].lo + k - ctl->pref[i];
+        for (uint32_t k = tid; k < total; k += TS) {
+          const uint32_t i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+          const uint32_t idx = sl[i].lo + k - tc->pref[i];
           const uint32_t v = a.ord[idx];
           const uint32_t dv = a.dist[v];
           if (!(dv & kFlag)) continue;
@@ -376,33 +435,33 @@ __device__ bool brandes_batch(const Realized &H, unsigned char *smem, const Layo
               rho = ((DT)1 + dep) / sv;
             }
             *reinterpret_cast<DT *>(&a.sig[v]) = rho;
-            if (v != ctl->slot[i].s) atomicAdd(&bc[v], (double)dep);
+            if (v != sl[i].s) atomicAdd(&bc[v], (double)dep);
             a.ord[idx] = (uint16_t)(v | kMark);
           } else {
             open = true;
           }
         }
-        __syncthreads();
-        for (uint32_t k = tid; k < total; k += T) {
-          const uint32_t i = find_slot(ctl->pref, S, k);
-          SlotArrays a = slot_arrays(smem, L, n, i);
-          const uint32_t idx = ctl->slot[i].lo + k - ctl->pref[i];
+        team.sync();
+        for (uint32_t k = tid; k < total; k += TS) {
+          const uint32_t i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
+          const uint32_t idx = sl[i].lo + k - tc->pref[i];
           const uint32_t e = a.ord[idx];
           if (e & kMark) {
             a.ord[idx] = (uint16_t)(e & ~kMark);
             a.dist[e & ~kMark] &= kMask;
           }
         }
-        if (!__syncthreads_or(open)) break;
+        if (!team.any(open)) break;
       }
       if (!ok) break;
-      for (uint32_t i = tid; i < S; i += T) ctl->slot[i].hi = ctl->slot[i].lo;
-      __syncthreads();
+      for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].lo;
+      team.sync();
     }
   }
   if (my_err) atomicOr(&ctl->err, my_err);
   if (my_ovf) atomicOr(&ctl->ovf, 1u);
-  __syncthreads();
+  team.sync();
   return ok;
 }
 
@@ -632,14 +691,21 @@ __device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_
 
 // ---------------------------------------------------------------------------------------
 // The persistent kernel.  Work item w enumerates (problem, realization) pairs of all
-// problems; items are visited in strided order by the CTAs.
+// problems; items are visited in strided order by the CTAs.  Inside a realization the CTA's
+// teams claim batches of sources dynamically.
 // ---------------------------------------------------------------------------------------
-template <int BLOCK>
+template <int BLOCK, int TS>
 __global__ void __launch_bounds__(BLOCK, 1)
 mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *item_prefix,
-                 uint64_t total_items, uint32_t nslots) {
+                 uint64_t total_items, uint32_t spt) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr uint32_t NT = BLOCK / TS;
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
+  Team<TS, BLOCK> team;
+  team.id = threadIdx.x / TS;
+  team.rank = threadIdx.x % TS;
+  team.tc = &ctl->team[team.id];
+  const uint32_t nslots = NT * spt;
   for (uint64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     int g = 0;
     while (g + 1 < nprob && item_prefix[g + 1] <= item) ++g;
@@ -657,7 +723,8 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     uint16_t *src = reinterpret_cast<uint16_t *>(smem + L.off_src);
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + L.off_sel);
     if (threadIdx.x == 0) {
-      ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->edges = 0; ctl->verts = 0; ctl->wmax = 1;
+      ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->cursor = 0;
+      ctl->edges = 0; ctl->verts = 0; ctl->wmax = 1;
     }
     __syncthreads();
 
@@ -679,7 +746,6 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
       if (up) atomicAdd(&cedges[root], up);
     }
     {
-      // ordered compaction of the sources (keeps the batches deterministic)
       const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
       const uint32_t v0 = min(n, threadIdx.x * per), v1 = min(n, v0 + per);
       uint32_t cnt = 0;
@@ -709,15 +775,24 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
       const bool use32 = fp32 && attempt == 0;
       if (attempt == 1) {
         for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] = 0.0;
+        if (threadIdx.x == 0) ctl->cursor = 0;
         __syncthreads();
       }
-      for (uint32_t k0 = 0; k0 < nsrc; k0 += nslots) {
-        const uint32_t S = min(nslots, nsrc - k0);
+      for (;;) {
+        if (team.rank == 0) team.tc->claim = atomicAdd(&ctl->cursor, spt);
+        team.sync();
+        const uint32_t k0 = team.tc->claim;
+        team.sync();
+        if (k0 >= nsrc) break;
+        const uint32_t S = min(spt, nsrc - k0);
         if (use32)
-          brandes_batch<float>(H, smem, L, S, src + k0, delta, ringB, bc, true, ctl);
+          brandes_batch<TS, BLOCK, float>(team, H, smem, L, team.id * spt, S, src + k0, delta,
+                                          ringB, bc, true, ctl);
         else
-          brandes_batch<double>(H, smem, L, S, src + k0, delta, ringB, bc, true, ctl);
+          brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, src + k0, delta,
+                                           ringB, bc, true, ctl);
       }
+      __syncthreads();
       const bool recheck = select_and_count(P, r_local, comp, cinfo, bc,
                                             slot_arrays(smem, L, n, 0), sel, use32, ctl);
       __syncthreads();
@@ -772,17 +847,18 @@ __global__ void debug_components_kernel(McDev P, int32_t *comp_out, int32_t *csi
   }
 }
 
-// Distances and path counts of given sources from the production batch routine: CTA b
-// handles sources [b*S, (b+1)*S) of the list on realization r.
-template <int BLOCK>
+// Distances and path counts of given sources from the production batch routine: team t of
+// CTA b handles the sources [(b * NT + t) * spt, ... + spt) of the list on realization r.
+template <int BLOCK, int TS>
 __global__ void __launch_bounds__(BLOCK, 1)
-debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t nslots,
+debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t spt,
                   uint32_t *dist_out, uint64_t *sigma_out) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr uint32_t NT = BLOCK / TS;
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
   const uint32_t n = P.n;
   Layout L;
-  L.make(n, (uint32_t)(2 * P.m), nslots);
+  L.make(n, (uint32_t)(2 * P.m), NT * spt);
   uint32_t *rp = reinterpret_cast<uint32_t *>(smem + L.off_rp);
   uint32_t *arc = reinterpret_cast<uint32_t *>(smem + L.off_arc);
   double *bc = reinterpret_cast<double *>(smem + L.off_bc);
@@ -792,18 +868,24 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
   realize_csr(P, r, rp, arc, ctl);
   Realized H{n, rp, arc};
   bucket_setup(ctl, P.delta);
-  const uint32_t k0 = blockIdx.x * nslots;
+  Team<TS, BLOCK> team;
+  team.id = threadIdx.x / TS;
+  team.rank = threadIdx.x % TS;
+  team.tc = &ctl->team[team.id];
+  const uint32_t k0 = (blockIdx.x * NT + team.id) * spt;
+  uint16_t *tsrc = src + team.id * spt;
   if (k0 < (uint32_t)nsrc) {
-    const uint32_t S = min(nslots, (uint32_t)nsrc - k0);
-    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+    const uint32_t S = min(spt, (uint32_t)nsrc - k0);
+    for (uint32_t i = team.rank; i < S; i += TS) {
       const int32_t s = sources[k0 + i];
-      src[i] = (uint16_t)((s >= 0 && (uint32_t)s < n) ? s : 0);
+      tsrc[i] = (uint16_t)((s >= 0 && (uint32_t)s < n) ? s : 0);
     }
-    __syncthreads();
-    brandes_batch<double>(H, smem, L, S, src, ctl->delta, ctl->ring_b, bc, false, ctl);
-    for (uint32_t t = threadIdx.x; t < S * n; t += blockDim.x) {
+    team.sync();
+    brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, tsrc, ctl->delta,
+                                     ctl->ring_b, bc, false, ctl);
+    for (uint32_t t = team.rank; t < S * n; t += TS) {
       const uint32_t i = t / n, v = t - i * n;
-      SlotArrays a = slot_arrays(smem, L, n, i);
+      SlotArrays a = slot_arrays(smem, L, n, team.id * spt + i);
       const uint32_t d = a.dist[v] & kMask;
       const bool reached = d < kInf;
       dist_out[(size_t)(k0 + i) * n + v] = reached ? d : 0xFFFFFFFFu;
@@ -826,25 +908,41 @@ uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots) {
   return L.total;
 }
 
-template <int BLOCK>
+// (block, team) pairs with an instantiation; named-barrier teams need ids <= 15.
+#define AFC_MC_CONFIGS(X) \
+  X(256, 32) X(256, 64) X(256, 128) X(256, 256) \
+  X(512, 32) X(512, 64) X(512, 128) X(512, 256) X(512, 512) \
+  X(1024, 32) X(1024, 128) X(1024, 256) X(1024, 1024)
+
+bool mc_config_supported(int block, int team) {
+#define AFC_X(B, T) if (block == B && team == T) return true;
+  AFC_MC_CONFIGS(AFC_X)
+#undef AFC_X
+  return false;
+}
+
+template <int BLOCK, int TS>
 static cudaError_t launch_counts_t(const McDev *probs_dev, int nprob, const uint64_t *prefix_dev,
-                                   uint64_t total_items, uint32_t nslots, uint32_t smem,
+                                   uint64_t total_items, uint32_t spt, uint32_t smem,
                                    uint32_t grid, cudaStream_t stream) {
-  cudaFuncSetAttribute(mc_counts_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  mc_counts_kernel<BLOCK><<<grid, BLOCK, smem, stream>>>(probs_dev, nprob, prefix_dev,
-                                                         total_items, nslots);
+  cudaFuncSetAttribute(mc_counts_kernel<BLOCK, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem);
+  mc_counts_kernel<BLOCK, TS><<<grid, BLOCK, smem, stream>>>(probs_dev, nprob, prefix_dev,
+                                                             total_items, spt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mc_counts(int block, const McDev *probs_dev, int nprob,
-                             const uint64_t *prefix_dev, uint64_t total_items, uint32_t nslots,
-                             uint32_t smem_bytes, uint32_t grid, cudaStream_t stream) {
-  switch (block) {
-    case 256: return launch_counts_t<256>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
-    case 512: return launch_counts_t<512>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
-    case 1024: return launch_counts_t<1024>(probs_dev, nprob, prefix_dev, total_items, nslots, smem_bytes, grid, stream);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_mc_counts(int block, int team, const McDev *probs_dev, int nprob,
+                             const uint64_t *prefix_dev, uint64_t total_items,
+                             uint32_t slots_per_team, uint32_t smem_bytes, uint32_t grid,
+                             cudaStream_t stream) {
+#define AFC_X(B, T)                                                                        \
+  if (block == B && team == T)                                                             \
+    return launch_counts_t<B, T>(probs_dev, nprob, prefix_dev, total_items, slots_per_team, \
+                                 smem_bytes, grid, stream);
+  AFC_MC_CONFIGS(AFC_X)
+#undef AFC_X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
@@ -865,25 +963,30 @@ cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *c
   return cudaGetLastError();
 }
 
-template <int BLOCK>
+template <int BLOCK, int TS>
 static cudaError_t launch_sssp_t(const McDev &P, uint32_t r, const int32_t *sources, int32_t nsrc,
-                                 uint32_t nslots, uint32_t smem, uint32_t *dist, uint64_t *sigma,
+                                 uint32_t spt, uint32_t smem, uint32_t *dist, uint64_t *sigma,
                                  cudaStream_t stream) {
-  const uint32_t grid = (uint32_t)((nsrc + (int32_t)nslots - 1) / (int32_t)nslots);
-  cudaFuncSetAttribute(debug_sssp_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  debug_sssp_kernel<BLOCK><<<grid, BLOCK, smem, stream>>>(P, r, sources, nsrc, nslots, dist, sigma);
+  const uint32_t per_cta = (BLOCK / TS) * spt;
+  const uint32_t grid = (uint32_t)((nsrc + (int32_t)per_cta - 1) / (int32_t)per_cta);
+  cudaFuncSetAttribute(debug_sssp_kernel<BLOCK, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       smem);
+  debug_sssp_kernel<BLOCK, TS><<<grid, BLOCK, smem, stream>>>(P, r, sources, nsrc, spt, dist,
+                                                              sigma);
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_sssp(int block, const McDev &P, uint32_t r, const int32_t *sources,
-                              int32_t nsrc, uint32_t nslots, uint32_t smem, uint32_t *dist,
-                              uint64_t *sigma, cudaStream_t stream) {
-  switch (block) {
-    case 256: return launch_sssp_t<256>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
-    case 512: return launch_sssp_t<512>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
-    case 1024: return launch_sssp_t<1024>(P, r, sources, nsrc, nslots, smem, dist, sigma, stream);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_debug_sssp(int block, int team, const McDev &P, uint32_t r,
+                              const int32_t *sources, int32_t nsrc, uint32_t slots_per_team,
+                              uint32_t smem, uint32_t *dist, uint64_t *sigma,
+                              cudaStream_t stream) {
+#define AFC_X(B, T)                                                                    \
+  if (block == B && team == T)                                                         \
+    return launch_sssp_t<B, T>(P, r, sources, nsrc, slots_per_team, smem, dist, sigma, \
+                               stream);
+  AFC_MC_CONFIGS(AFC_X)
+#undef AFC_X
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace afc

@@ -60,7 +60,8 @@ def _precision(p):
 
 
 def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=None,
-                 bucket_width: int = 0, block_threads: int = 0) -> McProblem:
+                 bucket_width: int = 0, block_threads: int = 0, team_threads: int = 0,
+                 slots_per_team: int = 0) -> McProblem:
     """McProblem for a workload on device tensors (per-edge arrays optional)."""
     p = McProblem()
     p.n, p.m = dg.n, dg.m
@@ -86,6 +87,8 @@ def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=No
     p.recheck_margin = float(wl.recheck_margin)
     p.bucket_width = int(bucket_width)
     p.block_threads = int(block_threads)
+    p.team_threads = int(team_threads)
+    p.slots_per_team = int(slots_per_team)
     return p
 
 
@@ -105,7 +108,8 @@ class QueryResult:
 class Query:
     """All device state of one stochastic-centrality query.  Build once, run many times."""
 
-    def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, stream=None):
+    def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
+                 slots_per_team=0, stream=None):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -131,7 +135,7 @@ class Query:
         self.s = None if wl.s_init is None else torch.from_numpy(np.asarray(wl.s_init, np.float64)).to(device)
         self.f = None if wl.reward is None else torch.from_numpy(np.asarray(wl.reward, np.float64)).to(device)
         self.prob = make_problem(self.graph, wl, self.thresh, self.w_lo, self.w_hi, self.in_w,
-                                 bucket_width, block_threads)
+                                 bucket_width, block_threads, team_threads, slots_per_team)
         self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
         self.stats = torch.zeros(7, dtype=torch.int64, device=device)
         wsb = afc_transition_counts_workspace(self.prob)

@@ -131,6 +131,21 @@ def test_sssp_sigma_ws1000_sampled(B, delta):
     _sssp_check(wl, 1, sources, block_threads=B, bucket_width=delta)
 
 
+@pytest.mark.parametrize("B,T", [(1024, 1024), (1024, 256), (1024, 32), (512, 64), (512, 128),
+                                 (256, 32), (256, 256)])
+def test_sssp_team_configurations(B, T):
+    """Every (block, team) shape of the counting kernel runs the same batch routine."""
+    wl = _ws1000()
+    rng = np.random.default_rng(B * 7 + T)
+    sources = sorted(rng.choice(wl.n, 40, replace=False).tolist())
+    _sssp_check(wl, 3, sources, block_threads=B, team_threads=T, bucket_width=24)
+
+
+@pytest.mark.parametrize("B,T,spt", [(1024, 256, 2), (512, 64, 1), (1024, 32, 0)])
+def test_counts_team_configurations(B, T, spt):
+    _mc_check(_small_er(), 0, 40, block_threads=B, team_threads=T, slots_per_team=spt)
+
+
 def test_sssp_unweighted_grid_large_sigma():
     eu, ev = grid_edges(30, 30)
     wl = Workload("grid", 900, eu, ev, 1.0, 1, 1, 1, seed=1)
