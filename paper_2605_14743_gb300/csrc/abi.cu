@@ -149,7 +149,8 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
     if (t > pl.block || !mc_config_supported(pl.block, t)) continue;
     const uint32_t nt = (uint32_t)(pl.block / t);
     if (fit < nt) continue;
-    uint32_t spt = std::min<uint32_t>(fit / nt, (uint32_t)kMaxSlotsPerTeam);
+    if (nt * 1u > (uint32_t)kMaxTeams) continue;
+    uint32_t spt = std::min<uint32_t>({fit / nt, (uint32_t)kMaxSlotsPerTeam, (uint32_t)kMaxSlots / nt});
     spt = std::min<uint32_t>(spt, std::max<uint32_t>(1u, (nmax + nt - 1) / nt));
     if (req_spt) spt = std::min<uint32_t>(spt, (uint32_t)req_spt);
     pl.team = t;

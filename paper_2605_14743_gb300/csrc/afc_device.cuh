@@ -44,44 +44,15 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t *counter) {
   return base + (uint32_t)__popc(mask & lanemask_lt());
 }
 
-// A group of G threads (G = 32, 64 or 128: whole warps) working on one problem instance.
-// For G > 32 the group synchronises on named barrier (index + 1) and reduces through a
-// three-slot rotating scratch in shared memory, so that each reduction needs one barrier.
-template <int G>
-struct Group {
-  uint32_t idx;   // group index inside the CTA
-  uint32_t rank;  // thread rank inside the group
-  uint32_t *red;  // 3 words of shared scratch (G > 32 only)
-  uint32_t turn;  // rotating slot
-
-  __device__ __forceinline__ void sync() const {
-    if constexpr (G == 32) {
-      __syncwarp();
-    } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(idx + 1), "r"(G) : "memory");
-    }
-  }
-
-  __device__ __forceinline__ uint32_t reduce_min(uint32_t x) {
-    if constexpr (G == 32) {
-      return __reduce_min_sync(kFull, x);
-    } else {
-      const uint32_t w = __reduce_min_sync(kFull, x);
-      const uint32_t slot = turn;
-      turn = (turn == 2) ? 0 : turn + 1;
-      if (rank == 0) red[turn] = 0xFFFFFFFFu;  // prepare the next slot (read two calls ago)
-      if (lane_id() == 0) atomicMin(&red[slot], w);
-      sync();
-      return red[slot];
-    }
-  }
-
-  __device__ __forceinline__ uint32_t reduce_max(uint32_t x) {
-    // max via min of the complement (slots are initialised for min)
-    return ~reduce_min(~x);
-  }
-
-  __device__ __forceinline__ bool any(bool p) { return reduce_min(p ? 0u : 1u) == 0u; }
-};
+// Warp-aggregated append keyed by `key`: lanes with equal keys share one atomicAdd on the
+// counter they all pass (lanes with different keys must pass different counters).
+__device__ __forceinline__ uint32_t warp_append_keyed(uint32_t *counter, uint32_t key) {
+  const uint32_t peers = __match_any_sync(__activemask(), key);
+  const uint32_t leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane_id() == leader) base = atomicAdd(counter, (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + (uint32_t)__popc(peers & lanemask_lt());
+}
 
 }  // namespace afc

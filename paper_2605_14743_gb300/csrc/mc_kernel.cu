@@ -261,6 +261,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
         const uint32_t i = find_slot(tc->pref, S, k);
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
         const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
+        if (v >= n) { my_err |= kErrCapacity; continue; }
         const uint32_t d = a.dist[v];
         if ((uint64_t)d == a.sig[v]) continue;
         a.sig[v] = d;
@@ -276,7 +277,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           if (nd < dend) {
             improved = true;
             if (old >= dend) {
-              const uint32_t pos = warp_append(&sl[i].nm);
+              const uint32_t pos = warp_append_keyed(&sl[i].nm, i);
               if (pos < n) { a.ord[pos] = (uint16_t)u; a.sig[u] = kNoRelax; }
               else my_err |= kErrCapacity;
             }
@@ -299,7 +300,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
       const uint32_t i = find_slot(tc->pref, S, k);
       SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
       const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-      a.sig[v] = (v == sl[i].s) ? 1ull : 0ull;
+      if (v < n) a.sig[v] = (v == sl[i].s) ? 1ull : 0ull;
     }
     team.sync();
     for (uint32_t pass = 0;; ++pass) {
@@ -310,6 +311,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
         const uint32_t idx = sl[i].mstart + k - tc->pref[i];
         const uint32_t v = a.ord[idx];
+        if (v >= n) { my_err |= kErrCapacity; continue; }
         const uint32_t dv = a.dist[v];
         if (dv & kFlag) continue;
         const uint32_t s = sl[i].s;
@@ -338,7 +340,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
         const uint32_t idx = sl[i].mstart + k - tc->pref[i];
         const uint32_t e = a.ord[idx];
-        if (e & kMark) {
+        if ((e & kMark) && (e & ~kMark) < n) {
           a.ord[idx] = (uint16_t)(e & ~kMark);
           a.dist[e & ~kMark] |= kFlag;
         }
@@ -368,7 +370,8 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           const uint32_t hi = sl[lane].hi;
           if (hi > 0) {
             SlotArrays a = slot_arrays(smem, L, n, slot0 + lane);
-            best = (a.dist[a.ord[hi - 1]] & kMask) / delta + 1u;
+            const uint32_t v = a.ord[hi - 1];
+            best = v < n ? (a.dist[v] & kMask) / delta + 1u : 1u;
           }
         }
         best = __reduce_max_sync(kFull, best);
@@ -383,13 +386,17 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
         const uint32_t hi = sl[i].hi;
         uint32_t lo = hi;
-        if (hi > 0 && (a.dist[a.ord[hi - 1]] & kMask) / delta == bcur) {
+        const uint32_t vh = hi > 0 ? a.ord[hi - 1] : 0u;
+        if (hi > 0 && vh < n && (a.dist[vh] & kMask) / delta == bcur) {
           lo = 0;
           for (uint32_t top = hi; top > 0;) {
             const uint32_t base = top > 32u ? top - 32u : 0u;
             const uint32_t p = base + lane;
             uint32_t cand = 0;
-            if (p < top && (a.dist[a.ord[p]] & kMask) / delta != bcur) cand = p + 1u;
+            if (p < top) {
+              const uint32_t vp = a.ord[p];
+              if (vp >= n || (a.dist[vp] & kMask) / delta != bcur) cand = p + 1u;
+            }
             const uint32_t found = __reduce_max_sync(kFull, cand);
             if (found > 0) { lo = found; break; }
             top = base;
@@ -409,6 +416,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
           const uint32_t idx = sl[i].lo + k - tc->pref[i];
           const uint32_t v = a.ord[idx];
+          if (v >= n) { my_err |= kErrCapacity; continue; }
           const uint32_t dv = a.dist[v];
           if (!(dv & kFlag)) continue;
           const uint32_t dvm = dv & kMask;
@@ -447,7 +455,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
           const uint32_t idx = sl[i].lo + k - tc->pref[i];
           const uint32_t e = a.ord[idx];
-          if (e & kMark) {
+          if ((e & kMark) && (e & ~kMark) < n) {
             a.ord[idx] = (uint16_t)(e & ~kMark);
             a.dist[e & ~kMark] &= kMask;
           }
