@@ -187,13 +187,12 @@ def run_ours(args):
         q.stats.zero_()
         if timers is not None:
             timers[0].record(stream)
-        afc.afc_transition_counts(q.prob, rank * R, R, q.counts, q.stats, None, None,
+        r0, rc = afc.engine.shard_range(R, rank, world)
+        afc.afc_transition_counts(q.prob, r0, rc, q.counts, q.stats, None, None,
                                   q.ws_counts, q.ws_counts.numel(), stream.cuda_stream)
         if timers is not None:
             timers[1].record(stream)
-        if dist:
-            import torch.distributed as tdist
-            tdist.all_reduce(q.counts)          # exact integer merge of the shards
+        afc.engine.merge_counts(q.counts)       # exact integer merge of the shards (N > 1)
         q.wl.realizations = R * world
         q.run_solve()
         q.run_perturb()
@@ -285,6 +284,22 @@ def run_ours(args):
     return 0
 
 
+def run_counts_only(args):
+    """One counting-kernel launch over realizations [0, R) of the workload (profiling aid)."""
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+    torch.cuda.set_device(0)
+    q = afc.Query(workload("ws1000"))
+    q.run_counts(0, args.counts_only)
+    torch.cuda.synchronize()
+    st = q.stats.cpu().numpy()
+    print(json.dumps({"counts_only": args.counts_only, "realizations": int(st[0]),
+                      "sources": int(st[1]), "edge_visits": int(st[2]),
+                      "device_error": int(st[5])}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,7 +307,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--counts-only", type=int, default=0,
+                    help="run one counting launch of this many realizations and exit")
     args = ap.parse_args()
+    if args.counts_only:
+        return run_counts_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

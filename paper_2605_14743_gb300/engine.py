@@ -306,3 +306,23 @@ def run_query_host(bufs: HostBuffers, stream=None) -> HostResult:
     s = stream if stream is not None else torch.cuda.current_stream()
     afc_run_host(bufs.query, bufs.result, s.cuda_stream)
     return bufs.result
+
+
+# ---- realization sharding across ranks -------------------------------------------------------
+
+def shard_range(realizations: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous realization range [begin, begin + count) of `rank` out of `world` when each
+    rank processes an equal share (weak scaling: every rank gets `realizations`)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    return rank * realizations, realizations
+
+
+def merge_counts(counts, group=None):
+    """Sums the count matrices of all ranks in place (integer all-reduce: order-independent,
+    so the merged matrix equals a single run over the union of the realization ranges bit
+    for bit).  `counts` is a torch tensor on the rank's device (or CPU with gloo)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
+    return counts

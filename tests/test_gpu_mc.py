@@ -131,7 +131,7 @@ def test_sssp_sigma_ws1000_sampled(B, delta):
     _sssp_check(wl, 1, sources, block_threads=B, bucket_width=delta)
 
 
-@pytest.mark.parametrize("B,T", [(1024, 1024), (1024, 256), (1024, 32), (512, 64), (512, 128),
+@pytest.mark.parametrize("B,T", [(1024, 1024), (1024, 256), (1024, 128), (512, 64), (512, 128),
                                  (256, 32), (256, 256)])
 def test_sssp_team_configurations(B, T):
     """Every (block, team) shape of the counting kernel runs the same batch routine."""
@@ -142,8 +142,17 @@ def test_sssp_team_configurations(B, T):
 
 
 @pytest.mark.parametrize("B,T,spt", [(1024, 256, 2), (512, 64, 1), (1024, 32, 0)])
+
 def test_counts_team_configurations(B, T, spt):
     _mc_check(_small_er(), 0, 40, block_threads=B, team_threads=T, slots_per_team=spt)
+
+
+def test_infeasible_team_shape_is_rejected():
+    """32 one-warp teams need 32 source slots; the 1000-node graph leaves room for about 11."""
+    wl = _ws1000()
+    with pytest.raises(afc.AfcError) as e:
+        _sssp_check(wl, 3, [0, 1], block_threads=1024, team_threads=32)
+    assert e.value.code == afc.AFC_EUNSUPPORTED
 
 
 def test_sssp_unweighted_grid_large_sigma():
