@@ -197,6 +197,22 @@ int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const in
                         double *lu, int32_t *piv, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/* Allocation-free variant of afc_absorbing_solve (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory themselves, e.g. code embedded in a host framework
+ * that hands out all device memory up front, or a plugin that may only use the buffers it is
+ * given).  It computes the observed states, assembles and solves the reduced system exactly as
+ * afc_absorbing_solve, but its whole workspace is one file-scope device array of about 0.6 MB
+ * inside the library; it allocates nothing and calls no allocating routine.
+ * In: chain, counts (DEVICE [n][n+1]).  Out (DEVICE): mu [n], b [n], scalars [4] as in
+ * afc_absorbing_solve.  Limits: n <= 4096 (else AFC_EUNSUPPORTED before any work) and at most
+ * 256 observed states (else AFC_EUNSUPPORTED after the states are counted).  SYNCHRONISES
+ * `stream`.  The first call on a device looks up the array's device address (once per device;
+ * make that first call before any stream capture).  Every call on a device shares the array and
+ * it keeps the last call's contents; calls whose work overlaps on the GPU (other streams or host
+ * threads) race on it, so serialise them. */
+int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,
+                                double *b, double *scalars, void *stream);
+
 /* ------------------------------------------------------------------------------------ */
 /* A9: row-wise perturbation sweep (Sec. 5.1 uncertainty set, Sec. 5.4 first-order        */
 /* sensitivity, Sec. 5.5 ranking reversals and certificates)                               */

@@ -27,7 +27,7 @@ __all__ = [
     "afc_transition_counts_batched_workspace", "afc_transition_counts_batched",
     "afc_debug_realize", "afc_debug_components", "afc_debug_sssp", "afc_observed_states",
     "afc_solve_workspace", "afc_absorbing_solve", "afc_perturb_sweep", "afc_certificates",
-    "afc_run_host", "AFC_FP64", "AFC_FP32_RECHECK",
+    "afc_run_host", "afc_absorbing_solve_noalloc", "AFC_FP64", "AFC_FP32_RECHECK",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -119,6 +119,8 @@ _SIGS = {
     "afc_certificates": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_f64,
                           c_f64, c_i32, c_p, c_p, c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_run_host": ([ctypes.POINTER(HostQuery), ctypes.POINTER(HostResult), c_p], ctypes.c_int),
+    "afc_absorbing_solve_noalloc": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p, c_p],
+                                    ctypes.c_int),
 }
 
 
@@ -229,6 +231,12 @@ def afc_absorbing_solve(chain, counts, c_index, c_list, c, mu, b, scalars, lu, p
     _chk(lib().afc_absorbing_solve(ctypes.byref(chain), _ptr(counts), _ptr(c_index), _ptr(c_list), c,
                                    _ptr(mu), _ptr(b), _ptr(scalars), _ptr(lu), _ptr(piv),
                                    _ptr(workspace), workspace_bytes, _ptr(stream)))
+
+
+def afc_absorbing_solve_noalloc(chain, counts, mu, b, scalars, stream):
+    """Allocation-free solve for callers that cannot allocate device memory; see afc.h."""
+    _chk(lib().afc_absorbing_solve_noalloc(ctypes.byref(chain), _ptr(counts), _ptr(mu), _ptr(b),
+                                           _ptr(scalars), _ptr(stream)))
 
 
 def afc_perturb_sweep(chain, pp, counts, c_index, c_list, c, mu0, b0, lu0, piv0, counters,

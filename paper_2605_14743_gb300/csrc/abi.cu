@@ -473,6 +473,27 @@ int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "certificates launch");
 }
 
+int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,
+                                double *b, double *scalars, void *stream) {
+  if (!chain || !counts || !mu || !b || !scalars) return fail(AFC_EINVAL, "null argument");
+  if (chain->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
+  if (chain->n > 4096)
+    return fail(AFC_EUNSUPPORTED, "the allocation-free solve supports n <= 4096 (got %d)", chain->n);
+  if (chain->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
+  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  uint32_t status = 0;
+  int32_t c = 0;
+  cudaError_t e = launch_solve_static(chain->n, chain->realizations, chain->alpha,
+                                      chain->absorb_floor, chain->s_init, chain->reward, counts, mu,
+                                      b, scalars, &status, &c, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "allocation-free solve");
+  if (status == 1u)
+    return fail(AFC_EUNSUPPORTED, "the allocation-free solve supports at most 256 observed states (got %d)", c);
+  if (status == 2u) return fail(AFC_ESINGULAR, "zero pivot in the LU of I - Q_CC");
+  return AFC_OK;
+}
+
 // ---- end to end from host memory ----------------------------------------------------------------
 
 int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream) {

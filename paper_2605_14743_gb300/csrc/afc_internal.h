@@ -120,6 +120,13 @@ cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const doub
                                 const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                                 unsigned char *ws, const SolveWs &L, cudaStream_t stream);
 size_t perturb_slab_bytes(int32_t n, int32_t c);
+
+// solve_static.cu (allocation-free solve; scratch is a file-scope device array)
+cudaError_t launch_solve_static(int32_t n, uint32_t R, double alpha, double eta, const double *s,
+                                const double *f, const uint32_t *counts, double *mu, double *b,
+                                double *scalars, uint32_t *status_host, int32_t *c_host,
+                                cudaStream_t stream);
+size_t solve_static_bytes();
 uint32_t perturb_smem_bytes(int32_t n, int32_t c);
 
 }  // namespace afc
