@@ -22,8 +22,9 @@ def test_run_host_matches_device_path_and_oracle():
     res = afc.run_query_host(bufs)
     counts = bufs.counts.numpy().view(np.uint32)
     assert (counts == dev.counts).all()
-    assert np.array_equal(bufs.b.numpy(), dev.b)
-    assert res.c == dev.c and abs(res.expected_T - dev.expected_T) == 0.0
+    # the solve accumulates its right-hand side with atomics: equal up to rounding order
+    assert close(bufs.b.numpy(), dev.b, rel=1e-12)
+    assert res.c == dev.c and abs(res.expected_T - dev.expected_T) <= 1e-12 * dev.expected_T
     assert list(res.perturb_counters) == dev.perturb["counters"].tolist()
     oc, _ = oracle_counts(wl, 0, wl.realizations, threads=4)
     assert (counts == oc).all()
