@@ -32,12 +32,19 @@ __device__ __forceinline__ unsigned long long *u64p(uint64_t *p) {
 constexpr uint32_t kInf = 0x7FFFFFFFu;    // unreached distance
 constexpr uint32_t kFlag = 0x80000000u;   // "sigma final" (forward) / "delta pending" (backward)
 constexpr uint32_t kMask = 0x7FFFFFFFu;
-constexpr uint16_t kMark = 0x8000u;       // finalise-this-member mark in ord
 constexpr uint64_t kNoRelax = ~0ull;
+constexpr uint64_t kIntTag = 0x8000000000000000ull;   // rho stored as an exact integer
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+  return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+__device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
+  *reinterpret_cast<volatile uint32_t *>(p) = v;
+}
 
 // Shared-memory layout of one CTA for a graph of n nodes, `arcs` arcs and S source slots.
 struct Layout {
-  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_src, off_sel, off_slots;
+  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_bci, off_src, off_sel, off_slots;
   uint32_t slot_bytes, words, total;
   __host__ __device__ static uint32_t al(uint32_t x) { return (x + 15u) & ~15u; }
   __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t nslots) {
@@ -48,6 +55,7 @@ struct Layout {
     off_comp = o;   o = al(o + 4u * n);
     off_cinfo = o;  o = al(o + 4u * n);
     off_bc = o;     o = al(o + 8u * n);
+    off_bci = o;    o = al(o + 4u * n);
     off_src = o;    o = al(o + 2u * (n > nslots ? n : nslots));
     off_sel = o;    o = al(o + 4u * n);
     off_slots = o;
@@ -149,8 +157,8 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, 
 template <int TS, int BLOCK, typename DT>
 __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, unsigned char *smem,
                               const Layout &L, uint32_t slot0, uint32_t S, const uint16_t *srcs,
-                              uint32_t delta, uint32_t ringB, double *bc, bool want_delta,
-                              CtaCtl *ctl) {
+                              uint32_t delta, uint32_t ringB, double *bc, uint32_t *bci,
+                              bool want_delta, CtaCtl *ctl) {
   const uint32_t n = H.n, W = L.words;
   const uint32_t tid = team.rank;
   TeamCtl *tc = team.tc;
@@ -292,57 +300,47 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
       if (!team.any(improved)) break;
     }
     if (!ok) break;
-    // path counts of the bucket: a member is final once its same-bucket predecessors are
+    // path counts of the bucket.  A member is final once all its predecessors are (earlier
+    // buckets are); it then publishes sigma before its flag (fence), and a reader that sees
+    // the flag of a same-bucket predecessor fences before reading that sigma.
     slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
     team.sync();
     const uint32_t total = tc->pref[S];
-    for (uint32_t k = tid; k < total; k += TS) {
-      const uint32_t i = find_slot(tc->pref, S, k);
-      SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-      const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-      if (v < n) a.sig[v] = (v == sl[i].s) ? 1ull : 0ull;
-    }
-    team.sync();
+    const uint32_t dstart = b * delta;
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
       bool open = false;
       for (uint32_t k = tid; k < total; k += TS) {
         const uint32_t i = find_slot(tc->pref, S, k);
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t idx = sl[i].mstart + k - tc->pref[i];
-        const uint32_t v = a.ord[idx];
+        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
         if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t dv = a.dist[v];
+        const uint32_t dv = ld_volatile(&a.dist[v]);
         if (dv & kFlag) continue;
-        const uint32_t s = sl[i].s;
-        uint64_t acc = (v == s) ? 1ull : 0ull;
+        uint64_t acc = 0;
         bool all_final = true;
-        if (v != s) {
+        if (v == sl[i].s) {
+          acc = 1;
+        } else {
           const uint32_t e1 = H.rp[v + 1];
           for (uint32_t e = H.rp[v]; e < e1; ++e) {
             const uint32_t pk = H.arc[e];
             const uint32_t u = pk & 0xFFFFu;
-            const uint32_t du = a.dist[u];
+            const uint32_t du = ld_volatile(&a.dist[u]);
             if ((du & kMask) + (pk >> 16) != dv) continue;
+            if (!(du & kFlag)) { all_final = false; break; }
+            if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
             const uint64_t nx = acc + a.sig[u];
             if (nx < acc) my_ovf = 1;
             acc = nx;
-            if (!(du & kFlag)) all_final = false;
           }
         }
-        a.sig[v] = acc;
-        if (all_final) a.ord[idx] = (uint16_t)(v | kMark);
-        else open = true;
-      }
-      team.sync();
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t idx = sl[i].mstart + k - tc->pref[i];
-        const uint32_t e = a.ord[idx];
-        if ((e & kMark) && (e & ~kMark) < n) {
-          a.ord[idx] = (uint16_t)(e & ~kMark);
-          a.dist[e & ~kMark] |= kFlag;
+        if (all_final) {
+          a.sig[v] = acc;
+          __threadfence_block();
+          st_volatile(&a.dist[v], dv | kFlag);
+        } else {
+          open = true;
         }
       }
       if (!team.any(open)) break;
@@ -408,33 +406,48 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
       slot_prefix(tc, tid, S, [&](uint32_t i) { return sl[i].hi - sl[i].lo; });
       team.sync();
       const uint32_t total = tc->pref[S];
+      const uint32_t dlo = bcur * delta, dhi = dlo + delta;
       for (uint32_t pass = 0;; ++pass) {
         if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
         bool open = false;
         for (uint32_t k = tid; k < total; k += TS) {
           const uint32_t i = find_slot(tc->pref, S, k);
           SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-          const uint32_t idx = sl[i].lo + k - tc->pref[i];
-          const uint32_t v = a.ord[idx];
+          const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
           if (v >= n) { my_err |= kErrCapacity; continue; }
-          const uint32_t dv = a.dist[v];
+          const uint32_t dv = ld_volatile(&a.dist[v]);
           if (!(dv & kFlag)) continue;
           const uint32_t dvm = dv & kMask;
-          DT acc = 0;
-          bool all_final = true;
+          uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
+          DT acc_f = 0;           // sum of the other rho
+          bool integral = true, all_final = true;
           const uint32_t e1 = H.rp[v + 1];
           for (uint32_t e = H.rp[v]; e < e1; ++e) {
             const uint32_t pk = H.arc[e];
             const uint32_t w = pk & 0xFFFFu;
-            const uint32_t dw = a.dist[w];
+            const uint32_t dw = ld_volatile(&a.dist[w]);
             if ((dw & kMask) != dvm + (pk >> 16)) continue;
-            acc += *reinterpret_cast<const DT *>(&a.sig[w]);   // rho(w) once w is final
-            if (dw & kFlag) all_final = false;
+            if (dw & kFlag) { all_final = false; break; }
+            if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
+            const uint64_t rw = a.sig[w];
+            if (rw & kIntTag) {
+              acc_i += (uint32_t)rw;
+            } else {
+              acc_f += *reinterpret_cast<const DT *>(&rw);
+              integral = false;
+            }
           }
-          if (all_final) {
-            const uint64_t sg = a.sig[v];
+          if (!all_final) { open = true; continue; }
+          const uint64_t sg = a.sig[v];
+          const bool is_src = (v == sl[i].s);
+          if (sg == 1ull && integral) {
+            // delta(v) = sum of the successors' subtree sizes: exact in integers
+            a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
+            if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+          } else {
+            const DT acc = (DT)acc_i + acc_f;
             DT dep, rho;
-            if (sg == 1ull) {           // unique shortest path: no division needed
+            if (sg == 1ull) {
               dep = acc;
               rho = (DT)1 + dep;
             } else {
@@ -442,23 +455,13 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
               dep = sv * acc;
               rho = ((DT)1 + dep) / sv;
             }
-            *reinterpret_cast<DT *>(&a.sig[v]) = rho;
-            if (v != sl[i].s) atomicAdd(&bc[v], (double)dep);
-            a.ord[idx] = (uint16_t)(v | kMark);
-          } else {
-            open = true;
+            uint64_t bits = 0;
+            *reinterpret_cast<DT *>(&bits) = rho;
+            a.sig[v] = bits;
+            if (!is_src) atomicAdd(&bc[v], (double)dep);
           }
-        }
-        team.sync();
-        for (uint32_t k = tid; k < total; k += TS) {
-          const uint32_t i = find_slot(tc->pref, S, k);
-          SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-          const uint32_t idx = sl[i].lo + k - tc->pref[i];
-          const uint32_t e = a.ord[idx];
-          if ((e & kMark) && (e & ~kMark) < n) {
-            a.ord[idx] = (uint16_t)(e & ~kMark);
-            a.dist[e & ~kMark] &= kMask;
-          }
+          __threadfence_block();
+          st_volatile(&a.dist[v], dvm);
         }
         if (!team.any(open)) break;
       }
@@ -728,6 +731,7 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     uint32_t *comp = reinterpret_cast<uint32_t *>(smem + L.off_comp);
     uint32_t *cinfo = reinterpret_cast<uint32_t *>(smem + L.off_cinfo);
     double *bc = reinterpret_cast<double *>(smem + L.off_bc);
+    uint32_t *bci = reinterpret_cast<uint32_t *>(smem + L.off_bci);
     uint16_t *src = reinterpret_cast<uint16_t *>(smem + L.off_src);
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + L.off_sel);
     if (threadIdx.x == 0) {
@@ -744,7 +748,7 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
 
     // sources: every node of a valid component (ascending), alive edges per root for TEPS
     uint32_t *cedges = sel;
-    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { cedges[v] = 0; bc[v] = 0.0; }
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { cedges[v] = 0; bc[v] = 0.0; bci[v] = 0; }
     __syncthreads();
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
       const uint32_t root = comp[v];
@@ -782,7 +786,7 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool use32 = fp32 && attempt == 0;
       if (attempt == 1) {
-        for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] = 0.0;
+        for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { bc[v] = 0.0; bci[v] = 0; }
         if (threadIdx.x == 0) ctl->cursor = 0;
         __syncthreads();
       }
@@ -795,11 +799,14 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
         const uint32_t S = min(spt, nsrc - k0);
         if (use32)
           brandes_batch<TS, BLOCK, float>(team, H, smem, L, team.id * spt, S, src + k0, delta,
-                                          ringB, bc, true, ctl);
+                                          ringB, bc, bci, true, ctl);
         else
           brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, src + k0, delta,
-                                           ringB, bc, true, ctl);
+                                           ringB, bc, bci, true, ctl);
       }
+      __syncthreads();
+      // betweenness = integral part (unique-path subtrees, exact) + floating part
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] += (double)bci[v];
       __syncthreads();
       const bool recheck = select_and_count(P, r_local, comp, cinfo, bc,
                                             slot_arrays(smem, L, n, 0), sel, use32, ctl);
@@ -870,6 +877,7 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
   uint32_t *rp = reinterpret_cast<uint32_t *>(smem + L.off_rp);
   uint32_t *arc = reinterpret_cast<uint32_t *>(smem + L.off_arc);
   double *bc = reinterpret_cast<double *>(smem + L.off_bc);
+  uint32_t *bci = reinterpret_cast<uint32_t *>(smem + L.off_bci);
   uint16_t *src = reinterpret_cast<uint16_t *>(smem + L.off_src);
   if (threadIdx.x == 0) { ctl->err = 0; ctl->ovf = 0; ctl->wmax = 1; }
   __syncthreads();
@@ -890,7 +898,7 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
     }
     team.sync();
     brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, tsrc, ctl->delta,
-                                     ctl->ring_b, bc, false, ctl);
+                                     ctl->ring_b, bc, bci, false, ctl);
     for (uint32_t t = team.rank; t < S * n; t += TS) {
       const uint32_t i = t / n, v = t - i * n;
       SlotArrays a = slot_arrays(smem, L, n, team.id * spt + i);
