@@ -315,7 +315,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
         const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
         if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t dv = ld_volatile(&a.dist[v]);
+        const uint32_t dv = a.dist[v];
         if (dv & kFlag) continue;
         uint64_t acc = 0;
         bool all_final = true;
@@ -326,7 +326,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           for (uint32_t e = H.rp[v]; e < e1; ++e) {
             const uint32_t pk = H.arc[e];
             const uint32_t u = pk & 0xFFFFu;
-            const uint32_t du = ld_volatile(&a.dist[u]);
+            const uint32_t du = a.dist[u];
             if ((du & kMask) + (pk >> 16) != dv) continue;
             if (!(du & kFlag)) { all_final = false; break; }
             if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
@@ -415,7 +415,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
           const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
           if (v >= n) { my_err |= kErrCapacity; continue; }
-          const uint32_t dv = ld_volatile(&a.dist[v]);
+          const uint32_t dv = a.dist[v];
           if (!(dv & kFlag)) continue;
           const uint32_t dvm = dv & kMask;
           uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
@@ -425,7 +425,7 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
           for (uint32_t e = H.rp[v]; e < e1; ++e) {
             const uint32_t pk = H.arc[e];
             const uint32_t w = pk & 0xFFFFu;
-            const uint32_t dw = ld_volatile(&a.dist[w]);
+            const uint32_t dw = a.dist[w];
             if ((dw & kMask) != dvm + (pk >> 16)) continue;
             if (dw & kFlag) { all_final = false; break; }
             if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
