@@ -34,12 +34,10 @@ constexpr uint32_t kFlag = 0x80000000u;   // "sigma final" (forward) / "delta pe
 constexpr uint32_t kMask = 0x7FFFFFFFu;
 constexpr uint64_t kNoRelax = ~0ull;
 constexpr uint64_t kIntTag = 0x8000000000000000ull;   // rho stored as an exact integer
-// dependency-counter states (values below kCntDone are pending same-bucket dependencies;
-// 0 = made ready by a decrement and owned by the thread that made it so)
-constexpr uint32_t kCntDone = 0xFFFFFFFDu;
-constexpr uint32_t kCntSeed = 0xFFFFFFFEu;    // ready from the start of the phase
-constexpr uint32_t kCntOrphan = 0xFFFFFFFFu;  // made ready, left for the next scan
 
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
+  return *reinterpret_cast<const volatile uint32_t *>(p);
+}
 __device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
   *reinterpret_cast<volatile uint32_t *>(p) = v;
 }
@@ -61,7 +59,7 @@ struct Layout {
     off_src = o;    o = al(o + 2u * (n > nslots ? n : nslots));
     off_sel = o;    o = al(o + 4u * n);
     off_slots = o;
-    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n) + al(4u * kRing * words) + al(4u * n);
+    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n) + al(4u * kRing * words);
     total = o + nslots * slot_bytes;
   }
 };
@@ -71,7 +69,6 @@ struct SlotArrays {
   uint64_t *sig;
   uint16_t *ord;
   uint32_t *ring;   // [kRing][words]
-  uint32_t *cnt;    // same-bucket dependency counters / states
 };
 
 __device__ __forceinline__ SlotArrays slot_arrays(unsigned char *smem, const Layout &L, uint32_t n,
@@ -81,8 +78,7 @@ __device__ __forceinline__ SlotArrays slot_arrays(unsigned char *smem, const Lay
   a.dist = reinterpret_cast<uint32_t *>(p);  p += Layout::al(4u * n);
   a.sig = reinterpret_cast<uint64_t *>(p);   p += Layout::al(8u * n);
   a.ord = reinterpret_cast<uint16_t *>(p);   p += Layout::al(2u * n);
-  a.ring = reinterpret_cast<uint32_t *>(p);  p += Layout::al(4u * kRing * L.words);
-  a.cnt = reinterpret_cast<uint32_t *>(p);
+  a.ring = reinterpret_cast<uint32_t *>(p);
   return a;
 }
 
@@ -304,88 +300,47 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
       if (!team.any(improved)) break;
     }
     if (!ok) break;
-    // path counts of the bucket.  Round A: each member sums the (final) counts of its
-    // predecessors in earlier buckets and counts its same-bucket predecessors.  Then members
-    // become final in dependency order: a member with no pending predecessor pulls the
-    // same-bucket counts, publishes sigma (fence, then the flag) and decrements its same-bucket
-    // successors; a decrement to zero hands that successor to the decrementing thread, which
-    // continues the chain (further successors it frees are left for the next scan).
+    // path counts of the bucket.  A member is final once all its predecessors are (earlier
+    // buckets are); it then publishes sigma before its flag (fence), and a reader that sees
+    // the flag of a same-bucket predecessor fences before reading that sigma.
     slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
     team.sync();
     const uint32_t total = tc->pref[S];
     const uint32_t dstart = b * delta;
-    for (uint32_t k = tid; k < total; k += TS) {
-      const uint32_t i = find_slot(tc->pref, S, k);
-      SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-      const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-      if (v >= n) { my_err |= kErrCapacity; continue; }
-      const uint32_t dv = a.dist[v];
-      uint64_t acc = 0;
-      uint32_t c = 0;
-      if (v == sl[i].s) {
-        acc = 1;
-      } else {
-        const uint32_t e1 = H.rp[v + 1];
-        for (uint32_t e = H.rp[v]; e < e1; ++e) {
-          const uint32_t pk = H.arc[e];
-          const uint32_t du = a.dist[pk & 0xFFFFu] & kMask;
-          if (du + (pk >> 16) != dv) continue;
-          if (du < dstart) {
-            const uint64_t nx = acc + a.sig[pk & 0xFFFFu];
-            if (nx < acc) my_ovf = 1;
-            acc = nx;
-          } else {
-            ++c;
-          }
-        }
-      }
-      a.sig[v] = acc;
-      a.cnt[v] = c ? c : kCntSeed;
-    }
-    team.sync();
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
       bool open = false;
       for (uint32_t k = tid; k < total; k += TS) {
         const uint32_t i = find_slot(tc->pref, S, k);
         SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-        if (v >= n) continue;
-        const uint32_t st = a.cnt[v];
-        if (st == kCntDone) continue;
-        if (st != kCntSeed && st != kCntOrphan) { open = true; continue; }
-        for (uint32_t chain = 0; chain <= n; ++chain) {
-          const uint32_t dv = a.dist[v];
-          uint64_t acc = a.sig[v];
+        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
+        if (v >= n) { my_err |= kErrCapacity; continue; }
+        const uint32_t dv = a.dist[v];
+        if (dv & kFlag) continue;
+        uint64_t acc = 0;
+        bool all_final = true;
+        if (v == sl[i].s) {
+          acc = 1;
+        } else {
           const uint32_t e1 = H.rp[v + 1];
-          if (v != sl[i].s) {
-            for (uint32_t e = H.rp[v]; e < e1; ++e) {   // same-bucket predecessors (final)
-              const uint32_t pk = H.arc[e];
-              const uint32_t du = a.dist[pk & 0xFFFFu] & kMask;
-              if (du + (pk >> 16) != dv || du < dstart) continue;
-              __threadfence_block();
-              const uint64_t nx = acc + a.sig[pk & 0xFFFFu];
-              if (nx < acc) my_ovf = 1;
-              acc = nx;
-            }
+          for (uint32_t e = H.rp[v]; e < e1; ++e) {
+            const uint32_t pk = H.arc[e];
+            const uint32_t u = pk & 0xFFFFu;
+            const uint32_t du = a.dist[u];
+            if ((du & kMask) + (pk >> 16) != dv) continue;
+            if (!(du & kFlag)) { all_final = false; break; }
+            if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
+            const uint64_t nx = acc + a.sig[u];
+            if (nx < acc) my_ovf = 1;
+            acc = nx;
           }
+        }
+        if (all_final) {
           a.sig[v] = acc;
-          a.cnt[v] = kCntDone;
           __threadfence_block();
           st_volatile(&a.dist[v], dv | kFlag);
-          uint32_t next = 0xFFFFFFFFu;
-          for (uint32_t e = H.rp[v]; e < e1; ++e) {     // same-bucket successors
-            const uint32_t pk = H.arc[e];
-            const uint32_t w = pk & 0xFFFFu;
-            const uint32_t dw = a.dist[w] & kMask;
-            if (dw != dv + (pk >> 16) || dw >= dend) continue;
-            if (atomicSub(&a.cnt[w], 1u) == 1u) {
-              if (next == 0xFFFFFFFFu) next = w;
-              else a.cnt[w] = kCntOrphan;
-            }
-          }
-          if (next == 0xFFFFFFFFu) break;
-          v = next;
+        } else {
+          open = true;
         }
       }
       if (!team.any(open)) break;
@@ -452,95 +407,61 @@ __device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, un
       team.sync();
       const uint32_t total = tc->pref[S];
       const uint32_t dlo = bcur * delta, dhi = dlo + delta;
-      // Round A: count same-bucket successors.  Then dependency order as in the forward
-      // phase: a member whose successors are all final pulls their rho, publishes its own
-      // rho and decrements its same-bucket predecessors.
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
-        if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t dvm = a.dist[v] & kMask;
-        uint32_t c = 0;
-        const uint32_t e1 = H.rp[v + 1];
-        for (uint32_t e = H.rp[v]; e < e1; ++e) {
-          const uint32_t pk = H.arc[e];
-          const uint32_t dw = a.dist[pk & 0xFFFFu] & kMask;
-          c += (dw == dvm + (pk >> 16) && dw < dhi) ? 1u : 0u;
-        }
-        a.cnt[v] = c ? c : kCntSeed;
-      }
-      team.sync();
       for (uint32_t pass = 0;; ++pass) {
         if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
         bool open = false;
         for (uint32_t k = tid; k < total; k += TS) {
           const uint32_t i = find_slot(tc->pref, S, k);
           SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-          uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
-          if (v >= n) continue;
-          const uint32_t st = a.cnt[v];
-          if (st == kCntDone) continue;
-          if (st != kCntSeed && st != kCntOrphan) { open = true; continue; }
-          for (uint32_t chain = 0; chain <= n; ++chain) {
-            const uint32_t dvm = a.dist[v] & kMask;
-            uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
-            DT acc_f = 0;           // sum of the other rho
-            bool integral = true;
-            const uint32_t e1 = H.rp[v + 1];
-            for (uint32_t e = H.rp[v]; e < e1; ++e) {   // successors (all final)
-              const uint32_t pk = H.arc[e];
-              const uint32_t w = pk & 0xFFFFu;
-              const uint32_t dw = a.dist[w] & kMask;
-              if (dw != dvm + (pk >> 16)) continue;
-              if (dw < dhi) __threadfence_block();       // same-bucket successor
-              const uint64_t rw = a.sig[w];
-              if (rw & kIntTag) {
-                acc_i += (uint32_t)rw;
-              } else {
-                acc_f += *reinterpret_cast<const DT *>(&rw);
-                integral = false;
-              }
-            }
-            const uint64_t sg = a.sig[v];
-            const bool is_src = (v == sl[i].s);
-            if (sg == 1ull && integral) {
-              // delta(v) = sum of the successors' subtree sizes: exact in integers
-              a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-              if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+          const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
+          if (v >= n) { my_err |= kErrCapacity; continue; }
+          const uint32_t dv = a.dist[v];
+          if (!(dv & kFlag)) continue;
+          const uint32_t dvm = dv & kMask;
+          uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
+          DT acc_f = 0;           // sum of the other rho
+          bool integral = true, all_final = true;
+          const uint32_t e1 = H.rp[v + 1];
+          for (uint32_t e = H.rp[v]; e < e1; ++e) {
+            const uint32_t pk = H.arc[e];
+            const uint32_t w = pk & 0xFFFFu;
+            const uint32_t dw = a.dist[w];
+            if ((dw & kMask) != dvm + (pk >> 16)) continue;
+            if (dw & kFlag) { all_final = false; break; }
+            if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
+            const uint64_t rw = a.sig[w];
+            if (rw & kIntTag) {
+              acc_i += (uint32_t)rw;
             } else {
-              const DT acc = (DT)acc_i + acc_f;
-              DT dep, rho;
-              if (sg == 1ull) {
-                dep = acc;
-                rho = (DT)1 + dep;
-              } else {
-                const DT sv = (DT)sg;
-                dep = sv * acc;
-                rho = ((DT)1 + dep) / sv;
-              }
-              uint64_t bits = 0;
-              *reinterpret_cast<DT *>(&bits) = rho;
-              a.sig[v] = bits;
-              if (!is_src) atomicAdd(&bc[v], (double)dep);
+              acc_f += *reinterpret_cast<const DT *>(&rw);
+              integral = false;
             }
-            a.cnt[v] = kCntDone;
-            __threadfence_block();
-            st_volatile(&a.dist[v], dvm);
-            uint32_t next = 0xFFFFFFFFu;
-            for (uint32_t e = H.rp[v]; e < e1; ++e) {   // same-bucket predecessors
-              const uint32_t pk = H.arc[e];
-              const uint32_t u = pk & 0xFFFFu;
-              const uint32_t du = a.dist[u] & kMask;
-              if (du + (pk >> 16) != dvm || du < dlo) continue;
-              if (atomicSub(&a.cnt[u], 1u) == 1u) {
-                if (next == 0xFFFFFFFFu) next = u;
-                else a.cnt[u] = kCntOrphan;
-              }
-            }
-            if (next == 0xFFFFFFFFu) break;
-            v = next;
           }
+          if (!all_final) { open = true; continue; }
+          const uint64_t sg = a.sig[v];
+          const bool is_src = (v == sl[i].s);
+          if (sg == 1ull && integral) {
+            // delta(v) = sum of the successors' subtree sizes: exact in integers
+            a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
+            if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+          } else {
+            const DT acc = (DT)acc_i + acc_f;
+            DT dep, rho;
+            if (sg == 1ull) {
+              dep = acc;
+              rho = (DT)1 + dep;
+            } else {
+              const DT sv = (DT)sg;
+              dep = sv * acc;
+              rho = ((DT)1 + dep) / sv;
+            }
+            uint64_t bits = 0;
+            *reinterpret_cast<DT *>(&bits) = rho;
+            a.sig[v] = bits;
+            if (!is_src) atomicAdd(&bc[v], (double)dep);
+          }
+          __threadfence_block();
+          st_volatile(&a.dist[v], dvm);
         }
         if (!team.any(open)) break;
       }
