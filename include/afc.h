@@ -38,9 +38,14 @@ extern "C" {
 #define AFC_ECUDA 6        /* a CUDA runtime call failed                                   */
 #define AFC_EUNSUPPORTED 7 /* the problem exceeds an implementation limit                  */
 #define AFC_EDEVICE 8      /* a device-side consistency check failed (see message)        */
+#define AFC_EBUSY 9        /* serving: refused for now (over budget, queue full) or pending */
 
 #define AFC_FP64 0          /* dependencies delta accumulated in FP64                        */
 #define AFC_FP32_RECHECK 1  /* delta in FP32, realizations with a near-tied top two in FP64 */
+
+#define AFC_PATH_AUTO 0     /* counting path chosen by what fits in shared memory            */
+#define AFC_PATH_SHARED 1   /* realization and source state in shared memory (small graphs)  */
+#define AFC_PATH_GLOBAL 2   /* realized graph and source state in device memory (any size)   */
 
 const char *afc_last_error(void);
 int afc_version(void);
@@ -95,14 +100,18 @@ typedef struct {
   int32_t precision;         /* AFC_FP64 or AFC_FP32_RECHECK                              */
   double recheck_margin;     /* FP32 mode: recompute a realization in FP64 when some valid */
                              /* component's top-two gap (B1 - B2) / B1 < recheck_margin    */
-  uint32_t bucket_width;     /* SSSP bucket width Delta (raised, per realization, to at     */
-                             /* least ceil(max length / 10)); 0 = automatic                */
+  uint32_t bucket_width;     /* SSSP bucket width Delta, rounded up per realization to a    */
+                             /* power of two >= ceil(max length / 14); 0 = automatic       */
   int32_t block_threads;     /* threads per CTA of the counting kernel: 256, 512 or 1024;  */
                              /* 0 = automatic                                              */
   int32_t team_threads;      /* threads of one team (32 .. block_threads, a power of two); */
                              /* each team advances its own batch of sources; 0 = auto      */
   int32_t slots_per_team;    /* sources a team advances in lockstep (1..16); 0 = as many   */
                              /* as shared memory holds                                     */
+  int32_t memory_path;       /* AFC_PATH_AUTO: realizations of graphs whose per-CTA state  */
+                             /* fits in shared memory run there, others on the global-     */
+                             /* memory path; AFC_PATH_SHARED / AFC_PATH_GLOBAL force one   */
+                             /* (AFC_EUNSUPPORTED if the shared path does not fit)          */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */
@@ -294,6 +303,65 @@ typedef struct {
  * the perturbation sweep, then device-to-host copies.  Allocates and frees its own device
  * memory (stream-ordered) and SYNCHRONISES `stream` before returning. */
 int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream);
+
+/* ------------------------------------------------------------------------------------ */
+/* Serving loop: continuous batching of queries that arrive at any time                   */
+/* ------------------------------------------------------------------------------------ */
+/* The paper defines one query (a base graph, its failure and weight laws, the sampling
+ * budget M and the chain parameters: Sec. 3 and Alg. 2); serving many of them at once is an
+ * engineering layer with no counterpart there.  Queries are admitted in arrival order while
+ * the device-memory footprint of the admitted ones stays within hbm_budget and at most
+ * max_active are admitted.  Every admitted query keeps its graph, parameters and partial
+ * counts on the device; a scheduler thread advances all admitted queries together, one
+ * batched counting launch per slice (slice_realizations more realizations of each), so a
+ * query that arrives while others run joins the next slice.  A query whose realizations are
+ * all counted is finished (observed states, absorbing-chain solve, perturbation sweep,
+ * device-to-host copy) on a second stream by a finisher thread while counting goes on, and
+ * its device memory is released.  Realization r of a query is the same draw whatever else
+ * runs beside it, so its counts equal those of afc_run_host exactly and its visit shares
+ * agree up to the rounding order of the solve's accumulations. */
+typedef struct afc_server afc_server;
+
+typedef struct {
+  uint64_t hbm_budget;         /* bytes admitted queries may hold; 0 = 80% of free memory   */
+  uint32_t max_active;         /* queries admitted at once; 0 = 64                          */
+  uint32_t max_waiting;        /* queue length beyond which submissions are refused         */
+                               /* (AFC_EBUSY, counted as shed); 0 = unbounded               */
+  uint32_t slice_realizations; /* realizations per admitted query per slice; 0 = automatic  */
+  int32_t keep_counts;         /* 1: results include the [n][n+1] count matrix              */
+} afc_server_cfg;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, shed, failed;
+  uint64_t realizations;       /* realizations of completed queries                          */
+  uint64_t edge_visits;        /* Graph500 edge count of completed queries                   */
+  uint64_t slices;             /* batched counting launches                                  */
+  uint64_t peak_bytes;         /* largest admitted footprint                                 */
+  double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> result ready, completed queries    */
+  double wait_p50_ms, wait_p99_ms;          /* submit -> admission                          */
+  double wall_s;               /* first submission -> last completion                       */
+  double realizations_per_s;   /* realizations / wall_s                                     */
+} afc_server_stats;
+
+/* Starts the scheduler and finisher threads on the current device. */
+int afc_server_create(const afc_server_cfg *cfg, afc_server **out);
+
+/* Copies the query (all HOST arrays are read during the call) and queues it.  AFC_EBUSY:
+ * the query alone exceeds hbm_budget, or max_waiting queries are already queued.  Argument
+ * errors as afc_run_host. */
+int afc_server_submit(afc_server *s, const afc_host_query *q, uint64_t *ticket);
+
+/* Waits up to wait_ms (negative: no limit, 0: just look) for the query's result.  AFC_EBUSY
+ * while it is pending; otherwise the query's status, its result copied into res (res->b
+ * required, res->mu and res->counts optional; counts only with keep_counts) and, when
+ * latency_ms is not NULL, its submit-to-ready time.  A ticket can be collected once. */
+int afc_server_poll(afc_server *s, uint64_t ticket, int32_t wait_ms, afc_host_result *res,
+                    double *latency_ms);
+
+int afc_server_get_stats(afc_server *s, afc_server_stats *out);
+
+/* Finishes every admitted and queued query, then stops the threads and frees everything. */
+void afc_server_destroy(afc_server *s);
 
 #ifdef __cplusplus
 }

@@ -28,11 +28,15 @@ __all__ = [
     "afc_debug_realize", "afc_debug_components", "afc_debug_sssp", "afc_observed_states",
     "afc_solve_workspace", "afc_absorbing_solve", "afc_perturb_sweep", "afc_certificates",
     "afc_run_host", "afc_absorbing_solve_noalloc", "AFC_FP64", "AFC_FP32_RECHECK",
+    "AFC_PATH_AUTO", "AFC_PATH_SHARED", "AFC_PATH_GLOBAL", "AFC_EBUSY", "ServerCfg",
+    "ServerStats", "afc_server_create", "afc_server_submit", "afc_server_poll",
+    "afc_server_get_stats", "afc_server_destroy",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
-AFC_ETIMEOUT, AFC_ECUDA, AFC_EUNSUPPORTED, AFC_EDEVICE = 5, 6, 7, 8
+AFC_ETIMEOUT, AFC_ECUDA, AFC_EUNSUPPORTED, AFC_EDEVICE, AFC_EBUSY = 5, 6, 7, 8, 9
 AFC_FP64, AFC_FP32_RECHECK = 0, 1
+AFC_PATH_AUTO, AFC_PATH_SHARED, AFC_PATH_GLOBAL = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -55,7 +59,7 @@ class McProblem(ctypes.Structure):
                 ("k_min", c_u32), ("in_w", c_p), ("top_k", c_u32), ("tie_rel", c_f64),
                 ("precision", c_i32), ("recheck_margin", c_f64), ("bucket_width", c_u32),
                 ("block_threads", c_i32), ("team_threads", c_i32),
-                ("slots_per_team", c_i32)]
+                ("slots_per_team", c_i32), ("memory_path", c_i32)]
 
 
 class McStats(ctypes.Structure):
@@ -93,6 +97,19 @@ class HostResult(ctypes.Structure):
                 ("device_ms", c_f64)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget", c_u64), ("max_active", c_u32), ("max_waiting", c_u32),
+                ("slice_realizations", c_u32), ("keep_counts", c_i32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_u64), ("admitted", c_u64), ("completed", c_u64), ("shed", c_u64),
+                ("failed", c_u64), ("realizations", c_u64), ("edge_visits", c_u64),
+                ("slices", c_u64), ("peak_bytes", c_u64), ("p50_ms", c_f64), ("p99_ms", c_f64),
+                ("mean_ms", c_f64), ("max_ms", c_f64), ("wait_p50_ms", c_f64),
+                ("wait_p99_ms", c_f64), ("wall_s", c_f64), ("realizations_per_s", c_f64)]
+
+
 _SIGS = {
     "afc_last_error": ([], ctypes.c_char_p),
     "afc_version": ([], ctypes.c_int),
@@ -121,6 +138,12 @@ _SIGS = {
     "afc_run_host": ([ctypes.POINTER(HostQuery), ctypes.POINTER(HostResult), c_p], ctypes.c_int),
     "afc_absorbing_solve_noalloc": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p, c_p],
                                     ctypes.c_int),
+    "afc_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_server_submit": ([c_p, ctypes.POINTER(HostQuery), ctypes.POINTER(c_u64)], ctypes.c_int),
+    "afc_server_poll": ([c_p, c_u64, c_i32, ctypes.POINTER(HostResult), ctypes.POINTER(c_f64)],
+                        ctypes.c_int),
+    "afc_server_get_stats": ([c_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "afc_server_destroy": ([c_p], None),
 }
 
 
@@ -259,9 +282,44 @@ def afc_run_host(query: HostQuery, result: HostResult, stream):
     _chk(lib().afc_run_host(ctypes.byref(query), ctypes.byref(result), _ptr(stream)))
 
 
+def afc_server_create(cfg: ServerCfg) -> int:
+    h = c_p()
+    _chk(lib().afc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def afc_server_submit(server: int, query: HostQuery) -> int:
+    """Ticket of the queued query; raises AfcError (code AFC_EBUSY when refused)."""
+    t = c_u64(0)
+    _chk(lib().afc_server_submit(server, ctypes.byref(query), ctypes.byref(t)))
+    return t.value
+
+
+def afc_server_poll(server: int, ticket: int, wait_ms: int, result: HostResult):
+    """(status, latency_ms): AFC_EBUSY while pending, AFC_OK when result holds the answer;
+    raises AfcError when the query failed."""
+    lat = c_f64(0.0)
+    code = lib().afc_server_poll(server, ticket, wait_ms, ctypes.byref(result), ctypes.byref(lat))
+    if code == AFC_EBUSY:
+        return code, None
+    _chk(code)
+    return code, lat.value
+
+
+def afc_server_get_stats(server: int) -> ServerStats:
+    st = ServerStats()
+    _chk(lib().afc_server_get_stats(server, ctypes.byref(st)))
+    return st
+
+
+def afc_server_destroy(server: int) -> None:
+    lib().afc_server_destroy(server)
+
+
 # ---- helpers over torch device memory -------------------------------------------------------
 
-from .engine import (DeviceGraph, Query, QueryResult, run_query, run_query_host,  # noqa: E402
-                     make_problem)
+from .engine import (DeviceGraph, Query, QueryResult, Server, run_query,  # noqa: E402
+                     run_query_host, make_problem)
 
-__all__ += ["DeviceGraph", "Query", "QueryResult", "run_query", "run_query_host", "make_problem"]
+__all__ += ["DeviceGraph", "Query", "QueryResult", "Server", "run_query", "run_query_host",
+            "make_problem"]

@@ -53,6 +53,7 @@ DevInfo dev_info() {
   return d;
 }
 
+// Requested bucket width; the kernels round it up to a power of two (and to the ring bound).
 uint32_t auto_delta(const afc_mc_problem &p) {
   if (p.bucket_width) return p.bucket_width;
   const double lo = p.w_lo ? 1.0 : (double)p.w_lo_all;
@@ -70,7 +71,16 @@ int auto_block(const afc_mc_problem &p) {
 
 int validate(const afc_mc_problem *p) {
   if (!p) return fail(AFC_EINVAL, "null problem");
-  if (p->n < 1 || p->n > 32767) return fail(AFC_EUNSUPPORTED, "n = %d outside [1, 32767]", p->n);
+  if (p->n < 1 || p->n > 65535) return fail(AFC_EUNSUPPORTED, "n = %d outside [1, 65535]", p->n);
+  {
+    // every distance, (n - 1) * max length at most, and one more arc must stay below 2^31
+    const uint64_t wmax = p->w_hi ? 65535u : p->w_hi_all;
+    if ((uint64_t)p->n * wmax >= 0x7FFFFFFFull)
+      return fail(AFC_EUNSUPPORTED, "n * max length = %llu reaches 2^31 (distance range)",
+                  (unsigned long long)((uint64_t)p->n * wmax));
+  }
+  if (p->memory_path < AFC_PATH_AUTO || p->memory_path > AFC_PATH_GLOBAL)
+    return fail(AFC_EINVAL, "memory_path must be AFC_PATH_AUTO, _SHARED or _GLOBAL");
   if (p->m < 0 || p->m > 0x3FFFFFFF) return fail(AFC_EINVAL, "m = %lld out of range", (long long)p->m);
   if (!p->row_ptr || (p->m > 0 && (!p->col || !p->eid)))
     return fail(AFC_EINVAL, "CSR pointers missing");
@@ -84,7 +94,8 @@ int validate(const afc_mc_problem *p) {
   if (p->precision == AFC_FP32_RECHECK && !(p->recheck_margin >= 0.0)) return fail(AFC_EINVAL, "bad recheck_margin");
   const int B = auto_block(*p);
   if (B != 256 && B != 512 && B != 1024) return fail(AFC_EINVAL, "block_threads must be 256, 512 or 1024");
-  if (p->team_threads && !mc_config_supported(B, p->team_threads))
+  if (p->team_threads && !mc_config_supported(B, p->team_threads) &&
+      !big_config_supported(B, p->team_threads))
     return fail(AFC_EINVAL, "team_threads %d not supported with block_threads %d", p->team_threads, B);
   if (p->slots_per_team < 0 || p->slots_per_team > kMaxSlotsPerTeam)
     return fail(AFC_EINVAL, "slots_per_team must be in [0, %d]", kMaxSlotsPerTeam);
@@ -171,57 +182,165 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
   return pl;
 }
 
-McPlan plan_counts(int nprob, const afc_mc_problem *probs, uint64_t total_items) {
-  uint32_t nmax = 1;
-  uint64_t amax = 1;
-  for (int g = 0; g < nprob; ++g) {
-    nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
-    amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
+// Launch plan of the global-memory path for one problem.
+struct BigPlan {
+  int block = 1024, team = 256;
+  uint32_t spt = 1, grid = 1, ngroups = 1;
+  size_t slot_stride = 0, group_bytes = 0;
+  size_t off_groups = 0, off_garr = 0, off_arena = 0, total = 0;   // relative to its base
+};
+
+BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
+  const DevInfo d = dev_info();
+  BigPlan b;
+  const uint32_t n = (uint32_t)p.n;
+  const uint64_t arcs = 2ull * (uint64_t)p.m;
+  b.block = p.block_threads ? p.block_threads : 1024;
+  b.slot_stride = big_slot_bytes(n);
+  if (p.team_threads) {
+    b.team = p.team_threads;
+  } else {
+    // source slots of all CTAs within about 48 MB, so that they stay resident in L2: as many
+    // teams per CTA as that allows (at most 8), each as wide as the block allows
+    const size_t per_cta = (48ull << 20) / (size_t)std::max(1, d.sms);
+    const size_t nt_fit = std::max<size_t>(1, per_cta / b.slot_stride);
+    b.team = b.block;
+    for (int t : {128, 256, 512, 1024}) {
+      if (t > b.block || !big_config_supported(b.block, t)) continue;
+      if ((size_t)(b.block / t) <= std::min<size_t>(nt_fit, 8)) { b.team = t; break; }
+    }
   }
-  McPlan pl = plan_for(probs[0], nmax, amax, total_items, probs[0].team_threads,
-                       probs[0].slots_per_team);
-  pl.ws_meta = ((sizeof(McDev) * (size_t)nprob + sizeof(uint64_t) * (size_t)(nprob + 1)) + 255) & ~size_t(255);
-  pl.ws_total = pl.ws_meta;
-  return pl;
+  const uint32_t nt = (uint32_t)(b.block / b.team);
+  b.spt = p.slots_per_team ? (uint32_t)p.slots_per_team : 1u;
+  b.spt = std::min<uint32_t>(b.spt, std::max<uint32_t>(1u, (uint32_t)kMaxSlots / nt));
+  b.grid = (uint32_t)std::max(1, d.sms) * (uint32_t)std::max(1, 1024 / b.block);
+  // realizations in flight: enough sources for every team a few times over
+  const uint64_t want = ((uint64_t)4 * b.grid * nt * b.spt + n - 1) / n;
+  b.ngroups = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({std::max<uint64_t>(want, 2), 64,
+                                                                   std::max<uint64_t>(r_count, 1)}));
+  b.group_bytes = big_group_bytes(n, arcs);
+  size_t o = 0;
+  b.off_groups = o; o += (sizeof(BigGroup) * b.ngroups + 255) & ~size_t(255);
+  b.off_garr = o;   o += b.group_bytes * b.ngroups;
+  b.off_arena = o;  o += b.slot_stride * (size_t)b.grid * nt * b.spt;
+  b.total = o;
+  return b;
+}
+
+bool smem_fits(const afc_mc_problem &p) {
+  return plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1, p.team_threads, p.slots_per_team).fits;
+}
+
+bool wants_global(const afc_mc_problem &p) {
+  if (p.memory_path == AFC_PATH_GLOBAL) return true;
+  if (p.memory_path == AFC_PATH_SHARED) return false;
+  return !smem_fits(p);
+}
+
+size_t meta_bytes(int nprob) {
+  return ((sizeof(McDev) * (size_t)nprob + sizeof(uint64_t) * (size_t)(nprob + 1)) + 255) &
+         ~size_t(255);
+}
+
+// Workspace: [McDev x nprob][item prefix of the shared-path problems] then the global path's
+// groups, group arrays and slot arena (reused by the global-path problems one after another).
+size_t counts_ws_total(int nprob, const afc_mc_problem *probs, const uint32_t *r_count) {
+  size_t big = 0;
+  for (int g = 0; g < nprob; ++g)
+    if (wants_global(probs[g])) big = std::max(big, plan_big(probs[g], r_count ? r_count[g] : 1u << 20).total);
+  return meta_bytes(nprob) + big;
 }
 
 int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
-               const uint32_t *r_count, uint32_t *const *counts, afc_mc_stats *stats,
+               const uint32_t *r_count, uint32_t *const *counts, afc_mc_stats *const *stats,
                double *dump_bc, int32_t *dump_next, void *workspace, size_t ws_bytes,
                cudaStream_t stream) {
   for (int g = 0; g < nprob; ++g) {
     int st = validate(&probs[g]);
     if (st) return st;
-    if (auto_block(probs[g]) != auto_block(probs[0]))
-      return fail(AFC_EINVAL, "all problems of a batch must use the same block_threads");
     if (!counts[g]) return fail(AFC_EINVAL, "counts[%d] is null", g);
+    if (probs[g].memory_path == AFC_PATH_SHARED && !smem_fits(probs[g]))
+      return fail(AFC_EUNSUPPORTED, "problem %d does not fit the shared-memory counting path", g);
   }
+  // problems on the shared-memory path first (one persistent launch), then the others
+  std::vector<int> order, big;
+  for (int g = 0; g < nprob; ++g) (wants_global(probs[g]) ? big : order).push_back(g);
+  const int ns = (int)order.size();
+  for (int g : order)
+    if (auto_block(probs[g]) != auto_block(probs[order[0]]))
+      return fail(AFC_EINVAL, "all shared-path problems of a batch must use the same block_threads");
+  order.insert(order.end(), big.begin(), big.end());
   std::vector<McDev> devs(nprob);
-  std::vector<uint64_t> prefix(nprob + 1, 0);
-  for (int g = 0; g < nprob; ++g) {
-    devs[g] = to_dev(probs[g], r_begin ? r_begin[g] : 0u, counts[g], stats ? stats + g : nullptr,
+  std::vector<uint64_t> prefix(ns + 1, 0);
+  uint32_t nmax = 1;
+  uint64_t amax = 1;
+  for (int k = 0; k < nprob; ++k) {
+    const int g = order[k];
+    devs[k] = to_dev(probs[g], r_begin ? r_begin[g] : 0u, counts[g], stats ? stats[g] : nullptr,
                      nprob == 1 ? dump_bc : nullptr, nprob == 1 ? dump_next : nullptr);
-    prefix[g + 1] = prefix[g] + r_count[g];
+    if (k < ns) {
+      prefix[k + 1] = prefix[k] + r_count[g];
+      nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
+      amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
+    }
   }
-  const uint64_t total = prefix[nprob];
-  if (total == 0) return AFC_OK;
-  const McPlan pl = plan_counts(nprob, probs, total);
-  if (!pl.fits)
-    return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory counting kernel");
-  if (!workspace || ws_bytes < pl.ws_total)
-    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", ws_bytes, pl.ws_total);
+  const size_t need = counts_ws_total(nprob, probs, r_count);
+  if (!workspace || ws_bytes < need)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", ws_bytes, need);
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   McDev *devs_d = reinterpret_cast<McDev *>(ws);
   uint64_t *prefix_d = reinterpret_cast<uint64_t *>(ws + sizeof(McDev) * (size_t)nprob);
   AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)nprob, cudaMemcpyHostToDevice, stream));
-  AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(nprob + 1), cudaMemcpyHostToDevice, stream));
-  cudaError_t e = launch_mc_counts(pl.block, pl.team, devs_d, nprob, prefix_d, total, pl.spt,
-                                   pl.smem, pl.grid, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
+  AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(ns + 1), cudaMemcpyHostToDevice, stream));
+  if (ns > 0 && prefix[ns] > 0) {
+    const afc_mc_problem &p0 = probs[order[0]];
+    const McPlan pl = plan_for(p0, nmax, amax, prefix[ns], p0.team_threads, p0.slots_per_team);
+    if (!pl.fits)
+      return fail(AFC_EUNSUPPORTED, "batch too large for the shared-memory counting kernel");
+    cudaError_t e = launch_mc_counts(pl.block, pl.team, devs_d, ns, prefix_d, prefix[ns], pl.spt,
+                                     pl.smem, pl.grid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
+  }
+  unsigned char *bigbase = ws + meta_bytes(nprob);
+  for (int k = ns; k < nprob; ++k) {
+    const afc_mc_problem &p = probs[order[k]];
+    const uint32_t rc = r_count[order[k]];
+    if (rc == 0) continue;
+    const BigPlan b = plan_big(p, rc);
+    std::vector<BigGroup> groups(b.ngroups);
+    for (uint32_t i = 0; i < b.ngroups; ++i)
+      big_group_carve(groups[i], bigbase + b.off_garr + b.group_bytes * i, (uint32_t)p.n,
+                      2ull * (uint64_t)p.m);
+    BigGroup *groups_d = reinterpret_cast<BigGroup *>(bigbase + b.off_groups);
+    AFC_CUDA(cudaMemcpyAsync(groups_d, groups.data(), sizeof(BigGroup) * b.ngroups,
+                             cudaMemcpyHostToDevice, stream));
+    cudaError_t e = launch_mc_global(b.block, b.team, devs_d + k, p.precision, groups_d, b.ngroups,
+                                     rc, bigbase + b.off_arena, b.slot_stride, b.spt, b.grid,
+                                     stream);
+    if (e != cudaSuccess) return cuda_fail(e, "global-path counting launch");
+  }
   return AFC_OK;
 }
 
 }  // namespace
+
+namespace afc {
+
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int counts_ranges(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
+                  const uint32_t *r_count, uint32_t *const *counts, afc_mc_stats *const *stats,
+                  void *workspace, size_t ws_bytes, cudaStream_t stream) {
+  if (nprob <= 0 || !probs || !r_count || !counts) return fail(AFC_EINVAL, "bad batch arguments");
+  return run_counts(nprob, probs, r_begin, r_count, counts, stats, nullptr, nullptr, workspace,
+                    ws_bytes, stream);
+}
+
+size_t counts_ranges_workspace(int nprob, const afc_mc_problem *probs, const uint32_t *r_count) {
+  return counts_ws_total(nprob, probs, r_count);
+}
+
+}  // namespace afc
 
 extern "C" {
 
@@ -270,7 +389,7 @@ uint64_t afc_survival_threshold(double p) {
 
 size_t afc_transition_counts_workspace(const afc_mc_problem *prob) {
   if (validate(prob)) return 0;
-  return plan_counts(1, prob, 1u << 20).ws_total;
+  return counts_ws_total(1, prob, nullptr);
 }
 
 int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count,
@@ -279,8 +398,9 @@ int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t
                           void *stream) {
   if (!prob) return fail(AFC_EINVAL, "null problem");
   uint32_t *cs[1] = {counts};
-  return run_counts(1, prob, &r_begin, &r_count, cs, stats, dump_bc, dump_next, workspace,
-                    workspace_bytes, (cudaStream_t)stream);
+  afc_mc_stats *sl[1] = {stats};
+  return run_counts(1, prob, &r_begin, &r_count, cs, stats ? sl : nullptr, dump_bc, dump_next,
+                    workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
 size_t afc_transition_counts_batched_workspace(int32_t nprob, const afc_mc_problem *probs,
@@ -290,7 +410,8 @@ size_t afc_transition_counts_batched_workspace(int32_t nprob, const afc_mc_probl
     if (validate(&probs[g])) return 0;
   uint64_t total = 0;
   for (int g = 0; g < nprob; ++g) total += r_count[g];
-  return plan_counts(nprob, probs, std::max<uint64_t>(total, 1)).ws_total;
+  (void)total;
+  return counts_ws_total(nprob, probs, r_count);
 }
 
 int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
@@ -298,8 +419,11 @@ int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
                                   afc_mc_stats *stats, void *workspace, size_t workspace_bytes,
                                   void *stream) {
   if (nprob <= 0 || !probs || !r_count || !counts) return fail(AFC_EINVAL, "bad batch arguments");
-  return run_counts(nprob, probs, nullptr, r_count, counts, stats, nullptr, nullptr, workspace,
-                    workspace_bytes, (cudaStream_t)stream);
+  std::vector<afc_mc_stats *> sl;
+  if (stats)
+    for (int g = 0; g < nprob; ++g) sl.push_back(stats + g);
+  return run_counts(nprob, probs, nullptr, r_count, counts, stats ? sl.data() : nullptr, nullptr,
+                    nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
 int afc_debug_realize(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count, uint8_t *alive,

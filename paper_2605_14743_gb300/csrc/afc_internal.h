@@ -44,7 +44,7 @@ struct McDev {
 constexpr int kMaxSlots = 64;          // sources in flight per CTA
 constexpr int kMaxTeams = 32;          // independent thread teams per CTA
 constexpr int kMaxSlotsPerTeam = 16;   // sources a team advances in lockstep
-constexpr int kRing = 12;              // bucket bitmaps per source (ring over pending distances)
+constexpr int kRing = 16;              // bucket bitmaps per source (ring over pending distances)
 
 struct SlotCtl {
   uint32_t s, nm, mstart, hi, lo, ring_mask, pad[2];
@@ -60,12 +60,45 @@ struct TeamCtl {
 struct CtaCtl {
   uint32_t err, ovf, nsrc, cursor;
   unsigned long long edges, verts;
-  uint32_t need_recheck, delta, ring_b, wmax;
+  uint32_t need_recheck, delta, dsh, wmax;
   uint32_t scan[32];
   uint32_t scan_total, pad1, pad2, pad3;
   SlotCtl slot[kMaxSlots];
   TeamCtl team[kMaxTeams];
 };
+
+// One realization in flight on the global-memory counting path.  The arrays are carved from
+// the caller's workspace by the host; the counters are (re)set by the preparation kernel.
+struct BigGroup {
+  uint32_t r_local;      // realization offset from the problem's r_begin
+  uint32_t active;       // 1 while the group holds a realization of the current batch
+  uint32_t nsrc, cursor, dsh, err, ovf, redo;
+  unsigned long long edges, verts;
+  uint32_t *rp, *arc, *comp, *cinfo, *bci, *centre, *rank;
+  uint16_t *src;
+  double *bc;
+  unsigned long long *best;
+};
+
+// bytes of one group's arrays and of one source slot (global path)
+size_t big_group_bytes(uint32_t n, uint64_t arcs);
+uint32_t big_slot_bytes(uint32_t n);
+void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs);
+bool big_config_supported(int block, int team);
+// Runs realizations [0, r_count) of the problem *Pd (device copy) through the global path in
+// batches of ngroups realizations.
+cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision,
+                             BigGroup *groups_d, uint32_t ngroups, uint32_t r_count,
+                             unsigned char *arena, size_t slot_stride, uint32_t spt,
+                             uint32_t grid, cudaStream_t stream);
+
+// abi.cu: counting over per-problem realization ranges (the batched launch of the serving
+// loop) and the thread-local error message of the C ABI
+int counts_ranges(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
+                  const uint32_t *r_count, uint32_t *const *counts, afc_mc_stats *const *stats,
+                  void *workspace, size_t ws_bytes, cudaStream_t stream);
+size_t counts_ranges_workspace(int nprob, const afc_mc_problem *probs, const uint32_t *r_count);
+int report_error(int code, const char *msg);
 
 // mc_kernel.cu
 uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots);

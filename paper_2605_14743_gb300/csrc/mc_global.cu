@@ -1,0 +1,257 @@
+// mc_global.cu -- Monte Carlo transition counts for graphs whose per-CTA state does not fit in
+// shared memory (sm_103a).
+//
+// The realizations of a problem are processed in batches of G ("groups").  Per batch:
+//   prep     one CTA per group: Philox edge draws -> alive-compacted CSR in device memory
+//            (A1), components and candidate flags (A2), the list of sources (nodes of valid
+//            components), zeroed betweenness accumulators
+//   brandes  a persistent grid; the teams of every CTA claim batches of sources of the G
+//            realizations from per-group cursors (group by group, so the realized graph being
+//            worked on stays hot in L2) and run the same bucketed Brandes routine as the
+//            shared-memory kernel (A3-A5), with their source slots in a per-CTA region of a
+//            device arena and betweenness accumulated with device-memory atomics
+//   select   one CTA per group: tie-ruled argmax and transition counts (A6); in FP32 mode a
+//            realization whose top-two gap is under the margin is flagged, its accumulators
+//            cleared, and a second brandes + select pair redoes exactly the flagged groups in
+//            FP64 (A7)
+// All launches are stream ordered; nothing waits on the host.
+#include "mc_common.cuh"
+
+namespace afc {
+
+namespace {
+
+constexpr int kPrepThreads = 1024;
+
+__global__ void __launch_bounds__(kPrepThreads, 1)
+big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uint32_t r_count) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
+  const McDev &P = *Pd;
+  BigGroup &G = groups[blockIdx.x];
+  const uint32_t r_local = r0 + blockIdx.x;
+  if (r_local >= r_count) {
+    if (threadIdx.x == 0) G.active = 0;
+    return;
+  }
+  const uint32_t n = (uint32_t)P.n;
+  if (threadIdx.x == 0) {
+    ctl->err = 0; ctl->wmax = 1; ctl->edges = 0; ctl->verts = 0; ctl->nsrc = 0;
+  }
+  __syncthreads();
+  realize_csr(P, P.r_begin + r_local, G.rp, G.arc, ctl);
+  Realized H{n, G.rp, G.arc};
+  components(P, H, G.comp, G.cinfo);
+  bucket_setup(ctl, P.delta);
+  uint32_t *cedges = G.centre;   // scratch until selection
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+    cedges[v] = 0; G.bc[v] = 0.0; G.bci[v] = 0;
+  }
+  __syncthreads();
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const uint32_t root = G.comp[v];
+    if (!comp_valid(G.cinfo[root], P.k_min)) continue;
+    uint32_t up = 0;
+    for (uint32_t e = G.rp[v]; e < G.rp[v + 1]; ++e) up += ((G.arc[e] & 0xFFFFu) > v) ? 1u : 0u;
+    if (up) atomicAdd(&cedges[root], up);
+  }
+  {
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t v0 = min(n, threadIdx.x * per), v1 = min(n, v0 + per);
+    uint32_t cnt = 0;
+    for (uint32_t v = v0; v < v1; ++v) cnt += comp_valid(G.cinfo[G.comp[v]], P.k_min) ? 1u : 0u;
+    uint32_t off = block_exclusive_scan(cnt, ctl->scan, &ctl->scan_total);
+    for (uint32_t v = v0; v < v1; ++v)
+      if (comp_valid(G.cinfo[G.comp[v]], P.k_min)) G.src[off++] = (uint16_t)v;
+    if (threadIdx.x == 0) ctl->nsrc = ctl->scan_total;
+  }
+  __syncthreads();
+  {
+    unsigned long long local = 0, lv = 0;
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x)
+      if (G.comp[v] == v && comp_valid(G.cinfo[v], P.k_min)) {
+        const unsigned long long sz = G.cinfo[v] & kSizeMask;
+        local += sz * cedges[v];
+        lv += sz * sz;
+      }
+    if (local) atomicAdd(&ctl->edges, local);
+    if (lv) atomicAdd(&ctl->verts, lv);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    G.r_local = r_local;
+    G.nsrc = ctl->nsrc;
+    G.cursor = 0;
+    G.dsh = ctl->dsh;
+    G.err = ctl->err;
+    G.ovf = 0;
+    G.redo = 0;
+    G.edges = ctl->edges;
+    G.verts = ctl->verts;
+    G.active = 1;
+  }
+}
+
+// mode 0: FP64, every active group.  1: FP32, every active group.  2: FP64, groups flagged
+// for a recheck only.
+template <int BLOCK, int TS>
+__global__ void __launch_bounds__(BLOCK, 1)
+big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngroups,
+                   unsigned char *arena, size_t slot_stride, uint32_t spt, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr uint32_t NT = BLOCK / TS;
+  CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
+  const uint32_t n = (uint32_t)Pd->n;
+  Team<TS, BLOCK> team;
+  team.id = threadIdx.x / TS;
+  team.rank = threadIdx.x % TS;
+  team.tc = &ctl->team[team.id];
+  const uint32_t nslots = NT * spt;
+  const SlotSpace sp{arena + (size_t)blockIdx.x * nslots * slot_stride, slot_stride, n,
+                     (n + 31u) / 32u};
+  for (uint32_t g = 0; g < ngroups; ++g) {
+    BigGroup &G = groups[g];
+    if (!G.active || (mode == 2 && !G.redo)) continue;
+    const Realized H{n, G.rp, G.arc};
+    const uint32_t nsrc = G.nsrc, dsh = G.dsh;
+    for (;;) {
+      if (team.rank == 0) team.tc->claim = atomicAdd(&G.cursor, spt);
+      team.sync();
+      const uint32_t k0 = team.tc->claim;
+      team.sync();
+      if (k0 >= nsrc) break;
+      const uint32_t S = min(spt, nsrc - k0);
+      if (mode == 1)
+        brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, G.src + k0, dsh, G.bc,
+                                        G.bci, true, ctl, &G.err, &G.ovf);
+      else
+        brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, G.src + k0, dsh, G.bc,
+                                         G.bci, true, ctl, &G.err, &G.ovf);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPrepThreads, 1)
+big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, int redo_only) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
+  const McDev &P = *Pd;
+  BigGroup &G = groups[blockIdx.x];
+  if (!G.active || (redo_only && !G.redo)) return;
+  const uint32_t n = (uint32_t)P.n;
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) G.bc[v] += (double)G.bci[v];
+  __syncthreads();
+  SlotArrays s0{};
+  s0.sig = reinterpret_cast<uint64_t *>(G.best);
+  s0.dist = G.centre;
+  const bool recheck =
+      select_and_count(P, G.r_local, G.comp, G.cinfo, G.bc, s0, G.rank, gap_test != 0, ctl);
+  __syncthreads();
+  if (recheck) {
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { G.bc[v] = 0.0; G.bci[v] = 0; }
+    if (threadIdx.x == 0) {
+      G.redo = 1;
+      G.cursor = 0;
+      if (P.stats) atomicAdd(u64p(&P.stats->rechecked), 1ull);
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    G.redo = 0;
+    if (P.stats) {
+      if (G.err) atomicOr(u64p(&P.stats->device_error), (unsigned long long)G.err);
+      atomicAdd(u64p(&P.stats->realizations), 1ull);
+      atomicAdd(u64p(&P.stats->sources), (unsigned long long)G.nsrc);
+      atomicAdd(u64p(&P.stats->edge_visits), G.edges);
+      atomicAdd(u64p(&P.stats->vertex_visits), G.verts);
+      if (G.ovf) atomicAdd(u64p(&P.stats->overflow), 1ull);
+    }
+  }
+}
+
+template <int BLOCK, int TS>
+cudaError_t launch_brandes_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups,
+                             unsigned char *arena, size_t stride, uint32_t spt, int mode,
+                             uint32_t grid, cudaStream_t stream) {
+  big_brandes_kernel<BLOCK, TS><<<grid, BLOCK, sizeof(CtaCtl), stream>>>(Pd, groups, ngroups,
+                                                                         arena, stride, spt, mode);
+  return cudaGetLastError();
+}
+
+// (block, team) pairs of the global path
+#define AFC_BIG_CONFIGS(X) \
+  X(256, 64) X(256, 128) X(256, 256) X(512, 128) X(512, 256) X(512, 512) \
+  X(1024, 128) X(1024, 256) X(1024, 1024)
+
+cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *groups,
+                           uint32_t ngroups, unsigned char *arena, size_t stride, uint32_t spt,
+                           int mode, uint32_t grid, cudaStream_t stream) {
+#define AFC_X(B, T)                                                                        \
+  if (block == B && team == T)                                                             \
+    return launch_brandes_t<B, T>(Pd, groups, ngroups, arena, stride, spt, mode, grid, stream);
+  AFC_BIG_CONFIGS(AFC_X)
+#undef AFC_X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool big_config_supported(int block, int team) {
+#define AFC_X(B, T) if (block == B && team == T) return true;
+  AFC_BIG_CONFIGS(AFC_X)
+#undef AFC_X
+  return false;
+}
+
+static size_t al256(size_t x) { return (x + 255u) & ~size_t(255); }
+
+size_t big_group_bytes(uint32_t n, uint64_t arcs) {
+  return al256(4ull * (n + 1)) + al256(4ull * (arcs > 0 ? arcs : 1)) + 5 * al256(4ull * n) +
+         al256(2ull * n) + 2 * al256(8ull * n);
+}
+
+uint32_t big_slot_bytes(uint32_t n) { return (slot_bytes_for(n) + 255u) & ~255u; }
+
+void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs) {
+  unsigned char *p = base;
+  auto take = [&](size_t bytes) { unsigned char *q = p; p += al256(bytes); return q; };
+  G = BigGroup{};
+  G.rp = reinterpret_cast<uint32_t *>(take(4ull * (n + 1)));
+  G.arc = reinterpret_cast<uint32_t *>(take(4ull * (arcs > 0 ? arcs : 1)));
+  G.comp = reinterpret_cast<uint32_t *>(take(4ull * n));
+  G.cinfo = reinterpret_cast<uint32_t *>(take(4ull * n));
+  G.bci = reinterpret_cast<uint32_t *>(take(4ull * n));
+  G.centre = reinterpret_cast<uint32_t *>(take(4ull * n));
+  G.rank = reinterpret_cast<uint32_t *>(take(4ull * n));
+  G.src = reinterpret_cast<uint16_t *>(take(2ull * n));
+  G.bc = reinterpret_cast<double *>(take(8ull * n));
+  G.best = reinterpret_cast<unsigned long long *>(take(8ull * n));
+}
+
+cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision,
+                             BigGroup *groups_d, uint32_t ngroups, uint32_t r_count,
+                             unsigned char *arena, size_t slot_stride, uint32_t spt,
+                             uint32_t grid, cudaStream_t stream) {
+  if (!big_config_supported(block, team)) return cudaErrorInvalidValue;
+  const bool fp32 = (precision == 1);
+  for (uint32_t r0 = 0; r0 < r_count; r0 += ngroups) {
+    big_prep_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, r0, r_count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, fp32 ? 1 : 0,
+                       grid, stream);
+    if (e != cudaSuccess) return e;
+    big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, fp32 ? 1 : 0, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (fp32) {
+      e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, 2, grid,
+                         stream);
+      if (e != cudaSuccess) return e;
+      big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, 0, 1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace afc

@@ -13,692 +13,9 @@
 //       and the transition-count update of every anchor (Alg. 1 / Alg. 2)
 //   A7  FP32 mode: a realization whose top-two gap is under the margin is redone in FP64
 //
-// Per source ("slot") state: dist[n] (u32 distance | flag), sig[n] (u64: last relaxed
-// distance while tentative, then sigma, then rho = (1 + delta) / sigma in the same slot),
-// ord[n] (u16 settled vertices grouped by bucket) and a ring of kRing bucket bitmaps that
-// holds the discovered-but-unsettled vertices by bucket.
-#include <cstdint>
-#include <cuda_runtime.h>
-
-#include "afc_device.cuh"
-#include "afc_internal.h"
+#include "mc_common.cuh"
 
 namespace afc {
-
-__device__ __forceinline__ unsigned long long *u64p(uint64_t *p) {
-  return reinterpret_cast<unsigned long long *>(p);
-}
-
-constexpr uint32_t kInf = 0x7FFFFFFFu;    // unreached distance
-constexpr uint32_t kFlag = 0x80000000u;   // "sigma final" (forward) / "delta pending" (backward)
-constexpr uint32_t kMask = 0x7FFFFFFFu;
-constexpr uint64_t kNoRelax = ~0ull;
-constexpr uint64_t kIntTag = 0x8000000000000000ull;   // rho stored as an exact integer
-
-__device__ __forceinline__ uint32_t ld_volatile(const uint32_t *p) {
-  return *reinterpret_cast<const volatile uint32_t *>(p);
-}
-__device__ __forceinline__ void st_volatile(uint32_t *p, uint32_t v) {
-  *reinterpret_cast<volatile uint32_t *>(p) = v;
-}
-
-// Shared-memory layout of one CTA for a graph of n nodes, `arcs` arcs and S source slots.
-struct Layout {
-  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_bci, off_src, off_sel, off_slots;
-  uint32_t slot_bytes, words, total;
-  __host__ __device__ static uint32_t al(uint32_t x) { return (x + 15u) & ~15u; }
-  __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t nslots) {
-    words = (n + 31u) / 32u;
-    uint32_t o = al(sizeof(CtaCtl));
-    off_rp = o;     o = al(o + 4u * (n + 1));
-    off_arc = o;    o = al(o + 4u * (arcs > 0 ? arcs : 1));
-    off_comp = o;   o = al(o + 4u * n);
-    off_cinfo = o;  o = al(o + 4u * n);
-    off_bc = o;     o = al(o + 8u * n);
-    off_bci = o;    o = al(o + 4u * n);
-    off_src = o;    o = al(o + 2u * (n > nslots ? n : nslots));
-    off_sel = o;    o = al(o + 4u * n);
-    off_slots = o;
-    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n) + al(4u * kRing * words);
-    total = o + nslots * slot_bytes;
-  }
-};
-
-struct SlotArrays {
-  uint32_t *dist;
-  uint64_t *sig;
-  uint16_t *ord;
-  uint32_t *ring;   // [kRing][words]
-};
-
-__device__ __forceinline__ SlotArrays slot_arrays(unsigned char *smem, const Layout &L, uint32_t n,
-                                                  uint32_t i) {
-  unsigned char *p = smem + L.off_slots + i * L.slot_bytes;
-  SlotArrays a;
-  a.dist = reinterpret_cast<uint32_t *>(p);  p += Layout::al(4u * n);
-  a.sig = reinterpret_cast<uint64_t *>(p);   p += Layout::al(8u * n);
-  a.ord = reinterpret_cast<uint16_t *>(p);   p += Layout::al(2u * n);
-  a.ring = reinterpret_cast<uint32_t *>(p);
-  return a;
-}
-
-struct Realized {
-  uint32_t n;
-  const uint32_t *rp;    // [n+1] alive-compacted row offsets
-  const uint32_t *arc;   // packed: neighbour (low 16 bits) | length << 16
-};
-
-// A team of TS threads (whole warps) of a BLOCK-thread CTA that advances its own subset of
-// source slots in lockstep.  TS == 32: warp-synchronous; TS == BLOCK: CTA barriers; otherwise
-// named barrier (team + 1) with bar.red for the OR reductions.
-template <int TS, int BLOCK>
-struct Team {
-  uint32_t id, rank;
-  TeamCtl *tc;
-  __device__ __forceinline__ void sync() const {
-    if constexpr (TS == 32) {
-      __syncwarp();
-    } else if constexpr (TS == BLOCK) {
-      __syncthreads();
-    } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "n"(TS) : "memory");
-    }
-  }
-  __device__ __forceinline__ bool any(bool p) const {
-    if constexpr (TS == 32) {
-      return __any_sync(kFull, p);
-    } else if constexpr (TS == BLOCK) {
-      return __syncthreads_or(p) != 0;
-    } else {
-      uint32_t r;
-      asm volatile(
-          "{ .reg .pred pa, pb;\n"
-          "  setp.ne.u32 pa, %1, 0;\n"
-          "  bar.red.or.pred pb, %2, %3, pa;\n"
-          "  selp.u32 %0, 1, 0, pb; }"
-          : "=r"(r)
-          : "r"((uint32_t)p), "r"(id + 1), "n"(TS)
-          : "memory");
-      return r != 0;
-    }
-  }
-};
-
-// Exclusive prefix of per-slot counts into tc->pref[0..S] (S <= 32); team's first warp only.
-template <typename F>
-__device__ __forceinline__ void slot_prefix(TeamCtl *tc, uint32_t rank, uint32_t S, F count) {
-  if (rank >= 32) return;
-  const uint32_t x = rank < S ? count(rank) : 0u;
-  uint32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, inc, o);
-    if (rank >= (uint32_t)o) inc += y;
-  }
-  if (rank < S) tc->pref[rank] = inc - x;
-  if (rank == 31) tc->pref[S] = inc;
-}
-
-// Largest slot i with pref[i] <= k (pref ascending, pref[S] = total > k).
-__device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, uint32_t k) {
-  uint32_t lo = 0, hi = S;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (pref[mid] <= k) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// ---------------------------------------------------------------------------------------
-// A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) advanced in lockstep by
-// one team.  Adds delta_s(v) to bc[v] for v != s.  With want_delta = false it stops after
-// distances and path counts (parity hook).  Every thread of the team must call it.
-// ---------------------------------------------------------------------------------------
-template <int TS, int BLOCK, typename DT>
-__device__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H, unsigned char *smem,
-                              const Layout &L, uint32_t slot0, uint32_t S, const uint16_t *srcs,
-                              uint32_t delta, uint32_t ringB, double *bc, uint32_t *bci,
-                              bool want_delta, CtaCtl *ctl) {
-  const uint32_t n = H.n, W = L.words;
-  const uint32_t tid = team.rank;
-  TeamCtl *tc = team.tc;
-  SlotCtl *sl = ctl->slot + slot0;
-  uint32_t my_err = 0, my_ovf = 0;
-  const uint32_t lane = tid & 31u, warp = tid >> 5;
-  constexpr uint32_t NW = TS / 32;
-
-  // ---- init
-  for (uint32_t t = tid; t < S * n; t += TS) {
-    const uint32_t i = t / n;
-    slot_arrays(smem, L, n, slot0 + i).dist[t - i * n] = kInf;
-  }
-  for (uint32_t t = tid; t < S * kRing * W; t += TS) {
-    const uint32_t i = t / (kRing * W);
-    slot_arrays(smem, L, n, slot0 + i).ring[t - i * kRing * W] = 0u;
-  }
-  team.sync();
-  for (uint32_t i = tid; i < S; i += TS) {
-    SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-    const uint32_t s = srcs[i];
-    SlotCtl &sc = sl[i];
-    sc.s = s;
-    sc.nm = 0; sc.mstart = 0; sc.hi = 0; sc.lo = 0;
-    sc.ring_mask = 1u;            // ring_mask: bucket 0 holds the source
-    a.dist[s] = 0;
-    a.ring[s >> 5] = 1u << (s & 31u);
-  }
-  team.sync();
-
-  // ---- forward: buckets in increasing order
-  bool ok = true;
-  uint32_t b = 0;
-  for (uint32_t guard = 0;; ++guard) {
-    if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
-    if (tid < 32) {
-      // first ring offset k (bucket b + k) holding discovered vertices in any slot
-      uint32_t m = tid < S ? sl[tid].ring_mask : 0u;
-      m = __reduce_or_sync(kFull, m);
-      uint32_t rot = 0;   // bit k <-> ring slot (b + k) % ringB
-      for (uint32_t k = 0; k < ringB; ++k) rot |= ((m >> ((b + k) % ringB)) & 1u) << k;
-      if (tid == 0) tc->bucket = rot ? b + (uint32_t)(__ffs(rot) - 1) : 0xFFFFFFFFu;
-    }
-    team.sync();
-    if (tc->bucket == 0xFFFFFFFFu) break;
-    b = tc->bucket;
-    const uint32_t rs = b % ringB;
-    const uint32_t dend = (b + 1u) * delta;
-    // extraction of bucket b into the member lists, appends aggregated per warp and slot
-    for (uint32_t base = warp * 32u; base < S * W; base += TS) {
-      const uint32_t item = base + lane;
-      uint32_t i = 0xFFFFu, live = 0;
-      uint16_t vb = 0;
-      if (item < S * W) {
-        i = item / W;
-        const uint32_t w = item - i * W;
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        uint32_t word = a.ring[rs * W + w];
-        if (word) {
-          a.ring[rs * W + w] = 0u;
-          while (word) {
-            const uint32_t j = __ffs(word) - 1;
-            word &= word - 1u;
-            const uint32_t d = a.dist[w * 32u + j];
-            if (!(d & kFlag) && d < dend) live |= 1u << j;   // else settled (stale bit)
-          }
-        }
-        vb = (uint16_t)(w * 32u);
-      }
-      const uint32_t cnt = __popc(live);
-      uint32_t inc = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
-      }
-      const uint32_t peers = __match_any_sync(kFull, i);
-      const uint32_t leader = __ffs(peers) - 1, last = 31 - __clz(peers);
-      const uint32_t before = __shfl_sync(kFull, inc, leader == 0 ? 0 : leader - 1);
-      const uint32_t gbase = leader == 0 ? 0u : before;
-      const uint32_t gtotal = __shfl_sync(kFull, inc, last) - gbase;
-      uint32_t pos0 = 0;
-      if (lane == leader && i != 0xFFFFu && gtotal) pos0 = atomicAdd(&sl[i].nm, gtotal);
-      pos0 = __shfl_sync(kFull, pos0, leader);
-      if (live) {
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        uint32_t pos = pos0 + inc - cnt - gbase;
-        while (live) {
-          const uint32_t j = __ffs(live) - 1;
-          live &= live - 1u;
-          const uint32_t v = (uint32_t)vb + j;
-          if (pos < n) { a.ord[pos] = (uint16_t)v; a.sig[v] = kNoRelax; }
-          else my_err |= kErrCapacity;
-          ++pos;
-        }
-      }
-    }
-    for (uint32_t i = tid; i < S; i += TS) sl[i].ring_mask &= ~(1u << rs);
-    team.sync();
-    // relaxation passes until no member of the bucket improves
-    for (uint32_t pass = 0;; ++pass) {
-      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-      slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
-      team.sync();
-      const uint32_t total = tc->pref[S];
-      bool improved = false;
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-        if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t d = a.dist[v];
-        if ((uint64_t)d == a.sig[v]) continue;
-        a.sig[v] = d;
-        const uint32_t e1 = H.rp[v + 1];
-        for (uint32_t e = H.rp[v]; e < e1; ++e) {
-          const uint32_t pk = H.arc[e];
-          const uint32_t u = pk & 0xFFFFu;
-          const uint32_t nd = d + (pk >> 16);
-          const uint32_t cur = a.dist[u];
-          if ((cur & kFlag) || nd >= cur) continue;
-          const uint32_t old = atomicMin(&a.dist[u], nd);
-          if (nd >= old) continue;
-          if (nd < dend) {
-            improved = true;
-            if (old >= dend) {
-              const uint32_t pos = warp_append_keyed(&sl[i].nm, i);
-              if (pos < n) { a.ord[pos] = (uint16_t)u; a.sig[u] = kNoRelax; }
-              else my_err |= kErrCapacity;
-            }
-          } else {
-            const uint32_t r2 = (nd / delta) % ringB;
-            const uint32_t bit = 1u << (u & 31u);
-            const uint32_t prev = atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
-            if (!(prev & bit) && !(sl[i].ring_mask & (1u << r2))) atomicOr(&sl[i].ring_mask, 1u << r2);
-          }
-        }
-      }
-      if (!team.any(improved)) break;
-    }
-    if (!ok) break;
-    // path counts of the bucket.  A member is final once all its predecessors are (earlier
-    // buckets are); it then publishes sigma before its flag (fence), and a reader that sees
-    // the flag of a same-bucket predecessor fences before reading that sigma.
-    slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
-    team.sync();
-    const uint32_t total = tc->pref[S];
-    const uint32_t dstart = b * delta;
-    for (uint32_t pass = 0;; ++pass) {
-      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-      bool open = false;
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-        if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t dv = a.dist[v];
-        if (dv & kFlag) continue;
-        uint64_t acc = 0;
-        bool all_final = true;
-        if (v == sl[i].s) {
-          acc = 1;
-        } else {
-          const uint32_t e1 = H.rp[v + 1];
-          for (uint32_t e = H.rp[v]; e < e1; ++e) {
-            const uint32_t pk = H.arc[e];
-            const uint32_t u = pk & 0xFFFFu;
-            const uint32_t du = a.dist[u];
-            if ((du & kMask) + (pk >> 16) != dv) continue;
-            if (!(du & kFlag)) { all_final = false; break; }
-            if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
-            const uint64_t nx = acc + a.sig[u];
-            if (nx < acc) my_ovf = 1;
-            acc = nx;
-          }
-        }
-        if (all_final) {
-          a.sig[v] = acc;
-          __threadfence_block();
-          st_volatile(&a.dist[v], dv | kFlag);
-        } else {
-          open = true;
-        }
-      }
-      if (!team.any(open)) break;
-    }
-    if (!ok) break;
-    for (uint32_t i = tid; i < S; i += TS) sl[i].mstart = min(sl[i].nm, n);
-    team.sync();
-    b += 1;
-  }
-  if (!ok) {
-    if (my_err) atomicOr(&ctl->err, my_err);
-    team.sync();
-    return false;
-  }
-
-  // ---- backward: dependencies, buckets in decreasing order; kFlag = "delta pending"
-  if (want_delta) {
-    for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].mstart;
-    team.sync();
-    for (uint32_t guard = 0;; ++guard) {
-      if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
-      if (tid < 32) {
-        uint32_t best = 0;  // 1 + bucket id of the last unprocessed member, 0 if none
-        if (lane < S) {
-          const uint32_t hi = sl[lane].hi;
-          if (hi > 0) {
-            SlotArrays a = slot_arrays(smem, L, n, slot0 + lane);
-            const uint32_t v = a.ord[hi - 1];
-            best = v < n ? (a.dist[v] & kMask) / delta + 1u : 1u;
-          }
-        }
-        best = __reduce_max_sync(kFull, best);
-        if (lane == 0) tc->bucket = best;
-      }
-      team.sync();
-      const uint32_t bb = tc->bucket;
-      if (bb == 0) break;
-      const uint32_t bcur = bb - 1u;
-      // per slot: start of the run of bucket bcur at the end of its settled list
-      for (uint32_t i = warp; i < S; i += NW) {
-        SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-        const uint32_t hi = sl[i].hi;
-        uint32_t lo = hi;
-        const uint32_t vh = hi > 0 ? a.ord[hi - 1] : 0u;
-        if (hi > 0 && vh < n && (a.dist[vh] & kMask) / delta == bcur) {
-          lo = 0;
-          for (uint32_t top = hi; top > 0;) {
-            const uint32_t base = top > 32u ? top - 32u : 0u;
-            const uint32_t p = base + lane;
-            uint32_t cand = 0;
-            if (p < top) {
-              const uint32_t vp = a.ord[p];
-              if (vp >= n || (a.dist[vp] & kMask) / delta != bcur) cand = p + 1u;
-            }
-            const uint32_t found = __reduce_max_sync(kFull, cand);
-            if (found > 0) { lo = found; break; }
-            top = base;
-          }
-        }
-        if (lane == 0) sl[i].lo = lo;
-      }
-      team.sync();
-      slot_prefix(tc, tid, S, [&](uint32_t i) { return sl[i].hi - sl[i].lo; });
-      team.sync();
-      const uint32_t total = tc->pref[S];
-      const uint32_t dlo = bcur * delta, dhi = dlo + delta;
-      for (uint32_t pass = 0;; ++pass) {
-        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-        bool open = false;
-        for (uint32_t k = tid; k < total; k += TS) {
-          const uint32_t i = find_slot(tc->pref, S, k);
-          SlotArrays a = slot_arrays(smem, L, n, slot0 + i);
-          const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
-          if (v >= n) { my_err |= kErrCapacity; continue; }
-          const uint32_t dv = a.dist[v];
-          if (!(dv & kFlag)) continue;
-          const uint32_t dvm = dv & kMask;
-          uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
-          DT acc_f = 0;           // sum of the other rho
-          bool integral = true, all_final = true;
-          const uint32_t e1 = H.rp[v + 1];
-          for (uint32_t e = H.rp[v]; e < e1; ++e) {
-            const uint32_t pk = H.arc[e];
-            const uint32_t w = pk & 0xFFFFu;
-            const uint32_t dw = a.dist[w];
-            if ((dw & kMask) != dvm + (pk >> 16)) continue;
-            if (dw & kFlag) { all_final = false; break; }
-            if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
-            const uint64_t rw = a.sig[w];
-            if (rw & kIntTag) {
-              acc_i += (uint32_t)rw;
-            } else {
-              acc_f += *reinterpret_cast<const DT *>(&rw);
-              integral = false;
-            }
-          }
-          if (!all_final) { open = true; continue; }
-          const uint64_t sg = a.sig[v];
-          const bool is_src = (v == sl[i].s);
-          if (sg == 1ull && integral) {
-            // delta(v) = sum of the successors' subtree sizes: exact in integers
-            a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-            if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
-          } else {
-            const DT acc = (DT)acc_i + acc_f;
-            DT dep, rho;
-            if (sg == 1ull) {
-              dep = acc;
-              rho = (DT)1 + dep;
-            } else {
-              const DT sv = (DT)sg;
-              dep = sv * acc;
-              rho = ((DT)1 + dep) / sv;
-            }
-            uint64_t bits = 0;
-            *reinterpret_cast<DT *>(&bits) = rho;
-            a.sig[v] = bits;
-            if (!is_src) atomicAdd(&bc[v], (double)dep);
-          }
-          __threadfence_block();
-          st_volatile(&a.dist[v], dvm);
-        }
-        if (!team.any(open)) break;
-      }
-      if (!ok) break;
-      for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].lo;
-      team.sync();
-    }
-  }
-  if (my_err) atomicOr(&ctl->err, my_err);
-  if (my_ovf) atomicOr(&ctl->ovf, 1u);
-  team.sync();
-  return ok;
-}
-
-// ---------------------------------------------------------------------------------------
-// CTA-wide pieces: realization (A1), components (A2)
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *tmp,
-                                                         uint32_t *total) {
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t nw = (blockDim.x + 31u) >> 5;
-  uint32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, inc, o);
-    if (lane >= (uint32_t)o) inc += y;
-  }
-  if (lane == 31) tmp[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t wv = lane < nw ? tmp[lane] : 0u;
-    uint32_t wi = wv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, wi, o);
-      if (lane >= (uint32_t)o) wi += y;
-    }
-    if (lane < nw) tmp[lane] = wi - wv;
-    if (lane == nw - 1) *total = wi;
-  }
-  __syncthreads();
-  const uint32_t r = tmp[warp] + inc - x;
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ void edge_draw(const McDev &P, uint32_t r, uint32_t e, bool &alive,
-                                          uint32_t &w) {
-  const uint4 u = philox4x32_10(make_uint4(e, r, P.graph_tag, 0u), P.key_lo, P.key_hi);
-  const uint64_t T = P.thresh ? P.thresh[e] : P.thresh_all;
-  const uint32_t lo = P.w_lo ? P.w_lo[e] : P.w_lo_all;
-  const uint32_t hi = P.w_hi ? P.w_hi[e] : P.w_hi_all;
-  alive = (uint64_t)u.x < T;
-  w = lo + (uint32_t)(((uint64_t)u.y * ((uint64_t)hi - lo + 1u)) >> 32);
-}
-
-// Builds the alive-compacted CSR of realization r into rp/arc (thread per contiguous vertex
-// range, offsets from one block scan) and the largest alive length into ctl->wmax.
-__device__ void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uint32_t *arc,
-                            CtaCtl *ctl) {
-  const uint32_t n = P.n;
-  const uint32_t cap = (uint32_t)(2 * P.m);   // arc slots reserved in the layout
-  const uint32_t T = blockDim.x;
-  const uint32_t per = (n + T - 1) / T;
-  const uint32_t v0 = min(n, threadIdx.x * per), v1 = min(n, v0 + per);
-  uint32_t cnt = 0;
-  for (uint32_t v = v0; v < v1; ++v) {
-    const int32_t a0 = P.row_ptr[v], a1 = P.row_ptr[v + 1];
-    for (int32_t a = a0; a < a1; ++a) {
-      const uint32_t e = (uint32_t)P.eid[a];
-      if (e >= (uint64_t)P.m) continue;
-      bool alive; uint32_t w;
-      edge_draw(P, r, e, alive, w);
-      cnt += alive ? 1u : 0u;
-    }
-  }
-  uint32_t off = block_exclusive_scan(cnt, ctl->scan, &ctl->scan_total);
-  uint32_t wmax = 1, err = 0;
-  for (uint32_t v = v0; v < v1; ++v) {
-    rp[v] = off;
-    const int32_t a0 = P.row_ptr[v], a1 = P.row_ptr[v + 1];
-    for (int32_t a = a0; a < a1; ++a) {
-      const uint32_t e = (uint32_t)P.eid[a];
-      const uint32_t u = (uint32_t)P.col[a];
-      if (e >= (uint64_t)P.m || u >= n) { err = kErrInput; continue; }
-      bool alive; uint32_t w;
-      edge_draw(P, r, e, alive, w);
-      if (!alive) continue;
-      if (w == 0 || w > 0xFFFFu || off >= cap) { err = kErrInput; continue; }
-      arc[off++] = u | (w << 16);
-      wmax = max(wmax, w);
-    }
-  }
-  if (err) atomicOr(&ctl->err, err);
-  wmax = __reduce_max_sync(kFull, wmax);
-  if ((threadIdx.x & 31u) == 0) atomicMax(&ctl->wmax, wmax);
-  const uint32_t total = ctl->scan_total;
-  if (threadIdx.x == 0) rp[n] = total < cap ? total : cap;
-  __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t uf_find(const uint32_t *parent, uint32_t x) {
-  uint32_t p = parent[x];
-  while (p != x) {
-    x = p;
-    p = parent[x];
-  }
-  return x;
-}
-
-// comp[v] <- smallest id of v's component; cinfo[root] <- size | has-candidate bit.
-__device__ void components(const McDev &P, const Realized &H, uint32_t *comp, uint32_t *cinfo) {
-  const uint32_t n = H.n;
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { comp[v] = v; cinfo[v] = 0; }
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    for (uint32_t e = H.rp[v]; e < H.rp[v + 1]; ++e) {
-      const uint32_t u = H.arc[e] & 0xFFFFu;
-      if (u <= v) continue;
-      uint32_t a = v, b = u;
-      for (;;) {
-        a = uf_find(comp, a);
-        b = uf_find(comp, b);
-        if (a == b) break;
-        if (a > b) { const uint32_t t = a; a = b; b = t; }
-        if (atomicCAS(&comp[b], b, a) == b) break;  // hook the larger root under the smaller
-      }
-    }
-  }
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) comp[v] = uf_find(comp, v);
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const uint32_t root = comp[v];
-    const bool cand = (P.in_w == nullptr) || P.in_w[v];
-    atomicAdd(&cinfo[root], 1u);
-    if (cand) atomicOr(&cinfo[root], kHasCand);
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ bool comp_valid(uint32_t info, uint32_t k_min) {
-  return (info & kHasCand) && (info & kSizeMask) >= k_min;
-}
-
-// Effective bucket width: at least ceil(wmax / (kRing - 2)) so that all discovered distances
-// beyond the current bucket fit into the ring of bucket bitmaps.
-__device__ __forceinline__ void bucket_setup(CtaCtl *ctl, uint32_t delta_req) {
-  if (threadIdx.x == 0) {
-    const uint32_t wmax = ctl->wmax;
-    const uint32_t dmin = (wmax + (kRing - 2) - 1) / (kRing - 2);
-    const uint32_t delta = max(max(delta_req, 1u), dmin);
-    ctl->delta = delta;
-    ctl->ring_b = min((uint32_t)kRing, (wmax + delta - 1) / delta + 2u);
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------------------
-// Select (A6) and count.  Scratch: slot 0's sig (u64 per root), slot 0's dist (centre per
-// root), the layout's sel array (rank per root).  Returns true when the FP32 gap test asks
-// for an FP64 recheck (then nothing is committed).
-// ---------------------------------------------------------------------------------------
-__device__ bool select_and_count(const McDev &P, uint32_t r_local, const uint32_t *comp,
-                                 const uint32_t *cinfo, const double *bc, SlotArrays s0,
-                                 uint32_t *rank, bool gap_test, CtaCtl *ctl) {
-  const uint32_t n = P.n;
-  unsigned long long *best = reinterpret_cast<unsigned long long *>(s0.sig);
-  uint32_t *centre = s0.dist;
-  if (threadIdx.x == 0) ctl->need_recheck = 0;
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    best[v] = 0ull; centre[v] = 0xFFFFFFFFu; rank[v] = 1u;
-  }
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const uint32_t root = comp[v];
-    if (!comp_valid(cinfo[root], P.k_min)) continue;
-    if (P.in_w == nullptr || P.in_w[v])
-      atomicMax(&best[root], (unsigned long long)__double_as_longlong(bc[v]));
-  }
-  __syncthreads();
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const uint32_t root = comp[v];
-    if (!comp_valid(cinfo[root], P.k_min)) continue;
-    if (!(P.in_w == nullptr || P.in_w[v])) continue;
-    const double bstar = __longlong_as_double((long long)best[root]);
-    if (bc[v] >= bstar - P.tie_rel * bstar) atomicMin(&centre[root], v);
-  }
-  __syncthreads();
-  if (P.top_k || gap_test) {
-    if (P.top_k) {   // best now becomes the maximum over the whole component
-      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) best[v] = 0ull;
-      __syncthreads();
-      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-        const uint32_t root = comp[v];
-        if (comp_valid(cinfo[root], P.k_min))
-          atomicMax(&best[root], (unsigned long long)__double_as_longlong(bc[v]));
-      }
-      __syncthreads();
-    }
-    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-      const uint32_t root = comp[v];
-      if (!comp_valid(cinfo[root], P.k_min)) continue;
-      const uint32_t c = centre[root];
-      if (c == v || c >= n) continue;
-      if (P.top_k) {
-        const double tauK = P.tie_rel * __longlong_as_double((long long)best[root]);
-        const double diff = bc[v] - bc[c];
-        if (diff > tauK || (fabs(diff) <= tauK && v < c)) atomicAdd(&rank[root], 1u);
-      }
-      if (gap_test && (P.top_k || P.in_w == nullptr || P.in_w[v])) {
-        // top-two gap of the candidate set (of the whole component when a rank cutoff is
-        // active): another node within the margin of B1 sends the realization to FP64
-        const double b1 = bc[c];
-        if (b1 > 0.0 && fabs(b1 - bc[v]) < P.recheck_margin * b1) ctl->need_recheck = 1;
-      }
-    }
-    __syncthreads();
-  }
-  if (gap_test && ctl->need_recheck) return true;
-  uint32_t *counts = P.counts;
-  const size_t stride = (size_t)n + 1;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint32_t root = comp[i];
-    uint32_t col = n;
-    if (comp_valid(cinfo[root], P.k_min)) {
-      const uint32_t c = centre[root];
-      if (c < n && (P.top_k == 0 || rank[root] <= P.top_k)) col = c;
-    }
-    atomicAdd(&counts[(size_t)i * stride + col], 1u);
-    if (P.dump_next) P.dump_next[(size_t)r_local * n + i] = (int32_t)col;
-  }
-  if (P.dump_bc)
-    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x)
-      P.dump_bc[(size_t)r_local * n + v] = bc[v];
-  return false;
-}
 
 // ---------------------------------------------------------------------------------------
 // The persistent kernel.  Work item w enumerates (problem, realization) pairs of all
@@ -744,7 +61,8 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     Realized H{n, rp, arc};
     components(P, H, comp, cinfo);
     bucket_setup(ctl, P.delta);
-    const uint32_t delta = ctl->delta, ringB = ctl->ring_b;
+    const uint32_t dsh = ctl->dsh;
+    const SlotSpace sp = smem_slots(smem, L, n);
 
     // sources: every node of a valid component (ascending), alive edges per root for TEPS
     uint32_t *cedges = sel;
@@ -798,18 +116,18 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
         if (k0 >= nsrc) break;
         const uint32_t S = min(spt, nsrc - k0);
         if (use32)
-          brandes_batch<TS, BLOCK, float>(team, H, smem, L, team.id * spt, S, src + k0, delta,
-                                          ringB, bc, bci, true, ctl);
+          brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, src + k0, dsh, bc, bci,
+                                          true, ctl, &ctl->err, &ctl->ovf);
         else
-          brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, src + k0, delta,
-                                           ringB, bc, bci, true, ctl);
+          brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, src + k0, dsh, bc, bci,
+                                           true, ctl, &ctl->err, &ctl->ovf);
       }
       __syncthreads();
       // betweenness = integral part (unique-path subtrees, exact) + floating part
       for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] += (double)bci[v];
       __syncthreads();
       const bool recheck = select_and_count(P, r_local, comp, cinfo, bc,
-                                            slot_arrays(smem, L, n, 0), sel, use32, ctl);
+                                            slot_arrays(sp, 0), sel, use32, ctl);
       __syncthreads();
       if (!recheck) break;
       if (threadIdx.x == 0 && P.stats) atomicAdd(u64p(&P.stats->rechecked), 1ull);
@@ -897,11 +215,12 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
       tsrc[i] = (uint16_t)((s >= 0 && (uint32_t)s < n) ? s : 0);
     }
     team.sync();
-    brandes_batch<TS, BLOCK, double>(team, H, smem, L, team.id * spt, S, tsrc, ctl->delta,
-                                     ctl->ring_b, bc, bci, false, ctl);
+    const SlotSpace sp = smem_slots(smem, L, n);
+    brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, tsrc, ctl->dsh, bc, bci,
+                                     false, ctl, &ctl->err, &ctl->ovf);
     for (uint32_t t = team.rank; t < S * n; t += TS) {
       const uint32_t i = t / n, v = t - i * n;
-      SlotArrays a = slot_arrays(smem, L, n, team.id * spt + i);
+      SlotArrays a = slot_arrays(sp, team.id * spt + i);
       const uint32_t d = a.dist[v] & kMask;
       const bool reached = d < kInf;
       dist_out[(size_t)(k0 + i) * n + v] = reached ? d : 0xFFFFFFFFu;

@@ -61,7 +61,7 @@ def _precision(p):
 
 def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=None,
                  bucket_width: int = 0, block_threads: int = 0, team_threads: int = 0,
-                 slots_per_team: int = 0) -> McProblem:
+                 slots_per_team: int = 0, memory_path: int = 0) -> McProblem:
     """McProblem for a workload on device tensors (per-edge arrays optional)."""
     p = McProblem()
     p.n, p.m = dg.n, dg.m
@@ -89,6 +89,7 @@ def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=No
     p.block_threads = int(block_threads)
     p.team_threads = int(team_threads)
     p.slots_per_team = int(slots_per_team)
+    p.memory_path = int(memory_path)
     return p
 
 
@@ -109,7 +110,7 @@ class Query:
     """All device state of one stochastic-centrality query.  Build once, run many times."""
 
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
-                 slots_per_team=0, stream=None):
+                 slots_per_team=0, stream=None, memory_path=0):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -135,7 +136,8 @@ class Query:
         self.s = None if wl.s_init is None else torch.from_numpy(np.asarray(wl.s_init, np.float64)).to(device)
         self.f = None if wl.reward is None else torch.from_numpy(np.asarray(wl.reward, np.float64)).to(device)
         self.prob = make_problem(self.graph, wl, self.thresh, self.w_lo, self.w_hi, self.in_w,
-                                 bucket_width, block_threads, team_threads, slots_per_team)
+                                 bucket_width, block_threads, team_threads, slots_per_team,
+                                 memory_path)
         self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
         self.stats = torch.zeros(7, dtype=torch.int64, device=device)
         wsb = afc_transition_counts_workspace(self.prob)
@@ -299,6 +301,105 @@ class HostBuffers:
     @property
     def d2h_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in (self.b, self.mu, self.counts))
+
+
+def host_query(wl, keep: list) -> HostQuery:
+    """HostQuery over numpy copies of a workload's arrays (appended to `keep`, which must
+    outlive the call that reads them)."""
+    def arr(x, dtype):
+        a = np.ascontiguousarray(x, dtype=dtype)
+        keep.append(a)
+        return a.ctypes.data
+
+    q = HostQuery()
+    q.n, q.m = int(wl.n), int(len(wl.eu))
+    q.eu, q.ev = arr(wl.eu, np.int32), arr(wl.ev, np.int32)
+    scalar_p = np.ndim(wl.p_survive) == 0
+    q.p_survive = None if scalar_p else arr(wl.p_survive, np.float64)
+    q.p_survive_all = float(wl.p_survive) if scalar_p else 0.0
+    q.w_lo = None if np.ndim(wl.w_lo) == 0 else arr(wl.w_lo, np.uint32)
+    q.w_hi = None if np.ndim(wl.w_hi) == 0 else arr(wl.w_hi, np.uint32)
+    q.w_lo_all = int(wl.w_lo) if np.ndim(wl.w_lo) == 0 else 0
+    q.w_hi_all = int(wl.w_hi) if np.ndim(wl.w_hi) == 0 else 0
+    q.seed, q.graph_tag, q.realizations = int(wl.seed), int(wl.graph_tag), int(wl.realizations)
+    q.k_min, q.alpha, q.absorb_floor = int(wl.k_min), float(wl.alpha), float(wl.absorb_floor)
+    q.s_init = None if wl.s_init is None else arr(wl.s_init, np.float64)
+    q.reward = None if wl.reward is None else arr(wl.reward, np.float64)
+    q.candidates = None if wl.candidates is None else arr(wl.candidates, np.int32)
+    q.n_candidates = 0 if wl.candidates is None else int(len(wl.candidates))
+    q.top_k, q.tie_rel = int(wl.top_k), float(wl.tie_rel)
+    q.precision, q.recheck_margin = _precision(wl.precision), float(wl.recheck_margin)
+    q.n_perturb, q.l1_radius, q.r_min = int(wl.n_perturb), float(wl.l1_radius), float(wl.r_min)
+    q.perturb_seed = int(wl.perturb_seed)
+    return q
+
+
+@dataclass
+class ServedResult:
+    ticket: int
+    b: np.ndarray
+    mu: np.ndarray
+    counts: Optional[np.ndarray]
+    expected_T: float
+    b_f: float
+    c: int
+    stats: dict
+    perturb_counters: np.ndarray
+    latency_ms: float
+
+
+class Server:
+    """The native serving loop (afc_server_*): submit workloads at any time, poll results."""
+
+    def __init__(self, hbm_budget=0, max_active=0, max_waiting=0, slice_realizations=0,
+                 keep_counts=False):
+        from . import ServerCfg, afc_server_create
+        cfg = ServerCfg()
+        cfg.hbm_budget, cfg.max_active, cfg.max_waiting = int(hbm_budget), int(max_active), int(max_waiting)
+        cfg.slice_realizations, cfg.keep_counts = int(slice_realizations), int(bool(keep_counts))
+        self.keep_counts = bool(keep_counts)
+        self.handle = afc_server_create(cfg)
+        self.n_of = {}
+
+    def submit(self, wl) -> int:
+        from . import afc_server_submit
+        keep = []
+        t = afc_server_submit(self.handle, host_query(wl, keep))
+        self.n_of[t] = int(wl.n)
+        return t
+
+    def poll(self, ticket: int, wait_ms: int = -1) -> Optional[ServedResult]:
+        from . import AFC_EBUSY, afc_server_poll
+        n = self.n_of[ticket]
+        b, mu = np.zeros(n), np.zeros(n)
+        counts = np.zeros((n, n + 1), np.uint32) if self.keep_counts else None
+        r = HostResult()
+        r.b, r.mu = b.ctypes.data, mu.ctypes.data
+        r.counts = None if counts is None else counts.ctypes.data
+        code, lat = afc_server_poll(self.handle, ticket, wait_ms, r)
+        if code == AFC_EBUSY:
+            return None
+        del self.n_of[ticket]
+        st = {f[0]: int(getattr(r.stats, f[0])) for f in McStats._fields_}
+        return ServedResult(ticket, b, mu, counts, r.expected_T, r.b_f, r.c, st,
+                            np.array(list(r.perturb_counters), np.uint64), lat)
+
+    def stats(self) -> dict:
+        from . import afc_server_get_stats
+        st = afc_server_get_stats(self.handle)
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+    def close(self):
+        from . import afc_server_destroy
+        if self.handle:
+            afc_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def run_query_host(bufs: HostBuffers, stream=None) -> HostResult:

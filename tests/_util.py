@@ -39,7 +39,29 @@ def oracle_counts(wl: Workload, r_begin: int, r_count: int, threads: int = 1):
                                wl.w_hi, wl.k_min, wl.candidates, wl.top_k, wl.tie_rel)
 
 
-def oracle_realization(wl: Workload, r: int):
+def _brandes_threads(g, alive, w, src, threads):
+    """The oracle's betweenness with the sources split into `threads` contiguous chunks run
+    concurrently (the C routine releases the GIL); partial sums added in chunk order."""
+    if threads <= 1:
+        return O.brandes(g, alive, w, src)
+    from concurrent.futures import ThreadPoolExecutor
+    idx = np.nonzero(src)[0]
+    chunks = [c for c in np.array_split(idx, threads) if c.size]
+
+    def part(c):
+        m = np.zeros(g.n, np.uint8)
+        m[c] = 1
+        return O.brandes(g, alive, w, m)
+
+    with ThreadPoolExecutor(len(chunks) or 1) as ex:
+        parts = list(ex.map(part, chunks))
+    out = np.zeros(g.n, np.float64)
+    for p in parts:
+        out += p
+    return out
+
+
+def oracle_realization(wl: Workload, r: int, threads: int = 1):
     """(alive, w, comp, size, bc over valid components, next state per anchor)."""
     g = oracle_graph(wl)
     alive, w = O.realize(g, wl.seed, wl.graph_tag, r, wl.p_survive, wl.w_lo, wl.w_hi)
@@ -50,7 +72,7 @@ def oracle_realization(wl: Workload, r: int):
         if size[v] >= wl.k_min and (inw is None or inw[v]):
             src[comp[v]] = 1
     src = src[comp]
-    bc = O.brandes(g, alive, w, src)
+    bc = _brandes_threads(g, alive, w, src, threads)
     cen = O.select(wl.n, comp, size, bc, wl.k_min, inw, wl.top_k, wl.tie_rel)
     nxt = np.array([wl.n if cen[comp[i]] < 0 else cen[comp[i]] for i in range(wl.n)], np.int32)
     return alive, w, comp, size, bc, nxt

@@ -55,10 +55,19 @@ def test_validation_errors_without_device():
     prob = afc.McProblem()
     prob.n = 0
     assert afc.afc_transition_counts_workspace(prob) == 0
-    prob.n, prob.m = 40000, 10
+    prob.n, prob.m = 70000, 10           # node ids are 16-bit in the kernels
     with pytest.raises(afc.AfcError) as e:
         afc.afc_transition_counts(prob, 0, 1, None, None, None, None, None, 0, None)
     assert e.value.code == afc.AFC_EUNSUPPORTED
+    prob.n, prob.w_hi_all = 40000, 60000   # n * max length reaches 2^31: distance range
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_transition_counts(prob, 0, 1, None, None, None, None, None, 0, None)
+    assert e.value.code == afc.AFC_EUNSUPPORTED
+    prob.w_hi_all, prob.memory_path = 3, 5
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_transition_counts(prob, 0, 1, None, None, None, None, None, 0, None)
+    assert e.value.code == afc.AFC_EINVAL
+    prob.memory_path = 0
     prob.n, prob.m, prob.row_ptr, prob.col, prob.eid = 10, 5, 8, 8, 8
     prob.w_lo_all, prob.w_hi_all, prob.k_min = 0, 3, 1
     with pytest.raises(afc.AfcError):
