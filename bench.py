@@ -300,6 +300,165 @@ def run_counts_only(args):
     return 0
 
 
+def _scaled(wl, scale, lo=16):
+    import copy
+    w2 = copy.copy(wl)
+    w2.realizations = max(lo, int(round(wl.realizations * scale)))
+    return w2
+
+
+def run_mix(args):
+    """The batched mix (64 graphs, n log-uniform in [200, 4000]): every graph's realizations in
+    one batched call with FP32 dependencies and FP64 recheck, against plain FP64 with one call
+    per graph, on the same GPU; the counts of the two must be identical."""
+    import numpy as np
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import mixed_batch
+    torch.cuda.set_device(0)
+    batch = [_scaled(w, args.mix_scale) for w in mixed_batch(64)]
+    stream = torch.cuda.current_stream()
+    q32 = [afc.Query(w) for w in batch]
+    q64 = [afc.Query(w) for w in batch]
+    for q in q64:
+        q.prob.precision = afc.AFC_FP64
+    probs = (afc.McProblem * len(batch))(*[q.prob for q in q32])
+    rc = np.array([w.realizations for w in batch], np.uint32)
+    ptrs = np.array([q.counts.data_ptr() for q in q32], np.uint64)
+    stats32 = torch.zeros((len(batch), 7), dtype=torch.int64, device="cuda")
+    wsb = afc.afc_transition_counts_batched_workspace(len(batch), probs, rc)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
+
+    def batched():
+        for q in q32:
+            q.counts.zero_()
+        stats32.zero_()
+        afc.afc_transition_counts_batched(len(batch), probs, rc, ptrs, stats32, ws, ws.numel(),
+                                          stream.cuda_stream)
+
+    def per_query():
+        for q in q64:
+            q.run_counts()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms32 = timed(batched)
+    ms64 = timed(per_query)
+    same = all(torch.equal(a.counts, b.counts) for a, b in zip(q32, q64))
+    st = stats32.cpu().numpy()
+    R = int(rc.sum())
+    edges = int(st[:, 2].sum())
+    glob = sum(1 for q in q32 if afc.afc_counts_path(q.prob) == afc.AFC_PATH_GLOBAL)
+    line = {"config": {"workload": "batched mix: 64 graphs (32 ER mean degree 8, 32 WS k=8 "
+                                   "beta=0.2), n log-U[200,4000], failure U(0.01,0.2), lengths "
+                                   "{1..50}, realizations U{256..4096} x %.3g" % args.mix_scale,
+                       "realizations_total": R, "graphs_on_global_path": glob},
+            "metric": "realizations/s", "fp32_recheck_batched": {
+                "value": R / (ms32 / 1e3), "ms": ms32, "gteps": edges / (ms32 / 1e3) / 1e9,
+                "rechecked": int(st[:, 4].sum()), "launch": "one batched call"},
+            "fp64_per_query": {"value": R / (ms64 / 1e3), "ms": ms64,
+                               "gteps": edges / (ms64 / 1e3) / 1e9, "launch": "64 calls"},
+            "speedup": ms64 / ms32, "counts_identical": bool(same),
+            "device_error": int(st[:, 5].sum())}
+    print(json.dumps(line))
+    return 0 if same else 1
+
+
+def run_ws20000(args):
+    """The 20,000-node workload: a sample of its 2048 realizations counted, then the FP64
+    reduced solve on those counts and the 10,000-perturbation sweep."""
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+    torch.cuda.set_device(0)
+    wl = workload("ws20000")
+    Rs = args.ws20000_sample
+    q = afc.Query(wl)
+    q.run_counts(0, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    q.run_counts(0, Rs)
+    ev[1].record(stream)
+    q.wl.realizations = Rs
+    q.run_solve()
+    ev[2].record(stream)
+    q.run_perturb()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    res = q.result()
+    ms_c, ms_s, ms_p = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                        ev[2].elapsed_time(ev[3]))
+    st = res.stats
+    line = {"config": {"workload": "ws20000: WS(20000, 10, 0.05), failure 0.1, lengths "
+                                   "{1..1000}, %d of 2048 realizations, reduced FP64 solve, "
+                                   "10000 perturbations radius 0.05" % Rs},
+            "metric": "realizations/s", "value": Rs / (ms_c / 1e3),
+            "gteps": st["edge_visits"] / (ms_c / 1e3) / 1e9, "counts_ms": ms_c,
+            "solve_ms": ms_s, "perturb_ms": ms_p, "c": res.c,
+            "full_2048_counts_s_extrapolated": 2048 * ms_c / Rs / 1e3,
+            "device_error": st["device_error"], "perturb_counters": res.perturb["counters"].tolist()}
+    print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """The serving stream through the native serving loop: a closed batch measures capacity,
+    then Poisson arrivals at a fraction of it for a bounded time; p50/p99 submit-to-result."""
+    import numpy as np
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import serving_stream
+    torch.cuda.set_device(0)
+    stream = [wl for _, wl in serving_stream(max_queries=400, seed=105)]
+    k = args.serve_probe
+    with afc.Server() as srv:
+        t0 = time.perf_counter()
+        ts = [srv.submit(wl) for wl in stream[:k]]
+        for t in ts:
+            srv.poll(t)
+        wall = time.perf_counter() - t0
+        probe = srv.stats()
+    cap = k / wall
+    rate = args.serve_rate_frac * cap
+    rng = np.random.default_rng(5)
+    with afc.Server() as srv:
+        t0 = time.perf_counter()
+        nxt, tickets, i = 0.0, [], k
+        while nxt < args.serve_seconds and i < len(stream):
+            delay = t0 + nxt - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(stream[i]))
+            i += 1
+            nxt += rng.exponential(1.0 / rate)
+        lat = [srv.poll(t).latency_ms for t in tickets]
+        st = srv.stats()
+    line = {"config": {"workload": "serving stream: Poisson arrivals, ER/WS 50/50, n log-U[100, "
+                                   "1e4], mean degree U(6,12), failure U(0.01,0.3), lengths "
+                                   "{1..100}, realizations log-U[256,8192], FP32 + recheck",
+                       "probe_queries": k, "rate_qps": rate, "rate_fraction_of_capacity":
+                       args.serve_rate_frac, "arrival_window_s": args.serve_seconds},
+            "capacity_qps": cap, "capacity_realizations_per_s": probe["realizations_per_s"],
+            "queries": len(tickets), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "wait_p50_ms": st["wait_p50_ms"],
+            "wait_p99_ms": st["wait_p99_ms"], "realizations_per_s": st["realizations_per_s"],
+            "gteps": st["edge_visits"] / max(st["wall_s"], 1e-9) / 1e9,
+            "slices": st["slices"], "shed": st["shed"], "failed": st["failed"],
+            "latency_check_ms": [float(np.percentile(lat, 50)), float(np.percentile(lat, 99))]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,7 +468,21 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--counts-only", type=int, default=0,
                     help="run one counting launch of this many realizations and exit")
+    ap.add_argument("--config", default="ws1000", choices=["ws1000", "mix", "ws20000", "serving"],
+                    help="ws1000: the benchmark line; the others print their own JSON line")
+    ap.add_argument("--mix-scale", type=float, default=0.125,
+                    help="fraction of each mixed-batch graph's realizations to run")
+    ap.add_argument("--ws20000-sample", type=int, default=16)
+    ap.add_argument("--serve-probe", type=int, default=6)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-rate-frac", type=float, default=0.7)
     args = ap.parse_args()
+    if args.config == "mix":
+        return run_mix(args)
+    if args.config == "ws20000":
+        return run_ws20000(args)
+    if args.config == "serving":
+        return run_serving(args)
     if args.counts_only:
         return run_counts_only(args)
     if args.impl == "reference":

@@ -126,6 +126,11 @@ typedef struct {
   uint64_t vertex_visits;    /* sum over solved sources of the size of the source's component */
 } afc_mc_stats;
 
+/* AFC_PATH_SHARED or AFC_PATH_GLOBAL: where afc_transition_counts runs this problem (the
+ * problem's memory_path, or for AFC_PATH_AUTO whether its per-CTA state fits in shared
+ * memory); a negative error code for an invalid problem. */
+int afc_counts_path(const afc_mc_problem *prob);
+
 /* Bytes of device workspace afc_transition_counts needs for this problem (0 when the whole
  * per-realization state fits in shared memory). */
 size_t afc_transition_counts_workspace(const afc_mc_problem *prob);
@@ -323,7 +328,9 @@ int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream);
 typedef struct afc_server afc_server;
 
 typedef struct {
-  uint64_t hbm_budget;         /* bytes admitted queries may hold; 0 = 80% of free memory   */
+  uint64_t hbm_budget;         /* bytes admitted queries may hold (graph, parameters, count */
+                               /* matrix); 0 = 80% of free memory.  The finisher's solve    */
+                               /* workspace (one query at a time) comes from outside it     */
   uint32_t max_active;         /* queries admitted at once; 0 = 64                          */
   uint32_t max_waiting;        /* queue length beyond which submissions are refused         */
                                /* (AFC_EBUSY, counted as shed); 0 = unbounded               */

@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = [
     "AfcError", "lib", "McProblem", "McStats", "Chain", "PerturbParams", "HostQuery", "HostResult",
     "afc_last_error", "afc_version", "afc_csr_from_edges", "afc_survival_threshold",
-    "afc_transition_counts_workspace", "afc_transition_counts",
+    "afc_transition_counts_workspace", "afc_transition_counts", "afc_counts_path",
     "afc_transition_counts_batched_workspace", "afc_transition_counts_batched",
     "afc_debug_realize", "afc_debug_components", "afc_debug_sssp", "afc_observed_states",
     "afc_solve_workspace", "afc_absorbing_solve", "afc_perturb_sweep", "afc_certificates",
@@ -116,6 +116,7 @@ _SIGS = {
     "afc_csr_from_edges": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_survival_threshold": ([c_f64], c_u64),
     "afc_transition_counts_workspace": ([ctypes.POINTER(McProblem)], c_sz),
+    "afc_counts_path": ([ctypes.POINTER(McProblem)], ctypes.c_int),
     "afc_transition_counts": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p, c_p, c_p,
                                c_sz, c_p], ctypes.c_int),
     "afc_transition_counts_batched_workspace": ([c_i32, ctypes.POINTER(McProblem), c_p], c_sz),
@@ -200,6 +201,13 @@ def afc_csr_from_edges(n, m, eu, ev, row_ptr, col, eid):
 
 def afc_survival_threshold(p: float) -> int:
     return int(lib().afc_survival_threshold(float(p)))
+
+
+def afc_counts_path(prob: McProblem) -> int:
+    code = lib().afc_counts_path(ctypes.byref(prob))
+    if code < 0:
+        raise AfcError(-code, afc_last_error())
+    return code
 
 
 def afc_transition_counts_workspace(prob: McProblem) -> int:

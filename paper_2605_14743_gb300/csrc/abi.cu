@@ -59,9 +59,11 @@ uint32_t auto_delta(const afc_mc_problem &p) {
   const double lo = p.w_lo ? 1.0 : (double)p.w_lo_all;
   const double hi = p.w_hi ? 100.0 : (double)p.w_hi_all;
   const double mean = 0.5 * (lo + hi);
-  // measured on the 1000-node Watts-Strogatz workload (lengths 1..100): the best width is about
-  // the mean length (fewer buckets outweigh the extra in-bucket relaxation passes)
-  return (uint32_t)std::max(1.0, std::floor(0.95 * mean));
+  // measured: on the 1000-node Watts-Strogatz workload (lengths 1..100) the best width is about
+  // the mean length (fewer buckets outweigh the extra in-bucket relaxation passes); on the
+  // 20,000-node one (lengths 1..1000) about a quarter of it, as buckets hold more members
+  const double shrink = std::min(1.0, std::sqrt(1000.0 / std::max(1, p.n)));
+  return (uint32_t)std::max(1.0, std::floor(0.95 * mean * shrink));
 }
 
 int auto_block(const afc_mc_problem &p) {
@@ -200,15 +202,11 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   if (p.team_threads) {
     b.team = p.team_threads;
   } else {
-    // source slots of all CTAs within about 48 MB, so that they stay resident in L2: as many
-    // teams per CTA as that allows (at most 8), each as wide as the block allows
-    const size_t per_cta = (48ull << 20) / (size_t)std::max(1, d.sms);
-    const size_t nt_fit = std::max<size_t>(1, per_cta / b.slot_stride);
-    b.team = b.block;
-    for (int t : {128, 256, 512, 1024}) {
-      if (t > b.block || !big_config_supported(b.block, t)) continue;
-      if ((size_t)(b.block / t) <= std::min<size_t>(nt_fit, 8)) { b.team = t; break; }
-    }
+    // measured on 1000- and 20,000-node graphs: teams of 128 threads (8 sources in flight per
+    // CTA) up to about 4,000 nodes, 256 beyond (wider teams for bigger buckets, and the slot
+    // arena of the grid stays within a few hundred MB)
+    b.team = std::min(b.block, n <= 4096 ? 128 : 256);
+    if (!big_config_supported(b.block, b.team)) b.team = b.block;
   }
   const uint32_t nt = (uint32_t)(b.block / b.team);
   b.spt = p.slots_per_team ? (uint32_t)p.slots_per_team : 1u;
@@ -385,6 +383,12 @@ uint64_t afc_survival_threshold(double p) {
   if (!(p > 0.0)) return 0;
   if (p >= 1.0) return 1ull << 32;
   return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+int afc_counts_path(const afc_mc_problem *prob) {
+  const int st = validate(prob);
+  if (st) return -st;
+  return wants_global(*prob) ? AFC_PATH_GLOBAL : AFC_PATH_SHARED;
 }
 
 size_t afc_transition_counts_workspace(const afc_mc_problem *prob) {

@@ -70,20 +70,14 @@ struct Job {
 
 using JobP = std::shared_ptr<Job>;
 
-size_t solve_reserve(int32_t n) {
-  // device memory the finisher needs for the solve, sized for up to min(n, 2048) observed
-  // states (the actual number is known only once the counts are in)
-  const int32_t c = std::min<int32_t>(n, 2048);
-  return afc_solve_workspace(n, c) + 8ull * (size_t)c * (size_t)c + 4ull * (size_t)c +
-         24ull * (size_t)n + 8ull * 128;
-}
-
+// Device memory an admitted query holds until it is finished: its graph, parameters, count
+// matrix and observed-state maps.  The finisher's solve workspace is transient and needed for
+// one query at a time; it comes out of the memory left outside the budget.
 size_t footprint_of(const Job &j) {
   const size_t n = (size_t)j.n, m = (size_t)j.m;
   size_t b = 4 * (n + 1) + 16 * m + 8 * j.th.size() + 4 * (j.wlo.size() + j.whi.size()) +
              j.inw.size() + 8 * (j.s.size() + j.f.size());
   b += 4 * n * (n + 1) + sizeof(afc_mc_stats) + 8 * n;   // counts, stats, observed-state maps
-  b += solve_reserve(j.n);
   return b;
 }
 
