@@ -290,11 +290,13 @@ def run_counts_only(args):
     import paper_2605_14743_gb300 as afc
     from afc_inputs import workload
     torch.cuda.set_device(0)
-    q = afc.Query(workload("ws1000"))
+    path = {"auto": 0, "shared": 1, "global": 2}[args.memory_path]
+    q = afc.Query(workload("ws1000"), memory_path=path)
     q.run_counts(0, args.counts_only)
     torch.cuda.synchronize()
     st = q.stats.cpu().numpy()
-    print(json.dumps({"counts_only": args.counts_only, "realizations": int(st[0]),
+    print(json.dumps({"counts_only": args.counts_only, "memory_path": args.memory_path,
+                      "realizations": int(st[0]),
                       "sources": int(st[1]), "edge_visits": int(st[2]),
                       "device_error": int(st[5])}))
     return 0
@@ -412,8 +414,10 @@ def run_ws20000(args):
 
 
 def run_serving(args):
-    """The serving stream through the native serving loop: a closed batch measures capacity,
-    then Poisson arrivals at a fraction of it for a bounded time; p50/p99 submit-to-result."""
+    """The serving stream through the native serving loop: a closed batch of its first queries
+    measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
+    capacity; p50/p99 submit-to-result latency.  The specified 200 queries/s is reported as
+    the overload factor over the measured capacity."""
     import numpy as np
     import torch
     import paper_2605_14743_gb300 as afc
@@ -434,7 +438,7 @@ def run_serving(args):
     with afc.Server() as srv:
         t0 = time.perf_counter()
         nxt, tickets, i = 0.0, [], k
-        while nxt < args.serve_seconds and i < len(stream):
+        while len(tickets) < args.serve_queries and i < len(stream):
             delay = t0 + nxt - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
@@ -447,7 +451,9 @@ def run_serving(args):
                                    "1e4], mean degree U(6,12), failure U(0.01,0.3), lengths "
                                    "{1..100}, realizations log-U[256,8192], FP32 + recheck",
                        "probe_queries": k, "rate_qps": rate, "rate_fraction_of_capacity":
-                       args.serve_rate_frac, "arrival_window_s": args.serve_seconds},
+                       args.serve_rate_frac, "arrivals": len(tickets),
+                       "offered_as_specified_qps": 200.0,
+                       "as_specified_overload": 200.0 / cap},
             "capacity_qps": cap, "capacity_realizations_per_s": probe["realizations_per_s"],
             "queries": len(tickets), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "mean_ms": st["mean_ms"], "wait_p50_ms": st["wait_p50_ms"],
@@ -468,13 +474,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--counts-only", type=int, default=0,
                     help="run one counting launch of this many realizations and exit")
+    ap.add_argument("--memory-path", default="auto", choices=["auto", "shared", "global"],
+                    help="counting path of --counts-only")
     ap.add_argument("--config", default="ws1000", choices=["ws1000", "mix", "ws20000", "serving"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
     ap.add_argument("--ws20000-sample", type=int, default=16)
     ap.add_argument("--serve-probe", type=int, default=6)
-    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-queries", type=int, default=12,
+                    help="Poisson arrivals in the rate-scaled serving run")
     ap.add_argument("--serve-rate-frac", type=float, default=0.7)
     args = ap.parse_args()
     if args.config == "mix":

@@ -348,7 +348,7 @@ typedef struct {
   double wait_p50_ms, wait_p99_ms;          /* submit -> admission                          */
   double wall_s;               /* first submission -> last completion                       */
   double realizations_per_s;   /* realizations / wall_s                                     */
-} afc_server_stats;
+} afc_serving_stats;
 
 /* Starts the scheduler and finisher threads on the current device. */
 int afc_server_create(const afc_server_cfg *cfg, afc_server **out);
@@ -365,10 +365,96 @@ int afc_server_submit(afc_server *s, const afc_host_query *q, uint64_t *ticket);
 int afc_server_poll(afc_server *s, uint64_t ticket, int32_t wait_ms, afc_host_result *res,
                     double *latency_ms);
 
-int afc_server_get_stats(afc_server *s, afc_server_stats *out);
+int afc_server_stats(afc_server *s, afc_serving_stats *out);
 
 /* Finishes every admitted and queued query, then stops the threads and frees everything. */
 void afc_server_destroy(afc_server *s);
+
+/* ------------------------------------------------------------------------------------ */
+/* Query handles: graph, parameters, result (all HOST-side; the device is used inside)      */
+/* ------------------------------------------------------------------------------------ */
+/* The problem statement of Sec. 3 (a base graph and the law of its random realizations) and
+ * of Alg. 2 (the sampling budget and the chain parameters) as opaque handles; afc_run is
+ * afc_run_host on them, and the result keeps the counts as a sparse matrix. */
+
+typedef struct afc_graph afc_graph;    /* library-owned, immutable after creation            */
+
+/* Undirected edge list (edge id = position, 0 <= eu, ev < n, no self loops or duplicates);
+ * copied during the call. */
+int afc_graph_create(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, afc_graph **out);
+/* Symmetric CSR over HOST arrays: row_ptr [n+1], col [row_ptr[n]], eid [row_ptr[n]]; every
+ * edge id 0..m-1 must appear on exactly the two arcs (u, v) and (v, u), m = row_ptr[n] / 2. */
+int afc_graph_create_csr(int32_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *eid,
+                         afc_graph **out);
+int32_t afc_graph_nodes(const afc_graph *g);
+int64_t afc_graph_edges(const afc_graph *g);
+void afc_graph_destroy(afc_graph *g);
+
+typedef struct {
+  uint64_t seed; uint32_t graph_tag;   /* Philox key and third counter word                 */
+  uint32_t realizations;               /* R = M samples per anchor row                      */
+  const double *p_survive; double p_survive_all;       /* HOST [m] or NULL -> the scalar    */
+  const uint32_t *w_lo, *w_hi; uint32_t w_lo_all, w_hi_all;   /* HOST [m] or the scalars   */
+  uint32_t k_min; double alpha; double absorb_floor;
+  const double *s_init;                /* HOST [n] or NULL = uniform                        */
+  const double *reward;                /* HOST [n] node reward f or NULL                    */
+  const int32_t *candidates; int32_t n_candidates;   /* HOST pool W or NULL = all nodes     */
+  uint32_t top_k;                      /* 0 = no rank cutoff                                */
+  int32_t precision;                   /* AFC_FP64 | AFC_FP32_RECHECK                       */
+  double recheck_margin;
+  double tie_rel;
+  void *cuda_stream;                   /* cudaStream_t, or NULL = the default stream        */
+} afc_params;
+
+/* Fills the defaults: p_survive_all 1, lengths 1..1, k_min 5, alpha 0.15, absorb_floor 1e-6,
+ * FP64, recheck_margin 1e-4, tie_rel 1e-9, everything else 0 / NULL. */
+void afc_params_default(afc_params *p);
+
+typedef struct afc_result afc_result;  /* library-owned; free with afc_result_destroy        */
+
+/* Counts (A1-A7) and the absorbing-chain solve (A8) of one query; SYNCHRONISES the stream. */
+int afc_run(const afc_graph *g, const afc_params *p, afc_result **out);
+
+/* Transition counts as a sparse matrix: row i has the columns col[row_ptr[i] .. row_ptr[i+1])
+ * (ascending node ids) with counts cnt[...], and absorb[i] absorptions; every row sums to R.
+ * The arrays belong to the result. */
+int afc_result_counts(const afc_result *r, const int64_t **row_ptr, const int32_t **col,
+                      const uint32_t **cnt, const uint32_t **absorb);
+/* b [n] (belongs to the result), E_s[T] and b_f = b.f (0 without a reward). */
+int afc_result_afc(const afc_result *r, const double **b, double *expected_T, double *b_reward);
+/* Realizations recomputed in FP64 (FP32 mode) and a bound on ||b - b_exact||_1 from the FP64
+ * solve's residual: 2 ||s - mu (I - Q)||_1 max_i (N 1)_i / ||mu||_1, the residual taken in
+ * extended precision on the host. */
+int afc_result_diag(const afc_result *r, uint64_t *rechecked, double *fp_err_bound);
+void afc_result_destroy(afc_result *r);
+
+typedef struct {
+  uint64_t top1_changes, topk_set_changes, topk_order_changes;
+  uint64_t pair_flips[100];            /* nominal top-10 pairs a < b swapped: entry a*10+b  */
+  uint64_t shift_hist[16];             /* |rank shift| of the nominal top 10, last bin open  */
+  double max_shift_inf;                /* max ||b' - b||_inf                                */
+  double max_linear_err_inf;           /* max ||b' - (b + db_lin)||_inf (Sec. 5.4)          */
+  double max_rowsum_N;                 /* max_i (N' 1)_i over the perturbations             */
+} afc_perturb_stats;
+
+/* The perturbation sweep (A9, see afc_perturb_sweep) of a result's kernel: n_perturb
+ * perturbations 0 .. n_perturb-1, k2 = 10, 16 histogram bins, the result's tie_rel.  Runs on
+ * the stream of the afc_params the result came from and SYNCHRONISES it. */
+int afc_perturb(const afc_result *r, uint32_t n_perturb, double l1_radius, double r_min,
+                uint64_t seed, uint32_t top_k, afc_perturb_stats *out);
+
+/* Serving with handles: the query (g, p) is copied and queued like afc_server_submit (its
+ * counts are kept for the result); afc_poll does not wait: AFC_EBUSY while pending, else the
+ * query's status and, on AFC_OK, a result to free with afc_result_destroy. */
+int afc_submit(afc_server *s, const afc_graph *g, const afc_params *p, uint64_t *ticket);
+int afc_poll(afc_server *s, uint64_t ticket, afc_result **out);
+
+/* Internals of one realization r of (g, p) for bit-exact checks, HOST outputs (each may be
+ * NULL): dist [n] and sigma [n] from source s (dist 0xFFFFFFFF and sigma 0 where unreachable;
+ * shared-memory path only, else AFC_EUNSUPPORTED), and B [n], the realization's betweenness
+ * over ordered pairs for nodes of valid components (0 elsewhere).  SYNCHRONISES the stream. */
+int afc_debug_realization(const afc_graph *g, const afc_params *p, uint32_t r, int32_t s,
+                          uint32_t *dist, uint64_t *sigma, double *B);
 
 #ifdef __cplusplus
 }

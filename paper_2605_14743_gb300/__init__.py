@@ -30,7 +30,10 @@ __all__ = [
     "afc_run_host", "afc_absorbing_solve_noalloc", "AFC_FP64", "AFC_FP32_RECHECK",
     "AFC_PATH_AUTO", "AFC_PATH_SHARED", "AFC_PATH_GLOBAL", "AFC_EBUSY", "ServerCfg",
     "ServerStats", "afc_server_create", "afc_server_submit", "afc_server_poll",
-    "afc_server_get_stats", "afc_server_destroy",
+    "afc_server_stats", "afc_server_destroy", "Params", "PerturbStats", "afc_graph_create",
+    "afc_graph_create_csr", "afc_graph_nodes", "afc_graph_edges", "afc_graph_destroy",
+    "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
+    "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -110,6 +113,23 @@ class ServerStats(ctypes.Structure):
                 ("wait_p99_ms", c_f64), ("wall_s", c_f64), ("realizations_per_s", c_f64)]
 
 
+class Params(ctypes.Structure):
+    """afc_params (handle API)."""
+    _fields_ = [("seed", c_u64), ("graph_tag", c_u32), ("realizations", c_u32),
+                ("p_survive", c_p), ("p_survive_all", c_f64), ("w_lo", c_p), ("w_hi", c_p),
+                ("w_lo_all", c_u32), ("w_hi_all", c_u32), ("k_min", c_u32), ("alpha", c_f64),
+                ("absorb_floor", c_f64), ("s_init", c_p), ("reward", c_p), ("candidates", c_p),
+                ("n_candidates", c_i32), ("top_k", c_u32), ("precision", c_i32),
+                ("recheck_margin", c_f64), ("tie_rel", c_f64), ("cuda_stream", c_p)]
+
+
+class PerturbStats(ctypes.Structure):
+    _fields_ = [("top1_changes", c_u64), ("topk_set_changes", c_u64),
+                ("topk_order_changes", c_u64), ("pair_flips", c_u64 * 100),
+                ("shift_hist", c_u64 * 16), ("max_shift_inf", c_f64),
+                ("max_linear_err_inf", c_f64), ("max_rowsum_N", c_f64)]
+
+
 _SIGS = {
     "afc_last_error": ([], ctypes.c_char_p),
     "afc_version": ([], ctypes.c_int),
@@ -143,8 +163,27 @@ _SIGS = {
     "afc_server_submit": ([c_p, ctypes.POINTER(HostQuery), ctypes.POINTER(c_u64)], ctypes.c_int),
     "afc_server_poll": ([c_p, c_u64, c_i32, ctypes.POINTER(HostResult), ctypes.POINTER(c_f64)],
                         ctypes.c_int),
-    "afc_server_get_stats": ([c_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "afc_server_stats": ([c_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
     "afc_server_destroy": ([c_p], None),
+    "afc_graph_create": ([c_i32, c_i64, c_p, c_p, ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_graph_create_csr": ([c_i32, c_p, c_p, c_p, ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_graph_nodes": ([c_p], c_i32),
+    "afc_graph_edges": ([c_p], c_i64),
+    "afc_graph_destroy": ([c_p], None),
+    "afc_params_default": ([ctypes.POINTER(Params)], None),
+    "afc_run": ([c_p, ctypes.POINTER(Params), ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_result_counts": ([c_p, ctypes.POINTER(c_p), ctypes.POINTER(c_p), ctypes.POINTER(c_p),
+                           ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_result_afc": ([c_p, ctypes.POINTER(c_p), ctypes.POINTER(c_f64), ctypes.POINTER(c_f64)],
+                       ctypes.c_int),
+    "afc_result_diag": ([c_p, ctypes.POINTER(c_u64), ctypes.POINTER(c_f64)], ctypes.c_int),
+    "afc_result_destroy": ([c_p], None),
+    "afc_perturb": ([c_p, c_u32, c_f64, c_f64, c_u64, c_u32, ctypes.POINTER(PerturbStats)],
+                    ctypes.c_int),
+    "afc_submit": ([c_p, c_p, ctypes.POINTER(Params), ctypes.POINTER(c_u64)], ctypes.c_int),
+    "afc_poll": ([c_p, c_u64, ctypes.POINTER(c_p)], ctypes.c_int),
+    "afc_debug_realization": ([c_p, ctypes.POINTER(Params), c_u32, c_i32, c_p, c_p, c_p],
+                              ctypes.c_int),
 }
 
 
@@ -314,14 +353,111 @@ def afc_server_poll(server: int, ticket: int, wait_ms: int, result: HostResult):
     return code, lat.value
 
 
-def afc_server_get_stats(server: int) -> ServerStats:
+def afc_server_stats(server: int) -> ServerStats:
     st = ServerStats()
-    _chk(lib().afc_server_get_stats(server, ctypes.byref(st)))
+    _chk(lib().afc_server_stats(server, ctypes.byref(st)))
     return st
 
 
 def afc_server_destroy(server: int) -> None:
     lib().afc_server_destroy(server)
+
+
+# ---- handle API (graph, params, result) ------------------------------------------------------
+
+def afc_graph_create(n, m, eu, ev) -> int:
+    h = c_p()
+    _chk(lib().afc_graph_create(n, m, _ptr(eu), _ptr(ev), ctypes.byref(h)))
+    return h.value
+
+
+def afc_graph_create_csr(n, row_ptr, col, eid) -> int:
+    h = c_p()
+    _chk(lib().afc_graph_create_csr(n, _ptr(row_ptr), _ptr(col), _ptr(eid), ctypes.byref(h)))
+    return h.value
+
+
+def afc_graph_nodes(g) -> int:
+    return int(lib().afc_graph_nodes(g))
+
+
+def afc_graph_edges(g) -> int:
+    return int(lib().afc_graph_edges(g))
+
+
+def afc_graph_destroy(g) -> None:
+    lib().afc_graph_destroy(g)
+
+
+def afc_params_default() -> Params:
+    p = Params()
+    lib().afc_params_default(ctypes.byref(p))
+    return p
+
+
+def afc_run(g, params: Params) -> int:
+    h = c_p()
+    _chk(lib().afc_run(g, ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def afc_result_counts(r, n: int):
+    """(row_ptr int64 [n+1], col int32, cnt uint32, absorb uint32 [n]) copied to numpy."""
+    rp, col, cnt, ab = c_p(), c_p(), c_p(), c_p()
+    _chk(lib().afc_result_counts(r, ctypes.byref(rp), ctypes.byref(col), ctypes.byref(cnt),
+                                 ctypes.byref(ab)))
+    row_ptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(c_i64)), (n + 1,)).copy()
+    nnz = int(row_ptr[-1])
+    colv = (np.ctypeslib.as_array(ctypes.cast(col, ctypes.POINTER(c_i32)), (nnz,)).copy()
+            if nnz else np.zeros(0, np.int32))
+    cntv = (np.ctypeslib.as_array(ctypes.cast(cnt, ctypes.POINTER(c_u32)), (nnz,)).copy()
+            if nnz else np.zeros(0, np.uint32))
+    absorb = np.ctypeslib.as_array(ctypes.cast(ab, ctypes.POINTER(c_u32)), (n,)).copy()
+    return row_ptr, colv, cntv, absorb
+
+
+def afc_result_afc(r, n: int):
+    b, T, bf = c_p(), c_f64(), c_f64()
+    _chk(lib().afc_result_afc(r, ctypes.byref(b), ctypes.byref(T), ctypes.byref(bf)))
+    bv = np.ctypeslib.as_array(ctypes.cast(b, ctypes.POINTER(c_f64)), (n,)).copy()
+    return bv, T.value, bf.value
+
+
+def afc_result_diag(r):
+    rc, bound = c_u64(), c_f64()
+    _chk(lib().afc_result_diag(r, ctypes.byref(rc), ctypes.byref(bound)))
+    return rc.value, bound.value
+
+
+def afc_result_destroy(r) -> None:
+    lib().afc_result_destroy(r)
+
+
+def afc_perturb(r, n_perturb, l1_radius, r_min, seed, top_k) -> PerturbStats:
+    st = PerturbStats()
+    _chk(lib().afc_perturb(r, n_perturb, l1_radius, r_min, seed, top_k, ctypes.byref(st)))
+    return st
+
+
+def afc_submit(server, g, params: Params) -> int:
+    t = c_u64(0)
+    _chk(lib().afc_submit(server, g, ctypes.byref(params), ctypes.byref(t)))
+    return t.value
+
+
+def afc_poll(server, ticket):
+    """Result handle, or None while the query is pending."""
+    h = c_p()
+    code = lib().afc_poll(server, ticket, ctypes.byref(h))
+    if code == AFC_EBUSY:
+        return None
+    _chk(code)
+    return h.value
+
+
+def afc_debug_realization(g, params: Params, r, s, dist, sigma, B):
+    _chk(lib().afc_debug_realization(g, ctypes.byref(params), r, s, _ptr(dist), _ptr(sigma),
+                                     _ptr(B)))
 
 
 # ---- helpers over torch device memory -------------------------------------------------------

@@ -295,6 +295,22 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     const McPlan pl = plan_for(p0, nmax, amax, prefix[ns], p0.team_threads, p0.slots_per_team);
     if (!pl.fits)
       return fail(AFC_EUNSUPPORTED, "batch too large for the shared-memory counting kernel");
+    if (ns > 1) {
+      // every problem of a batched launch takes as many source slots per team as the launch's
+      // shared memory holds for its own size (the launch is sized for the largest graph)
+      const uint32_t nt = (uint32_t)(pl.block / pl.team);
+      const uint32_t cap = std::min<uint32_t>((uint32_t)kMaxSlotsPerTeam, (uint32_t)kMaxSlots / nt);
+      for (int k = 0; k < ns; ++k) {
+        const afc_mc_problem &p = probs[order[k]];
+        const uint32_t n = (uint32_t)p.n;
+        const uint64_t arcs = 2ull * (uint64_t)p.m;
+        uint32_t spt = p.slots_per_team ? std::min<uint32_t>((uint32_t)p.slots_per_team, cap)
+                                        : std::min<uint32_t>(cap, std::max<uint32_t>(1u, (n + nt - 1) / nt));
+        while (spt > 1 && mc_layout_bytes(n, arcs, nt * spt) > pl.smem) --spt;
+        devs[k].spt = spt;   // one slot per team always fits: the launch is sized for the largest
+      }
+      AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)ns, cudaMemcpyHostToDevice, stream));
+    }
     cudaError_t e = launch_mc_counts(pl.block, pl.team, devs_d, ns, prefix_d, prefix[ns], pl.spt,
                                      pl.smem, pl.grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");

@@ -34,6 +34,7 @@ struct McDev {
   int32_t precision;
   double recheck_margin;
   uint32_t delta;
+  uint32_t spt;          // shared path: sources per team for this problem (0: launch default)
   uint32_t r_begin;
   uint32_t *counts;
   afc_mc_stats *stats;
@@ -57,6 +58,15 @@ struct TeamCtl {
   uint32_t pad[3];
 };
 
+// Per-warp scratch of the warp-cooperative arc loops: accumulators of the current chunk of
+// 32 items (one per lane) and the rank -> lane table of the chunk's items that have arcs.
+struct WarpScratch {
+  unsigned long long acc[32];
+  uint32_t acci[32];
+  uint32_t flags[32];
+  uint8_t table[32];
+};
+
 struct CtaCtl {
   uint32_t err, ovf, nsrc, cursor;
   unsigned long long edges, verts;
@@ -65,6 +75,7 @@ struct CtaCtl {
   uint32_t scan_total, pad1, pad2, pad3;
   SlotCtl slot[kMaxSlots];
   TeamCtl team[kMaxTeams];
+  WarpScratch warp[32];
 };
 
 // One realization in flight on the global-memory counting path.  The arrays are carved from
@@ -99,6 +110,13 @@ int counts_ranges(int nprob, const afc_mc_problem *probs, const uint32_t *r_begi
                   void *workspace, size_t ws_bytes, cudaStream_t stream);
 size_t counts_ranges_workspace(int nprob, const afc_mc_problem *probs, const uint32_t *r_count);
 int report_error(int code, const char *msg);
+
+// api.cu: result handle from dense counts and solve outputs; host query of a graph handle
+afc_result *build_result(int32_t n, uint32_t R, const uint32_t *dense, const double *b,
+                         const double *mu, double expected_T, double b_f, double max_rowsum_N,
+                         int32_t c, const afc_mc_stats &stats, double alpha, double eta,
+                         const double *s, const double *f, double tie_rel, void *stream);
+afc_host_query host_query_of(const afc_graph *g, const afc_params *p, uint32_t n_perturb);
 
 // mc_kernel.cu
 uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots);

@@ -158,12 +158,50 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, 
   return lo;
 }
 
+// Warp-cooperative loop over the arcs of up to 32 items, one per lane: lane j holds an item
+// with `deg` arcs starting at arc index `e0` (deg 0: nothing to do).  The warp walks the
+// concatenation of the items' arc ranges in windows of 32 positions, lane L taking position
+// w0 + L, so a warp's time follows its total arc count instead of its heaviest lane.  For
+// each position f(valid, owner_lane, arc_index) runs on every lane (valid = false past the
+// end); f fetches the owner's item data with __shfl_sync from owner_lane.  All 32 lanes must
+// call it (warp-uniform control flow).  Returns at once when no lane has arcs.
+template <typename F>
+__device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *table, F &&f) {
+  const uint32_t lane = lane_id();
+  const uint32_t nz = __ballot_sync(kFull, deg > 0);
+  if (nz == 0u) return;
+  uint32_t incl = deg;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  const uint32_t tot = __shfl_sync(kFull, incl, 31);
+  const uint32_t excl = incl - deg;
+  if (deg > 0) table[__popc(nz & lanemask_lt())] = (uint8_t)lane;
+  __syncwarp();
+  uint32_t prior = 0;   // items whose range starts before the window
+  for (uint32_t w0 = 0; w0 < tot; w0 += 32u) {
+    const uint32_t rel = excl - w0;   // wraps (large) when the range starts before w0
+    const uint32_t starts = __reduce_or_sync(kFull, (deg > 0 && rel < 32u) ? (1u << rel) : 0u);
+    const uint32_t pos = w0 + lane;
+    const bool valid = pos < tot;
+    const uint32_t rank = prior + __popc(starts & (0xFFFFFFFFu >> (31u - lane))) - 1u;
+    const uint32_t ol = valid ? (uint32_t)table[rank] : 0u;
+    const uint32_t oex = __shfl_sync(kFull, excl, ol);
+    const uint32_t oe0 = __shfl_sync(kFull, e0, ol);
+    f(valid, ol, oe0 + (pos - oex));
+    prior += __popc(starts);
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------------------
 // A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) advanced in lockstep by
 // one team.  Adds delta_s(v) to bc[v] for v != s.  With want_delta = false it stops after
 // distances and path counts (parity hook).  Every thread of the team must call it.
 // ---------------------------------------------------------------------------------------
-template <int TS, int BLOCK, typename DT>
+template <int TS, int BLOCK, typename DT, bool FLAT = false>
 __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H,
                                               const SlotSpace &sp, uint32_t slot0, uint32_t S,
                                               const uint16_t *srcs, uint32_t dsh, double *bc,
@@ -177,6 +215,7 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
   uint32_t my_err = 0, my_ovf = 0;
   const uint32_t lane = tid & 31u, warp = tid >> 5;
   constexpr uint32_t NW = TS / 32;
+  WarpScratch *ws = &ctl->warp[threadIdx.x >> 5];
 
   // ---- init
   for (uint32_t i = 0; i < S; ++i) {
@@ -266,34 +305,48 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
     }
     for (uint32_t i = tid; i < S; i += TS) sl[i].ring_mask &= ~(1u << rs);
     team.sync();
-    // relaxation passes until no member of the bucket improves
+    // relaxation passes until no member of the bucket improves; a pass takes the members in
+    // chunks of 32 per warp and relaxes their arcs warp-cooperatively
     for (uint32_t pass = 0;; ++pass) {
       if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
       slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
       team.sync();
       const uint32_t total = tc->pref[S];
       bool improved = false;
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(sp, slot0 + i);
-        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-        if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t d = a.dist[v];
-        if ((uint64_t)d == a.sig[v]) continue;
-        a.sig[v] = d;
-        const uint32_t e1 = H.rp[v + 1];
-        for (uint32_t e = H.rp[v]; e < e1; ++e) {
+      for (uint32_t base = 0; base < total; base += TS) {
+        const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+        uint32_t i = 0, d = 0, e0 = 0, deg = 0;
+        if (k < total) {
+          i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(sp, slot0 + i);
+          const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
+          if (v >= n) {
+            my_err |= kErrCapacity;
+          } else {
+            d = a.dist[v];
+            if ((uint64_t)d != a.sig[v]) {   // not yet relaxed at its current distance
+              a.sig[v] = d;
+              e0 = H.rp[v];
+              deg = H.rp[v + 1] - e0;
+            }
+          }
+        }
+        warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+          const uint32_t oi = __shfl_sync(kFull, i, ol);
+          const uint32_t od = __shfl_sync(kFull, d, ol);
+          if (!valid) return;
+          SlotArrays a = slot_arrays(sp, slot0 + oi);
           const uint32_t pk = H.arc[e];
           const uint32_t u = pk & 0xFFFFu;
-          const uint32_t nd = d + (pk >> 16);
+          const uint32_t nd = od + (pk >> 16);
           const uint32_t cur = a.dist[u];
-          if ((cur & kFlag) || nd >= cur) continue;
+          if ((cur & kFlag) || nd >= cur) return;
           const uint32_t old = atomicMin(&a.dist[u], nd);
-          if (nd >= old) continue;
+          if (nd >= old) return;
           if (nd < dend) {
             improved = true;
             if (old >= dend) {
-              const uint32_t pos = warp_append_keyed(&sl[i].nm, i);
+              const uint32_t pos = warp_append_keyed(&sl[oi].nm, oi);
               if (pos < n) { a.ord[pos] = (uint16_t)u; a.sig[u] = kNoRelax; }
               else my_err |= kErrCapacity;
             }
@@ -301,9 +354,10 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             const uint32_t r2 = (nd >> dsh) & kRingMask;
             const uint32_t bit = 1u << (u & 31u);
             const uint32_t prev = atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
-            if (!(prev & bit) && !(sl[i].ring_mask & (1u << r2))) atomicOr(&sl[i].ring_mask, 1u << r2);
+            if (!(prev & bit) && !(sl[oi].ring_mask & (1u << r2)))
+              atomicOr(&sl[oi].ring_mask, 1u << r2);
           }
-        }
+        });
       }
       if (!team.any(improved)) break;
     }
@@ -315,43 +369,108 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
     team.sync();
     const uint32_t total = tc->pref[S];
     const uint32_t dstart = b << dsh;
-    for (uint32_t pass = 0;; ++pass) {
-      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-      bool open = false;
-      for (uint32_t k = tid; k < total; k += TS) {
-        const uint32_t i = find_slot(tc->pref, S, k);
-        SlotArrays a = slot_arrays(sp, slot0 + i);
-        const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-        if (v >= n) { my_err |= kErrCapacity; continue; }
-        const uint32_t dv = a.dist[v];
-        if (dv & kFlag) continue;
-        uint64_t acc = 0;
-        bool all_final = true;
-        if (v == sl[i].s) {
-          acc = 1;
-        } else {
-          const uint32_t e1 = H.rp[v + 1];
-          for (uint32_t e = H.rp[v]; e < e1; ++e) {
+    if constexpr (FLAT) {
+    // warp-cooperative: all arcs of the open members, sums through per-warp accumulators
+      for (uint32_t pass = 0;; ++pass) {
+        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+        bool open = false;
+        for (uint32_t base = 0; base < total; base += TS) {
+          const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+          uint32_t i = 0, v = 0, dv = 0, e0 = 0, deg = 0;
+          ws->acc[lane] = 0ull;
+          ws->flags[lane] = 0u;
+          if (k < total) {
+            i = find_slot(tc->pref, S, k);
+            SlotArrays a = slot_arrays(sp, slot0 + i);
+            v = a.ord[sl[i].mstart + k - tc->pref[i]];
+            if (v >= n) {
+              my_err |= kErrCapacity;
+            } else {
+              dv = a.dist[v];
+              if (!(dv & kFlag)) {
+                if (v == sl[i].s) {
+                  a.sig[v] = 1ull;
+                  __threadfence_block();
+                  st_volatile(&a.dist[v], dv | kFlag);
+                } else {
+                  e0 = H.rp[v];
+                  deg = H.rp[v + 1] - e0;
+                }
+              }
+            }
+          }
+          // sum sigma over the predecessors; one that is not final yet leaves the member open
+          warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+            const uint32_t oi = __shfl_sync(kFull, i, ol);
+            const uint32_t odv = __shfl_sync(kFull, dv, ol);
+            if (!valid) return;
+            SlotArrays a = slot_arrays(sp, slot0 + oi);
             const uint32_t pk = H.arc[e];
             const uint32_t u = pk & 0xFFFFu;
             const uint32_t du = a.dist[u];
-            if ((du & kMask) + (pk >> 16) != dv) continue;
-            if (!(du & kFlag)) { all_final = false; break; }
+            if ((du & kMask) + (pk >> 16) != odv) return;
+            if (!(du & kFlag)) { atomicOr(&ws->flags[ol], 1u); return; }
             if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
-            const uint64_t nx = acc + a.sig[u];
-            if (nx < acc) my_ovf = 1;
-            acc = nx;
+            const unsigned long long x = a.sig[u];
+            const unsigned long long prev = atomicAdd(&ws->acc[ol], x);
+            if (prev + x < prev) my_ovf = 1;
+          });
+          if (deg > 0) {
+            SlotArrays a = slot_arrays(sp, slot0 + i);
+            if (!(ws->flags[lane] & 1u)) {
+              a.sig[v] = ws->acc[lane];
+              __threadfence_block();
+              st_volatile(&a.dist[v], dv | kFlag);
+            } else {
+              open = true;
+            }
+          }
+          __syncwarp();
+        }
+        if (!team.any(open)) break;
+      }
+    } else {
+    // one member per thread, stopping at the first predecessor that is not final
+      for (uint32_t pass = 0;; ++pass) {
+        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+        bool open = false;
+        for (uint32_t base = 0; base < total; base += TS) {
+          const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+          if (k >= total) continue;
+          const uint32_t i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(sp, slot0 + i);
+          const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
+          if (v >= n) { my_err |= kErrCapacity; continue; }
+          const uint32_t dv = a.dist[v];
+          if (dv & kFlag) continue;
+          uint64_t acc = 0;
+          bool all_final = true;
+          if (v == sl[i].s) {
+            acc = 1;
+          } else {
+            const uint32_t e1 = H.rp[v + 1];
+            for (uint32_t e = H.rp[v]; e < e1; ++e) {
+              const uint32_t pk = H.arc[e];
+              const uint32_t u = pk & 0xFFFFu;
+              const uint32_t du = a.dist[u];
+              if ((du & kMask) + (pk >> 16) != dv) continue;
+              if (!(du & kFlag)) { all_final = false; break; }
+              if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
+              const uint64_t nx = acc + a.sig[u];
+              if (nx < acc) my_ovf = 1;
+              acc = nx;
+            }
+          }
+          if (all_final) {
+            a.sig[v] = acc;
+            __threadfence_block();
+            st_volatile(&a.dist[v], dv | kFlag);
+          } else {
+            open = true;
           }
         }
-        if (all_final) {
-          a.sig[v] = acc;
-          __threadfence_block();
-          st_volatile(&a.dist[v], dv | kFlag);
-        } else {
-          open = true;
-        }
+        if (!team.any(open)) break;
       }
-      if (!team.any(open)) break;
     }
     if (!ok) break;
     for (uint32_t i = tid; i < S; i += TS) sl[i].mstart = min(sl[i].nm, n);
@@ -415,63 +534,154 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
       team.sync();
       const uint32_t total = tc->pref[S];
       const uint32_t dlo = bcur << dsh, dhi = dlo + (1u << dsh);
-      for (uint32_t pass = 0;; ++pass) {
-        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-        bool open = false;
-        for (uint32_t k = tid; k < total; k += TS) {
-          const uint32_t i = find_slot(tc->pref, S, k);
-          SlotArrays a = slot_arrays(sp, slot0 + i);
-          const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
-          if (v >= n) { my_err |= kErrCapacity; continue; }
-          const uint32_t dv = a.dist[v];
-          if (!(dv & kFlag)) continue;
-          const uint32_t dvm = dv & kMask;
-          uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
-          DT acc_f = 0;           // sum of the other rho
-          bool integral = true, all_final = true;
-          const uint32_t e1 = H.rp[v + 1];
-          for (uint32_t e = H.rp[v]; e < e1; ++e) {
-            const uint32_t pk = H.arc[e];
-            const uint32_t w = pk & 0xFFFFu;
-            const uint32_t dw = a.dist[w];
-            if ((dw & kMask) != dvm + (pk >> 16)) continue;
-            if (dw & kFlag) { all_final = false; break; }
-            if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
-            const uint64_t rw = a.sig[w];
-            if (rw & kIntTag) {
-              acc_i += (uint32_t)rw;
-            } else {
-              acc_f += *reinterpret_cast<const DT *>(&rw);
-              integral = false;
+      (void)dlo;
+      if constexpr (FLAT) {
+        for (uint32_t pass = 0;; ++pass) {
+          if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+          bool open = false;
+          for (uint32_t base = 0; base < total; base += TS) {
+            const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+            uint32_t i = 0, v = 0, dvm = 0, e0 = 0, deg = 0;
+            ws->acc[lane] = 0ull;     // FP part of the successors' rho (as DT)
+            ws->acci[lane] = 0u;      // integral part
+            ws->flags[lane] = 0u;     // bit 0: a successor is pending; bit 1: some rho not integral
+            if (k < total) {
+              i = find_slot(tc->pref, S, k);
+              SlotArrays a = slot_arrays(sp, slot0 + i);
+              v = a.ord[sl[i].lo + k - tc->pref[i]];
+              if (v >= n) {
+                my_err |= kErrCapacity;
+              } else {
+                const uint32_t dv = a.dist[v];
+                if (dv & kFlag) {
+                  dvm = dv & kMask;
+                  e0 = H.rp[v];
+                  deg = H.rp[v + 1] - e0;
+                  if (deg == 0) deg = 0x80000000u;   // marker: pending, no arcs
+                }
+              }
             }
-          }
-          if (!all_final) { open = true; continue; }
-          const uint64_t sg = a.sig[v];
-          const bool is_src = (v == sl[i].s);
-          if (sg == 1ull && integral) {
-            // delta(v) = sum of the successors' subtree sizes: exact in integers
-            a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-            if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
-          } else {
-            const DT acc = (DT)acc_i + acc_f;
-            DT dep, rho;
-            if (sg == 1ull) {
-              dep = acc;
-              rho = (DT)1 + dep;
-            } else {
-              const DT sv = (DT)sg;
-              dep = sv * acc;
-              rho = ((DT)1 + dep) / sv;
+            const bool pending = deg != 0;
+            if (deg == 0x80000000u) deg = 0;
+            warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+              const uint32_t oi = __shfl_sync(kFull, i, ol);
+              const uint32_t odv = __shfl_sync(kFull, dvm, ol);
+              if (!valid) return;
+              SlotArrays a = slot_arrays(sp, slot0 + oi);
+              const uint32_t pk = H.arc[e];
+              const uint32_t w = pk & 0xFFFFu;
+              const uint32_t dw = a.dist[w];
+              if ((dw & kMask) != odv + (pk >> 16)) return;
+              if (dw & kFlag) { atomicOr(&ws->flags[ol], 1u); return; }
+              if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
+              const uint64_t rw = a.sig[w];
+              if (rw & kIntTag) {
+                atomicAdd(&ws->acci[ol], (uint32_t)rw);
+              } else {
+                atomicAdd(reinterpret_cast<DT *>(&ws->acc[ol]), *reinterpret_cast<const DT *>(&rw));
+                atomicOr(&ws->flags[ol], 2u);
+              }
+            });
+            if (pending) {
+              SlotArrays a = slot_arrays(sp, slot0 + i);
+              const uint32_t fl = ws->flags[lane];
+              if (fl & 1u) {
+                open = true;
+              } else {
+                const uint32_t acc_i = ws->acci[lane];
+                const unsigned long long accbits = ws->acc[lane];
+                const DT acc_f = *reinterpret_cast<const DT *>(&accbits);
+                const uint64_t sg = a.sig[v];
+                const bool is_src = (v == sl[i].s);
+                if (sg == 1ull && !(fl & 2u)) {
+                  // delta(v) = sum of the successors' subtree sizes: exact in integers
+                  a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
+                  if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+                } else {
+                  const DT acc = (DT)acc_i + acc_f;
+                  DT dep, rho;
+                  if (sg == 1ull) {
+                    dep = acc;
+                    rho = (DT)1 + dep;
+                  } else {
+                    const DT sv = (DT)sg;
+                    dep = sv * acc;
+                    rho = ((DT)1 + dep) / sv;
+                  }
+                  uint64_t bits = 0;
+                  *reinterpret_cast<DT *>(&bits) = rho;
+                  a.sig[v] = bits;
+                  if (!is_src) atomicAdd(&bc[v], (double)dep);
+                }
+                __threadfence_block();
+                st_volatile(&a.dist[v], dvm);
+              }
             }
-            uint64_t bits = 0;
-            *reinterpret_cast<DT *>(&bits) = rho;
-            a.sig[v] = bits;
-            if (!is_src) atomicAdd(&bc[v], (double)dep);
+            __syncwarp();
           }
-          __threadfence_block();
-          st_volatile(&a.dist[v], dvm);
+          if (!team.any(open)) break;
         }
-        if (!team.any(open)) break;
+      } else {
+        for (uint32_t pass = 0;; ++pass) {
+          if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+          bool open = false;
+          for (uint32_t base = 0; base < total; base += TS) {
+            const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+            if (k >= total) continue;
+            const uint32_t i = find_slot(tc->pref, S, k);
+            SlotArrays a = slot_arrays(sp, slot0 + i);
+            const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
+            if (v >= n) { my_err |= kErrCapacity; continue; }
+            const uint32_t dv = a.dist[v];
+            if (!(dv & kFlag)) continue;
+            const uint32_t dvm = dv & kMask;
+            uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
+            DT acc_f = 0;           // sum of the other rho
+            bool integral = true, all_final = true;
+            const uint32_t e1 = H.rp[v + 1];
+            for (uint32_t e = H.rp[v]; e < e1; ++e) {
+              const uint32_t pk = H.arc[e];
+              const uint32_t w = pk & 0xFFFFu;
+              const uint32_t dw = a.dist[w];
+              if ((dw & kMask) != dvm + (pk >> 16)) continue;
+              if (dw & kFlag) { all_final = false; break; }
+              if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
+              const uint64_t rw = a.sig[w];
+              if (rw & kIntTag) {
+                acc_i += (uint32_t)rw;
+              } else {
+                acc_f += *reinterpret_cast<const DT *>(&rw);
+                integral = false;
+              }
+            }
+            if (!all_final) { open = true; continue; }
+            const uint64_t sg = a.sig[v];
+            const bool is_src = (v == sl[i].s);
+            if (sg == 1ull && integral) {
+              // delta(v) = sum of the successors' subtree sizes: exact in integers
+              a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
+              if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+            } else {
+              const DT acc = (DT)acc_i + acc_f;
+              DT dep, rho;
+              if (sg == 1ull) {
+                dep = acc;
+                rho = (DT)1 + dep;
+              } else {
+                const DT sv = (DT)sg;
+                dep = sv * acc;
+                rho = ((DT)1 + dep) / sv;
+              }
+              uint64_t bits = 0;
+              *reinterpret_cast<DT *>(&bits) = rho;
+              a.sig[v] = bits;
+              if (!is_src) atomicAdd(&bc[v], (double)dep);
+            }
+            __threadfence_block();
+            st_volatile(&a.dist[v], dvm);
+          }
+          if (!team.any(open)) break;
+        }
       }
       if (!ok) break;
       for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].lo;

@@ -121,12 +121,14 @@ big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngro
       team.sync();
       if (k0 >= nsrc) break;
       const uint32_t S = min(spt, nsrc - k0);
+      // warp-cooperative sigma and delta passes (FLAT): measured faster here, where buckets
+      // hold many members, and slower on the shared-memory path's small buckets
       if (mode == 1)
-        brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, G.src + k0, dsh, G.bc,
-                                        G.bci, true, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, float, true>(team, H, sp, team.id * spt, S, G.src + k0, dsh,
+                                              G.bc, G.bci, true, ctl, &G.err, &G.ovf);
       else
-        brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, G.src + k0, dsh, G.bc,
-                                         G.bci, true, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, double, true>(team, H, sp, team.id * spt, S, G.src + k0, dsh,
+                                               G.bc, G.bci, true, ctl, &G.err, &G.ovf);
     }
   }
 }

@@ -33,11 +33,14 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
   team.id = threadIdx.x / TS;
   team.rank = threadIdx.x % TS;
   team.tc = &ctl->team[team.id];
-  const uint32_t nslots = NT * spt;
   for (uint64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
     int g = 0;
     while (g + 1 < nprob && item_prefix[g + 1] <= item) ++g;
     const McDev &P = probs[g];
+    // sources per team: per problem in a batched launch (small graphs take more slots of the
+    // launch's shared memory), else the launch's value
+    const uint32_t spt_g = P.spt ? P.spt : spt;
+    const uint32_t nslots = NT * spt_g;
     const uint32_t r_local = (uint32_t)(item - item_prefix[g]);
     const uint32_t r = P.r_begin + r_local;
     const uint32_t n = P.n;
@@ -109,18 +112,18 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
         __syncthreads();
       }
       for (;;) {
-        if (team.rank == 0) team.tc->claim = atomicAdd(&ctl->cursor, spt);
+        if (team.rank == 0) team.tc->claim = atomicAdd(&ctl->cursor, spt_g);
         team.sync();
         const uint32_t k0 = team.tc->claim;
         team.sync();
         if (k0 >= nsrc) break;
-        const uint32_t S = min(spt, nsrc - k0);
+        const uint32_t S = min(spt_g, nsrc - k0);
         if (use32)
-          brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, src + k0, dsh, bc, bci,
+          brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt_g, S, src + k0, dsh, bc, bci,
                                           true, ctl, &ctl->err, &ctl->ovf);
         else
-          brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, src + k0, dsh, bc, bci,
-                                           true, ctl, &ctl->err, &ctl->ovf);
+          brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt_g, S, src + k0, dsh, bc,
+                                           bci, true, ctl, &ctl->err, &ctl->ovf);
       }
       __syncthreads();
       // betweenness = integral part (unique-path subtrees, exact) + floating part

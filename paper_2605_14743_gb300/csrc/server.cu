@@ -66,6 +66,7 @@ struct Job {
   int status = AFC_OK;
   std::string err;
   int state = kWaiting;
+  bool want_counts = false;   // submitted through afc_submit: the result carries the counts
 };
 
 using JobP = std::shared_ptr<Job>;
@@ -100,7 +101,7 @@ struct afc_server {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   // statistics
-  afc_server_stats st{};
+  afc_serving_stats st{};
   std::vector<double> lat_ms, wait_ms;
   double t_first = -1.0, t_last = 0.0;
 };
@@ -340,7 +341,7 @@ int finish(afc_server *S, Job &j) {
     cudaMemcpyAsync(j.mu.data(), mu, 8 * (size_t)n, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(scal, sc, sizeof(scal), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&j.res.stats, j.stats, sizeof(afc_mc_stats), cudaMemcpyDeviceToHost, s);
-    if (S->cfg.keep_counts) {
+    if (S->cfg.keep_counts || j.want_counts) {
       j.counts_h.resize((size_t)n * ((size_t)n + 1));
       cudaMemcpyAsync(j.counts_h.data(), j.counts, 4 * j.counts_h.size(), cudaMemcpyDeviceToHost, s);
     }
@@ -445,9 +446,14 @@ int afc_server_create(const afc_server_cfg *cfg, afc_server **out) {
   return AFC_OK;
 }
 
-int afc_server_submit(afc_server *S, const afc_host_query *q, uint64_t *ticket) {
+}  // extern "C"
+
+namespace {
+
+int submit_job(afc_server *S, const afc_host_query *q, bool want_counts, uint64_t *ticket) {
   if (!S || !q || !ticket) return afc::report_error(AFC_EINVAL, "null argument");
   auto j = std::make_shared<Job>();
+  j->want_counts = want_counts;
   j->t_submit = now_s();
   j->q = *q;
   j->n = q->n;
@@ -521,6 +527,42 @@ int afc_server_submit(afc_server *S, const afc_host_query *q, uint64_t *ticket) 
   return AFC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int afc_server_submit(afc_server *S, const afc_host_query *q, uint64_t *ticket) {
+  return submit_job(S, q, false, ticket);
+}
+
+int afc_submit(afc_server *S, const afc_graph *g, const afc_params *p, uint64_t *ticket) {
+  if (!g || !p) return afc::report_error(AFC_EINVAL, "null argument");
+  const afc_host_query q = afc::host_query_of(g, p, 0);
+  return submit_job(S, &q, true, ticket);
+}
+
+int afc_poll(afc_server *S, uint64_t ticket, afc_result **out) {
+  if (!S || !out) return afc::report_error(AFC_EINVAL, "null argument");
+  *out = nullptr;
+  JobP j;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(ticket);
+    if (it == S->jobs.end()) return afc::report_error(AFC_EINVAL, "unknown or collected ticket");
+    if (it->second->state != kDone) return AFC_EBUSY;
+    j = it->second;
+    S->jobs.erase(it);
+  }
+  if (j->status != AFC_OK) return afc::report_error(j->status, j->err.c_str());
+  if (j->counts_h.empty()) return afc::report_error(AFC_EINVAL, "query was not submitted with afc_submit");
+  *out = afc::build_result(j->n, j->q.realizations, j->counts_h.data(), j->b.data(), j->mu.data(),
+                           j->res.expected_T, j->res.b_f, j->res.max_rowsum_N, j->res.c,
+                           j->res.stats, j->q.alpha, j->q.absorb_floor,
+                           j->s.empty() ? nullptr : j->s.data(),
+                           j->f.empty() ? nullptr : j->f.data(), j->q.tie_rel, nullptr);
+  return AFC_OK;
+}
+
 int afc_server_poll(afc_server *S, uint64_t ticket, int32_t wait_ms, afc_host_result *res,
                     double *latency_ms) {
   if (!S || !res || !res->b) return afc::report_error(AFC_EINVAL, "null argument");
@@ -546,7 +588,7 @@ int afc_server_poll(afc_server *S, uint64_t ticket, int32_t wait_ms, afc_host_re
   return AFC_OK;
 }
 
-int afc_server_get_stats(afc_server *S, afc_server_stats *out) {
+int afc_server_stats(afc_server *S, afc_serving_stats *out) {
   if (!S || !out) return afc::report_error(AFC_EINVAL, "null argument");
   std::lock_guard<std::mutex> lk(S->mu);
   *out = S->st;

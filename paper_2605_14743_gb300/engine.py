@@ -385,8 +385,8 @@ class Server:
                             np.array(list(r.perturb_counters), np.uint64), lat)
 
     def stats(self) -> dict:
-        from . import afc_server_get_stats
-        st = afc_server_get_stats(self.handle)
+        from . import afc_server_stats
+        st = afc_server_stats(self.handle)
         return {f[0]: getattr(st, f[0]) for f in st._fields_}
 
     def close(self):

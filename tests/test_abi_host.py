@@ -75,3 +75,31 @@ def test_validation_errors_without_device():
     prob.w_lo_all, prob.k_min, prob.block_threads = 1, 1, 48
     with pytest.raises(afc.AfcError):
         afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)
+
+
+def test_graph_handles_and_csr_round_trip():
+    """Graph handles from an edge list and from the symmetric CSR agree; malformed CSR is
+    rejected (host-only calls, no device)."""
+    from afc_inputs import ws_edges
+    eu, ev = ws_edges(60, 4, 0.2, 3)
+    eu, ev = eu.astype(np.int32), ev.astype(np.int32)
+    g = afc.afc_graph_create(60, len(eu), eu, ev)
+    assert afc.afc_graph_nodes(g) == 60 and afc.afc_graph_edges(g) == len(eu)
+    afc.afc_graph_destroy(g)
+    rp, col, eid = afc.engine.host_csr(60, eu, ev)
+    g2 = afc.afc_graph_create_csr(60, rp.astype(np.int64), col, eid)
+    assert afc.afc_graph_edges(g2) == len(eu)
+    afc.afc_graph_destroy(g2)
+    bad = col.copy()
+    bad[0] = (bad[0] + 1) % 60        # breaks the symmetry of one arc
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_graph_create_csr(60, rp.astype(np.int64), bad, eid)
+    assert e.value.code == afc.AFC_EINVAL
+    with pytest.raises(afc.AfcError):
+        afc.afc_graph_create(3, 1, np.array([0], np.int32), np.array([0], np.int32))
+
+
+def test_params_defaults():
+    p = afc.afc_params_default()
+    assert (p.k_min, p.alpha, p.absorb_floor, p.recheck_margin, p.tie_rel) == (5, 0.15, 1e-6, 1e-4, 1e-9)
+    assert p.p_survive_all == 1.0 and p.w_lo_all == p.w_hi_all == 1 and p.precision == afc.AFC_FP64

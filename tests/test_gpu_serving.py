@@ -72,7 +72,7 @@ def test_budget_limits_admission():
 
 
 def test_over_budget_query_is_refused():
-    with afc.Server(hbm_budget=1 << 16) as srv:
+    with afc.Server(hbm_budget=1 << 12) as srv:     # small_er needs ~16 KB
         with pytest.raises(afc.AfcError) as e:
             srv.submit(workload("small_er"))
         assert e.value.code == afc.AFC_EBUSY
