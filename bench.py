@@ -43,6 +43,40 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+# DRAM bytes of one counting launch of the benchmark, from ncu (profiles/counts_traffic.txt); valid
+# only for the kernel sources it was taken on, so the file records their hash.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "counts_traffic.txt")
+KERNEL_SOURCES = ["mc_common.cuh", "mc_kernel.cu", "afc_internal.h", "afc_device.cuh"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2605_14743_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(realizations: int):
+    """DRAM read + write bytes of one counting launch over `realizations`, if the recorded
+    capture was taken on the current kernel sources (else None)."""
+    try:
+        fields = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("source_sha256") != kernel_source_hash():
+            return None
+        if int(fields["realizations_per_launch"]) != realizations:
+            return None
+        return int(fields["dram_bytes_read"]) + int(fields["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -238,7 +272,7 @@ def run_ours(args):
     peaks, src = _peaks()
     achieved = alg_bytes / (kavg / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(R),
             "peak_source": f"{src} HBM copy bandwidth",
             "kernel": "mc_counts_kernel", "kernel_ms": kavg,
             "model": f"{BYTES_PER_ARC} B per alive arc + {BYTES_PER_VERTEX} B per vertex per source"}

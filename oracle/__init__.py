@@ -64,6 +64,9 @@ def _declare(L):
     L.orc_select.argtypes = [i32, P, P, P, u32, P, u32, f64, P]
     L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
                                         u32, u32, u32, P, u32, f64, P, P]
+    L.orc_topk_order.argtypes = [i32, P, P, P, u32, u32, f64, P, P]
+    L.orc_count_rewards.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P, u32,
+                                    u32, u32, f64, u32, P, P, u32, P, P]
     L.orc_gauss_solve.argtypes = [i32, P, P, i32]
     L.orc_assemble_q.argtypes = [i32, P, u32, f64, f64, P, P]
     L.orc_afc_from_q.argtypes = [i32, P, P, P, P, P, P, P]
@@ -75,7 +78,7 @@ def _declare(L):
     L.orc_perturb_sweep.argtypes = [i32, P, P, P, u32, u32, f64, f64, u64, i32, i32, i32, f64,
                                     P, P, P, P, P, P]
     for name in ("orc_build_csr", "orc_components", "orc_sssp", "orc_brandes",
-                 "orc_count_transitions", "orc_gauss_solve", "orc_afc_from_q", "orc_solve_full",
+                 "orc_count_transitions", "orc_count_rewards", "orc_gauss_solve", "orc_afc_from_q", "orc_solve_full",
                  "orc_solve_reduced", "orc_certificates", "orc_perturb_sweep"):
         getattr(L, name).restype = ctypes.c_int
 
@@ -261,6 +264,59 @@ def count_transitions_parallel(g: Graph, seed, graph_tag, r_begin, r_count, p_su
         counts += c
         ovf += o
     return counts.astype(np.uint32), ovf, threads
+
+
+def topk_order(n, comp, csize, bc, k_min, k, tie_rel=1e-9):
+    """Ordered local Top-k per valid component root: array [n, k] (pi(1), pi(2), ...; -1
+    past |K| and on roots of invalid components / non-roots)."""
+    order = np.zeros((n, k), np.int32)
+    taken = np.zeros(max(n, 1), np.uint8)
+    lib().orc_topk_order(n, _p(np.ascontiguousarray(comp, np.int32)),
+                         _p(np.ascontiguousarray(csize, np.int32)),
+                         _p(np.ascontiguousarray(bc, np.float64)), k_min, k, tie_rel,
+                         _p(order), _p(taken))
+    return order
+
+
+def count_rewards(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                  reward_k=0, gamma=None, pool=None, report_rank=1, tie_rel=1e-9):
+    """(counts [n, n+1] with the rank-`report_rank` node reported, psi_sum [n] = sum over
+    the realizations of the valued Top-`reward_k` step reward of each anchor)."""
+    th, th_all = thresholds(p_survive, g.m)
+    lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
+    hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
+    gam = None if gamma is None else np.ascontiguousarray(gamma, np.float64)
+    pl = candidate_mask(g.n, pool)
+    counts = np.zeros((g.n, g.n + 1), np.uint32)
+    psi = np.zeros(max(g.n, 1), np.float64)
+    st = lib().orc_count_rewards(
+        g.n, g.m, _p(g.row_ptr), _p(g.col), _p(g.eid), seed, graph_tag, r_begin, r_count,
+        _p(th), th_all, _p(lo_arr), _p(hi_arr),
+        0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
+        k_min, tie_rel, reward_k, _p(gam), _p(pl), report_rank, _p(counts), _p(psi))
+    if st not in (ORC_OK, ORC_EOVERFLOW):
+        _check(st, "count_rewards")
+    return counts, psi[:g.n]
+
+
+def reward_afc(b, psi):
+    """Reward-AFC of an expected one-step reward psi (Prop. reward-afc-general,
+    eq. mr-afc-def): s N psi / s N 1 = b . psi."""
+    return float(np.dot(np.asarray(b, np.float64), np.asarray(psi, np.float64)))
+
+
+def topk_psi(psi_sum, R, alpha):
+    """Expected one-step reward of the Top-k step reward under the exogenous stop alpha
+    (the stop coin is independent of the realization and a stopped step earns nothing):
+    psi_i = (1 - alpha) * psi_sum_i / R."""
+    return (1.0 - alpha) * np.asarray(psi_sum, np.float64) / float(R)
+
+
+def switching_psi(Q):
+    """Switching count of Sec. 6.4 (eta_sw(i, j) = 1 for j in V, j != i; 0 into bottom):
+    psi_i = sum_{j != i} Q_ij."""
+    Q = np.asarray(Q, np.float64)
+    return Q.sum(axis=1) - np.diag(Q)
 
 
 # ---------------------------------------------------------------- linear algebra ----

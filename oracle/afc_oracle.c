@@ -24,6 +24,10 @@
  *   orc_certificates                      : Appendix B printed thresholds.
  *   orc_perturb_sweep                     : parity unpinned beyond invariants (no printed
  *                                           values exist for this statistic).
+ *   orc_topk_order / orc_count_rewards    : closed-form orderings (complete graph, star,
+ *                                           path), rank-1 equals orc_select, the Top-1
+ *                                           reward identity b_{1,f} = b.f - s.f / E[T],
+ *                                           exhaustive failure patterns (Hoeffding bound).
  */
 #include <math.h>
 #include <stdint.h>
@@ -407,6 +411,105 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
   }
 out:
   free(alive); free(w); free(comp); free(csize); free(centre); free(src); free(bc);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Ordered local Top-k of every valid component (Sec. 2.3: the component-wise top-k set   */
+/* of eq. topk-comp, the local top-k of Def. local-topk, and the rank-r centre of the      */
+/* remark after the Prop. on set-valued states).  The ordering pi of K repeats the          */
+/* tie-broken centre rule on what is left of K: pi(1) is the centre of K (candidates =     */
+/* K), pi(t) the centre of K minus {pi(1), ..., pi(t-1)}: B* = max over the remaining      */
+/* nodes, ties = {v : B_v >= B* - tie_rel * B*}, smallest id.                              */
+/* order[root * k + t] = pi(t + 1) for t < min(k, |K|) on valid roots (|K| >= k_min),       */
+/* -1 elsewhere.  taken: scratch of n bytes.                                              */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_topk_order(int32_t n, const int32_t *comp, const int32_t *csize, const double *bc,
+                    uint32_t k_min, uint32_t k, double tie_rel, int32_t *order,
+                    uint8_t *taken) {
+  for (size_t q = 0; q < (size_t)n * k; ++q) order[q] = -1;
+  for (int32_t v = 0; v < n; ++v) taken[v] = 0;
+  for (int32_t root = 0; root < n; ++root) {
+    if (comp[root] != root || (uint32_t)csize[root] < k_min) continue;
+    for (uint32_t t = 0; t < k; ++t) {
+      double bstar = -1.0;
+      for (int32_t v = 0; v < n; ++v)
+        if (comp[v] == root && !taken[v] && bc[v] > bstar) bstar = bc[v];
+      if (bstar < 0.0) break; /* K exhausted */
+      const double tau = tie_rel * bstar;
+      int32_t pick = -1;
+      for (int32_t v = 0; v < n && pick < 0; ++v)
+        if (comp[v] == root && !taken[v] && bc[v] >= bstar - tau) pick = v;
+      taken[pick] = 1;
+      order[(size_t)root * k + t] = pick;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Transition counts with a rank-r report and the valued local Top-k step reward          */
+/* (Sec. 6.2 ell^(k,gamma)_i = sum of gamma_v over the local Top-k set of anchor i, and     */
+/* Sec. 6.3 its pool-restricted form over Top-k intersect W_pool).  Per realization and     */
+/* anchor i with a valid component K = K(i):                                               */
+/*   next(i) = pi_K(report_rank) if |K| >= report_rank, else bottom (report_rank = 1 is the  */
+/*   tie-broken centre of orc_select with no candidate pool and no rank cutoff);            */
+/*   psi_sum[i] += sum_{t < min(reward_k, |K|)} gamma[pi_K(t+1)] * [pi_K(t+1) in pool]      */
+/* (gamma NULL: 1; pool NULL: every node); an anchor of an invalid component adds nothing   */
+/* and moves to bottom.  counts and psi_sum may each be NULL; both are accumulated.         */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_count_rewards(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                      const int32_t *eid, uint64_t seed, uint32_t graph_tag,
+                      uint32_t r_begin, uint32_t r_count,
+                      const uint64_t *thresh, uint64_t thresh_all,
+                      const uint32_t *w_lo, const uint32_t *w_hi,
+                      uint32_t w_lo_all, uint32_t w_hi_all,
+                      uint32_t k_min, double tie_rel, uint32_t reward_k, const double *gamma,
+                      const uint8_t *pool, uint32_t report_rank, uint32_t *counts,
+                      double *psi_sum) {
+  if (report_rank < 1) return ORC_EINVAL;
+  const uint32_t k = reward_k > report_rank ? reward_k : report_rank;
+  size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
+  uint8_t *alive = (uint8_t *)malloc(mm);
+  uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
+  int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *csize = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint8_t *src = (uint8_t *)malloc(nn);
+  double *bc = (double *)malloc(sizeof(double) * nn);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * nn * k);
+  int status = ORC_OK;
+  if (!alive || !w || !comp || !csize || !src || !bc || !order) { status = ORC_ENOMEM; goto out; }
+  for (uint32_t q = 0; q < r_count; ++q) {
+    uint32_t r = r_begin + q;
+    orc_realize(m, seed, graph_tag, r, thresh, thresh_all, w_lo, w_hi, w_lo_all, w_hi_all, alive, w);
+    int st = orc_components(n, row_ptr, col, eid, alive, comp, csize);
+    if (st != ORC_OK) { status = st; goto out; }
+    for (int32_t v = 0; v < n; ++v) src[v] = (uint32_t)csize[comp[v]] >= k_min ? 1 : 0;
+    st = orc_brandes(n, row_ptr, col, eid, alive, w, src, bc);
+    if (st == ORC_ENOMEM) { status = st; goto out; }
+    if (st == ORC_EOVERFLOW) status = ORC_EOVERFLOW;
+    orc_topk_order(n, comp, csize, bc, k_min, k, tie_rel, order, src);
+    for (int32_t i = 0; i < n; ++i) {
+      const int32_t *pi = order + (size_t)comp[i] * k;
+      if (counts) {
+        const int32_t c = pi[report_rank - 1];
+        counts[(size_t)i * (size_t)(n + 1) + (c < 0 ? (size_t)n : (size_t)c)] += 1u;
+      }
+      if (psi_sum) {
+        double ell = 0.0;
+        for (uint32_t t = 0; t < reward_k; ++t) {
+          const int32_t v = pi[t];
+          if (v < 0) break;
+          if (pool && !pool[v]) continue;
+          ell += gamma ? gamma[v] : 1.0;
+        }
+        psi_sum[i] += ell;
+      }
+    }
+  }
+out:
+  free(alive); free(w); free(comp); free(csize); free(src); free(bc); free(order);
   return status;
 }
 

@@ -255,8 +255,10 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
     const uint32_t rs = b & kRingMask;
     const uint32_t dend = (b + 1u) << dsh;
     // extraction of bucket b into the member lists, appends aggregated per warp and slot
-    for (uint32_t base = warp * 32u; base < S * W; base += TS) {
-      const uint32_t item = base + lane;
+    // words interleaved over the team's warps (item increases with the lane, so the lanes of
+    // one slot stay contiguous for the keyed prefix below)
+    for (uint32_t base = 0; base < S * W; base += TS) {
+      const uint32_t item = base + lane * NW + warp;
       uint32_t i = 0xFFFFu, live = 0;
       uint16_t vb = 0;
       if (item < S * W) {
