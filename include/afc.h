@@ -112,6 +112,18 @@ typedef struct {
                              /* fits in shared memory run there, others on the global-     */
                              /* memory path; AFC_PATH_SHARED / AFC_PATH_GLOBAL force one   */
                              /* (AFC_EUNSUPPORTED if the shared path does not fit)          */
+  /* Simulator-level rewards (Sec. 6) and rank-r reports.  The ordering pi of a valid        */
+  /* component K repeats the centre rule on the nodes of K not yet listed (B* over the rest, */
+  /* the tie_rel band, smallest id), so pi(1) is the centre (Sec. 2.3 eq. topk-comp).        */
+  uint32_t reward_k;         /* 0: off.  k > 0: every anchor of a valid component adds the  */
+                             /* valued Top-k step reward sum_{t <= min(k,|K|)} gamma[pi(t)]  */
+                             /* over pi(t) in reward_pool (Sec. 6.2-6.3) to psi_sum[anchor]  */
+  const double *reward_gamma;  /* [n] DEVICE node values gamma >= 0, or NULL = 1           */
+  const uint8_t *reward_pool;  /* [n] DEVICE pool mask W, or NULL = every node             */
+  double *psi_sum;           /* [n] DEVICE accumulator (not cleared); required with reward_k */
+  uint32_t report_rank;      /* 0 or 1: report the centre; r > 1: report pi(r), the rank-r   */
+                             /* centre (bottom if |K| < r).  reward_k > 0 or report_rank > 1 */
+                             /* needs AFC_FP64, in_w NULL, top_k 0 and at most 256 ranks      */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */
@@ -210,6 +222,16 @@ int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const in
                         const int32_t *c_list, int32_t c, double *mu, double *b, double *scalars,
                         double *lu, int32_t *piv, void *workspace, size_t workspace_bytes,
                         void *stream);
+
+/* Reward-AFC of the simulator-level rewards (Prop. reward-afc-general: s N psi / s N 1 =
+ * b . psi for an expected one-step reward psi).  DEVICE out [2]: out[0] = b . psi_topk with
+ * psi_topk_i = (1 - alpha) psi_sum[i] / R (the exogenous stop ends a step without reward; 0
+ * when psi_sum is NULL); out[1] = b . psi_sw, the switching count of Sec. 6.4 (eta_sw(i, j) = 1
+ * for j in V, j != i), psi_sw_i = sum_{j != i} Q_ij with Q assembled as afc_absorbing_solve
+ * does.  DEVICE in: counts [n][n+1], b [n] (afc_absorbing_solve), psi_sum [n] or NULL.
+ * Asynchronous on `stream`. */
+int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double *b,
+                   const double *psi_sum, double *out, void *stream);
 
 /* Allocation-free variant of afc_absorbing_solve (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory themselves, e.g. code embedded in a host framework
@@ -317,9 +339,9 @@ int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream);
  * engineering layer with no counterpart there.  Queries are admitted in arrival order while
  * the device-memory footprint of the admitted ones stays within hbm_budget and at most
  * max_active are admitted.  Every admitted query keeps its graph, parameters and partial
- * counts on the device; a scheduler thread advances all admitted queries together, one
- * batched counting launch per slice (slice_realizations more realizations of each), so a
- * query that arrives while others run joins the next slice.  A query whose realizations are
+ * counts on the device; a scheduler thread advances the admitted queries with the least
+ * remaining work (up to slice_queries of them) by one batched counting launch per slice, so a
+ * query that arrives while others run joins a slice as soon as it is among the shortest.  A query whose realizations are
  * all counted is finished (observed states, absorbing-chain solve, perturbation sweep,
  * device-to-host copy) on a second stream by a finisher thread while counting goes on, and
  * its device memory is released.  Realization r of a query is the same draw whatever else
@@ -334,8 +356,11 @@ typedef struct {
   uint32_t max_active;         /* queries admitted at once; 0 = 64                          */
   uint32_t max_waiting;        /* queue length beyond which submissions are refused         */
                                /* (AFC_EBUSY, counted as shed); 0 = unbounded               */
-  uint32_t slice_realizations; /* realizations per admitted query per slice; 0 = automatic  */
+  uint32_t slice_realizations; /* realizations per query per slice; 0 = automatic (about   */
+                               /* two waves of 1000-node realizations of work per slice)   */
   int32_t keep_counts;         /* 1: results include the [n][n+1] count matrix              */
+  uint32_t slice_queries;      /* queries advanced per slice, least remaining work first;   */
+                               /* 0 = 4                                                     */
 } afc_server_cfg;
 
 typedef struct {

@@ -24,6 +24,7 @@ __all__ = [
     "AfcError", "lib", "McProblem", "McStats", "Chain", "PerturbParams", "HostQuery", "HostResult",
     "afc_last_error", "afc_version", "afc_csr_from_edges", "afc_survival_threshold",
     "afc_transition_counts_workspace", "afc_transition_counts", "afc_counts_path",
+    "afc_reward_afc",
     "afc_transition_counts_batched_workspace", "afc_transition_counts_batched",
     "afc_debug_realize", "afc_debug_components", "afc_debug_sssp", "afc_observed_states",
     "afc_solve_workspace", "afc_absorbing_solve", "afc_perturb_sweep", "afc_certificates",
@@ -62,7 +63,9 @@ class McProblem(ctypes.Structure):
                 ("k_min", c_u32), ("in_w", c_p), ("top_k", c_u32), ("tie_rel", c_f64),
                 ("precision", c_i32), ("recheck_margin", c_f64), ("bucket_width", c_u32),
                 ("block_threads", c_i32), ("team_threads", c_i32),
-                ("slots_per_team", c_i32), ("memory_path", c_i32)]
+                ("slots_per_team", c_i32), ("memory_path", c_i32), ("reward_k", c_u32),
+                ("reward_gamma", c_p), ("reward_pool", c_p), ("psi_sum", c_p),
+                ("report_rank", c_u32)]
 
 
 class McStats(ctypes.Structure):
@@ -102,7 +105,7 @@ class HostResult(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("hbm_budget", c_u64), ("max_active", c_u32), ("max_waiting", c_u32),
-                ("slice_realizations", c_u32), ("keep_counts", c_i32)]
+                ("slice_realizations", c_u32), ("keep_counts", c_i32), ("slice_queries", c_u32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -159,6 +162,7 @@ _SIGS = {
     "afc_run_host": ([ctypes.POINTER(HostQuery), ctypes.POINTER(HostResult), c_p], ctypes.c_int),
     "afc_absorbing_solve_noalloc": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p, c_p],
                                     ctypes.c_int),
+    "afc_reward_afc": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_server_create": ([ctypes.POINTER(ServerCfg), ctypes.POINTER(c_p)], ctypes.c_int),
     "afc_server_submit": ([c_p, ctypes.POINTER(HostQuery), ctypes.POINTER(c_u64)], ctypes.c_int),
     "afc_server_poll": ([c_p, c_u64, c_i32, ctypes.POINTER(HostResult), ctypes.POINTER(c_f64)],
@@ -307,6 +311,11 @@ def afc_absorbing_solve_noalloc(chain, counts, mu, b, scalars, stream):
     """Allocation-free solve for callers that cannot allocate device memory; see afc.h."""
     _chk(lib().afc_absorbing_solve_noalloc(ctypes.byref(chain), _ptr(counts), _ptr(mu), _ptr(b),
                                            _ptr(scalars), _ptr(stream)))
+
+
+def afc_reward_afc(chain, counts, b, psi_sum, out, stream):
+    _chk(lib().afc_reward_afc(ctypes.byref(chain), _ptr(counts), _ptr(b), _ptr(psi_sum),
+                              _ptr(out), _ptr(stream)))
 
 
 def afc_perturb_sweep(chain, pp, counts, c_index, c_list, c, mu0, b0, lu0, piv0, counters,

@@ -83,6 +83,13 @@ int validate(const afc_mc_problem *p) {
   }
   if (p->memory_path < AFC_PATH_AUTO || p->memory_path > AFC_PATH_GLOBAL)
     return fail(AFC_EINVAL, "memory_path must be AFC_PATH_AUTO, _SHARED or _GLOBAL");
+  if (p->reward_k || p->report_rank > 1) {
+    if (p->precision != AFC_FP64 || p->in_w || p->top_k)
+      return fail(AFC_EINVAL, "rewards and rank-r reports need FP64, no candidate pool and no rank cutoff");
+    if (p->reward_k > 256 || p->report_rank > 256)
+      return fail(AFC_EUNSUPPORTED, "at most 256 ranks per component");
+    if (p->reward_k && !p->psi_sum) return fail(AFC_EINVAL, "reward_k needs psi_sum");
+  }
   if (p->m < 0 || p->m > 0x3FFFFFFF) return fail(AFC_EINVAL, "m = %lld out of range", (long long)p->m);
   if (!p->row_ptr || (p->m > 0 && (!p->col || !p->eid)))
     return fail(AFC_EINVAL, "CSR pointers missing");
@@ -129,6 +136,11 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   d.precision = p.precision;
   d.recheck_margin = p.recheck_margin;
   d.delta = auto_delta(p);
+  d.reward_k = p.reward_k;
+  d.reward_gamma = p.reward_gamma;
+  d.reward_pool = p.reward_pool;
+  d.psi = p.psi_sum;
+  d.report_rank = p.report_rank;
   d.r_begin = r_begin;
   d.counts = counts;
   d.stats = stats;
@@ -615,6 +627,16 @@ int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32
   cudaError_t e = launch_certificates(C, mu0, lu0, piv0, eps_bar, r_min, npairs, pu, pv, gap, sharp,
                                       static_cast<unsigned char *>(workspace), L, (cudaStream_t)stream);
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "certificates launch");
+}
+
+int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double *b,
+                   const double *psi_sum, double *out, void *stream) {
+  if (!chain || !counts || !b || !out || chain->n < 1 || chain->realizations == 0)
+    return fail(AFC_EINVAL, "bad arguments");
+  cudaError_t e = launch_reward_afc(chain->n, chain->realizations, chain->alpha,
+                                    chain->absorb_floor, counts, b, psi_sum, out,
+                                    (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "reward_afc");
 }
 
 int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,

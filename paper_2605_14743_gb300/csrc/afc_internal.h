@@ -36,6 +36,11 @@ struct McDev {
   uint32_t delta;
   uint32_t spt;          // shared path: sources per team for this problem (0: launch default)
   uint32_t r_begin;
+  uint32_t reward_k;             // valued Top-k step reward (0: off)
+  const double *reward_gamma;    // [n] or null (1)
+  const uint8_t *reward_pool;    // [n] or null (every node)
+  double *psi;                   // [n] step-reward accumulator
+  uint32_t report_rank;          // 0 / 1: the centre; r > 1: the r-th node of the ordering
   uint32_t *counts;
   afc_mc_stats *stats;
   double *dump_bc;
@@ -171,6 +176,9 @@ cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const doub
                                 const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                                 unsigned char *ws, const SolveWs &L, cudaStream_t stream);
 size_t perturb_slab_bytes(int32_t n, int32_t c);
+cudaError_t launch_reward_afc(int32_t n, uint32_t R, double alpha, double eta,
+                              const uint32_t *counts, const double *b, const double *psi_sum,
+                              double *out, cudaStream_t stream);
 
 // solve_static.cu (allocation-free solve; scratch is a file-scope device array)
 cudaError_t launch_solve_static(int32_t n, uint32_t R, double alpha, double eta, const double *s,

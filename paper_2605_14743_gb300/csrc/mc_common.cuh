@@ -854,12 +854,56 @@ __device__ __forceinline__ void bucket_setup(CtaCtl *ctl, uint32_t delta_req) {
 // for an FP64 recheck (then nothing is committed).
 // ---------------------------------------------------------------------------------------
 __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const uint32_t *comp,
-                                 const uint32_t *cinfo, const double *bc, SlotArrays s0,
-                                 uint32_t *rank, bool gap_test, CtaCtl *ctl) {
+                                        const uint32_t *cinfo, const double *bc, SlotArrays s0,
+                                        uint32_t *rank, uint16_t *mark, bool gap_test,
+                                        CtaCtl *ctl) {
   const uint32_t n = P.n;
   unsigned long long *best = reinterpret_cast<unsigned long long *>(s0.sig);
   uint32_t *centre = s0.dist;
   if (threadIdx.x == 0) ctl->need_recheck = 0;
+  if (P.reward_k || P.report_rank > 1) {
+    // Ordered local Top-k (Sec. 2.3 eq. topk-comp): round t picks the tie-broken centre of the
+    // nodes of K not picked before (B* over the remaining nodes, relative band, smallest id).
+    // Round report_rank - 1 gives the reported node (rank-r centre), rounds below reward_k the
+    // valued Top-k step reward of every anchor of K (Sec. 6.2, pool-restricted: Sec. 6.3).
+    // The host admits this mode only in FP64, without a candidate pool or rank cutoff, where
+    // round 0 is exactly the centre rule below.
+    const uint32_t rr = P.report_rank > 1 ? P.report_rank : 1u;
+    const uint32_t rounds = P.reward_k > rr ? P.reward_k : rr;
+    uint32_t *pick = rank;   // per root: node picked in the current round
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { mark[v] = 0; centre[v] = 0xFFFFFFFFu; }
+    for (uint32_t t = 0; t < rounds; ++t) {
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { best[v] = 0ull; pick[v] = 0xFFFFFFFFu; }
+      __syncthreads();
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+        const uint32_t root = comp[v];
+        if (comp_valid(cinfo[root], P.k_min) && !mark[v])
+          atomicMax(&best[root], (unsigned long long)__double_as_longlong(bc[v]));
+      }
+      __syncthreads();
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+        const uint32_t root = comp[v];
+        if (!comp_valid(cinfo[root], P.k_min) || mark[v]) continue;
+        const double bstar = __longlong_as_double((long long)best[root]);
+        if (bc[v] >= bstar - P.tie_rel * bstar) atomicMin(&pick[root], v);
+      }
+      __syncthreads();
+      for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+        if (comp[v] == v && pick[v] < n) {
+          mark[pick[v]] = 1;
+          if (t == rr - 1) centre[v] = pick[v];
+        }
+        if (t < P.reward_k && P.psi) {
+          const uint32_t p = pick[comp[v]];
+          if (p < n && (P.reward_pool == nullptr || P.reward_pool[p]))
+            atomicAdd(&P.psi[v], P.reward_gamma ? P.reward_gamma[p] : 1.0);
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) rank[v] = 1u;
+    __syncthreads();
+  } else {
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
     best[v] = 0ull; centre[v] = 0xFFFFFFFFu; rank[v] = 1u;
   }
@@ -908,6 +952,7 @@ __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const 
       }
     }
     __syncthreads();
+  }
   }
   if (gap_test && ctl->need_recheck) return true;
   uint32_t *counts = P.counts;

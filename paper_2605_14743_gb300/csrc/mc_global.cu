@@ -147,7 +147,8 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
   s0.sig = reinterpret_cast<uint64_t *>(G.best);
   s0.dist = G.centre;
   const bool recheck =
-      select_and_count(P, G.r_local, G.comp, G.cinfo, G.bc, s0, G.rank, gap_test != 0, ctl);
+      select_and_count(P, G.r_local, G.comp, G.cinfo, G.bc, s0, G.rank, G.src, gap_test != 0,
+                       ctl);
   __syncthreads();
   if (recheck) {
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { G.bc[v] = 0.0; G.bci[v] = 0; }

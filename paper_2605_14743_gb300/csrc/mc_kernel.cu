@@ -129,8 +129,8 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
       // betweenness = integral part (unique-path subtrees, exact) + floating part
       for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) bc[v] += (double)bci[v];
       __syncthreads();
-      const bool recheck = select_and_count(P, r_local, comp, cinfo, bc,
-                                            slot_arrays(sp, 0), sel, use32, ctl);
+      const bool recheck = select_and_count(P, r_local, comp, cinfo, bc, slot_arrays(sp, 0),
+                                            sel, src, use32, ctl);
       __syncthreads();
       if (!recheck) break;
       if (threadIdx.x == 0 && P.stats) atomicAdd(u64p(&P.stats->rechecked), 1ull);

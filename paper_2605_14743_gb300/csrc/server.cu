@@ -6,10 +6,11 @@
 //   scheduler (thread 1) admits queued queries in arrival order while the footprint of the
 //                        admitted ones fits the budget, uploads each admitted query to the
 //                        device once (graph, thresholds, candidate mask, zeroed counts), and
-//                        then loops: one batched counting launch per slice advancing every
-//                        admitted query by its next chunk of realizations, on the counting
-//                        stream; a query whose last chunk is enqueued gets an event and goes
-//                        to the finisher.  At most two slices are in flight.
+//                        then loops: one batched counting launch per slice advancing the
+//                        admitted queries with the least remaining work by their next chunk
+//                        of realizations, on the counting stream; a query whose last chunk is
+//                        enqueued gets an event and goes to the finisher.  At most two slices
+//                        are in flight.
 //   finisher  (thread 2) per counted query, on the finishing stream (waits on its event):
 //                        observed states, absorbing-chain solve, perturbation sweep,
 //                        device-to-host copies; then frees the query's device memory and
@@ -18,6 +19,7 @@
 // changes a query's counts.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -81,6 +83,16 @@ size_t footprint_of(const Job &j) {
   b += 4 * n * (n + 1) + sizeof(afc_mc_stats) + 8 * n;   // counts, stats, observed-state maps
   return b;
 }
+
+// Work of one realization of a query: n single-source problems over its n nodes and 2m arcs.
+double realization_work(const Job &j) {
+  return (double)j.n * ((double)j.n + 2.0 * (double)j.m);
+}
+double remaining_work(const Job &j) {
+  return realization_work(j) * (double)(j.q.realizations - j.next_r);
+}
+// Reference work: one realization of a 1000-node graph with 3000 edges.
+constexpr double kUnitWork = 1000.0 * 7000.0;
 
 }  // namespace
 
@@ -206,18 +218,28 @@ void scheduler_main(afc_server *S) {
         if (j->status == AFC_OK) S->active.push_back(j);
       batch = S->active;
     }
-    // the next slice: a chunk of realizations of every admitted query
+    // The next slice: the admitted queries with the least remaining work first (at most
+    // slice_queries of them), each advanced by a chunk of realizations sized so that the slice
+    // holds about two waves of 1000-node realizations of work: small queries finish within a
+    // few slices and every slice stays short, so new arrivals join quickly.
+    std::sort(batch.begin(), batch.end(), [](const JobP &a, const JobP &b) {
+      const double ca = remaining_work(*a), cb = remaining_work(*b);
+      return ca < cb || (ca == cb && a->ticket < b->ticket);
+    });
+    if (batch.size() > S->cfg.slice_queries) batch.resize(S->cfg.slice_queries);
     std::vector<JobP> done;
     if (!batch.empty()) {
-      const uint32_t na = (uint32_t)batch.size();
-      const uint32_t auto_slice = std::max<uint32_t>(16u, (2u * (uint32_t)S->sms + na - 1) / na);
-      const uint32_t slice = S->cfg.slice_realizations ? S->cfg.slice_realizations : auto_slice;
+      const double share = 2.0 * (double)S->sms * kUnitWork / (double)batch.size();
       std::vector<afc_mc_problem> probs;
       std::vector<uint32_t> rb, rc;
       std::vector<uint32_t *> cnt;
       std::vector<afc_mc_stats *> sts;
       for (JobP &j : batch) {
         const uint32_t left = j->q.realizations - j->next_r;
+        const double per = std::max(1.0, std::floor(share / realization_work(*j)));
+        const uint32_t slice = S->cfg.slice_realizations
+                                   ? S->cfg.slice_realizations
+                                   : (uint32_t)std::min<double>(per, 4096.0);
         const uint32_t k = std::min(left, slice);
         probs.push_back(j->prob);
         rb.push_back(j->next_r);
@@ -431,6 +453,7 @@ int afc_server_create(const afc_server_cfg *cfg, afc_server **out) {
     return afc::report_error(AFC_ECUDA, "no CUDA device");
   cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
   if (S->cfg.max_active == 0) S->cfg.max_active = 64;
+  if (S->cfg.slice_queries == 0) S->cfg.slice_queries = 4;
   if (S->cfg.hbm_budget == 0) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return afc::report_error(AFC_ECUDA, "cudaMemGetInfo");

@@ -5,6 +5,7 @@
 //
 // With the columns of U = V \ C zero, N = (I - Q)^-1 has the block form [[I, Q_UC N_CC],
 // [0, N_CC]] in (U, C) order, so mu_U = s_U and mu_C (I - Q_CC) = s_C + s_U Q_UC.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -333,6 +334,56 @@ certificates_kernel(ChainDev C, const double *mu0, const double *lu0, const int3
     }
     __syncthreads();
   }
+}
+
+// Reward-AFC of the Top-k and switching rewards (warp per count row, partial sums added to
+// out with atomics): out[0] += b_i (1 - alpha) psi_sum_i / R, out[1] += b_i sum_{j != i} Q_ij.
+__global__ void reward_afc_kernel(int32_t n, uint32_t R, double alpha, double eta,
+                                  const uint32_t *counts, const double *b, const double *psi_sum,
+                                  double *out) {
+  __shared__ double red0[33], red1[33];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const size_t stride = (size_t)n + 1;
+  double p0 = 0.0, p1 = 0.0;
+  for (uint32_t i = warp; i < (uint32_t)n; i += nwarps) {
+    const uint32_t *row = counts + (size_t)i * stride;
+    unsigned long long all = 0, self = 0;
+    for (uint32_t j = lane; j < (uint32_t)n; j += 32u) {
+      const uint32_t c = row[j];
+      all += c;
+      if (j == i) self = c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      all += __shfl_xor_sync(0xFFFFFFFFu, all, o);
+      self += __shfl_xor_sync(0xFFFFFFFFu, self, o);
+    }
+    if (lane == 0) {
+      const double q_sum = (1.0 - alpha) * (double)all / (double)R;
+      const double r_i = alpha + (1.0 - alpha) * (double)row[n] / (double)R;
+      const double scale = (r_i == 0.0 && q_sum > 0.0) ? (1.0 - eta) / q_sum : 1.0;
+      p1 += b[i] * (1.0 - alpha) * (double)(all - self) / (double)R * scale;
+      if (psi_sum) p0 += b[i] * (1.0 - alpha) * psi_sum[i] / (double)R;
+    }
+  }
+  const double s0 = block_sum(p0, red0);
+  const double s1 = block_sum(p1, red1);
+  if (threadIdx.x == 0) {
+    atomicAdd(&out[0], s0);
+    atomicAdd(&out[1], s1);
+  }
+}
+
+cudaError_t launch_reward_afc(int32_t n, uint32_t R, double alpha, double eta,
+                              const uint32_t *counts, const double *b, const double *psi_sum,
+                              double *out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), stream);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<int64_t>(((int64_t)n + 7) / 8, 1024);
+  reward_afc_kernel<<<grid, 256, 0, stream>>>(n, R, alpha, eta, counts, b, psi_sum, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const double *lu0,

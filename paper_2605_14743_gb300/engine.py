@@ -61,7 +61,8 @@ def _precision(p):
 
 def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=None,
                  bucket_width: int = 0, block_threads: int = 0, team_threads: int = 0,
-                 slots_per_team: int = 0, memory_path: int = 0) -> McProblem:
+                 slots_per_team: int = 0, memory_path: int = 0, reward_k: int = 0,
+                 reward_gamma=None, reward_pool=None, psi=None, report_rank: int = 0) -> McProblem:
     """McProblem for a workload on device tensors (per-edge arrays optional)."""
     p = McProblem()
     p.n, p.m = dg.n, dg.m
@@ -90,6 +91,11 @@ def make_problem(dg: DeviceGraph, wl, thresh=None, w_lo=None, w_hi=None, in_w=No
     p.team_threads = int(team_threads)
     p.slots_per_team = int(slots_per_team)
     p.memory_path = int(memory_path)
+    p.reward_k = int(reward_k)
+    p.reward_gamma = None if reward_gamma is None else reward_gamma.data_ptr()
+    p.reward_pool = None if reward_pool is None else reward_pool.data_ptr()
+    p.psi_sum = None if psi is None else psi.data_ptr()
+    p.report_rank = int(report_rank)
     return p
 
 
@@ -110,7 +116,8 @@ class Query:
     """All device state of one stochastic-centrality query.  Build once, run many times."""
 
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
-                 slots_per_team=0, stream=None, memory_path=0):
+                 slots_per_team=0, stream=None, memory_path=0, reward_k=0, reward_gamma=None,
+                 reward_pool=None, report_rank=0):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -135,9 +142,19 @@ class Query:
             self.in_w = torch.from_numpy(mask).to(device)
         self.s = None if wl.s_init is None else torch.from_numpy(np.asarray(wl.s_init, np.float64)).to(device)
         self.f = None if wl.reward is None else torch.from_numpy(np.asarray(wl.reward, np.float64)).to(device)
+        # simulator-level rewards (valued / pool-restricted local Top-k) and rank-r reports
+        self.gamma = None if reward_gamma is None else torch.from_numpy(
+            np.ascontiguousarray(reward_gamma, np.float64)).to(device)
+        self.pool = None
+        if reward_pool is not None:
+            pm = np.zeros(n, np.uint8)
+            pm[np.asarray(reward_pool, np.int64)] = 1
+            self.pool = torch.from_numpy(pm).to(device)
+        self.psi = torch.zeros(n, dtype=torch.float64, device=device) if reward_k else None
         self.prob = make_problem(self.graph, wl, self.thresh, self.w_lo, self.w_hi, self.in_w,
                                  bucket_width, block_threads, team_threads, slots_per_team,
-                                 memory_path)
+                                 memory_path, reward_k, self.gamma, self.pool, self.psi,
+                                 report_rank)
         self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
         self.stats = torch.zeros(7, dtype=torch.int64, device=device)
         wsb = afc_transition_counts_workspace(self.prob)
@@ -171,6 +188,8 @@ class Query:
         if zero:
             self.counts.zero_()
             self.stats.zero_()
+            if self.psi is not None:
+                self.psi.zero_()
         r_count = int(self.wl.realizations) if r_count is None else int(r_count)
         afc_transition_counts(self.prob, r_begin, r_count, self.counts, self.stats, dump_bc,
                               dump_next, self.ws_counts, self.ws_counts.numel(), self._stream())
@@ -189,6 +208,13 @@ class Query:
         afc_absorbing_solve(self.chain(), self.counts, self.c_index, self.c_list, c, self.mu, self.b,
                             self.scalars, self.lu, self.piv, self.ws_solve, self.ws_solve.numel(),
                             self._stream())
+
+    def reward_afc(self):
+        """(b . psi_topk, b . psi_switching) after run_solve (reward-AFC, Sec. 6)."""
+        from . import afc_reward_afc
+        out = self.torch.zeros(2, dtype=self.torch.float64, device=self.device)
+        afc_reward_afc(self.chain(), self.counts, self.b, self.psi, out, self._stream())
+        return tuple(float(x) for x in out.cpu().numpy())
 
     def perturb_params(self, p_begin=0, p_count=None, top_k=5, k2=10, hist=16) -> PerturbParams:
         pp = PerturbParams()
@@ -352,11 +378,12 @@ class Server:
     """The native serving loop (afc_server_*): submit workloads at any time, poll results."""
 
     def __init__(self, hbm_budget=0, max_active=0, max_waiting=0, slice_realizations=0,
-                 keep_counts=False):
+                 keep_counts=False, slice_queries=0):
         from . import ServerCfg, afc_server_create
         cfg = ServerCfg()
         cfg.hbm_budget, cfg.max_active, cfg.max_waiting = int(hbm_budget), int(max_active), int(max_waiting)
         cfg.slice_realizations, cfg.keep_counts = int(slice_realizations), int(bool(keep_counts))
+        cfg.slice_queries = int(slice_queries)
         self.keep_counts = bool(keep_counts)
         self.handle = afc_server_create(cfg)
         self.n_of = {}
