@@ -357,7 +357,7 @@ typedef struct {
   uint32_t max_waiting;        /* queue length beyond which submissions are refused         */
                                /* (AFC_EBUSY, counted as shed); 0 = unbounded               */
   uint32_t slice_realizations; /* realizations per query per slice; 0 = automatic (about   */
-                               /* two waves of 1000-node realizations of work per slice)   */
+                               /* four waves of 1000-node realizations of work per slice)  */
   int32_t keep_counts;         /* 1: results include the [n][n+1] count matrix              */
   uint32_t slice_queries;      /* queries advanced per slice, least remaining work first;   */
                                /* 0 = 4                                                     */

@@ -200,6 +200,7 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
 struct BigPlan {
   int block = 1024, team = 256;
   uint32_t spt = 1, grid = 1, ngroups = 1;
+  uint32_t dist_smem = 0;   // shared memory per CTA when the distances live there, else 0
   size_t slot_stride = 0, group_bytes = 0;
   size_t off_groups = 0, off_garr = 0, off_arena = 0, total = 0;   // relative to its base
 };
@@ -215,15 +216,29 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
     b.team = p.team_threads;
   } else {
     // measured on 1000- and 20,000-node graphs: teams of 128 threads (8 sources in flight per
-    // CTA) up to about 4,000 nodes, 256 beyond (wider teams for bigger buckets, and the slot
-    // arena of the grid stays within a few hundred MB)
-    b.team = std::min(b.block, n <= 4096 ? 128 : 256);
+    // CTA) up to about 4,000 nodes; beyond, teams of 512 whose two slots keep their distance
+    // arrays in shared memory (7.0 realizations/s on the 20,000-node workload, against 6.1 with
+    // four teams of 256 and distances in device memory), or 256 when two such arrays do not fit
+    if (n <= 4096) {
+      b.team = 128;
+    } else {
+      const bool two_fit = (int)big_dist_smem_bytes(n, 2u) + 1024 <= d.smem_optin;
+      b.team = (b.block >= 1024 && two_fit) ? 512 : 256;
+    }
+    b.team = std::min(b.block, b.team);
     if (!big_config_supported(b.block, b.team)) b.team = b.block;
   }
   const uint32_t nt = (uint32_t)(b.block / b.team);
   b.spt = p.slots_per_team ? (uint32_t)p.slots_per_team : 1u;
   b.spt = std::min<uint32_t>(b.spt, std::max<uint32_t>(1u, (uint32_t)kMaxSlots / nt));
-  b.grid = (uint32_t)std::max(1, d.sms) * (uint32_t)std::max(1, 1024 / b.block);
+  // distances of the CTA's slots in shared memory when they fit (every arc reads them and the
+  // relaxations update them atomically: on chip instead of L2 round trips)
+  const uint32_t ds = big_dist_smem_bytes(n, nt * b.spt);
+  if ((int)ds + 1024 <= d.smem_optin) b.dist_smem = ds;
+  const uint32_t smem_cta = b.dist_smem ? b.dist_smem : (uint32_t)sizeof(CtaCtl);
+  const uint32_t per_sm = std::max<uint32_t>(
+      1u, std::min<uint32_t>((uint32_t)std::max(1, 1024 / b.block), (228u * 1024u) / (smem_cta + 1024u)));
+  b.grid = (uint32_t)std::max(1, d.sms) * per_sm;
   // realizations in flight: enough sources for every team a few times over
   const uint64_t want = ((uint64_t)4 * b.grid * nt * b.spt + n - 1) / n;
   b.ngroups = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({std::max<uint64_t>(want, 2), 64,
@@ -341,8 +356,8 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     AFC_CUDA(cudaMemcpyAsync(groups_d, groups.data(), sizeof(BigGroup) * b.ngroups,
                              cudaMemcpyHostToDevice, stream));
     cudaError_t e = launch_mc_global(b.block, b.team, devs_d + k, p.precision, groups_d, b.ngroups,
-                                     rc, bigbase + b.off_arena, b.slot_stride, b.spt, b.grid,
-                                     stream);
+                                     rc, bigbase + b.off_arena, b.slot_stride, b.spt, b.dist_smem,
+                                     b.grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "global-path counting launch");
   }
   return AFC_OK;
@@ -512,24 +527,26 @@ int afc_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index, int
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "observed_states");
 }
 
-static size_t solve_ws_bytes(int32_t n, int32_t c) {
-  const DevInfo d = dev_info();
-  // nonzeros of the kernel: at most the transient columns in C plus the absorbing column
-  const size_t nnz_cap = (size_t)n * ((size_t)std::min<int32_t>(c, n) + 1);
-  const size_t slab = std::max<size_t>(perturb_slab_bytes(n, c) + nnz_cap * 8, 8 * (size_t)(c + 1) * 64 / (size_t)std::max(1, d.sms) + 256);
-  return solve_ws_layout(n, c, nnz_cap, (uint32_t)std::max(1, d.sms), slab).total;
-}
-
-size_t afc_solve_workspace(int32_t n, int32_t c) {
-  if (n < 1 || c < 0 || c > n) return 0;
-  return solve_ws_bytes(n, c);
+// Perturbation slabs (one per resident perturbation CTA): two per SM while they take at most
+// 8 GB together, else one per SM.
+static uint32_t perturb_slabs(const DevInfo &d, size_t slab) {
+  const uint32_t sms = (uint32_t)std::max(1, d.sms);
+  return (size_t)2 * sms * slab <= (8ull << 30) ? 2 * sms : sms;
 }
 
 static SolveWs ws_layout_for(int32_t n, int32_t c) {
   const DevInfo d = dev_info();
+  // nonzeros of the kernel: at most the transient columns in C plus the absorbing column
   const size_t nnz_cap = (size_t)n * ((size_t)std::min<int32_t>(c, n) + 1);
   const size_t slab = std::max<size_t>(perturb_slab_bytes(n, c) + nnz_cap * 8, 8 * (size_t)(c + 1) * 64 / (size_t)std::max(1, d.sms) + 256);
-  return solve_ws_layout(n, c, nnz_cap, (uint32_t)std::max(1, d.sms), slab);
+  return solve_ws_layout(n, c, nnz_cap, perturb_slabs(d, slab), slab);
+}
+
+static size_t solve_ws_bytes(int32_t n, int32_t c) { return ws_layout_for(n, c).total; }
+
+size_t afc_solve_workspace(int32_t n, int32_t c) {
+  if (n < 1 || c < 0 || c > n) return 0;
+  return solve_ws_bytes(n, c);
 }
 
 static int chain_checks(const afc_chain *ch, const uint32_t *counts, const int32_t *c_index,

@@ -74,13 +74,17 @@ struct SlotSpace {
   unsigned char *base;
   size_t stride;
   uint32_t n, words;
+  unsigned char *dist_base = nullptr;   // if set: dist of slot i at dist_base + i * dist_stride
+  uint32_t dist_stride = 0;             // (the global path keeps dist in shared memory)
 };
 
 __device__ __forceinline__ SlotArrays slot_arrays(const SlotSpace &sp, uint32_t i) {
   unsigned char *p = sp.base + (size_t)i * sp.stride;
   const uint32_t n = sp.n;
   SlotArrays a;
-  a.dist = reinterpret_cast<uint32_t *>(p);  p += al16(4u * n);
+  a.dist = reinterpret_cast<uint32_t *>(sp.dist_base ? sp.dist_base + (size_t)i * sp.dist_stride
+                                                     : p);
+  p += al16(4u * n);
   a.sig = reinterpret_cast<uint64_t *>(p);   p += al16(8u * n);
   a.ord = reinterpret_cast<uint16_t *>(p);   p += al16(2u * n);
   a.ring = reinterpret_cast<uint32_t *>(p);

@@ -97,7 +97,8 @@ big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uin
 template <int BLOCK, int TS>
 __global__ void __launch_bounds__(BLOCK, 1)
 big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngroups,
-                   unsigned char *arena, size_t slot_stride, uint32_t spt, int mode) {
+                   unsigned char *arena, size_t slot_stride, uint32_t spt, int mode,
+                   int dist_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr uint32_t NT = BLOCK / TS;
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
@@ -107,8 +108,12 @@ big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngro
   team.rank = threadIdx.x % TS;
   team.tc = &ctl->team[team.id];
   const uint32_t nslots = NT * spt;
-  const SlotSpace sp{arena + (size_t)blockIdx.x * nslots * slot_stride, slot_stride, n,
-                     (n + 31u) / 32u};
+  SlotSpace sp{arena + (size_t)blockIdx.x * nslots * slot_stride, slot_stride, n,
+               (n + 31u) / 32u};
+  if (dist_smem) {   // distances of the CTA's slots in shared memory, after the control block
+    sp.dist_base = smem + al16((uint32_t)sizeof(CtaCtl));
+    sp.dist_stride = al16(4u * n);
+  }
   for (uint32_t g = 0; g < ngroups; ++g) {
     BigGroup &G = groups[g];
     if (!G.active || (mode == 2 && !G.redo)) continue;
@@ -175,23 +180,29 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
 template <int BLOCK, int TS>
 cudaError_t launch_brandes_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups,
                              unsigned char *arena, size_t stride, uint32_t spt, int mode,
-                             uint32_t grid, cudaStream_t stream) {
-  big_brandes_kernel<BLOCK, TS><<<grid, BLOCK, sizeof(CtaCtl), stream>>>(Pd, groups, ngroups,
-                                                                         arena, stride, spt, mode);
+                             uint32_t dist_smem_bytes, uint32_t grid, cudaStream_t stream) {
+  const uint32_t smem = dist_smem_bytes ? dist_smem_bytes : (uint32_t)sizeof(CtaCtl);
+  if (smem > 48u * 1024u)
+    cudaFuncSetAttribute(big_brandes_kernel<BLOCK, TS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  big_brandes_kernel<BLOCK, TS><<<grid, BLOCK, smem, stream>>>(
+      Pd, groups, ngroups, arena, stride, spt, mode, dist_smem_bytes ? 1 : 0);
   return cudaGetLastError();
 }
 
 // (block, team) pairs of the global path
 #define AFC_BIG_CONFIGS(X) \
   X(256, 64) X(256, 128) X(256, 256) X(512, 128) X(512, 256) X(512, 512) \
-  X(1024, 128) X(1024, 256) X(1024, 1024)
+  X(1024, 128) X(1024, 256) X(1024, 512) X(1024, 1024)
 
 cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *groups,
                            uint32_t ngroups, unsigned char *arena, size_t stride, uint32_t spt,
-                           int mode, uint32_t grid, cudaStream_t stream) {
-#define AFC_X(B, T)                                                                        \
-  if (block == B && team == T)                                                             \
-    return launch_brandes_t<B, T>(Pd, groups, ngroups, arena, stride, spt, mode, grid, stream);
+                           int mode, uint32_t dist_smem_bytes, uint32_t grid,
+                           cudaStream_t stream) {
+#define AFC_X(B, T)                                                                   \
+  if (block == B && team == T)                                                        \
+    return launch_brandes_t<B, T>(Pd, groups, ngroups, arena, stride, spt, mode,      \
+                                  dist_smem_bytes, grid, stream);
   AFC_BIG_CONFIGS(AFC_X)
 #undef AFC_X
   return cudaErrorInvalidValue;
@@ -231,10 +242,14 @@ void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs
   G.best = reinterpret_cast<unsigned long long *>(take(8ull * n));
 }
 
+uint32_t big_dist_smem_bytes(uint32_t n, uint32_t nslots) {
+  return al16((uint32_t)sizeof(CtaCtl)) + nslots * al16(4u * n);
+}
+
 cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision,
                              BigGroup *groups_d, uint32_t ngroups, uint32_t r_count,
                              unsigned char *arena, size_t slot_stride, uint32_t spt,
-                             uint32_t grid, cudaStream_t stream) {
+                             uint32_t dist_smem_bytes, uint32_t grid, cudaStream_t stream) {
   if (!big_config_supported(block, team)) return cudaErrorInvalidValue;
   const bool fp32 = (precision == 1);
   for (uint32_t r0 = 0; r0 < r_count; r0 += ngroups) {
@@ -242,13 +257,13 @@ cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, fp32 ? 1 : 0,
-                       grid, stream);
+                       dist_smem_bytes, grid, stream);
     if (e != cudaSuccess) return e;
     big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, fp32 ? 1 : 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fp32) {
-      e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, 2, grid,
-                         stream);
+      e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, 2,
+                         dist_smem_bytes, grid, stream);
       if (e != cudaSuccess) return e;
       big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, 0, 1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -15,7 +15,10 @@
 
 namespace afc {
 
-constexpr int kPerturbThreads = 512;
+// 256 threads and two resident CTAs per SM: the factorisation and the triangular solves of one
+// perturbation are barrier-bound, so two perturbations per SM overlap their barrier waits.
+constexpr int kPerturbThreads = 256;
+constexpr int kPerturbCtasPerSm = 2;
 constexpr int kMaxK2 = 32;
 constexpr int kMaxHist = 64;
 
@@ -27,9 +30,11 @@ struct PerturbArena {
   int32_t *piv; // [c]
 };
 
+// Bytes of one perturbation's arena, a multiple of 256: the perturbed rows (doubles) follow it
+// in the device slab, so its size must keep them 8-byte aligned whatever the parity of c.
 __host__ __device__ inline size_t arena_bytes(int32_t c) {
   const size_t cc = (size_t)(c > 0 ? c : 1);
-  return 8 * cc * cc + 3 * 8 * cc + 4 * cc + 64;
+  return (8 * cc * cc + 3 * 8 * cc + 4 * cc + 64 + 255) & ~size_t(255);
 }
 
 __device__ inline PerturbArena carve(unsigned char *base, int32_t c) {
@@ -80,7 +85,7 @@ __device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(kPerturbThreads, 1)
+__global__ void __launch_bounds__(kPerturbThreads, kPerturbCtasPerSm)
 perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const double *b0,
                const double *lu0, const int32_t *piv0, const int32_t *nzptr, const int32_t *nzcol,
                const double *nzval, const int32_t *byrank0, uint64_t *counters,
@@ -318,7 +323,7 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   const size_t slab_bytes = ((use_smem ? 0 : arena_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
   const size_t avail = L.total - L.off_slab;
   size_t fit = avail / (slab_bytes ? slab_bytes : 1);
-  if (fit > (size_t)num_sms) fit = (size_t)num_sms;
+  if (fit > (size_t)num_sms * kPerturbCtasPerSm) fit = (size_t)num_sms * kPerturbCtasPerSm;
   if (fit > (size_t)pp.p_count) fit = (size_t)pp.p_count;
   const int grid = (int)fit;
   if (grid <= 0) return cudaErrorMemoryAllocation;

@@ -220,7 +220,7 @@ void scheduler_main(afc_server *S) {
     }
     // The next slice: the admitted queries with the least remaining work first (at most
     // slice_queries of them), each advanced by a chunk of realizations sized so that the slice
-    // holds about two waves of 1000-node realizations of work: small queries finish within a
+    // holds about four waves of 1000-node realizations of work: small queries finish within a
     // few slices and every slice stays short, so new arrivals join quickly.
     std::sort(batch.begin(), batch.end(), [](const JobP &a, const JobP &b) {
       const double ca = remaining_work(*a), cb = remaining_work(*b);
@@ -229,7 +229,7 @@ void scheduler_main(afc_server *S) {
     if (batch.size() > S->cfg.slice_queries) batch.resize(S->cfg.slice_queries);
     std::vector<JobP> done;
     if (!batch.empty()) {
-      const double share = 2.0 * (double)S->sms * kUnitWork / (double)batch.size();
+      const double share = 4.0 * (double)S->sms * kUnitWork / (double)batch.size();
       std::vector<afc_mc_problem> probs;
       std::vector<uint32_t> rb, rc;
       std::vector<uint32_t *> cnt;

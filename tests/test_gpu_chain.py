@@ -219,12 +219,20 @@ def test_perturb_sweep_ranges_add_up(er_counts):
     assert (a[0] == b[0] + c[0]).all() and (a[1] == b[1] + c[1]).all() and (a[2] == b[2] + c[2]).all()
 
 
-def test_perturb_large_support_global_slab():
-    """A pool large enough that the perturbed matrix no longer fits in shared memory."""
+@pytest.mark.parametrize("parity", [0, 1])
+def test_perturb_large_support_global_slab(parity):
+    """A pool large enough that the perturbed matrix no longer fits in shared memory, with an
+    even and an odd number of observed states (the perturbed rows follow the c x c arena in
+    the device slab, so an odd c must not misalign them)."""
     n = 400
     counts = _random_counts(n, 300, 9, support_frac=0.6)
+    cols = np.nonzero(counts[:, :n].sum(axis=0))[0]
+    if len(cols) % 2 != parity:   # fold one observed state into absorption
+        j = cols[-1]
+        counts[:, n] += counts[:, j]
+        counts[:, j] = 0
     ch = Chain(counts, 300, 0.15)
-    assert ch.c > 170
+    assert ch.c > 170 and ch.c % 2 == parity
     Q, r = O.assemble_q(counts, 300, 0.15)
     cnt, pairs, hst, mx, bo = ch.sweep(5, 3, 0.05, 0.05, 11)
     ref = O.perturb_sweep(Q, r, None, 5, 3, 0.05, 0.05, 11, keep=True)
