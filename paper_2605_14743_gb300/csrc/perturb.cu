@@ -69,6 +69,13 @@ __global__ void nominal_rank_kernel(int32_t n, const double *b0, double tie_rel,
   }
 }
 
+__device__ __forceinline__ uint32_t draw_u32(uint32_t j, uint32_t i, uint32_t p, uint32_t k0,
+                                              uint32_t k1) {
+  return philox4x32_10(make_uint4(j, i, p, 1u), k0, k1).x;
+}
+
+constexpr double kTwoM31 = 1.0 / 2147483648.0;   // 2^-31, exact
+
 __device__ __forceinline__ double uniform_draw(uint32_t j, uint32_t i, uint32_t p, uint32_t k0,
                                                uint32_t k1) {
   const uint4 u = philox4x32_10(make_uint4(j, i, p, 1u), k0, k1);
@@ -81,6 +88,15 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+__device__ __forceinline__ long long warp_sum_ll(long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+// Entries per lane a perturbed row keeps in registers (rows of up to 32 * kRowRegs entries).
+constexpr int kRowRegs = 4;
+
 __device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
@@ -90,7 +106,8 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
                const double *lu0, const int32_t *piv0, const int32_t *nzptr, const int32_t *nzcol,
                const double *nzval, const int32_t *byrank0, uint64_t *counters,
                uint64_t *pair_flips, uint64_t *shift_hist, double *maxima, double *b_out,
-               unsigned char *slabs, size_t slab_bytes, int use_smem, uint32_t *status) {
+               unsigned char *slabs, size_t slab_bytes, int use_smem, int use_priv,
+               uint32_t *status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sval[33];
   __shared__ int32_t sidx[32];
@@ -103,6 +120,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
   __shared__ uint32_t loc_cnt[3];
   LinScratch ls{sval, sidx, sb, sflag};
   const int32_t n = C.n, c = C.c;
+  const double s_unif = 1.0 / (double)n;   // the uniform initial law, divided once
   const int32_t k2 = min(pp.k2, min(kMaxK2, n));
   const int32_t kk = min(pp.top_k, n);
   const int32_t H = min(pp.hist_bins, kMaxHist);
@@ -111,6 +129,10 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
   double *qp = reinterpret_cast<double *>(slab + (use_smem ? 0 : arena_bytes(c)));
   const uint32_t k0 = (uint32_t)pp.seed, k1 = (uint32_t)(pp.seed >> 32);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u, nw = blockDim.x >> 5;
+  // warp-private column sums of the perturbed rows (shared memory, after the arena): a warp
+  // handles one row at a time and a row's columns are distinct, so they need no atomics
+  double *wy = use_priv ? reinterpret_cast<double *>(smem + arena_bytes(c)) : nullptr;
+  double *wx = use_priv ? wy + (size_t)nw * c : nullptr;
   for (int32_t k = threadIdx.x; k < kMaxK2 * kMaxK2; k += blockDim.x) loc_pair[k] = 0;
   for (int32_t k = threadIdx.x; k < kMaxHist; k += blockDim.x) loc_hist[k] = 0;
   if (threadIdx.x < 3) loc_cnt[threadIdx.x] = 0;
@@ -126,60 +148,143 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
     for (size_t k = threadIdx.x; k < (size_t)c * c; k += blockDim.x)
       ar.A[k] = (k / c == k % c) ? 1.0 : 0.0;
     for (int32_t k = threadIdx.x; k < c; k += blockDim.x) { ar.y[k] = 0.0; ar.x[k] = 0.0; }
+    if (use_priv)
+      for (int32_t k = threadIdx.x; k < 2 * (int32_t)nw * c; k += blockDim.x) wy[k] = 0.0;
     __syncthreads();
-    // (2) perturb every row (warp per row)
+    // (2) perturb every row (warp per row).  The row lives in registers (kRowRegs entries per
+    // lane) through its five passes: draws, mean, l1 norm, clipped shift and total,
+    // normalisation; the draw sum is exact integer arithmetic (z = (u - 2^31) / 2^31 exactly,
+    // and so is their sum) and one reciprocal replaces the per-entry divisions.  Longer rows
+    // go through the slab.
     for (int32_t i = warp; i < n; i += nw) {
       const int32_t e0 = nzptr[i], e1 = nzptr[i + 1];
       const int32_t supp = e1 - e0;
-      double zs = 0.0;
-      for (int32_t e = e0 + lane; e < e1; e += 32) {
-        const int32_t pj = nzcol[e];
-        const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
-        const double z = 2.0 * uniform_draw(node, (uint32_t)i, p, k0, k1) - 1.0;
-        qp[e] = z;
-        zs += z;
-      }
-      const double mean = warp_sum(zs) / (double)supp;
-      double l1 = 0.0;
-      for (int32_t e = e0 + lane; e < e1; e += 32) l1 += fabs(qp[e] - mean);
-      l1 = warp_sum(l1);
-      const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
-      double tot = 0.0;
-      for (int32_t e = e0 + lane; e < e1; e += 32) {
-        double q = nzval[e] + (qp[e] - mean) * scale;
-        q = q < 0.0 ? 0.0 : q;
-        qp[e] = q;
-        tot += q;
-      }
-      tot = warp_sum(tot);
-      double ts = 0.0, ra = 0.0;
-      for (int32_t e = e0 + lane; e < e1; e += 32) {
-        const double q = qp[e] / tot;
-        qp[e] = q;
-        if (nzcol[e] < c) ts += q; else ra = q;
-      }
-      ts = warp_sum(ts);
-      ra = warp_sum(ra);
-      const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
       const int32_t pi = C.c_index[i];
-      const double si = C.s ? C.s[i] : 1.0 / (double)n;
+      const double si = C.s ? C.s[i] : s_unif;
       const double mi = mu0[i];
-      for (int32_t e = e0 + lane; e < e1; e += 32) {
-        const int32_t pj = nzcol[e];
-        double q = qp[e];
-        if (pj < c) {
-          if (ra < pp.r_min) q *= f;
+      double *py = use_priv ? wy + (size_t)warp * c : ar.y;
+      double *px = use_priv ? wx + (size_t)warp * c : ar.x;
+      auto add_y = [&](int32_t j, double v) { if (use_priv) py[j] += v; else atomicAdd(&py[j], v); };
+      auto add_x = [&](int32_t j, double v) { if (use_priv) px[j] += v; else atomicAdd(&px[j], v); };
+      if (supp <= 32 * kRowRegs) {
+        double z[kRowRegs], q0[kRowRegs], qv[kRowRegs];
+        int32_t col[kRowRegs];
+        long long isum = 0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t) {
+          const int32_t e = e0 + (int32_t)lane + 32 * t;
+          col[t] = -1; z[t] = 0.0; q0[t] = 0.0; qv[t] = 0.0;
+          if (e < e1) {
+            const int32_t pj = nzcol[e];
+            col[t] = pj;
+            q0[t] = nzval[e];
+            const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
+            const int32_t zi = (int32_t)(draw_u32(node, (uint32_t)i, p, k0, k1) - 0x80000000u);
+            isum += zi;
+            z[t] = (double)zi * kTwoM31;
+          }
+        }
+        const double mean = (double)warp_sum_ll(isum) * kTwoM31 / (double)supp;
+        double l1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t)
+          if (col[t] >= 0) l1 += fabs(z[t] - mean);
+        l1 = warp_sum(l1);
+        const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
+        double tot = 0.0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t)
+          if (col[t] >= 0) {
+            double v = q0[t] + (z[t] - mean) * scale;
+            v = v < 0.0 ? 0.0 : v;
+            qv[t] = v;
+            tot += v;
+          }
+        const double inv_tot = 1.0 / warp_sum(tot);
+        double ts = 0.0, ra = 0.0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t)
+          if (col[t] >= 0) {
+            qv[t] *= inv_tot;
+            if (col[t] < c) ts += qv[t]; else ra = qv[t];
+          }
+        ts = warp_sum(ts);
+        ra = warp_sum(ra);
+        const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+#pragma unroll
+        for (int t = 0; t < kRowRegs; ++t) {
+          const int32_t pj = col[t];
+          if (pj < 0) continue;
+          const int32_t e = e0 + (int32_t)lane + 32 * t;
+          double v = qv[t];
+          if (pj < c) {
+            if (ra < pp.r_min) v *= f;
+            qp[e] = v;
+            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= v;
+            else add_y(pj, si * v);
+            add_x(pj, mi * (v - q0[t]));
+          } else {
+            qp[e] = (ra < pp.r_min) ? pp.r_min : v;
+          }
+        }
+      } else {
+        double zs = 0.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          const int32_t pj = nzcol[e];
+          const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
+          const double z = 2.0 * uniform_draw(node, (uint32_t)i, p, k0, k1) - 1.0;
+          qp[e] = z;
+          zs += z;
+        }
+        const double mean = warp_sum(zs) / (double)supp;
+        double l1 = 0.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) l1 += fabs(qp[e] - mean);
+        l1 = warp_sum(l1);
+        const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
+        double tot = 0.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          double q = nzval[e] + (qp[e] - mean) * scale;
+          q = q < 0.0 ? 0.0 : q;
           qp[e] = q;
-          if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
-          else atomicAdd(&ar.y[pj], si * q);
-          atomicAdd(&ar.x[pj], mi * (q - nzval[e]));
-        } else {
-          qp[e] = (ra < pp.r_min) ? pp.r_min : q;
+          tot += q;
+        }
+        tot = warp_sum(tot);
+        double ts = 0.0, ra = 0.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          const double q = qp[e] / tot;
+          qp[e] = q;
+          if (nzcol[e] < c) ts += q; else ra = q;
+        }
+        ts = warp_sum(ts);
+        ra = warp_sum(ra);
+        const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          const int32_t pj = nzcol[e];
+          double q = qp[e];
+          if (pj < c) {
+            if (ra < pp.r_min) q *= f;
+            qp[e] = q;
+            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
+            else add_y(pj, si * q);
+            add_x(pj, mi * (q - nzval[e]));
+          } else {
+            qp[e] = (ra < pp.r_min) ? pp.r_min : q;
+          }
         }
       }
-      if (lane == 0 && pi >= 0) atomicAdd(&ar.y[pi], si);
+      __syncwarp();
+      if (lane == 0 && pi >= 0) add_y(pi, si);
     }
     __syncthreads();
+    if (use_priv) {
+      for (int32_t k = threadIdx.x; k < c; k += blockDim.x) {
+        double sy = 0.0, sx = 0.0;
+        for (uint32_t w = 0; w < nw; ++w) { sy += wy[w * c + k]; sx += wx[w * c + k]; }
+        ar.y[k] += sy;
+        ar.x[k] += sx;
+      }
+      __syncthreads();
+    }
     // (3) factor, mu'_C, (N' 1)_C, first-order y_lin = x N0
     bool ok = true;
     if (c > 0) {
@@ -200,14 +305,15 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
     double pT = 0.0, pY = 0.0, pm = 0.0;
     for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
       const int32_t pv = C.c_index[v];
-      pT += pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n);
+      pT += pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : s_unif);
       if (pv >= 0) pY += ar.x[pv];
     }
     const double T = block_sum(pT, red);
     const double Y1 = block_sum(pY, red);
+    const double invT = 1.0 / T;
     for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
       const int32_t pv = C.c_index[v];
-      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n)) / T;
+      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : s_unif)) * invT;
       pm = fmax(pm, bv);
       const double lin = b0[v] + (pv >= 0 ? ar.x[pv] : 0.0) / T0 - b0[v] * Y1 / T0;
       loc_db = fmax(loc_db, fabs(bv - b0[v]));
@@ -233,12 +339,12 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
     for (int32_t a = warp; a < k2; a += nw) {
       const int32_t v = byrank0[a];
       const int32_t pv = C.c_index[v];
-      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : 1.0 / (double)n)) / T;
+      const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : s_unif)) * invT;
       int32_t r = 0;
       for (int32_t u = lane; u < n; u += 32) {
         if (u == v) continue;
         const int32_t pu = C.c_index[u];
-        const double bu = (pu >= 0 ? ar.y[pu] : (C.s ? C.s[u] : 1.0 / (double)n)) / T;
+        const double bu = (pu >= 0 ? ar.y[pu] : (C.s ? C.s[u] : s_unif)) * invT;
         const double d = bu - bv;
         if (d > tau || (fabs(d) <= tau && u < v)) ++r;
       }
@@ -319,6 +425,9 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int use_smem = (int)smem + 16 * 1024 <= max_optin ? 1 : 0;
+  const uint32_t priv = 2u * (kPerturbThreads / 32) * (uint32_t)(c > 0 ? c : 1) * 8u;
+  const int use_priv = (use_smem && (int)(smem + priv) + 16 * 1024 <= max_optin) ? 1 : 0;
+  const uint32_t dyn = use_smem ? smem + (use_priv ? priv : 0u) : 0u;
   const size_t nnz_bytes = L.nnz_cap * 8;
   const size_t slab_bytes = ((use_smem ? 0 : arena_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
   const size_t avail = L.total - L.off_slab;
@@ -328,10 +437,10 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   const int grid = (int)fit;
   if (grid <= 0) return cudaErrorMemoryAllocation;
   if (use_smem)
-    cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  perturb_kernel<<<grid, kPerturbThreads, use_smem ? smem : 0, stream>>>(
+    cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  perturb_kernel<<<grid, kPerturbThreads, dyn, stream>>>(
       C, pp, mu0, b0, lu0, piv0, nzptr, nzcol, nzval, byrank0, counters, pair_flips, shift_hist,
-      maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, status_dev);
+      maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, use_priv, status_dev);
   return cudaGetLastError();
 }
 

@@ -219,6 +219,28 @@ def test_perturb_sweep_ranges_add_up(er_counts):
     assert (a[0] == b[0] + c[0]).all() and (a[1] == b[1] + c[1]).all() and (a[2] == b[2] + c[2]).all()
 
 
+def test_perturb_long_rows():
+    """Rows spread over about 200 states (longer than the rows the kernel keeps in registers),
+    with the matrix in the device slab: the row-by-row perturbation through the slab."""
+    n, R = 300, 4000
+    rng = np.random.default_rng(21)
+    C = rng.choice(n, size=220, replace=False)
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        p = rng.dirichlet(np.ones(len(C) + 1))
+        d = rng.multinomial(R, p)
+        counts[i, C] = d[:-1].astype(np.uint32)
+        counts[i, n] = d[-1]
+    ch = Chain(counts, R, 0.15)
+    assert ch.c > 200
+    assert ((counts[:, :n] > 0).sum(axis=1) > 128).all()
+    Q, r = O.assemble_q(counts, R, 0.15)
+    cnt, pairs, hst, mx, bo = ch.sweep(0, 4, 0.05, 0.05, 13)
+    ref = O.perturb_sweep(Q, r, None, 0, 4, 0.05, 0.05, 13, keep=True)
+    assert close(bo, ref.b)
+    assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+
+
 @pytest.mark.parametrize("parity", [0, 1])
 def test_perturb_large_support_global_slab(parity):
     """A pool large enough that the perturbed matrix no longer fits in shared memory, with an
