@@ -313,6 +313,9 @@ typedef struct {
   const int32_t *candidates; int32_t n_candidates;   /* HOST W or NULL                      */
   uint32_t top_k; double tie_rel; int32_t precision; double recheck_margin;
   uint32_t n_perturb; double l1_radius; double r_min; uint64_t perturb_seed;
+  uint32_t r_begin;                  /* first realization index: the query draws realizations */
+                                     /* r_begin .. r_begin + realizations - 1 (shards of one    */
+                                     /* query on several GPUs take disjoint ranges); 0 usually */
 } afc_host_query;
 
 typedef struct {

@@ -93,7 +93,8 @@ class HostQuery(ctypes.Structure):
                 ("absorb_floor", c_f64), ("s_init", c_p), ("reward", c_p), ("candidates", c_p),
                 ("n_candidates", c_i32), ("top_k", c_u32), ("tie_rel", c_f64),
                 ("precision", c_i32), ("recheck_margin", c_f64), ("n_perturb", c_u32),
-                ("l1_radius", c_f64), ("r_min", c_f64), ("perturb_seed", c_u64)]
+                ("l1_radius", c_f64), ("r_min", c_f64), ("perturb_seed", c_u64),
+                ("r_begin", c_u32)]
 
 
 class HostResult(ctypes.Structure):

@@ -753,7 +753,8 @@ int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream) {
     if (wsc == 0) { rc = validate(&p); if (!rc) rc = fail(AFC_EINVAL, "problem rejected"); break; }
     void *d_wsc = dalloc(wsc);
     if (!d_wsc) { rc = fail(AFC_ENOMEM, "device allocation"); break; }
-    rc = afc_transition_counts(&p, 0, q->realizations, d_counts, d_stats, nullptr, nullptr, d_wsc, wsc, s);
+    rc = afc_transition_counts(&p, q->r_begin, q->realizations, d_counts, d_stats, nullptr, nullptr,
+                               d_wsc, wsc, s);
     if (rc) break;
     int32_t *d_cidx = (int32_t *)dalloc(4 * (size_t)n);
     int32_t *d_clist = (int32_t *)dalloc(4 * (size_t)n);

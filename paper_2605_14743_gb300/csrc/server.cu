@@ -242,7 +242,7 @@ void scheduler_main(afc_server *S) {
                                    : (uint32_t)std::min<double>(per, 4096.0);
         const uint32_t k = std::min(left, slice);
         probs.push_back(j->prob);
-        rb.push_back(j->next_r);
+        rb.push_back(j->q.r_begin + j->next_r);
         rc.push_back(k);
         cnt.push_back(j->counts);
         sts.push_back(j->stats);

@@ -42,3 +42,19 @@ def test_run_host_reward_and_pool():
     assert (bufs.counts.numpy().view(np.uint32) == oc).all()
     mu, b, T, bf, c = O.solve_counts(oc, 16, wl.alpha, f=wl.reward, reduced=True)
     assert close(bufs.b.numpy(), b) and abs(res.b_f - bf) <= 1e-9 * bf and res.c == c
+
+
+def test_run_host_realization_range():
+    """A query shard (r_begin > 0) draws exactly the realizations of that range: its counts
+    equal the device path's over the same range and the oracle's."""
+    wl = variant(workload("small_er"), realizations=150)
+    bufs = afc.engine.HostBuffers(wl, pinned=False)
+    bufs.query.r_begin = 333
+    afc.run_query_host(bufs)
+    q = afc.Query(wl)
+    q.run_counts(333, 150)
+    torch.cuda.synchronize()
+    counts = bufs.counts.numpy().view(np.uint32)
+    assert (counts == q.counts.cpu().numpy().view(np.uint32)).all()
+    oc, _ = oracle_counts(wl, 333, 150)
+    assert (counts == oc).all()
