@@ -58,6 +58,35 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
+def _traffic_fields():
+    fields = {}
+    try:
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    fields[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return fields if fields.get("source_sha256") == kernel_source_hash() else {}
+
+
+def issue_roofline(realizations: int, kernel_ms: float, sm_mhz):
+    """Warp-instruction issue rate of the counting launch against the SMs' issue peak (4 warp
+    schedulers per SM, one instruction each per cycle, at the clock sampled during the run);
+    the instruction count per realization comes from the ncu capture of the same sources."""
+    import torch
+    f = _traffic_fields()
+    if "warp_instructions_per_realization" not in f or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    achieved = int(f["warp_instructions_per_realization"]) * realizations / (kernel_ms / 1000.0)
+    peak = sms * 4 * float(sm_mhz) * 1e6
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp inst/s",
+            "frac": achieved / peak,
+            "source": "ncu smsp__inst_executed per realization (profiles/counts_traffic.txt)"}
+
+
 def measured_traffic(realizations: int):
     """DRAM read + write bytes of one counting launch over `realizations`, if the recorded
     capture was taken on the current kernel sources (else None)."""
@@ -317,7 +346,8 @@ def run_ours(args):
                 "gteps": gteps, "counts_kernel_ms": kavg,
                 "query_latency_ms_p50": statistics.median(step_ms),
                 "query_latency_ms_p99": max(step_ms),
-                "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "roofline": roof, "issue_roofline": issue_roofline(R, kavg, clocks.get("sm_mhz")),
+                "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
                 "check": {"c": res.c, "expected_T": res.expected_T, "b_f": res.b_f,
                           "device_error": int(stats[5]), "overflow": int(stats[3])}}
