@@ -44,6 +44,7 @@ extern "C" {
 #define AFC_FP32_RECHECK 1  /* delta in FP32, realizations with a near-tied top two in FP64 */
 
 #define AFC_PATH_AUTO 0     /* counting path chosen by what fits in shared memory            */
+                            /* (and, with automatic teams, holds at least four of them)      */
 #define AFC_PATH_SHARED 1   /* realization and source state in shared memory (small graphs)  */
 #define AFC_PATH_GLOBAL 2   /* realized graph and source state in device memory (any size)   */
 
@@ -109,9 +110,10 @@ typedef struct {
   int32_t slots_per_team;    /* sources a team advances in lockstep (1..16); 0 = as many   */
                              /* as shared memory holds                                     */
   int32_t memory_path;       /* AFC_PATH_AUTO: realizations of graphs whose per-CTA state  */
-                             /* fits in shared memory run there, others on the global-     */
-                             /* memory path; AFC_PATH_SHARED / AFC_PATH_GLOBAL force one   */
-                             /* (AFC_EUNSUPPORTED if the shared path does not fit)          */
+                             /* fits in shared memory run there (with team_threads 0: only */
+                             /* if it holds at least four teams per CTA), others on the    */
+                             /* global-memory path; AFC_PATH_SHARED / AFC_PATH_GLOBAL force */
+                             /* one (AFC_EUNSUPPORTED if the shared path does not fit)      */
   /* Simulator-level rewards (Sec. 6) and rank-r reports.  The ordering pi of a valid        */
   /* component K repeats the centre rule on the nodes of K not yet listed (B* over the rest, */
   /* the tie_rel band, smallest id), so pi(1) is the centre (Sec. 2.3 eq. topk-comp).        */
@@ -139,8 +141,8 @@ typedef struct {
 } afc_mc_stats;
 
 /* AFC_PATH_SHARED or AFC_PATH_GLOBAL: where afc_transition_counts runs this problem (the
- * problem's memory_path, or for AFC_PATH_AUTO whether its per-CTA state fits in shared
- * memory); a negative error code for an invalid problem. */
+ * problem's memory_path, or for AFC_PATH_AUTO the rule given at memory_path); a negative error
+ * code for an invalid problem. */
 int afc_counts_path(const afc_mc_problem *prob);
 
 /* Bytes of device workspace afc_transition_counts needs for this problem (0 when the whole
@@ -160,6 +162,27 @@ int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t
                           uint32_t *counts, afc_mc_stats *stats, double *dump_bc,
                           int32_t *dump_next, void *workspace, size_t workspace_bytes,
                           void *stream);
+
+/* Autotuner of the counting launch (an engineering layer; the paper has no counterpart).  Times
+ * a small grid of launch configurations on `sample` realizations of the problem (r_begin .. r_begin
+ * + sample - 1) and writes the fastest into prob->block_threads, team_threads, bucket_width and,
+ * when prob->memory_path is AFC_PATH_AUTO, memory_path.  Grid: bucket widths {1/2, 1, 2} x the
+ * automatic one; on the shared-memory path the block/team pairs (1024,32), (1024,128),
+ * (1024,256), (1024,1024), (512,64), (512,512), (256,256) that fit; on the global path (1024,128),
+ * (1024,256), (1024,512) (tried also for AUTO problems that fit in shared memory).  The automatic
+ * configuration is timed too, so the winner is never slower on the sample.  The configuration
+ * never changes the results, only the speed.  Allocates and frees its own device scratch (stream
+ * ordered) and SYNCHRONISES `stream`.  sample 0 = ceil(2000 x SMs / n) realizations, clamped to
+ * [2, 2 x SMs].  Errors: those of afc_transition_counts (the problem is left unchanged). */
+typedef struct {
+  int32_t block_threads, team_threads;
+  uint32_t bucket_width;
+  double realizations_per_s;  /* of the winner on the sample                                 */
+  double default_per_s;       /* of the automatic configuration on the same sample           */
+  int32_t candidates;         /* configurations timed                                         */
+} afc_tune_result;
+int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *stream,
+                 afc_tune_result *out);
 
 /* Several base graphs in one persistent launch (the batched mix).  probs: HOST array of
  * nprob problems; r_count: HOST [nprob]; counts: HOST array of nprob DEVICE count matrices;

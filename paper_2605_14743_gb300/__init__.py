@@ -35,6 +35,7 @@ __all__ = [
     "afc_graph_create_csr", "afc_graph_nodes", "afc_graph_edges", "afc_graph_destroy",
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
+    "TuneResult", "afc_autotune",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -127,6 +128,12 @@ class Params(ctypes.Structure):
                 ("recheck_margin", c_f64), ("tie_rel", c_f64), ("cuda_stream", c_p)]
 
 
+class TuneResult(ctypes.Structure):
+    """afc_tune_result."""
+    _fields_ = [("block_threads", c_i32), ("team_threads", c_i32), ("bucket_width", c_u32),
+                ("realizations_per_s", c_f64), ("default_per_s", c_f64), ("candidates", c_i32)]
+
+
 class PerturbStats(ctypes.Structure):
     _fields_ = [("top1_changes", c_u64), ("topk_set_changes", c_u64),
                 ("topk_order_changes", c_u64), ("pair_flips", c_u64 * 100),
@@ -141,6 +148,8 @@ _SIGS = {
     "afc_survival_threshold": ([c_f64], c_u64),
     "afc_transition_counts_workspace": ([ctypes.POINTER(McProblem)], c_sz),
     "afc_counts_path": ([ctypes.POINTER(McProblem)], ctypes.c_int),
+    "afc_autotune": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, ctypes.POINTER(TuneResult)],
+                     ctypes.c_int),
     "afc_transition_counts": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p, c_p, c_p,
                                c_sz, c_p], ctypes.c_int),
     "afc_transition_counts_batched_workspace": ([c_i32, ctypes.POINTER(McProblem), c_p], c_sz),
@@ -252,6 +261,16 @@ def afc_counts_path(prob: McProblem) -> int:
     if code < 0:
         raise AfcError(-code, afc_last_error())
     return code
+
+
+def afc_autotune(prob: McProblem, r_begin: int, sample: int, stream) -> TuneResult:
+    """Times the candidate launch configurations on `sample` realizations and writes the fastest
+    into `prob` (block_threads, team_threads, bucket_width, and memory_path when it was automatic);
+    synchronises `stream`."""
+    out = TuneResult()
+    _chk(lib().afc_autotune(ctypes.byref(prob), int(r_begin), int(sample), stream,
+                            ctypes.byref(out)))
+    return out
 
 
 def afc_transition_counts_workspace(prob: McProblem) -> int:

@@ -67,8 +67,9 @@ uint32_t auto_delta(const afc_mc_problem &p) {
 }
 
 int auto_block(const afc_mc_problem &p) {
-  if (p.block_threads) return p.block_threads;
-  return p.n >= 128 ? 1024 : 256;
+  // measured: 1024-thread CTAs with one-warp teams are the fastest shape for small graphs too
+  // (n = 64: 1.7x the former 256-thread CTAs)
+  return p.block_threads ? p.block_threads : 1024;
 }
 
 int validate(const afc_mc_problem *p) {
@@ -167,10 +168,12 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
   const uint32_t one = mc_layout_bytes(nmax, amax, 1) - base;
   const uint32_t cap = (uint32_t)std::max(0, d.smem_optin - 1024);
   const uint32_t fit = base <= cap ? (cap - base) / one : 0u;
-  // preferred team sizes, largest team last so that small graphs / small shared memory work
+  // preferred team sizes, largest team last so that small graphs / small shared memory work.
+  // Measured on ER and WS graphs of mean degree 8: one-warp teams wherever 32 of them fit
+  // (1.25-1.36x teams of 128 up to n = 300), then teams of 128, then larger teams
   std::vector<int> prefs;
   if (req_team) prefs.push_back(req_team);
-  else prefs = {128, 64, 256, 32, 512, 1024};
+  else prefs = {32, 128, 64, 256, 512, 1024};
   pl.fits = false;
   for (int t : prefs) {
     if (t > pl.block || !mc_config_supported(pl.block, t)) continue;
@@ -259,7 +262,14 @@ bool smem_fits(const afc_mc_problem &p) {
 bool wants_global(const afc_mc_problem &p) {
   if (p.memory_path == AFC_PATH_GLOBAL) return true;
   if (p.memory_path == AFC_PATH_SHARED) return false;
-  return !smem_fits(p);
+  const McPlan pl = plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1, p.team_threads,
+                             p.slots_per_team);
+  if (!pl.fits) return true;
+  // measured on ER and WS graphs of mean degree 8, n = 1,000 .. 2,400: once shared memory holds
+  // fewer than four teams' sources per CTA (one team of 512 or 1024 threads) the global-memory
+  // path with teams of 128 is faster (1.17x at n = 1,800, 1.9x at n = 2,400); with four teams
+  // of 256 the shared path still wins (1.4x at n = 1,600)
+  return p.team_threads == 0 && pl.block / pl.team < 4;
 }
 
 size_t meta_bytes(int nprob) {
@@ -471,6 +481,128 @@ int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
     for (int g = 0; g < nprob; ++g) sl.push_back(stats + g);
   return run_counts(nprob, probs, nullptr, r_count, counts, stats ? sl.data() : nullptr, nullptr,
                     nullptr, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *stream,
+                 afc_tune_result *out) {
+  int st = validate(prob);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevInfo d = dev_info();
+  const afc_mc_problem base = *prob;
+  const bool global = wants_global(base);
+  if (sample == 0)
+    sample = (uint32_t)std::min<uint64_t>(2ull * d.sms,
+                                          std::max<uint64_t>(2, (2000ull * d.sms + base.n - 1) / base.n));
+  // bucket widths: the power of two the kernels would use for the automatic request, half and
+  // double (the kernels raise a width below ceil(wmax / 14) to that bound; those duplicates go)
+  const uint32_t wmax = base.w_hi ? 0u : (uint32_t)base.w_hi_all;
+  const uint32_t dmin = wmax ? (wmax + (kRing - 2) - 1) / (kRing - 2) : 1u;
+  auto eff = [&](uint32_t w) {
+    const uint32_t want = std::max(std::max(w, 1u), dmin);
+    uint32_t p2 = 1;
+    while (p2 < want && p2 < (1u << 30)) p2 <<= 1;
+    return p2;
+  };
+  const uint32_t w0 = eff(auto_delta(base));
+  std::vector<uint32_t> widths;
+  for (uint32_t w : {w0, w0 > 1 ? w0 / 2 : 1u, w0 * 2})
+    if (std::find(widths.begin(), widths.end(), eff(w)) == widths.end()) widths.push_back(eff(w));
+  static const std::pair<int, int> kShared[] = {{1024, 32}, {1024, 128}, {1024, 256}, {1024, 1024},
+                                                 {512, 64}, {512, 512}, {256, 256}};
+  static const std::pair<int, int> kGlobal[] = {{1024, 128}, {1024, 256}, {1024, 512}};
+  // the automatic configuration first (it is also the warm-up), then the grid; a problem on
+  // AFC_PATH_AUTO whose state fits in shared memory also tries the global-memory path
+  std::vector<afc_mc_problem> cands;
+  cands.push_back(base);
+  cands.back().bucket_width = w0;
+  auto add = [&](int path, int block, int team, uint32_t w) {
+    afc_mc_problem c = base;
+    c.block_threads = block;
+    c.team_threads = team;
+    c.bucket_width = w;
+    c.memory_path = path;
+    if (validate(&c) != AFC_OK) return;
+    if (path == AFC_PATH_SHARED && !smem_fits(c)) return;
+    cands.push_back(c);
+  };
+  for (uint32_t w : widths) {
+    if (!global)
+      for (const auto &sh : kShared) add(AFC_PATH_SHARED, sh.first, sh.second, w);
+    if (global || base.memory_path == AFC_PATH_AUTO)
+      for (const auto &sh : kGlobal) add(AFC_PATH_GLOBAL, sh.first, sh.second, w);
+  }
+  g_err.clear();
+  size_t ws = 0;
+  for (const auto &c : cands) ws = std::max(ws, counts_ws_total(1, &c, &sample));
+  const size_t counts_bytes = sizeof(uint32_t) * (size_t)base.n * (size_t)(base.n + 1);
+  const size_t psi_bytes = base.reward_k ? sizeof(double) * (size_t)base.n : 0;
+  const size_t off_psi = (counts_bytes + 255) & ~size_t(255);
+  const size_t off_ws = off_psi + ((psi_bytes + 255) & ~size_t(255));
+  void *buf = nullptr;
+  AFC_CUDA(cudaMallocAsync(&buf, off_ws + ws, s));
+  unsigned char *b = static_cast<unsigned char *>(buf);
+  uint32_t *counts = reinterpret_cast<uint32_t *>(b);
+  double *psi = psi_bytes ? reinterpret_cast<double *>(b + off_psi) : nullptr;
+  void *wsp = b + off_ws;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_t = 0.0, default_t = 0.0;
+  size_t best = 0;
+  int timed = 0;
+  for (size_t k = 0; k < cands.size() + 1 && st == AFC_OK; ++k) {
+    // k = 0 warms up with the automatic configuration; k >= 1 times candidate k - 1
+    afc_mc_problem c = cands[k == 0 ? 0 : k - 1];
+    if (psi) c.psi_sum = psi;   // the caller's accumulator is never touched
+    uint32_t *cs[1] = {counts};
+    cudaEventRecord(e0, s);
+    st = run_counts(1, &c, &r_begin, &sample, cs, nullptr, nullptr, nullptr, wsp, ws, s);
+    cudaEventRecord(e1, s);
+    if (st != AFC_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = cuda_fail(e, "autotune launch"); break; }
+    if (k == 0) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ++timed;
+    if (k == 1) default_t = ms;
+    if (k == 1 || ms < best_t) { best_t = ms; best = k - 1; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st != AFC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  const afc_mc_problem &w = cands[best];
+  if (best == 0) {
+    // the automatic configuration won: pin what it resolves to
+    if (global) {
+      const BigPlan bp = plan_big(base, sample);
+      prob->block_threads = bp.block;
+      prob->team_threads = bp.team;
+    } else {
+      const McPlan pl = plan_for(base, (uint32_t)base.n, 2ull * (uint64_t)base.m, sample,
+                                 base.team_threads, base.slots_per_team);
+      prob->block_threads = pl.block;
+      prob->team_threads = pl.team;
+    }
+  } else {
+    prob->block_threads = w.block_threads;
+    prob->team_threads = w.team_threads;
+    if (base.memory_path == AFC_PATH_AUTO) prob->memory_path = w.memory_path;
+  }
+  prob->bucket_width = w.bucket_width;
+  if (out) {
+    out->block_threads = prob->block_threads;
+    out->team_threads = prob->team_threads;
+    out->bucket_width = prob->bucket_width;
+    out->realizations_per_s = best_t > 0 ? 1e3 * sample / best_t : 0.0;
+    out->default_per_s = default_t > 0 ? 1e3 * sample / default_t : 0.0;
+    out->candidates = timed;
+  }
+  return AFC_OK;
 }
 
 int afc_debug_realize(const afc_mc_problem *prob, uint32_t r_begin, uint32_t r_count, uint8_t *alive,

@@ -16,7 +16,7 @@ import numpy as np
 from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
-               afc_transition_counts, afc_transition_counts_workspace)
+               afc_autotune, afc_transition_counts, afc_transition_counts_workspace)
 
 
 def _torch():
@@ -183,6 +183,16 @@ class Query:
         ch.s_init = None if self.s is None else self.s.data_ptr()
         ch.reward = None if self.f is None else self.f.data_ptr()
         return ch
+
+    def autotune(self, r_begin=0, sample=0):
+        """Picks the counting launch configuration by timing candidates on `sample`
+        realizations (0 = the library's default sample) and resizes the workspace for it."""
+        res = afc_autotune(self.prob, r_begin, sample, self._stream())
+        wsb = afc_transition_counts_workspace(self.prob)
+        if wsb > self.ws_counts.numel():
+            self.ws_counts = self.torch.empty(wsb, dtype=self.torch.uint8,
+                                              device=self.counts.device)
+        return res
 
     def run_counts(self, r_begin=0, r_count=None, zero=True, dump_bc=None, dump_next=None):
         if zero:

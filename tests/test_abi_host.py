@@ -103,3 +103,17 @@ def test_params_defaults():
     p = afc.afc_params_default()
     assert (p.k_min, p.alpha, p.absorb_floor, p.recheck_margin, p.tie_rel) == (5, 0.15, 1e-6, 1e-4, 1e-9)
     assert p.p_survive_all == 1.0 and p.w_lo_all == p.w_hi_all == 1 and p.precision == afc.AFC_FP64
+
+
+def test_autotune_validates_before_touching_the_device():
+    prob = afc.McProblem()
+    prob.n, prob.m = 70000, 10
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_autotune(prob, 0, 4, None)
+    assert e.value.code == afc.AFC_EUNSUPPORTED
+    prob.n, prob.m, prob.row_ptr, prob.col, prob.eid = 10, 5, 8, 8, 8
+    prob.w_lo_all, prob.w_hi_all, prob.k_min, prob.block_threads = 1, 3, 1, 48
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_autotune(prob, 0, 4, None)
+    assert e.value.code == afc.AFC_EINVAL
+    assert prob.block_threads == 48 and prob.bucket_width == 0     # left as given
