@@ -203,7 +203,8 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
 struct BigPlan {
   int block = 1024, team = 256;
   uint32_t spt = 1, grid = 1, ngroups = 1;
-  uint32_t dist_smem = 0;   // shared memory per CTA when the distances live there, else 0
+  uint32_t smem = 0;        // dynamic shared memory per Brandes CTA (0: control block only)
+  int on_chip = 0;          // 0: slots in the arena, 1: their distances on chip, 2: whole slots
   size_t slot_stride = 0, group_bytes = 0;
   size_t off_groups = 0, off_garr = 0, off_arena = 0, total = 0;   // relative to its base
 };
@@ -218,12 +219,18 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   if (p.team_threads) {
     b.team = p.team_threads;
   } else {
-    // measured on 1000- and 20,000-node graphs: teams of 128 threads (8 sources in flight per
-    // CTA) up to about 4,000 nodes; beyond, teams of 512 whose two slots keep their distance
-    // arrays in shared memory (7.0 realizations/s on the 20,000-node workload, against 6.1 with
-    // four teams of 256 and distances in device memory), or 256 when two such arrays do not fit
+    // measured on ER and WS graphs of mean degree 8 (n = 1,000 .. 6,000) and on the
+    // 20,000-node workload: up to about 4,000 nodes, teams of 128 threads (8 sources in flight
+    // per CTA), except where only four whole slots fit in shared memory: then four teams of 256
+    // with their slots on chip (+7% at n = 1,800, +10-14% at n = 3,200 over teams of 128 with
+    // only their distances on chip); beyond, teams of 512 whose two slots keep at least their
+    // distance arrays in shared memory (7.1 realizations/s on the 20,000-node workload, against
+    // 6.2 with four teams of 256 and distances in device memory), or 256 when two such arrays
+    // do not fit
     if (n <= 4096) {
-      b.team = 128;
+      const bool eight = (int)big_slots_smem_bytes(n, 8u) + 1024 <= d.smem_optin;
+      const bool four = (int)big_slots_smem_bytes(n, 4u) + 1024 <= d.smem_optin;
+      b.team = (b.block == 1024 && !eight && four) ? 256 : 128;
     } else {
       const bool two_fit = (int)big_dist_smem_bytes(n, 2u) + 1024 <= d.smem_optin;
       b.team = (b.block >= 1024 && two_fit) ? 512 : 256;
@@ -234,11 +241,19 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   const uint32_t nt = (uint32_t)(b.block / b.team);
   b.spt = p.slots_per_team ? (uint32_t)p.slots_per_team : 1u;
   b.spt = std::min<uint32_t>(b.spt, std::max<uint32_t>(1u, (uint32_t)kMaxSlots / nt));
-  // distances of the CTA's slots in shared memory when they fit (every arc reads them and the
-  // relaxations update them atomically: on chip instead of L2 round trips)
+  // the CTA's source slots in shared memory when they fit, else their distance arrays (every
+  // arc reads them and the relaxations update them atomically: on chip instead of L2 round
+  // trips), else nothing
+  const uint32_t whole = big_slots_smem_bytes(n, nt * b.spt);
   const uint32_t ds = big_dist_smem_bytes(n, nt * b.spt);
-  if ((int)ds + 1024 <= d.smem_optin) b.dist_smem = ds;
-  const uint32_t smem_cta = b.dist_smem ? b.dist_smem : (uint32_t)sizeof(CtaCtl);
+  if ((int)whole + 1024 <= d.smem_optin) {
+    b.smem = whole;
+    b.on_chip = 2;
+  } else if ((int)ds + 1024 <= d.smem_optin) {
+    b.smem = ds;
+    b.on_chip = 1;
+  }
+  const uint32_t smem_cta = b.on_chip ? b.smem : (uint32_t)sizeof(CtaCtl);
   const uint32_t per_sm = std::max<uint32_t>(
       1u, std::min<uint32_t>((uint32_t)std::max(1, 1024 / b.block), (228u * 1024u) / (smem_cta + 1024u)));
   b.grid = (uint32_t)std::max(1, d.sms) * per_sm;
@@ -250,7 +265,7 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   size_t o = 0;
   b.off_groups = o; o += (sizeof(BigGroup) * b.ngroups + 255) & ~size_t(255);
   b.off_garr = o;   o += b.group_bytes * b.ngroups;
-  b.off_arena = o;  o += b.slot_stride * (size_t)b.grid * nt * b.spt;
+  b.off_arena = o;  o += b.on_chip == 2 ? 0 : b.slot_stride * (size_t)b.grid * nt * b.spt;
   b.total = o;
   return b;
 }
@@ -366,7 +381,7 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     AFC_CUDA(cudaMemcpyAsync(groups_d, groups.data(), sizeof(BigGroup) * b.ngroups,
                              cudaMemcpyHostToDevice, stream));
     cudaError_t e = launch_mc_global(b.block, b.team, devs_d + k, p.precision, groups_d, b.ngroups,
-                                     rc, bigbase + b.off_arena, b.slot_stride, b.spt, b.dist_smem,
+                                     rc, bigbase + b.off_arena, b.slot_stride, b.spt, b.smem, b.on_chip,
                                      b.grid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "global-path counting launch");
   }

@@ -103,12 +103,18 @@ void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs
 bool big_config_supported(int block, int team);
 // Runs realizations [0, r_count) of the problem *Pd (device copy) through the global path in
 // batches of ngroups realizations.
+// slots_on_chip 0: source slots in the arena; 1: their distance arrays in shared memory
+// (smem_bytes = big_dist_smem_bytes); 2: the whole slots in shared memory (smem_bytes =
+// big_slots_smem_bytes, the arena unused).
 // Shared memory of a Brandes CTA that keeps its slots' distance arrays on chip.
 uint32_t big_dist_smem_bytes(uint32_t n, uint32_t nslots);
+// Shared memory of a Brandes CTA that keeps its whole slots (stride big_slot_bytes) on chip.
+uint32_t big_slots_smem_bytes(uint32_t n, uint32_t nslots);
 cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision,
                              BigGroup *groups_d, uint32_t ngroups, uint32_t r_count,
                              unsigned char *arena, size_t slot_stride, uint32_t spt,
-                             uint32_t dist_smem_bytes, uint32_t grid, cudaStream_t stream);
+                             uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
+                             cudaStream_t stream);
 
 // abi.cu: counting over per-problem realization ranges (the batched launch of the serving
 // loop) and the thread-local error message of the C ABI

@@ -93,12 +93,14 @@ big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uin
 }
 
 // mode 0: FP64, every active group.  1: FP32, every active group.  2: FP64, groups flagged
-// for a recheck only.
+// for a recheck only.  slots_on_chip 0: the CTA's source slots live in its region of the
+// device arena; 1: their distance arrays live in shared memory after the control block, the
+// rest in the arena; 2: the whole slots live in shared memory (the arena is not used).
 template <int BLOCK, int TS>
 __global__ void __launch_bounds__(BLOCK, 1)
 big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngroups,
                    unsigned char *arena, size_t slot_stride, uint32_t spt, int mode,
-                   int dist_smem) {
+                   int slots_on_chip) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr uint32_t NT = BLOCK / TS;
   CtaCtl *ctl = reinterpret_cast<CtaCtl *>(smem);
@@ -108,10 +110,11 @@ big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngro
   team.rank = threadIdx.x % TS;
   team.tc = &ctl->team[team.id];
   const uint32_t nslots = NT * spt;
-  SlotSpace sp{arena + (size_t)blockIdx.x * nslots * slot_stride, slot_stride, n,
-               (n + 31u) / 32u};
-  if (dist_smem) {   // distances of the CTA's slots in shared memory, after the control block
-    sp.dist_base = smem + al16((uint32_t)sizeof(CtaCtl));
+  unsigned char *const chip = smem + al16((uint32_t)sizeof(CtaCtl));
+  SlotSpace sp{slots_on_chip == 2 ? chip : arena + (size_t)blockIdx.x * nslots * slot_stride,
+               slot_stride, n, (n + 31u) / 32u};
+  if (slots_on_chip == 1) {
+    sp.dist_base = chip;
     sp.dist_stride = al16(4u * n);
   }
   for (uint32_t g = 0; g < ngroups; ++g) {
@@ -180,13 +183,14 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
 template <int BLOCK, int TS>
 cudaError_t launch_brandes_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups,
                              unsigned char *arena, size_t stride, uint32_t spt, int mode,
-                             uint32_t dist_smem_bytes, uint32_t grid, cudaStream_t stream) {
-  const uint32_t smem = dist_smem_bytes ? dist_smem_bytes : (uint32_t)sizeof(CtaCtl);
+                             uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
+                             cudaStream_t stream) {
+  const uint32_t smem = slots_on_chip ? smem_bytes : (uint32_t)sizeof(CtaCtl);
   if (smem > 48u * 1024u)
     cudaFuncSetAttribute(big_brandes_kernel<BLOCK, TS>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   big_brandes_kernel<BLOCK, TS><<<grid, BLOCK, smem, stream>>>(
-      Pd, groups, ngroups, arena, stride, spt, mode, dist_smem_bytes ? 1 : 0);
+      Pd, groups, ngroups, arena, stride, spt, mode, slots_on_chip);
   return cudaGetLastError();
 }
 
@@ -197,12 +201,12 @@ cudaError_t launch_brandes_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups
 
 cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *groups,
                            uint32_t ngroups, unsigned char *arena, size_t stride, uint32_t spt,
-                           int mode, uint32_t dist_smem_bytes, uint32_t grid,
+                           int mode, uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
                            cudaStream_t stream) {
 #define AFC_X(B, T)                                                                   \
   if (block == B && team == T)                                                        \
     return launch_brandes_t<B, T>(Pd, groups, ngroups, arena, stride, spt, mode,      \
-                                  dist_smem_bytes, grid, stream);
+                                  smem_bytes, slots_on_chip, grid, stream);
   AFC_BIG_CONFIGS(AFC_X)
 #undef AFC_X
   return cudaErrorInvalidValue;
@@ -246,10 +250,15 @@ uint32_t big_dist_smem_bytes(uint32_t n, uint32_t nslots) {
   return al16((uint32_t)sizeof(CtaCtl)) + nslots * al16(4u * n);
 }
 
+uint32_t big_slots_smem_bytes(uint32_t n, uint32_t nslots) {
+  return al16((uint32_t)sizeof(CtaCtl)) + nslots * big_slot_bytes(n);
+}
+
 cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision,
                              BigGroup *groups_d, uint32_t ngroups, uint32_t r_count,
                              unsigned char *arena, size_t slot_stride, uint32_t spt,
-                             uint32_t dist_smem_bytes, uint32_t grid, cudaStream_t stream) {
+                             uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
+                             cudaStream_t stream) {
   if (!big_config_supported(block, team)) return cudaErrorInvalidValue;
   const bool fp32 = (precision == 1);
   for (uint32_t r0 = 0; r0 < r_count; r0 += ngroups) {
@@ -257,13 +266,13 @@ cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, fp32 ? 1 : 0,
-                       dist_smem_bytes, grid, stream);
+                       smem_bytes, slots_on_chip, grid, stream);
     if (e != cudaSuccess) return e;
     big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, fp32 ? 1 : 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (fp32) {
       e = launch_brandes(block, team, Pd, groups_d, ngroups, arena, slot_stride, spt, 2,
-                         dist_smem_bytes, grid, stream);
+                         smem_bytes, slots_on_chip, grid, stream);
       if (e != cudaSuccess) return e;
       big_select_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, 0, 1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -90,6 +90,17 @@ def test_forced_global_team_configurations(B, T, spt):
     assert worst < 1e-9
 
 
+@pytest.mark.parametrize("B,T,spt", [(1024, 512, 1), (1024, 128, 1), (256, 64, 16)])
+def test_global_slot_placements_3000_nodes(B, T, spt):
+    """The three places of a CTA's source slots on the global path, chosen by size: n = 3000
+    gives 48 KB slots, so two slots (teams of 512) live wholly in shared memory, eight (teams
+    of 128) keep only their 12 KB distance arrays there, and 64 (16 per team of 64) stay in the
+    device arena."""
+    worst, _ = _check(_ws3000(), 2, 2, oracle_threads=8, full_counts=False, block_threads=B,
+                      team_threads=T, slots_per_team=spt, memory_path=GLOBAL)
+    assert worst < 1e-9
+
+
 def test_forced_global_fp32_recheck():
     """FP32 dependencies with the FP64 recheck on the global path report the FP64 centres."""
     for wl in mixed_batch(count=4, n_lo=200, n_hi=400, r_lo=8, r_hi=12):
