@@ -63,7 +63,7 @@ def _declare(L):
     L.orc_brandes.argtypes = [i32, P, P, P, P, P, P, P]
     L.orc_select.argtypes = [i32, P, P, P, u32, P, u32, f64, P]
     L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
-                                        u32, u32, u32, P, u32, f64, P, P]
+                                        u32, u32, u32, P, u32, f64, P, P, i32, P]
     L.orc_topk_order.argtypes = [i32, P, P, P, u32, u32, f64, P, P]
     L.orc_count_rewards.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P, u32,
                                     u32, u32, f64, u32, P, P, u32, P, P]
@@ -222,21 +222,59 @@ def count_transitions(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_
                       k_min, candidates=None, top_k=0, tie_rel=1e-9, counts=None):
     """Transition counts [n, n+1] (uint32, last column = absorption) for realizations
     r_begin .. r_begin + r_count - 1.  Returns (counts, n_sigma_overflow_realizations)."""
+    counts, _, ovf = _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                            candidates, top_k, tie_rel, -1, counts)
+    return counts, ovf
+
+
+def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, candidates,
+           top_k, tie_rel, fb_node, counts=None):
     th, th_all = thresholds(p_survive, g.m)
     lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
     hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
     inw = candidate_mask(g.n, candidates)
     if counts is None:
         counts = np.zeros((g.n, g.n + 1), np.uint32)
+    fb = np.zeros(max(g.n, 1), np.uint32) if fb_node >= 0 else None
     stats = np.zeros(1, np.uint64)
     st = lib().orc_count_transitions(
         g.n, g.m, _p(g.row_ptr), _p(g.col), _p(g.eid), seed, graph_tag, r_begin, r_count,
         _p(th), th_all, _p(lo_arr), _p(hi_arr),
         0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
-        k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats))
+        k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats), int(fb_node), _p(fb))
     if st not in (ORC_OK, ORC_EOVERFLOW):
         _check(st, "count_transitions")
-    return counts, int(stats[0])
+    return counts, (None if fb is None else fb[:g.n]), int(stats[0])
+
+
+def count_constrained(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi,
+                      k_min, candidates, top_k, fallback, tie_rel=1e-9, threads=1):
+    """Counts under the fallback selector Sel_{W,fb} (Sec. 7.3): a valid component with no
+    admissible candidate in W reports `fallback` instead of absorbing.  Returns (counts
+    [n, n+1], fb_count [n] = redirected draws per anchor, overflows); realization ranges split
+    over `threads` threads."""
+    threads = max(1, min(threads, r_count)) if r_count > 0 else 1
+    bounds = [r_begin + (r_count * t) // threads for t in range(threads + 1)]
+    parts = [None] * threads
+
+    def work(t):
+        parts[t] = _count(g, seed, graph_tag, bounds[t], bounds[t + 1] - bounds[t], p_survive,
+                          w_lo, w_hi, k_min, candidates, top_k, tie_rel, int(fallback))
+
+    ts = [threading.Thread(target=work, args=(t,)) for t in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    counts = np.zeros((g.n, g.n + 1), np.uint64)
+    fb = np.zeros(g.n, np.uint64)
+    ovf = 0
+    for c, f, o in parts:
+        counts += c
+        if f is not None:       # fallback < 0: nothing is redirected
+            fb += f
+        ovf += o
+    return counts.astype(np.uint32), fb.astype(np.uint32), ovf
 
 
 def count_transitions_parallel(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo,
@@ -320,6 +358,64 @@ def switching_psi(Q):
 
 
 # ---------------------------------------------------------------- linear algebra ----
+
+def feasibility(counts, fb_count, R, alpha, eta=1e-6):
+    """One-step feasibility xi_i = P_i(C_k(i) cap W nonempty) of the constrained kernel
+    (Sec. 7.1 eq. settopk-xi: xi_i = sum_{j in W} P^W_ij), estimated on the kernel assembled
+    from `counts`: every transient entry of row i carries the same row scale, so xi_i is the
+    row's transient mass times the share of its non-absorbed draws that reached W directly
+    (the fallback draws, fb_count, excluded; fb_count None = no fallback)."""
+    counts = np.ascontiguousarray(counts, dtype=np.uint32)
+    n = counts.shape[0]
+    Q, _ = assemble_q(counts, R, alpha, eta)
+    tot = counts[:, :n].astype(np.float64).sum(axis=1)
+    fb = np.zeros(n) if fb_count is None else np.asarray(fb_count, np.float64)
+    xi = np.zeros(n)
+    nz = tot > 0
+    xi[nz] = Q[nz].sum(axis=1) * (tot[nz] - fb[nz]) / tot[nz]
+    return xi
+
+
+def pool_summaries(b, in_w, fb_set=None):
+    """Pool mass m_W = sum_{v in W} b_v (Sec. 7.2 eq. settopk-bPsi), the within-pool profile
+    b_v / m_W on W, the non-fallback mass c_fb = sum_{u not in V_fb} b_u and the censored
+    profile b_v / c_fb off V_fb (Sec. 7.4).  Returns (m_W, b_pool, c_fb, b_censored); profiles
+    are 0 outside their sets and everywhere when their mass is 0."""
+    b = np.asarray(b, np.float64)
+    w = np.asarray(in_w).astype(bool)
+    fb = np.zeros(b.shape[0], bool) if fb_set is None else np.asarray(fb_set).astype(bool)
+    m_w = float(b[w].sum())
+    c_fb = float(b[~fb].sum())
+    b_pool = np.where(w, b / m_w, 0.0) if m_w > 0 else np.zeros_like(b)
+    b_cens = np.where(~fb, b / c_fb, 0.0) if c_fb > 0 else np.zeros_like(b)
+    return m_w, b_pool, c_fb, b_cens
+
+
+def clique_pool(n, eu, ev, S):
+    """3-clique target pool (Sec. 9 structure-constrained experiment): all triangles of the
+    base graph, scored by the sum of their nodes' base degrees, the S best kept (score
+    descending, ties by the ascending node triple), W = their union, v_fb = the smallest id of
+    the first kept triangle.  Returns (mask [n] uint8, v_fb or -1, kept triangles)."""
+    adj = [set() for _ in range(n)]
+    for a, c in zip(np.asarray(eu).tolist(), np.asarray(ev).tolist()):
+        adj[a].add(c)
+        adj[c].add(a)
+    deg = [len(x) for x in adj]
+    tri = []
+    for u in range(n):
+        for v in adj[u]:
+            if v <= u:
+                continue
+            for w in adj[u] & adj[v]:
+                if w > v:
+                    tri.append((u, v, w))
+    tri.sort(key=lambda t: (-(deg[t[0]] + deg[t[1]] + deg[t[2]]), t))
+    kept = tri[:S]
+    mask = np.zeros(n, np.uint8)
+    for t in kept:
+        mask[list(t)] = 1
+    return mask, (kept[0][0] if kept else -1), kept
+
 
 def gauss_solve(A, b):
     A = np.array(A, dtype=np.float64, order="C", copy=True)

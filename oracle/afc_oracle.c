@@ -365,6 +365,9 @@ void orc_select(int32_t n, const int32_t *comp, const int32_t *csize, const doub
 /* law depends only on the law of H, Prop. on order/branch invariance):                   */
 /*   next(i) = bottom if |K(i;H)| < k_min or K(i;H) has no admissible centre,             */
 /*   next(i) = centre of K(i;H) otherwise;  counts[i*(n+1) + next(i)] += 1 (bottom = n).  */
+/* Fallback selector Sel_{W,fb} (Sec. 7.3): with fb_node >= 0, a valid component whose    */
+/* candidate set admits no centre reports fb_node instead of bottom, and fb_count[i]      */
+/* (when given) counts those redirected draws; invalid components still absorb.           */
 /* Only sources inside valid components enter the betweenness (a vertex's betweenness     */
 /* only depends on sources of its own component).                                         */
 /* stats[0] += realizations whose sigma overflowed 64 bits.                               */
@@ -377,7 +380,8 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
                           const uint32_t *w_lo, const uint32_t *w_hi,
                           uint32_t w_lo_all, uint32_t w_hi_all,
                           uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
-                          uint32_t *counts, uint64_t *stats) {
+                          uint32_t *counts, uint64_t *stats, int32_t fb_node,
+                          uint32_t *fb_count) {
   size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
   uint8_t *alive = (uint8_t *)malloc(mm);
   uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
@@ -406,6 +410,10 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
     for (int32_t i = 0; i < n; ++i) {
       int32_t c = centre[comp[i]];
       size_t col_idx = (c < 0) ? (size_t)n : (size_t)c;
+      if (c < 0 && fb_node >= 0 && (uint32_t)csize[comp[i]] >= k_min) {
+        col_idx = (size_t)fb_node;
+        if (fb_count) fb_count[i] += 1u;
+      }
       counts[(size_t)i * (size_t)(n + 1) + col_idx] += 1u;
     }
   }
