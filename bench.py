@@ -486,6 +486,52 @@ def run_ws20000(args):
     return 0
 
 
+def run_constrained(args):
+    """The 1000-node workload under the set-constrained fallback kernel (Sec. 7.3) with the
+    paper's 3-clique target pool (Sec. 9: the 8 triangles of largest degree sum, v_fb = the
+    smallest id of the first), Top-5 filtering: counts, solve, feasibility xi and pool mass."""
+    import numpy as np
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+    torch.cuda.set_device(0)
+    wl = workload("ws1000")
+    mask, v_fb, tri = afc.afc_clique_pool(wl.n, wl.eu, wl.ev, 8)
+    wl.candidates = np.flatnonzero(mask).astype(np.int32)
+    wl.top_k = 5
+    R = args.constrained_realizations
+    q = afc.Query(wl, fallback_node=v_fb)
+    q.run_counts(0, 152)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    q.run_counts(0, R)
+    ev[1].record(stream)
+    q.wl.realizations = R
+    q.run_solve()
+    xi = q.feasibility()
+    ev[2].record(stream)
+    m_w, c_fb, _, _ = q.pool_summaries()
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    ms_c, ms_s, ms_p = (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                        ev[2].elapsed_time(ev[3]))
+    st = q.stats.cpu().numpy()
+    fb = q.fb_count.cpu().numpy()
+    xi = xi.cpu().numpy()
+    line = {"config": {"workload": "ws1000 under the fallback kernel P^W,fb: 3-clique pool "
+                                   "(8 triangles, %d nodes), Top-5 filter, v_fb = %d, %d "
+                                   "realizations" % (int(mask.sum()), v_fb, R)},
+            "metric": "realizations/s", "value": R / (ms_c / 1e3),
+            "gteps": float(st[2]) / (ms_c / 1e3) / 1e9, "counts_ms": ms_c,
+            "solve_and_xi_ms": ms_s, "pool_summaries_ms": ms_p,
+            "redirected_share": float(fb.sum()) / (R * wl.n), "xi_mean": float(xi.mean()),
+            "m_W_fb": m_w, "c_fb": c_fb, "device_error": int(st[5])}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     """The serving stream through the native serving loop: a closed batch of its first queries
     measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
@@ -549,11 +595,13 @@ def main():
                     help="run one counting launch of this many realizations and exit")
     ap.add_argument("--memory-path", default="auto", choices=["auto", "shared", "global"],
                     help="counting path of --counts-only")
-    ap.add_argument("--config", default="ws1000", choices=["ws1000", "mix", "ws20000", "serving"],
+    ap.add_argument("--config", default="ws1000",
+                    choices=["ws1000", "mix", "ws20000", "serving", "constrained"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
     ap.add_argument("--ws20000-sample", type=int, default=16)
+    ap.add_argument("--constrained-realizations", type=int, default=10_000)
     ap.add_argument("--serve-probe", type=int, default=6)
     ap.add_argument("--serve-queries", type=int, default=12,
                     help="Poisson arrivals in the rate-scaled serving run")
@@ -563,6 +611,8 @@ def main():
         return run_mix(args)
     if args.config == "ws20000":
         return run_ws20000(args)
+    if args.config == "constrained":
+        return run_constrained(args)
     if args.config == "serving":
         return run_serving(args)
     if args.counts_only:

@@ -126,6 +126,13 @@ typedef struct {
   uint32_t report_rank;      /* 0 or 1: report the centre; r > 1: report pi(r), the rank-r   */
                              /* centre (bottom if |K| < r).  reward_k > 0 or report_rank > 1 */
                              /* needs AFC_FP64, in_w NULL, top_k 0 and at most 256 ranks      */
+  /* Fallback selector Sel_{W,fb} (Sec. 7.3).  With use_fallback 0 a valid component whose     */
+  /* candidate set (in_w, top_k) admits no centre absorbs: the hard-filtered kernel P^W of     */
+  /* Sec. 7.1.  With 1 it reports fallback_node instead; invalid components still absorb.      */
+  int32_t use_fallback;
+  int32_t fallback_node;     /* v_fb in [0, n) (inside or outside W)                          */
+  uint32_t *fallback_count;  /* [n] DEVICE u32, accumulated (not cleared), or NULL: draws of  */
+                             /* anchor i redirected to v_fb (afc_feasibility needs them)       */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */
@@ -255,6 +262,37 @@ int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const in
  * Asynchronous on `stream`. */
 int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double *b,
                    const double *psi_sum, double *out, void *stream);
+
+/* Set-constrained kernels (Sec. 7).  Counts of the hard-filtered kernel P^W come from
+ * afc_transition_counts with in_w / top_k; of the fallback kernel P^{W,fb} with use_fallback,
+ * which also fills fallback_count.  b^W, b^{W,fb} and b^W . f come from afc_absorbing_solve on
+ * those counts (Sec. 7.2: the same linear-algebraic pipeline).
+ *
+ * afc_feasibility: xi[i] = sum_{j in W} P^W_ij (Sec. 7.1 eq. settopk-xi), the probability that
+ * a step from anchor i reaches the target pool directly, estimated on the kernel assembled from
+ * `counts` as afc_absorbing_solve assembles it: the row's transient mass times the share of its
+ * non-absorbed draws that were not redirected to v_fb.  DEVICE in: counts [n][n+1],
+ * fallback_count [n] (or NULL: no fallback).  DEVICE out: xi [n].  Asynchronous on `stream`. */
+int afc_feasibility(const afc_chain *chain, const uint32_t *counts, const uint32_t *fallback_count,
+                    double *xi, void *stream);
+
+/* afc_pool_summaries: mass[0] = m_W = sum_{v in W} b_v (Sec. 7.2 eq. settopk-bPsi; m_W^fb for
+ * the fallback kernel's b), mass[1] = c_fb = sum_{u not in V_fb} b_u (Sec. 7.4); b_pool[v] =
+ * b_v / m_W on W (the within-pool profile), b_censored[v] = b_v / c_fb off V_fb (fallback visits
+ * censored); both 0 elsewhere, and everywhere when their mass is 0.  DEVICE in: b [n], in_w [n]
+ * (pool mask W), fallback_set [n] (mask of V_fb, or NULL = empty).  DEVICE out: mass [2], b_pool
+ * [n] and b_censored [n] (each may be NULL).  One CTA; asynchronous on `stream`. */
+int afc_pool_summaries(int32_t n, const double *b, const uint8_t *in_w, const uint8_t *fallback_set,
+                       double *b_pool, double *b_censored, double *mass, void *stream);
+
+/* afc_clique_pool (host): the 3-clique target pool of the paper's structure-constrained
+ * experiment (Sec. 9): every triangle of the base graph (HOST edge lists eu, ev of length m, as
+ * afc_csr_from_edges), scored by the sum of its nodes' base degrees; the S best kept (score
+ * descending, ties by the ascending node triple).  HOST out: in_w [n] = their union,
+ * *fallback_node = smallest id of the first kept triangle (-1 if none), triangles [3 S] the kept
+ * (u < v < w) triples (or NULL), *kept = how many (or NULL).  Errors: AFC_EINVAL for bad edges. */
+int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t S,
+                    uint8_t *in_w, int32_t *fallback_node, int32_t *triangles, int32_t *kept);
 
 /* Allocation-free variant of afc_absorbing_solve (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory themselves, e.g. code embedded in a host framework

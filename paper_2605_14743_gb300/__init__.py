@@ -35,7 +35,7 @@ __all__ = [
     "afc_graph_create_csr", "afc_graph_nodes", "afc_graph_edges", "afc_graph_destroy",
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
-    "TuneResult", "afc_autotune",
+    "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -66,7 +66,8 @@ class McProblem(ctypes.Structure):
                 ("block_threads", c_i32), ("team_threads", c_i32),
                 ("slots_per_team", c_i32), ("memory_path", c_i32), ("reward_k", c_u32),
                 ("reward_gamma", c_p), ("reward_pool", c_p), ("psi_sum", c_p),
-                ("report_rank", c_u32)]
+                ("report_rank", c_u32), ("use_fallback", c_i32), ("fallback_node", c_i32),
+                ("fallback_count", c_p)]
 
 
 class McStats(ctypes.Structure):
@@ -148,6 +149,9 @@ _SIGS = {
     "afc_survival_threshold": ([c_f64], c_u64),
     "afc_transition_counts_workspace": ([ctypes.POINTER(McProblem)], c_sz),
     "afc_counts_path": ([ctypes.POINTER(McProblem)], ctypes.c_int),
+    "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
+    "afc_pool_summaries": ([c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
+    "afc_clique_pool": ([c_i32, c_i64, c_p, c_p, c_i32, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_autotune": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, ctypes.POINTER(TuneResult)],
                      ctypes.c_int),
     "afc_transition_counts": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, c_p, c_p, c_p, c_p,
@@ -271,6 +275,29 @@ def afc_autotune(prob: McProblem, r_begin: int, sample: int, stream) -> TuneResu
     _chk(lib().afc_autotune(ctypes.byref(prob), int(r_begin), int(sample), stream,
                             ctypes.byref(out)))
     return out
+
+
+def afc_feasibility(chain, counts, fallback_count, xi, stream):
+    _chk(lib().afc_feasibility(ctypes.byref(chain), _ptr(counts), _ptr(fallback_count), _ptr(xi),
+                               stream))
+
+
+def afc_pool_summaries(n, b, in_w, fallback_set, b_pool, b_censored, mass, stream):
+    _chk(lib().afc_pool_summaries(int(n), _ptr(b), _ptr(in_w), _ptr(fallback_set), _ptr(b_pool),
+                                  _ptr(b_censored), _ptr(mass), stream))
+
+
+def afc_clique_pool(n, eu, ev, S):
+    """3-clique target pool on the host: (mask [n] uint8, v_fb or -1, kept triangles [k, 3])."""
+    eu = np.ascontiguousarray(eu, np.int32)
+    ev = np.ascontiguousarray(ev, np.int32)
+    mask = np.zeros(max(int(n), 1), np.uint8)
+    fb = ctypes.c_int32(-1)
+    kept = ctypes.c_int32(0)
+    tri = np.zeros(3 * max(int(S), 1), np.int32)
+    _chk(lib().afc_clique_pool(int(n), int(eu.shape[0]), _ptr(eu), _ptr(ev), int(S), _ptr(mask),
+                               ctypes.byref(fb), _ptr(tri), ctypes.byref(kept)))
+    return mask[:int(n)], int(fb.value), tri[:3 * kept.value].reshape(-1, 3)
 
 
 def afc_transition_counts_workspace(prob: McProblem) -> int:

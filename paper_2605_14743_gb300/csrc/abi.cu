@@ -91,6 +91,13 @@ int validate(const afc_mc_problem *p) {
       return fail(AFC_EUNSUPPORTED, "at most 256 ranks per component");
     if (p->reward_k && !p->psi_sum) return fail(AFC_EINVAL, "reward_k needs psi_sum");
   }
+  if (p->use_fallback != 0 && p->use_fallback != 1) return fail(AFC_EINVAL, "use_fallback must be 0 or 1");
+  if (p->use_fallback) {
+    if (p->fallback_node < 0 || p->fallback_node >= p->n)
+      return fail(AFC_EINVAL, "fallback_node %d outside [0, n)", p->fallback_node);
+    if (p->reward_k || p->report_rank > 1)
+      return fail(AFC_EINVAL, "the fallback selector does not combine with rewards or rank-r reports");
+  }
   if (p->m < 0 || p->m > 0x3FFFFFFF) return fail(AFC_EINVAL, "m = %lld out of range", (long long)p->m);
   if (!p->row_ptr || (p->m > 0 && (!p->col || !p->eid)))
     return fail(AFC_EINVAL, "CSR pointers missing");
@@ -142,6 +149,8 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   d.reward_pool = p.reward_pool;
   d.psi = p.psi_sum;
   d.report_rank = p.report_rank;
+  d.fb_node = p.use_fallback ? (uint32_t)p.fallback_node : 0xFFFFFFFFu;
+  d.fb_count = p.use_fallback ? p.fallback_count : nullptr;
   d.r_begin = r_begin;
   d.counts = counts;
   d.stats = stats;
@@ -569,7 +578,8 @@ int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *
   for (size_t k = 0; k < cands.size() + 1 && st == AFC_OK; ++k) {
     // k = 0 warms up with the automatic configuration; k >= 1 times candidate k - 1
     afc_mc_problem c = cands[k == 0 ? 0 : k - 1];
-    if (psi) c.psi_sum = psi;   // the caller's accumulator is never touched
+    if (psi) c.psi_sum = psi;   // the caller's accumulators are never touched
+    c.fallback_count = nullptr;
     uint32_t *cs[1] = {counts};
     cudaEventRecord(e0, s);
     st = run_counts(1, &c, &r_begin, &sample, cs, nullptr, nullptr, nullptr, wsp, ws, s);
@@ -801,6 +811,46 @@ int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double 
                                     chain->absorb_floor, counts, b, psi_sum, out,
                                     (cudaStream_t)stream);
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "reward_afc");
+}
+
+int afc_feasibility(const afc_chain *chain, const uint32_t *counts, const uint32_t *fallback_count,
+                    double *xi, void *stream) {
+  if (!chain || !counts || !xi) return fail(AFC_EINVAL, "null argument");
+  if (chain->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
+  if (chain->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
+  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  cudaError_t e = launch_feasibility(chain->n, chain->realizations, chain->alpha,
+                                     chain->absorb_floor, counts, fallback_count, xi,
+                                     (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "feasibility");
+}
+
+int afc_pool_summaries(int32_t n, const double *b, const uint8_t *in_w, const uint8_t *fallback_set,
+                       double *b_pool, double *b_censored, double *mass, void *stream) {
+  if (n < 1 || !b || !in_w || !mass) return fail(AFC_EINVAL, "bad arguments");
+  cudaError_t e = launch_pool_summaries(n, b, in_w, fallback_set, b_pool, b_censored, mass,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "pool_summaries");
+}
+
+int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t S,
+                    uint8_t *in_w, int32_t *fallback_node, int32_t *triangles, int32_t *kept) {
+  if (n < 1 || m < 0 || S < 0 || !in_w || !fallback_node || (m > 0 && (!eu || !ev)))
+    return fail(AFC_EINVAL, "bad arguments");
+  std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
+      eid((size_t)std::max<int64_t>(2 * m, 1));
+  int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
+  if (st) return st;
+  std::vector<int32_t> tri;
+  clique_pool_host(n, rp.data(), col.data(), S, tri);
+  const int32_t k = (int32_t)(tri.size() / 3);
+  std::fill(in_w, in_w + n, (uint8_t)0);
+  for (int32_t t = 0; t < 3 * k; ++t) in_w[tri[t]] = 1;
+  *fallback_node = k > 0 ? tri[0] : -1;
+  if (triangles) std::copy(tri.begin(), tri.begin() + 3 * k, triangles);
+  if (kept) *kept = k;
+  return AFC_OK;
 }
 
 int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,

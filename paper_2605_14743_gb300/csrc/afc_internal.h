@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "afc.h"
@@ -41,6 +42,8 @@ struct McDev {
   const uint8_t *reward_pool;    // [n] or null (every node)
   double *psi;                   // [n] step-reward accumulator
   uint32_t report_rank;          // 0 / 1: the centre; r > 1: the r-th node of the ordering
+  uint32_t fb_node;              // fallback node v_fb, or 0xFFFFFFFF (infeasible draws absorb)
+  uint32_t *fb_count;            // [n] redirected draws per anchor, or null
   uint32_t *counts;
   afc_mc_stats *stats;
   double *dump_bc;
@@ -184,6 +187,18 @@ cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const doub
                                 const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                                 unsigned char *ws, const SolveWs &L, cudaStream_t stream);
 size_t perturb_slab_bytes(int32_t n, int32_t c);
+// constrained.cu: feasibility xi per row, pool mass / censoring summaries, 3-clique pools
+cudaError_t launch_feasibility(int32_t n, uint32_t R, double alpha, double eta,
+                               const uint32_t *counts, const uint32_t *fb_count, double *xi,
+                               cudaStream_t stream);
+cudaError_t launch_pool_summaries(int32_t n, const double *b, const uint8_t *in_w,
+                                  const uint8_t *fb_set, double *b_pool, double *b_censored,
+                                  double *mass, cudaStream_t stream);
+// Sets tri to the kept triangles as consecutive (u, v, w) triples (min(S, number of
+// triangles) of them).
+void clique_pool_host(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t S,
+                      std::vector<int32_t> &tri);
+
 cudaError_t launch_reward_afc(int32_t n, uint32_t R, double alpha, double eta,
                               const uint32_t *counts, const double *b, const double *psi_sum,
                               double *out, cudaStream_t stream);

@@ -966,7 +966,12 @@ __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const 
     uint32_t col = n;
     if (comp_valid(cinfo[root], P.k_min)) {
       const uint32_t c = centre[root];
-      if (c < n && (P.top_k == 0 || rank[root] <= P.top_k)) col = c;
+      if (c < n && (P.top_k == 0 || rank[root] <= P.top_k)) {
+        col = c;
+      } else if (P.fb_node < n) {   // Sel_{W,fb} (Sec. 7.3): valid but infeasible -> v_fb
+        col = P.fb_node;
+        if (P.fb_count) atomicAdd(&P.fb_count[i], 1u);
+      }
     }
     atomicAdd(&counts[(size_t)i * stride + col], 1u);
     if (P.dump_next) P.dump_next[(size_t)r_local * n + i] = (int32_t)col;

@@ -16,7 +16,8 @@ import numpy as np
 from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
-               afc_autotune, afc_transition_counts, afc_transition_counts_workspace)
+               afc_autotune, afc_feasibility, afc_pool_summaries, afc_transition_counts,
+               afc_transition_counts_workspace)
 
 
 def _torch():
@@ -117,7 +118,7 @@ class Query:
 
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
                  slots_per_team=0, stream=None, memory_path=0, reward_k=0, reward_gamma=None,
-                 reward_pool=None, report_rank=0):
+                 reward_pool=None, report_rank=0, fallback_node=None):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -155,6 +156,13 @@ class Query:
                                  bucket_width, block_threads, team_threads, slots_per_team,
                                  memory_path, reward_k, self.gamma, self.pool, self.psi,
                                  report_rank)
+        # fallback selector Sel_{W,fb}: infeasible valid draws report v_fb (counted per anchor)
+        self.fb_count = None
+        if fallback_node is not None:
+            self.fb_count = torch.zeros(n, dtype=torch.int32, device=device)
+            self.prob.use_fallback = 1
+            self.prob.fallback_node = int(fallback_node)
+            self.prob.fallback_count = self.fb_count.data_ptr()
         self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
         self.stats = torch.zeros(7, dtype=torch.int64, device=device)
         wsb = afc_transition_counts_workspace(self.prob)
@@ -184,6 +192,32 @@ class Query:
         ch.reward = None if self.f is None else self.f.data_ptr()
         return ch
 
+    def feasibility(self):
+        """xi [n] (device, FP64): per anchor, the estimated probability that a step reaches the
+        candidate pool directly (Sec. 7.1), on the counts of the last run_counts."""
+        xi = self.torch.empty(self.n, dtype=self.torch.float64, device=self.counts.device)
+        afc_feasibility(self.chain(), self.counts, self.fb_count, xi, self._stream())
+        return xi
+
+    def pool_summaries(self, fallback_set=None):
+        """(m_W, c_fb, b_pool, b_censored) of the last run_solve's b for the candidate pool W
+        (Sec. 7.2) and the fallback set (Sec. 7.4; default {fallback_node}, or none)."""
+        torch = self.torch
+        if self.in_w is None:
+            raise ValueError("pool summaries need a candidate pool")
+        fb = None
+        if fallback_set is not None or self.fb_count is not None:
+            m = np.zeros(self.n, np.uint8)
+            m[np.asarray([self.prob.fallback_node] if fallback_set is None else fallback_set,
+                         np.int64)] = 1
+            fb = torch.from_numpy(m).to(self.counts.device)
+        b_pool = torch.empty(self.n, dtype=torch.float64, device=self.counts.device)
+        b_cens = torch.empty_like(b_pool)
+        mass = torch.empty(2, dtype=torch.float64, device=self.counts.device)
+        afc_pool_summaries(self.n, self.b, self.in_w, fb, b_pool, b_cens, mass, self._stream())
+        mass = mass.cpu().numpy()
+        return float(mass[0]), float(mass[1]), b_pool, b_cens
+
     def autotune(self, r_begin=0, sample=0):
         """Picks the counting launch configuration by timing candidates on `sample`
         realizations (0 = the library's default sample) and resizes the workspace for it."""
@@ -200,6 +234,8 @@ class Query:
             self.stats.zero_()
             if self.psi is not None:
                 self.psi.zero_()
+            if self.fb_count is not None:
+                self.fb_count.zero_()
         r_count = int(self.wl.realizations) if r_count is None else int(r_count)
         afc_transition_counts(self.prob, r_begin, r_count, self.counts, self.stats, dump_bc,
                               dump_next, self.ws_counts, self.ws_counts.numel(), self._stream())

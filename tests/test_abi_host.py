@@ -117,3 +117,36 @@ def test_autotune_validates_before_touching_the_device():
         afc.afc_autotune(prob, 0, 4, None)
     assert e.value.code == afc.AFC_EINVAL
     assert prob.block_threads == 48 and prob.bucket_width == 0     # left as given
+
+
+def test_clique_pool_host_matches_oracle():
+    import oracle as O
+    from afc_inputs import crossroads_edges, er_edges, workload
+    eu, ev, _ = crossroads_edges()
+    mask, v_fb, tri = afc.afc_clique_pool(10, eu, ev, 2)
+    assert mask.tolist() == [1, 1, 1, 1, 1, 1, 0, 0, 0, 0] and v_fb == 0
+    assert tri.tolist() == [[0, 1, 2], [3, 4, 5]]
+    cases = [(40, *er_edges(40, 0.2, s)) for s in (1, 2, 3)]
+    wl = workload("ws1000")
+    cases.append((wl.n, wl.eu, wl.ev))
+    for n, eu, ev in cases:
+        for S in (0, 1, 8, 50):
+            mask, v_fb, tri = afc.afc_clique_pool(n, eu, ev, S)
+            omask, ofb, otri = O.clique_pool(n, eu, ev, S)
+            assert (mask == omask).all() and v_fb == ofb
+            assert [tuple(t) for t in tri.tolist()] == otri
+    assert afc.afc_clique_pool(5, [0, 1, 2, 3], [1, 2, 3, 4], 8)[1] == -1
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_clique_pool(4, [0, 1, 0], [1, 2, 1], 8)             # duplicate edge
+    assert e.value.code == afc.AFC_EINVAL
+
+
+def test_fallback_validation_without_device():
+    prob = afc.McProblem()
+    prob.n, prob.m, prob.row_ptr, prob.col, prob.eid = 10, 5, 8, 8, 8
+    prob.w_lo_all, prob.w_hi_all, prob.k_min = 1, 3, 1
+    for use, node, rk in ((1, 10, 0), (1, -1, 0), (2, 0, 0), (1, 3, 2)):
+        prob.use_fallback, prob.fallback_node, prob.reward_k = use, node, rk
+        with pytest.raises(afc.AfcError) as e:
+            afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)
+        assert e.value.code == afc.AFC_EINVAL
