@@ -53,6 +53,8 @@ i32, i64, u32, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctype
 
 def _declare(L):
     L.orc_philox4x32_10.argtypes = [P, P, P]
+    L.orc_bootstrap_weights.argtypes = [u32, u32, u64, P]
+    L.orc_bootstrap_weights.restype = None
     L.orc_philox4x64_10.argtypes = [P, P, P]
     L.orc_build_csr.argtypes = [i32, i64, P, P, P, P, P]
     L.orc_survival_threshold.argtypes = [f64]
@@ -415,6 +417,43 @@ def clique_pool(n, eu, ev, S):
     for t in kept:
         mask[list(t)] = 1
     return mask, (kept[0][0] if kept else -1), kept
+
+
+def bootstrap_weights(R, b, seed):
+    """Realization weights of bootstrap replicate b (multinomial: R draws with replacement)."""
+    w = np.zeros(max(int(R), 1), np.uint32)
+    lib().orc_bootstrap_weights(int(R), int(b), int(seed), _p(w))
+    return w[:int(R)]
+
+
+def counts_from_records(next_states, w=None):
+    """Transition counts [n, n+1] from per-realization next states next_states [R, n]
+    (value n = absorption), realization r counted w[r] times (default once)."""
+    rec = np.asarray(next_states, np.int64)
+    R, n = rec.shape
+    w = np.ones(R, np.uint64) if w is None else np.asarray(w, np.uint64)
+    counts = np.zeros((n, n + 1), np.uint64)
+    np.add.at(counts, (np.tile(np.arange(n), R), rec.ravel()), np.repeat(w, n))
+    return counts.astype(np.uint32)
+
+
+def bootstrap(next_states, alpha, B, seed, level=0.95, s=None, eta=1e-6):
+    """Realization-level bootstrap of b (Sec. 8): replicate b re-counts the records with the
+    weights of bootstrap_weights(R, b, seed) and solves the full chain.  Returns (b_rep [B, n],
+    T_rep [B], lo [n], hi [n]) with lo / hi the replicates at sorted positions
+    floor(q (B - 1)) and ceil((1 - q) (B - 1)), q = (1 - level) / 2."""
+    rec = np.asarray(next_states)
+    R, n = rec.shape
+    b_rep = np.zeros((B, n))
+    T_rep = np.zeros(B)
+    for b in range(B):
+        counts = counts_from_records(rec, bootstrap_weights(R, b, seed))
+        _, b_rep[b], T_rep[b], _ = solve_counts(counts, R, alpha, eta, s=s)
+    q = (1.0 - level) / 2.0
+    srt = np.sort(b_rep, axis=0, kind="stable")
+    lo = srt[int(np.floor(q * (B - 1)))]
+    hi = srt[int(np.ceil((1.0 - q) * (B - 1)))]
+    return b_rep, T_rep, lo, hi
 
 
 def gauss_solve(A, b):

@@ -423,6 +423,25 @@ out:
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Realization-level bootstrap weights (Sec. 8: nonparametric bootstrap of b by resampling */
+/* the draws with replacement; with realization sharing the draws of all anchors come from */
+/* the same realizations, so whole realizations are resampled).  Replicate b draws R       */
+/* indices k = 0 .. R-1: u = Philox4x32-10(counter (k, b, 0, 2), key = seed)[0], index =     */
+/* floor(u R / 2^32); w[r] = how often r was drawn (sum w = R).                             */
+/* ------------------------------------------------------------------------------------ */
+
+void orc_bootstrap_weights(uint32_t R, uint32_t b, uint64_t seed, uint32_t *w) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (uint32_t r = 0; r < R; ++r) w[r] = 0;
+  for (uint32_t k = 0; k < R; ++k) {
+    const uint32_t ctr[4] = {k, b, 0u, 2u};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    w[(uint32_t)(((uint64_t)out[0] * (uint64_t)R) >> 32)] += 1u;
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Ordered local Top-k of every valid component (Sec. 2.3: the component-wise top-k set   */
 /* of eq. topk-comp, the local top-k of Def. local-topk, and the rank-r centre of the      */
 /* remark after the Prop. on set-valued states).  The ordering pi of K repeats the          */
