@@ -532,6 +532,45 @@ def run_constrained(args):
     return 0
 
 
+def run_bootstrap(args):
+    """Bootstrap intervals of b on the 1000-node workload (Sec. 8): the 10,000-realization
+    counting run with its next-state records, the solve, then B realization-level replicates
+    (multinomial re-weighting of the records, one reduced FP64 solve each) and the 95%
+    percentile interval per node."""
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+    torch.cuda.set_device(0)
+    wl = workload("ws1000")
+    R, B = int(wl.realizations), args.bootstrap_replicates
+    q = afc.Query(wl)
+    rec = torch.empty((R, wl.n), dtype=torch.int32, device="cuda")
+    q.run_counts(0, R, dump_next=rec)
+    q.run_solve()
+    q.bootstrap(rec, B=8, seed=99)            # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lo, hi, _, T_rep = q.bootstrap(rec, B=B, seed=1, level=0.95)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b = q.b.cpu().numpy()
+    lo, hi = lo.cpu().numpy(), hi.cpu().numpy()
+    top = b.argsort()[::-1][:5]
+    line = {"config": {"workload": "ws1000 bootstrap: %d realizations (next-state records %.0f MB), "
+                                   "%d replicates, 95%% percentile intervals, c = %d"
+                                   % (R, R * wl.n * 4 / 1e6, B, q.c)},
+            "metric": "bootstrap replicates/s", "value": B / (ms / 1e3), "ms": ms,
+            "record_bytes_per_replicate": R * wl.n * 4,
+            "top5": [int(v) for v in top],
+            "top5_interval": [[float(lo[v]), float(b[v]), float(hi[v])] for v in top],
+            "T_rep_range": [float(T_rep.min()), float(T_rep.max())]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     """The serving stream through the native serving loop: a closed batch of its first queries
     measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
@@ -596,12 +635,13 @@ def main():
     ap.add_argument("--memory-path", default="auto", choices=["auto", "shared", "global"],
                     help="counting path of --counts-only")
     ap.add_argument("--config", default="ws1000",
-                    choices=["ws1000", "mix", "ws20000", "serving", "constrained"],
+                    choices=["ws1000", "mix", "ws20000", "serving", "constrained", "bootstrap"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
     ap.add_argument("--ws20000-sample", type=int, default=16)
     ap.add_argument("--constrained-realizations", type=int, default=10_000)
+    ap.add_argument("--bootstrap-replicates", type=int, default=200)
     ap.add_argument("--serve-probe", type=int, default=6)
     ap.add_argument("--serve-queries", type=int, default=12,
                     help="Poisson arrivals in the rate-scaled serving run")
@@ -613,6 +653,8 @@ def main():
         return run_ws20000(args)
     if args.config == "constrained":
         return run_constrained(args)
+    if args.config == "bootstrap":
+        return run_bootstrap(args)
     if args.config == "serving":
         return run_serving(args)
     if args.counts_only:

@@ -263,6 +263,27 @@ int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const in
 int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double *b,
                    const double *psi_sum, double *out, void *stream);
 
+/* Realization-level bootstrap of b (Sec. 8: nonparametric bootstrap intervals by resampling
+ * the draws with replacement; every anchor's draws come from the same realizations, so whole
+ * realizations are resampled).  Replicate b (0 <= b < B) draws R = chain->realizations indices
+ * k = 0 .. R-1 with u = Philox4x32-10(counter (k, b, 0, 2), key = seed)[0], realization
+ * floor(u R / 2^32); it re-counts the next-state records with those multiplicities and solves
+ * the reduced chain on the nominal observed states exactly as afc_absorbing_solve (states not
+ * re-drawn into keep only their initial mass, as they would as unobserved states).
+ * DEVICE in: next_states [R][n] int32 (the dump_next records of afc_transition_counts over the
+ * same realizations; n = absorption), c_index / c_list / c of afc_observed_states on the
+ * nominal counts.  DEVICE out: b_rep [B][n] (or NULL: kept in the workspace), T_rep [B] E_s[T]
+ * per replicate (or NULL), b_lo / b_hi [n] (or NULL): per node the replicates at sorted
+ * positions floor(q (B-1)) and ceil((1-q) (B-1)), q = (1 - level) / 2 (ties by replicate index).
+ * Workspace: afc_bootstrap_workspace bytes (fewer work with fewer resident replicates).
+ * SYNCHRONISES `stream`.  Errors: AFC_EINVAL for a record outside absorption and the observed
+ * states, AFC_ESINGULAR for a zero pivot. */
+size_t afc_bootstrap_workspace(int32_t n, int32_t c, uint32_t R, uint32_t B);
+int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int32_t *c_index,
+                  const int32_t *c_list, int32_t c, uint32_t B, uint64_t seed, double level,
+                  double *b_rep, double *T_rep, double *b_lo, double *b_hi, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
 /* Set-constrained kernels (Sec. 7).  Counts of the hard-filtered kernel P^W come from
  * afc_transition_counts with in_w / top_k; of the fallback kernel P^{W,fb} with use_fallback,
  * which also fills fallback_count.  b^W, b^{W,fb} and b^W . f come from afc_absorbing_solve on

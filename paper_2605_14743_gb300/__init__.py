@@ -36,6 +36,7 @@ __all__ = [
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
+    "afc_bootstrap_workspace", "afc_bootstrap",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -150,6 +151,9 @@ _SIGS = {
     "afc_transition_counts_workspace": ([ctypes.POINTER(McProblem)], c_sz),
     "afc_counts_path": ([ctypes.POINTER(McProblem)], ctypes.c_int),
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
+    "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
+    "afc_bootstrap": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_u32, c_u64, c_f64, c_p, c_p,
+                       c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_pool_summaries": ([c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_clique_pool": ([c_i32, c_i64, c_p, c_p, c_i32, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_autotune": ([ctypes.POINTER(McProblem), c_u32, c_u32, c_p, ctypes.POINTER(TuneResult)],
@@ -280,6 +284,18 @@ def afc_autotune(prob: McProblem, r_begin: int, sample: int, stream) -> TuneResu
 def afc_feasibility(chain, counts, fallback_count, xi, stream):
     _chk(lib().afc_feasibility(ctypes.byref(chain), _ptr(counts), _ptr(fallback_count), _ptr(xi),
                                stream))
+
+
+def afc_bootstrap_workspace(n, c, R, B) -> int:
+    return int(lib().afc_bootstrap_workspace(int(n), int(c), int(R), int(B)))
+
+
+def afc_bootstrap(chain, next_states, c_index, c_list, c, B, seed, level, b_rep, T_rep, b_lo,
+                  b_hi, workspace, workspace_bytes, stream):
+    _chk(lib().afc_bootstrap(ctypes.byref(chain), _ptr(next_states), _ptr(c_index), _ptr(c_list),
+                             int(c), int(B), int(seed), float(level), _ptr(b_rep), _ptr(T_rep),
+                             _ptr(b_lo), _ptr(b_hi), _ptr(workspace), int(workspace_bytes),
+                             stream))
 
 
 def afc_pool_summaries(n, b, in_w, fallback_set, b_pool, b_censored, mass, stream):

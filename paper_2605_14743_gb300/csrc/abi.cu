@@ -784,6 +784,65 @@ int afc_perturb_sweep(const afc_chain *chain, const afc_perturb_params *pp, cons
   return AFC_OK;
 }
 
+// Bootstrap workspace: [status | b_rep [B][n] | per-CTA slabs], at most 4 GB of slabs.
+static size_t boot_ws_head(int32_t n, uint32_t B) {
+  return 256 + ((8ull * (size_t)B * (size_t)n + 255) & ~size_t(255));
+}
+
+size_t afc_bootstrap_workspace(int32_t n, int32_t c, uint32_t R, uint32_t B) {
+  if (n < 1 || c < 0 || c > n || R == 0 || B == 0) return 0;
+  const DevInfo d = dev_info();
+  const size_t slab = bootstrap_slab_bytes(n, c, R);
+  size_t grid = std::min<size_t>((size_t)B, (size_t)std::max(1, d.sms) * 2);
+  grid = std::max<size_t>(1, std::min<size_t>(grid, (4ull << 30) / std::max<size_t>(slab, 1)));
+  return boot_ws_head(n, B) + grid * slab;
+}
+
+int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int32_t *c_index,
+                  const int32_t *c_list, int32_t c, uint32_t B, uint64_t seed, double level,
+                  double *b_rep, double *T_rep, double *b_lo, double *b_hi, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+  if (!chain || !next_states || !c_index || !c_list) return fail(AFC_EINVAL, "null argument");
+  if (chain->n < 1 || c < 0 || c > chain->n) return fail(AFC_EINVAL, "bad n or c");
+  if (chain->realizations == 0 || B == 0) return fail(AFC_EINVAL, "realizations and B must be > 0");
+  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (!(level > 0.0 && level < 1.0)) return fail(AFC_EINVAL, "level outside (0, 1)");
+  const int32_t n = chain->n;
+  const uint32_t R = chain->realizations;
+  const size_t head = boot_ws_head(n, B);
+  const size_t slab = bootstrap_slab_bytes(n, c, R);
+  if (!workspace || workspace_bytes < head + slab)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, at least %zu needed", workspace_bytes,
+                head + slab);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  double *rep = b_rep ? b_rep : reinterpret_cast<double *>(ws + 256);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  ChainDev C{};
+  C.n = n;
+  C.R = R;
+  C.alpha = chain->alpha;
+  C.eta = chain->absorb_floor;
+  C.s = chain->s_init;
+  C.f = chain->reward;
+  C.c_index = c_index;
+  C.c_list = c_list;
+  C.c = c;
+  const DevInfo d = dev_info();
+  cudaError_t e = launch_bootstrap(C, next_states, R, B, seed, level, rep, T_rep, b_lo, b_hi,
+                                   ws + head, workspace_bytes - head, status, d.sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "bootstrap launch");
+  uint32_t st_host = 0;
+  AFC_CUDA(cudaMemcpyAsync(&st_host, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AFC_CUDA(cudaStreamSynchronize(s));
+  if (st_host & kErrInput)
+    return fail(AFC_EINVAL, "a next state is neither absorption nor an observed state of c_index");
+  if (st_host & kErrSolve) return fail(AFC_ESINGULAR, "zero pivot in a bootstrap replicate");
+  return AFC_OK;
+}
+
 int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32_t *c_index,
                      const int32_t *c_list, int32_t c, const double *mu0, const double *lu0,
                      const int32_t *piv0, double eps_bar, double r_min, int32_t npairs,

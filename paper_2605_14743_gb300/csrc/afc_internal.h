@@ -187,6 +187,13 @@ cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const doub
                                 const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                                 unsigned char *ws, const SolveWs &L, cudaStream_t stream);
 size_t perturb_slab_bytes(int32_t n, int32_t c);
+// bootstrap.cu: realization-level bootstrap replicates of b and their percentile intervals
+size_t bootstrap_slab_bytes(int32_t n, int32_t c, uint32_t R);
+cudaError_t launch_bootstrap(const ChainDev &C, const int32_t *rec, uint32_t R, uint32_t B,
+                             uint64_t seed, double level, double *b_rep, double *T_rep,
+                             double *lo, double *hi, unsigned char *slabs, size_t slab_space,
+                             uint32_t *status, int num_sms, cudaStream_t stream);
+
 // constrained.cu: feasibility xi per row, pool mass / censoring summaries, 3-clique pools
 cudaError_t launch_feasibility(int32_t n, uint32_t R, double alpha, double eta,
                                const uint32_t *counts, const uint32_t *fb_count, double *xi,

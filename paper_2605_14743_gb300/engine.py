@@ -16,7 +16,8 @@ import numpy as np
 from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
-               afc_autotune, afc_feasibility, afc_pool_summaries, afc_transition_counts,
+               afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility,
+               afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
 
 
@@ -191,6 +192,22 @@ class Query:
         ch.s_init = None if self.s is None else self.s.data_ptr()
         ch.reward = None if self.f is None else self.f.data_ptr()
         return ch
+
+    def bootstrap(self, next_states, B=200, seed=1, level=0.95):
+        """Realization-level bootstrap of b (Sec. 8) from the next-state records [R, n] of the
+        last run_counts (its dump_next) and the observed states of the last run_solve.
+        Returns (b_lo [n], b_hi [n], b_rep [B, n], T_rep [B]) as device tensors."""
+        torch = self.torch
+        dev = self.counts.device
+        wsb = afc_bootstrap_workspace(self.n, self.c, int(self.wl.realizations), B)
+        ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+        b_rep = torch.empty((B, self.n), dtype=torch.float64, device=dev)
+        T_rep = torch.empty(B, dtype=torch.float64, device=dev)
+        lo = torch.empty(self.n, dtype=torch.float64, device=dev)
+        hi = torch.empty_like(lo)
+        afc_bootstrap(self.chain(), next_states, self.c_index, self.c_list, self.c, B, seed, level,
+                      b_rep, T_rep, lo, hi, ws, ws.numel(), self._stream())
+        return lo, hi, b_rep, T_rep
 
     def feasibility(self):
         """xi [n] (device, FP64): per anchor, the estimated probability that a step reaches the
