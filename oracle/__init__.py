@@ -78,7 +78,9 @@ def _declare(L):
     L.orc_certificates.argtypes = [i32, P, P, f64, f64, i32, P, P, P, P, P]
     L.orc_perturb_row.argtypes = [i32, P, f64, u64, u32, u32, f64, f64, P, P]
     L.orc_perturb_sweep.argtypes = [i32, P, P, P, u32, u32, f64, f64, u64, i32, i32, i32, f64,
-                                    P, P, P, P, P, P]
+                                    P, P, P, P, P, P, i32, P]
+    L.orc_perturb_row_mult.argtypes = [i32, P, u64, u32, u32, f64, f64, P, P]
+    L.orc_perturb_row_mult.restype = None
     for name in ("orc_build_csr", "orc_components", "orc_sssp", "orc_brandes",
                  "orc_count_transitions", "orc_count_rewards", "orc_gauss_solve", "orc_afc_from_q", "orc_solve_full",
                  "orc_solve_reduced", "orc_certificates", "orc_perturb_sweep"):
@@ -540,6 +542,15 @@ def perturb_row(q0, r0, seed, i, p, radius, r_min):
     return q, r.value
 
 
+def perturb_row_mult(q0, seed, i, p, rel, r_min):
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    n = q0.shape[0]
+    q = np.zeros(n)
+    r = ctypes.c_double(0)
+    lib().orc_perturb_row_mult(n, _p(q0), seed, i, p, rel, r_min, _p(q), ctypes.byref(r))
+    return q, r.value
+
+
 @dataclass
 class PerturbStats:
     top1_changes: int
@@ -552,10 +563,13 @@ class PerturbStats:
     max_rowsum_N: float
     b: Optional[np.ndarray] = None       # [p_count, n] if requested
     ranks: Optional[np.ndarray] = None   # [p_count, n] if requested
+    kl: Optional[np.ndarray] = None      # [p_count] KL(b' || b0) if requested
 
 
 def perturb_sweep(Q0, r0, s, p_begin, p_count, radius, r_min, seed, top_k=5, K2=10, H=16,
-                  tie_rel=1e-9, keep=False) -> PerturbStats:
+                  tie_rel=1e-9, keep=False, model=0) -> PerturbStats:
+    """model 0: l1 row model (radius = l1 radius); 1: multiplicative (radius = relative
+    radius).  keep=True also returns b' and ranks per perturbation and KL(b' || b0)."""
     Q0 = np.ascontiguousarray(Q0, dtype=np.float64)
     r0 = np.ascontiguousarray(r0, dtype=np.float64)
     n = Q0.shape[0]
@@ -566,8 +580,32 @@ def perturb_sweep(Q0, r0, s, p_begin, p_count, radius, r_min, seed, top_k=5, K2=
     of = np.zeros(3, np.float64)
     b_out = np.zeros((p_count, n)) if keep else None
     r_out = np.zeros((p_count, n), np.int32) if keep else None
+    kl = np.zeros(max(p_count, 1)) if keep else None
     _check(lib().orc_perturb_sweep(n, _p(Q0), _p(r0), _p(s_), p_begin, p_count, radius, r_min,
                                    seed, top_k, K2, H, tie_rel, _p(oc), _p(pf), _p(sh), _p(of),
-                                   _p(b_out), _p(r_out)), "perturb_sweep")
+                                   _p(b_out), _p(r_out), int(model), _p(kl)), "perturb_sweep")
     return PerturbStats(int(oc[0]), int(oc[1]), int(oc[2]), pf.reshape(K2, K2), sh,
-                        float(of[0]), float(of[1]), float(of[2]), b_out, r_out)
+                        float(of[0]), float(of[1]), float(of[2]), b_out, r_out,
+                        None if kl is None else kl[:p_count])
+
+
+def w1_graph(n, eu, ev, x, y):
+    """Wasserstein-1 distance between distributions x and y on the nodes with the base
+    graph's shortest-path (hop) metric (Sec. 9 robust experiment): the transshipment LP
+    min sum_e (f+_e + f-_e) with net outflow x - y at every node (Beckmann's formulation),
+    solved by scipy's HiGHS.  Assumes sum x = sum y and a connected support."""
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    eu = np.asarray(eu, np.int64)
+    ev = np.asarray(ev, np.int64)
+    m = eu.shape[0]
+    e = np.arange(m)
+    rows = np.concatenate([eu, ev, ev, eu])
+    cols = np.concatenate([e, e, m + e, m + e])
+    vals = np.concatenate([np.ones(m), -np.ones(m), np.ones(m), -np.ones(m)])
+    A = coo_matrix((vals, (rows, cols)), shape=(n, 2 * m)).tocsr()
+    res = linprog(np.ones(2 * m), A_eq=A, b_eq=np.asarray(x, np.float64) - np.asarray(y, np.float64),
+                  bounds=(0, None), method="highs")
+    if not res.success:
+        raise RuntimeError("w1_graph: " + res.message)
+    return float(res.fun)

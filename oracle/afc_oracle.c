@@ -834,11 +834,41 @@ void orc_perturb_row(int32_t n, const double *q0, double r0, uint64_t seed, uint
   *r = ra;
 }
 
+/* Multiplicative row perturbation (Sec. 9 robust experiment): every transient entry with  */
+/* q0_j > 0 becomes min(max(q0_j (1 + rel z_j), 0), 1), z_j = 2u - 1 with u from counter   */
+/* (j, i, p, 1); if the transient sum exceeds 1 - r_min it is scaled to 1 - r_min; the     */
+/* absorption is the remainder 1 - sum_j q_j.  (r0 is not used: absorption is implied.)    */
+void orc_perturb_row_mult(int32_t n, const double *q0, uint64_t seed, uint32_t i, uint32_t p,
+                          double rel, double r_min, double *q, double *r) {
+  double ts = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    q[j] = 0.0;
+    if (q0[j] > 0.0) {
+      double z = 2.0 * perturb_uniform(seed, (uint32_t)j, i, p) - 1.0;
+      double v = q0[j] * (1.0 + rel * z);
+      if (v < 0.0) v = 0.0;
+      if (v > 1.0) v = 1.0;
+      q[j] = v;
+      ts += v;
+    }
+  }
+  if (ts > 1.0 - r_min) {
+    double f = (1.0 - r_min) / ts;
+    ts = 0.0;
+    for (int32_t j = 0; j < n; ++j) { q[j] *= f; ts += q[j]; }
+  }
+  *r = 1.0 - ts;
+}
+
+/* model 0: the l1 row model of orc_perturb_row (radius = l1 radius); model 1: the          */
+/* multiplicative model of orc_perturb_row_mult (radius = relative radius).  kl_out[k]     */
+/* (optional) = KL(b' || b0) = sum_v b'_v log(b'_v / b0_v) of perturbation p_begin + k.     */
 int orc_perturb_sweep(int32_t n, const double *Q0, const double *r0, const double *s,
                       uint32_t p_begin, uint32_t p_count, double radius, double r_min,
                       uint64_t seed, int32_t top_k, int32_t K2, int32_t H, double tie_rel,
                       uint64_t *out_counts, uint64_t *pair_flips, uint64_t *shift_hist,
-                      double *out_f64, double *b_out, int32_t *rank_out) {
+                      double *out_f64, double *b_out, int32_t *rank_out, int32_t model,
+                      double *kl_out) {
   size_t nn = (size_t)n;
   double *Qp = (double *)malloc(sizeof(double) * nn * nn);
   double *rp = (double *)malloc(sizeof(double) * nn);
@@ -867,12 +897,23 @@ int orc_perturb_sweep(int32_t n, const double *Q0, const double *r0, const doubl
   for (int32_t h = 0; h < H; ++h) shift_hist[h] = 0;
   for (uint32_t k = 0; k < p_count; ++k) {
     uint32_t p = p_begin + k;
-    for (int32_t i = 0; i < n; ++i)
-      orc_perturb_row(n, Q0 + (size_t)i * nn, r0[i], seed, (uint32_t)i, p, radius, r_min,
-                      Qp + (size_t)i * nn, rp + i);
+    for (int32_t i = 0; i < n; ++i) {
+      if (model == 1)
+        orc_perturb_row_mult(n, Q0 + (size_t)i * nn, seed, (uint32_t)i, p, radius, r_min,
+                             Qp + (size_t)i * nn, rp + i);
+      else
+        orc_perturb_row(n, Q0 + (size_t)i * nn, r0[i], seed, (uint32_t)i, p, radius, r_min,
+                        Qp + (size_t)i * nn, rp + i);
+    }
     double T = 0.0;
     st = orc_afc_from_q(n, Qp, s, NULL, mu, b, &T, NULL);
     if (st != ORC_OK) goto out;
+    if (kl_out) {
+      double kl = 0.0;
+      for (int32_t v = 0; v < n; ++v)
+        if (b[v] > 0.0) kl += b[v] * log(b[v] / b0[v]);
+      kl_out[k] = kl;
+    }
     /* first-order prediction: x = mu0 E, then y = x N0 (solve (I - Q0)^T y^T = x^T) */
     for (int32_t j = 0; j < n; ++j) {
       double acc = 0.0;

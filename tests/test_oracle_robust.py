@@ -1,0 +1,84 @@
+"""Pins of the oracle's robust-search pieces (Sec. 9 robust sensitivity experiment, Remark on
+the robust optimisation viewpoint in Sec. 5): the multiplicative row model with its leak
+enforcement, KL(b' || b0) per sampled kernel, and the Wasserstein-1 distance on the base graph's
+hop metric (closed form on a path, an independent transport LP over all-pairs distances)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from afc_inputs import er_edges, workload
+from tests._util import variant
+
+
+def test_w1_closed_form_on_a_path_and_transport_lp():
+    rng = np.random.default_rng(3)
+    n = 12
+    eu, ev = np.arange(n - 1), np.arange(1, n)
+    for _ in range(5):
+        x, y = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(n))
+        # on a path the transport cost is the l1 distance of the cumulative distributions
+        ref = np.abs(np.cumsum(x - y)[:-1]).sum()
+        assert abs(O.w1_graph(n, eu, ev, x, y) - ref) <= 1e-9
+    nx = pytest.importorskip("networkx")
+    from scipy.optimize import linprog
+    for seed in (1, 2):
+        n = 15
+        eu, ev = er_edges(n, 0.3, seed)
+        G = nx.Graph()
+        G.add_nodes_from(range(n))
+        G.add_edges_from(zip(eu.tolist(), ev.tolist()))
+        if not nx.is_connected(G):
+            continue
+        D = np.array([[nx.shortest_path_length(G, a, b) for b in range(n)] for a in range(n)], float)
+        x, y = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(n))
+        # Kantorovich transport plan over all pairs: rows sum to x, columns to y
+        A = np.zeros((2 * n, n * n))
+        for a in range(n):
+            A[a, a * n:(a + 1) * n] = 1.0
+            A[n + a, a::n] = 1.0
+        res = linprog(D.ravel(), A_eq=A, b_eq=np.concatenate([x, y]), bounds=(0, None),
+                      method="highs")
+        assert abs(O.w1_graph(n, eu, ev, x, y) - res.fun) <= 1e-9
+        assert O.w1_graph(n, eu, ev, x, x) <= 1e-12
+        assert abs(O.w1_graph(n, eu, ev, x, y) - O.w1_graph(n, eu, ev, y, x)) <= 1e-9
+
+
+def test_multiplicative_row_model():
+    rng = np.random.default_rng(5)
+    n, rel, r_min = 40, 0.5, 0.05
+    q0 = np.zeros(n)
+    sup = rng.choice(n, 10, replace=False)
+    q0[sup] = rng.dirichlet(np.ones(10)) * 0.5          # transient mass 0.5: never rescaled
+    ratios = []
+    for p in range(400):
+        q, r = O.perturb_row_mult(q0, 9, 3, p, rel, r_min)
+        assert (q[q0 == 0] == 0).all()
+        ratio = q[sup] / q0[sup]
+        assert (ratio >= 1 - rel - 1e-12).all() and (ratio <= 1 + rel + 1e-12).all()
+        assert abs(r - (1 - q.sum())) <= 1e-15
+        ratios.append(ratio)
+    # z uniform on [-1, 1]: the mean ratio is 1 within the CLT band of rel / sqrt(3 N)
+    assert np.all(np.abs(np.mean(ratios, axis=0) - 1) <= 5 * rel / np.sqrt(3 * 400))
+    q0 = q0 / q0.sum() * 0.94                           # near the leak bound: often rescaled
+    hits = 0
+    for p in range(200):
+        q, r = O.perturb_row_mult(q0, 9, 3, p, rel, r_min)
+        assert q.sum() <= 1 - r_min + 1e-15 and r >= r_min - 1e-15
+        hits += abs(q.sum() - (1 - r_min)) <= 1e-15
+    assert hits > 20
+
+
+def test_multiplicative_sweep_kl():
+    wl = variant(workload("small_er"), realizations=300)
+    g = O.build_graph(wl.n, wl.eu, wl.ev)
+    counts, _ = O.count_transitions(g, wl.seed, wl.graph_tag, 0, 300, wl.p_survive, wl.w_lo,
+                                    wl.w_hi, wl.k_min)
+    Q0, r0 = O.assemble_q(counts, 300, wl.alpha)
+    # zero radius: the nominal kernel itself (its leak alpha = 0.15 >= r_min), b' = b0, KL 0
+    st = O.perturb_sweep(Q0, r0, None, 0, 5, 0.0, 0.05, 3, keep=True, model=1)
+    assert np.abs(st.kl).max() <= 1e-15 and st.max_db <= 1e-15 and st.top1_changes == 0
+    st = O.perturb_sweep(Q0, r0, None, 0, 40, 0.5, 0.05, 3, keep=True, model=1)
+    _, b0, _, _ = O.afc_from_q(Q0)
+    assert (st.kl >= 0).all() and st.kl.max() > 0      # Gibbs' inequality, strict somewhere
+    k = int(st.kl.argmax())
+    assert st.kl[k] == pytest.approx(float(np.sum(st.b[k] * np.log(st.b[k] / b0))), rel=1e-12)
