@@ -284,6 +284,14 @@ int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int3
                   double *b_rep, double *T_rep, double *b_lo, double *b_hi, void *workspace,
                   size_t workspace_bytes, void *stream);
 
+/* Wasserstein-1 distances under the base graph's shortest-path (hop) metric, the second
+ * discrepancy of the paper's robust search (Sec. 9): out[k] = W1(x_k, y) for the `count` HOST
+ * rows x_k = x + k n (each summing to sum y), over the HOST edge lists eu, ev (as
+ * afc_csr_from_edges).  Exact (successive shortest paths on the graph; masses settled to a
+ * relative 1e-14).  Host code.  Errors: AFC_EINVAL for bad edges. */
+int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
+                 const double *y, int32_t count, double *out);
+
 /* Set-constrained kernels (Sec. 7).  Counts of the hard-filtered kernel P^W come from
  * afc_transition_counts with in_w / top_k; of the fallback kernel P^{W,fb} with use_fallback,
  * which also fills fallback_count.  b^W, b^{W,fb} and b^W . f come from afc_absorbing_solve on
@@ -352,6 +360,15 @@ typedef struct {
   int32_t k2;                /* nominal top-k2 nodes tracked for pair flips / shifts (10)  */
   int32_t hist_bins;         /* bins of the rank-shift histogram (16)                      */
   double tie_rel;
+  /* Row model.  0: the l1 model above.  1: the multiplicative model of the paper's robust   */
+  /* experiment (Sec. 9): every transient entry with Q_ij > 0 becomes                         */
+  /* min(max(Q_ij (1 + rel_radius z_j), 0), 1) (z_j as above, no draw for absorption); a     */
+  /* transient sum above 1 - r_min is scaled to 1 - r_min; the absorption is the remainder.  */
+  int32_t model;
+  double rel_radius;         /* model 1: relative radius (0.5 in the experiment)            */
+  double *kl_out;            /* [p_count] DEVICE or NULL: KL(b' || b0) = sum_v b'_v          */
+                             /* log(b'_v / b0_v) per perturbation (the robust search's       */
+                             /* discrepancy; pair it with b_out to pick the maximiser)        */
 } afc_perturb_params;
 
 /* DEVICE outputs (accumulated, caller zeroes): counters [3] = {top-1 changes, top-k set

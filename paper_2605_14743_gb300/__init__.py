@@ -36,7 +36,7 @@ __all__ = [
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
-    "afc_bootstrap_workspace", "afc_bootstrap",
+    "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -85,7 +85,7 @@ class Chain(ctypes.Structure):
 class PerturbParams(ctypes.Structure):
     _fields_ = [("p_begin", c_u32), ("p_count", c_u32), ("l1_radius", c_f64), ("r_min", c_f64),
                 ("seed", c_u64), ("top_k", c_i32), ("k2", c_i32), ("hist_bins", c_i32),
-                ("tie_rel", c_f64)]
+                ("tie_rel", c_f64), ("model", c_i32), ("rel_radius", c_f64), ("kl_out", c_p)]
 
 
 class HostQuery(ctypes.Structure):
@@ -152,6 +152,7 @@ _SIGS = {
     "afc_counts_path": ([ctypes.POINTER(McProblem)], ctypes.c_int),
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
+    "afc_w1_graph": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_i32, c_p], ctypes.c_int),
     "afc_bootstrap": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_u32, c_u64, c_f64, c_p, c_p,
                        c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_pool_summaries": ([c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
@@ -296,6 +297,18 @@ def afc_bootstrap(chain, next_states, c_index, c_list, c, B, seed, level, b_rep,
                              int(c), int(B), int(seed), float(level), _ptr(b_rep), _ptr(T_rep),
                              _ptr(b_lo), _ptr(b_hi), _ptr(workspace), int(workspace_bytes),
                              stream))
+
+
+def afc_w1_graph(n, eu, ev, x, y):
+    """W1 between each row of x ([k, n] or [n], host) and y ([n]) on the graph's hop metric."""
+    eu = np.ascontiguousarray(eu, np.int32)
+    ev = np.ascontiguousarray(ev, np.int32)
+    x = np.ascontiguousarray(np.atleast_2d(x), np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    out = np.zeros(x.shape[0])
+    _chk(lib().afc_w1_graph(int(n), int(eu.shape[0]), _ptr(eu), _ptr(ev), _ptr(x), _ptr(y),
+                            int(x.shape[0]), _ptr(out)))
+    return out
 
 
 def afc_pool_summaries(n, b, in_w, fallback_set, b_pool, b_censored, mass, stream):

@@ -769,6 +769,8 @@ int afc_perturb_sweep(const afc_chain *chain, const afc_perturb_params *pp, cons
     return fail(AFC_EINVAL, "need 1 <= top_k <= k2 <= 32 and 1 <= hist_bins <= 64");
   if (!(pp->l1_radius >= 0.0) || !(pp->r_min >= 0.0 && pp->r_min < 1.0) || !(pp->tie_rel >= 0.0))
     return fail(AFC_EINVAL, "bad perturbation parameters");
+  if ((pp->model != 0 && pp->model != 1) || (pp->model == 1 && !(pp->rel_radius >= 0.0)))
+    return fail(AFC_EINVAL, "model must be 0 (l1) or 1 (multiplicative, rel_radius >= 0)");
   const SolveWs L = ws_layout_for(chain->n, c);
   if (!workspace || workspace_bytes < L.total)
     return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, L.total);
@@ -909,6 +911,19 @@ int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, 
   *fallback_node = k > 0 ? tri[0] : -1;
   if (triangles) std::copy(tri.begin(), tri.begin() + 3 * k, triangles);
   if (kept) *kept = k;
+  return AFC_OK;
+}
+
+int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
+                 const double *y, int32_t count, double *out) {
+  if (n < 1 || m < 0 || count < 0 || !x || !y || !out || (m > 0 && (!eu || !ev)))
+    return fail(AFC_EINVAL, "bad arguments");
+  std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
+      eid((size_t)std::max<int64_t>(2 * m, 1));
+  int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
+  if (st) return st;
+  for (int32_t k = 0; k < count; ++k)
+    out[k] = w1_graph_host(n, rp.data(), col.data(), eid.data(), x + (size_t)k * n, y);
   return AFC_OK;
 }
 

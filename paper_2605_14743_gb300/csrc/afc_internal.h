@@ -194,6 +194,10 @@ cudaError_t launch_bootstrap(const ChainDev &C, const int32_t *rec, uint32_t R, 
                              double *lo, double *hi, unsigned char *slabs, size_t slab_space,
                              uint32_t *status, int num_sms, cudaStream_t stream);
 
+// robust.cu: Wasserstein-1 distance of two node distributions on the graph's hop metric
+double w1_graph_host(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *eid,
+                     const double *x, const double *y);
+
 // constrained.cu: feasibility xi per row, pool mass / censoring summaries, 3-clique pools
 cudaError_t launch_feasibility(int32_t n, uint32_t R, double alpha, double eta,
                                const uint32_t *counts, const uint32_t *fb_count, double *xi,

@@ -1,5 +1,7 @@
 // perturb.cu -- A9: row-wise perturbation sweep of the estimated kernel (Sec. 5.1 row-wise
-// uncertainty, Sec. 5.4 first-order sensitivity, Sec. 5.5 ranking reversals).
+// uncertainty, Sec. 5.4 first-order sensitivity, Sec. 5.5 ranking reversals), with the l1 row
+// model or the multiplicative one of the robust experiment (Sec. 9), and KL(b' || b0) per
+// perturbation for the sampled robust search (Remark on the robust optimisation viewpoint).
 //
 // One CTA handles one perturbation p at a time (persistent over p).  The perturbation is
 // regenerated from Philox (counter (column, row, p, 1)), never stored: every row i is moved on
@@ -178,53 +180,110 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
             const int32_t pj = nzcol[e];
             col[t] = pj;
             q0[t] = nzval[e];
-            const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
-            const int32_t zi = (int32_t)(draw_u32(node, (uint32_t)i, p, k0, k1) - 0x80000000u);
-            isum += zi;
-            z[t] = (double)zi * kTwoM31;
+            if (pp.model == 0 || pj < c) {
+              const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
+              const int32_t zi = (int32_t)(draw_u32(node, (uint32_t)i, p, k0, k1) - 0x80000000u);
+              isum += zi;
+              z[t] = (double)zi * kTwoM31;
+            }
           }
         }
-        const double mean = (double)warp_sum_ll(isum) * kTwoM31 / (double)supp;
-        double l1 = 0.0;
+        double rfin = 0.0;   // the perturbed absorption of the row
+        if (pp.model == 1) {
+          // multiplicative: q' = clamp(q (1 + rel z), 0, 1) on the transient entries, scaled to
+          // 1 - r_min when above it; the absorption is the remainder
+          double ts = 0.0;
 #pragma unroll
-        for (int t = 0; t < kRowRegs; ++t)
-          if (col[t] >= 0) l1 += fabs(z[t] - mean);
-        l1 = warp_sum(l1);
-        const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
-        double tot = 0.0;
+          for (int t = 0; t < kRowRegs; ++t)
+            if (col[t] >= 0 && col[t] < c) {
+              qv[t] = fmin(fmax(q0[t] * (1.0 + pp.rel_radius * z[t]), 0.0), 1.0);
+              ts += qv[t];
+            }
+          ts = warp_sum(ts);
+          if (ts > 1.0 - pp.r_min) {
+            const double f = (1.0 - pp.r_min) / ts;
+            ts = 0.0;
 #pragma unroll
-        for (int t = 0; t < kRowRegs; ++t)
-          if (col[t] >= 0) {
-            double v = q0[t] + (z[t] - mean) * scale;
-            v = v < 0.0 ? 0.0 : v;
-            qv[t] = v;
-            tot += v;
+            for (int t = 0; t < kRowRegs; ++t)
+              if (col[t] >= 0 && col[t] < c) { qv[t] *= f; ts += qv[t]; }
+            ts = warp_sum(ts);
           }
-        const double inv_tot = 1.0 / warp_sum(tot);
-        double ts = 0.0, ra = 0.0;
+          rfin = 1.0 - ts;
+        } else {
+          const double mean = (double)warp_sum_ll(isum) * kTwoM31 / (double)supp;
+          double l1 = 0.0;
 #pragma unroll
-        for (int t = 0; t < kRowRegs; ++t)
-          if (col[t] >= 0) {
-            qv[t] *= inv_tot;
-            if (col[t] < c) ts += qv[t]; else ra = qv[t];
-          }
-        ts = warp_sum(ts);
-        ra = warp_sum(ra);
-        const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+          for (int t = 0; t < kRowRegs; ++t)
+            if (col[t] >= 0) l1 += fabs(z[t] - mean);
+          l1 = warp_sum(l1);
+          const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
+          double tot = 0.0;
+#pragma unroll
+          for (int t = 0; t < kRowRegs; ++t)
+            if (col[t] >= 0) {
+              double v = q0[t] + (z[t] - mean) * scale;
+              v = v < 0.0 ? 0.0 : v;
+              qv[t] = v;
+              tot += v;
+            }
+          const double inv_tot = 1.0 / warp_sum(tot);
+          double ts = 0.0, ra = 0.0;
+#pragma unroll
+          for (int t = 0; t < kRowRegs; ++t)
+            if (col[t] >= 0) {
+              qv[t] *= inv_tot;
+              if (col[t] < c) ts += qv[t]; else ra = qv[t];
+            }
+          ts = warp_sum(ts);
+          ra = warp_sum(ra);
+          const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+#pragma unroll
+          for (int t = 0; t < kRowRegs; ++t)
+            if (col[t] >= 0 && col[t] < c && ra < pp.r_min) qv[t] *= f;
+          rfin = ra < pp.r_min ? pp.r_min : ra;
+        }
 #pragma unroll
         for (int t = 0; t < kRowRegs; ++t) {
           const int32_t pj = col[t];
           if (pj < 0) continue;
           const int32_t e = e0 + (int32_t)lane + 32 * t;
-          double v = qv[t];
           if (pj < c) {
-            if (ra < pp.r_min) v *= f;
+            const double v = qv[t];
             qp[e] = v;
             if (pi >= 0) ar.A[(size_t)pi * c + pj] -= v;
             else add_y(pj, si * v);
             add_x(pj, mi * (v - q0[t]));
           } else {
-            qp[e] = (ra < pp.r_min) ? pp.r_min : v;
+            qp[e] = rfin;
+          }
+        }
+      } else if (pp.model == 1) {
+        double ts = 0.0;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          const int32_t pj = nzcol[e];
+          if (pj >= c) continue;
+          const double z = 2.0 * uniform_draw((uint32_t)C.c_list[pj], (uint32_t)i, p, k0, k1) - 1.0;
+          const double v = fmin(fmax(nzval[e] * (1.0 + pp.rel_radius * z), 0.0), 1.0);
+          qp[e] = v;
+          ts += v;
+        }
+        ts = warp_sum(ts);
+        if (ts > 1.0 - pp.r_min) {
+          const double f = (1.0 - pp.r_min) / ts;
+          ts = 0.0;
+          for (int32_t e = e0 + lane; e < e1; e += 32)
+            if (nzcol[e] < c) { qp[e] *= f; ts += qp[e]; }
+          ts = warp_sum(ts);
+        }
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+          const int32_t pj = nzcol[e];
+          if (pj < c) {
+            const double q = qp[e];
+            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
+            else add_y(pj, si * q);
+            add_x(pj, mi * (q - nzval[e]));
+          } else {
+            qp[e] = 1.0 - ts;
           }
         }
       } else {
@@ -319,6 +378,16 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
       loc_db = fmax(loc_db, fabs(bv - b0[v]));
       loc_lin = fmax(loc_lin, fabs(bv - lin));
       if (b_out) b_out[(size_t)(p - pp.p_begin) * n + v] = bv;
+    }
+    if (pp.kl_out) {   // KL(b' || b0), the discrepancy the robust search maximises
+      double kl = 0.0;
+      for (int32_t v = threadIdx.x; v < n; v += blockDim.x) {
+        const int32_t pv = C.c_index[v];
+        const double bv = (pv >= 0 ? ar.y[pv] : (C.s ? C.s[v] : s_unif)) * invT;
+        if (bv > 0.0) kl += bv * log(bv / b0[v]);
+      }
+      kl = block_sum(kl, red);
+      if (threadIdx.x == 0) pp.kl_out[p - pp.p_begin] = kl;
     }
     const double bmax = block_max(pm, red);
     const double tau = pp.tie_rel * bmax;

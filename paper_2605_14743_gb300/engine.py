@@ -16,7 +16,7 @@ import numpy as np
 from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
-               afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility,
+               afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility, afc_w1_graph,
                afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
 
@@ -301,6 +301,38 @@ class Query:
         afc_perturb_sweep(self.chain(), pp, self.counts, self.c_index, self.c_list, self.c, self.mu,
                           self.b, self.lu, self.piv, self.p_counters, self.p_pairs, self.p_hist,
                           self.p_max, b_out, self.ws_solve, self.ws_solve.numel(), self._stream())
+
+    def robust_search(self, samples=100, rel_radius=0.5, r_min=0.05, seed=None):
+        """Sampled robust search of the paper's robust experiment (Sec. 9; Remark on the robust
+        optimisation viewpoint in Sec. 5): `samples` multiplicative row perturbations of the
+        estimated kernel (relative radius, leak r_min), the perturbed AFC b' of each, and the
+        maximisers of KL(b' || b) and of W1(b', b) on the base graph's hop metric.  Needs
+        run_solve first.  Returns a dict with b_kl, b_w1, the index and value of each maximiser,
+        and the per-sample kl and w1 arrays."""
+        torch = self.torch
+        dev = self.counts.device
+        pp = self.perturb_params(0, samples)
+        pp.model, pp.rel_radius, pp.r_min = 1, float(rel_radius), float(r_min)
+        if seed is not None:
+            pp.seed = int(seed)
+        kl = torch.empty(samples, dtype=torch.float64, device=dev)
+        pp.kl_out = kl.data_ptr()
+        b_out = torch.empty((samples, self.n), dtype=torch.float64, device=dev)
+        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+        pairs = torch.zeros(100, dtype=torch.int64, device=dev)
+        hist = torch.zeros(16, dtype=torch.int64, device=dev)
+        mx = torch.zeros(3, dtype=torch.float64, device=dev)
+        afc_perturb_sweep(self.chain(), pp, self.counts, self.c_index, self.c_list, self.c,
+                          self.mu, self.b, self.lu, self.piv, cnt, pairs, hist, mx, b_out,
+                          self.ws_solve, self.ws_solve.numel(), self._stream())
+        bs = b_out.cpu().numpy()
+        b0 = self.b.cpu().numpy()
+        kl = kl.cpu().numpy()
+        w1 = afc_w1_graph(self.n, self.wl.eu, self.wl.ev, bs, b0)
+        k_kl, k_w1 = int(np.argmax(kl)), int(np.argmax(w1))
+        return {"b_kl": bs[k_kl], "b_w1": bs[k_w1], "k_kl": k_kl, "k_w1": k_w1,
+                "kl_max": float(kl[k_kl]), "w1_max": float(w1[k_w1]), "kl": kl, "w1": w1,
+                "counters": cnt.cpu().numpy()}
 
     def step(self, perturb=True):
         """One pass of the whole path: counts -> solve -> (perturbation sweep)."""

@@ -150,3 +150,20 @@ def test_fallback_validation_without_device():
         with pytest.raises(afc.AfcError) as e:
             afc.afc_transition_counts(prob, 0, 1, 8, None, None, None, None, 0, None)
         assert e.value.code == afc.AFC_EINVAL
+
+
+def test_w1_graph_host_matches_oracle():
+    import oracle as O
+    from afc_inputs import workload
+    rng = np.random.default_rng(2)
+    n = 12
+    eu, ev = np.arange(n - 1), np.arange(1, n)
+    x, y = rng.dirichlet(np.ones(n), size=3), rng.dirichlet(np.ones(n))
+    ref = [np.abs(np.cumsum(x[k] - y)[:-1]).sum() for k in range(3)]
+    assert np.allclose(afc.afc_w1_graph(n, eu, ev, x, y), ref, rtol=0, atol=1e-12)
+    for n, eu, ev in [(40, *er_edges(40, 0.25, 4)), (300, *ws_edges(300, 6, 0.1, 5))]:
+        x, y = rng.dirichlet(np.ones(n), size=2), rng.dirichlet(np.ones(n))
+        got = afc.afc_w1_graph(n, eu, ev, x, y)
+        for k in range(2):
+            assert abs(got[k] - O.w1_graph(n, eu, ev, x[k], y)) <= 1e-9
+        assert afc.afc_w1_graph(n, eu, ev, y, y)[0] <= 1e-12

@@ -52,10 +52,13 @@ class Chain:
         torch.cuda.synchronize()
 
     def sweep(self, p_begin, p_count, radius, r_min, seed, keep=True, top_k=5, k2=10, hist=16,
-              tie_rel=1e-9):
+              tie_rel=1e-9, model=0, kl=None):
         pp = afc.PerturbParams()
         pp.p_begin, pp.p_count, pp.l1_radius, pp.r_min, pp.seed = p_begin, p_count, radius, r_min, seed
         pp.top_k, pp.k2, pp.hist_bins, pp.tie_rel = top_k, k2, hist, tie_rel
+        if model == 1:   # radius is the relative radius of the multiplicative model
+            pp.model, pp.rel_radius, pp.l1_radius = 1, radius, 0.0
+        pp.kl_out = None if kl is None else kl.data_ptr()
         cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         pairs = torch.zeros(k2 * k2, dtype=torch.int64, device="cuda")
         hst = torch.zeros(hist, dtype=torch.int64, device="cuda")
@@ -260,3 +263,45 @@ def test_perturb_large_support_global_slab(parity):
     ref = O.perturb_sweep(Q, r, None, 5, 3, 0.05, 0.05, 11, keep=True)
     assert close(bo, ref.b)
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+
+
+# ------------------------------------------------ multiplicative model (robust search) ----
+
+def _mult_check(counts, R, alpha, p_begin, P, seed, rel=0.5):
+    ch = Chain(counts, R, alpha)
+    Q, r = O.assemble_q(counts, R, alpha)
+    kl = torch.empty(P, dtype=torch.float64, device="cuda")
+    cnt, pairs, hst, mx, bo = ch.sweep(p_begin, P, rel, 0.05, seed, model=1, kl=kl)
+    ref = O.perturb_sweep(Q, r, None, p_begin, P, rel, 0.05, seed, keep=True, model=1)
+    assert close(bo, ref.b)
+    assert close(kl.cpu().numpy(), ref.kl, rel=1e-7, abs_floor=1e-14)
+    assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+    assert (pairs == ref.pair_flips).all() and (hst == ref.shift_hist).all()
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    return ch
+
+
+def test_multiplicative_sweep_vs_oracle(er_counts):
+    wl, counts = er_counts
+    _mult_check(counts, wl.realizations, wl.alpha, 0, 200, 7)
+
+
+def test_multiplicative_long_rows():
+    """Rows over 128 entries (the slab path of the row perturbation), model 1."""
+    n, R = 300, 4000
+    rng = np.random.default_rng(22)
+    C = rng.choice(n, size=220, replace=False)
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        d = rng.multinomial(R, rng.dirichlet(np.ones(len(C) + 1)))
+        counts[i, C] = d[:-1].astype(np.uint32)
+        counts[i, n] = d[-1]
+    assert ((counts[:, :n] > 0).sum(axis=1) > 128).all()
+    _mult_check(counts, R, 0.15, 3, 4, 13)
+
+
+def test_multiplicative_large_support_global_slab():
+    counts = _random_counts(400, 300, 9, support_frac=0.6)
+    ch = _mult_check(counts, 300, 0.15, 5, 3, 11)
+    assert ch.c > 170
+

@@ -1,0 +1,39 @@
+"""The sampled robust search on the GPU (Sec. 9 robust experiment): multiplicative kernels,
+their perturbed AFC vectors and KL discrepancies from the sweep kernel, W1 on the base graph's
+hop metric from the host solver, and the two maximisers, against the oracle on the same
+estimated kernel."""
+import numpy as np
+import pytest
+
+import oracle as O
+from afc_inputs import workload
+from tests._util import close, oracle_counts, variant
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+afc = pytest.importorskip("paper_2605_14743_gb300")
+
+
+@pytest.mark.parametrize("name,R", [("small_er", 400), ("paper_ws100", 60)])
+def test_robust_search_maximisers(name, R):
+    wl = variant(workload(name), realizations=R)
+    q = afc.Query(wl)
+    q.run_counts()
+    q.run_solve()
+    res = q.robust_search(samples=40, rel_radius=0.5, r_min=0.05, seed=17)
+    counts, _ = oracle_counts(wl, 0, R)
+    assert (q.counts.cpu().numpy().view(np.uint32) == counts).all()
+    Q, r = O.assemble_q(counts, R, wl.alpha)
+    ref = O.perturb_sweep(Q, r, None, 0, 40, 0.5, 0.05, 17, keep=True, model=1)
+    assert close(res["kl"], ref.kl, rel=1e-7, abs_floor=1e-14)
+    _, b0, _, _ = O.afc_from_q(Q)
+    w1 = np.array([O.w1_graph(wl.n, wl.eu, wl.ev, ref.b[k], b0) for k in range(40)])
+    assert np.allclose(res["w1"], w1, rtol=1e-8, atol=1e-12)
+    # the maximisers (unique here: the runner-up is clearly below)
+    for key, vals in (("k_kl", ref.kl), ("k_w1", w1)):
+        srt = np.sort(vals)
+        assert srt[-1] - srt[-2] > 1e-6 * abs(srt[-1])
+        assert res[key] == int(np.argmax(vals))
+    assert close(res["b_kl"], ref.b[int(np.argmax(ref.kl))])
+    assert close(res["b_w1"], ref.b[int(np.argmax(w1))])
