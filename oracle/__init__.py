@@ -458,6 +458,59 @@ def bootstrap(next_states, alpha, B, seed, level=0.95, s=None, eta=1e-6):
     return b_rep, T_rep, lo, hi
 
 
+def robust_inner(Q0, eps, r_min, v, v_bot, support_only=True):
+    """Row-wise robust inner problem (Sec. 8, post-processing on the estimated AMC):
+    T_i(v) = inf over q_i in U_i of sum_j q_ij v_j + (1 - sum_j q_ij) v_bot, with U_i the box
+    [(Q0_ij - eps)_+, min(Q0_ij + eps, 1)] of Sec. 5.1 (on the support {j : Q0_ij > 0} when
+    support_only, else on every j) and sum_j q_ij <= 1 - r_min.  One LP per row (scipy HiGHS).
+    Returns (T [n], Qstar [n, n] a minimiser)."""
+    from scipy.optimize import linprog
+    Q0 = np.asarray(Q0, np.float64)
+    v = np.asarray(v, np.float64)
+    n = Q0.shape[0]
+    T = np.zeros(n)
+    Qs = np.zeros((n, n))
+    for i in range(n):
+        cols = np.flatnonzero(Q0[i] > 0) if support_only else np.arange(n)
+        if cols.size == 0:
+            T[i] = v_bot
+            continue
+        lo = np.maximum(Q0[i, cols] - eps, 0.0)
+        hi = np.minimum(Q0[i, cols] + eps, 1.0)
+        res = linprog(v[cols] - v_bot, A_ub=np.ones((1, cols.size)), b_ub=[1.0 - r_min],
+                      bounds=list(zip(lo, hi)), method="highs")
+        if not res.success:
+            raise RuntimeError("robust_inner: row %d: %s" % (i, res.message))
+        T[i] = v_bot + res.fun
+        Qs[i, cols] = res.x
+    return T, Qs
+
+
+def robust_value(Q0, eps, r_min, f, sense=-1, support_only=True, s=None, max_iter=100):
+    """Robust expected accumulated reward under the rectangular set U (Sec. 8: a scenario
+    kernel P* chosen by a robust Bellman operator): V = f + T(V) with v_bot = 0, T the inner
+    problem (sense -1: the adversary minimises; +1: maximises, via T_max(v) = -T(-v)), solved
+    by policy iteration (evaluate V = (I - Q*)^-1 f, improve every row by its LP, until the
+    value stops changing).  Returns (V, Qstar, b*, E_s*[T], b*_f) with b* the AFC of P*."""
+    Q0 = np.asarray(Q0, np.float64)
+    f = np.asarray(f, np.float64)
+    n = Q0.shape[0]
+    V = np.zeros(n)
+    Qs = None
+    for _ in range(max_iter):
+        if sense < 0:
+            _, Qn = robust_inner(Q0, eps, r_min, V, 0.0, support_only)
+        else:
+            _, Qn = robust_inner(Q0, eps, r_min, -V, 0.0, support_only)
+        Vn = np.linalg.solve(np.eye(n) - Qn, f)
+        done = Qs is not None and np.max(np.abs(Vn - V)) <= 1e-13 * max(1.0, np.max(np.abs(Vn)))
+        V, Qs = Vn, Qn
+        if done:
+            break
+    mu, b, T, bf = afc_from_q(Qs, s, f)
+    return V, Qs, b, T, bf
+
+
 def gauss_solve(A, b):
     A = np.array(A, dtype=np.float64, order="C", copy=True)
     b = np.array(b, dtype=np.float64, order="C", copy=True)

@@ -302,6 +302,32 @@ class Query:
                           self.b, self.lu, self.piv, self.p_counters, self.p_pairs, self.p_hist,
                           self.p_max, b_out, self.ws_solve, self.ws_solve.numel(), self._stream())
 
+    def _topk(self, k):
+        """Nominal Top-k under the ranking rule of the sweep (u ahead of v when b_u - b_v >
+        tie_rel max b, or within that band and u < v)."""
+        b = self.b.cpu().numpy()
+        tau = float(self.wl.tie_rel) * float(b.max())
+        d = b[None, :] - b[:, None]                       # d[v, u] = b_u - b_v
+        ids = np.arange(self.n)
+        ahead = (d > tau) | ((np.abs(d) <= tau) & (ids[None, :] < ids[:, None]))
+        rank = ahead.sum(axis=1)
+        return [int(v) for v in np.argsort(rank, kind="stable")[:k]]
+
+    def rank_stability(self, M=None, k=5):
+        """The rank-stability check the paper recommends with the bootstrap (Sec. 8): the chain
+        estimated from realizations [0, M) and from [0, 2M) (the first M reused); stable when
+        the Top-k sets agree.  Leaves the Query holding the 2M-realization estimate."""
+        M = int(self.wl.realizations) if M is None else int(M)
+        self.run_counts(0, M)
+        self.wl.realizations = M
+        self.run_solve()
+        top_m = self._topk(k)
+        self.run_counts(M, M, zero=False)
+        self.wl.realizations = 2 * M
+        self.run_solve()
+        top_2m = self._topk(k)
+        return {"stable": set(top_m) == set(top_2m), "top_M": top_m, "top_2M": top_2m}
+
     def robust_search(self, samples=100, rel_radius=0.5, r_min=0.05, seed=None):
         """Sampled robust search of the paper's robust experiment (Sec. 9; Remark on the robust
         optimisation viewpoint in Sec. 5): `samples` multiplicative row perturbations of the

@@ -37,3 +37,16 @@ def test_robust_search_maximisers(name, R):
         assert res[key] == int(np.argmax(vals))
     assert close(res["b_kl"], ref.b[int(np.argmax(ref.kl))])
     assert close(res["b_w1"], ref.b[int(np.argmax(w1))])
+
+
+def test_rank_stability_m_and_2m():
+    wl = variant(workload("small_er"), realizations=300)
+    q = afc.Query(wl)
+    res = q.rank_stability(M=300, k=5)
+    for M, key in ((300, "top_M"), (600, "top_2M")):
+        counts, _ = oracle_counts(wl, 0, M)
+        _, b, _, _ = O.solve_counts(counts, M, wl.alpha)
+        rk = O.rank(b)
+        assert res[key] == [int(v) for v in np.argsort(rk, kind="stable")[:5]]
+    assert res["stable"] == (set(res["top_M"]) == set(res["top_2M"]))
+    assert (q.counts.cpu().numpy().view(np.uint32) == oracle_counts(wl, 0, 600)[0]).all()
