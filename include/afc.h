@@ -284,6 +284,34 @@ int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int3
                   double *b_rep, double *T_rep, double *b_lo, double *b_hi, void *workspace,
                   size_t workspace_bytes, void *stream);
 
+/* Row-wise robust inner problem (Sec. 8 post-processing, over the uncertainty set of Sec. 5.1):
+ * T[i] = inf over q_i in U_i of sum_j q_ij v_j + (1 - sum_j q_ij) v_bot, with U_i the box
+ * [(Q_ij - eps)_+, min(Q_ij + eps, 1)] around the kernel assembled from `counts` (as
+ * afc_absorbing_solve assembles it) and sum_j q_ij <= 1 - r_min.  support_only 1: the box on
+ * the row's observed support (q_ij = 0 elsewhere); 0: on every j (new transitions up to eps).
+ * Solved exactly per row (lower bounds, then the budget to the most negative coefficients
+ * v_j - v_bot first, ties by j).  DEVICE in: counts [n][n+1], v [n].  DEVICE out: T [n],
+ * Qstar [n][n] a minimising kernel (or NULL).  Workspace: 256 bytes.  SYNCHRONISES `stream`.
+ * Errors: AFC_EINVAL when some U_i is empty (its lower bounds exceed 1 - r_min). */
+int afc_robust_inner(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                     int32_t support_only, const double *v, double v_bot, double *T, double *Qstar,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/* Robust value and its scenario kernel (Sec. 8: a kernel P* in U chosen by a robust Bellman
+ * operator; Remark on the robust optimisation viewpoint in Sec. 5): V = f + T_sense(V) with
+ * v_bot = 0, f = chain->reward (NULL = 1: the robust expected length), sense -1 the adversary
+ * minimises, +1 maximises.  Policy iteration: the inner problem's optimiser at V, V of that
+ * kernel by an FP64 LU of I - Q*, until V changes by at most 1e-13 relative (at most 100
+ * rounds).  DEVICE out: V [n], Qstar [n][n] (or NULL), b_star [n] = the AFC of P*, scalars [2]
+ * = {E_s[T] under P*, b* . f}; HOST out: *iterations (or NULL).  n <= 4096 (dense solve in one
+ * CTA).  Workspace: afc_robust_value_workspace(n).  SYNCHRONISES `stream`.  Errors as
+ * afc_robust_inner, AFC_ESINGULAR for a zero pivot. */
+size_t afc_robust_value_workspace(int32_t n);
+int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                     int32_t support_only, int32_t sense, double *V, double *Qstar, double *b_star,
+                     double *scalars, int32_t *iterations, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
 /* Wasserstein-1 distances under the base graph's shortest-path (hop) metric, the second
  * discrepancy of the paper's robust search (Sec. 9): out[k] = W1(x_k, y) for the `count` HOST
  * rows x_k = x + k n (each summing to sum y), over the HOST edge lists eu, ev (as

@@ -36,7 +36,8 @@ __all__ = [
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
-    "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph",
+    "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_robust_inner",
+    "afc_robust_value_workspace", "afc_robust_value",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -153,6 +154,11 @@ _SIGS = {
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
     "afc_w1_graph": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_i32, c_p], ctypes.c_int),
+    "afc_robust_inner": ([ctypes.POINTER(Chain), c_p, c_f64, c_f64, c_i32, c_p, c_f64, c_p, c_p,
+                          c_p, c_sz, c_p], ctypes.c_int),
+    "afc_robust_value_workspace": ([c_i32], c_sz),
+    "afc_robust_value": ([ctypes.POINTER(Chain), c_p, c_f64, c_f64, c_i32, c_i32, c_p, c_p, c_p,
+                          c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_bootstrap": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_i32, c_u32, c_u64, c_f64, c_p, c_p,
                        c_p, c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_pool_summaries": ([c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
@@ -297,6 +303,27 @@ def afc_bootstrap(chain, next_states, c_index, c_list, c, B, seed, level, b_rep,
                              int(c), int(B), int(seed), float(level), _ptr(b_rep), _ptr(T_rep),
                              _ptr(b_lo), _ptr(b_hi), _ptr(workspace), int(workspace_bytes),
                              stream))
+
+
+def afc_robust_inner(chain, counts, eps, r_min, support_only, v, v_bot, T, Qstar, workspace,
+                     stream):
+    _chk(lib().afc_robust_inner(ctypes.byref(chain), _ptr(counts), float(eps), float(r_min),
+                                int(support_only), _ptr(v), float(v_bot), _ptr(T), _ptr(Qstar),
+                                _ptr(workspace), 256, stream))
+
+
+def afc_robust_value_workspace(n) -> int:
+    return int(lib().afc_robust_value_workspace(int(n)))
+
+
+def afc_robust_value(chain, counts, eps, r_min, support_only, sense, V, Qstar, b_star, scalars,
+                     workspace, workspace_bytes, stream) -> int:
+    it = ctypes.c_int32(0)
+    _chk(lib().afc_robust_value(ctypes.byref(chain), _ptr(counts), float(eps), float(r_min),
+                                int(support_only), int(sense), _ptr(V), _ptr(Qstar), _ptr(b_star),
+                                _ptr(scalars), ctypes.byref(it), _ptr(workspace),
+                                int(workspace_bytes), stream))
+    return int(it.value)
 
 
 def afc_w1_graph(n, eu, ev, x, y):

@@ -914,6 +914,96 @@ int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, 
   return AFC_OK;
 }
 
+static int robust_checks(const afc_chain *chain, const uint32_t *counts, double eps, double r_min) {
+  if (!chain || !counts) return fail(AFC_EINVAL, "null argument");
+  if (chain->n < 1 || chain->realizations == 0) return fail(AFC_EINVAL, "bad n or realizations");
+  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (!(eps >= 0.0) || !(r_min > 0.0 && r_min < 1.0)) return fail(AFC_EINVAL, "need eps >= 0 and 0 < r_min < 1");
+  return AFC_OK;
+}
+
+int afc_robust_inner(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                     int32_t support_only, const double *v, double v_bot, double *T, double *Qstar,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+  int st = robust_checks(chain, counts, eps, r_min);
+  if (st) return st;
+  if (!v || !T) return fail(AFC_EINVAL, "null argument");
+  if (!workspace || workspace_bytes < 256) return fail(AFC_ENOMEM, "need 256 bytes of workspace");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *status = static_cast<uint32_t *>(workspace);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  cudaError_t e = launch_robust_inner(chain->n, chain->realizations, chain->alpha,
+                                      chain->absorb_floor, counts, eps, r_min, support_only ? 1 : 0,
+                                      v, v_bot, 1.0, T, Qstar, status, s);
+  if (e != cudaSuccess) return cuda_fail(e, "robust inner launch");
+  uint32_t h = 0;
+  AFC_CUDA(cudaMemcpyAsync(&h, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AFC_CUDA(cudaStreamSynchronize(s));
+  if (h) return fail(AFC_EINVAL, "empty uncertainty set: a row's lower bounds exceed 1 - r_min");
+  return AFC_OK;
+}
+
+static size_t al256h(size_t x) { return (x + 255u) & ~size_t(255); }
+
+size_t afc_robust_value_workspace(int32_t n) {
+  if (n < 1 || n > 4096) return 0;
+  const size_t nn = (size_t)n * (size_t)n;
+  return 256 + 2 * al256h(8 * nn) + al256h(4 * (size_t)n) + 3 * al256h(8 * (size_t)n);
+}
+
+int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                     int32_t support_only, int32_t sense, double *V, double *Qstar, double *b_star,
+                     double *scalars, int32_t *iterations, void *workspace, size_t workspace_bytes,
+                     void *stream) {
+  int st = robust_checks(chain, counts, eps, r_min);
+  if (st) return st;
+  if (!V || !b_star || !scalars) return fail(AFC_EINVAL, "null argument");
+  if (sense != -1 && sense != 1) return fail(AFC_EINVAL, "sense must be -1 (min) or +1 (max)");
+  const int32_t n = chain->n;
+  if (n > 4096) return fail(AFC_EUNSUPPORTED, "the robust value takes n <= 4096 (dense LU)");
+  const size_t need = afc_robust_value_workspace(n);
+  if (!workspace || workspace_bytes < need)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nn = (size_t)n * (size_t)n;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  double *diff = reinterpret_cast<double *>(ws + 8);
+  size_t o = 256;
+  double *Qs = reinterpret_cast<double *>(ws + o); o += al256h(8 * nn);
+  double *A = reinterpret_cast<double *>(ws + o);  o += al256h(8 * nn);
+  int32_t *piv = reinterpret_cast<int32_t *>(ws + o); o += al256h(4 * (size_t)n);
+  double *x = reinterpret_cast<double *>(ws + o);  o += al256h(8 * (size_t)n);
+  double *T = reinterpret_cast<double *>(ws + o);  o += al256h(8 * (size_t)n);
+  double *mu = reinterpret_cast<double *>(ws + o);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  AFC_CUDA(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)n, s));
+  // policy iteration: the inner problem's minimiser (or maximiser) at V, then V of that kernel
+  int it = 0;
+  for (; it < 100; ++it) {
+    cudaError_t e = launch_robust_inner(n, chain->realizations, chain->alpha, chain->absorb_floor,
+                                        counts, eps, r_min, support_only ? 1 : 0, V, 0.0,
+                                        sense < 0 ? 1.0 : -1.0, T, Qs, status, s);
+    if (e == cudaSuccess) e = launch_robust_eval(n, Qs, A, piv, chain->reward, V, x, diff, status, s);
+    if (e != cudaSuccess) return cuda_fail(e, "robust value launch");
+    double h_diff = 0.0;
+    uint32_t h_st = 0;
+    AFC_CUDA(cudaMemcpyAsync(&h_diff, diff, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AFC_CUDA(cudaMemcpyAsync(&h_st, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AFC_CUDA(cudaStreamSynchronize(s));
+    if (h_st & kErrInput) return fail(AFC_EINVAL, "empty uncertainty set: a row's lower bounds exceed 1 - r_min");
+    if (h_st & kErrSolve) return fail(AFC_ESINGULAR, "zero pivot in I - Q*");
+    if (it > 0 && h_diff <= 1e-13) { ++it; break; }
+  }
+  if (Qstar) AFC_CUDA(cudaMemcpyAsync(Qstar, Qs, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  cudaError_t e = launch_robust_star(n, A, piv, chain->s_init, chain->reward, mu, b_star, scalars, s);
+  if (e != cudaSuccess) return cuda_fail(e, "robust star launch");
+  AFC_CUDA(cudaStreamSynchronize(s));
+  if (iterations) *iterations = it;
+  return AFC_OK;
+}
+
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out) {
   if (n < 1 || m < 0 || count < 0 || !x || !y || !out || (m > 0 && (!eu || !ev)))

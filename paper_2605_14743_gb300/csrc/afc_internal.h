@@ -194,7 +194,18 @@ cudaError_t launch_bootstrap(const ChainDev &C, const int32_t *rec, uint32_t R, 
                              double *lo, double *hi, unsigned char *slabs, size_t slab_space,
                              uint32_t *status, int num_sms, cudaStream_t stream);
 
-// robust.cu: Wasserstein-1 distance of two node distributions on the graph's hop metric
+// robust.cu: row-wise robust inner problem, policy evaluation and scenario AFC; Wasserstein-1
+// distance of two node distributions on the graph's hop metric
+cudaError_t launch_robust_inner(int32_t n, uint32_t R, double alpha, double eta,
+                                const uint32_t *counts, double eps, double r_min,
+                                int support_only, const double *v, double v_bot, double vsign,
+                                double *T, double *Qstar, uint32_t *status, cudaStream_t stream);
+cudaError_t launch_robust_eval(int32_t n, const double *Qstar, double *A, int32_t *piv,
+                               const double *f, double *V, double *x, double *diff,
+                               uint32_t *status, cudaStream_t stream);
+cudaError_t launch_robust_star(int32_t n, const double *A, const int32_t *piv, const double *s,
+                               const double *f, double *mu, double *b, double *out,
+                               cudaStream_t stream);
 double w1_graph_host(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *eid,
                      const double *x, const double *y);
 

@@ -1,13 +1,19 @@
-// robust.cu -- host side of the sampled robust search (Sec. 9 robust sensitivity experiment):
-// the Wasserstein-1 distance between two node distributions under the base graph's hop metric.
+// robust.cu -- robust analysis on the estimated AMC.
 //
-// W1 on a graph metric is an uncapacitated transshipment problem on the graph itself (each
-// unit of mass moved across an edge costs 1).  It is solved exactly by successive shortest
-// paths: node potentials keep the reduced arc costs non-negative, each round runs a
-// multi-source Dijkstra from every node with excess mass and stops at the first node with a
-// deficit, then pushes as much as the path allows (the source's excess, the sink's deficit,
-// the flow on any arc the path cancels).  Costs are integers, so distances and potentials are
-// exact; the masses are doubles and are settled to within a relative 1e-14.
+// Device (Sec. 8 post-processing; uncertainty set of Sec. 5.1):
+//   robust_inner_kernel  T_i(v) = inf over q_i in U_i of sum_j q_ij v_j + (1 - sum_j q_ij) v_bot,
+//                        U_i the box [(Q0_ij - eps)_+, min(Q0_ij + eps, 1)] (on the row's
+//                        support, or on every j) with sum_j q_ij <= 1 - r_min.  A warp per row
+//                        solves the LP exactly: every entry starts at its lower bound, then the
+//                        budget goes to the entries in ascending order of v_j - v_bot (ties by
+//                        j) while that coefficient is negative, each up to its upper bound.
+//   eval_kernel          one CTA: A = I - Q*, V = A^-1 f (FP64 LU with partial pivoting) and
+//                        the change of V; the robust value comes from policy iteration on the
+//                        host (inner problem at V, evaluate, until V stops changing)
+//   star_kernel          the AFC of the scenario kernel: A^T mu = s with the last factors
+// Host (Sec. 9 robust experiment): the Wasserstein-1 distance between two node distributions
+// under the base graph's hop metric.
+//
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -17,15 +23,206 @@
 #include <utility>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "afc_internal.h"
+#include "linalg.cuh"
 
 namespace afc {
 
+namespace {
+
+// The transient row of the estimated kernel: Q0_ij = scale_i counts_ij with the assembly's
+// row-scale rule.  Returns scale_i; the warp's lanes all get it.
+__device__ double row_scale_warp(const uint32_t *row, int32_t n, uint32_t R, double alpha,
+                                 double eta) {
+  unsigned long long all = 0;
+  for (int32_t j = threadIdx.x & 31; j < n; j += 32) all += row[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(0xFFFFFFFFu, all, o);
+  const double q_sum = (1.0 - alpha) * (double)all / (double)R;
+  const double r_i = alpha + (1.0 - alpha) * (double)row[n] / (double)R;
+  double scale = (1.0 - alpha) / (double)R;
+  if (r_i == 0.0 && q_sum > 0.0) scale *= (1.0 - eta) / q_sum;
+  return scale;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+// Row-wise inner problem (warp per row) at the continuation value vsign * (v, v_bot).
+__global__ void robust_inner_kernel(int32_t n, uint32_t R, double alpha, double eta,
+                                    const uint32_t *counts, double eps, double r_min,
+                                    int support_only, const double *v, double v_bot, double vsign,
+                                    double *T, double *Qstar, uint32_t *status) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const size_t stride = (size_t)n + 1;
+  const double vb = vsign * v_bot;
+  for (uint32_t i = warp; i < (uint32_t)n; i += nwarps) {
+    const uint32_t *row = counts + (size_t)i * stride;
+    const double scale = row_scale_warp(row, n, R, alpha, eta);
+    double *qs = Qstar ? Qstar + (size_t)i * n : nullptr;
+    // every entry at its lower bound
+    double base = 0.0, low = 0.0;
+    for (int32_t j = lane; j < n; j += 32) {
+      const double q = scale * (double)row[j];
+      const double l = q > eps ? q - eps : 0.0;
+      base += l * (vsign * v[j] - vb);
+      low += l;
+      if (qs) qs[j] = l;
+    }
+    base = warp_sum_d(base);
+    low = warp_sum_d(low);
+    __syncwarp();   // the lower bounds written by every lane, before lane 0 adds to them
+    double budget = (1.0 - r_min) - low;
+    if (budget < -1e-12) {
+      if (lane == 0) atomicOr(status, kErrInput);   // U_i is empty
+      budget = 0.0;
+    }
+    // the budget to the most negative coefficients first, each entry up to its upper bound
+    double acc = 0.0, last_c = -INFINITY;
+    int32_t last_j = -1;
+    while (budget > 0.0) {
+      double bc = 0.0;
+      int32_t bj = 0x7FFFFFFF;
+      double bcap = 0.0;
+      for (int32_t j = lane; j < n; j += 32) {
+        const double cf = vsign * v[j] - vb;
+        if (!(cf < 0.0)) continue;
+        if (cf < last_c || (cf == last_c && j <= last_j)) continue;   // already filled
+        const double q = scale * (double)row[j];
+        double cap;
+        if (q > 0.0) cap = fmin(q + eps, 1.0) - (q > eps ? q - eps : 0.0);
+        else cap = support_only ? 0.0 : fmin(eps, 1.0);
+        if (!(cap > 0.0)) continue;
+        if (bj == 0x7FFFFFFF || cf < bc || (cf == bc && j < bj)) { bc = cf; bj = j; bcap = cap; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double oc = __shfl_xor_sync(0xFFFFFFFFu, bc, o);
+        const int32_t oj = __shfl_xor_sync(0xFFFFFFFFu, bj, o);
+        const double ocap = __shfl_xor_sync(0xFFFFFFFFu, bcap, o);
+        if (oj != 0x7FFFFFFF && (bj == 0x7FFFFFFF || oc < bc || (oc == bc && oj < bj))) {
+          bc = oc; bj = oj; bcap = ocap;
+        }
+      }
+      if (bj == 0x7FFFFFFF) break;
+      const double d = fmin(bcap, budget);
+      acc += d * bc;
+      budget -= d;
+      if (qs && lane == 0) qs[bj] += d;
+      last_c = bc;
+      last_j = bj;
+    }
+    if (lane == 0) T[i] = vsign * (vb + base + acc);
+  }
+}
+
+__global__ void build_a_kernel(int32_t n, const double *Qstar, double *A) {
+  const size_t nn = (size_t)n * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nn;
+       k += (size_t)gridDim.x * blockDim.x)
+    A[k] = ((k / n) == (k % n) ? 1.0 : 0.0) - Qstar[k];
+}
+
+// One CTA: factor A, V_new = A^-1 f (f = 1 when null), diff = max |V_new - V|, V <- V_new.
+__global__ void __launch_bounds__(1024, 1)
+eval_kernel(int32_t n, double *A, int32_t *piv, const double *f, double *V, double *x,
+            double *diff, uint32_t *status) {
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  LinScratch ls{sval, sidx, sb, sflag};
+  if (!lu_factor(A, n, n, piv, ls)) {
+    if (threadIdx.x == 0) { atomicOr(status, kErrSolve); *diff = 0.0; }
+    return;
+  }
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = f ? f[i] : 1.0;
+  __syncthreads();
+  lu_solve(A, n, n, piv, x, ls);
+  double m = 0.0, scale = 1.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    m = fmax(m, fabs(x[i] - V[i]));
+    scale = fmax(scale, fabs(x[i]));
+  }
+  m = block_max(m, red);
+  scale = block_max(scale, red);
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = x[i];
+  if (threadIdx.x == 0) *diff = m / scale;
+}
+
+// The AFC of the scenario kernel from the factors of the last evaluation: A^T mu = s,
+// out[0] = E_s[T] = sum mu, out[1] = b . f (f = 1 when null gives 1).
+__global__ void __launch_bounds__(1024, 1)
+star_kernel(int32_t n, const double *A, const int32_t *piv, const double *s, const double *f,
+            double *mu, double *b, double *out) {
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  LinScratch ls{sval, sidx, sb, sflag};
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) mu[i] = s ? s[i] : 1.0 / (double)n;
+  __syncthreads();
+  lu_solve_transposed(A, n, n, piv, mu, ls);
+  double t = 0.0, tf = 0.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    t += mu[i];
+    tf += mu[i] * (f ? f[i] : 1.0);
+  }
+  const double T = block_sum(t, red);
+  const double TF = block_sum(tf, red);
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = mu[i] / T;
+  if (threadIdx.x == 0) { out[0] = T; out[1] = TF / T; }
+}
+
+}  // namespace
+
+cudaError_t launch_robust_inner(int32_t n, uint32_t R, double alpha, double eta,
+                                const uint32_t *counts, double eps, double r_min,
+                                int support_only, const double *v, double v_bot, double vsign,
+                                double *T, double *Qstar, uint32_t *status, cudaStream_t stream) {
+  const int grid = (int)std::min<int64_t>(((int64_t)n + 7) / 8, 1024);
+  robust_inner_kernel<<<grid, 256, 0, stream>>>(n, R, alpha, eta, counts, eps, r_min,
+                                                support_only, v, v_bot, vsign, T, Qstar, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_robust_eval(int32_t n, const double *Qstar, double *A, int32_t *piv,
+                               const double *f, double *V, double *x, double *diff,
+                               uint32_t *status, cudaStream_t stream) {
+  const int grid = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
+  build_a_kernel<<<grid, 256, 0, stream>>>(n, Qstar, A);
+  eval_kernel<<<1, 1024, 0, stream>>>(n, A, piv, f, V, x, diff, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_robust_star(int32_t n, const double *A, const int32_t *piv, const double *s,
+                               const double *f, double *mu, double *b, double *out,
+                               cudaStream_t stream) {
+  star_kernel<<<1, 1024, 0, stream>>>(n, A, piv, s, f, mu, b, out);
+  return cudaGetLastError();
+}
+
+// W1 on a graph metric is an uncapacitated transshipment problem on the graph itself (each
+// unit of mass moved across an edge costs 1).  It is solved exactly by successive shortest
+// paths: node potentials keep the reduced arc costs non-negative, each round runs a
+// multi-source Dijkstra from every node with excess mass and stops at the first node with a
+// deficit, then pushes as much as the path allows (the source's excess, the sink's deficit,
+// the flow on any arc the path cancels).  Costs are integers, so distances and potentials are
+// exact; the masses are doubles and are settled to within a relative 1e-14.
 double w1_graph_host(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *eid,
                      const double *x, const double *y) {
   const int32_t arcs = rp[n];
   // partner arc of every arc (the other direction of the same edge)
-  std::vector<int32_t> first(std::max<int32_t>(arcs, 1), -1), rev(std::max<int32_t>(arcs, 1), -1);
+  std::vector<int32_t> rev(std::max<int32_t>(arcs, 1), -1);
   int32_t maxe = 0;
   for (int32_t a = 0; a < arcs; ++a) maxe = std::max(maxe, eid[a] + 1);
   std::vector<int32_t> seen((size_t)maxe, -1);

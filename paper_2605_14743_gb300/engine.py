@@ -17,6 +17,7 @@ from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProbl
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
                afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility, afc_w1_graph,
+               afc_robust_inner, afc_robust_value, afc_robust_value_workspace,
                afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
 
@@ -327,6 +328,25 @@ class Query:
         self.run_solve()
         top_2m = self._topk(k)
         return {"stable": set(top_m) == set(top_2m), "top_M": top_m, "top_2M": top_2m}
+
+    def robust_value(self, eps=0.05, r_min=0.05, support_only=True, sense=-1):
+        """Robust value and scenario kernel (Sec. 8): V = f + T(V) over the box-and-budget set
+        around the estimated kernel (reward f of the workload, else 1), the adversary minimising
+        (sense -1) or maximising (+1); returns V, Q*, the AFC b* of Q*, E_s*[T], b* . f and the
+        policy-iteration rounds (device tensors / floats)."""
+        torch = self.torch
+        dev = self.counts.device
+        n = self.n
+        ws = torch.empty(max(afc_robust_value_workspace(n), 256), dtype=torch.uint8, device=dev)
+        V = torch.empty(n, dtype=torch.float64, device=dev)
+        Qs = torch.empty((n, n), dtype=torch.float64, device=dev)
+        b = torch.empty(n, dtype=torch.float64, device=dev)
+        sc = torch.empty(2, dtype=torch.float64, device=dev)
+        it = afc_robust_value(self.chain(), self.counts, eps, r_min, support_only, sense, V, Qs, b,
+                              sc, ws, ws.numel(), self._stream())
+        sc = sc.cpu().numpy()
+        return {"V": V, "Qstar": Qs, "b_star": b, "expected_T": float(sc[0]), "b_f": float(sc[1]),
+                "iterations": it}
 
     def robust_search(self, samples=100, rel_radius=0.5, r_min=0.05, seed=None):
         """Sampled robust search of the paper's robust experiment (Sec. 9; Remark on the robust

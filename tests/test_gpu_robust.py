@@ -50,3 +50,45 @@ def test_rank_stability_m_and_2m():
         assert res[key] == [int(v) for v in np.argsort(rk, kind="stable")[:5]]
     assert res["stable"] == (set(res["top_M"]) == set(res["top_2M"]))
     assert (q.counts.cpu().numpy().view(np.uint32) == oracle_counts(wl, 0, 600)[0]).all()
+
+
+def _device_chain(wl, counts):
+    q = afc.Query(wl)
+    q.counts.copy_(torch.from_numpy(counts.view(np.int32)).cuda())
+    return q
+
+
+@pytest.mark.parametrize("support_only", [1, 0])
+def test_robust_inner_problem_vs_lp(support_only):
+    wl = variant(workload("small_er"), realizations=400)
+    counts, _ = oracle_counts(wl, 0, 400)
+    Q, _ = O.assemble_q(counts, 400, wl.alpha)
+    q = _device_chain(wl, counts)
+    rng = np.random.default_rng(12)
+    v = rng.normal(size=wl.n)
+    T = torch.empty(wl.n, dtype=torch.float64, device="cuda")
+    Qs = torch.empty((wl.n, wl.n), dtype=torch.float64, device="cuda")
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    afc.afc_robust_inner(q.chain(), q.counts, 0.05, 0.05, support_only,
+                         torch.from_numpy(v).cuda(), 0.3, T, Qs, ws,
+                         torch.cuda.current_stream().cuda_stream)
+    oT, oQ = O.robust_inner(Q, 0.05, 0.05, v, 0.3, bool(support_only))
+    assert np.allclose(T.cpu().numpy(), oT, rtol=0, atol=1e-9)
+    assert np.allclose(Qs.cpu().numpy(), oQ, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("sense,support_only", [(-1, 1), (1, 0)])
+def test_robust_value_vs_oracle(sense, support_only):
+    wl = variant(workload("small_er"), realizations=400)
+    wl.reward = np.random.default_rng(3).random(wl.n)
+    counts, _ = oracle_counts(wl, 0, 400)
+    Q, _ = O.assemble_q(counts, 400, wl.alpha)
+    q = _device_chain(wl, counts)
+    res = q.robust_value(eps=0.05, r_min=0.05, support_only=bool(support_only), sense=sense)
+    V, Qs, b, T, bf = O.robust_value(Q, 0.05, 0.05, wl.reward, sense=sense,
+                                     support_only=bool(support_only))
+    assert close(res["V"].cpu().numpy(), V, rel=1e-9)
+    assert close(res["b_star"].cpu().numpy(), b, rel=1e-8)
+    assert abs(res["expected_T"] - T) <= 1e-9 * T and abs(res["b_f"] - bf) <= 1e-9 * abs(bf)
+    assert np.allclose(res["Qstar"].cpu().numpy(), Qs, rtol=0, atol=1e-9)
+    assert 2 <= res["iterations"] <= 100
