@@ -65,7 +65,7 @@ def _declare(L):
     L.orc_brandes.argtypes = [i32, P, P, P, P, P, P, P]
     L.orc_select.argtypes = [i32, P, P, P, u32, P, u32, f64, P]
     L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
-                                        u32, u32, u32, P, u32, f64, P, P, i32, P]
+                                        u32, u32, u32, P, u32, f64, P, P, i32, P, i32]
     L.orc_topk_order.argtypes = [i32, P, P, P, u32, u32, f64, P, P]
     L.orc_count_rewards.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P, u32,
                                     u32, u32, f64, u32, P, P, u32, P, P]
@@ -232,7 +232,7 @@ def count_transitions(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_
 
 
 def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, candidates,
-           top_k, tie_rel, fb_node, counts=None):
+           top_k, tie_rel, fb_node, counts=None, tie_random=False):
     th, th_all = thresholds(p_survive, g.m)
     lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
     hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
@@ -245,10 +245,20 @@ def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, c
         g.n, g.m, _p(g.row_ptr), _p(g.col), _p(g.eid), seed, graph_tag, r_begin, r_count,
         _p(th), th_all, _p(lo_arr), _p(hi_arr),
         0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
-        k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats), int(fb_node), _p(fb))
+        k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats), int(fb_node), _p(fb),
+        1 if tie_random else 0)
     if st not in (ORC_OK, ORC_EOVERFLOW):
         _check(st, "count_transitions")
     return counts, (None if fb is None else fb[:g.n]), int(stats[0])
+
+
+def count_random_ties(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi,
+                      k_min, candidates=None, top_k=0, tie_rel=1e-9):
+    """Counts with the uniformly randomised tie-break (Remark on randomized tie-breaking,
+    Sec. 4.1) in place of the smallest-index rule.  Returns (counts, overflows)."""
+    counts, _, ovf = _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                            candidates, top_k, tie_rel, -1, tie_random=True)
+    return counts, ovf
 
 
 def count_constrained(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi,

@@ -324,9 +324,25 @@ int orc_brandes(int32_t n, const int64_t *row_ptr, const int32_t *col, const int
 /*   tauK = tie_rel * max_K B.  centre[root] = -1 encodes "no valid continuation".         */
 /* ------------------------------------------------------------------------------------ */
 
+/* With tie_random the centre is drawn uniformly from the tie set instead (Remark on        */
+/* randomized tie-breaking, Sec. 4.1): u = Philox4x32-10(counter (root, r, graph_tag, 3),    */
+/* key = seed)[0] with root the smallest id of K, the floor(u |ties| / 2^32)-th tied        */
+/* candidate in ascending id order.                                                         */
+void orc_select_ex(int32_t n, const int32_t *comp, const int32_t *csize, const double *bc,
+                   uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
+                   int32_t tie_random, uint64_t seed, uint32_t graph_tag, uint32_t r,
+                   int32_t *centre);
+
 void orc_select(int32_t n, const int32_t *comp, const int32_t *csize, const double *bc,
                 uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
                 int32_t *centre) {
+  orc_select_ex(n, comp, csize, bc, k_min, in_w, top_k, tie_rel, 0, 0, 0, 0, centre);
+}
+
+void orc_select_ex(int32_t n, const int32_t *comp, const int32_t *csize, const double *bc,
+                   uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
+                   int32_t tie_random, uint64_t seed, uint32_t graph_tag, uint32_t r,
+                   int32_t *centre) {
   for (int32_t v = 0; v < n; ++v) centre[v] = -1;
   for (int32_t root = 0; root < n; ++root) {
     if (comp[root] != root) continue;
@@ -341,9 +357,24 @@ void orc_select(int32_t n, const int32_t *comp, const int32_t *csize, const doub
     if (bstar < 0.0) continue; /* K has no candidate */
     double tau = tie_rel * bstar;
     int32_t c = -1;
-    for (int32_t v = 0; v < n && c < 0; ++v) {
-      if (comp[v] != root || (in_w && !in_w[v])) continue;
-      if (bc[v] >= bstar - tau) c = v;
+    if (tie_random) {
+      uint32_t ties = 0;
+      for (int32_t v = 0; v < n; ++v)
+        if (comp[v] == root && !(in_w && !in_w[v]) && bc[v] >= bstar - tau) ties++;
+      const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      const uint32_t ctr[4] = {(uint32_t)root, r, graph_tag, 3u};
+      uint32_t u[4];
+      orc_philox4x32_10(ctr, key, u);
+      uint32_t k = (uint32_t)(((uint64_t)u[0] * (uint64_t)ties) >> 32);
+      for (int32_t v = 0; v < n && c < 0; ++v) {
+        if (comp[v] != root || (in_w && !in_w[v]) || bc[v] < bstar - tau) continue;
+        if (k == 0) c = v; else k--;
+      }
+    } else {
+      for (int32_t v = 0; v < n && c < 0; ++v) {
+        if (comp[v] != root || (in_w && !in_w[v])) continue;
+        if (bc[v] >= bstar - tau) c = v;
+      }
     }
     if (top_k > 0) {
       double tauK = tie_rel * bmaxK;
@@ -381,7 +412,7 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
                           uint32_t w_lo_all, uint32_t w_hi_all,
                           uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
                           uint32_t *counts, uint64_t *stats, int32_t fb_node,
-                          uint32_t *fb_count) {
+                          uint32_t *fb_count, int32_t tie_random) {
   size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
   uint8_t *alive = (uint8_t *)malloc(mm);
   uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
@@ -406,7 +437,8 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
     st = orc_brandes(n, row_ptr, col, eid, alive, w, src, bc);
     if (st == ORC_ENOMEM) { status = st; goto out; }
     if (st == ORC_EOVERFLOW) { if (stats) stats[0]++; status = ORC_EOVERFLOW; }
-    orc_select(n, comp, csize, bc, k_min, in_w, top_k, tie_rel, centre);
+    orc_select_ex(n, comp, csize, bc, k_min, in_w, top_k, tie_rel, tie_random, seed, graph_tag,
+                  r, centre);
     for (int32_t i = 0; i < n; ++i) {
       int32_t c = centre[comp[i]];
       size_t col_idx = (c < 0) ? (size_t)n : (size_t)c;
