@@ -133,6 +133,12 @@ typedef struct {
   int32_t fallback_node;     /* v_fb in [0, n) (inside or outside W)                          */
   uint32_t *fallback_count;  /* [n] DEVICE u32, accumulated (not cleared), or NULL: draws of  */
                              /* anchor i redirected to v_fb (afc_feasibility needs them)       */
+  int32_t tie_random;        /* 0: ties of the centre rule go to the smallest id.  1: drawn   */
+                             /* uniformly (Remark on randomized tie-breaking, Sec. 4.1): the   */
+                             /* floor(u t / 2^32)-th of the t tied candidates by id, u =       */
+                             /* Philox4x32-10(counter (root, r, graph_tag, 3), key = seed)[0], */
+                             /* root = the smallest id of the component.  Not with reward_k or */
+                             /* report_rank > 1                                                */
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */

@@ -65,7 +65,11 @@ def _declare(L):
     L.orc_brandes.argtypes = [i32, P, P, P, P, P, P, P]
     L.orc_select.argtypes = [i32, P, P, P, u32, P, u32, f64, P]
     L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
-                                        u32, u32, u32, P, u32, f64, P, P, i32, P, i32]
+                                        u32, u32, u32, P, u32, f64, P, P, i32, P, i32, P, P]
+    L.orc_weight_table_normal.argtypes = [i64, P, u32, f64, f64, P, P]
+    L.orc_realize_law.argtypes = [i64, u64, u32, u32, P, u64, P, P, u32, u32, P, P, P, P]
+    L.orc_realize_law.restype = None
+    L.orc_weight_table_normal.restype = None
     L.orc_topk_order.argtypes = [i32, P, P, P, u32, u32, f64, P, P]
     L.orc_count_rewards.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P, u32,
                                     u32, u32, f64, u32, P, P, u32, P, P]
@@ -231,8 +235,34 @@ def count_transitions(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_
     return counts, ovf
 
 
+def realize_law(g: Graph, seed, graph_tag, r, p_survive, w_lo, w_hi, wtab):
+    """(alive [m], length [m]) of realization r with lengths from the tables wtab."""
+    th, th_all = thresholds(p_survive, g.m)
+    lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
+    hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
+    alive = np.zeros(max(g.m, 1), np.uint8)
+    w = np.zeros(max(g.m, 1), np.uint32)
+    lib().orc_realize_law(g.m, seed, graph_tag, r, _p(th), th_all, _p(lo_arr), _p(hi_arr),
+                          0 if lo_arr is not None else int(w_lo),
+                          0 if hi_arr is not None else int(w_hi), _p(wtab[0]), _p(wtab[1]),
+                          _p(alive), _p(w))
+    return alive[:g.m], w[:g.m]
+
+
+def weight_table_normal(w0, wmax, rho_mu, rho_sigma):
+    """Per-edge thresholds of the rounded and clipped normal length law (Sec. 9): (ptr [m+1],
+    tab) as orc_weight_table_normal."""
+    w0 = np.ascontiguousarray(w0, np.uint32)
+    m = w0.shape[0]
+    ptr = np.zeros(m + 1, np.uint32)
+    tab = np.zeros(max(int(np.sum(int(wmax) - w0.astype(np.int64))), 1), np.uint32)
+    lib().orc_weight_table_normal(m, _p(w0), int(wmax), float(rho_mu), float(rho_sigma), _p(ptr),
+                                  _p(tab))
+    return ptr, tab[:int(ptr[m])]
+
+
 def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, candidates,
-           top_k, tie_rel, fb_node, counts=None, tie_random=False):
+           top_k, tie_rel, fb_node, counts=None, tie_random=False, wtab=None):
     th, th_all = thresholds(p_survive, g.m)
     lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
     hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
@@ -246,10 +276,20 @@ def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, c
         _p(th), th_all, _p(lo_arr), _p(hi_arr),
         0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
         k_min, _p(inw), top_k, tie_rel, _p(counts), _p(stats), int(fb_node), _p(fb),
-        1 if tie_random else 0)
+        1 if tie_random else 0, _p(None if wtab is None else wtab[0]),
+        _p(None if wtab is None else wtab[1]))
     if st not in (ORC_OK, ORC_EOVERFLOW):
         _check(st, "count_transitions")
     return counts, (None if fb is None else fb[:g.n]), int(stats[0])
+
+
+def count_with_law(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                   wtab, candidates=None, top_k=0, tie_rel=1e-9):
+    """Counts with edge lengths drawn from per-edge threshold tables wtab = (ptr, tab):
+    length = w_lo + #{thresholds <= u}, capped at w_hi.  Returns (counts, overflows)."""
+    counts, _, ovf = _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                            candidates, top_k, tie_rel, -1, wtab=wtab)
+    return counts, ovf
 
 
 def count_random_ties(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi,

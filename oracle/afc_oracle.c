@@ -145,10 +145,14 @@ uint64_t orc_survival_threshold(double p) {
   return (uint64_t)floor(p * 4294967296.0);
 }
 
-void orc_realize(int64_t m, uint64_t seed, uint32_t graph_tag, uint32_t r,
-                 const uint64_t *thresh, uint64_t thresh_all,
-                 const uint32_t *w_lo, const uint32_t *w_hi, uint32_t w_lo_all, uint32_t w_hi_all,
-                 uint8_t *alive, uint32_t *w) {
+/* With a weight table (wtab_ptr non-NULL) edge e's length is discrete with the law given by  */
+/* its thresholds t_k = wtab[wtab_ptr[e] + k] (non-decreasing): lo + #{k : t_k <= u1},         */
+/* capped at hi (the integer inverse-CDF draw of Sec. 9's rounded and clipped normal law).    */
+void orc_realize_law(int64_t m, uint64_t seed, uint32_t graph_tag, uint32_t r,
+                     const uint64_t *thresh, uint64_t thresh_all,
+                     const uint32_t *w_lo, const uint32_t *w_hi, uint32_t w_lo_all,
+                     uint32_t w_hi_all, const uint32_t *wtab_ptr, const uint32_t *wtab,
+                     uint8_t *alive, uint32_t *w) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   for (int64_t e = 0; e < m; ++e) {
     uint32_t ctr[4] = {(uint32_t)e, r, graph_tag, 0u};
@@ -158,9 +162,46 @@ void orc_realize(int64_t m, uint64_t seed, uint32_t graph_tag, uint32_t r,
     uint32_t lo = w_lo ? w_lo[e] : w_lo_all;
     uint32_t hi = w_hi ? w_hi[e] : w_hi_all;
     alive[e] = ((uint64_t)u[0] < T) ? 1 : 0;
-    uint64_t span = (uint64_t)hi - (uint64_t)lo + 1u;
-    w[e] = lo + (uint32_t)(((uint64_t)u[1] * span) >> 32);
+    if (wtab_ptr) {
+      uint32_t k = 0;
+      for (uint32_t t = wtab_ptr[e]; t < wtab_ptr[e + 1]; ++t) k += (wtab[t] <= u[1]) ? 1u : 0u;
+      w[e] = (lo + k < hi) ? lo + k : hi;
+    } else {
+      uint64_t span = (uint64_t)hi - (uint64_t)lo + 1u;
+      w[e] = lo + (uint32_t)(((uint64_t)u[1] * span) >> 32);
+    }
   }
+}
+
+void orc_realize(int64_t m, uint64_t seed, uint32_t graph_tag, uint32_t r,
+                 const uint64_t *thresh, uint64_t thresh_all,
+                 const uint32_t *w_lo, const uint32_t *w_hi, uint32_t w_lo_all, uint32_t w_hi_all,
+                 uint8_t *alive, uint32_t *w) {
+  orc_realize_law(m, seed, graph_tag, r, thresh, thresh_all, w_lo, w_hi, w_lo_all, w_hi_all,
+                  NULL, NULL, alive, w);
+}
+
+/* Thresholds of the rounded and clipped normal length law (Sec. 9, Les Miserables setting):  */
+/* x ~ N(mu_e, sigma_e^2), mu_e = w0_e + rho_mu (wmax - w0_e), sigma_e = rho_sigma (wmax -    */
+/* w0_e), length = round(x) clipped to [w0_e, wmax].  Edge e gets wmax - w0_e thresholds       */
+/* t_k = min(floor(2^32 F(w0_e + k)), 2^32 - 1), F(x) = Phi((x + 1/2 - mu_e) / sigma_e), the   */
+/* probability that the clipped, rounded draw is at most x; ptr[e] indexes them.             */
+void orc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double rho_mu,
+                             double rho_sigma, uint32_t *ptr, uint32_t *tab) {
+  uint32_t o = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    ptr[e] = o;
+    const double span = (double)wmax - (double)w0[e];
+    const double mu = (double)w0[e] + rho_mu * span, sigma = rho_sigma * span;
+    for (uint32_t x = w0[e]; x < wmax; ++x) {
+      double F;
+      if (sigma > 0.0) F = 0.5 * erfc(-(((double)x + 0.5 - mu) / sigma) / sqrt(2.0));
+      else F = ((double)x + 0.5 >= mu) ? 1.0 : 0.0;
+      double t = floor(ldexp(F, 32));
+      tab[o++] = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+    }
+  }
+  ptr[m] = o;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -412,7 +453,8 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
                           uint32_t w_lo_all, uint32_t w_hi_all,
                           uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
                           uint32_t *counts, uint64_t *stats, int32_t fb_node,
-                          uint32_t *fb_count, int32_t tie_random) {
+                          uint32_t *fb_count, int32_t tie_random, const uint32_t *wtab_ptr,
+                          const uint32_t *wtab) {
   size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
   uint8_t *alive = (uint8_t *)malloc(mm);
   uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
@@ -425,7 +467,8 @@ int orc_count_transitions(int32_t n, int64_t m, const int64_t *row_ptr, const in
   if (!alive || !w || !comp || !csize || !centre || !src || !bc) { status = ORC_ENOMEM; goto out; }
   for (uint32_t k = 0; k < r_count; ++k) {
     uint32_t r = r_begin + k;
-    orc_realize(m, seed, graph_tag, r, thresh, thresh_all, w_lo, w_hi, w_lo_all, w_hi_all, alive, w);
+    orc_realize_law(m, seed, graph_tag, r, thresh, thresh_all, w_lo, w_hi, w_lo_all, w_hi_all,
+                    wtab_ptr, wtab, alive, w);
     int st = orc_components(n, row_ptr, col, eid, alive, comp, csize);
     if (st != ORC_OK) { status = st; goto out; }
     /* sources: members of valid components that contain at least one candidate */

@@ -92,6 +92,9 @@ int validate(const afc_mc_problem *p) {
     if (p->reward_k && !p->psi_sum) return fail(AFC_EINVAL, "reward_k needs psi_sum");
   }
   if (p->use_fallback != 0 && p->use_fallback != 1) return fail(AFC_EINVAL, "use_fallback must be 0 or 1");
+  if (p->tie_random != 0 && p->tie_random != 1) return fail(AFC_EINVAL, "tie_random must be 0 or 1");
+  if (p->tie_random && (p->reward_k || p->report_rank > 1))
+    return fail(AFC_EINVAL, "the randomised tie-break does not combine with rewards or rank-r reports");
   if (p->use_fallback) {
     if (p->fallback_node < 0 || p->fallback_node >= p->n)
       return fail(AFC_EINVAL, "fallback_node %d outside [0, n)", p->fallback_node);
@@ -151,6 +154,7 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   d.report_rank = p.report_rank;
   d.fb_node = p.use_fallback ? (uint32_t)p.fallback_node : 0xFFFFFFFFu;
   d.fb_count = p.use_fallback ? p.fallback_count : nullptr;
+  d.tie_random = p.tie_random ? 1u : 0u;
   d.r_begin = r_begin;
   d.counts = counts;
   d.stats = stats;

@@ -44,6 +44,7 @@ struct McDev {
   uint32_t report_rank;          // 0 / 1: the centre; r > 1: the r-th node of the ordering
   uint32_t fb_node;              // fallback node v_fb, or 0xFFFFFFFF (infeasible draws absorb)
   uint32_t *fb_count;            // [n] redirected draws per anchor, or null
+  uint32_t tie_random;           // 1: uniformly drawn tie-break instead of the smallest id
   uint32_t *counts;
   afc_mc_stats *stats;
   double *dump_bc;

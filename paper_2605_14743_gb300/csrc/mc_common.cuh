@@ -924,9 +924,39 @@ __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const 
     if (!comp_valid(cinfo[root], P.k_min)) continue;
     if (!(P.in_w == nullptr || P.in_w[v])) continue;
     const double bstar = __longlong_as_double((long long)best[root]);
-    if (bc[v] >= bstar - P.tie_rel * bstar) atomicMin(&centre[root], v);
+    if (bc[v] >= bstar - P.tie_rel * bstar) {
+      atomicMin(&centre[root], v);
+      if (P.tie_random) atomicAdd(&rank[root], 1u);   // 1 + number of ties
+    }
   }
   __syncthreads();
+  if (P.tie_random) {
+    // uniformly randomised tie-break (Remark on randomized tie-breaking, Sec. 4.1): the
+    // floor(u |ties| / 2^32)-th tied candidate in ascending id, u from Philox counter
+    // (root, realization, graph tag, 3); the root is the smallest id of its component
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+      if (comp[v] != v || !comp_valid(cinfo[v], P.k_min)) continue;
+      const uint32_t ties = rank[v] - 1u;
+      if (ties < 2u) continue;
+      const uint4 u = philox4x32_10(make_uint4(v, P.r_begin + r_local, P.graph_tag, 3u),
+                                    P.key_lo, P.key_hi);
+      uint32_t k = (uint32_t)(((uint64_t)u.x * (uint64_t)ties) >> 32);
+      const double bstar = __longlong_as_double((long long)best[v]);
+      for (uint32_t w = v; w < n && k > 0u; ++w) {
+        if (comp[w] != v || !(P.in_w == nullptr || P.in_w[w])) continue;
+        if (bc[w] < bstar - P.tie_rel * bstar) continue;
+        if (--k == 0u) {
+          // the next tied candidate after w
+          for (uint32_t x = w + 1; x < n; ++x)
+            if (comp[x] == v && (P.in_w == nullptr || P.in_w[x]) &&
+                bc[x] >= bstar - P.tie_rel * bstar) { centre[v] = x; break; }
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) rank[v] = 1u;
+    __syncthreads();
+  }
   if (P.top_k || gap_test) {
     if (P.top_k) {   // best now becomes the maximum over the whole component
       for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) best[v] = 0ull;

@@ -120,7 +120,7 @@ class Query:
 
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
                  slots_per_team=0, stream=None, memory_path=0, reward_k=0, reward_gamma=None,
-                 reward_pool=None, report_rank=0, fallback_node=None):
+                 reward_pool=None, report_rank=0, fallback_node=None, tie_random=False):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -158,6 +158,7 @@ class Query:
                                  bucket_width, block_threads, team_threads, slots_per_team,
                                  memory_path, reward_k, self.gamma, self.pool, self.psi,
                                  report_rank)
+        self.prob.tie_random = 1 if tie_random else 0
         # fallback selector Sel_{W,fb}: infeasible valid draws report v_fb (counted per anchor)
         self.fb_count = None
         if fallback_node is not None:
