@@ -139,6 +139,12 @@ typedef struct {
                              /* Philox4x32-10(counter (root, r, graph_tag, 3), key = seed)[0], */
                              /* root = the smallest id of the component.  Not with reward_k or */
                              /* report_rank > 1                                                */
+  /* Discrete length law (Sec. 9 weighted-network experiment).  With wtab_ptr non-NULL edge e's */
+  /* length is lo_e + #{k : wtab[wtab_ptr[e] + k] <= u1}, capped at hi_e, u1 the same Philox     */
+  /* word that the uniform law uses (thresholds non-decreasing per edge; afc_weight_table_normal */
+  /* builds them for the rounded and clipped normal law).  DEVICE [m+1] and thresholds.        */
+  const uint32_t *wtab_ptr;
+  const uint32_t *wtab;
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */
@@ -196,6 +202,18 @@ typedef struct {
 } afc_tune_result;
 int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *stream,
                  afc_tune_result *out);
+
+/* Threshold tables of the rounded and clipped normal length law of the paper's weighted-network
+ * experiment (Sec. 9): x ~ N(mu_e, sigma_e^2) with mu_e = w0_e + rho_mu (wmax - w0_e), sigma_e =
+ * rho_sigma (wmax - w0_e), length round(x) clipped to [w0_e, wmax].  Edge e gets wmax - w0_e
+ * thresholds t_k = min(floor(2^32 F(w0_e + k)), 2^32 - 1), F(x) = Phi((x + 1/2 - mu_e) /
+ * sigma_e), indexed by ptr[e] .. ptr[e+1]-1 (a law quantised to 2^-32).  HOST in: w0 [m] (each
+ * in [1, wmax]); HOST out: ptr [m+1], tab [capacity]; *used = thresholds written.  Use with
+ * afc_mc_problem.w_lo = w0 and w_hi_all = wmax.  Errors: AFC_EINVAL for bad arguments,
+ * AFC_ENOMEM when capacity < sum_e (wmax - w0_e). */
+int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double rho_mu,
+                            double rho_sigma, uint32_t *ptr, uint32_t *tab, size_t capacity,
+                            size_t *used);
 
 /* Several base graphs in one persistent launch (the batched mix).  probs: HOST array of
  * nprob problems; r_count: HOST [nprob]; counts: HOST array of nprob DEVICE count matrices;

@@ -37,7 +37,7 @@ __all__ = [
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
     "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_robust_inner",
-    "afc_robust_value_workspace", "afc_robust_value",
+    "afc_robust_value_workspace", "afc_robust_value", "afc_weight_table_normal",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -69,7 +69,7 @@ class McProblem(ctypes.Structure):
                 ("slots_per_team", c_i32), ("memory_path", c_i32), ("reward_k", c_u32),
                 ("reward_gamma", c_p), ("reward_pool", c_p), ("psi_sum", c_p),
                 ("report_rank", c_u32), ("use_fallback", c_i32), ("fallback_node", c_i32),
-                ("fallback_count", c_p), ("tie_random", c_i32)]
+                ("fallback_count", c_p), ("tie_random", c_i32), ("wtab_ptr", c_p), ("wtab", c_p)]
 
 
 class McStats(ctypes.Structure):
@@ -154,6 +154,8 @@ _SIGS = {
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
     "afc_w1_graph": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_i32, c_p], ctypes.c_int),
+    "afc_weight_table_normal": ([c_i64, c_p, c_u32, c_f64, c_f64, c_p, c_p, c_sz, c_p],
+                                ctypes.c_int),
     "afc_robust_inner": ([ctypes.POINTER(Chain), c_p, c_f64, c_f64, c_i32, c_p, c_f64, c_p, c_p,
                           c_p, c_sz, c_p], ctypes.c_int),
     "afc_robust_value_workspace": ([c_i32], c_sz),
@@ -324,6 +326,19 @@ def afc_robust_value(chain, counts, eps, r_min, support_only, sense, V, Qstar, b
                                 _ptr(scalars), ctypes.byref(it), _ptr(workspace),
                                 int(workspace_bytes), stream))
     return int(it.value)
+
+
+def afc_weight_table_normal(w0, wmax, rho_mu, rho_sigma):
+    """Host threshold tables (ptr [m+1], tab) of the rounded and clipped normal length law."""
+    w0 = np.ascontiguousarray(w0, np.uint32)
+    m = w0.shape[0]
+    cap = int(np.sum(int(wmax) - w0.astype(np.int64))) if m else 0
+    ptr = np.zeros(m + 1, np.uint32)
+    tab = np.zeros(max(cap, 1), np.uint32)
+    used = ctypes.c_size_t(0)
+    _chk(lib().afc_weight_table_normal(m, _ptr(w0), int(wmax), float(rho_mu), float(rho_sigma),
+                                       _ptr(ptr), _ptr(tab), cap, ctypes.byref(used)))
+    return ptr, tab[:used.value]
 
 
 def afc_w1_graph(n, eu, ev, x, y):

@@ -93,6 +93,7 @@ int validate(const afc_mc_problem *p) {
   }
   if (p->use_fallback != 0 && p->use_fallback != 1) return fail(AFC_EINVAL, "use_fallback must be 0 or 1");
   if (p->tie_random != 0 && p->tie_random != 1) return fail(AFC_EINVAL, "tie_random must be 0 or 1");
+  if (p->wtab_ptr && !p->wtab) return fail(AFC_EINVAL, "wtab_ptr without wtab");
   if (p->tie_random && (p->reward_k || p->report_rank > 1))
     return fail(AFC_EINVAL, "the randomised tie-break does not combine with rewards or rank-r reports");
   if (p->use_fallback) {
@@ -155,6 +156,8 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   d.fb_node = p.use_fallback ? (uint32_t)p.fallback_node : 0xFFFFFFFFu;
   d.fb_count = p.use_fallback ? p.fallback_count : nullptr;
   d.tie_random = p.tie_random ? 1u : 0u;
+  d.wtab_ptr = p.wtab_ptr;
+  d.wtab = p.wtab_ptr ? p.wtab : nullptr;
   d.r_begin = r_begin;
   d.counts = counts;
   d.stats = stats;
@@ -464,6 +467,38 @@ uint64_t afc_survival_threshold(double p) {
   if (!(p > 0.0)) return 0;
   if (p >= 1.0) return 1ull << 32;
   return (uint64_t)std::floor(p * 4294967296.0);
+}
+
+int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double rho_mu,
+                            double rho_sigma, uint32_t *ptr, uint32_t *tab, size_t capacity,
+                            size_t *used) {
+  if (m < 0 || !ptr || (m > 0 && !w0) || wmax < 1 || wmax > 65535 || !(rho_sigma >= 0.0) ||
+      !std::isfinite(rho_mu))
+    return fail(AFC_EINVAL, "bad arguments");
+  size_t need = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    if (w0[e] < 1 || w0[e] > wmax) return fail(AFC_EINVAL, "w0[%lld] = %u outside [1, wmax]", (long long)e, w0[e]);
+    need += wmax - w0[e];
+  }
+  if (need > capacity || (need > 0 && !tab))
+    return fail(AFC_ENOMEM, "%zu thresholds needed, capacity %zu", need, capacity);
+  size_t o = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    ptr[e] = (uint32_t)o;
+    const double span = (double)wmax - (double)w0[e];
+    const double mu = (double)w0[e] + rho_mu * span, sigma = rho_sigma * span;
+    for (uint32_t x = w0[e]; x < wmax; ++x) {
+      // P(the rounded, clipped draw is at most x) = Phi((x + 1/2 - mu) / sigma)
+      double F;
+      if (sigma > 0.0) F = 0.5 * std::erfc(-(((double)x + 0.5 - mu) / sigma) / std::sqrt(2.0));
+      else F = ((double)x + 0.5 >= mu) ? 1.0 : 0.0;
+      const double t = std::floor(std::ldexp(F, 32));
+      tab[o++] = t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+    }
+  }
+  ptr[m] = (uint32_t)o;
+  if (used) *used = o;
+  return AFC_OK;
 }
 
 int afc_counts_path(const afc_mc_problem *prob) {

@@ -45,6 +45,8 @@ struct McDev {
   uint32_t fb_node;              // fallback node v_fb, or 0xFFFFFFFF (infeasible draws absorb)
   uint32_t *fb_count;            // [n] redirected draws per anchor, or null
   uint32_t tie_random;           // 1: uniformly drawn tie-break instead of the smallest id
+  const uint32_t *wtab_ptr;      // [m+1] per-edge threshold ranges of a discrete length law, or null
+  const uint32_t *wtab;          // thresholds
   uint32_t *counts;
   afc_mc_stats *stats;
   double *dump_bc;

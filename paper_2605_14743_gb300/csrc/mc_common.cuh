@@ -739,7 +739,13 @@ __device__ __forceinline__ void edge_draw(const McDev &P, uint32_t r, uint32_t e
   const uint32_t lo = P.w_lo ? P.w_lo[e] : P.w_lo_all;
   const uint32_t hi = P.w_hi ? P.w_hi[e] : P.w_hi_all;
   alive = (uint64_t)u.x < T;
-  w = lo + (uint32_t)(((uint64_t)u.y * ((uint64_t)hi - lo + 1u)) >> 32);
+  if (P.wtab_ptr) {   // discrete law: lo + #{thresholds <= u}, capped at hi
+    uint32_t k = 0;
+    for (uint32_t t = P.wtab_ptr[e]; t < P.wtab_ptr[e + 1]; ++t) k += P.wtab[t] <= u.y ? 1u : 0u;
+    w = min(lo + k, hi);
+  } else {
+    w = lo + (uint32_t)(((uint64_t)u.y * ((uint64_t)hi - lo + 1u)) >> 32);
+  }
 }
 
 // Builds the alive-compacted CSR of realization r into rp/arc (thread per contiguous vertex

@@ -120,7 +120,8 @@ class Query:
 
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
                  slots_per_team=0, stream=None, memory_path=0, reward_k=0, reward_gamma=None,
-                 reward_pool=None, report_rank=0, fallback_node=None, tie_random=False):
+                 reward_pool=None, report_rank=0, fallback_node=None, tie_random=False,
+                 length_table=None):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -159,6 +160,13 @@ class Query:
                                  memory_path, reward_k, self.gamma, self.pool, self.psi,
                                  report_rank)
         self.prob.tie_random = 1 if tie_random else 0
+        # discrete length law: host tables (ptr, thresholds), e.g. afc_weight_table_normal's
+        self.wtab = None
+        if length_table is not None:
+            self.wtab = tuple(torch.from_numpy(np.ascontiguousarray(a, np.uint32).view(np.int32))
+                              .to(device) for a in length_table)
+            self.prob.wtab_ptr = self.wtab[0].data_ptr()
+            self.prob.wtab = self.wtab[1].data_ptr() if self.wtab[1].numel() else self.wtab[0].data_ptr()
         # fallback selector Sel_{W,fb}: infeasible valid draws report v_fb (counted per anchor)
         self.fb_count = None
         if fallback_node is not None:

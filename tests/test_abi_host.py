@@ -167,3 +167,15 @@ def test_w1_graph_host_matches_oracle():
         for k in range(2):
             assert abs(got[k] - O.w1_graph(n, eu, ev, x[k], y)) <= 1e-9
         assert afc.afc_w1_graph(n, eu, ev, y, y)[0] <= 1e-12
+
+
+def test_weight_tables_match_the_oracle_bit_for_bit():
+    import oracle as O
+    rng = np.random.default_rng(8)
+    for wmax, rm, rs in ((31, 0.3, 0.2), (12, 0.0, 0.5), (50, 0.9, 0.05), (7, 0.5, 0.0)):
+        w0 = rng.integers(1, wmax + 1, size=200).astype(np.uint32)
+        ptr, tab = afc.afc_weight_table_normal(w0, wmax, rm, rs)
+        optr, otab = O.weight_table_normal(w0, wmax, rm, rs)
+        assert (ptr == optr).all() and (tab == otab).all()
+    with pytest.raises(afc.AfcError):
+        afc.afc_weight_table_normal(np.array([0, 3], np.uint32), 5, 0.1, 0.1)
