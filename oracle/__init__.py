@@ -67,6 +67,9 @@ def _declare(L):
     L.orc_count_transitions.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P,
                                         u32, u32, u32, P, u32, f64, P, P, i32, P, i32, P, P]
     L.orc_weight_table_normal.argtypes = [i64, P, u32, f64, f64, P, P]
+    L.orc_count_per_row.argtypes = [i32, i64, P, P, P, u64, u32, u32, u32, P, u64, P, P, u32,
+                                    u32, P, P, u32, P, u32, f64, i32, i32, u32, P, P, P]
+    L.orc_count_per_row.restype = ctypes.c_int
     L.orc_realize_law.argtypes = [i64, u64, u32, u32, P, u64, P, P, u32, u32, P, P, P, P]
     L.orc_realize_law.restype = None
     L.orc_weight_table_normal.restype = None
@@ -281,6 +284,31 @@ def _count(g, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min, c
     if st not in (ORC_OK, ORC_EOVERFLOW):
         _check(st, "count_transitions")
     return counts, (None if fb is None else fb[:g.n]), int(stats[0])
+
+
+def count_per_row(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,
+                  candidates=None, top_k=0, tie_rel=1e-9, tie_random=False, fallback=-1,
+                  hop_radius=0, wtab=None):
+    """Literal row-wise counts (Alg. 2: r_count independent draws per row, draw m of row i on
+    realization m n + i), optionally on r-hop neighbourhoods of the base graph.  Returns
+    (counts [n, n+1], fb_count [n], overflows)."""
+    th, th_all = thresholds(p_survive, g.m)
+    lo_arr = None if np.ndim(w_lo) == 0 else np.ascontiguousarray(w_lo, dtype=np.uint32)
+    hi_arr = None if np.ndim(w_hi) == 0 else np.ascontiguousarray(w_hi, dtype=np.uint32)
+    inw = candidate_mask(g.n, candidates)
+    counts = np.zeros((g.n, g.n + 1), np.uint32)
+    fb = np.zeros(max(g.n, 1), np.uint32)
+    stats = np.zeros(1, np.uint64)
+    st = lib().orc_count_per_row(
+        g.n, g.m, _p(g.row_ptr), _p(g.col), _p(g.eid), seed, graph_tag, r_begin, r_count,
+        _p(th), th_all, _p(lo_arr), _p(hi_arr),
+        0 if lo_arr is not None else int(w_lo), 0 if hi_arr is not None else int(w_hi),
+        _p(None if wtab is None else wtab[0]), _p(None if wtab is None else wtab[1]),
+        k_min, _p(inw), top_k, tie_rel, 1 if tie_random else 0, int(fallback), int(hop_radius),
+        _p(counts), _p(fb), _p(stats))
+    if st not in (ORC_OK, ORC_EOVERFLOW):
+        _check(st, "count_per_row")
+    return counts, fb[:g.n], int(stats[0])
 
 
 def count_with_law(g: Graph, seed, graph_tag, r_begin, r_count, p_survive, w_lo, w_hi, k_min,

@@ -498,6 +498,90 @@ out:
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Literal row-wise construction (Alg. 2 with M independent SampleNext(i) calls per row,   */
+/* no realization shared between rows), optionally on anchor-dependent r-hop               */
+/* neighbourhoods (Sec. 9 weighted-network experiment).  Draw m of row i uses realization  */
+/* rho = m n + i.  With hop_radius > 0 the working graph is the realized graph induced on   */
+/* S_r(i), the nodes within hop_radius hops of i in the base graph; K is i's component      */
+/* there.  next(i) as in orc_count_transitions (fallback and randomised ties included,      */
+/* with rho as the realization index of the tie draw).                                      */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_count_per_row(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                      const int32_t *eid, uint64_t seed, uint32_t graph_tag, uint32_t r_begin,
+                      uint32_t r_count, const uint64_t *thresh, uint64_t thresh_all,
+                      const uint32_t *w_lo, const uint32_t *w_hi, uint32_t w_lo_all,
+                      uint32_t w_hi_all, const uint32_t *wtab_ptr, const uint32_t *wtab,
+                      uint32_t k_min, const uint8_t *in_w, uint32_t top_k, double tie_rel,
+                      int32_t tie_random, int32_t fb_node, uint32_t hop_radius,
+                      uint32_t *counts, uint32_t *fb_count, uint64_t *stats) {
+  size_t nn = (size_t)(n > 0 ? n : 1), mm = (size_t)(m > 0 ? m : 1);
+  uint8_t *alive = (uint8_t *)malloc(mm);
+  uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * mm);
+  int32_t *comp = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *csize = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *centre = (int32_t *)malloc(sizeof(int32_t) * nn);
+  uint8_t *src = (uint8_t *)malloc(nn);
+  double *bc = (double *)malloc(sizeof(double) * nn);
+  int32_t *hop = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int status = ORC_OK;
+  if (!alive || !w || !comp || !csize || !centre || !src || !bc || !hop || !queue) {
+    status = ORC_ENOMEM;
+    goto out;
+  }
+  for (uint32_t k = 0; k < r_count; ++k) {
+    for (int32_t i = 0; i < n; ++i) {
+      const uint32_t rho = (r_begin + k) * (uint32_t)n + (uint32_t)i;
+      orc_realize_law(m, seed, graph_tag, rho, thresh, thresh_all, w_lo, w_hi, w_lo_all,
+                      w_hi_all, wtab_ptr, wtab, alive, w);
+      if (hop_radius > 0) {
+        /* S_r(i): breadth-first search of the base graph from i, hop_radius levels */
+        for (int32_t v = 0; v < n; ++v) hop[v] = -1;
+        int32_t head = 0, tail = 0;
+        hop[i] = 0;
+        queue[tail++] = i;
+        while (head < tail) {
+          const int32_t v = queue[head++];
+          if ((uint32_t)hop[v] == hop_radius) continue;
+          for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a)
+            if (hop[col[a]] < 0) { hop[col[a]] = hop[v] + 1; queue[tail++] = col[a]; }
+        }
+        for (int32_t v = 0; v < n; ++v)
+          for (int64_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a)
+            if (hop[v] < 0 || hop[col[a]] < 0) alive[eid[a]] = 0;
+      }
+      int st = orc_components(n, row_ptr, col, eid, alive, comp, csize);
+      if (st != ORC_OK) { status = st; goto out; }
+      const int32_t root = comp[i];
+      int has_cand = 0;
+      for (int32_t v = 0; v < n; ++v) {
+        src[v] = (comp[v] == root) ? 1 : 0;
+        if (src[v] && (!in_w || in_w[v])) has_cand = 1;
+      }
+      size_t col_idx = (size_t)n;
+      if ((uint32_t)csize[i] >= k_min && has_cand) {
+        st = orc_brandes(n, row_ptr, col, eid, alive, w, src, bc);
+        if (st == ORC_ENOMEM) { status = st; goto out; }
+        if (st == ORC_EOVERFLOW) { if (stats) stats[0]++; status = ORC_EOVERFLOW; }
+        orc_select_ex(n, comp, csize, bc, k_min, in_w, top_k, tie_rel, tie_random, seed,
+                      graph_tag, rho, centre);
+        if (centre[root] >= 0) col_idx = (size_t)centre[root];
+      }
+      if (col_idx == (size_t)n && fb_node >= 0 && (uint32_t)csize[i] >= k_min) {
+        col_idx = (size_t)fb_node;
+        if (fb_count) fb_count[i] += 1u;
+      }
+      counts[(size_t)i * (size_t)(n + 1) + col_idx] += 1u;
+    }
+  }
+out:
+  free(alive); free(w); free(comp); free(csize); free(centre); free(src); free(bc); free(hop);
+  free(queue);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Realization-level bootstrap weights (Sec. 8: nonparametric bootstrap of b by resampling */
 /* the draws with replacement; with realization sharing the draws of all anchors come from */
 /* the same realizations, so whole realizations are resampled).  Replicate b draws R       */
