@@ -145,6 +145,16 @@ typedef struct {
   /* builds them for the rounded and clipped normal law).  DEVICE [m+1] and thresholds.        */
   const uint32_t *wtab_ptr;
   const uint32_t *wtab;
+  /* Row-wise mode (Alg. 2 taken literally: every row i gets its own independent draws, no      */
+  /* realization shared between rows).  per_row 1: a call over realizations [r_begin, r_begin   */
+  /* + r_count) makes r_count draws for every row, draw m of row i on realization m n + i      */
+  /* ((r_begin + r_count) n < 2^32); only row i is counted, from the betweenness of i's         */
+  /* component (r_count x n items: n times the work of the shared mode; stats count items).     */
+  /* hop_radius r > 0 (row-wise mode only): the working graph is the realization induced on    */
+  /* S_r(i), the nodes within r hops of i in the base graph, and K is i's component there      */
+  /* (Sec. 9 weighted-network experiment).  No dump_bc / dump_next, rewards or rank-r reports. */
+  int32_t per_row;
+  uint32_t hop_radius;
 } afc_mc_problem;
 
 /* Device-side counters of one or more afc_transition_counts calls (caller zeroes them). */

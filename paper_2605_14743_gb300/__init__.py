@@ -69,7 +69,8 @@ class McProblem(ctypes.Structure):
                 ("slots_per_team", c_i32), ("memory_path", c_i32), ("reward_k", c_u32),
                 ("reward_gamma", c_p), ("reward_pool", c_p), ("psi_sum", c_p),
                 ("report_rank", c_u32), ("use_fallback", c_i32), ("fallback_node", c_i32),
-                ("fallback_count", c_p), ("tie_random", c_i32), ("wtab_ptr", c_p), ("wtab", c_p)]
+                ("fallback_count", c_p), ("tie_random", c_i32), ("wtab_ptr", c_p), ("wtab", c_p),
+                ("per_row", c_i32), ("hop_radius", c_u32)]
 
 
 class McStats(ctypes.Structure):

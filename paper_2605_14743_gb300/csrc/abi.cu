@@ -94,6 +94,10 @@ int validate(const afc_mc_problem *p) {
   if (p->use_fallback != 0 && p->use_fallback != 1) return fail(AFC_EINVAL, "use_fallback must be 0 or 1");
   if (p->tie_random != 0 && p->tie_random != 1) return fail(AFC_EINVAL, "tie_random must be 0 or 1");
   if (p->wtab_ptr && !p->wtab) return fail(AFC_EINVAL, "wtab_ptr without wtab");
+  if (p->per_row != 0 && p->per_row != 1) return fail(AFC_EINVAL, "per_row must be 0 or 1");
+  if (p->hop_radius && !p->per_row) return fail(AFC_EINVAL, "hop_radius needs the row-wise mode (per_row = 1)");
+  if (p->per_row && (p->reward_k || p->report_rank > 1))
+    return fail(AFC_EINVAL, "the row-wise mode does not combine with rewards or rank-r reports");
   if (p->tie_random && (p->reward_k || p->report_rank > 1))
     return fail(AFC_EINVAL, "the randomised tie-break does not combine with rewards or rank-r reports");
   if (p->use_fallback) {
@@ -158,6 +162,8 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   d.tie_random = p.tie_random ? 1u : 0u;
   d.wtab_ptr = p.wtab_ptr;
   d.wtab = p.wtab_ptr ? p.wtab : nullptr;
+  d.per_row = p.per_row ? 1u : 0u;
+  d.hop_radius = p.per_row ? p.hop_radius : 0u;
   d.r_begin = r_begin;
   d.counts = counts;
   d.stats = stats;
@@ -286,6 +292,12 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   return b;
 }
 
+// Items of a counting call: r_count realizations, or in the row-wise mode r_count draws for
+// each of the n rows (one item per draw and row).
+uint64_t items_of(const afc_mc_problem &p, uint32_t r_count) {
+  return p.per_row ? (uint64_t)r_count * (uint64_t)p.n : (uint64_t)r_count;
+}
+
 bool smem_fits(const afc_mc_problem &p) {
   return plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1, p.team_threads, p.slots_per_team).fits;
 }
@@ -313,7 +325,8 @@ size_t meta_bytes(int nprob) {
 size_t counts_ws_total(int nprob, const afc_mc_problem *probs, const uint32_t *r_count) {
   size_t big = 0;
   for (int g = 0; g < nprob; ++g)
-    if (wants_global(probs[g])) big = std::max(big, plan_big(probs[g], r_count ? r_count[g] : 1u << 20).total);
+    if (wants_global(probs[g]))
+      big = std::max(big, plan_big(probs[g], r_count ? items_of(probs[g], r_count[g]) : 1u << 20).total);
   return meta_bytes(nprob) + big;
 }
 
@@ -327,6 +340,13 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     if (!counts[g]) return fail(AFC_EINVAL, "counts[%d] is null", g);
     if (probs[g].memory_path == AFC_PATH_SHARED && !smem_fits(probs[g]))
       return fail(AFC_EUNSUPPORTED, "problem %d does not fit the shared-memory counting path", g);
+    if (probs[g].per_row) {
+      const uint64_t rb = r_begin ? r_begin[g] : 0u;
+      if ((rb + r_count[g]) * (uint64_t)probs[g].n > 0xFFFFFFFFull)
+        return fail(AFC_EUNSUPPORTED, "row-wise mode: (r_begin + r_count) x n must stay below 2^32");
+      if (dump_bc || dump_next)
+        return fail(AFC_EINVAL, "the row-wise mode writes no per-realization dumps");
+    }
   }
   // problems on the shared-memory path first (one persistent launch), then the others
   std::vector<int> order, big;
@@ -345,7 +365,7 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     devs[k] = to_dev(probs[g], r_begin ? r_begin[g] : 0u, counts[g], stats ? stats[g] : nullptr,
                      nprob == 1 ? dump_bc : nullptr, nprob == 1 ? dump_next : nullptr);
     if (k < ns) {
-      prefix[k + 1] = prefix[k] + r_count[g];
+      prefix[k + 1] = prefix[k] + items_of(probs[g], r_count[g]);
       nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
       amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
     }
@@ -386,7 +406,7 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   unsigned char *bigbase = ws + meta_bytes(nprob);
   for (int k = ns; k < nprob; ++k) {
     const afc_mc_problem &p = probs[order[k]];
-    const uint32_t rc = r_count[order[k]];
+    const uint32_t rc = (uint32_t)items_of(p, r_count[order[k]]);
     if (rc == 0) continue;
     const BigPlan b = plan_big(p, rc);
     std::vector<BigGroup> groups(b.ngroups);

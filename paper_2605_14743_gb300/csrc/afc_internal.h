@@ -47,6 +47,8 @@ struct McDev {
   uint32_t tie_random;           // 1: uniformly drawn tie-break instead of the smallest id
   const uint32_t *wtab_ptr;      // [m+1] per-edge threshold ranges of a discrete length law, or null
   const uint32_t *wtab;          // thresholds
+  uint32_t per_row;              // 1: independent draws per row (items = draws x n)
+  uint32_t hop_radius;           // row-wise mode: r of the r-hop neighbourhood (0 = whole graph)
   uint32_t *counts;
   afc_mc_stats *stats;
   double *dump_bc;

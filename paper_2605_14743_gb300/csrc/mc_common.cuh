@@ -748,10 +748,53 @@ __device__ __forceinline__ void edge_draw(const McDev &P, uint32_t r, uint32_t e
   }
 }
 
+// Item r_local of a problem: its realization index and, in the row-wise mode (independent
+// draws per row, Alg. 2), its anchor (draw m of row i uses realization m n + i); otherwise
+// anchor = 0xFFFFFFFF and the realization serves every row.
+__device__ __forceinline__ uint32_t item_rho(const McDev &P, uint32_t r_local, uint32_t &anchor) {
+  if (!P.per_row) {
+    anchor = 0xFFFFFFFFu;
+    return P.r_begin + r_local;
+  }
+  const uint32_t n = (uint32_t)P.n;
+  anchor = r_local % n;
+  return (P.r_begin + r_local / n) * n + anchor;
+}
+
+// Hop distances from the anchor in the base graph, up to P.hop_radius (0xFFFFFFFF beyond):
+// the neighbourhood S_r(i) of the r-hop mode.  Level-synchronous; a node reached twice in one
+// level gets the same value from every writer.
+__device__ inline void hop_ball(const McDev &P, uint32_t anchor, uint32_t *hop) {
+  const uint32_t n = (uint32_t)P.n;
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) hop[v] = v == anchor ? 0u : 0xFFFFFFFFu;
+  __syncthreads();
+  for (uint32_t lev = 0; lev < P.hop_radius; ++lev) {
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+      if (hop[v] != lev) continue;
+      for (int32_t a = P.row_ptr[v]; a < P.row_ptr[v + 1]; ++a) {
+        const uint32_t u = (uint32_t)P.col[a];
+        if (u < n && hop[u] == 0xFFFFFFFFu) hop[u] = lev + 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Row-wise mode: only the anchor's component stays valid (the other components neither
+// contribute sources nor report).
+__device__ inline void keep_anchor_component(uint32_t n, uint32_t anchor, const uint32_t *comp,
+                                             uint32_t *cinfo) {
+  const uint32_t ra = comp[anchor];
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x)
+    if (comp[v] == v && v != ra) cinfo[v] &= ~kHasCand;
+  __syncthreads();
+}
+
 // Builds the alive-compacted CSR of realization r into rp/arc (thread per contiguous vertex
-// range, offsets from one block scan) and the largest alive length into ctl->wmax.
+// range, offsets from one block scan) and the largest alive length into ctl->wmax.  With hop
+// distances given, only arcs between nodes within P.hop_radius of the anchor are kept.
 __device__ inline void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uint32_t *arc,
-                            CtaCtl *ctl) {
+                            CtaCtl *ctl, const uint32_t *hop = nullptr) {
   const uint32_t n = P.n;
   const uint32_t cap = (uint32_t)(2 * P.m);   // arc slots reserved in the layout
   const uint32_t T = blockDim.x;
@@ -763,6 +806,8 @@ __device__ inline void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uin
     for (int32_t a = a0; a < a1; ++a) {
       const uint32_t e = (uint32_t)P.eid[a];
       if (e >= (uint64_t)P.m) continue;
+      if (hop && (hop[v] > P.hop_radius || (uint32_t)P.col[a] >= n ||
+                  hop[P.col[a]] > P.hop_radius)) continue;
       bool alive; uint32_t w;
       edge_draw(P, r, e, alive, w);
       cnt += alive ? 1u : 0u;
@@ -777,6 +822,7 @@ __device__ inline void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uin
       const uint32_t e = (uint32_t)P.eid[a];
       const uint32_t u = (uint32_t)P.col[a];
       if (e >= (uint64_t)P.m || u >= n) { err = kErrInput; continue; }
+      if (hop && (hop[v] > P.hop_radius || hop[u] > P.hop_radius)) continue;
       bool alive; uint32_t w;
       edge_draw(P, r, e, alive, w);
       if (!alive) continue;
@@ -944,8 +990,9 @@ __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const 
       if (comp[v] != v || !comp_valid(cinfo[v], P.k_min)) continue;
       const uint32_t ties = rank[v] - 1u;
       if (ties < 2u) continue;
-      const uint4 u = philox4x32_10(make_uint4(v, P.r_begin + r_local, P.graph_tag, 3u),
-                                    P.key_lo, P.key_hi);
+      uint32_t anchor_unused;
+      const uint4 u = philox4x32_10(make_uint4(v, item_rho(P, r_local, anchor_unused),
+                                               P.graph_tag, 3u), P.key_lo, P.key_hi);
       uint32_t k = (uint32_t)(((uint64_t)u.x * (uint64_t)ties) >> 32);
       const double bstar = __longlong_as_double((long long)best[v]);
       for (uint32_t w = v; w < n && k > 0u; ++w) {
@@ -997,11 +1044,16 @@ __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const 
   if (gap_test && ctl->need_recheck) return true;
   uint32_t *counts = P.counts;
   const size_t stride = (size_t)n + 1;
+  uint32_t anchor;
+  item_rho(P, r_local, anchor);
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    if (anchor != 0xFFFFFFFFu && i != anchor) continue;   // row-wise mode: the anchor's row only
     const uint32_t root = comp[i];
     uint32_t col = n;
-    if (comp_valid(cinfo[root], P.k_min)) {
-      const uint32_t c = centre[root];
+    const uint32_t info = cinfo[root];
+    if ((info & kSizeMask) >= P.k_min) {
+      // a component without a candidate of W has no centre (and no betweenness was computed)
+      const uint32_t c = (info & kHasCand) ? centre[root] : 0xFFFFFFFFu;
       if (c < n && (P.top_k == 0 || rank[root] <= P.top_k)) {
         col = c;
       } else if (P.fb_node < n) {   // Sel_{W,fb} (Sec. 7.3): valid but infeasible -> v_fb

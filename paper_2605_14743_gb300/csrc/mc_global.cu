@@ -39,9 +39,14 @@ big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uin
     ctl->err = 0; ctl->wmax = 1; ctl->edges = 0; ctl->verts = 0; ctl->nsrc = 0;
   }
   __syncthreads();
-  realize_csr(P, P.r_begin + r_local, G.rp, G.arc, ctl);
+  uint32_t anchor;
+  const uint32_t rho = item_rho(P, r_local, anchor);
+  const bool ball = P.per_row && P.hop_radius;
+  if (ball) hop_ball(P, anchor, G.cinfo);   // cinfo is free until the components
+  realize_csr(P, rho, G.rp, G.arc, ctl, ball ? G.cinfo : nullptr);
   Realized H{n, G.rp, G.arc};
   components(P, H, G.comp, G.cinfo);
+  if (P.per_row) keep_anchor_component(n, anchor, G.comp, G.cinfo);
   bucket_setup(ctl, P.delta);
   uint32_t *cedges = G.centre;   // scratch until selection
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {

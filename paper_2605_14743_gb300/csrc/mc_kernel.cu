@@ -42,7 +42,8 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     const uint32_t spt_g = P.spt ? P.spt : spt;
     const uint32_t nslots = NT * spt_g;
     const uint32_t r_local = (uint32_t)(item - item_prefix[g]);
-    const uint32_t r = P.r_begin + r_local;
+    uint32_t anchor;
+    const uint32_t r = item_rho(P, r_local, anchor);
     const uint32_t n = P.n;
     Layout L;
     L.make(n, (uint32_t)(2 * P.m), nslots);
@@ -60,9 +61,12 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     }
     __syncthreads();
 
-    realize_csr(P, r, rp, arc, ctl);
+    const bool ball = P.per_row && P.hop_radius;
+    if (ball) hop_ball(P, anchor, cinfo);   // cinfo is free until the components
+    realize_csr(P, r, rp, arc, ctl, ball ? cinfo : nullptr);
     Realized H{n, rp, arc};
     components(P, H, comp, cinfo);
+    if (P.per_row) keep_anchor_component(n, anchor, comp, cinfo);
     bucket_setup(ctl, P.delta);
     const uint32_t dsh = ctl->dsh;
     const SlotSpace sp = smem_slots(smem, L, n);

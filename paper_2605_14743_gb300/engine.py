@@ -121,7 +121,7 @@ class Query:
     def __init__(self, wl, device="cuda", bucket_width=0, block_threads=0, team_threads=0,
                  slots_per_team=0, stream=None, memory_path=0, reward_k=0, reward_gamma=None,
                  reward_pool=None, report_rank=0, fallback_node=None, tie_random=False,
-                 length_table=None):
+                 length_table=None, per_row=False, hop_radius=0):
         torch = _torch()
         self.torch = torch
         self.wl = wl
@@ -160,6 +160,8 @@ class Query:
                                  memory_path, reward_k, self.gamma, self.pool, self.psi,
                                  report_rank)
         self.prob.tie_random = 1 if tie_random else 0
+        self.prob.per_row = 1 if per_row else 0     # independent draws per row (Alg. 2)
+        self.prob.hop_radius = int(hop_radius)      # r-hop neighbourhoods (row-wise mode)
         # discrete length law: host tables (ptr, thresholds), e.g. afc_weight_table_normal's
         self.wtab = None
         if length_table is not None:

@@ -48,6 +48,20 @@ def test_fallback_counts_exact_small_er(path, inside):
     assert (counts == oc).all() and (fb == ofb).all()
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_fallback_for_components_without_candidates(path):
+    """The crossroads' lone triangle C holds no candidate of W = {0, 4}: large enough, so its
+    anchors go to v_fb rather than absorbing."""
+    from afc_inputs import Workload, crossroads_edges
+    eu, ev, p = crossroads_edges()
+    wl = Workload("crossroads", 10, eu, ev, p, 1, 1, 300, seed=7, k_min=3, alpha=0.1, top_k=2,
+                  candidates=np.array([0, 4], np.int32))
+    oc, ofb, _ = _oracle(wl, 0, 300, 8)
+    _, counts, fb = _gpu(wl, 0, 300, 8, memory_path=path)
+    assert ofb[7] > 0 and oc[7, 10] == 0
+    assert (counts == oc).all() and (fb == ofb).all()
+
+
 def test_fallback_fp32_recheck_exact():
     for wl in mixed_batch(count=4, n_lo=150, n_hi=300, r_lo=8, r_hi=12):
         wl.candidates = np.arange(0, wl.n, 5, dtype=np.int32)
