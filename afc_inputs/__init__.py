@@ -57,6 +57,22 @@ def er_edges(n: int, p: float, seed: int) -> tuple[np.ndarray, np.ndarray]:
     return (keys // n).astype(np.int32), (keys % n).astype(np.int32)
 
 
+def connected_edges(n: int, m: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """A connected simple graph with n nodes and m edges: a uniformly random labelled tree
+    (random attachment order) plus m - (n - 1) further pairs drawn uniformly without repeats."""
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(n)
+    edges = set()
+    for k in range(1, n):
+        a, b = int(order[k]), int(order[rng.integers(0, k)])
+        edges.add((min(a, b), max(a, b)))
+    while len(edges) < m:
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        edges.add((min(a, b), max(a, b)))
+    e = np.array(sorted(edges), np.int32)
+    return e[:, 0].copy(), e[:, 1].copy()
+
+
 def ws_edges(n: int, k: int, beta: float, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """Watts-Strogatz graph: ring lattice with k/2 neighbours per side, each lattice edge
     (i, i+j) rewired with probability beta to (i, u) for a uniformly drawn u that is neither
@@ -209,6 +225,16 @@ def workload(name: str) -> Workload:
     if name == "ws20000":
         eu, ev = ws_edges(20000, 10, 0.05, 104)
         return Workload(name, 20000, eu, ev, 0.9, 1, 1000, 2048, seed=1, n_perturb=10_000)
+    if name == "weighted77":
+        # stand-in for the paper's weighted co-occurrence network (77 nodes, 254 edges, base
+        # lengths in [1, 31]; the data set is not available): a connected 77-node graph with 254
+        # edges (a random spanning tree plus random extra pairs), base lengths uniform on
+        # {1..31}, every edge always present; lengths redrawn per step from the rounded and
+        # clipped normal law (rho_mu 0.2, rho_sigma 0.1) and betweenness on 2-hop
+        # neighbourhoods with independent draws per row (M = 60)
+        eu, ev = connected_edges(77, 254, 107)
+        w0 = np.random.default_rng(207).integers(1, 32, size=len(eu)).astype(np.uint32)
+        return Workload(name, 77, eu, ev, 1.0, w0, 31, 60, seed=1)
     if name == "paper_er100":
         eu, ev = er_edges(100, 0.08, 105)
         return Workload(name, 100, eu, ev, 0.85, 1, 1, 60, seed=1)

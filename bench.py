@@ -607,6 +607,57 @@ def run_robust(args):
     return 0
 
 
+def run_weighted(args):
+    """The weighted-network pipeline of the paper's last experiment (Sec. 9) on a 77-node
+    stand-in: lengths redrawn per step from the rounded and clipped normal law, betweenness on
+    2-hop neighbourhoods, M = 60 independent draws per row; then the AFC, the sampled robust
+    search (100 multiplicative kernels) and the 3-clique constrained kernel with fallback."""
+    import time as _time
+    import numpy as np
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import workload
+    torch.cuda.set_device(0)
+    wl = workload("weighted77")
+    M = int(wl.realizations)
+    law = afc.afc_weight_table_normal(wl.w_lo, wl.w_hi, 0.2, 0.1)
+    q = afc.Query(wl, per_row=True, hop_radius=2, length_table=law)
+    q.run_counts(0, 4)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    q.run_counts(0, M)
+    e1.record(stream)
+    q.run_solve()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b = q.b.cpu().numpy()
+    top = lambda v: [int(x) for x in np.argsort(-v, kind="stable")[:5]]
+    t0 = _time.perf_counter()
+    rob = q.robust_search(samples=100, rel_radius=0.5, r_min=0.05, seed=1)
+    t_rob = _time.perf_counter() - t0
+    mask, v_fb, _ = afc.afc_clique_pool(wl.n, wl.eu, wl.ev, 8)
+    wl_c = workload("weighted77")
+    wl_c.candidates = np.flatnonzero(mask).astype(np.int32)
+    wl_c.top_k = 5
+    qc = afc.Query(wl_c, per_row=True, hop_radius=2, length_table=law, fallback_node=v_fb)
+    qc.run_counts(0, M)
+    qc.run_solve()
+    m_w, _, _, _ = qc.pool_summaries()
+    st = q.stats.cpu().numpy()
+    line = {"config": {"workload": "weighted77 stand-in (77 nodes, 254 edges, base lengths "
+                                   "{1..31}, rounded-clipped normal law rho_mu 0.2 rho_sigma "
+                                   "0.1, 2-hop neighbourhoods, M = 60 draws per row)"},
+            "metric": "row draws/s", "value": M * wl.n / (ms / 1e3), "counts_ms": ms,
+            "items": int(st[0]), "c": q.c, "top5": top(b), "expected_T": float(q.scalars[0]),
+            "robust_top5_kl": top(rob["b_kl"]), "robust_top5_w1": top(rob["b_w1"]),
+            "robust_s": t_rob, "clique_top5": top(qc.b.cpu().numpy()), "clique_m_W": m_w,
+            "fallback_node": v_fb, "device_error": int(st[5])}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     """The serving stream through the native serving loop: a closed batch of its first queries
     measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
@@ -672,7 +723,7 @@ def main():
                     help="counting path of --counts-only")
     ap.add_argument("--config", default="ws1000",
                     choices=["ws1000", "mix", "ws20000", "serving", "constrained", "bootstrap",
-                             "robust"],
+                             "robust", "weighted"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
@@ -694,6 +745,8 @@ def main():
         return run_bootstrap(args)
     if args.config == "robust":
         return run_robust(args)
+    if args.config == "weighted":
+        return run_weighted(args)
     if args.config == "serving":
         return run_serving(args)
     if args.counts_only:

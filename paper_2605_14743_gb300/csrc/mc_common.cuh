@@ -739,10 +739,17 @@ __device__ __forceinline__ void edge_draw(const McDev &P, uint32_t r, uint32_t e
   const uint32_t lo = P.w_lo ? P.w_lo[e] : P.w_lo_all;
   const uint32_t hi = P.w_hi ? P.w_hi[e] : P.w_hi_all;
   alive = (uint64_t)u.x < T;
-  if (P.wtab_ptr) {   // discrete law: lo + #{thresholds <= u}, capped at hi
-    uint32_t k = 0;
-    for (uint32_t t = P.wtab_ptr[e]; t < P.wtab_ptr[e + 1]; ++t) k += P.wtab[t] <= u.y ? 1u : 0u;
-    w = min(lo + k, hi);
+  if (P.wtab_ptr) {
+    // discrete law: lo + #{thresholds <= u}, capped at hi; the thresholds are non-decreasing,
+    // so the count is the upper-bound position (a binary search: its short loop also keeps
+    // the counting kernel's register allocation lower than a linear count does)
+    uint32_t a = P.wtab_ptr[e], b = P.wtab_ptr[e + 1];
+    const uint32_t a0 = a;
+    while (a < b) {
+      const uint32_t mid = (a + b) >> 1;
+      if (P.wtab[mid] <= u.y) a = mid + 1; else b = mid;
+    }
+    w = min(lo + (a - a0), hi);
   } else {
     w = lo + (uint32_t)(((uint64_t)u.y * ((uint64_t)hi - lo + 1u)) >> 32);
   }
