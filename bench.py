@@ -658,6 +658,56 @@ def run_weighted(args):
     return 0
 
 
+def run_perturb_large(args):
+    """The perturbation sweep at the 20,000-node workload's size (c = 1,251 observed states,
+    rows of ~100-400 entries, R = 2048) on synthetic counts of that shape: a popularity-skewed
+    support per row, multinomial counts, about 10% absorption.  Times the sweep of
+    --perturb-count perturbations (l1 radius 0.05, r_min 0.05)."""
+    import numpy as np
+    import torch
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import Workload
+    torch.cuda.set_device(0)
+    n, c, R = 20000, 1251, 2048
+    rng = np.random.default_rng(2048)
+    C = rng.choice(n, c, replace=False)
+    pop = 1.0 / np.arange(1, c + 1) ** 0.8
+    pop /= pop.sum()
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        k = int(rng.integers(100, 401))
+        cols = rng.choice(c, k, replace=False, p=pop)
+        d = rng.multinomial(R, np.append(rng.dirichlet(np.ones(k)) * 0.9, 0.1))
+        counts[i, C[cols]] = d[:-1].astype(np.uint32)
+        counts[i, n] = d[-1]
+    eu = np.arange(n - 1, dtype=np.int32)
+    wl = Workload("perturb_large", n, eu, eu + 1, 1.0, 1, 1, R, seed=1,
+                  n_perturb=args.perturb_count)
+    q = afc.Query(wl)
+    q.counts.copy_(torch.from_numpy(counts.view(np.int32)).cuda())
+    del counts
+    q.run_solve()
+    q.run_perturb(0, 16)                          # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    q.run_perturb(0, args.perturb_count)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lu_flop = 2.0 / 3.0 * q.c ** 3
+    line = {"config": {"workload": "synthetic chain of the 20,000-node workload's shape: n "
+                                   "20000, c %d, rows of 100-400 entries, R 2048; %d l1 "
+                                   "perturbations" % (q.c, args.perturb_count)},
+            "metric": "perturbations/s", "value": args.perturb_count / (ms / 1e3), "ms": ms,
+            "c": q.c, "lu_fp64_tflops": lu_flop * args.perturb_count / (ms / 1e3) / 1e12,
+            "extrapolated_10000_s": 10000 * ms / args.perturb_count / 1e3,
+            "counters": q.p_counters.cpu().numpy().tolist()}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serving(args):
     """The serving stream through the native serving loop: a closed batch of its first queries
     measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
@@ -723,13 +773,14 @@ def main():
                     help="counting path of --counts-only")
     ap.add_argument("--config", default="ws1000",
                     choices=["ws1000", "mix", "ws20000", "serving", "constrained", "bootstrap",
-                             "robust", "weighted"],
+                             "robust", "weighted", "perturb-large"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
     ap.add_argument("--ws20000-sample", type=int, default=16)
     ap.add_argument("--constrained-realizations", type=int, default=10_000)
     ap.add_argument("--bootstrap-replicates", type=int, default=200)
+    ap.add_argument("--perturb-count", type=int, default=1000)
     ap.add_argument("--serve-probe", type=int, default=6)
     ap.add_argument("--serve-queries", type=int, default=12,
                     help="Poisson arrivals in the rate-scaled serving run")
@@ -747,6 +798,8 @@ def main():
         return run_robust(args)
     if args.config == "weighted":
         return run_weighted(args)
+    if args.config == "perturb-large":
+        return run_perturb_large(args)
     if args.config == "serving":
         return run_serving(args)
     if args.counts_only:

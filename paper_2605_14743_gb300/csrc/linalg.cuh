@@ -83,6 +83,103 @@ __device__ inline bool lu_factor(double *A, int32_t c, int32_t lda, int32_t *piv
   return true;
 }
 
+// Blocked right-looking form of lu_factor for matrices in device memory (same factors, same
+// pivot rule, same piv format): a panel of kLuB columns is factored with full-row swaps and
+// rank-1 updates inside the panel, then U12 = L11^-1 A12 by forward substitution (a column
+// per thread), then the trailing matrix takes A22 -= L21 U12 in 64 x 64 tiles staged through
+// shared memory (each thread a 4 x 4 register tile).  The trailing matrix is read and written
+// once per panel instead of once per column, which is what bounds lu_factor on large c.
+// Needs blockDim.x == 256 and lu_blocked_smem_doubles() doubles of shared memory at tile.
+constexpr int kLuB = 32;
+constexpr int kLuT = 64;
+__host__ __device__ constexpr int lu_blocked_smem_doubles() { return kLuT * (kLuB + 1) + kLuB * (kLuT + 1); }
+
+__device__ inline bool lu_factor_blocked(double *A, int32_t c, int32_t lda, int32_t *piv,
+                                         LinScratch s, double *tile) {
+  const uint32_t tid = threadIdx.x;
+  double *Lt = tile;                          // [kLuT][kLuB + 1]
+  double *Ut = tile + kLuT * (kLuB + 1);      // [kLuB][kLuT + 1]
+  for (int32_t kb = 0; kb < c; kb += kLuB) {
+    const int32_t nb = min(kLuB, c - kb), ke = kb + nb;
+    // (1) panel: columns kb .. ke-1, rows kb .. c-1
+    for (int32_t k = kb; k < ke; ++k) {
+      const int32_t p = pivot_search(A, c, lda, k, s);
+      if (p < 0) return false;
+      if (tid == 0) piv[k] = p;
+      if (p != k) {
+        for (int32_t j = tid; j < c; j += blockDim.x) {
+          const double t = A[(size_t)k * lda + j];
+          A[(size_t)k * lda + j] = A[(size_t)p * lda + j];
+          A[(size_t)p * lda + j] = t;
+        }
+        __syncthreads();
+      }
+      const double inv = 1.0 / A[(size_t)k * lda + k];
+      for (int32_t i = k + 1 + tid; i < c; i += blockDim.x) A[(size_t)i * lda + k] *= inv;
+      __syncthreads();
+      const int32_t w = ke - (k + 1);         // panel columns right of k
+      if (w > 0) {
+        const int64_t tot = (int64_t)(c - (k + 1)) * w;
+        for (int64_t q = tid; q < tot; q += blockDim.x) {
+          const int32_t i = k + 1 + (int32_t)(q / w), j = k + 1 + (int32_t)(q % w);
+          A[(size_t)i * lda + j] = fma(-A[(size_t)i * lda + k], A[(size_t)k * lda + j], A[(size_t)i * lda + j]);
+        }
+      }
+      __syncthreads();
+    }
+    if (ke >= c) break;
+    // (2) U12 = L11^-1 A12 (L11 unit lower), a column per thread
+    for (int32_t j = ke + tid; j < c; j += blockDim.x)
+      for (int32_t r = 1; r < nb; ++r) {
+        double acc = A[(size_t)(kb + r) * lda + j];
+        for (int32_t t = 0; t < r; ++t)
+          acc = fma(-A[(size_t)(kb + r) * lda + kb + t], A[(size_t)(kb + t) * lda + j], acc);
+        A[(size_t)(kb + r) * lda + j] = acc;
+      }
+    __syncthreads();
+    // (3) A22 -= L21 U12 in kLuT x kLuT tiles
+    const uint32_t ty = tid / 16u, tx = tid % 16u;
+    for (int32_t i0 = ke; i0 < c; i0 += kLuT)
+      for (int32_t j0 = ke; j0 < c; j0 += kLuT) {
+        for (uint32_t q = tid; q < (uint32_t)(kLuT * kLuB); q += blockDim.x) {
+          const int32_t r = (int32_t)(q / kLuB), t = (int32_t)(q % kLuB);
+          Lt[r * (kLuB + 1) + t] = (i0 + r < c && t < nb) ? A[(size_t)(i0 + r) * lda + kb + t] : 0.0;
+          const int32_t t2 = (int32_t)(q / kLuT), col = (int32_t)(q % kLuT);
+          Ut[t2 * (kLuT + 1) + col] = (j0 + col < c && t2 < nb) ? A[(size_t)(kb + t2) * lda + j0 + col] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int32_t t = 0; t < nb; ++t) {
+          double l[4], u[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) l[a] = Lt[(ty * 4 + a) * (kLuB + 1) + t];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) u[b] = Ut[t * (kLuT + 1) + tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(l[a], u[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int32_t i = i0 + (int32_t)ty * 4 + a;
+          if (i >= c) continue;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int32_t j = j0 + (int32_t)tx * 4 + b;
+            if (j < c) A[(size_t)i * lda + j] -= acc[a][b];
+          }
+        }
+        __syncthreads();
+      }
+  }
+  return true;
+}
+
 // Solves A x = b in place (b -> x) with the factors of lu_factor.
 __device__ inline void lu_solve(const double *LU, int32_t c, int32_t lda, const int32_t *piv, double *b,
                          LinScratch s) {

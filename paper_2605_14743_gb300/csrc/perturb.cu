@@ -347,7 +347,10 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
     // (3) factor, mu'_C, (N' 1)_C, first-order y_lin = x N0
     bool ok = true;
     if (c > 0) {
-      ok = lu_factor(ar.A, c, c, ar.piv, ls);
+      // A in shared memory: the column-by-column LU; in the device slab (large c): the
+      // blocked LU, whose trailing updates go through shared-memory tiles
+      ok = use_smem ? lu_factor(ar.A, c, c, ar.piv, ls)
+                    : lu_factor_blocked(ar.A, c, c, ar.piv, ls, reinterpret_cast<double *>(smem));
       if (ok) {
         lu_solve_transposed(ar.A, c, c, ar.piv, ar.y, ls);
         for (int32_t k = threadIdx.x; k < c; k += blockDim.x) ar.t[k] = 1.0;
@@ -496,7 +499,9 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   const int use_smem = (int)smem + 16 * 1024 <= max_optin ? 1 : 0;
   const uint32_t priv = 2u * (kPerturbThreads / 32) * (uint32_t)(c > 0 ? c : 1) * 8u;
   const int use_priv = (use_smem && (int)(smem + priv) + 16 * 1024 <= max_optin) ? 1 : 0;
-  const uint32_t dyn = use_smem ? smem + (use_priv ? priv : 0u) : 0u;
+  // the slab path takes the blocked LU's tiles as dynamic shared memory
+  const uint32_t dyn = use_smem ? smem + (use_priv ? priv : 0u)
+                                : (uint32_t)(sizeof(double) * lu_blocked_smem_doubles());
   const size_t nnz_bytes = L.nnz_cap * 8;
   const size_t slab_bytes = ((use_smem ? 0 : arena_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
   const size_t avail = L.total - L.off_slab;
@@ -505,8 +510,9 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   if (fit > (size_t)pp.p_count) fit = (size_t)pp.p_count;
   const int grid = (int)fit;
   if (grid <= 0) return cudaErrorMemoryAllocation;
-  if (use_smem)
-    cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  // set on every launch: the attribute is the kernel's limit, and an earlier launch may have
+  // left it below what this one needs
+  cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   perturb_kernel<<<grid, kPerturbThreads, dyn, stream>>>(
       C, pp, mu0, b0, lu0, piv0, nzptr, nzcol, nzval, byrank0, counters, pair_flips, shift_hist,
       maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, use_priv, status_dev);
