@@ -598,7 +598,12 @@ def run_robust(args):
         wall = _time.perf_counter() - t0
         b = q.b.cpu().numpy()
         top = lambda v: [int(x) for x in np.argsort(-v, kind="stable")[:5]]
+        t0 = _time.perf_counter()
+        rv = q.robust_value(eps=0.05, r_min=0.05, support_only=False, sense=+1)
+        t_rv = _time.perf_counter() - t0
         out["runs"][name] = {"seconds": wall, "samples_per_s": 100 / wall, "c": q.c,
+                             "robust_value_s": t_rv, "robust_value_rounds": rv["iterations"],
+                             "robust_max_expected_T": rv["expected_T"],
                              "top5_nominal": top(b), "top5_kl": top(res["b_kl"]),
                              "top5_w1": top(res["b_w1"]), "kl_max": res["kl_max"],
                              "w1_max": res["w1_max"]}

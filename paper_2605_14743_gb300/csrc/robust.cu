@@ -7,7 +7,7 @@
 //                        solves the LP exactly: every entry starts at its lower bound, then the
 //                        budget goes to the entries in ascending order of v_j - v_bot (ties by
 //                        j) while that coefficient is negative, each up to its upper bound.
-//   eval_kernel          one CTA: A = I - Q*, V = A^-1 f (FP64 LU with partial pivoting) and
+//   eval_kernel          one CTA: A = I - Q*, V = A^-1 f (blocked FP64 LU with partial pivoting) and
 //                        the change of V; the robust value comes from policy iteration on the
 //                        host (inner problem at V, evaluate, until V stops changing)
 //   star_kernel          the AFC of the scenario kernel: A^T mu = s with the last factors
@@ -130,17 +130,19 @@ __global__ void build_a_kernel(int32_t n, const double *Qstar, double *A) {
     A[k] = ((k / n) == (k % n) ? 1.0 : 0.0) - Qstar[k];
 }
 
-// One CTA: factor A, V_new = A^-1 f (f = 1 when null), diff = max |V_new - V|, V <- V_new.
-__global__ void __launch_bounds__(1024, 1)
+// One CTA of 256 threads: factor A (the blocked LU: the matrix is in device memory), V_new =
+// A^-1 f (f = 1 when null), diff = max |V_new - V|, V <- V_new.
+__global__ void __launch_bounds__(256, 1)
 eval_kernel(int32_t n, double *A, int32_t *piv, const double *f, double *V, double *x,
             double *diff, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sval[33];
   __shared__ int32_t sidx[32];
   __shared__ double sb[2];
   __shared__ int32_t sflag[1];
   __shared__ double red[33];
   LinScratch ls{sval, sidx, sb, sflag};
-  if (!lu_factor(A, n, n, piv, ls)) {
+  if (!lu_factor_blocked(A, n, n, piv, ls, reinterpret_cast<double *>(smem))) {
     if (threadIdx.x == 0) { atomicOr(status, kErrSolve); *diff = 0.0; }
     return;
   }
@@ -200,7 +202,8 @@ cudaError_t launch_robust_eval(int32_t n, const double *Qstar, double *A, int32_
                                uint32_t *status, cudaStream_t stream) {
   const int grid = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 4096);
   build_a_kernel<<<grid, 256, 0, stream>>>(n, Qstar, A);
-  eval_kernel<<<1, 1024, 0, stream>>>(n, A, piv, f, V, x, diff, status);
+  eval_kernel<<<1, 256, sizeof(double) * lu_blocked_smem_doubles(), stream>>>(n, A, piv, f, V, x,
+                                                                              diff, status);
   return cudaGetLastError();
 }
 
