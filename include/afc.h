@@ -350,7 +350,8 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
  * discrepancy of the paper's robust search (Sec. 9): out[k] = W1(x_k, y) for the `count` HOST
  * rows x_k = x + k n (each summing to sum y), over the HOST edge lists eu, ev (as
  * afc_csr_from_edges).  Exact (successive shortest paths on the graph; masses settled to a
- * relative 1e-14).  Host code.  Errors: AFC_EINVAL for bad edges. */
+ * relative 1e-14).  Host code; the rows run on parallel host threads.  Errors: AFC_EINVAL for
+ * bad edges. */
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out);
 

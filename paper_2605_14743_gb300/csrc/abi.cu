@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -1071,8 +1072,15 @@ int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, con
       eid((size_t)std::max<int64_t>(2 * m, 1));
   int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
   if (st) return st;
-  for (int32_t k = 0; k < count; ++k)
-    out[k] = w1_graph_host(n, rp.data(), col.data(), eid.data(), x + (size_t)k * n, y);
+  // rows are independent: spread them over the host's cores
+  const int32_t nth = std::max(1, std::min<int32_t>(count, (int32_t)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int32_t t = 0; t < nth; ++t)
+    pool.emplace_back([&, t] {
+      for (int32_t k = t; k < count; k += nth)
+        out[k] = w1_graph_host(n, rp.data(), col.data(), eid.data(), x + (size_t)k * n, y);
+    });
+  for (auto &th : pool) th.join();
   return AFC_OK;
 }
 

@@ -10,7 +10,8 @@
 //   (3) the reduced system of the solve: A = I - Q_CC, y = s_C + s_U Q_UC with the same row
 //       scale rule as the kernel assembly (exact integer counts, then one scale per row; the
 //       U-row sums run per column in ascending row order, so the result is deterministic)
-//   (4) FP64 LU with partial pivoting, A^T mu_C = y, E[T] and b for every node
+//   (4) FP64 LU with partial pivoting (blocked when the matrix is in the device slab),
+//       A^T mu_C = y, E[T] and b for every node
 // A second kernel takes, per node, the replicates at the two sorted positions of the
 // percentile interval (rank by value, ties by replicate index).
 #include <algorithm>
@@ -128,7 +129,10 @@ bootstrap_kernel(ChainDev C, const int32_t *__restrict__ rec, uint32_t R, uint32
     // (4) solve, E[T], b
     bool ok = true;
     if (c > 0) {
-      ok = lu_factor(A, c, c, piv, ls);
+      // on chip: the column-by-column LU; in the device slab: the blocked LU, its tiles in
+      // the dynamic shared memory the matrix does not use
+      ok = a_in_smem ? lu_factor(A, c, c, piv, ls)
+                     : lu_factor_blocked(A, c, c, piv, ls, reinterpret_cast<double *>(smem));
       if (ok) lu_solve_transposed(A, c, c, piv, y, ls);
     }
     if (!ok) {
@@ -192,9 +196,9 @@ cudaError_t launch_bootstrap(const ChainDev &C, const int32_t *rec, uint32_t R, 
   size_t grid = slab_space / std::max<size_t>(slab, 1);
   grid = std::min<size_t>({grid, (size_t)B, (size_t)num_sms * kBootCtasPerSm});
   if (grid == 0) return cudaErrorMemoryAllocation;
-  const uint32_t dyn = a_smem ? (uint32_t)a_bytes : 0u;
-  if (dyn > 48u * 1024u)
-    cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+  const uint32_t dyn = a_smem ? (uint32_t)a_bytes
+                              : (uint32_t)(sizeof(double) * lu_blocked_smem_doubles());
+  cudaFuncSetAttribute(bootstrap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   bootstrap_kernel<<<(unsigned)grid, kBootThreads, dyn, stream>>>(
       C, rec, R, B, (uint32_t)seed, (uint32_t)(seed >> 32), slabs, slab, a_smem ? 1 : 0, b_rep,
       T_rep, status);
