@@ -96,6 +96,7 @@ __host__ __device__ constexpr int lu_blocked_smem_doubles() { return kLuT * (kLu
 
 __device__ inline bool lu_factor_blocked(double *A, int32_t c, int32_t lda, int32_t *piv,
                                          LinScratch s, double *tile) {
+  if (blockDim.x != 256u) return lu_factor(A, c, lda, piv, s);   // the tile mapping needs 256
   const uint32_t tid = threadIdx.x;
   double *Lt = tile;                          // [kLuT][kLuB + 1]
   double *Ut = tile + kLuT * (kLuB + 1);      // [kLuB][kLuT + 1]
