@@ -387,8 +387,11 @@ class Query:
         kl = kl.cpu().numpy()
         w1 = afc_w1_graph(self.n, self.wl.eu, self.wl.ev, bs, b0)
         k_kl, k_w1 = int(np.argmax(kl)), int(np.argmax(w1))
+        # sampled envelopes of each b_v: the range over the sampled admissible kernels (and the
+        # nominal one), an inner approximation of inf / sup over the whole set
         return {"b_kl": bs[k_kl], "b_w1": bs[k_w1], "k_kl": k_kl, "k_w1": k_w1,
                 "kl_max": float(kl[k_kl]), "w1_max": float(w1[k_w1]), "kl": kl, "w1": w1,
+                "b_low": np.minimum(bs.min(axis=0), b0), "b_high": np.maximum(bs.max(axis=0), b0),
                 "counters": cnt.cpu().numpy()}
 
     def step(self, perturb=True):

@@ -37,6 +37,10 @@ def test_robust_search_maximisers(name, R):
         assert res[key] == int(np.argmax(vals))
     assert close(res["b_kl"], ref.b[int(np.argmax(ref.kl))])
     assert close(res["b_w1"], ref.b[int(np.argmax(w1))])
+    # sampled envelopes: per node the range over the samples and the nominal AFC
+    assert close(res["b_low"], np.minimum(ref.b.min(axis=0), b0))
+    assert close(res["b_high"], np.maximum(ref.b.max(axis=0), b0))
+    assert np.all(res["b_low"] <= res["b_high"])
 
 
 def test_rank_stability_m_and_2m():
