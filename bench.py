@@ -673,7 +673,7 @@ def run_perturb_large(args):
     import paper_2605_14743_gb300 as afc
     from afc_inputs import Workload
     torch.cuda.set_device(0)
-    n, c, R = 20000, 1251, 2048
+    n, c, R = args.perturb_n, 1251, 2048
     rng = np.random.default_rng(2048)
     C = rng.choice(n, c, replace=False)
     pop = 1.0 / np.arange(1, c + 1) ** 0.8
@@ -703,8 +703,8 @@ def run_perturb_large(args):
     ms = e0.elapsed_time(e1)
     lu_flop = 2.0 / 3.0 * q.c ** 3
     line = {"config": {"workload": "synthetic chain of the 20,000-node workload's shape: n "
-                                   "20000, c %d, rows of 100-400 entries, R 2048; %d l1 "
-                                   "perturbations" % (q.c, args.perturb_count)},
+                                   "%d, c %d, rows of 100-400 entries, R 2048; %d l1 "
+                                   "perturbations" % (n, q.c, args.perturb_count)},
             "metric": "perturbations/s", "value": args.perturb_count / (ms / 1e3), "ms": ms,
             "c": q.c, "lu_fp64_tflops": lu_flop * args.perturb_count / (ms / 1e3) / 1e12,
             "extrapolated_10000_s": 10000 * ms / args.perturb_count / 1e3,
@@ -786,6 +786,8 @@ def main():
     ap.add_argument("--constrained-realizations", type=int, default=10_000)
     ap.add_argument("--bootstrap-replicates", type=int, default=200)
     ap.add_argument("--perturb-count", type=int, default=1000)
+    ap.add_argument("--perturb-n", type=int, default=20000,
+                    help="nodes of the synthetic chain of --config perturb-large")
     ap.add_argument("--serve-probe", type=int, default=6)
     ap.add_argument("--serve-queries", type=int, default=12,
                     help="Poisson arrivals in the rate-scaled serving run")
