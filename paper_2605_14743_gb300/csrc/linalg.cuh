@@ -181,6 +181,193 @@ __device__ inline bool lu_factor_blocked(double *A, int32_t c, int32_t lda, int3
   return true;
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed precision: the same blocked factorisation on a copy of the matrix in another type
+// (FP32 here), and triangular solves that apply those factors to FP64 vectors, so that FP64
+// iterative refinement (residual with the FP64 matrix, correction with the FP32 factors)
+// reaches the FP64 solution.  Same pivot rule and piv format as lu_factor.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int32_t pivot_search_t(const T *A, int32_t c, int32_t lda, int32_t k,
+                                                  LinScratch s) {
+  double best = -1.0;
+  int32_t bi = k;
+  for (int32_t i = k + (int32_t)threadIdx.x; i < c; i += blockDim.x) {
+    const double a = fabs((double)A[(size_t)i * lda + k]);
+    if (a > best) { best = a; bi = i; }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_down_sync(0xFFFFFFFFu, best, o);
+    const int32_t oi = __shfl_down_sync(0xFFFFFFFFu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  if (lane == 0) { s.val[warp] = best; s.idx[warp] = bi; }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t nw = (blockDim.x + 31u) >> 5;
+    best = lane < nw ? s.val[lane] : -1.0;
+    bi = lane < nw ? s.idx[lane] : 0x7FFFFFFF;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xFFFFFFFFu, best, o);
+      const int32_t oi = __shfl_down_sync(0xFFFFFFFFu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s.idx[0] = bi; s.val[0] = best; }
+  }
+  __syncthreads();
+  const int32_t p = s.idx[0];
+  const double pv = s.val[0];
+  __syncthreads();
+  return pv > 0.0 ? p : -1;
+}
+
+template <typename T>
+__host__ __device__ constexpr int lu_blocked_smem_elems() { return kLuT * (kLuB + 1) + kLuB * (kLuT + 1); }
+
+// lu_factor_blocked on a matrix of T (256 threads; lu_blocked_smem_elems<T>() elements of T at
+// tile).
+template <typename T>
+__device__ inline bool lu_factor_blocked_t(T *A, int32_t c, int32_t lda, int32_t *piv,
+                                           LinScratch s, T *tile) {
+  const uint32_t tid = threadIdx.x;
+  if (blockDim.x != 256u) return false;
+  T *Lt = tile;
+  T *Ut = tile + kLuT * (kLuB + 1);
+  for (int32_t kb = 0; kb < c; kb += kLuB) {
+    const int32_t nb = min(kLuB, c - kb), ke = kb + nb;
+    for (int32_t k = kb; k < ke; ++k) {
+      const int32_t p = pivot_search_t(A, c, lda, k, s);
+      if (p < 0) return false;
+      if (tid == 0) piv[k] = p;
+      if (p != k) {
+        for (int32_t j = tid; j < c; j += blockDim.x) {
+          const T t = A[(size_t)k * lda + j];
+          A[(size_t)k * lda + j] = A[(size_t)p * lda + j];
+          A[(size_t)p * lda + j] = t;
+        }
+        __syncthreads();
+      }
+      const T inv = (T)1 / A[(size_t)k * lda + k];
+      for (int32_t i = k + 1 + tid; i < c; i += blockDim.x) A[(size_t)i * lda + k] *= inv;
+      __syncthreads();
+      const int32_t w = ke - (k + 1);
+      if (w > 0) {
+        const int64_t tot = (int64_t)(c - (k + 1)) * w;
+        for (int64_t q = tid; q < tot; q += blockDim.x) {
+          const int32_t i = k + 1 + (int32_t)(q / w), j = k + 1 + (int32_t)(q % w);
+          A[(size_t)i * lda + j] = fma(-A[(size_t)i * lda + k], A[(size_t)k * lda + j], A[(size_t)i * lda + j]);
+        }
+      }
+      __syncthreads();
+    }
+    if (ke >= c) break;
+    for (int32_t j = ke + tid; j < c; j += blockDim.x)
+      for (int32_t r = 1; r < nb; ++r) {
+        T acc = A[(size_t)(kb + r) * lda + j];
+        for (int32_t t = 0; t < r; ++t)
+          acc = fma(-A[(size_t)(kb + r) * lda + kb + t], A[(size_t)(kb + t) * lda + j], acc);
+        A[(size_t)(kb + r) * lda + j] = acc;
+      }
+    __syncthreads();
+    const uint32_t ty = tid / 16u, tx = tid % 16u;
+    for (int32_t i0 = ke; i0 < c; i0 += kLuT)
+      for (int32_t j0 = ke; j0 < c; j0 += kLuT) {
+        for (uint32_t q = tid; q < (uint32_t)(kLuT * kLuB); q += blockDim.x) {
+          const int32_t r = (int32_t)(q / kLuB), t = (int32_t)(q % kLuB);
+          Lt[r * (kLuB + 1) + t] = (i0 + r < c && t < nb) ? A[(size_t)(i0 + r) * lda + kb + t] : (T)0;
+          const int32_t t2 = (int32_t)(q / kLuT), col = (int32_t)(q % kLuT);
+          Ut[t2 * (kLuT + 1) + col] = (j0 + col < c && t2 < nb) ? A[(size_t)(kb + t2) * lda + j0 + col] : (T)0;
+        }
+        __syncthreads();
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+        for (int32_t t = 0; t < nb; ++t) {
+          T l[4], u[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) l[a] = Lt[(ty * 4 + a) * (kLuB + 1) + t];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) u[b] = Ut[t * (kLuT + 1) + tx * 4 + b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(l[a], u[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int32_t i = i0 + (int32_t)ty * 4 + a;
+          if (i >= c) continue;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int32_t j = j0 + (int32_t)tx * 4 + b;
+            if (j < c) A[(size_t)i * lda + j] -= acc[a][b];
+          }
+        }
+        __syncthreads();
+      }
+  }
+  return true;
+}
+
+// A x = b with factors of type F (lu_factor_blocked_t), b and x in FP64 (in place).
+template <typename F>
+__device__ inline void lu_solve_t(const F *LU, int32_t c, int32_t lda, const int32_t *piv,
+                                  double *b, LinScratch s) {
+  if (threadIdx.x == 0)
+    for (int32_t k = 0; k < c; ++k) {
+      const int32_t p = piv[k];
+      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+  __syncthreads();
+  for (int32_t k = 0; k < c; ++k) {
+    const double yk = b[k];
+    for (int32_t i = k + 1 + threadIdx.x; i < c; i += blockDim.x)
+      b[i] = fma(-(double)LU[(size_t)i * lda + k], yk, b[i]);
+    __syncthreads();
+  }
+  for (int32_t k = c - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) s.bcast[0] = b[k] / (double)LU[(size_t)k * lda + k];
+    __syncthreads();
+    const double xk = s.bcast[0];
+    for (int32_t i = threadIdx.x; i < k; i += blockDim.x)
+      b[i] = fma(-(double)LU[(size_t)i * lda + k], xk, b[i]);
+    if (threadIdx.x == 0) b[k] = xk;
+    __syncthreads();
+  }
+}
+
+// A^T x = b with factors of type F, FP64 vectors (in place).
+template <typename F>
+__device__ inline void lu_solve_transposed_t(const F *LU, int32_t c, int32_t lda,
+                                             const int32_t *piv, double *b, LinScratch s) {
+  for (int32_t k = 0; k < c; ++k) {
+    if (threadIdx.x == 0) s.bcast[0] = b[k] / (double)LU[(size_t)k * lda + k];
+    __syncthreads();
+    const double zk = s.bcast[0];
+    for (int32_t i = k + 1 + threadIdx.x; i < c; i += blockDim.x)
+      b[i] = fma(-(double)LU[(size_t)k * lda + i], zk, b[i]);
+    if (threadIdx.x == 0) b[k] = zk;
+    __syncthreads();
+  }
+  for (int32_t k = c - 1; k >= 0; --k) {
+    const double wk = b[k];
+    for (int32_t i = threadIdx.x; i < k; i += blockDim.x)
+      b[i] = fma(-(double)LU[(size_t)k * lda + i], wk, b[i]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int32_t k = c - 1; k >= 0; --k) {
+      const int32_t p = piv[k];
+      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+  __syncthreads();
+}
+
 // Solves A x = b in place (b -> x) with the factors of lu_factor.
 __device__ inline void lu_solve(const double *LU, int32_t c, int32_t lda, const int32_t *piv, double *b,
                          LinScratch s) {

@@ -39,6 +39,13 @@ __host__ __device__ inline size_t arena_bytes(int32_t c) {
   return (8 * cc * cc + 3 * 8 * cc + 4 * cc + 64 + 255) & ~size_t(255);
 }
 
+// Device-slab path (large c): after the arena, an FP32 copy of the matrix for the factors and
+// two FP64 vectors of refinement scratch.
+__host__ __device__ inline size_t mixed_bytes(int32_t c) {
+  const size_t cc = (size_t)(c > 0 ? c : 1);
+  return ((4 * cc * cc + 255) & ~size_t(255)) + 2 * ((8 * cc + 255) & ~size_t(255));
+}
+
 __device__ inline PerturbArena carve(unsigned char *base, int32_t c) {
   const size_t cc = (size_t)(c > 0 ? c : 1);
   PerturbArena a;
@@ -96,6 +103,45 @@ __device__ __forceinline__ long long warp_sum_ll(long long x) {
   return x;
 }
 
+// FP64 iterative refinement with FP32 factors: x <- x + F^-1 (b - op(A) x) until the update
+// is below 1e-15 of x (op(A) = A^T when TRANS); b = NULL means all ones.  Since every admissible
+// kernel has ||N||_inf <= 1 / r_min, I - Q' is well conditioned and each round gains about
+// seven digits.  Returns false when 12 rounds do not get there.
+template <bool TRANS>
+__device__ bool refine(const double *A, const float *Af, const int32_t *piv, int32_t c,
+                       const double *b, double *x, double *r, LinScratch ls, double *red) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = 0; it < 12; ++it) {
+    if (TRANS) {
+      for (int32_t j = threadIdx.x; j < c; j += blockDim.x) {
+        double acc = b ? b[j] : 1.0;
+        for (int32_t i = 0; i < c; ++i) acc = fma(-A[(size_t)i * c + j], x[i], acc);
+        r[j] = acc;
+      }
+    } else {
+      for (int32_t i = warp; i < c; i += nw) {
+        double acc = 0.0;
+        for (int32_t j = lane; j < c; j += 32) acc = fma(A[(size_t)i * c + j], x[j], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) r[i] = (b ? b[i] : 1.0) - acc;
+      }
+    }
+    __syncthreads();
+    if (TRANS) lu_solve_transposed_t(Af, c, c, piv, r, ls);
+    else lu_solve_t(Af, c, c, piv, r, ls);
+    double dm = 0.0, xm = 0.0;
+    for (int32_t k = threadIdx.x; k < c; k += blockDim.x) {
+      x[k] += r[k];
+      dm = fmax(dm, fabs(r[k]));
+      xm = fmax(xm, fabs(x[k]));
+    }
+    dm = block_max(dm, red);
+    xm = block_max(xm, red);
+    if (dm <= 1e-15 * xm) return true;
+  }
+  return false;
+}
+
 // Entries per lane a perturbed row keeps in registers (rows of up to 32 * kRowRegs entries).
 constexpr int kRowRegs = 4;
 
@@ -128,7 +174,12 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
   const int32_t H = min(pp.hist_bins, kMaxHist);
   unsigned char *slab = slabs + (size_t)blockIdx.x * slab_bytes;
   PerturbArena ar = carve(use_smem ? smem : slab, c);
-  double *qp = reinterpret_cast<double *>(slab + (use_smem ? 0 : arena_bytes(c)));
+  // device-slab path: [arena | FP32 copy of A | refinement vectors | perturbed rows]
+  unsigned char *mx = slab + arena_bytes(c);
+  float *af = reinterpret_cast<float *>(mx);
+  double *by = reinterpret_cast<double *>(mx + (((size_t)4 * c * c + 255) & ~size_t(255)));
+  double *rv = by + (((size_t)8 * c + 255) & ~size_t(255)) / 8;
+  double *qp = reinterpret_cast<double *>(slab + (use_smem ? 0 : arena_bytes(c) + mixed_bytes(c)));
   const uint32_t k0 = (uint32_t)pp.seed, k1 = (uint32_t)(pp.seed >> 32);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u, nw = blockDim.x >> 5;
   // warp-private column sums of the perturbed rows (shared memory, after the arena): a warp
@@ -346,19 +397,43 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
     }
     // (3) factor, mu'_C, (N' 1)_C, first-order y_lin = x N0
     bool ok = true;
-    if (c > 0) {
-      // A in shared memory: the column-by-column LU; in the device slab (large c): the
-      // blocked LU, whose trailing updates go through shared-memory tiles
-      ok = use_smem ? lu_factor(ar.A, c, c, ar.piv, ls)
-                    : lu_factor_blocked(ar.A, c, c, ar.piv, ls, reinterpret_cast<double *>(smem));
+    if (c > 0 && use_smem) {
+      // A in shared memory: the column-by-column FP64 LU
+      ok = lu_factor(ar.A, c, c, ar.piv, ls);
       if (ok) {
         lu_solve_transposed(ar.A, c, c, ar.piv, ar.y, ls);
         for (int32_t k = threadIdx.x; k < c; k += blockDim.x) ar.t[k] = 1.0;
         __syncthreads();
         lu_solve(ar.A, c, c, ar.piv, ar.t, ls);
-        lu_solve_transposed(lu0, c, c, piv0, ar.x, ls);
+      }
+    } else if (c > 0) {
+      // A in the device slab (large c): blocked LU of an FP32 copy (GB300's FP32 rate is many
+      // times its FP64 rate), then FP64 iterative refinement against the FP64 matrix; if the
+      // refinement stalls, the FP64 blocked LU of A itself
+      const size_t cc = (size_t)c * c;
+      for (size_t k = threadIdx.x; k < cc; k += blockDim.x) af[k] = (float)ar.A[k];
+      for (int32_t k = threadIdx.x; k < c; k += blockDim.x) { by[k] = ar.y[k]; ar.t[k] = 1.0; }
+      __syncthreads();
+      bool mixed = lu_factor_blocked_t<float>(af, c, c, ar.piv, ls, reinterpret_cast<float *>(smem));
+      if (mixed) {
+        lu_solve_transposed_t(af, c, c, ar.piv, ar.y, ls);
+        mixed = refine<true>(ar.A, af, ar.piv, c, by, ar.y, rv, ls, red);
+      }
+      if (mixed) {
+        lu_solve_t(af, c, c, ar.piv, ar.t, ls);
+        mixed = refine<false>(ar.A, af, ar.piv, c, nullptr, ar.t, rv, ls, red);
+      }
+      if (!mixed) {
+        for (int32_t k = threadIdx.x; k < c; k += blockDim.x) { ar.y[k] = by[k]; ar.t[k] = 1.0; }
+        __syncthreads();
+        ok = lu_factor_blocked(ar.A, c, c, ar.piv, ls, reinterpret_cast<double *>(smem));
+        if (ok) {
+          lu_solve_transposed(ar.A, c, c, ar.piv, ar.y, ls);
+          lu_solve(ar.A, c, c, ar.piv, ar.t, ls);
+        }
       }
     }
+    if (ok && c > 0) lu_solve_transposed(lu0, c, c, piv0, ar.x, ls);
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(status, kErrSolve);
       continue;
@@ -468,7 +543,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
 
 size_t perturb_slab_bytes(int32_t n, int32_t c) {
   (void)n;
-  return (arena_bytes(c) + 255) & ~size_t(255);
+  return (arena_bytes(c) + mixed_bytes(c) + 255) & ~size_t(255);
 }
 
 uint32_t perturb_smem_bytes(int32_t n, int32_t c) {
@@ -501,9 +576,10 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   const int use_priv = (use_smem && (int)(smem + priv) + 16 * 1024 <= max_optin) ? 1 : 0;
   // the slab path takes the blocked LU's tiles as dynamic shared memory
   const uint32_t dyn = use_smem ? smem + (use_priv ? priv : 0u)
-                                : (uint32_t)(sizeof(double) * lu_blocked_smem_doubles());
+                                : (uint32_t)(sizeof(double) * lu_blocked_smem_doubles());   // >= the FP32 tiles
   const size_t nnz_bytes = L.nnz_cap * 8;
-  const size_t slab_bytes = ((use_smem ? 0 : arena_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
+  const size_t slab_bytes =
+      ((use_smem ? 0 : arena_bytes(c) + mixed_bytes(c)) + nnz_bytes + 255) & ~size_t(255);
   const size_t avail = L.total - L.off_slab;
   size_t fit = avail / (slab_bytes ? slab_bytes : 1);
   if (fit > (size_t)num_sms * kPerturbCtasPerSm) fit = (size_t)num_sms * kPerturbCtasPerSm;
