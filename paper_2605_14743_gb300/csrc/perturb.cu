@@ -127,8 +127,8 @@ __device__ bool refine(const double *A, const float *Af, const int32_t *piv, int
       }
     }
     __syncthreads();
-    if (TRANS) lu_solve_transposed_t(Af, c, c, piv, r, ls);
-    else lu_solve_t(Af, c, c, piv, r, ls);
+    if (TRANS) lu_solve_transposed_blocked_t(Af, c, c, piv, r);
+    else lu_solve_blocked_t(Af, c, c, piv, r);
     double dm = 0.0, xm = 0.0;
     for (int32_t k = threadIdx.x; k < c; k += blockDim.x) {
       x[k] += r[k];
@@ -416,11 +416,11 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
       __syncthreads();
       bool mixed = lu_factor_blocked_t<float>(af, c, c, ar.piv, ls, reinterpret_cast<float *>(smem));
       if (mixed) {
-        lu_solve_transposed_t(af, c, c, ar.piv, ar.y, ls);
+        lu_solve_transposed_blocked_t(af, c, c, ar.piv, ar.y);
         mixed = refine<true>(ar.A, af, ar.piv, c, by, ar.y, rv, ls, red);
       }
       if (mixed) {
-        lu_solve_t(af, c, c, ar.piv, ar.t, ls);
+        lu_solve_blocked_t(af, c, c, ar.piv, ar.t);
         mixed = refine<false>(ar.A, af, ar.piv, c, nullptr, ar.t, rv, ls, red);
       }
       if (!mixed) {
@@ -433,7 +433,10 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
         }
       }
     }
-    if (ok && c > 0) lu_solve_transposed(lu0, c, c, piv0, ar.x, ls);
+    if (ok && c > 0) {
+      if (use_smem) lu_solve_transposed(lu0, c, c, piv0, ar.x, ls);
+      else lu_solve_transposed_blocked_t(lu0, c, c, piv0, ar.x);   // large c: blocked
+    }
     if (!ok) {
       if (threadIdx.x == 0) atomicOr(status, kErrSolve);
       continue;
