@@ -31,3 +31,20 @@ def test_counts_with_normal_length_law(path, n, wmax, rho_mu, rho_sigma, p):
     oc, _ = O.count_with_law(g, 5, 0, 0, 150, p, w0, wmax, 3,
                              O.weight_table_normal(w0, wmax, rho_mu, rho_sigma))
     assert (q.counts.cpu().numpy().view(np.uint32) == oc).all()
+
+
+def test_law_with_empty_tables_is_the_base_length():
+    """Base lengths at wmax leave every table empty: the realized lengths are w0, so the counts
+    equal those of the uniform law on [w0, w0]."""
+    n = 40
+    eu, ev = er_edges(n, 0.15, 3)
+    w0 = np.full(len(eu), 9, np.uint32)
+    wl = Workload("flat", n, eu, ev, 0.85, w0, 9, 60, seed=2, k_min=3)
+    ptr, tab = afc.afc_weight_table_normal(w0, 9, 0.3, 0.2)
+    assert tab.size == 0
+    q = afc.Query(wl, length_table=(ptr, tab))
+    q.run_counts()
+    ref = afc.Query(wl)
+    ref.run_counts()
+    torch.cuda.synchronize()
+    assert torch.equal(q.counts, ref.counts)

@@ -62,3 +62,21 @@ def test_per_row_with_pool_and_fallback():
                                  fallback=8)
     counts, fb = _run(wl, 40, 1, fallback_node=8)
     assert (counts == oc).all() and (fb == ofb).all() and ofb.sum() > 0
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_per_row_edge_cases(path):
+    """Isolated nodes with k_min = 1 (each reports itself), a radius of 1 on a path, and a
+    k_min above every component (everything absorbs)."""
+    n = 12
+    eu, ev = np.arange(0, 8), np.arange(1, 9)            # path 0..8, nodes 9..11 isolated
+    for k_min, hop in ((1, 0), (2, 1), (50, 2)):
+        wl = Workload("edge", n, eu, ev, 0.8, 1, 3, 6, seed=13, k_min=k_min)
+        g = O.build_graph(n, eu, ev)
+        oc, _, _ = O.count_per_row(g, 13, 0, 0, 6, 0.8, 1, 3, k_min, hop_radius=hop)
+        counts, _ = _run(wl, 6, path, hop_radius=hop)
+        assert (counts == oc).all(), (k_min, hop)
+        if k_min == 1:
+            assert (counts[9:, 9:12].diagonal() == 6).all()
+        if k_min == 50:
+            assert (counts[:, n] == 6).all()
