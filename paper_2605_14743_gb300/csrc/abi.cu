@@ -2,10 +2,13 @@
 // configuration (shared-memory layout, thread groups, bucket width), the stream-ordered
 // end-to-end query path and the bucket-width / group-size autotuner.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -55,6 +58,19 @@ DevInfo dev_info() {
 }
 
 // Requested bucket width; the kernels round it up to a power of two (and to the ring bound).
+// Host entry points that allocate run their body through this: a C caller gets AFC_ENOMEM
+// (or AFC_EDEVICE for anything else) instead of an exception crossing the C ABI.
+template <typename Fn>
+int guarded(const char *what, Fn &&fn) {
+  try {
+    return fn();
+  } catch (const std::bad_alloc &) {
+    return fail(AFC_ENOMEM, "%s: host allocation failed", what);
+  } catch (const std::exception &e) {
+    return fail(AFC_EDEVICE, "%s: %s", what, e.what());
+  }
+}
+
 uint32_t auto_delta(const afc_mc_problem &p) {
   if (p.bucket_width) return p.bucket_width;
   const double lo = p.w_lo ? 1.0 : (double)p.w_lo_all;
@@ -453,35 +469,37 @@ int afc_version(void) { return 10000; }
 
 int afc_csr_from_edges(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t *row_ptr,
                        int32_t *col, int32_t *eid) {
-  if (n < 0 || m < 0 || !row_ptr || (m > 0 && (!eu || !ev || !col || !eid)))
-    return fail(AFC_EINVAL, "bad arguments");
-  if (2 * m > 0x7FFFFFFF) return fail(AFC_EUNSUPPORTED, "too many edges");
-  for (int64_t e = 0; e < m; ++e)
-    if (eu[e] < 0 || eu[e] >= n || ev[e] < 0 || ev[e] >= n || eu[e] == ev[e])
-      return fail(AFC_EINVAL, "edge %lld = (%d, %d) invalid", (long long)e, eu[e], ev[e]);
-  std::vector<int32_t> deg((size_t)n + 1, 0);
-  for (int64_t e = 0; e < m; ++e) { deg[eu[e]]++; deg[ev[e]]++; }
-  row_ptr[0] = 0;
-  for (int32_t v = 0; v < n; ++v) row_ptr[v + 1] = row_ptr[v] + deg[v];
-  std::vector<int32_t> fill(row_ptr, row_ptr + n);
-  for (int64_t e = 0; e < m; ++e) {
-    const int32_t a = eu[e], b = ev[e];
-    col[fill[a]] = b; eid[fill[a]++] = (int32_t)e;
-    col[fill[b]] = a; eid[fill[b]++] = (int32_t)e;
-  }
-  std::vector<std::pair<int32_t, int32_t>> row;
-  for (int32_t v = 0; v < n; ++v) {
-    row.clear();
-    for (int32_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) row.emplace_back(col[a], eid[a]);
-    std::sort(row.begin(), row.end());
-    for (size_t k = 0; k < row.size(); ++k) {
-      if (k > 0 && row[k].first == row[k - 1].first)
-        return fail(AFC_EINVAL, "duplicate edge (%d, %d)", v, row[k].first);
-      col[row_ptr[v] + k] = row[k].first;
-      eid[row_ptr[v] + k] = row[k].second;
+  return guarded("afc_csr_from_edges", [&]() -> int {
+    if (n < 0 || m < 0 || !row_ptr || (m > 0 && (!eu || !ev || !col || !eid)))
+      return fail(AFC_EINVAL, "bad arguments");
+    if (2 * m > 0x7FFFFFFF) return fail(AFC_EUNSUPPORTED, "too many edges");
+    for (int64_t e = 0; e < m; ++e)
+      if (eu[e] < 0 || eu[e] >= n || ev[e] < 0 || ev[e] >= n || eu[e] == ev[e])
+        return fail(AFC_EINVAL, "edge %lld = (%d, %d) invalid", (long long)e, eu[e], ev[e]);
+    std::vector<int32_t> deg((size_t)n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) { deg[eu[e]]++; deg[ev[e]]++; }
+    row_ptr[0] = 0;
+    for (int32_t v = 0; v < n; ++v) row_ptr[v + 1] = row_ptr[v] + deg[v];
+    std::vector<int32_t> fill(row_ptr, row_ptr + n);
+    for (int64_t e = 0; e < m; ++e) {
+      const int32_t a = eu[e], b = ev[e];
+      col[fill[a]] = b; eid[fill[a]++] = (int32_t)e;
+      col[fill[b]] = a; eid[fill[b]++] = (int32_t)e;
     }
-  }
-  return AFC_OK;
+    std::vector<std::pair<int32_t, int32_t>> row;
+    for (int32_t v = 0; v < n; ++v) {
+      row.clear();
+      for (int32_t a = row_ptr[v]; a < row_ptr[v + 1]; ++a) row.emplace_back(col[a], eid[a]);
+      std::sort(row.begin(), row.end());
+      for (size_t k = 0; k < row.size(); ++k) {
+        if (k > 0 && row[k].first == row[k - 1].first)
+          return fail(AFC_EINVAL, "duplicate edge (%d, %d)", v, row[k].first);
+        col[row_ptr[v] + k] = row[k].first;
+        eid[row_ptr[v] + k] = row[k].second;
+      }
+    }
+    return AFC_OK;
+  });
 }
 
 uint64_t afc_survival_threshold(double p) {
@@ -957,21 +975,23 @@ int afc_pool_summaries(int32_t n, const double *b, const uint8_t *in_w, const ui
 
 int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, int32_t S,
                     uint8_t *in_w, int32_t *fallback_node, int32_t *triangles, int32_t *kept) {
-  if (n < 1 || m < 0 || S < 0 || !in_w || !fallback_node || (m > 0 && (!eu || !ev)))
-    return fail(AFC_EINVAL, "bad arguments");
-  std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
-      eid((size_t)std::max<int64_t>(2 * m, 1));
-  int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
-  if (st) return st;
-  std::vector<int32_t> tri;
-  clique_pool_host(n, rp.data(), col.data(), S, tri);
-  const int32_t k = (int32_t)(tri.size() / 3);
-  std::fill(in_w, in_w + n, (uint8_t)0);
-  for (int32_t t = 0; t < 3 * k; ++t) in_w[tri[t]] = 1;
-  *fallback_node = k > 0 ? tri[0] : -1;
-  if (triangles) std::copy(tri.begin(), tri.begin() + 3 * k, triangles);
-  if (kept) *kept = k;
-  return AFC_OK;
+  return guarded("afc_clique_pool", [&]() -> int {
+    if (n < 1 || m < 0 || S < 0 || !in_w || !fallback_node || (m > 0 && (!eu || !ev)))
+      return fail(AFC_EINVAL, "bad arguments");
+    std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
+        eid((size_t)std::max<int64_t>(2 * m, 1));
+    int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
+    if (st) return st;
+    std::vector<int32_t> tri;
+    clique_pool_host(n, rp.data(), col.data(), S, tri);
+    const int32_t k = (int32_t)(tri.size() / 3);
+    std::fill(in_w, in_w + n, (uint8_t)0);
+    for (int32_t t = 0; t < 3 * k; ++t) in_w[tri[t]] = 1;
+    *fallback_node = k > 0 ? tri[0] : -1;
+    if (triangles) std::copy(tri.begin(), tri.begin() + 3 * k, triangles);
+    if (kept) *kept = k;
+    return AFC_OK;
+  });
 }
 
 static int robust_checks(const afc_chain *chain, const uint32_t *counts, double eps, double r_min) {
@@ -1066,22 +1086,37 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
 
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out) {
-  if (n < 1 || m < 0 || count < 0 || !x || !y || !out || (m > 0 && (!eu || !ev)))
-    return fail(AFC_EINVAL, "bad arguments");
-  std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
-      eid((size_t)std::max<int64_t>(2 * m, 1));
-  int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
-  if (st) return st;
-  // rows are independent: spread them over the host's cores
-  const int32_t nth = std::max(1, std::min<int32_t>(count, (int32_t)std::thread::hardware_concurrency()));
-  std::vector<std::thread> pool;
-  for (int32_t t = 0; t < nth; ++t)
-    pool.emplace_back([&, t] {
-      for (int32_t k = t; k < count; k += nth)
-        out[k] = w1_graph_host(n, rp.data(), col.data(), eid.data(), x + (size_t)k * n, y);
-    });
-  for (auto &th : pool) th.join();
-  return AFC_OK;
+  return guarded("afc_w1_graph", [&]() -> int {
+    if (n < 1 || m < 0 || count < 0 || !x || !y || !out || (m > 0 && (!eu || !ev)))
+      return fail(AFC_EINVAL, "bad arguments");
+    std::vector<int32_t> rp((size_t)n + 1), col((size_t)std::max<int64_t>(2 * m, 1)),
+        eid((size_t)std::max<int64_t>(2 * m, 1));
+    int st = afc_csr_from_edges(n, m, eu, ev, rp.data(), col.data(), eid.data());
+    if (st) return st;
+    // rows are independent: spread them over the host's cores (a row whose solve fails to
+    // allocate flags the call; threads that could not start leave their rows to this one)
+    const int32_t nth = std::max(1, std::min<int32_t>(count, (int32_t)std::thread::hardware_concurrency()));
+    std::atomic<int> failed{0};
+    auto rows = [&](int32_t t0, int32_t step) {
+      try {
+        for (int32_t k = t0; k < count; k += step)
+          out[k] = w1_graph_host(n, rp.data(), col.data(), eid.data(), x + (size_t)k * n, y);
+      } catch (...) {
+        failed = 1;
+      }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve((size_t)nth);
+    int32_t started = 0;
+    try {
+      for (; started < nth; ++started) pool.emplace_back(rows, started, nth);
+    } catch (...) {
+    }
+    for (int32_t t = started; t < nth; ++t) rows(t, nth);
+    for (auto &th : pool) th.join();
+    if (failed) return fail(AFC_ENOMEM, "afc_w1_graph: host allocation failed");
+    return AFC_OK;
+  });
 }
 
 int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,
