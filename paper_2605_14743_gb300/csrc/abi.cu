@@ -508,6 +508,7 @@ int afc_transition_counts(const afc_mc_problem *prob, uint32_t r_begin, uint32_t
                           uint32_t *counts, afc_mc_stats *stats, double *dump_bc,
                           int32_t *dump_next, void *workspace, size_t workspace_bytes,
                           void *stream) {
+  NvtxRange nvtx_range("afc.transition_counts");
   if (!prob) return fail(AFC_EINVAL, "null problem");
   uint32_t *cs[1] = {counts};
   afc_mc_stats *sl[1] = {stats};
@@ -530,6 +531,7 @@ int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
                                   const uint32_t *r_count, uint32_t *const *counts,
                                   afc_mc_stats *stats, void *workspace, size_t workspace_bytes,
                                   void *stream) {
+  NvtxRange nvtx_range("afc.transition_counts_batched");
   if (nprob <= 0 || !probs || !r_count || !counts) return fail(AFC_EINVAL, "bad batch arguments");
   std::vector<afc_mc_stats *> sl;
   if (stats)
@@ -540,6 +542,7 @@ int afc_transition_counts_batched(int32_t nprob, const afc_mc_problem *probs,
 
 int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *stream,
                  afc_tune_result *out) {
+  NvtxRange nvtx_range("afc.autotune");
   int st = validate(prob);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -704,6 +707,7 @@ int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *source
 
 int afc_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index, int32_t *c_list,
                         int32_t *c_host, void *stream) {
+  NvtxRange nvtx_range("afc.observed_states");
   if (n < 1 || !counts || !c_index || !c_list || !c_host) return fail(AFC_EINVAL, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   int32_t *c_dev = nullptr;
@@ -767,6 +771,7 @@ int afc_absorbing_solve(const afc_chain *chain, const uint32_t *counts, const in
                         const int32_t *c_list, int32_t c, double *mu, double *b, double *scalars,
                         double *lu, int32_t *piv, void *workspace, size_t workspace_bytes,
                         void *stream) {
+  NvtxRange nvtx_range("afc.absorbing_solve");
   int st = chain_checks(chain, counts, c_index, c_list, c);
   if (st) return st;
   if (!mu || !b || !scalars || (c > 0 && (!lu || !piv))) return fail(AFC_EINVAL, "null output");
@@ -792,6 +797,7 @@ int afc_perturb_sweep(const afc_chain *chain, const afc_perturb_params *pp, cons
                       const double *b0, const double *lu0, const int32_t *piv0, uint64_t *counters,
                       uint64_t *pair_flips, uint64_t *shift_hist, double *maxima, double *b_out,
                       void *workspace, size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.perturb_sweep");
   int st = chain_checks(chain, counts, c_index, c_list, c);
   if (st) return st;
   if (!pp || !mu0 || !b0 || (c > 0 && (!lu0 || !piv0)) || !counters || !pair_flips || !shift_hist || !maxima)
@@ -822,6 +828,7 @@ int afc_certificates(const afc_chain *chain, const uint32_t *counts, const int32
                      const int32_t *piv0, double eps_bar, double r_min, int32_t npairs,
                      const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                      void *workspace, size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.certificates");
   int st = chain_checks(chain, counts, c_index, c_list, c);
   if (st) return st;
   if (npairs < 0 || (npairs > 0 && (!pu || !pv || !gap || !sharp)) || !mu0 || (c > 0 && (!lu0 || !piv0)))
@@ -870,6 +877,7 @@ int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, 
 // ---- end to end from host memory ----------------------------------------------------------------
 
 int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream) {
+  NvtxRange nvtx_range("afc.run_host");
   if (!q || !res || !res->b) return fail(AFC_EINVAL, "null query/result");
   const int32_t n = q->n;
   const int64_t m = q->m;

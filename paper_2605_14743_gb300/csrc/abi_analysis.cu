@@ -72,6 +72,7 @@ int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double
 
 int afc_feasibility(const afc_chain *chain, const uint32_t *counts, const uint32_t *fallback_count,
                     double *xi, void *stream) {
+  NvtxRange nvtx_range("afc.feasibility");
   if (!chain || !counts || !xi) return fail(AFC_EINVAL, "null argument");
   if (chain->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
   if (chain->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
@@ -125,6 +126,7 @@ int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int3
                   const int32_t *c_list, int32_t c, uint32_t B, uint64_t seed, double level,
                   double *b_rep, double *T_rep, double *b_lo, double *b_hi, void *workspace,
                   size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.bootstrap");
   if (!chain || !next_states || !c_index || !c_list) return fail(AFC_EINVAL, "null argument");
   if (chain->n < 1 || c < 0 || c > chain->n) return fail(AFC_EINVAL, "bad n or c");
   if (chain->realizations == 0 || B == 0) return fail(AFC_EINVAL, "realizations and B must be > 0");
@@ -169,6 +171,7 @@ int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int3
 int afc_robust_inner(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
                      int32_t support_only, const double *v, double v_bot, double *T, double *Qstar,
                      void *workspace, size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.robust_inner");
   int st = robust_checks(chain, counts, eps, r_min);
   if (st) return st;
   if (!v || !T) return fail(AFC_EINVAL, "null argument");
@@ -197,6 +200,7 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
                      int32_t support_only, int32_t sense, double *V, double *Qstar, double *b_star,
                      double *scalars, int32_t *iterations, void *workspace, size_t workspace_bytes,
                      void *stream) {
+  NvtxRange nvtx_range("afc.robust_value");
   int st = robust_checks(chain, counts, eps, r_min);
   if (st) return st;
   if (!V || !b_star || !scalars) return fail(AFC_EINVAL, "null argument");
@@ -247,6 +251,7 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
 
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out) {
+  NvtxRange nvtx_range("afc.w1_graph");
   return guarded("afc_w1_graph", [&]() -> int {
     if (n < 1 || m < 0 || count < 0 || !x || !y || !out || (m > 0 && (!eu || !ev)))
       return fail(AFC_EINVAL, "bad arguments");

@@ -10,10 +10,19 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "afc.h"
 
 namespace afc {
+
+// An NVTX range around a C-ABI call (shows up in Nsight timelines; a no-op without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // The calling thread's last error message (afc_last_error) and the helpers that set it.
 std::string &abi_error_text();

@@ -221,6 +221,50 @@ class Query:
                       b_rep, T_rep, lo, hi, ws, ws.numel(), self._stream())
         return lo, hi, b_rep, T_rep
 
+    def fingerprint(self) -> str:
+        """Hash of everything that decides the counts: the graph, the edge law (survival, lengths,
+        length-law tables), seed and graph tag, and the selection rule and its modes."""
+        import hashlib
+        h = hashlib.sha256()
+        wl, pr = self.wl, self.prob
+        for a in (wl.eu, wl.ev, wl.p_survive, wl.w_lo, wl.w_hi, wl.candidates):
+            h.update(np.ascontiguousarray(np.asarray(a if a is not None else [])).tobytes())
+        for v in (wl.n, wl.seed, wl.graph_tag, wl.k_min, wl.top_k, wl.tie_rel, pr.precision,
+                  pr.recheck_margin, pr.use_fallback, pr.fallback_node, pr.tie_random,
+                  pr.per_row, pr.hop_radius, pr.reward_k, pr.report_rank):
+            h.update(repr(v).encode())
+        for t in (self.wtab or ()) + (self.gamma, self.pool):
+            if t is not None:
+                h.update(t.cpu().numpy().tobytes())
+        return h.hexdigest()
+
+    def checkpoint(self, path, r_done):
+        """Saves what resuming needs after realizations [0, r_done) have been counted: the count
+        matrix (and the redirected-draw and step-reward accumulators when present), r_done and
+        the query's fingerprint.  Counts are additive and every draw is keyed by (seed,
+        realization, edge), so a resumed run equals the uninterrupted one bit for bit (the FP64
+        step rewards up to the order of their additions)."""
+        self.torch.cuda.synchronize()
+        np.savez(path, counts=self.counts.cpu().numpy(), r_done=np.int64(r_done),
+                 fingerprint=np.array(self.fingerprint()),
+                 fb=(self.fb_count.cpu().numpy() if self.fb_count is not None else np.zeros(0)),
+                 psi=(self.psi.cpu().numpy() if self.psi is not None else np.zeros(0)))
+
+    def resume(self, path) -> int:
+        """Loads a checkpoint of the same query into this one and returns the realization to
+        continue from; continue with run_counts(r_done, ..., zero=False)."""
+        ck = np.load(path)
+        if str(ck["fingerprint"]) != self.fingerprint():
+            raise ValueError("checkpoint belongs to another query")
+        torch = self.torch
+        self.counts.copy_(torch.from_numpy(ck["counts"]).to(self.counts.device))
+        if self.fb_count is not None:
+            self.fb_count.copy_(torch.from_numpy(ck["fb"]).to(self.counts.device))
+        if self.psi is not None:
+            self.psi.copy_(torch.from_numpy(ck["psi"]).to(self.counts.device))
+        self.stats.zero_()
+        return int(ck["r_done"])
+
     def feasibility(self):
         """xi [n] (device, FP64): per anchor, the estimated probability that a step reaches the
         candidate pool directly (Sec. 7.1), on the counts of the last run_counts."""
