@@ -713,6 +713,18 @@ def run_perturb_large(args):
     return 0
 
 
+def run_fma_peak(args):
+    """Measured FP64 and FP32 FMA throughput (the denominators of the FP64-bound kernels)."""
+    import torch
+    import paper_2605_14743_gb300 as afc
+    torch.cuda.set_device(0)
+    fp64 = max(afc.afc_measure_fma_rate(True) for _ in range(3))
+    fp32 = max(afc.afc_measure_fma_rate(False) for _ in range(3))
+    print(json.dumps({"config": {"workload": "register-resident FMA loop, 4 x 256 threads per SM"},
+                      "metric": "TFLOP/s", "fp64": fp64, "fp32": fp32, "ratio": fp32 / fp64}))
+    return 0
+
+
 def run_serving(args):
     """The serving stream through the native serving loop: a closed batch of its first queries
     measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
@@ -778,7 +790,7 @@ def main():
                     help="counting path of --counts-only")
     ap.add_argument("--config", default="ws1000",
                     choices=["ws1000", "mix", "ws20000", "serving", "constrained", "bootstrap",
-                             "robust", "weighted", "perturb-large"],
+                             "robust", "weighted", "perturb-large", "fma-peak"],
                     help="ws1000: the benchmark line; the others print their own JSON line")
     ap.add_argument("--mix-scale", type=float, default=0.125,
                     help="fraction of each mixed-batch graph's realizations to run")
@@ -807,6 +819,8 @@ def main():
         return run_weighted(args)
     if args.config == "perturb-large":
         return run_perturb_large(args)
+    if args.config == "fma-peak":
+        return run_fma_peak(args)
     if args.config == "serving":
         return run_serving(args)
     if args.counts_only:

@@ -225,6 +225,13 @@ int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double
                             double rho_sigma, uint32_t *ptr, uint32_t *tab, size_t capacity,
                             size_t *used);
 
+/* Measured FMA throughput of the current GPU (a diagnostic; the paper has no counterpart):
+ * *tflops = 2 x FMAs per second / 1e12 of a register-resident FMA loop over 4 CTAs of 256
+ * threads per SM, in FP64 (fp64 != 0) or FP32.  The FP64 figure is the denominator of the
+ * FP64-bound kernels' rooflines (GB300's FP64 rate is a small fraction of its FP32 rate).
+ * Allocates 8 bytes (stream ordered) and SYNCHRONISES `stream`. */
+int afc_measure_fma_rate(int32_t fp64, double *tflops, void *stream);
+
 /* Several base graphs in one persistent launch (the batched mix).  probs: HOST array of
  * nprob problems; r_count: HOST [nprob]; counts: HOST array of nprob DEVICE count matrices;
  * stats: DEVICE afc_mc_stats [nprob] or NULL.  workspace: DEVICE, at least

@@ -38,6 +38,7 @@ __all__ = [
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
     "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_robust_inner",
     "afc_robust_value_workspace", "afc_robust_value", "afc_weight_table_normal",
+    "afc_measure_fma_rate",
 ]
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
@@ -155,6 +156,7 @@ _SIGS = {
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
     "afc_w1_graph": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_i32, c_p], ctypes.c_int),
+    "afc_measure_fma_rate": ([c_i32, c_p, c_p], ctypes.c_int),
     "afc_weight_table_normal": ([c_i64, c_p, c_u32, c_f64, c_f64, c_p, c_p, c_sz, c_p],
                                 ctypes.c_int),
     "afc_robust_inner": ([ctypes.POINTER(Chain), c_p, c_f64, c_f64, c_i32, c_p, c_f64, c_p, c_p,
@@ -340,6 +342,13 @@ def afc_weight_table_normal(w0, wmax, rho_mu, rho_sigma):
     _chk(lib().afc_weight_table_normal(m, _ptr(w0), int(wmax), float(rho_mu), float(rho_sigma),
                                        _ptr(ptr), _ptr(tab), cap, ctypes.byref(used)))
     return ptr, tab[:used.value]
+
+
+def afc_measure_fma_rate(fp64: bool, stream=None) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    out = ctypes.c_double(0.0)
+    _chk(lib().afc_measure_fma_rate(1 if fp64 else 0, ctypes.byref(out), stream))
+    return float(out.value)
 
 
 def afc_w1_graph(n, eu, ev, x, y):
