@@ -220,13 +220,13 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
       auto add_y = [&](int32_t j, double v) { if (use_priv) py[j] += v; else atomicAdd(&py[j], v); };
       auto add_x = [&](int32_t j, double v) { if (use_priv) px[j] += v; else atomicAdd(&px[j], v); };
       if (supp <= 32 * kRowRegs) {
-        double z[kRowRegs], q0[kRowRegs], qv[kRowRegs];
-        int32_t col[kRowRegs];
+        double q0[kRowRegs], qv[kRowRegs];
+        int32_t col[kRowRegs], zi_raw[kRowRegs];
         long long isum = 0;
 #pragma unroll
         for (int t = 0; t < kRowRegs; ++t) {
           const int32_t e = e0 + (int32_t)lane + 32 * t;
-          col[t] = -1; z[t] = 0.0; q0[t] = 0.0; qv[t] = 0.0;
+          col[t] = -1; zi_raw[t] = 0; q0[t] = 0.0; qv[t] = 0.0;
           if (e < e1) {
             const int32_t pj = nzcol[e];
             col[t] = pj;
@@ -235,7 +235,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
               const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
               const int32_t zi = (int32_t)(draw_u32(node, (uint32_t)i, p, k0, k1) - 0x80000000u);
               isum += zi;
-              z[t] = (double)zi * kTwoM31;
+              zi_raw[t] = zi;
             }
           }
         }
@@ -247,7 +247,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
 #pragma unroll
           for (int t = 0; t < kRowRegs; ++t)
             if (col[t] >= 0 && col[t] < c) {
-              qv[t] = fmin(fmax(q0[t] * (1.0 + pp.rel_radius * z[t]), 0.0), 1.0);
+              qv[t] = fmin(fmax(q0[t] * (1.0 + pp.rel_radius * ((double)zi_raw[t] * kTwoM31)), 0.0), 1.0);
               ts += qv[t];
             }
           ts = warp_sum(ts);
@@ -261,36 +261,54 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
           }
           rfin = 1.0 - ts;
         } else {
-          const double mean = (double)warp_sum_ll(isum) * kTwoM31 / (double)supp;
-          double l1 = 0.0;
+          // l1 model with integer draws: with d_j = z_j supp - sum_k z_k (exact integers, z_j =
+          // zi_j 2^-31), the shift is (z_j - mean) l1_radius / ||z - mean||_1 = d_j l1_radius /
+          // sum_k |d_k|, so the mean and the l1 norm need no FP64 sums.  The shifts sum to 0 and
+          // the nominal row sums to 1, so the perturbed row sums to 1 plus what clipping at 0
+          // adds; the absorbing entry (always the row's last) then gives ts = 1 - ra.  Same
+          // values as the per-entry FP64 form up to rounding, with far fewer FP64 operations
+          // (the sweep is bound by GB300's FP64 pipe).
+          const long long S = warp_sum_ll(isum);
+          long long dab = 0;
+          long long dv[kRowRegs];
 #pragma unroll
-          for (int t = 0; t < kRowRegs; ++t)
-            if (col[t] >= 0) l1 += fabs(z[t] - mean);
-          l1 = warp_sum(l1);
-          const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
-          double tot = 0.0;
+          for (int t = 0; t < kRowRegs; ++t) {
+            dv[t] = 0;
+            if (col[t] >= 0) {
+              dv[t] = (long long)(int32_t)zi_raw[t] * (long long)supp - S;
+              dab += dv[t] < 0 ? -dv[t] : dv[t];
+            }
+          }
+          dab = warp_sum_ll(dab);
+          const double coef = dab > 0 ? pp.l1_radius / (double)dab : 0.0;
+          double clip = 0.0;
 #pragma unroll
           for (int t = 0; t < kRowRegs; ++t)
             if (col[t] >= 0) {
-              double v = q0[t] + (z[t] - mean) * scale;
-              v = v < 0.0 ? 0.0 : v;
+              double v = fma((double)dv[t], coef, q0[t]);
+              if (v < 0.0) { clip -= v; v = 0.0; }
               qv[t] = v;
-              tot += v;
             }
-          const double inv_tot = 1.0 / warp_sum(tot);
-          double ts = 0.0, ra = 0.0;
+          const bool clipped = __any_sync(0xFFFFFFFFu, clip != 0.0);
+          if (clipped) {
+            const double inv_tot = 1.0 / (1.0 + warp_sum(clip));
+#pragma unroll
+            for (int t = 0; t < kRowRegs; ++t) qv[t] *= inv_tot;
+          }
+          // the absorbing entry: position supp - 1 of the row
+          const int32_t la = (supp - 1) & 31, ta = (supp - 1) >> 5;
+          double mine = 0.0;
 #pragma unroll
           for (int t = 0; t < kRowRegs; ++t)
-            if (col[t] >= 0) {
-              qv[t] *= inv_tot;
-              if (col[t] < c) ts += qv[t]; else ra = qv[t];
-            }
-          ts = warp_sum(ts);
-          ra = warp_sum(ra);
-          const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
+            if (t == ta) mine = qv[t];
+          const double ra = __shfl_sync(0xFFFFFFFFu, mine, la);
+          const double ts = 1.0 - ra;
+          if (ra < pp.r_min && ts > 0.0) {
+            const double f = (1.0 - pp.r_min) / ts;
 #pragma unroll
-          for (int t = 0; t < kRowRegs; ++t)
-            if (col[t] >= 0 && col[t] < c && ra < pp.r_min) qv[t] *= f;
+            for (int t = 0; t < kRowRegs; ++t)
+              if (col[t] >= 0 && col[t] < c) qv[t] *= f;
+          }
           rfin = ra < pp.r_min ? pp.r_min : ra;
         }
 #pragma unroll
