@@ -356,35 +356,37 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
           }
         }
       } else {
-        double zs = 0.0;
+        // the integer form of the register path (see there), through the slab
+        long long isum = 0;
         for (int32_t e = e0 + lane; e < e1; e += 32) {
           const int32_t pj = nzcol[e];
           const uint32_t node = pj < c ? (uint32_t)C.c_list[pj] : (uint32_t)n;
-          const double z = 2.0 * uniform_draw(node, (uint32_t)i, p, k0, k1) - 1.0;
-          qp[e] = z;
-          zs += z;
+          const int32_t zi = (int32_t)(draw_u32(node, (uint32_t)i, p, k0, k1) - 0x80000000u);
+          qp[e] = (double)zi;   // exact
+          isum += zi;
         }
-        const double mean = warp_sum(zs) / (double)supp;
-        double l1 = 0.0;
-        for (int32_t e = e0 + lane; e < e1; e += 32) l1 += fabs(qp[e] - mean);
-        l1 = warp_sum(l1);
-        const double scale = l1 > 0.0 ? pp.l1_radius / l1 : 0.0;
-        double tot = 0.0;
+        const long long S = warp_sum_ll(isum);
+        long long dab = 0;
         for (int32_t e = e0 + lane; e < e1; e += 32) {
-          double q = nzval[e] + (qp[e] - mean) * scale;
-          q = q < 0.0 ? 0.0 : q;
-          qp[e] = q;
-          tot += q;
+          const long long d = (long long)qp[e] * (long long)supp - S;
+          dab += d < 0 ? -d : d;
         }
-        tot = warp_sum(tot);
-        double ts = 0.0, ra = 0.0;
+        dab = warp_sum_ll(dab);
+        const double coef = dab > 0 ? pp.l1_radius / (double)dab : 0.0;
+        double clip = 0.0;
         for (int32_t e = e0 + lane; e < e1; e += 32) {
-          const double q = qp[e] / tot;
-          qp[e] = q;
-          if (nzcol[e] < c) ts += q; else ra = q;
+          const long long d = (long long)qp[e] * (long long)supp - S;
+          double v = fma((double)d, coef, nzval[e]);
+          if (v < 0.0) { clip -= v; v = 0.0; }
+          qp[e] = v;
         }
-        ts = warp_sum(ts);
-        ra = warp_sum(ra);
+        if (__any_sync(0xFFFFFFFFu, clip != 0.0)) {
+          const double inv_tot = 1.0 / (1.0 + warp_sum(clip));
+          for (int32_t e = e0 + lane; e < e1; e += 32) qp[e] *= inv_tot;
+        }
+        __syncwarp();
+        const double ra = qp[e1 - 1];   // the absorbing entry is the row's last
+        const double ts = 1.0 - ra;
         const double f = (ra < pp.r_min && ts > 0.0) ? (1.0 - pp.r_min) / ts : 1.0;
         for (int32_t e = e0 + lane; e < e1; e += 32) {
           const int32_t pj = nzcol[e];
