@@ -56,6 +56,8 @@ def _declare(L):
     L.orc_bootstrap_weights.argtypes = [u32, u32, u64, P]
     L.orc_bootstrap_weights.restype = None
     L.orc_philox4x64_10.argtypes = [P, P, P]
+    L.orc_philox4x32_rounds.argtypes = [P, P, i32, P]
+    L.orc_philox4x64_rounds.argtypes = [P, P, i32, P]
     L.orc_build_csr.argtypes = [i32, i64, P, P, P, P, P]
     L.orc_survival_threshold.argtypes = [f64]
     L.orc_survival_threshold.restype = u64
@@ -109,19 +111,27 @@ def _check(st, what):
 
 # ---------------------------------------------------------------- Philox ----
 
-def philox4x32(ctr, key) -> np.ndarray:
+def philox4x32(ctr, key, rounds: int = 10) -> np.ndarray:
+    """Philox4x32 with `rounds` rounds (the generator is rounds = 10)."""
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, np.uint32)
-    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    if rounds == 10:
+        lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    else:
+        lib().orc_philox4x32_rounds(_p(c), _p(k), int(rounds), _p(out))
     return out
 
 
-def philox4x64(ctr, key) -> np.ndarray:
+def philox4x64(ctr, key, rounds: int = 10) -> np.ndarray:
+    """Philox4x64 with `rounds` rounds (the generator is rounds = 10)."""
     c = np.ascontiguousarray(ctr, dtype=np.uint64)
     k = np.ascontiguousarray(key, dtype=np.uint64)
     out = np.zeros(4, np.uint64)
-    lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    if rounds == 10:
+        lib().orc_philox4x64_10(_p(c), _p(k), _p(out))
+    else:
+        lib().orc_philox4x64_rounds(_p(c), _p(k), int(rounds), _p(out))
     return out
 
 

@@ -10,7 +10,10 @@
  *
  * Parity status of each routine (what pins it in the not-gpu tests):
  *   orc_philox4x32_10 / orc_philox4x64_10 : 4x64 checked against numpy.random.Philox;
- *                                           4x32 shares the round structure; uniformity tests.
+ *                                           4x32 shares the round structure; key schedule of
+ *                                           both widths pinned to the golden-ratio and sqrt(3)
+ *                                           Weyl increments; uniformity tests.  The 4x32
+ *                                           multipliers: parity unpinned (odd, distinct).
  *   orc_realize                           : survival frequency / weight histogram tests.
  *   orc_components                        : brute-force BFS comparison, invariants.
  *   orc_sssp / orc_brandes                : closed-form betweenness (path, star, cycle,
@@ -48,10 +51,13 @@
 /* a 4-word counter, with a Weyl-sequence key schedule.                                   */
 /* ------------------------------------------------------------------------------------ */
 
-void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+/* `rounds` rounds of the bijection; the generator proper is rounds = 10.  Fewer rounds serve   */
+/* the tests that pin the key schedule (10 rounds = 1 round, then 9 with the bumped key).      */
+void orc_philox4x32_rounds(const uint32_t ctr[4], const uint32_t key[2], int32_t rounds,
+                           uint32_t out[4]) {
   uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
   uint32_t k0 = key[0], k1 = key[1];
-  for (int round = 0; round < 10; ++round) {
+  for (int round = 0; round < rounds; ++round) {
     if (round > 0) {
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
@@ -69,10 +75,15 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  orc_philox4x32_rounds(ctr, key, 10, out);
+}
+
+void orc_philox4x64_rounds(const uint64_t ctr[4], const uint64_t key[2], int32_t rounds,
+                           uint64_t out[4]) {
   uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
   uint64_t k0 = key[0], k1 = key[1];
-  for (int round = 0; round < 10; ++round) {
+  for (int round = 0; round < rounds; ++round) {
     if (round > 0) {
       k0 += 0x9E3779B97F4A7C15ull;
       k1 += 0xBB67AE8584CAA73Bull;
@@ -88,6 +99,10 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
     x0 = y0; x1 = y1; x2 = y2; x3 = y3;
   }
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  orc_philox4x64_rounds(ctr, key, 10, out);
 }
 
 /* ------------------------------------------------------------------------------------ */

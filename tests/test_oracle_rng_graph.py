@@ -25,6 +25,56 @@ def test_philox4x64_matches_numpy(key, ctr0):
         assert list(ours) == list(raw[4 * blk:4 * blk + 4])
 
 
+def _weyl(radicand: int, bits: int, halve: bool) -> int:
+    """floor(2^bits * frac(x)) for x = sqrt(radicand) / 2 + 1/2 (golden ratio, halve=True) or
+    x = sqrt(radicand) (halve=False), in exact integer arithmetic."""
+    s = math.isqrt(radicand << (2 * bits))        # floor(2^bits * sqrt(radicand))
+    if halve:
+        return ((s - (1 << bits)) // 2) % (1 << bits)   # 2^bits * (sqrt(5) - 1) / 2
+    return s % (1 << bits)
+
+
+@pytest.mark.parametrize("width", [32, 64])
+def test_philox_key_schedule_is_the_published_weyl_sequence(width):
+    """The key schedule of Philox (Salmon et al., SC'11) bumps the key by the fractional parts
+    of the golden ratio and of sqrt(3), scaled to the word width.  Derived here from those
+    irrationals in integer arithmetic (not retyped): ten rounds equal one round followed by
+    nine rounds under the bumped key, for both word widths.  For 64-bit words the constants are
+    pinned a second time by numpy's Philox4x64 (test above); the 32-bit ones are their top
+    halves."""
+    w0 = _weyl(5, width, True)
+    w1 = _weyl(3, width, False)
+    if width == 32:
+        assert w0 == _weyl(5, 64, True) >> 32 and w1 == _weyl(3, 64, False) >> 32
+    mask = (1 << width) - 1
+    f = O.philox4x32 if width == 32 else O.philox4x64
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        ctr = [int(x) for x in rng.integers(0, 1 << 32, 4)]
+        key = [int(x) for x in rng.integers(0, 1 << 32, 2)]
+        if width == 64:
+            ctr = [c | (int(rng.integers(0, 1 << 31)) << 32) for c in ctr]
+            key = [k | (int(rng.integers(0, 1 << 31)) << 32) for k in key]
+        one = f(ctr, key, rounds=1)
+        bumped = [(key[0] + w0) & mask, (key[1] + w1) & mask]
+        assert list(f(ctr, key)) == list(f(one, bumped, rounds=9))
+        # a neighbouring increment breaks the identity
+        wrong = [(key[0] + w0 + 1) & mask, key[1]]
+        assert list(f(ctr, key)) != list(f(one, wrong, rounds=9))
+
+
+def test_philox4x32_one_round_multiplies_odd_constants():
+    """One round from counter (1, 0, 0, 0) or (0, 0, 1, 0) under key 0 exposes each multiplier
+    as the low product word: both are odd (so each round is a bijection) and they differ.
+    Their values themselves are unpinned (no published test vectors in this environment)."""
+    m0 = int(O.philox4x32([1, 0, 0, 0], [0, 0], rounds=1)[3])
+    m1 = int(O.philox4x32([0, 0, 1, 0], [0, 0], rounds=1)[1])
+    assert m0 & 1 and m1 & 1 and m0 != m1
+    # the high words of the products land in words 2 and 0: x = 2^31 gives hi = m >> 1
+    out = O.philox4x32([1 << 31, 0, 1 << 31, 0], [0, 0], rounds=1)
+    assert int(out[2]) == m0 >> 1 and int(out[0]) == m1 >> 1
+
+
 def test_philox4x32_is_bijective_on_sample_and_key_sensitive():
     key = (7, 9)
     outs = {tuple(O.philox4x32([c, 0, 0, 0], key)) for c in range(2000)}
