@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 from afc_inputs import Workload, crossroads_edges, mixed_batch, workload, ws_edges
-from tests._util import close, max_rel, oracle_counts, oracle_realization, variant
+import oracle as O
+from tests._util import close, max_rel, oracle_counts, oracle_graph, oracle_realization, variant
 
 pytestmark = pytest.mark.gpu
 
@@ -170,3 +171,41 @@ def test_ws20000_sampled_realization():
     wl = workload("ws20000")
     worst, q = _check(wl, 1, 1, oracle_threads=16, full_counts=False)
     assert worst < 1e-9
+
+
+def test_maximum_node_count_and_length_star():
+    """The largest graph the boundary accepts: 65,535 nodes (vertex ids fill the 16-bit packed
+    arcs and settled lists) with lengths up to 32,767, the longest this node count allows
+    (n x max length < 2^31 keeps every distance below the flag bit), on a star.  A tree has
+    unique shortest paths, so with a alive leaves the centre's betweenness is a (a - 1) over
+    ordered pairs and every leaf's is 0, whatever the lengths; the anchors of the centre's
+    component report the centre, the isolated leaves are absorbed.  The alive edges come from
+    the oracle's draws.  The 65,535 x 65,536 count matrix (17 GB) stays on the device: its two
+    used columns are compared."""
+    n = 65535
+    eu = np.zeros(n - 1, np.int32)
+    ev = np.arange(1, n, dtype=np.int32)
+    R = 2
+    wl = Workload("star65535", n, eu, ev, 0.9995, 1, 32767, R, seed=21, k_min=5)
+    q = afc.Query(wl)
+    bc = torch.empty((R, n), dtype=torch.float64, device="cuda")
+    nx = torch.empty((R, n), dtype=torch.int32, device="cuda")
+    q.run_counts(0, R, dump_bc=bc, dump_next=nx)
+    torch.cuda.synchronize()
+    bc, nx = bc.cpu().numpy(), nx.cpu().numpy()
+    g = oracle_graph(wl)
+    col0 = np.zeros(n, np.int64)
+    for r in range(R):
+        alive, _ = O.realize(g, wl.seed, wl.graph_tag, r, wl.p_survive, wl.w_lo, wl.w_hi)
+        a = int(alive.sum())
+        assert 5 <= a < n - 1
+        assert bc[r, 0] == float(a) * (a - 1)
+        assert (bc[r, 1:] == 0.0).all()
+        expect = np.where(np.concatenate(([1], alive)) != 0, 0, n).astype(np.int32)
+        assert (nx[r] == expect).all(), f"next states differ at realization {r}"
+        col0 += expect == 0
+    assert (q.counts[:, 0].cpu().numpy().astype(np.int64) == col0).all()
+    assert (q.counts[:, n].cpu().numpy().astype(np.int64) == R - col0).all()
+    assert int(q.counts.sum(dtype=torch.int64)) == R * n
+    st = q.stats.cpu().numpy()
+    assert st[0] == R and st[5] == 0, st
