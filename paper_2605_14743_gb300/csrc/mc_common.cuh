@@ -491,6 +491,29 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
 
   // ---- backward: dependencies, buckets in decreasing order; kFlag = "delta pending"
   if (want_delta) {
+    // where each bucket's run of the settled list starts: bit p of a bitmap over list
+    // positions, set when ord[p] opens a new bucket (kept in the ring words, unused from here on)
+    for (uint32_t i = 0; i < S; ++i) {
+      SlotArrays a = slot_arrays(sp, slot0 + i);
+      const uint32_t cnt = sl[i].mstart;
+      for (uint32_t base = 0; base < cnt; base += TS) {   // TS is a multiple of 32
+        const uint32_t p = base + tid;
+        bool start = false;
+        if (p < cnt) {
+          const uint32_t v = a.ord[p];
+          const uint32_t bv = v < n ? (a.dist[v] & kMask) >> dsh : 0xFFFFFFFFu;
+          uint32_t bu = 0xFFFFFFFEu;
+          if (p > 0) {
+            const uint32_t u = a.ord[p - 1];
+            bu = u < n ? (a.dist[u] & kMask) >> dsh : 0xFFFFFFFFu;
+          }
+          start = bu != bv;
+        }
+        const uint32_t word = __ballot_sync(kFull, start);
+        const uint32_t p0 = base + (tid & ~31u);
+        if (lane == 0 && p0 < cnt) a.ring[p0 >> 5] = word;
+      }
+    }
     for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].mstart;
     team.sync();
     for (uint32_t guard = 0;; ++guard) {
@@ -519,18 +542,24 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
         uint32_t lo = hi;
         const uint32_t vh = hi > 0 ? a.ord[hi - 1] : 0u;
         if (hi > 0 && vh < n && ((a.dist[vh] & kMask) >> dsh) == bcur) {
+          // the run's start: the highest start bit at or below position hi - 1 (bit 0 is set),
+          // 32 bitmap words per step, lane l taking the l-th word down
           lo = 0;
-          for (uint32_t top = hi; top > 0;) {
-            const uint32_t base = top > 32u ? top - 32u : 0u;
-            const uint32_t p = base + lane;
-            uint32_t cand = 0;
-            if (p < top) {
-              const uint32_t vp = a.ord[p];
-              if (vp >= n || ((a.dist[vp] & kMask) >> dsh) != bcur) cand = p + 1u;
+          const int32_t wtop = (int32_t)((hi - 1u) >> 5);
+          for (int32_t w0 = wtop; w0 >= 0; w0 -= 32) {
+            const int32_t w = w0 - (int32_t)lane;
+            uint32_t word = 0;
+            if (w >= 0) {
+              word = a.ring[w];
+              if (w == wtop) word &= (2u << ((hi - 1u) & 31u)) - 1u;
             }
-            const uint32_t found = __reduce_max_sync(kFull, cand);
-            if (found > 0) { lo = found; break; }
-            top = base;
+            const uint32_t nz = __ballot_sync(kFull, word != 0u);
+            if (nz) {
+              const uint32_t l = __ffs(nz) - 1;
+              const uint32_t wl = __shfl_sync(kFull, word, l);
+              lo = (uint32_t)(w0 - (int32_t)l) * 32u + 31u - __clz(wl);
+              break;
+            }
           }
         }
         if (lane == 0) sl[i].lo = lo;
