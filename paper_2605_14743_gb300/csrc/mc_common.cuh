@@ -359,9 +359,10 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
           } else {
             const uint32_t r2 = (nd >> dsh) & kRingMask;
             const uint32_t bit = 1u << (u & 31u);
-            const uint32_t prev = atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
-            if (!(prev & bit) && !(sl[oi].ring_mask & (1u << r2)))
-              atomicOr(&sl[oi].ring_mask, 1u << r2);
+            // the old word is not needed: a reduction, off the dependency chain (on the
+            // global path the ring lives in device memory)
+            atomicOr(&a.ring[r2 * W + (u >> 5)], bit);
+            if (!(sl[oi].ring_mask & (1u << r2))) atomicOr(&sl[oi].ring_mask, 1u << r2);
           }
         });
       }
