@@ -25,8 +25,11 @@
  *                                           chain closed form (Prop. in App. A); constant-
  *                                           hazard discounted occupancy (Sec. 5.3).
  *   orc_certificates                      : Appendix B printed thresholds.
- *   orc_perturb_sweep                     : parity unpinned beyond invariants (no printed
- *                                           values exist for this statistic).
+ *   orc_perturb_sweep                     : invariants; every perturbed solve against
+ *                                           numpy's dense solve and the counters recounted
+ *                                           from those solves; pair reversals never on a
+ *                                           pair the Sec. 5.5 certificate protects (no
+ *                                           printed values exist for these statistics).
  *   orc_topk_order / orc_count_rewards    : closed-form orderings (complete graph, star,
  *                                           path), rank-1 equals orc_select, the Top-1
  *                                           reward identity b_{1,f} = b.f - s.f / E[T],
