@@ -34,6 +34,20 @@
  *                                           path), rank-1 equals orc_select, the Top-1
  *                                           reward identity b_{1,f} = b.f - s.f / E[T],
  *                                           exhaustive failure patterns (Hoeffding bound).
+ *   orc_select_ex (filter, fallback)      : exhaustive failure enumeration with networkx
+ *                                           betweenness; identities between unconstrained,
+ *                                           filtered and fallback counts (Sec. 7).
+ *   orc_count_transitions, random ties    : exhaustive enumeration of the induced kernel on
+ *                                           the crossroads example; label invariance.
+ *   orc_weight_table_normal / _realize_law: scipy's normal distribution; realized histograms.
+ *   orc_count_per_row (Alg. 2, r-hop)     : exhaustive enumeration; path and star closed
+ *                                           forms; a radius covering the graph changes nothing.
+ *   orc_bootstrap_weights                 : multinomial moments; coverage of the exact
+ *                                           crossroads AFC.
+ *   orc_perturb_row_mult                  : row validity, leak floor, KL of the sweep.
+ * The robust inner problem, robust value and graph Wasserstein distance live in the Python
+ * part of the oracle and are pinned in its tests (closed forms, brute-force value iteration,
+ * an independent transport LP).
  */
 #include <math.h>
 #include <stdint.h>
