@@ -166,11 +166,14 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, 
 // with `deg` arcs starting at arc index `e0` (deg 0: nothing to do).  The warp walks the
 // concatenation of the items' arc ranges in windows of 32 positions, lane L taking position
 // w0 + L, so a warp's time follows its total arc count instead of its heaviest lane.  For
-// each position f(valid, owner_lane, arc_index) runs on every lane (valid = false past the
-// end); f fetches the owner's item data with __shfl_sync from owner_lane.  All 32 lanes must
-// call it (warp-uniform control flow).  Returns at once when no lane has arcs.
-template <typename F>
-__device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *table, F &&f) {
+// each position f(valid, owner_lane, arc[arc_index]) runs on every lane (valid = false past
+// the end, arc word 0 then); f fetches the owner's item data with __shfl_sync from owner_lane.
+// All 32 lanes must call it (warp-uniform control flow).  Returns at once when no lane has
+// arcs.  PREFETCH (arcs in device memory) issues the next window's arc loads before f runs on
+// the current window, so their latency overlaps f's work.
+template <bool PREFETCH, typename F>
+__device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *table,
+                                          const uint32_t *arc, F &&f) {
   const uint32_t lane = lane_id();
   const uint32_t nz = __ballot_sync(kFull, deg > 0);
   if (nz == 0u) return;
@@ -185,17 +188,44 @@ __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *ta
   if (deg > 0) table[__popc(nz & lanemask_lt())] = (uint8_t)lane;
   __syncwarp();
   uint32_t prior = 0;   // items whose range starts before the window
-  for (uint32_t w0 = 0; w0 < tot; w0 += 32u) {
+  // owner lane and arc index of this lane's position in the window starting at w0
+  auto locate = [&](uint32_t w0, bool &valid, uint32_t &ol, uint32_t &e) {
     const uint32_t rel = excl - w0;   // wraps (large) when the range starts before w0
     const uint32_t starts = __reduce_or_sync(kFull, (deg > 0 && rel < 32u) ? (1u << rel) : 0u);
     const uint32_t pos = w0 + lane;
-    const bool valid = pos < tot;
+    valid = pos < tot;
     const uint32_t rank = prior + __popc(starts & (0xFFFFFFFFu >> (31u - lane))) - 1u;
-    const uint32_t ol = valid ? (uint32_t)table[rank] : 0u;
+    ol = valid ? (uint32_t)table[rank] : 0u;
     const uint32_t oex = __shfl_sync(kFull, excl, ol);
     const uint32_t oe0 = __shfl_sync(kFull, e0, ol);
-    f(valid, ol, oe0 + (pos - oex));
+    e = oe0 + (pos - oex);
     prior += __popc(starts);
+  };
+  if constexpr (PREFETCH) {
+    bool valid;
+    uint32_t ol, e;
+    locate(0u, valid, ol, e);
+    uint32_t pk = valid ? arc[e] : 0u;
+    for (uint32_t w0 = 0; w0 < tot; w0 += 32u) {
+      bool nvalid = false;
+      uint32_t nol = 0, npk = 0;
+      if (w0 + 32u < tot) {   // warp-uniform
+        uint32_t ne;
+        locate(w0 + 32u, nvalid, nol, ne);
+        npk = nvalid ? arc[ne] : 0u;
+      }
+      f(valid, ol, pk);
+      valid = nvalid;
+      ol = nol;
+      pk = npk;
+    }
+  } else {
+    for (uint32_t w0 = 0; w0 < tot; w0 += 32u) {
+      bool valid;
+      uint32_t ol, e;
+      locate(w0, valid, ol, e);
+      f(valid, ol, valid ? arc[e] : 0u);
+    }
   }
   __syncwarp();
 }
@@ -337,12 +367,11 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             }
           }
         }
-        warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+        warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
           const uint32_t oi = __shfl_sync(kFull, i, ol);
           const uint32_t od = __shfl_sync(kFull, d, ol);
           if (!valid) return;
           SlotArrays a = slot_arrays(sp, slot0 + oi);
-          const uint32_t pk = H.arc[e];
           const uint32_t u = pk & 0xFFFFu;
           const uint32_t nd = od + (pk >> 16);
           const uint32_t cur = a.dist[u];
@@ -407,12 +436,11 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             }
           }
           // sum sigma over the predecessors; one that is not final yet leaves the member open
-          warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+          warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
             const uint32_t oi = __shfl_sync(kFull, i, ol);
             const uint32_t odv = __shfl_sync(kFull, dv, ol);
             if (!valid) return;
             SlotArrays a = slot_arrays(sp, slot0 + oi);
-            const uint32_t pk = H.arc[e];
             const uint32_t u = pk & 0xFFFFu;
             const uint32_t du = a.dist[u];
             if ((du & kMask) + (pk >> 16) != odv) return;
@@ -599,12 +627,11 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             }
             const bool pending = deg != 0;
             if (deg == 0x80000000u) deg = 0;
-            warp_arcs(deg, e0, ws->table, [&](bool valid, uint32_t ol, uint32_t e) {
+            warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
               const uint32_t oi = __shfl_sync(kFull, i, ol);
               const uint32_t odv = __shfl_sync(kFull, dvm, ol);
               if (!valid) return;
               SlotArrays a = slot_arrays(sp, slot0 + oi);
-              const uint32_t pk = H.arc[e];
               const uint32_t w = pk & 0xFFFFu;
               const uint32_t dw = a.dist[w];
               if ((dw & kMask) != odv + (pk >> 16)) return;
