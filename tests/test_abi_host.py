@@ -179,3 +179,35 @@ def test_weight_tables_match_the_oracle_bit_for_bit():
         assert (ptr == optr).all() and (tab == otab).all()
     with pytest.raises(afc.AfcError):
         afc.afc_weight_table_normal(np.array([0, 3], np.uint32), 5, 0.1, 0.1)
+
+
+def test_library_that_cannot_be_built_fails_loudly(monkeypatch):
+    """With the CUDA library missing and no way to build it, the binding raises: nothing falls
+    back to a host computation."""
+    monkeypatch.setattr(afc, "_lib", None)
+    monkeypatch.setattr(afc._build, "stale", lambda: True)
+
+    def no_nvcc(*a, **k):
+        raise RuntimeError("nvcc not found")
+
+    monkeypatch.setattr(afc._build, "build", no_nvcc)
+    with pytest.raises(RuntimeError):
+        afc.lib()
+
+
+def test_no_host_fallback_without_a_device():
+    """A valid query on a machine without a GPU ends in an error status from the library (its
+    first device allocation fails); the library never computes on the host instead."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the behaviour without a GPU")
+    eu = np.array([0, 1, 2, 3], np.int32)
+    ev = np.array([1, 2, 3, 4], np.int32)
+    g = afc.afc_graph_create(5, 4, eu, ev)
+    try:
+        p = afc.afc_params_default()
+        p.realizations = 8
+        with pytest.raises(afc.AfcError):
+            afc.afc_run(g, p)
+    finally:
+        afc.afc_graph_destroy(g)
