@@ -220,7 +220,8 @@ int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *
  * sigma_e), indexed by ptr[e] .. ptr[e+1]-1 (a law quantised to 2^-32).  HOST in: w0 [m] (each
  * in [1, wmax]); HOST out: ptr [m+1], tab [capacity]; *used = thresholds written.  Use with
  * afc_mc_problem.w_lo = w0 and w_hi_all = wmax.  Errors: AFC_EINVAL for bad arguments,
- * AFC_ENOMEM when capacity < sum_e (wmax - w0_e). */
+ * AFC_EUNSUPPORTED when sum_e (wmax - w0_e) >= 2^32 (32-bit offsets), AFC_ENOMEM when
+ * capacity < sum_e (wmax - w0_e). */
 int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double rho_mu,
                             double rho_sigma, uint32_t *ptr, uint32_t *tab, size_t capacity,
                             size_t *used);

@@ -337,10 +337,12 @@ def afc_weight_table_normal(w0, wmax, rho_mu, rho_sigma):
     m = w0.shape[0]
     cap = int(np.sum(int(wmax) - w0.astype(np.int64))) if m else 0
     ptr = np.zeros(m + 1, np.uint32)
-    tab = np.zeros(max(cap, 1), np.uint32)
+    # past 32-bit offsets the library refuses before writing a table: allocate none
+    tab = np.zeros(max(cap, 1), np.uint32) if cap <= 0xFFFFFFFF else None
     used = ctypes.c_size_t(0)
     _chk(lib().afc_weight_table_normal(m, _ptr(w0), int(wmax), float(rho_mu), float(rho_sigma),
-                                       _ptr(ptr), _ptr(tab), cap, ctypes.byref(used)))
+                                       _ptr(ptr), _ptr(tab), cap if tab is not None else 0,
+                                       ctypes.byref(used)))
     return ptr, tab[:used.value]
 
 

@@ -49,6 +49,8 @@ int afc_weight_table_normal(int64_t m, const uint32_t *w0, uint32_t wmax, double
     if (w0[e] < 1 || w0[e] > wmax) return fail(AFC_EINVAL, "w0[%lld] = %u outside [1, wmax]", (long long)e, w0[e]);
     need += wmax - w0[e];
   }
+  if (need > 0xFFFFFFFFull)
+    return fail(AFC_EUNSUPPORTED, "%zu thresholds do not fit 32-bit table offsets", need);
   if (need > capacity || (need > 0 && !tab))
     return fail(AFC_ENOMEM, "%zu thresholds needed, capacity %zu", need, capacity);
   size_t o = 0;

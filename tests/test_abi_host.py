@@ -179,6 +179,10 @@ def test_weight_tables_match_the_oracle_bit_for_bit():
         assert (ptr == optr).all() and (tab == otab).all()
     with pytest.raises(afc.AfcError):
         afc.afc_weight_table_normal(np.array([0, 3], np.uint32), 5, 0.1, 0.1)
+    # 65,540 edges x 65,534 thresholds pass 2^32: refused before any table is written
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_weight_table_normal(np.ones(65540, np.uint32), 65535, 0.5, 0.2)
+    assert e.value.code == afc.AFC_EUNSUPPORTED
 
 
 def test_library_that_cannot_be_built_fails_loudly(monkeypatch):
