@@ -744,10 +744,8 @@ size_t afc_solve_workspace(int32_t n, int32_t c) {
 static int chain_checks(const afc_chain *ch, const uint32_t *counts, const int32_t *c_index,
                         const int32_t *c_list, int32_t c) {
   if (!ch || !counts || !c_index || !c_list) return fail(AFC_EINVAL, "null argument");
-  if (ch->n < 1 || c < 0 || c > ch->n) return fail(AFC_EINVAL, "bad n or c");
-  if (ch->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
-  if (!(ch->alpha >= 0.0 && ch->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
-  if (!(ch->absorb_floor > 0.0 && ch->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (const int st = chain_params_check(ch)) return st;
+  if (c < 0 || c > ch->n) return fail(AFC_EINVAL, "bad n or c");
   return AFC_OK;
 }
 
@@ -856,12 +854,9 @@ int afc_reward_afc(const afc_chain *chain, const uint32_t *counts, const double 
 int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,
                                 double *b, double *scalars, void *stream) {
   if (!chain || !counts || !mu || !b || !scalars) return fail(AFC_EINVAL, "null argument");
-  if (chain->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
+  if (const int st = chain_params_check(chain)) return st;
   if (chain->n > 4096)
     return fail(AFC_EUNSUPPORTED, "the allocation-free solve supports n <= 4096 (got %d)", chain->n);
-  if (chain->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
-  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
-  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
   uint32_t status = 0;
   int32_t c = 0;
   cudaError_t e = launch_solve_static(chain->n, chain->realizations, chain->alpha,

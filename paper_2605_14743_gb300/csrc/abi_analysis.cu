@@ -25,9 +25,7 @@ size_t boot_ws_head(int32_t n, uint32_t B) {
 
 int robust_checks(const afc_chain *chain, const uint32_t *counts, double eps, double r_min) {
   if (!chain || !counts) return fail(AFC_EINVAL, "null argument");
-  if (chain->n < 1 || chain->realizations == 0) return fail(AFC_EINVAL, "bad n or realizations");
-  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
-  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (const int st = chain_params_check(chain)) return st;
   if (!(eps >= 0.0) || !(r_min > 0.0 && r_min < 1.0)) return fail(AFC_EINVAL, "need eps >= 0 and 0 < r_min < 1");
   return AFC_OK;
 }
@@ -76,10 +74,7 @@ int afc_feasibility(const afc_chain *chain, const uint32_t *counts, const uint32
                     double *xi, void *stream) {
   NvtxRange nvtx_range("afc.feasibility");
   if (!chain || !counts || !xi) return fail(AFC_EINVAL, "null argument");
-  if (chain->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
-  if (chain->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
-  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
-  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (const int st = chain_params_check(chain)) return st;
   cudaError_t e = launch_feasibility(chain->n, chain->realizations, chain->alpha,
                                      chain->absorb_floor, counts, fallback_count, xi,
                                      (cudaStream_t)stream);
@@ -130,10 +125,9 @@ int afc_bootstrap(const afc_chain *chain, const int32_t *next_states, const int3
                   size_t workspace_bytes, void *stream) {
   NvtxRange nvtx_range("afc.bootstrap");
   if (!chain || !next_states || !c_index || !c_list) return fail(AFC_EINVAL, "null argument");
-  if (chain->n < 1 || c < 0 || c > chain->n) return fail(AFC_EINVAL, "bad n or c");
-  if (chain->realizations == 0 || B == 0) return fail(AFC_EINVAL, "realizations and B must be > 0");
-  if (!(chain->alpha >= 0.0 && chain->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
-  if (!(chain->absorb_floor > 0.0 && chain->absorb_floor < 1.0)) return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  if (const int st = chain_params_check(chain)) return st;
+  if (c < 0 || c > chain->n) return fail(AFC_EINVAL, "bad n or c");
+  if (B == 0) return fail(AFC_EINVAL, "B must be > 0");
   if (!(level > 0.0 && level < 1.0)) return fail(AFC_EINVAL, "level outside (0, 1)");
   const int32_t n = chain->n;
   const uint32_t R = chain->realizations;

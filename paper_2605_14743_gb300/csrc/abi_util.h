@@ -40,6 +40,17 @@ struct DevInfo {
 };
 DevInfo dev_info();
 
+// The chain parameters every analysis entry point needs: n >= 1, R > 0, alpha in [0, 1] (the
+// absorption probability of Sec. 4) and the floor eta in (0, 1) (Sec. 8.2 stabilisation).
+inline int chain_params_check(const afc_chain *ch) {
+  if (ch->n < 1) return fail(AFC_EINVAL, "n must be >= 1");
+  if (ch->realizations == 0) return fail(AFC_EINVAL, "realizations must be > 0");
+  if (!(ch->alpha >= 0.0 && ch->alpha <= 1.0)) return fail(AFC_EINVAL, "alpha outside [0, 1]");
+  if (!(ch->absorb_floor > 0.0 && ch->absorb_floor < 1.0))
+    return fail(AFC_EINVAL, "absorb_floor outside (0, 1)");
+  return AFC_OK;
+}
+
 // Host entry points that allocate run their body through this: a C caller gets AFC_ENOMEM
 // (or AFC_EDEVICE for anything else) instead of an exception crossing the C ABI.
 template <typename Fn>
