@@ -17,7 +17,7 @@ from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProbl
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
                afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility, afc_w1_graph,
-               afc_robust_inner, afc_robust_value, afc_robust_value_workspace,
+               afc_robust_value, afc_robust_value_workspace,
                afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
 

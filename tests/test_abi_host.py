@@ -1,7 +1,6 @@
 """Not-gpu checks of the C ABI: the sm_103a library builds and loads, exports every entry point
 declared in include/afc.h, and its host-side helpers (CSR construction, survival thresholds,
 argument validation) behave as documented."""
-import ctypes
 import os
 import re
 

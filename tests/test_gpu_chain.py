@@ -8,8 +8,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from afc_inputs import Workload, workload
-from tests._util import close, max_rel, oracle_counts, variant
+from afc_inputs import workload
+from tests._util import close, max_rel, oracle_counts
 
 pytestmark = pytest.mark.gpu
 

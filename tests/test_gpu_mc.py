@@ -5,8 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from afc_inputs import (Workload, crossroads_edges, er_edges, grid_edges, mixed_batch, workload,
-                        ws_edges)
+from afc_inputs import Workload, crossroads_edges, er_edges, grid_edges, mixed_batch, workload
 from tests._util import close, max_rel, oracle_counts, oracle_graph, oracle_realization, variant
 
 pytestmark = pytest.mark.gpu

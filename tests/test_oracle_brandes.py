@@ -1,6 +1,5 @@
 """Oracle pins for weighted shortest paths, path counts and ordered-pair betweenness
 (Sec. 3.1 definition of B_v(H))."""
-import itertools
 from math import comb
 
 import numpy as np

@@ -1,7 +1,6 @@
 """Pins of the oracle's discrete length law (Sec. 9, Les Miserables setting: a normal draw
 around a base length, rounded and clipped to [w0, wmax]): the law its threshold tables encode
 against scipy's normal distribution, and the lengths realized from them."""
-import math
 
 import numpy as np
 import pytest

@@ -1,5 +1,4 @@
 """Oracle pins: Philox generator, realization sampler, CSR construction, components."""
-import itertools
 import math
 
 import numpy as np
