@@ -222,6 +222,25 @@ def test_canonical_chain_closed_form(alpha):
     assert np.allclose(b, alpha * s + (1 - alpha) * p, atol=1e-13)
 
 
+def test_mixture_theorem_with_state_dependent_absorption():
+    """App. A mixture theorem under (S1): if every surviving step lands on a fresh draw from p,
+    whatever the current node and however its absorption r_i varies, the visits after the
+    first are distributed as p, so b(s) = s / E_s[T] + (1 - 1 / E_s[T]) p and b+(s) = p."""
+    rng = np.random.default_rng(12)
+    n = 10
+    p = rng.random(n)
+    p /= p.sum()
+    s = rng.random(n)
+    s /= s.sum()
+    r = rng.uniform(0.05, 0.6, size=n)
+    Q = np.outer(1 - r, p)
+    mu, b, T, _ = O.afc_from_q(Q, s)
+    assert np.allclose(b, s / T + (1 - 1 / T) * p, atol=1e-13)
+    assert np.allclose((mu - s) / (T - 1), p, atol=1e-12)       # b+(s) = p
+    # E_s[T] = 1 + (s.(1 - r)) / (p.r): one first step, then geometric with mean 1 / (p.r)
+    assert T == pytest.approx(1 + (s @ (1 - r)) / (p @ r), rel=1e-12)
+
+
 def test_constant_hazard_discounted_occupancy_and_survival_decomposition():
     """Sec. 5.3: with r = alpha 1, b = alpha sum_t (1-alpha)^t s M^t.  Cor. (survival
     decomposition): b = sum_t w_t pi_t with w_t = s Q^t 1 / E[T], pi_t = s Q^t / s Q^t 1."""
