@@ -152,6 +152,29 @@ def test_canonical_chain_closed_form():
     assert abs(ch.sc.cpu().numpy()[0] - 1.0 / alpha) <= 1e-12 / alpha
 
 
+def test_mixture_theorem_closed_form():
+    """App. A mixture theorem under (S1): every row's transient counts proportional to one p,
+    with a row-dependent survival (1 - alpha) 20 k_i / R.  Then b = s / E[T] + (1 - 1/E[T]) p
+    with E[T] = 1 + s.(1 - r) / (p.r), a closed form the device solve must reach."""
+    n, R, alpha = 30, 1000, 0.1
+    rng = np.random.default_rng(8)
+    base = np.zeros(n, np.int64)
+    base[rng.choice(n, 6, replace=False)] = [1, 2, 3, 4, 5, 5]
+    k = rng.integers(5, 45, size=n)
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        counts[i, :n] = k[i] * base
+        counts[i, n] = R - 20 * k[i]
+    p = base / 20.0
+    r = 1 - (1 - alpha) * 20 * k / R
+    s = np.full(n, 1.0 / n)
+    T = 1 + (s @ (1 - r)) / (p @ r)
+    ch = Chain(counts, R, alpha)
+    assert ch.c == 6
+    assert close(ch.b.cpu().numpy(), s / T + (1 - 1 / T) * p)
+    assert abs(ch.sc.cpu().numpy()[0] - T) <= 1e-12 * T
+
+
 def test_appendix_b_on_gpu():
     """Appendix B through the device path: Q0 as counts with alpha = 0 and R = 100."""
     gold = json.load(open(os.path.join(GOLD, "appendix_b.json")))
