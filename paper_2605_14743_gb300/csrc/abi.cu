@@ -873,7 +873,8 @@ int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, 
 
 int afc_run_host(const afc_host_query *q, afc_host_result *res, void *stream) {
   NvtxRange nvtx_range("afc.run_host");
-  if (!q || !res || !res->b) return fail(AFC_EINVAL, "null query/result");
+  if (!q || !res) return fail(AFC_EINVAL, "null query or result");
+  if (!res->b) return fail(AFC_EINVAL, "result.b (host output [n]) is null");
   const int32_t n = q->n;
   const int64_t m = q->m;
   if (n < 1 || m < 0) return fail(AFC_EINVAL, "bad n/m");

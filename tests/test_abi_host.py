@@ -214,3 +214,12 @@ def test_no_host_fallback_without_a_device():
             afc.afc_run(g, p)
     finally:
         afc.afc_graph_destroy(g)
+
+
+def test_run_host_names_the_missing_output():
+    """afc_run_host checks its host output buffers before touching the device."""
+    q = afc.HostQuery()
+    q.n, q.m = 5, 0
+    with pytest.raises(afc.AfcError) as e:
+        afc.afc_run_host(q, afc.HostResult(), None)
+    assert e.value.code == afc.AFC_EINVAL and "result.b" in str(e.value)
