@@ -10,10 +10,11 @@
  *
  * Parity status of each routine (what pins it in the not-gpu tests):
  *   orc_philox4x32_10 / orc_philox4x64_10 : 4x64 checked against numpy.random.Philox;
- *                                           4x32 shares the round structure; key schedule of
- *                                           both widths pinned to the golden-ratio and sqrt(3)
- *                                           Weyl increments; uniformity tests.  The 4x32
- *                                           multipliers: parity unpinned (odd, distinct).
+ *                                           4x32 (multipliers included) checked block by
+ *                                           block against PyTorch's header-only Philox
+ *                                           engine; key schedule of both widths pinned to the
+ *                                           golden-ratio and sqrt(3) Weyl increments;
+ *                                           uniformity tests.
  *   orc_realize                           : survival frequency / weight histogram tests.
  *   orc_components                        : brute-force BFS comparison, invariants.
  *   orc_sssp / orc_brandes                : closed-form betweenness (path, star, cycle,

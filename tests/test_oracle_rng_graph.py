@@ -65,13 +65,64 @@ def test_philox_key_schedule_is_the_published_weyl_sequence(width):
 def test_philox4x32_one_round_multiplies_odd_constants():
     """One round from counter (1, 0, 0, 0) or (0, 0, 1, 0) under key 0 exposes each multiplier
     as the low product word: both are odd (so each round is a bijection) and they differ.
-    Their values themselves are unpinned (no published test vectors in this environment)."""
+    Their values are pinned by the independent implementation in the next test."""
     m0 = int(O.philox4x32([1, 0, 0, 0], [0, 0], rounds=1)[3])
     m1 = int(O.philox4x32([0, 0, 1, 0], [0, 0], rounds=1)[1])
     assert m0 & 1 and m1 & 1 and m0 != m1
     # the high words of the products land in words 2 and 0: x = 2^31 gives hi = m >> 1
     out = O.philox4x32([1 << 31, 0, 1 << 31, 0], [0, 0], rounds=1)
     assert int(out[2]) == m0 >> 1 and int(out[0]) == m1 >> 1
+
+
+_ATEN_HARNESS = r"""
+#include <ATen/core/PhiloxRNGEngine.h>
+#include <cstdio>
+// one line per case on stdin: counter words c0 c1 c2 c3, key words k0 k1 (decimal);
+// prints the four 32-bit outputs of that counter block
+int main() {
+  unsigned long long v[6];
+  while (scanf("%llu %llu %llu %llu %llu %llu", v, v + 1, v + 2, v + 3, v + 4, v + 5) == 6) {
+    // the engine keys Philox with the seed, puts the subsequence in counter words 2-3 and
+    // the offset (128-bit blocks to skip) in words 0-1
+    at::philox_engine e(v[4] | (v[5] << 32), v[2] | (v[3] << 32), v[0] | (v[1] << 32));
+    for (int i = 0; i < 4; ++i) printf("%u ", e());
+    printf("\n");
+  }
+  return 0;
+}
+"""
+
+
+def test_philox4x32_matches_an_independent_implementation(tmp_path):
+    """Pins the whole Philox4x32-10 block function -- the two 32-bit multipliers included --
+    against PyTorch's header-only engine (ATen/core/PhiloxRNGEngine.h, an implementation of
+    the same SC'11 generator written independently of this project), compiled here as a
+    small host program.  Counter and key words span the full 32-bit range; a digit changed
+    in either multiplier, a swapped output word or a wrong key bump fails the comparison."""
+    import os
+    import shutil
+    import subprocess
+    torch = pytest.importorskip("torch")
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    if shutil.which("g++") is None or not os.path.exists(
+            os.path.join(inc, "ATen", "core", "PhiloxRNGEngine.h")):
+        pytest.skip("g++ or PyTorch's Philox header not available")
+    src = tmp_path / "h.cpp"
+    exe = tmp_path / "h"
+    src.write_text(_ATEN_HARNESS)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-I", inc, "-o", str(exe), str(src)], check=True)
+    rng = np.random.default_rng(2024)
+    cases = [[0, 0, 0, 0, 0, 0], [1, 0, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0],
+             [2**32 - 1] * 6, [5, 7, 0, 0, 1, 0]]
+    cases += [[int(x) for x in rng.integers(0, 2**32, 6, dtype=np.uint64)] for _ in range(200)]
+    # the counter layout of the realization draws: (edge, realization, graph tag, 0), key = seed
+    cases += [[e, r, g, 0, 1, 0] for e in (0, 17, 2999) for r in (0, 9999) for g in (0, 63)]
+    out = subprocess.run([str(exe)], input="\n".join(" ".join(map(str, c)) for c in cases),
+                         capture_output=True, text=True, check=True).stdout.split("\n")
+    for c, line in zip(cases, out):
+        theirs = [int(x) for x in line.split()]
+        ours = [int(x) for x in O.philox4x32(c[:4], c[4:])]
+        assert ours == theirs, (c, ours, theirs)
 
 
 def test_philox4x32_is_bijective_on_sample_and_key_sensitive():
