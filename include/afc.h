@@ -34,7 +34,7 @@ extern "C" {
 #define AFC_ENOMEM 2       /* a device or host allocation failed, or workspace too small   */
 #define AFC_EOVERFLOW 3    /* a shortest-path count exceeded 2^64 - 1 in some realization  */
 #define AFC_ESINGULAR 4    /* I - Q was numerically singular                               */
-#define AFC_ETIMEOUT 5     /* a bounded device wait expired                                */
+#define AFC_ETIMEOUT 5     /* a bounded wait for device work expired (afc_server_poll)     */
 #define AFC_ECUDA 6        /* a CUDA runtime call failed                                   */
 #define AFC_EUNSUPPORTED 7 /* the problem exceeds an implementation limit                  */
 #define AFC_EDEVICE 8      /* a device-side consistency check failed (see message)        */
@@ -403,8 +403,12 @@ int afc_clique_pool(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, 
  * In: chain, counts (DEVICE [n][n+1]).  Out (DEVICE): mu [n], b [n], scalars [4] as in
  * afc_absorbing_solve.  Limits: n <= 4096 (else AFC_EUNSUPPORTED before any work) and at most
  * 256 observed states (else AFC_EUNSUPPORTED after the states are counted).  SYNCHRONISES
- * `stream`.  The first call on a device looks up the array's device address (once per device;
- * make that first call before any stream capture).  Every call on a device shares the array and
+ * `stream` (it reads the state count and status back before returning).  The first call on a
+ * device looks up the array's device address (once per device; make that first call before any
+ * stream capture).  The CUDA driver places the array when it loads the library's device code:
+ * under lazy module loading (the default) that happens at the first use of that code, so a
+ * caller that reserves all device memory up front should make one call (or load modules
+ * eagerly, CUDA_MODULE_LOADING=EAGER) before doing so.  Every call on a device shares the array and
  * it keeps the last call's contents; calls whose work overlaps on the GPU (other streams or host
  * threads) race on it, so serialise them. */
 int afc_absorbing_solve_noalloc(const afc_chain *chain, const uint32_t *counts, double *mu,
@@ -556,10 +560,12 @@ int afc_server_create(const afc_server_cfg *cfg, afc_server **out);
  * errors as afc_run_host. */
 int afc_server_submit(afc_server *s, const afc_host_query *q, uint64_t *ticket);
 
-/* Waits up to wait_ms (negative: no limit, 0: just look) for the query's result.  AFC_EBUSY
- * while it is pending; otherwise the query's status, its result copied into res (res->b
- * required, res->mu and res->counts optional; counts only with keep_counts) and, when
- * latency_ms is not NULL, its submit-to-ready time.  A ticket can be collected once. */
+/* Waits up to wait_ms (negative: no limit, 0: just look) for the query's result.  While the
+ * query is pending: AFC_EBUSY for a look (wait_ms 0), AFC_ETIMEOUT when a wait of wait_ms > 0
+ * ran out (the ticket stays valid; poll again).  Otherwise the query's status, its result
+ * copied into res (res->b required, res->mu and res->counts optional; counts only with
+ * keep_counts) and, when latency_ms is not NULL, its submit-to-ready time.  A ticket can be
+ * collected once. */
 int afc_server_poll(afc_server *s, uint64_t ticket, int32_t wait_ms, afc_host_result *res,
                     double *latency_ms);
 

@@ -482,11 +482,12 @@ def afc_server_submit(server: int, query: HostQuery) -> int:
 
 
 def afc_server_poll(server: int, ticket: int, wait_ms: int, result: HostResult):
-    """(status, latency_ms): AFC_EBUSY while pending, AFC_OK when result holds the answer;
-    raises AfcError when the query failed."""
+    """(status, latency_ms): AFC_EBUSY (a look, wait_ms 0) or AFC_ETIMEOUT (a bounded wait ran
+    out) while pending, AFC_OK when result holds the answer; raises AfcError when the query
+    failed."""
     lat = c_f64(0.0)
     code = lib().afc_server_poll(server, ticket, wait_ms, ctypes.byref(result), ctypes.byref(lat))
-    if code == AFC_EBUSY:
+    if code in (AFC_EBUSY, AFC_ETIMEOUT):
         return code, None
     _chk(code)
     return code, lat.value

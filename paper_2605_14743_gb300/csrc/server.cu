@@ -596,7 +596,8 @@ int afc_server_poll(afc_server *S, uint64_t ticket, int32_t wait_ms, afc_host_re
   auto ready = [&] { return j->state == kDone; };
   if (wait_ms < 0) S->cv_done.wait(lk, ready);
   else if (wait_ms > 0) S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), ready);
-  if (!ready()) return AFC_EBUSY;
+  // a look (wait_ms 0) at a pending query: busy; a bounded wait that ran out: timeout
+  if (!ready()) return wait_ms == 0 ? AFC_EBUSY : AFC_ETIMEOUT;
   S->jobs.erase(it);
   lk.unlock();
   if (latency_ms) *latency_ms = 1e3 * (j->t_done - j->t_submit);

@@ -595,7 +595,7 @@ class Server:
         return t
 
     def poll(self, ticket: int, wait_ms: int = -1) -> Optional[ServedResult]:
-        from . import AFC_EBUSY, afc_server_poll
+        from . import AFC_EBUSY, AFC_ETIMEOUT, afc_server_poll
         n = self.n_of[ticket]
         b, mu = np.zeros(n), np.zeros(n)
         counts = np.zeros((n, n + 1), np.uint32) if self.keep_counts else None
@@ -603,7 +603,7 @@ class Server:
         r.b, r.mu = b.ctypes.data, mu.ctypes.data
         r.counts = None if counts is None else counts.ctypes.data
         code, lat = afc_server_poll(self.handle, ticket, wait_ms, r)
-        if code == AFC_EBUSY:
+        if code in (AFC_EBUSY, AFC_ETIMEOUT):   # still pending (looked, or the wait ran out)
             return None
         del self.n_of[ticket]
         st = {f[0]: int(getattr(r.stats, f[0])) for f in McStats._fields_}
@@ -653,3 +653,64 @@ def merge_counts(counts, group=None):
     if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
         dist.all_reduce(counts, op=dist.ReduceOp.SUM, group=group)
     return counts
+
+
+def split_range(begin: int, count: int, index: int, parts: int) -> tuple[int, int]:
+    """Part `index` of `parts` contiguous, near-equal parts of [begin, begin + count)."""
+    if parts < 1 or not 0 <= index < parts:
+        raise ValueError("bad index/parts")
+    lo = begin + (count * index) // parts
+    hi = begin + (count * (index + 1)) // parts
+    return lo, hi - lo
+
+
+class ElasticShards:
+    """Realization schedule over ranks that may leave between steps (strong scaling of one
+    query).  Step k covers realizations [k * step, min((k + 1) * step, total)), split over the
+    ranks still present.  Membership lives in a key-value store that every rank reaches
+    (torch.distributed's TCPStore): after its share of a step a rank posts `done/k/rank`; a
+    rank that leaves posts its partial count matrix and `left/rank` first.  Before each step the
+    others wait for every member's `done` of the previous step, then drop the ranks that left,
+    so a departure is seen on the host before the next launch and the remaining realizations
+    are re-split among the survivors.  Counts are integers and add, so the survivors' counts plus
+    the handed-over ones equal a single run bit for bit.  No rank may leave in the middle of a
+    step (nothing of its own may be in flight)."""
+
+    def __init__(self, store, rank: int, world: int, total: int, step: int):
+        self.store, self.rank, self.total, self.step = store, rank, total, step
+        self.world = world
+        self.members = list(range(world))
+        self.k = 0
+
+    def steps(self) -> int:
+        return (self.total + self.step - 1) // self.step
+
+    def next_range(self) -> Optional[tuple[int, int]]:
+        """This rank's realization range of the next step, or None when all steps are done."""
+        if self.k > 0:
+            prev = self.k - 1
+            self.store.wait([f"done/{prev}/{m}" for m in self.members])
+            self.members = [m for m in self.members if not self.store.check([f"left/{m}"])]
+        if self.k >= self.steps():
+            return None
+        b0 = self.k * self.step
+        cnt = min(self.step, self.total - b0)
+        return split_range(b0, cnt, self.members.index(self.rank), len(self.members))
+
+    def finish_step(self):
+        self.store.set(f"done/{self.k}/{self.rank}", "1")
+        self.k += 1
+
+    def leave(self, counts: np.ndarray):
+        """Hands this rank's counts over and leaves after the current step."""
+        self.store.set(f"handover/{self.rank}", np.ascontiguousarray(counts, np.int64).tobytes())
+        self.store.set(f"left/{self.rank}", str(self.k))
+        self.finish_step()
+
+    def handovers(self, shape) -> np.ndarray:
+        """Sum of the counts handed over by the ranks that left (call after the last step)."""
+        out = np.zeros(shape, np.int64)
+        for m in range(self.world):
+            if m not in self.members:
+                out += np.frombuffer(self.store.get(f"handover/{m}"), np.int64).reshape(shape)
+        return out

@@ -87,3 +87,23 @@ def test_poll_without_wait_reports_pending():
         res = first if first is not None else srv.poll(t)
     assert first is None or first.stats["realizations"] == 600
     assert res.stats["realizations"] == 600
+
+
+def test_bounded_wait_runs_out_with_timeout():
+    """A poll whose bounded wait ends before the query does returns AFC_ETIMEOUT and leaves the
+    ticket valid; a look (wait 0) at a pending query returns AFC_EBUSY; an unbounded wait then
+    collects the result.  The query (10,000 realizations of the 1000-node workload and 10,000
+    perturbations) runs for far longer than the 1 ms wait."""
+    wl = workload("ws1000")
+    with afc.Server() as srv:
+        t = srv.submit(wl)
+        b, mu = np.zeros(wl.n), np.zeros(wl.n)
+        r = afc.HostResult()
+        r.b, r.mu, r.counts = b.ctypes.data, mu.ctypes.data, None
+        code, lat = afc.afc_server_poll(srv.handle, t, 1, r)
+        assert code == afc.AFC_ETIMEOUT and lat is None
+        code, lat = afc.afc_server_poll(srv.handle, t, 0, r)
+        assert code == afc.AFC_EBUSY and lat is None
+        res = srv.poll(t)
+    assert res is not None and res.stats["realizations"] == wl.realizations
+    assert abs(res.b.sum() - 1.0) < 1e-9

@@ -5,7 +5,8 @@ touch buffers they are handed), so the library offers a solve whose scratch is a
 array inside the library.  This test calls it through the C ABI twice in a row -- the array keeps
 the previous call's contents, so the second call checks that everything that must start from zero
 is cleared -- and compares mu, b and the scalars with afc_absorbing_solve within the tolerance of
-the other parity tests.  It is collected last and passes alone or after the other tests."""
+the other parity tests, with a uniform and a non-uniform initial law, and with alpha = 0 and rows
+that never absorb (the absorption floor).  It is collected last and passes alone or after the other tests."""
 import numpy as np
 import pytest
 
@@ -56,7 +57,7 @@ def test_noalloc_solve_matches_workspace_solve_twice():
     g = O.build_graph(wl.n, wl.eu, wl.ev)
     counts, _ = O.count_transitions(g, wl.seed, wl.graph_tag, 0, 300, wl.p_survive, wl.w_lo,
                                     wl.w_hi, wl.k_min)
-    cases.append((counts, 300, 0.15, None))
+    cases.append((counts, 300, 0.15, None, None))
     rng = np.random.default_rng(3)
     n2, R2 = 700, 200
     counts2 = np.zeros((n2, n2 + 1), np.uint32)
@@ -66,12 +67,24 @@ def test_noalloc_solve_matches_workspace_solve_twice():
         d = rng.multinomial(R2, rng.dirichlet(np.ones(4)))
         counts2[i, t] += d[:3].astype(np.uint32)
         counts2[i, n2] += d[3]
-    cases.append((counts2, R2, 0.3, rng.random(n2)))
-    for counts, R, alpha, f in cases:
+    cases.append((counts2, R2, 0.3, rng.random(n2), None))
+    # a non-uniform initial law (the s_U Q_UC part of the right-hand side and mu_U = s_U)
+    s3 = rng.random(n2) ** 3
+    cases.append((counts2, R2, 0.2, None, s3 / s3.sum()))
+    # alpha = 0 and rows without any absorption count: those rows take the floor eta and
+    # their transient part is rescaled to 1 - eta
+    counts4 = counts2.copy()
+    # (pool rows keep their absorption, so every walk still ends quickly)
+    dry = rng.choice(np.setdiff1d(np.arange(n2), pool), 200, replace=False)
+    counts4[dry, pool[0]] += counts4[dry, n2]
+    counts4[dry, n2] = 0
+    cases.append((counts4, R2, 0.0, rng.random(n2), None))
+    for counts, R, alpha, f, s in cases:
         n = counts.shape[0]
         ct = torch.from_numpy(counts.view(np.int32)).cuda()
         ft = None if f is None else torch.from_numpy(f).cuda()
-        ch = _chain(n, R, alpha, f=ft)
+        stt = None if s is None else torch.from_numpy(s).cuda()
+        ch = _chain(n, R, alpha, s=stt, f=ft)
         mu_ref, b_ref, sc_ref = _workspace_solve(ct, ch, n)
         for _ in range(2):  # two calls in a row share the scratch array
             mu = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
