@@ -174,8 +174,10 @@ typedef struct {
  * code for an invalid problem. */
 int afc_counts_path(const afc_mc_problem *prob);
 
-/* Bytes of device workspace afc_transition_counts needs for this problem (0 when the whole
- * per-realization state fits in shared memory). */
+/* Bytes of device workspace afc_transition_counts needs for this problem, for any realization
+ * count (0 for an invalid problem): on the shared-memory path one region per CTA (components,
+ * source list, selection scratch, betweenness accumulators), on the global path the
+ * realizations in flight and the source-slot arena. */
 size_t afc_transition_counts_workspace(const afc_mc_problem *prob);
 
 /* Adds the outcomes of realizations r_begin .. r_begin + r_count - 1 to counts, a DEVICE

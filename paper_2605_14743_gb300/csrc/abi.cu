@@ -121,8 +121,7 @@ int validate(const afc_mc_problem *p) {
   if (p->precision == AFC_FP32_RECHECK && !(p->recheck_margin >= 0.0)) return fail(AFC_EINVAL, "bad recheck_margin");
   const int B = auto_block(*p);
   if (B != 256 && B != 512 && B != 1024) return fail(AFC_EINVAL, "block_threads must be 256, 512 or 1024");
-  if (p->team_threads && !mc_config_supported(B, p->team_threads) &&
-      !big_config_supported(B, p->team_threads))
+  if (p->team_threads && !big_config_supported(B, p->team_threads))
     return fail(AFC_EINVAL, "team_threads %d not supported with block_threads %d", p->team_threads, B);
   if (p->slots_per_team < 0 || p->slots_per_team > kMaxSlotsPerTeam)
     return fail(AFC_EINVAL, "slots_per_team must be in [0, %d]", kMaxSlotsPerTeam);
@@ -174,46 +173,44 @@ McDev to_dev(const afc_mc_problem &p, uint32_t r_begin, uint32_t *counts, afc_mc
   return d;
 }
 
-// Launch plan of the counting kernel for a set of problems: block size, team size, slots
-// per team (sources a team advances together) and grid.
+// Launch plan of the shared-memory counting kernel for a set of problems: block size, source
+// warps (one source slot each: as many of the CTA's warps as shared memory holds slots for,
+// the other warps help with the per-realization steps only) and grid.
 struct McPlan {
-  int block = 1024, team = 256;
-  uint32_t spt = 1, smem = 0, grid = 1;
-  size_t ws_meta = 0, ws_total = 0;
+  int block = 1024;
+  uint32_t nsw = 1, smem = 0, grid = 1;
   bool fits = true;
 };
 
+// Source slots that fit next to the realization of an (n, arcs) graph within `bytes` of
+// shared memory.
+uint32_t slots_within(uint32_t n, uint64_t arcs, uint32_t bytes) {
+  const uint32_t base = mc_layout_bytes(n, arcs, 0);
+  const uint32_t one = mc_layout_bytes(n, arcs, 1) - base;
+  return base <= bytes ? (bytes - base) / one : 0u;
+}
+
+// want_warps: source warps the launch should offer (0: as many as fit for the largest graph;
+// a batched launch passes the most that any of its problems can use).
 McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t total_items,
-                int req_team, int req_spt) {
+                uint32_t want_warps = 0) {
   const DevInfo d = dev_info();
   McPlan pl;
-  pl.block = auto_block(p0);
-  const uint32_t base = mc_layout_bytes(nmax, amax, 0);
-  const uint32_t one = mc_layout_bytes(nmax, amax, 1) - base;
   const uint32_t cap = (uint32_t)std::max(0, d.smem_optin - 1024);
-  const uint32_t fit = base <= cap ? (cap - base) / one : 0u;
-  // preferred team sizes, largest team last so that small graphs / small shared memory work.
-  // Measured on ER and WS graphs of mean degree 8: one-warp teams wherever 32 of them fit
-  // (1.25-1.36x teams of 128 up to n = 300), then teams of 128, then larger teams
-  std::vector<int> prefs;
-  if (req_team) prefs.push_back(req_team);
-  else prefs = {32, 128, 64, 256, 512, 1024};
-  pl.fits = false;
-  for (int t : prefs) {
-    if (t > pl.block || !mc_config_supported(pl.block, t)) continue;
-    const uint32_t nt = (uint32_t)(pl.block / t);
-    if (fit < nt) continue;
-    if (nt * 1u > (uint32_t)kMaxTeams) continue;
-    uint32_t spt = std::min<uint32_t>({fit / nt, (uint32_t)kMaxSlotsPerTeam, (uint32_t)kMaxSlots / nt});
-    spt = std::min<uint32_t>(spt, std::max<uint32_t>(1u, (nmax + nt - 1) / nt));
-    if (req_spt) spt = std::min<uint32_t>(spt, (uint32_t)req_spt);
-    pl.team = t;
-    pl.spt = std::max<uint32_t>(1u, spt);
-    pl.fits = true;
-    break;
+  // node ids share their 16-bit settle-order entries with a step mark: below 2^15 nodes
+  const uint32_t fit = nmax < 32768u ? slots_within(nmax, amax, cap) : 0u;
+  if (p0.block_threads) {
+    pl.block = p0.block_threads;
+  } else {
+    // the smallest CTA that holds a warp for every slot that fits (fewer threads per CTA leave
+    // each thread more registers for the source warps' caches)
+    const uint32_t want = 32u * std::min<uint32_t>(std::max(fit, want_warps), 32u);
+    pl.block = want <= 256u ? 256 : want <= 512u ? 512 : 1024;
   }
+  pl.nsw = std::min<uint32_t>(fit, (uint32_t)pl.block / 32u);
+  pl.fits = pl.nsw >= 1;
   if (pl.fits) {
-    pl.smem = mc_layout_bytes(nmax, amax, (uint32_t)(pl.block / pl.team) * pl.spt);
+    pl.smem = mc_layout_bytes(nmax, amax, pl.nsw);
     const uint32_t smem_sm = 228u * 1024u;
     const uint32_t per_sm = std::max<uint32_t>(1u, std::min<uint32_t>(smem_sm / (pl.smem + 1024u),
                                                                       2048u / (uint32_t)pl.block));
@@ -301,20 +298,17 @@ uint64_t items_of(const afc_mc_problem &p, uint32_t r_count) {
 }
 
 bool smem_fits(const afc_mc_problem &p) {
-  return plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1, p.team_threads, p.slots_per_team).fits;
+  return plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1).fits;
 }
+
+// AFC_PATH_AUTO: the shared-memory path when shared memory holds at least this many source slots
+constexpr uint32_t kMinSharedSlots = 4;
 
 bool wants_global(const afc_mc_problem &p) {
   if (p.memory_path == AFC_PATH_GLOBAL) return true;
   if (p.memory_path == AFC_PATH_SHARED) return false;
-  const McPlan pl = plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1, p.team_threads,
-                             p.slots_per_team);
-  if (!pl.fits) return true;
-  // measured on ER and WS graphs of mean degree 8, n = 1,000 .. 2,400: once shared memory holds
-  // fewer than four teams' sources per CTA (one team of 512 or 1024 threads) the global-memory
-  // path with teams of 128 is faster (1.17x at n = 1,800, 1.9x at n = 2,400); with four teams
-  // of 256 the shared path still wins (1.4x at n = 1,600)
-  return p.team_threads == 0 && pl.block / pl.team < 4;
+  const McPlan pl = plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1);
+  return !pl.fits || pl.nsw < kMinSharedSlots;
 }
 
 size_t meta_bytes(int nprob) {
@@ -322,14 +316,49 @@ size_t meta_bytes(int nprob) {
          ~size_t(255);
 }
 
-// Workspace: [McDev x nprob][item prefix of the shared-path problems] then the global path's
-// groups, group arrays and slot arena (reused by the global-path problems one after another).
+// The shared-memory problems of a call, in launch order, and their launch: one persistent
+// kernel sized for the largest graph, each CTA with its region of device scratch.
+struct SharedBatch {
+  std::vector<int> order;
+  uint32_t nmax = 1;
+  uint64_t amax = 1, items = 0;
+  uint32_t want_warps = 0;
+  McPlan pl;
+  size_t scratch_stride = 0, scratch_bytes = 0;
+};
+
+SharedBatch shared_batch(int nprob, const afc_mc_problem *probs, const uint32_t *r_count) {
+  SharedBatch sb;
+  for (int g = 0; g < nprob; ++g)
+    if (!wants_global(probs[g])) sb.order.push_back(g);
+  if (sb.order.empty()) return sb;
+  const DevInfo di = dev_info();
+  const uint32_t cap = (uint32_t)std::max(0, di.smem_optin - 1024);
+  for (int g : sb.order) {
+    const afc_mc_problem &p = probs[g];
+    sb.nmax = std::max<uint32_t>(sb.nmax, (uint32_t)p.n);
+    sb.amax = std::max<uint64_t>(sb.amax, 2ull * (uint64_t)p.m);
+    // no count given: size for a launch that fills the GPU
+    sb.items += r_count ? items_of(p, r_count[g]) : (uint64_t)1 << 40;
+    if (sb.order.size() > 1)
+      sb.want_warps = std::max(sb.want_warps, slots_within((uint32_t)p.n, 2ull * (uint64_t)p.m, cap));
+  }
+  sb.pl = plan_for(probs[sb.order[0]], sb.nmax, sb.amax, std::max<uint64_t>(sb.items, 1),
+                   sb.want_warps);
+  sb.scratch_stride = (mc_cta_scratch_bytes(sb.nmax) + 255) & ~size_t(255);
+  sb.scratch_bytes = sb.pl.fits ? sb.scratch_stride * sb.pl.grid : 0;
+  return sb;
+}
+
+// Workspace: [McDev x nprob][item prefix of the shared-path problems], the shared path's CTA
+// scratch, then the global path's groups, group arrays and slot arena (reused by the
+// global-path problems one after another).
 size_t counts_ws_total(int nprob, const afc_mc_problem *probs, const uint32_t *r_count) {
   size_t big = 0;
   for (int g = 0; g < nprob; ++g)
     if (wants_global(probs[g]))
       big = std::max(big, plan_big(probs[g], r_count ? items_of(probs[g], r_count[g]) : 1u << 20).total);
-  return meta_bytes(nprob) + big;
+  return meta_bytes(nprob) + shared_batch(nprob, probs, r_count).scratch_bytes + big;
 }
 
 int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
@@ -351,8 +380,10 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
     }
   }
   // problems on the shared-memory path first (one persistent launch), then the others
-  std::vector<int> order, big;
-  for (int g = 0; g < nprob; ++g) (wants_global(probs[g]) ? big : order).push_back(g);
+  const SharedBatch sb = shared_batch(nprob, probs, r_count);
+  std::vector<int> order = sb.order, big;
+  for (int g = 0; g < nprob; ++g)
+    if (wants_global(probs[g])) big.push_back(g);
   const int ns = (int)order.size();
   for (int g : order)
     if (auto_block(probs[g]) != auto_block(probs[order[0]]))
@@ -360,17 +391,11 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   order.insert(order.end(), big.begin(), big.end());
   std::vector<McDev> devs(nprob);
   std::vector<uint64_t> prefix(ns + 1, 0);
-  uint32_t nmax = 1;
-  uint64_t amax = 1;
   for (int k = 0; k < nprob; ++k) {
     const int g = order[k];
     devs[k] = to_dev(probs[g], r_begin ? r_begin[g] : 0u, counts[g], stats ? stats[g] : nullptr,
                      nprob == 1 ? dump_bc : nullptr, nprob == 1 ? dump_next : nullptr);
-    if (k < ns) {
-      prefix[k + 1] = prefix[k] + items_of(probs[g], r_count[g]);
-      nmax = std::max<uint32_t>(nmax, (uint32_t)probs[g].n);
-      amax = std::max<uint64_t>(amax, 2ull * (uint64_t)probs[g].m);
-    }
+    if (k < ns) prefix[k + 1] = prefix[k] + items_of(probs[g], r_count[g]);
   }
   const size_t need = counts_ws_total(nprob, probs, r_count);
   if (!workspace || ws_bytes < need)
@@ -381,31 +406,27 @@ int run_counts(int nprob, const afc_mc_problem *probs, const uint32_t *r_begin,
   AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)nprob, cudaMemcpyHostToDevice, stream));
   AFC_CUDA(cudaMemcpyAsync(prefix_d, prefix.data(), sizeof(uint64_t) * (size_t)(ns + 1), cudaMemcpyHostToDevice, stream));
   if (ns > 0 && prefix[ns] > 0) {
-    const afc_mc_problem &p0 = probs[order[0]];
-    const McPlan pl = plan_for(p0, nmax, amax, prefix[ns], p0.team_threads, p0.slots_per_team);
+    const McPlan &pl = sb.pl;
     if (!pl.fits)
       return fail(AFC_EUNSUPPORTED, "batch too large for the shared-memory counting kernel");
     if (ns > 1) {
-      // every problem of a batched launch takes as many source slots per team as the launch's
-      // shared memory holds for its own size (the launch is sized for the largest graph)
-      const uint32_t nt = (uint32_t)(pl.block / pl.team);
-      const uint32_t cap = std::min<uint32_t>((uint32_t)kMaxSlotsPerTeam, (uint32_t)kMaxSlots / nt);
+      // every problem of a batched launch takes as many source warps as the launch's shared
+      // memory holds slots for at its own size (the launch is sized for the largest graph)
       for (int k = 0; k < ns; ++k) {
         const afc_mc_problem &p = probs[order[k]];
-        const uint32_t n = (uint32_t)p.n;
-        const uint64_t arcs = 2ull * (uint64_t)p.m;
-        uint32_t spt = p.slots_per_team ? std::min<uint32_t>((uint32_t)p.slots_per_team, cap)
-                                        : std::min<uint32_t>(cap, std::max<uint32_t>(1u, (n + nt - 1) / nt));
-        while (spt > 1 && mc_layout_bytes(n, arcs, nt * spt) > pl.smem) --spt;
-        devs[k].spt = spt;   // one slot per team always fits: the launch is sized for the largest
+        const uint32_t fit = slots_within((uint32_t)p.n, 2ull * (uint64_t)p.m, pl.smem);
+        devs[k].spt = std::max<uint32_t>(1u, std::min<uint32_t>(fit, (uint32_t)pl.block / 32u));
       }
       AFC_CUDA(cudaMemcpyAsync(devs_d, devs.data(), sizeof(McDev) * (size_t)ns, cudaMemcpyHostToDevice, stream));
     }
-    cudaError_t e = launch_mc_counts(pl.block, pl.team, devs_d, ns, prefix_d, prefix[ns], pl.spt,
-                                     pl.smem, pl.grid, stream);
+    // the shared batch's grid was sized for all its items: the launch may use fewer CTAs
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(pl.grid, prefix[ns]);
+    cudaError_t e = launch_mc_counts(pl.block, devs_d, ns, prefix_d, prefix[ns], pl.nsw, pl.smem,
+                                     std::max<uint32_t>(grid, 1u), ws + meta_bytes(nprob),
+                                     sb.scratch_stride, stream);
     if (e != cudaSuccess) return cuda_fail(e, "counting kernel launch");
   }
-  unsigned char *bigbase = ws + meta_bytes(nprob);
+  unsigned char *bigbase = ws + meta_bytes(nprob) + sb.scratch_bytes;
   for (int k = ns; k < nprob; ++k) {
     const afc_mc_problem &p = probs[order[k]];
     const uint32_t rc = (uint32_t)items_of(p, r_count[order[k]]);
@@ -566,8 +587,9 @@ int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *
   std::vector<uint32_t> widths;
   for (uint32_t w : {w0, w0 > 1 ? w0 / 2 : 1u, w0 * 2})
     if (std::find(widths.begin(), widths.end(), eff(w)) == widths.end()) widths.push_back(eff(w));
-  static const std::pair<int, int> kShared[] = {{1024, 32}, {1024, 128}, {1024, 256}, {1024, 1024},
-                                                 {512, 64}, {512, 512}, {256, 256}};
+  // shared-memory path: the CTA size (its warps are the source warps where slots fit; bucket
+  // widths do not apply); global path: (block, team) pairs and bucket widths
+  static const int kShared[] = {1024, 512, 256};
   static const std::pair<int, int> kGlobal[] = {{1024, 128}, {1024, 256}, {1024, 512}};
   // the automatic configuration first (it is also the warm-up), then the grid; a problem on
   // AFC_PATH_AUTO whose state fits in shared memory also tries the global-memory path
@@ -584,12 +606,11 @@ int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *
     if (path == AFC_PATH_SHARED && !smem_fits(c)) return;
     cands.push_back(c);
   };
-  for (uint32_t w : widths) {
-    if (!global)
-      for (const auto &sh : kShared) add(AFC_PATH_SHARED, sh.first, sh.second, w);
+  if (!global)
+    for (int blk : kShared) add(AFC_PATH_SHARED, blk, 0, w0);
+  for (uint32_t w : widths)
     if (global || base.memory_path == AFC_PATH_AUTO)
       for (const auto &sh : kGlobal) add(AFC_PATH_GLOBAL, sh.first, sh.second, w);
-  }
   abi_error_text().clear();
   size_t ws = 0;
   for (const auto &c : cands) ws = std::max(ws, counts_ws_total(1, &c, &sample));
@@ -642,10 +663,8 @@ int afc_autotune(afc_mc_problem *prob, uint32_t r_begin, uint32_t sample, void *
       prob->block_threads = bp.block;
       prob->team_threads = bp.team;
     } else {
-      const McPlan pl = plan_for(base, (uint32_t)base.n, 2ull * (uint64_t)base.m, sample,
-                                 base.team_threads, base.slots_per_team);
+      const McPlan pl = plan_for(base, (uint32_t)base.n, 2ull * (uint64_t)base.m, sample);
       prob->block_threads = pl.block;
-      prob->team_threads = pl.team;
     }
   } else {
     prob->block_threads = w.block_threads;
@@ -694,12 +713,11 @@ int afc_debug_sssp(const afc_mc_problem *prob, uint32_t r, const int32_t *source
   if (st) return st;
   if (nsrc < 0 || (nsrc > 0 && (!sources || !dist || !sigma))) return fail(AFC_EINVAL, "bad outputs");
   if (nsrc == 0) return AFC_OK;
-  const McPlan pl = plan_for(*prob, (uint32_t)prob->n, 2ull * (uint64_t)prob->m, (uint64_t)nsrc,
-                             prob->team_threads, prob->slots_per_team);
+  const McPlan pl = plan_for(*prob, (uint32_t)prob->n, 2ull * (uint64_t)prob->m, (uint64_t)nsrc);
   if (!pl.fits) return fail(AFC_EUNSUPPORTED, "graph too large for the shared-memory SSSP kernel");
   McDev d = to_dev(*prob, 0, nullptr, stats, nullptr, nullptr);
-  cudaError_t e = launch_debug_sssp(pl.block, pl.team, d, r, sources, nsrc, pl.spt, pl.smem, dist,
-                                    sigma, (cudaStream_t)stream);
+  cudaError_t e = launch_debug_sssp(pl.block, d, r, sources, nsrc, pl.nsw, pl.smem, dist, sigma,
+                                    (cudaStream_t)stream);
   return e == cudaSuccess ? AFC_OK : cuda_fail(e, "debug_sssp");
 }
 

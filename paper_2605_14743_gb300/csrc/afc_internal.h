@@ -35,7 +35,7 @@ struct McDev {
   int32_t precision;
   double recheck_margin;
   uint32_t delta;
-  uint32_t spt;          // shared path: sources per team for this problem (0: launch default)
+  uint32_t spt;          // shared path: source warps for this problem (0: the launch's value)
   uint32_t r_begin;
   uint32_t reward_k;             // valued Top-k step reward (0: off)
   const double *reward_gamma;    // [n] or null (1)
@@ -72,20 +72,28 @@ struct TeamCtl {
 };
 
 // Per-warp scratch of the warp-cooperative arc loops: accumulators of the current chunk of
-// 32 items (one per lane) and the rank -> lane table of the chunk's items that have arcs.
+// 32 items (one per lane), the floating contributions of the current window of 32 arc
+// positions (summed by their owners in arc order, so sums never depend on the schedule) and
+// the rank -> lane table of the chunk's items that have arcs.
 struct WarpScratch {
   unsigned long long acc[32];
+  double buf[32];
   uint32_t acci[32];
   uint32_t flags[32];
   uint8_t table[32];
 };
 
-struct CtaCtl {
+// Control fields of a CTA that works on one realization (realization, components, selection).
+struct CtaHead {
   uint32_t err, ovf, nsrc, cursor;
   unsigned long long edges, verts;
   uint32_t need_recheck, delta, dsh, wmax;
   uint32_t scan[32];
   uint32_t scan_total, pad1, pad2, pad3;
+};
+
+// The bucketed kernel's control block: the head plus its slot, team and warp tables.
+struct CtaCtl : CtaHead {
   SlotCtl slot[kMaxSlots];
   TeamCtl team[kMaxTeams];
   WarpScratch warp[32];
@@ -98,9 +106,12 @@ struct BigGroup {
   uint32_t active;       // 1 while the group holds a realization of the current batch
   uint32_t nsrc, cursor, dsh, err, ovf, redo;
   unsigned long long edges, verts;
-  uint32_t *rp, *arc, *comp, *cinfo, *bci, *centre, *rank;
+  uint32_t *rp, *arc, *comp, *cinfo, *centre, *rank;
   uint16_t *src;
+  // betweenness: 128-bit fixed point accumulated as (bhi, bc's bits) with 64 fraction bits,
+  // converted to doubles in place (bc) before the selection
   double *bc;
+  unsigned long long *bhi;
   unsigned long long *best;
 };
 
@@ -139,22 +150,24 @@ afc_result *build_result(int32_t n, uint32_t R, const uint32_t *dense, const dou
                          const double *s, const double *f, double tie_rel, void *stream);
 afc_host_query host_query_of(const afc_graph *g, const afc_params *p, uint32_t n_perturb);
 
-// mc_kernel.cu
-uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nslots);
-// team sizes with a kernel instantiation for a given block size
-bool mc_config_supported(int block, int team);
-cudaError_t launch_mc_counts(int block, int team, const McDev *probs_dev, int nprob,
+// mc_kernel.cu: the shared-memory path (one warp per source, settle steps)
+// Shared memory of a counting CTA of the shared-memory path: a graph of n nodes and `arcs`
+// arcs, and `nsw` warps that each own one source slot.
+uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nsw);
+// Device memory of one counting CTA of the shared-memory path (graphs of up to n nodes):
+// components, source list, selection scratch and betweenness accumulators.
+size_t mc_cta_scratch_bytes(uint32_t n);
+cudaError_t launch_mc_counts(int block, const McDev *probs_dev, int nprob,
                              const uint64_t *prefix_dev, uint64_t total_items,
-                             uint32_t slots_per_team, uint32_t smem_bytes, uint32_t grid,
-                             cudaStream_t stream);
+                             uint32_t source_warps, uint32_t smem_bytes, uint32_t grid,
+                             unsigned char *scratch, size_t scratch_stride, cudaStream_t stream);
 cudaError_t launch_debug_realize(const McDev &P, uint32_t r_count, uint8_t *alive, uint32_t *w,
                                  cudaStream_t stream);
 cudaError_t launch_debug_components(const McDev &P, uint32_t r_count, int32_t *comp,
                                     int32_t *csize, cudaStream_t stream);
-cudaError_t launch_debug_sssp(int block, int team, const McDev &P, uint32_t r,
-                              const int32_t *sources, int32_t nsrc, uint32_t slots_per_team,
-                              uint32_t smem, uint32_t *dist, uint64_t *sigma,
-                              cudaStream_t stream);
+cudaError_t launch_debug_sssp(int block, const McDev &P, uint32_t r, const int32_t *sources,
+                              int32_t nsrc, uint32_t source_warps, uint32_t smem, uint32_t *dist,
+                              uint64_t *sigma, cudaStream_t stream);
 
 // solve.cu / perturb.cu
 struct ChainDev {

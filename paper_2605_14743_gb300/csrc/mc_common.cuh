@@ -1,11 +1,12 @@
 // mc_common.cuh -- device routines of the Monte Carlo counting path shared by the
 // shared-memory kernel (graphs that fit on chip) and the global-memory kernels (larger
-// graphs): realization, components, the batched bucketed Brandes routine and selection.
+// graphs): realization, components, the exact betweenness accumulators, the warp-cooperative
+// arc loop, the bucketed Brandes routine of the global path and selection.
 //
-// Per source ("slot") state: dist[n] (u32 distance | flag), sig[n] (u64: last relaxed
-// distance while tentative, then sigma, then rho = (1 + delta) / sigma in the same slot),
-// ord[n] (u16 settled vertices grouped by bucket) and a ring of kRing bucket bitmaps that
-// holds the discovered-but-unsettled vertices by bucket.
+// Per source ("slot") state of the bucketed routine: dist[n] (u32 distance | flag), sig[n]
+// (u64: last relaxed distance while tentative, then sigma, then rho = (1 + delta) / sigma in
+// the same slot), ord[n] (u16 settled vertices grouped by bucket) and a ring of kRing bucket
+// bitmaps that holds the discovered-but-unsettled vertices by bucket.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -39,28 +40,6 @@ __host__ __device__ __forceinline__ uint32_t slot_bytes_for(uint32_t n) {
   return al16(4u * n) + al16(8u * n) + al16(2u * n) + al16(4u * kRing * words);
 }
 
-// Shared-memory layout of one CTA for a graph of n nodes, `arcs` arcs and S source slots.
-struct Layout {
-  uint32_t off_rp, off_arc, off_comp, off_cinfo, off_bc, off_bci, off_src, off_sel, off_slots;
-  uint32_t slot_bytes, words, total;
-  __host__ __device__ static uint32_t al(uint32_t x) { return al16(x); }
-  __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t nslots) {
-    words = (n + 31u) / 32u;
-    uint32_t o = al(sizeof(CtaCtl));
-    off_rp = o;     o = al(o + 4u * (n + 1));
-    off_arc = o;    o = al(o + 4u * (arcs > 0 ? arcs : 1));
-    off_comp = o;   o = al(o + 4u * n);
-    off_cinfo = o;  o = al(o + 4u * n);
-    off_bc = o;     o = al(o + 8u * n);
-    off_bci = o;    o = al(o + 4u * n);
-    off_src = o;    o = al(o + 2u * (n > nslots ? n : nslots));
-    off_sel = o;    o = al(o + 4u * n);
-    off_slots = o;
-    slot_bytes = slot_bytes_for(n);
-    total = o + nslots * slot_bytes;
-  }
-};
-
 struct SlotArrays {
   uint32_t *dist;
   uint64_t *sig;
@@ -89,10 +68,6 @@ __device__ __forceinline__ SlotArrays slot_arrays(const SlotSpace &sp, uint32_t 
   a.ord = reinterpret_cast<uint16_t *>(p);   p += al16(2u * n);
   a.ring = reinterpret_cast<uint32_t *>(p);
   return a;
-}
-
-__device__ __forceinline__ SlotSpace smem_slots(unsigned char *smem, const Layout &L, uint32_t n) {
-  return SlotSpace{smem + L.off_slots, L.slot_bytes, n, L.words};
 }
 
 struct Realized {
@@ -168,12 +143,18 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *pref, uint32_t S, 
 // w0 + L, so a warp's time follows its total arc count instead of its heaviest lane.  For
 // each position f(valid, owner_lane, arc[arc_index]) runs on every lane (valid = false past
 // the end, arc word 0 then); f fetches the owner's item data with __shfl_sync from owner_lane.
-// All 32 lanes must call it (warp-uniform control flow).  Returns at once when no lane has
-// arcs.  PREFETCH (arcs in device memory) issues the next window's arc loads before f runs on
-// the current window, so their latency overlaps f's work.
-template <bool PREFETCH, typename F>
+// After f, g(lo, hi) runs on every lane with [lo, hi) the positions of the window (0..32) that
+// belong to the lane's own item (lo == hi when none): the owner can then read, in arc order,
+// what f left per position.  All 32 lanes must call it (warp-uniform control flow).  Returns
+// at once when no lane has arcs.  PREFETCH (arcs in device memory) issues the next window's
+// arc loads before f runs on the current window, so their latency overlaps f's work.
+struct NoWindowHook {
+  __device__ __forceinline__ void operator()(uint32_t, uint32_t) const {}
+};
+
+template <bool PREFETCH, typename F, typename G = NoWindowHook>
 __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *table,
-                                          const uint32_t *arc, F &&f) {
+                                          const uint32_t *arc, F &&f, G &&g = G{}) {
   const uint32_t lane = lane_id();
   const uint32_t nz = __ballot_sync(kFull, deg > 0);
   if (nz == 0u) return;
@@ -201,6 +182,11 @@ __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *ta
     e = oe0 + (pos - oex);
     prior += __popc(starts);
   };
+  // this lane's own positions inside the window starting at w0
+  auto own = [&](uint32_t w0) {
+    const uint32_t a = max(excl, w0), b = min(excl + deg, w0 + 32u);
+    return a < b ? make_uint2(a - w0, b - w0) : make_uint2(0u, 0u);
+  };
   if constexpr (PREFETCH) {
     bool valid;
     uint32_t ol, e;
@@ -215,6 +201,8 @@ __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *ta
         npk = nvalid ? arc[ne] : 0u;
       }
       f(valid, ol, pk);
+      const uint2 r = own(w0);
+      g(r.x, r.y);
       valid = nvalid;
       ol = nol;
       pk = npk;
@@ -225,22 +213,88 @@ __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *ta
       uint32_t ol, e;
       locate(w0, valid, ol, e);
       f(valid, ol, valid ? arc[e] : 0u);
+      const uint2 r = own(w0);
+      g(r.x, r.y);
     }
   }
   __syncwarp();
 }
 
+// Betweenness accumulators: B_v = sum over sources of delta_s(v), kept exactly as a 128-bit
+// fixed-point number with 64 fraction bits in two 64-bit words (hi: integer part and carries,
+// lo: fraction).  Every addend x (0 <= x < 2^64) is split exactly, from its bits, into the
+// integer part and the fraction scaled by 2^64 (truncated below 2^-64, i.e. exact whenever
+// x >= 2^-12); integer additions are associative, so the sum does not depend on the order in
+// which sources finish, and B is the same bit for bit whatever the launch shape.  Unique-path
+// dependencies (exact integers) go straight to hi.  Integer operations only: no FP64 work.
+__device__ __forceinline__ void fx_add(unsigned long long *lo, unsigned long long *hi, uint32_t v,
+                                       double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FFu);
+  if (ex == 0 || (b >> 63)) return;   // zero (or a subnormal far below 2^-64); never negative
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // x = m 2^(ex - 1075)
+  const int sh = ex - 1075 + 64;   // x 2^64 = m 2^sh
+  unsigned long long xi, xf;
+  if (sh >= 64) {
+    xi = m << (sh - 64);
+    xf = 0ull;
+  } else if (sh > 0) {
+    xi = m >> (64 - sh);
+    xf = m << sh;
+  } else if (sh > -53) {
+    xi = 0ull;
+    xf = m >> (-sh);
+  } else {
+    return;
+  }
+  if (xf) {
+    const unsigned long long old = atomicAdd(&lo[v], xf);
+    if (old + xf < old) ++xi;   // carry out of the fraction word
+  }
+  if (xi) atomicAdd(&hi[v], xi);
+}
+
+// Correctly rounded reciprocal in the dependency precision.
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
+// The dependency step of v from acc = sum of its successors' rho (Sec. 3.1, Brandes):
+// delta(v) = sigma(v) acc and rho(v) = (1 + delta(v)) / sigma(v) = acc + 1 / sigma(v).
+template <typename DT>
+__device__ __forceinline__ void dependency(uint64_t sg, DT acc, DT &dep, DT &rho) {
+  if (sg == 1ull) {
+    dep = acc;
+    rho = (DT)1 + dep;
+  } else {
+    const DT sv = (DT)sg;
+    dep = sv * acc;
+    rho = acc + recip(sv);
+  }
+}
+
+// The accumulated value as a double, in the storage of the fraction word (B = hi + lo 2^-64;
+// each thread converts its own entries).
+__device__ __forceinline__ void fx_finalize(unsigned long long *lo, const unsigned long long *hi,
+                                            uint32_t n) {
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const double b = (double)hi[v] + __ull2double_rn(lo[v]) * 0x1p-64;
+    reinterpret_cast<double *>(lo)[v] = b;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
-// A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) advanced in lockstep by
-// one team.  Adds delta_s(v) to bc[v] for v != s.  With want_delta = false it stops after
-// distances and path counts (parity hook).  Every thread of the team must call it.
+// Bucketed Brandes for graphs whose per-source state does not fit on chip (the global-memory
+// path).  A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) is advanced in
+// lockstep by one team, bucket by bucket (integer Delta-stepping), every pass warp-cooperative
+// over the members' arcs.  Adds delta_s(v) for v != s to the fixed-point accumulators
+// (blo, bhi) of fx_add.  Every thread of the team must call it.
 // ---------------------------------------------------------------------------------------
-template <int TS, int BLOCK, typename DT, bool FLAT = false>
+template <int TS, int BLOCK, typename DT>
 __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H,
                                               const SlotSpace &sp, uint32_t slot0, uint32_t S,
-                                              const uint16_t *srcs, uint32_t dsh, double *bc,
-                                              uint32_t *bci, bool want_delta, CtaCtl *ctl,
-                                              uint32_t *err_out, uint32_t *ovf_out) {
+                                              const uint16_t *srcs, uint32_t dsh,
+                                              unsigned long long *blo, unsigned long long *bhi,
+                                              CtaCtl *ctl, uint32_t *err_out, uint32_t *ovf_out) {
   const uint32_t n = H.n, W = sp.words;
   constexpr uint32_t kRingMask = kRing - 1u;
   const uint32_t tid = team.rank;
@@ -367,7 +421,7 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             }
           }
         }
-        warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
+        warp_arcs<true>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
           const uint32_t oi = __shfl_sync(kFull, i, ol);
           const uint32_t od = __shfl_sync(kFull, d, ol);
           if (!valid) return;
@@ -400,112 +454,69 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
     if (!ok) break;
     // path counts of the bucket.  A member is final once all its predecessors are (earlier
     // buckets are); it then publishes sigma before its flag (fence), and a reader that sees
-    // the flag of a same-bucket predecessor fences before reading that sigma.
+    // the flag of a same-bucket predecessor fences before reading that sigma.  All arcs of the
+    // open members are walked warp-cooperatively, sums through per-warp accumulators (exact
+    // 64-bit integers)
     slot_prefix(tc, tid, S, [&](uint32_t i) { return min(sl[i].nm, n) - sl[i].mstart; });
     team.sync();
     const uint32_t total = tc->pref[S];
     const uint32_t dstart = b << dsh;
-    if constexpr (FLAT) {
-    // warp-cooperative: all arcs of the open members, sums through per-warp accumulators
-      for (uint32_t pass = 0;; ++pass) {
-        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-        bool open = false;
-        for (uint32_t base = 0; base < total; base += TS) {
-          const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
-          uint32_t i = 0, v = 0, dv = 0, e0 = 0, deg = 0;
-          ws->acc[lane] = 0ull;
-          ws->flags[lane] = 0u;
-          if (k < total) {
-            i = find_slot(tc->pref, S, k);
-            SlotArrays a = slot_arrays(sp, slot0 + i);
-            v = a.ord[sl[i].mstart + k - tc->pref[i]];
-            if (v >= n) {
-              my_err |= kErrCapacity;
-            } else {
-              dv = a.dist[v];
-              if (!(dv & kFlag)) {
-                if (v == sl[i].s) {
-                  a.sig[v] = 1ull;
-                  __threadfence_block();
-                  st_volatile(&a.dist[v], dv | kFlag);
-                } else {
-                  e0 = H.rp[v];
-                  deg = H.rp[v + 1] - e0;
-                }
+    for (uint32_t pass = 0;; ++pass) {
+      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+      bool open = false;
+      for (uint32_t base = 0; base < total; base += TS) {
+        const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+        uint32_t i = 0, v = 0, dv = 0, e0 = 0, deg = 0;
+        ws->acc[lane] = 0ull;
+        ws->flags[lane] = 0u;
+        if (k < total) {
+          i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(sp, slot0 + i);
+          v = a.ord[sl[i].mstart + k - tc->pref[i]];
+          if (v >= n) {
+            my_err |= kErrCapacity;
+          } else {
+            dv = a.dist[v];
+            if (!(dv & kFlag)) {
+              if (v == sl[i].s) {
+                a.sig[v] = 1ull;
+                __threadfence_block();
+                st_volatile(&a.dist[v], dv | kFlag);
+              } else {
+                e0 = H.rp[v];
+                deg = H.rp[v + 1] - e0;
               }
             }
           }
-          // sum sigma over the predecessors; one that is not final yet leaves the member open
-          warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
-            const uint32_t oi = __shfl_sync(kFull, i, ol);
-            const uint32_t odv = __shfl_sync(kFull, dv, ol);
-            if (!valid) return;
-            SlotArrays a = slot_arrays(sp, slot0 + oi);
-            const uint32_t u = pk & 0xFFFFu;
-            const uint32_t du = a.dist[u];
-            if ((du & kMask) + (pk >> 16) != odv) return;
-            if (!(du & kFlag)) { atomicOr(&ws->flags[ol], 1u); return; }
-            if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
-            const unsigned long long x = a.sig[u];
-            const unsigned long long prev = atomicAdd(&ws->acc[ol], x);
-            if (prev + x < prev) my_ovf = 1;
-          });
-          if (deg > 0) {
-            SlotArrays a = slot_arrays(sp, slot0 + i);
-            if (!(ws->flags[lane] & 1u)) {
-              a.sig[v] = ws->acc[lane];
-              __threadfence_block();
-              st_volatile(&a.dist[v], dv | kFlag);
-            } else {
-              open = true;
-            }
-          }
-          __syncwarp();
         }
-        if (!team.any(open)) break;
-      }
-    } else {
-    // one member per thread, stopping at the first predecessor that is not final
-      for (uint32_t pass = 0;; ++pass) {
-        if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-        bool open = false;
-        for (uint32_t base = 0; base < total; base += TS) {
-          const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
-          if (k >= total) continue;
-          const uint32_t i = find_slot(tc->pref, S, k);
+        // sum sigma over the predecessors; one that is not final yet leaves the member open
+        warp_arcs<true>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
+          const uint32_t oi = __shfl_sync(kFull, i, ol);
+          const uint32_t odv = __shfl_sync(kFull, dv, ol);
+          if (!valid) return;
+          SlotArrays a = slot_arrays(sp, slot0 + oi);
+          const uint32_t u = pk & 0xFFFFu;
+          const uint32_t du = a.dist[u];
+          if ((du & kMask) + (pk >> 16) != odv) return;
+          if (!(du & kFlag)) { atomicOr(&ws->flags[ol], 1u); return; }
+          if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
+          const unsigned long long x = a.sig[u];
+          const unsigned long long prev = atomicAdd(&ws->acc[ol], x);
+          if (prev + x < prev) my_ovf = 1;
+        });
+        if (deg > 0) {
           SlotArrays a = slot_arrays(sp, slot0 + i);
-          const uint32_t v = a.ord[sl[i].mstart + k - tc->pref[i]];
-          if (v >= n) { my_err |= kErrCapacity; continue; }
-          const uint32_t dv = a.dist[v];
-          if (dv & kFlag) continue;
-          uint64_t acc = 0;
-          bool all_final = true;
-          if (v == sl[i].s) {
-            acc = 1;
-          } else {
-            const uint32_t e1 = H.rp[v + 1];
-            for (uint32_t e = H.rp[v]; e < e1; ++e) {
-              const uint32_t pk = H.arc[e];
-              const uint32_t u = pk & 0xFFFFu;
-              const uint32_t du = a.dist[u];
-              if ((du & kMask) + (pk >> 16) != dv) continue;
-              if (!(du & kFlag)) { all_final = false; break; }
-              if ((du & kMask) >= dstart) __threadfence_block();   // same-bucket predecessor
-              const uint64_t nx = acc + a.sig[u];
-              if (nx < acc) my_ovf = 1;
-              acc = nx;
-            }
-          }
-          if (all_final) {
-            a.sig[v] = acc;
+          if (!(ws->flags[lane] & 1u)) {
+            a.sig[v] = ws->acc[lane];
             __threadfence_block();
             st_volatile(&a.dist[v], dv | kFlag);
           } else {
             open = true;
           }
         }
-        if (!team.any(open)) break;
+        __syncwarp();
       }
+      if (!team.any(open)) break;
     }
     if (!ok) break;
     for (uint32_t i = tid; i < S; i += TS) sl[i].mstart = min(sl[i].nm, n);
@@ -519,237 +530,183 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
   }
 
   // ---- backward: dependencies, buckets in decreasing order; kFlag = "delta pending"
-  if (want_delta) {
-    // where each bucket's run of the settled list starts: bit p of a bitmap over list
-    // positions, set when ord[p] opens a new bucket (kept in the ring words, unused from here on)
-    for (uint32_t i = 0; i < S; ++i) {
-      SlotArrays a = slot_arrays(sp, slot0 + i);
-      const uint32_t cnt = sl[i].mstart;
-      for (uint32_t base = 0; base < cnt; base += TS) {   // TS is a multiple of 32
-        const uint32_t p = base + tid;
-        bool start = false;
-        if (p < cnt) {
-          const uint32_t v = a.ord[p];
-          const uint32_t bv = v < n ? (a.dist[v] & kMask) >> dsh : 0xFFFFFFFFu;
-          uint32_t bu = 0xFFFFFFFEu;
-          if (p > 0) {
-            const uint32_t u = a.ord[p - 1];
-            bu = u < n ? (a.dist[u] & kMask) >> dsh : 0xFFFFFFFFu;
-          }
-          start = bu != bv;
+  // where each bucket's run of the settled list starts: bit p of a bitmap over list
+  // positions, set when ord[p] opens a new bucket (kept in the ring words, unused from here on)
+  for (uint32_t i = 0; i < S; ++i) {
+    SlotArrays a = slot_arrays(sp, slot0 + i);
+    const uint32_t cnt = sl[i].mstart;
+    for (uint32_t base = 0; base < cnt; base += TS) {   // TS is a multiple of 32
+      const uint32_t p = base + tid;
+      bool start = false;
+      if (p < cnt) {
+        const uint32_t v = a.ord[p];
+        const uint32_t bv = v < n ? (a.dist[v] & kMask) >> dsh : 0xFFFFFFFFu;
+        uint32_t bu = 0xFFFFFFFEu;
+        if (p > 0) {
+          const uint32_t u = a.ord[p - 1];
+          bu = u < n ? (a.dist[u] & kMask) >> dsh : 0xFFFFFFFFu;
         }
-        const uint32_t word = __ballot_sync(kFull, start);
-        const uint32_t p0 = base + (tid & ~31u);
-        if (lane == 0 && p0 < cnt) a.ring[p0 >> 5] = word;
+        start = bu != bv;
       }
+      const uint32_t word = __ballot_sync(kFull, start);
+      const uint32_t p0 = base + (tid & ~31u);
+      if (lane == 0 && p0 < cnt) a.ring[p0 >> 5] = word;
     }
-    for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].mstart;
+  }
+  for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].mstart;
+  team.sync();
+  for (uint32_t guard = 0;; ++guard) {
+    if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
+    if (tid < 32) {
+      uint32_t best = 0;  // 1 + bucket id of the last unprocessed member, 0 if none
+      if (lane < S) {
+        const uint32_t hi = sl[lane].hi;
+        if (hi > 0) {
+          SlotArrays a = slot_arrays(sp, slot0 + lane);
+          const uint32_t v = a.ord[hi - 1];
+          best = v < n ? ((a.dist[v] & kMask) >> dsh) + 1u : 1u;
+        }
+      }
+      best = __reduce_max_sync(kFull, best);
+      if (lane == 0) tc->bucket = best;
+    }
     team.sync();
-    for (uint32_t guard = 0;; ++guard) {
-      if (guard > 2u * n + 2u) { my_err |= kErrPassLimit; ok = false; break; }
-      if (tid < 32) {
-        uint32_t best = 0;  // 1 + bucket id of the last unprocessed member, 0 if none
-        if (lane < S) {
-          const uint32_t hi = sl[lane].hi;
-          if (hi > 0) {
-            SlotArrays a = slot_arrays(sp, slot0 + lane);
-            const uint32_t v = a.ord[hi - 1];
-            best = v < n ? ((a.dist[v] & kMask) >> dsh) + 1u : 1u;
+    const uint32_t bb = tc->bucket;
+    if (bb == 0) break;
+    const uint32_t bcur = bb - 1u;
+    // per slot: start of the run of bucket bcur at the end of its settled list
+    for (uint32_t i = warp; i < S; i += NW) {
+      SlotArrays a = slot_arrays(sp, slot0 + i);
+      const uint32_t hi = sl[i].hi;
+      uint32_t lo = hi;
+      const uint32_t vh = hi > 0 ? a.ord[hi - 1] : 0u;
+      if (hi > 0 && vh < n && ((a.dist[vh] & kMask) >> dsh) == bcur) {
+        // the run's start: the highest start bit at or below position hi - 1 (bit 0 is set),
+        // 32 bitmap words per step, lane l taking the l-th word down
+        lo = 0;
+        const int32_t wtop = (int32_t)((hi - 1u) >> 5);
+        for (int32_t w0 = wtop; w0 >= 0; w0 -= 32) {
+          const int32_t w = w0 - (int32_t)lane;
+          uint32_t word = 0;
+          if (w >= 0) {
+            word = a.ring[w];
+            if (w == wtop) word &= (2u << ((hi - 1u) & 31u)) - 1u;
+          }
+          const uint32_t nz = __ballot_sync(kFull, word != 0u);
+          if (nz) {
+            const uint32_t l = __ffs(nz) - 1;
+            const uint32_t wl = __shfl_sync(kFull, word, l);
+            lo = (uint32_t)(w0 - (int32_t)l) * 32u + 31u - __clz(wl);
+            break;
           }
         }
-        best = __reduce_max_sync(kFull, best);
-        if (lane == 0) tc->bucket = best;
       }
-      team.sync();
-      const uint32_t bb = tc->bucket;
-      if (bb == 0) break;
-      const uint32_t bcur = bb - 1u;
-      // per slot: start of the run of bucket bcur at the end of its settled list
-      for (uint32_t i = warp; i < S; i += NW) {
-        SlotArrays a = slot_arrays(sp, slot0 + i);
-        const uint32_t hi = sl[i].hi;
-        uint32_t lo = hi;
-        const uint32_t vh = hi > 0 ? a.ord[hi - 1] : 0u;
-        if (hi > 0 && vh < n && ((a.dist[vh] & kMask) >> dsh) == bcur) {
-          // the run's start: the highest start bit at or below position hi - 1 (bit 0 is set),
-          // 32 bitmap words per step, lane l taking the l-th word down
-          lo = 0;
-          const int32_t wtop = (int32_t)((hi - 1u) >> 5);
-          for (int32_t w0 = wtop; w0 >= 0; w0 -= 32) {
-            const int32_t w = w0 - (int32_t)lane;
-            uint32_t word = 0;
-            if (w >= 0) {
-              word = a.ring[w];
-              if (w == wtop) word &= (2u << ((hi - 1u) & 31u)) - 1u;
-            }
-            const uint32_t nz = __ballot_sync(kFull, word != 0u);
-            if (nz) {
-              const uint32_t l = __ffs(nz) - 1;
-              const uint32_t wl = __shfl_sync(kFull, word, l);
-              lo = (uint32_t)(w0 - (int32_t)l) * 32u + 31u - __clz(wl);
-              break;
+      if (lane == 0) sl[i].lo = lo;
+    }
+    team.sync();
+    slot_prefix(tc, tid, S, [&](uint32_t i) { return sl[i].hi - sl[i].lo; });
+    team.sync();
+    const uint32_t total = tc->pref[S];
+    const uint32_t dhi = (bcur << dsh) + (1u << dsh);
+    for (uint32_t pass = 0;; ++pass) {
+      if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
+      bool open = false;
+      for (uint32_t base = 0; base < total; base += TS) {
+        const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
+        uint32_t i = 0, v = 0, dvm = 0, e0 = 0, deg = 0;
+        ws->acci[lane] = 0u;      // integral part of the successors' rho
+        ws->flags[lane] = 0u;     // bit 0: a successor is still pending
+        if (k < total) {
+          i = find_slot(tc->pref, S, k);
+          SlotArrays a = slot_arrays(sp, slot0 + i);
+          v = a.ord[sl[i].lo + k - tc->pref[i]];
+          if (v >= n) {
+            my_err |= kErrCapacity;
+          } else {
+            const uint32_t dv = a.dist[v];
+            if (dv & kFlag) {
+              dvm = dv & kMask;
+              e0 = H.rp[v];
+              deg = H.rp[v + 1] - e0;
+              if (deg == 0) deg = 0x80000000u;   // marker: pending, no arcs
             }
           }
         }
-        if (lane == 0) sl[i].lo = lo;
-      }
-      team.sync();
-      slot_prefix(tc, tid, S, [&](uint32_t i) { return sl[i].hi - sl[i].lo; });
-      team.sync();
-      const uint32_t total = tc->pref[S];
-      const uint32_t dlo = bcur << dsh, dhi = dlo + (1u << dsh);
-      (void)dlo;
-      if constexpr (FLAT) {
-        for (uint32_t pass = 0;; ++pass) {
-          if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-          bool open = false;
-          for (uint32_t base = 0; base < total; base += TS) {
-            const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
-            uint32_t i = 0, v = 0, dvm = 0, e0 = 0, deg = 0;
-            ws->acc[lane] = 0ull;     // FP part of the successors' rho (as DT)
-            ws->acci[lane] = 0u;      // integral part
-            ws->flags[lane] = 0u;     // bit 0: a successor is pending; bit 1: some rho not integral
-            if (k < total) {
-              i = find_slot(tc->pref, S, k);
-              SlotArrays a = slot_arrays(sp, slot0 + i);
-              v = a.ord[sl[i].lo + k - tc->pref[i]];
-              if (v >= n) {
-                my_err |= kErrCapacity;
-              } else {
-                const uint32_t dv = a.dist[v];
-                if (dv & kFlag) {
-                  dvm = dv & kMask;
-                  e0 = H.rp[v];
-                  deg = H.rp[v + 1] - e0;
-                  if (deg == 0) deg = 0x80000000u;   // marker: pending, no arcs
-                }
-              }
-            }
-            const bool pending = deg != 0;
-            if (deg == 0x80000000u) deg = 0;
-            warp_arcs<FLAT>(deg, e0, ws->table, H.arc, [&](bool valid, uint32_t ol, uint32_t pk) {
+        const bool pending = deg != 0;
+        if (deg == 0x80000000u) deg = 0;
+        // the successors' rho: integral ones summed exactly, the others by the owner in arc
+        // order (so the sum is the same whatever the window split)
+        DT acc_f = 0;
+        bool any_f = false;
+        uint32_t fpm = 0;
+        warp_arcs<true>(
+            deg, e0, ws->table, H.arc,
+            [&](bool valid, uint32_t ol, uint32_t pk) {
               const uint32_t oi = __shfl_sync(kFull, i, ol);
               const uint32_t odv = __shfl_sync(kFull, dvm, ol);
-              if (!valid) return;
-              SlotArrays a = slot_arrays(sp, slot0 + oi);
-              const uint32_t w = pk & 0xFFFFu;
-              const uint32_t dw = a.dist[w];
-              if ((dw & kMask) != odv + (pk >> 16)) return;
-              if (dw & kFlag) { atomicOr(&ws->flags[ol], 1u); return; }
-              if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
-              const uint64_t rw = a.sig[w];
-              if (rw & kIntTag) {
-                atomicAdd(&ws->acci[ol], (uint32_t)rw);
-              } else {
-                atomicAdd(reinterpret_cast<DT *>(&ws->acc[ol]), *reinterpret_cast<const DT *>(&rw));
-                atomicOr(&ws->flags[ol], 2u);
+              bool fp = false;
+              double x = 0.0;
+              if (valid) {
+                SlotArrays a = slot_arrays(sp, slot0 + oi);
+                const uint32_t w = pk & 0xFFFFu;
+                const uint32_t dw = a.dist[w];
+                if ((dw & kMask) == odv + (pk >> 16)) {
+                  if (dw & kFlag) {
+                    atomicOr(&ws->flags[ol], 1u);
+                  } else {
+                    if ((dw & kMask) < dhi) __threadfence_block();   // same-bucket successor
+                    const uint64_t rw = a.sig[w];
+                    if (rw & kIntTag) {
+                      atomicAdd(&ws->acci[ol], (uint32_t)rw);
+                    } else {
+                      x = (double)*reinterpret_cast<const DT *>(&rw);
+                      fp = true;
+                    }
+                  }
+                }
+              }
+              fpm = __ballot_sync(kFull, fp);
+              if (fpm) ws->buf[lane] = x;
+            },
+            [&](uint32_t lo, uint32_t hi) {
+              if (fpm) {   // warp-uniform
+                __syncwarp();
+                for (uint32_t t = lo; t < hi; ++t)
+                  if ((fpm >> t) & 1u) { acc_f += (DT)ws->buf[t]; any_f = true; }
+                __syncwarp();
               }
             });
-            if (pending) {
-              SlotArrays a = slot_arrays(sp, slot0 + i);
-              const uint32_t fl = ws->flags[lane];
-              if (fl & 1u) {
-                open = true;
-              } else {
-                const uint32_t acc_i = ws->acci[lane];
-                const unsigned long long accbits = ws->acc[lane];
-                const DT acc_f = *reinterpret_cast<const DT *>(&accbits);
-                const uint64_t sg = a.sig[v];
-                const bool is_src = (v == sl[i].s);
-                if (sg == 1ull && !(fl & 2u)) {
-                  // delta(v) = sum of the successors' subtree sizes: exact in integers
-                  a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-                  if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
-                } else {
-                  const DT acc = (DT)acc_i + acc_f;
-                  DT dep, rho;
-                  if (sg == 1ull) {
-                    dep = acc;
-                    rho = (DT)1 + dep;
-                  } else {
-                    const DT sv = (DT)sg;
-                    dep = sv * acc;
-                    rho = ((DT)1 + dep) / sv;
-                  }
-                  uint64_t bits = 0;
-                  *reinterpret_cast<DT *>(&bits) = rho;
-                  a.sig[v] = bits;
-                  if (!is_src) atomicAdd(&bc[v], (double)dep);
-                }
-                __threadfence_block();
-                st_volatile(&a.dist[v], dvm);
-              }
-            }
-            __syncwarp();
-          }
-          if (!team.any(open)) break;
-        }
-      } else {
-        for (uint32_t pass = 0;; ++pass) {
-          if (pass > n + 1) { my_err |= kErrPassLimit; ok = false; break; }
-          bool open = false;
-          for (uint32_t base = 0; base < total; base += TS) {
-            const uint32_t k = base + lane * NW + warp;   // members interleaved over the warps
-            if (k >= total) continue;
-            const uint32_t i = find_slot(tc->pref, S, k);
-            SlotArrays a = slot_arrays(sp, slot0 + i);
-            const uint32_t v = a.ord[sl[i].lo + k - tc->pref[i]];
-            if (v >= n) { my_err |= kErrCapacity; continue; }
-            const uint32_t dv = a.dist[v];
-            if (!(dv & kFlag)) continue;
-            const uint32_t dvm = dv & kMask;
-            uint32_t acc_i = 0;     // sum of integral rho (unique-path subtrees)
-            DT acc_f = 0;           // sum of the other rho
-            bool integral = true, all_final = true;
-            const uint32_t e1 = H.rp[v + 1];
-            for (uint32_t e = H.rp[v]; e < e1; ++e) {
-              const uint32_t pk = H.arc[e];
-              const uint32_t w = pk & 0xFFFFu;
-              const uint32_t dw = a.dist[w];
-              if ((dw & kMask) != dvm + (pk >> 16)) continue;
-              if (dw & kFlag) { all_final = false; break; }
-              if ((dw & kMask) < dhi) __threadfence_block();       // same-bucket successor
-              const uint64_t rw = a.sig[w];
-              if (rw & kIntTag) {
-                acc_i += (uint32_t)rw;
-              } else {
-                acc_f += *reinterpret_cast<const DT *>(&rw);
-                integral = false;
-              }
-            }
-            if (!all_final) { open = true; continue; }
+        if (pending) {
+          SlotArrays a = slot_arrays(sp, slot0 + i);
+          if (ws->flags[lane] & 1u) {
+            open = true;
+          } else {
+            const uint32_t acc_i = ws->acci[lane];
             const uint64_t sg = a.sig[v];
             const bool is_src = (v == sl[i].s);
-            if (sg == 1ull && integral) {
+            if (sg == 1ull && !any_f) {
               // delta(v) = sum of the successors' subtree sizes: exact in integers
               a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-              if (!is_src && acc_i) atomicAdd(&bci[v], acc_i);
+              if (!is_src && acc_i) atomicAdd(&bhi[v], (unsigned long long)acc_i);
             } else {
-              const DT acc = (DT)acc_i + acc_f;
               DT dep, rho;
-              if (sg == 1ull) {
-                dep = acc;
-                rho = (DT)1 + dep;
-              } else {
-                const DT sv = (DT)sg;
-                dep = sv * acc;
-                rho = ((DT)1 + dep) / sv;
-              }
+              dependency<DT>(sg, (DT)acc_i + acc_f, dep, rho);
               uint64_t bits = 0;
               *reinterpret_cast<DT *>(&bits) = rho;
               a.sig[v] = bits;
-              if (!is_src) atomicAdd(&bc[v], (double)dep);
+              if (!is_src) fx_add(blo, bhi, v, (double)dep);
             }
             __threadfence_block();
             st_volatile(&a.dist[v], dvm);
           }
-          if (!team.any(open)) break;
         }
+        __syncwarp();
       }
-      if (!ok) break;
-      for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].lo;
-      team.sync();
+      if (!team.any(open)) break;
     }
+    if (!ok) break;
+    for (uint32_t i = tid; i < S; i += TS) sl[i].hi = sl[i].lo;
+    team.sync();
   }
   if (my_err) atomicOr(err_out, my_err);
   if (my_ovf) atomicOr(ovf_out, 1u);
@@ -858,7 +815,7 @@ __device__ inline void keep_anchor_component(uint32_t n, uint32_t anchor, const 
 // range, offsets from one block scan) and the largest alive length into ctl->wmax.  With hop
 // distances given, only arcs between nodes within P.hop_radius of the anchor are kept.
 __device__ inline void realize_csr(const McDev &P, uint32_t r, uint32_t *rp, uint32_t *arc,
-                            CtaCtl *ctl, const uint32_t *hop = nullptr) {
+                            CtaHead *ctl, const uint32_t *hop = nullptr) {
   const uint32_t n = P.n;
   const uint32_t cap = (uint32_t)(2 * P.m);   // arc slots reserved in the layout
   const uint32_t T = blockDim.x;
@@ -955,7 +912,7 @@ __device__ __forceinline__ bool comp_valid(uint32_t info, uint32_t k_min) {
 // (b + 1) * Delta - 1 + wmax < (b + kRing) * Delta, so every discovered distance beyond the
 // current bucket has its own entry in the ring of kRing bucket bitmaps; powers of two turn the
 // bucket and ring arithmetic into shifts and masks.
-__device__ __forceinline__ void bucket_setup(CtaCtl *ctl, uint32_t delta_req) {
+__device__ __forceinline__ void bucket_setup(CtaHead *ctl, uint32_t delta_req) {
   if (threadIdx.x == 0) {
     const uint32_t wmax = ctl->wmax;
     const uint32_t dmin = (wmax + (kRing - 2) - 1) / (kRing - 2);
@@ -976,7 +933,7 @@ __device__ __forceinline__ void bucket_setup(CtaCtl *ctl, uint32_t delta_req) {
 __device__ inline bool select_and_count(const McDev &P, uint32_t r_local, const uint32_t *comp,
                                         const uint32_t *cinfo, const double *bc, SlotArrays s0,
                                         uint32_t *rank, uint16_t *mark, bool gap_test,
-                                        CtaCtl *ctl) {
+                                        CtaHead *ctl) {
   const uint32_t n = P.n;
   unsigned long long *best = reinterpret_cast<unsigned long long *>(s0.sig);
   uint32_t *centre = s0.dist;

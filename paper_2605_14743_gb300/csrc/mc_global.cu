@@ -7,9 +7,9 @@
 //            components), zeroed betweenness accumulators
 //   brandes  a persistent grid; the teams of every CTA claim batches of sources of the G
 //            realizations from per-group cursors (group by group, so the realized graph being
-//            worked on stays hot in L2) and run the same bucketed Brandes routine as the
-//            shared-memory kernel (A3-A5), with their source slots in a per-CTA region of a
-//            device arena and betweenness accumulated with device-memory atomics
+//            worked on stays hot in L2) and run the bucketed Brandes routine (A3-A5), with
+//            their source slots in a per-CTA region of a device arena (or on chip where they
+//            fit) and betweenness accumulated exactly (128-bit fixed point, device atomics)
 //   select   one CTA per group: tie-ruled argmax and transition counts (A6); in FP32 mode a
 //            realization whose top-two gap is under the margin is flagged, its accumulators
 //            cleared, and a second brandes + select pair redoes exactly the flagged groups in
@@ -50,7 +50,7 @@ big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uin
   bucket_setup(ctl, P.delta);
   uint32_t *cedges = G.centre;   // scratch until selection
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    cedges[v] = 0; G.bc[v] = 0.0; G.bci[v] = 0;
+    cedges[v] = 0; reinterpret_cast<unsigned long long *>(G.bc)[v] = 0ull; G.bhi[v] = 0ull;
   }
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -134,14 +134,13 @@ big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngro
       team.sync();
       if (k0 >= nsrc) break;
       const uint32_t S = min(spt, nsrc - k0);
-      // warp-cooperative sigma and delta passes (FLAT): measured faster here, where buckets
-      // hold many members, and slower on the shared-memory path's small buckets
+      unsigned long long *blo = reinterpret_cast<unsigned long long *>(G.bc);
       if (mode == 1)
-        brandes_batch<TS, BLOCK, float, true>(team, H, sp, team.id * spt, S, G.src + k0, dsh,
-                                              G.bc, G.bci, true, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, G.src + k0, dsh, blo,
+                                        G.bhi, ctl, &G.err, &G.ovf);
       else
-        brandes_batch<TS, BLOCK, double, true>(team, H, sp, team.id * spt, S, G.src + k0, dsh,
-                                               G.bc, G.bci, true, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, G.src + k0, dsh, blo,
+                                         G.bhi, ctl, &G.err, &G.ovf);
     }
   }
 }
@@ -154,7 +153,7 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
   BigGroup &G = groups[blockIdx.x];
   if (!G.active || (redo_only && !G.redo)) return;
   const uint32_t n = (uint32_t)P.n;
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) G.bc[v] += (double)G.bci[v];
+  fx_finalize(reinterpret_cast<unsigned long long *>(G.bc), G.bhi, n);   // doubles in place
   __syncthreads();
   SlotArrays s0{};
   s0.sig = reinterpret_cast<uint64_t *>(G.best);
@@ -164,7 +163,10 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
                        ctl);
   __syncthreads();
   if (recheck) {
-    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) { G.bc[v] = 0.0; G.bci[v] = 0; }
+    for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+      reinterpret_cast<unsigned long long *>(G.bc)[v] = 0ull;
+      G.bhi[v] = 0ull;
+    }
     if (threadIdx.x == 0) {
       G.redo = 1;
       G.cursor = 0;
@@ -229,8 +231,8 @@ bool big_config_supported(int block, int team) {
 static size_t al256(size_t x) { return (x + 255u) & ~size_t(255); }
 
 size_t big_group_bytes(uint32_t n, uint64_t arcs) {
-  return al256(4ull * (n + 1)) + al256(4ull * (arcs > 0 ? arcs : 1)) + 5 * al256(4ull * n) +
-         al256(2ull * n) + 2 * al256(8ull * n);
+  return al256(4ull * (n + 1)) + al256(4ull * (arcs > 0 ? arcs : 1)) + 4 * al256(4ull * n) +
+         al256(2ull * n) + 3 * al256(8ull * n);
 }
 
 uint32_t big_slot_bytes(uint32_t n) { return (slot_bytes_for(n) + 255u) & ~255u; }
@@ -243,11 +245,11 @@ void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs
   G.arc = reinterpret_cast<uint32_t *>(take(4ull * (arcs > 0 ? arcs : 1)));
   G.comp = reinterpret_cast<uint32_t *>(take(4ull * n));
   G.cinfo = reinterpret_cast<uint32_t *>(take(4ull * n));
-  G.bci = reinterpret_cast<uint32_t *>(take(4ull * n));
   G.centre = reinterpret_cast<uint32_t *>(take(4ull * n));
   G.rank = reinterpret_cast<uint32_t *>(take(4ull * n));
   G.src = reinterpret_cast<uint16_t *>(take(2ull * n));
   G.bc = reinterpret_cast<double *>(take(8ull * n));
+  G.bhi = reinterpret_cast<unsigned long long *>(take(8ull * n));
   G.best = reinterpret_cast<unsigned long long *>(take(8ull * n));
 }
 

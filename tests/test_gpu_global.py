@@ -129,14 +129,19 @@ def _ws3000():
 
 
 def test_shared_path_rejects_graph_that_does_not_fit():
-    q = afc.Query(_ws3000(), memory_path=1)
+    """8,000 nodes: the realization and one source slot exceed shared memory."""
+    eu, ev = ws_edges(8000, 6, 0.1, 9)
+    q = afc.Query(Workload("ws8000", 8000, eu, ev, 0.95, 1, 100, 1, seed=1), memory_path=1)
     with pytest.raises(afc.AfcError) as e:
         q.run_counts(0, 1)
-    assert e.value.code == 7
+    assert e.value.code == afc.AFC_EUNSUPPORTED
 
 
 def test_auto_path_3000_nodes():
-    """A graph too large for the shared-memory kernel runs on the global path by itself."""
+    """A graph whose shared-memory CTA would hold fewer than four source slots runs on the
+    global path by itself."""
+    q = afc.Query(_ws3000())
+    assert afc.afc_counts_path(q.prob) == GLOBAL
     worst, _ = _check(_ws3000(), 0, 4, oracle_threads=8)
     assert worst < 1e-9
 

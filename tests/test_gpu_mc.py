@@ -130,27 +130,32 @@ def test_sssp_sigma_ws1000_sampled(B, delta):
     _sssp_check(wl, 1, sources, block_threads=B, bucket_width=delta)
 
 
-@pytest.mark.parametrize("B,T", [(1024, 1024), (1024, 256), (1024, 128), (512, 64), (512, 128),
-                                 (256, 32), (256, 256)])
-def test_sssp_team_configurations(B, T):
-    """Every (block, team) shape of the counting kernel runs the same batch routine."""
+@pytest.mark.parametrize("B", [256, 512, 1024])
+def test_sssp_every_source_of_a_realization(B):
+    """Every node of a ws1000 realization as a source, one warp each, over as many CTAs as the
+    block size gives: distances and path counts bit-exact."""
     wl = _ws1000()
-    rng = np.random.default_rng(B * 7 + T)
-    sources = sorted(rng.choice(wl.n, 40, replace=False).tolist())
-    _sssp_check(wl, 3, sources, block_threads=B, team_threads=T, bucket_width=24)
+    _sssp_check(wl, 3, list(range(wl.n)), block_threads=B)
 
 
-@pytest.mark.parametrize("B,T,spt", [(1024, 256, 2), (512, 64, 1), (1024, 32, 0)])
+@pytest.mark.parametrize("B", [256, 512, 1024])
+def test_counts_block_sizes(B):
+    _mc_check(_small_er(), 0, 40, block_threads=B)
 
-def test_counts_team_configurations(B, T, spt):
-    _mc_check(_small_er(), 0, 40, block_threads=B, team_threads=T, slots_per_team=spt)
 
-
-def test_infeasible_team_shape_is_rejected():
-    """32 one-warp teams need 32 source slots; the 1000-node graph leaves room for about 11."""
+def test_launch_shapes_are_validated():
+    """team_threads applies to the global path's teams and must be one of its shapes; a graph
+    whose realization and one source slot exceed shared memory cannot be forced onto the
+    shared-memory path."""
     wl = _ws1000()
     with pytest.raises(afc.AfcError) as e:
         _sssp_check(wl, 3, [0, 1], block_threads=1024, team_threads=32)
+    assert e.value.code == afc.AFC_EINVAL
+    from afc_inputs import ws_edges
+    eu, ev = ws_edges(8000, 6, 0.1, 9)
+    big = Workload("ws8000", 8000, eu, ev, 0.95, 1, 100, 1, seed=1)
+    with pytest.raises(afc.AfcError) as e:
+        _sssp_check(big, 0, [0])
     assert e.value.code == afc.AFC_EUNSUPPORTED
 
 
