@@ -149,14 +149,16 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
   return incl - x;
 }
 
-// Pending-list windows (32 nodes each) whose node, smallest length and distance stay in
-// registers between the bound scan and the selection of a step.
+// Pending-list windows (32 nodes each) loaded together at the start of a step's selection.
 constexpr int kPendCache = 8;
 
 // ---------------------------------------------------------------------------------------
 // Brandes from source s by one warp (Sec. 3.1 definitions: d_H, sigma_st, ordered-pair
 // betweenness).  Forward: settle steps (see the file comment), sigma pulled from the
-// predecessors while the step's arcs are relaxed.  Backward (want_delta): the steps in
+// predecessors while the step's arcs are relaxed; the next step's bounds d_min and
+// min (d + mw) come from the pending nodes that stay and from the relaxations (every pending
+// node's current distance is one of those values, and no recorded value is below the node's
+// current distance), so no separate pass over the pending list is needed.  Backward (want_delta): the steps in
 // reverse; rho(v) = (1 + delta(v)) / sigma(v) replaces sigma in place, delta(v) =
 // sigma(v) * sum over successors w of rho(w) in arc order; unique-path subtrees (sigma = 1
 // throughout) stay exact integers.  delta_s(v) for v != s goes to the exact accumulators of
@@ -178,47 +180,21 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
   __syncwarp();
 
   // ---- forward
-  uint32_t nord = 0, pc = 1;   // settled nodes, pending nodes (warp-uniform)
+  uint32_t nord = 0, pc = 1;                   // settled nodes, pending nodes (warp-uniform)
+  uint32_t dmin = 0u, lout = (uint32_t)mw[s];   // d_min and min (d + mw) over the pending nodes
   for (uint32_t step = 0;; ++step) {
     if (step > n) { err |= kErrPassLimit; return false; }
     if (pc == 0) break;   // nothing pending: the source's component is done
-    // (1) d_min and the OUT bound min (d(u) + mw(u)) over the pending nodes; the first
-    // kPendCache windows stay in registers
-    uint32_t dmin = kInf, lout = 0xFFFFFFFFu;
-    uint32_t cvm[kPendCache], cd[kPendCache];   // node | mw << 16, distance
-#pragma unroll
-    for (int c = 0; c < kPendCache; ++c) {
-      const uint32_t j = (uint32_t)c * 32u + lane;
-      cvm[c] = j < pc ? (uint32_t)sl.plist[j] : 0u;
-    }
-#pragma unroll
-    for (int c = 0; c < kPendCache; ++c) {
-      const uint32_t j = (uint32_t)c * 32u + lane;
-      cd[c] = kInf;
-      if (j < pc) {
-        const uint32_t v = cvm[c], m = mw[v], d = sl.dist[v];
-        cvm[c] = v | (m << 16);
-        cd[c] = d;
-        dmin = min(dmin, d);
-        lout = min(lout, d + m);
-      }
-    }
-    for (uint32_t j = kPendCache * 32u + lane; j < pc; j += 32u) {
-      const uint32_t v = sl.plist[j], d = sl.dist[v];
-      dmin = min(dmin, d);
-      lout = min(lout, d + (uint32_t)mw[v]);
-    }
-    dmin = __reduce_min_sync(kFull, dmin);
-    lout = __reduce_min_sync(kFull, lout);
-    // (2) settle every pending v with d(v) < d_min + mw(v) or d(v) < lout (the node at d_min
-    // always qualifies): append it to ord, flag it settled; the others stay, compacted in order
+    // (1) settle every pending v with d(v) < d_min + mw(v) (IN) or d(v) < lout (OUT; the node
+    // at d_min always qualifies): append it to ord, flag it settled; the others stay,
+    // compacted in order, and give the next step's bounds together with the relaxations below
     const uint32_t g0 = nord;
     const uint32_t below = lanemask_lt();
-    uint32_t kept = 0;
+    uint32_t kept = 0, ndmin = kInf, nlout = 0xFFFFFFFFu;
     auto place = [&](bool sel, bool keep, uint32_t sm, uint32_t km, uint32_t v, uint32_t d,
-                     uint32_t nbase, uint32_t kbase) {
+                     uint32_t m) {
       if (sel) {
-        const uint32_t pos = nbase + (uint32_t)__popc(sm & below);
+        const uint32_t pos = nord + (uint32_t)__popc(sm & below);
         if (pos < n) {
           sl.ord[pos] = (uint16_t)(v | (pos == g0 ? kStepStart : 0u));
           sl.dist[v] = d | kFlag;
@@ -226,29 +202,37 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
           err |= kErrCapacity;
         }
       } else if (keep) {
-        sl.plist[kbase + (uint32_t)__popc(km & below)] = (uint16_t)v;
+        sl.plist[kept + (uint32_t)__popc(km & below)] = (uint16_t)v;
+        ndmin = min(ndmin, d);
+        nlout = min(nlout, d + m);
       }
+      nord += (uint32_t)__popc(sm);
+      kept += (uint32_t)__popc(km);
     };
     {
-      // all windows' decisions first, then their positions, then the stores
-      uint32_t sm[kPendCache], km[kPendCache];
+      // the first kPendCache windows: every load first, then the decisions, then the stores
+      uint32_t cv[kPendCache], cm[kPendCache], cd[kPendCache];
+#pragma unroll
+      for (int c = 0; c < kPendCache; ++c) {
+        const uint32_t j = (uint32_t)c * 32u + lane;
+        cv[c] = j < pc ? (uint32_t)sl.plist[j] : 0u;
+      }
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
         const bool valid = (uint32_t)c * 32u + lane < pc;
-        const uint32_t m = cvm[c] >> 16, d = cd[c];
-        const bool sel = valid && (d < dmin + m || d < lout);
-        sm[c] = __ballot_sync(kFull, sel);
-        km[c] = __ballot_sync(kFull, valid && !sel);
+        cm[c] = valid ? (uint32_t)mw[cv[c]] : 0u;
+        cd[c] = valid ? (uint32_t)sl.dist[cv[c]] : 0u;
       }
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
-        const bool sel = (sm[c] >> lane) & 1u, keep = (km[c] >> lane) & 1u;
-        place(sel, keep, sm[c], km[c], cvm[c] & 0xFFFFu, cd[c], nord, kept);
-        nord += (uint32_t)__popc(sm[c]);
-        kept += (uint32_t)__popc(km[c]);
+        if ((uint32_t)c * 32u >= pc) break;   // warp-uniform
+        const bool valid = (uint32_t)c * 32u + lane < pc;
+        const bool sel = valid && (cd[c] < dmin + cm[c] || cd[c] < lout);
+        const uint32_t sm = __ballot_sync(kFull, sel), km = __ballot_sync(kFull, valid && !sel);
+        place(sel, valid && !sel, sm, km, cv[c], cd[c], cm[c]);
       }
     }
-    // the uncached windows: each is read before its kept nodes move down (to lower positions)
+    // the other windows: each is read before its kept nodes move down (to lower positions)
     for (uint32_t j0 = kPendCache * 32u; j0 < pc; j0 += 32u) {
       const uint32_t j = j0 + lane;
       uint32_t v = 0, d = 0, m = 0;
@@ -260,9 +244,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       const bool sel = j < pc && (d < dmin + m || d < lout);
       const uint32_t smw = __ballot_sync(kFull, sel);
       const uint32_t kmw = __ballot_sync(kFull, j < pc && !sel);
-      place(sel, j < pc && !sel, smw, kmw, v, d, nord, kept);
-      nord += (uint32_t)__popc(smw);
-      kept += (uint32_t)__popc(kmw);
+      place(sel, j < pc && !sel, smw, kmw, v, d, m);
     }
     pc = kept;
     __syncwarp();
@@ -294,7 +276,12 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
           const bool pred = (du[t] & kFlag) && (du[t] & kMask) + len == dv && e + t < e1;
           x[t] = pred ? sl.sig[u] : 0ull;
           const uint32_t nd = dv + len;
-          old[t] = (!(du[t] & kFlag) && nd < du[t]) ? atomicMin(&sl.dist[u], nd) : 0u;
+          const bool relax = !(du[t] & kFlag) && nd < du[t];
+          old[t] = relax ? atomicMin(&sl.dist[u], nd) : 0u;
+          if (relax) {   // a pending node's new distance: the next step's bounds
+            ndmin = min(ndmin, nd);
+            nlout = min(nlout, nd + (uint32_t)mw[u]);
+          }
         }
         // discovered now (each node once): onto the pending list
         uint32_t dm[4];
@@ -313,6 +300,8 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       }
       if (mine && v != s) sl.sig[v] = sg;
     }
+    dmin = __reduce_min_sync(kFull, ndmin);
+    lout = __reduce_min_sync(kFull, nlout);
     __syncwarp();
   }
   if (!want_delta) return true;

@@ -159,6 +159,19 @@ def test_launch_shapes_are_validated():
     assert e.value.code == afc.AFC_EUNSUPPORTED
 
 
+def test_long_distances():
+    """A 300-node path with lengths in {900..1000}: distances up to ~3e5 and some 300 settle
+    steps per source.  Distances, path counts, betweenness, next states and counts match the
+    oracle exactly, also when failed edges split the path."""
+    from afc_inputs import path_edges
+    eu, ev = path_edges(300)
+    wl = Workload("longpath", 300, eu, ev, 1.0, 900, 1000, 4, seed=5, k_min=2)
+    _sssp_check(wl, 1, [0, 150, 299])
+    _mc_check(wl, 0, 4)
+    # a few edges fail: some realizations split the path into pieces short enough for 16 bits
+    _mc_check(variant(wl, p_survive=0.97, realizations=6), 0, 6)
+
+
 def test_sssp_unweighted_grid_large_sigma():
     eu, ev = grid_edges(30, 30)
     wl = Workload("grid", 900, eu, ev, 1.0, 1, 1, 1, seed=1)
