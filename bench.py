@@ -46,7 +46,8 @@ def _env_rank():
 # DRAM bytes of one counting launch of the benchmark, from ncu (profiles/counts_traffic.txt); valid
 # only for the kernel sources it was taken on, so the file records their hash.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "counts_traffic.txt")
-KERNEL_SOURCES = ["mc_common.cuh", "mc_kernel.cu", "afc_internal.h", "afc_device.cuh"]
+KERNEL_SOURCES = ["mc_common.cuh", "mc_steps.cuh", "mc_kernel.cu", "afc_internal.h",
+                  "afc_device.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -335,6 +336,13 @@ def run_ours(args):
            "latency_ms_p99": 1000 * max(lat), "calls": len(lat),
            "ranks": world}
 
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the metric's comparisons, on the same GPU after the timed steps: FP32 + recheck in
+        # one batched launch against plain FP64 per graph (the mix), and the serving loop
+        from afc_inputs import mixed_batch
+        extras["fp32_vs_fp64"] = mix_compare(mixed_batch(64)[::4], MIX_SUBSET, local)
+        extras["serving"] = serving_leg(scale=1.0 / 64, clock_gpu=local)
     if rank == 0:
         cb = None if args.no_cpu else cpu_baseline(wl)
         line = {"metric": METRIC, "value": value, "unit": "realizations/s", "n_gpus": world,
@@ -352,7 +360,8 @@ def run_ours(args):
                 "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
                 "check": {"c": res.c, "expected_T": res.expected_T, "b_f": res.b_f,
-                          "device_error": int(stats[5]), "overflow": int(stats[3])}}
+                          "device_error": int(stats[5]), "overflow": int(stats[3])},
+                **extras}
         print(json.dumps(line))
     if dist:
         tdist.destroy_process_group()
@@ -384,16 +393,13 @@ def _scaled(wl, scale, lo=16):
     return w2
 
 
-def run_mix(args):
-    """The batched mix (64 graphs, n log-uniform in [200, 4000]): every graph's realizations in
-    one batched call with FP32 dependencies and FP64 recheck, against plain FP64 with one call
+def mix_compare(batch, label, clock_gpu=0):
+    """The metric's own comparison on the batched mix: every graph's realizations in one
+    batched call with FP32 dependencies and FP64 recheck, against plain FP64 with one call
     per graph, on the same GPU; the counts of the two must be identical."""
     import numpy as np
     import torch
     import paper_2605_14743_gb300 as afc
-    from afc_inputs import mixed_batch
-    torch.cuda.set_device(0)
-    batch = [_scaled(w, args.mix_scale) for w in mixed_batch(64)]
     stream = torch.cuda.current_stream()
     q32 = [afc.Query(w) for w in batch]
     q64 = [afc.Query(w) for w in batch]
@@ -403,6 +409,7 @@ def run_mix(args):
     rc = np.array([w.realizations for w in batch], np.uint32)
     ptrs = np.array([q.counts.data_ptr() for q in q32], np.uint64)
     stats32 = torch.zeros((len(batch), 7), dtype=torch.int64, device="cuda")
+    stats64 = [torch.zeros(7, dtype=torch.int64, device="cuda") for _ in batch]
     wsb = afc.afc_transition_counts_batched_workspace(len(batch), probs, rc)
     ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
 
@@ -414,39 +421,171 @@ def run_mix(args):
                                           stream.cuda_stream)
 
     def per_query():
-        for q in q64:
-            q.run_counts()
+        for q, st in zip(q64, stats64):
+            q.counts.zero_()
+            st.zero_()
+            afc.afc_transition_counts(q.prob, 0, q.wl.realizations, q.counts, st, None, None,
+                                      q.ws_counts, q.ws_counts.numel(), stream.cuda_stream)
+
+    # warm-up on a few realizations of the two smallest graphs (module loads, pools)
+    small = sorted(range(len(batch)), key=lambda g: batch[g].n)[:2]
+    for g in small:
+        for q in (q32[g], q64[g]):
+            q.run_counts(0, 4)
+    torch.cuda.synchronize()
 
     def timed(fn):
-        fn()
+        clk = ClockSampler(clock_gpu)
+        clk.start()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        return e0.elapsed_time(e1), clk.stop()
 
-    ms32 = timed(batched)
-    ms64 = timed(per_query)
+    ms32, clk32 = timed(batched)
+    ms64, clk64 = timed(per_query)
     same = all(torch.equal(a.counts, b.counts) for a, b in zip(q32, q64))
     st = stats32.cpu().numpy()
+    st64 = np.stack([x.cpu().numpy() for x in stats64])
     R = int(rc.sum())
-    edges = int(st[:, 2].sum())
     glob = sum(1 for q in q32 if afc.afc_counts_path(q.prob) == afc.AFC_PATH_GLOBAL)
-    line = {"config": {"workload": "batched mix: 64 graphs (32 ER mean degree 8, 32 WS k=8 "
-                                   "beta=0.2), n log-U[200,4000], failure U(0.01,0.2), lengths "
-                                   "{1..50}, realizations U{256..4096} x %.3g" % args.mix_scale,
-                       "realizations_total": R, "graphs_on_global_path": glob},
-            "metric": "realizations/s", "fp32_recheck_batched": {
-                "value": R / (ms32 / 1e3), "ms": ms32, "gteps": edges / (ms32 / 1e3) / 1e9,
-                "rechecked": int(st[:, 4].sum()), "launch": "one batched call"},
-            "fp64_per_query": {"value": R / (ms64 / 1e3), "ms": ms64,
-                               "gteps": edges / (ms64 / 1e3) / 1e9, "launch": "64 calls"},
-            "speedup": ms64 / ms32, "counts_identical": bool(same),
-            "device_error": int(st[:, 5].sum())}
+    return {"workload": label, "graphs": len(batch), "realizations_total": R,
+            "graphs_on_global_path": glob,
+            "fp32_recheck_batched": {"value": R / (ms32 / 1e3), "unit": "realizations/s",
+                                     "ms": ms32, "gteps": int(st[:, 2].sum()) / (ms32 / 1e3) / 1e9,
+                                     "rechecked": int(st[:, 4].sum()),
+                                     "launch": "one batched call", "clocks": clk32},
+            "fp64_per_query": {"value": R / (ms64 / 1e3), "unit": "realizations/s", "ms": ms64,
+                               "gteps": int(st64[:, 2].sum()) / (ms64 / 1e3) / 1e9,
+                               "launch": f"{len(batch)} calls", "clocks": clk64},
+            "vs_plain_fp64": ms64 / ms32, "counts_identical": bool(same),
+            "device_error": int(st[:, 5].sum() + st64[:, 5].sum())}
+
+
+MIX_SUBSET = ("batched mix, every 4th graph at full size: 16 of the 64 graphs (8 ER mean degree "
+              "8, 8 WS k=8 beta=0.2; n log-U[200,4000], failure U(0.01,0.2), lengths {1..50}), "
+              "each with its full realization count U{256..4096}")
+
+
+def run_mix(args):
+    """The batched mix (64 graphs, n log-uniform in [200, 4000]), or the every-4th-graph
+    subset at full size: FP32 + recheck batched against plain FP64 per graph."""
+    import torch
+    from afc_inputs import mixed_batch
+    torch.cuda.set_device(0)
+    if args.mix_subset:
+        batch = mixed_batch(64)[::4]
+        label = MIX_SUBSET
+    else:
+        batch = [_scaled(w, args.mix_scale) for w in mixed_batch(64)]
+        label = ("batched mix: 64 graphs (32 ER mean degree 8, 32 WS k=8 beta=0.2), n "
+                 "log-U[200,4000], failure U(0.01,0.2), lengths {1..50}, realizations "
+                 "U{256..4096} x %.3g" % args.mix_scale)
+    res = mix_compare(batch, label)
+    line = {"config": {"workload": label}, "metric": "realizations/s", **res}
     print(json.dumps(line))
-    return 0 if same else 1
+    return 0 if res["counts_identical"] else 1
+
+
+def serving_leg(scale=1.0 / 16, arrivals=100, probe=16, window_s=2.0, rate_frac=0.7,
+                clock_gpu=0):
+    """The serving stream through the native serving loop, three parts:
+    capacity  a closed batch of `probe` queries (realization budgets scaled by `scale`);
+    stream    `arrivals` Poisson arrivals of the next queries (same scaling) at rate_frac x the
+              capacity: p50/p99 submit-to-result latency over all of them;
+    window    the stream as specified (full budgets, 200 queries/s) for window_s seconds into a
+              server with a bounded queue: admitted, deferred (queued) and shed fractions at the
+              end of the window, after which everything not yet counted is cancelled."""
+    import numpy as np
+    import paper_2605_14743_gb300 as afc
+    from afc_inputs import serving_stream
+    full = serving_stream(rate_hz=200.0, duration_s=60.0, seed=105)
+    scaled = [_scaled(wl, scale, lo=8) for _, wl in full[:probe + arrivals]]
+    with afc.Server() as srv:
+        t0 = time.perf_counter()
+        ts = [srv.submit(wl) for wl in scaled[:probe]]
+        for t in ts:
+            srv.poll(t)
+        cap_wall = time.perf_counter() - t0
+    cap = probe / cap_wall
+    rate = rate_frac * cap
+    rng = np.random.default_rng(5)
+    clk = ClockSampler(clock_gpu)
+    clk.start()
+    with afc.Server() as srv:
+        t0 = time.perf_counter()
+        nxt, tickets = 0.0, []
+        for wl in scaled[probe:probe + arrivals]:
+            delay = t0 + nxt - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(wl))
+            nxt += rng.exponential(1.0 / rate)
+        lat = [srv.poll(t).latency_ms for t in tickets]
+        st = srv.stats()
+    clocks = clk.stop()
+    # the specified rate over a bounded window
+    max_waiting = 64
+    offered = accepted = 0
+    with afc.Server(max_waiting=max_waiting) as srv:
+        t0 = time.perf_counter()
+        tickets_w = []
+        for t_arr, wl in full:
+            if t_arr >= window_s:
+                break
+            delay = t0 + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            offered += 1
+            try:
+                tickets_w.append(srv.submit(wl))
+                accepted += 1
+            except afc.AfcError as e:
+                if e.code != afc.AFC_EBUSY:
+                    raise
+        t_end = time.perf_counter() - t0
+        sw = srv.stats()
+        srv.cancel()
+        completed_w = sum(1 for t in tickets_w if _poll_done(srv, t))   # counted before the cancel
+    admitted = int(sw["admitted"])
+    return {"workload": "serving stream: Poisson arrivals, ER/WS 50/50, n log-U[100, 1e4], mean "
+                        "degree U(6,12), failure U(0.01,0.3), lengths {1..100}, realizations "
+                        "log-U[256,8192], FP32 + recheck",
+            "capacity": {"queries": probe, "realization_scale": scale, "qps": cap,
+                         "wall_s": cap_wall},
+            "stream": {"arrivals": len(tickets), "rate_qps": rate,
+                       "rate_fraction_of_capacity": rate_frac, "realization_scale": scale,
+                       "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                       "max_ms": st["max_ms"], "wait_p50_ms": st["wait_p50_ms"],
+                       "wait_p99_ms": st["wait_p99_ms"],
+                       "realizations_per_s": st["realizations_per_s"],
+                       "gteps": st["edge_visits"] / max(st["wall_s"], 1e-9) / 1e9,
+                       "slices": int(st["slices"]), "failed": int(st["failed"]),
+                       "latency_check_ms": [float(np.percentile(lat, 50)),
+                                            float(np.percentile(lat, 99))],
+                       "clocks": clocks},
+            "as_specified_window": {"rate_qps": 200.0, "window_s": window_s,
+                                    "achieved_offered_qps": offered / max(t_end, 1e-9),
+                                    "offered": offered, "max_waiting": max_waiting,
+                                    "admitted_fraction": admitted / max(offered, 1),
+                                    "deferred_fraction": (accepted - admitted) / max(offered, 1),
+                                    "shed_fraction": (offered - accepted) / max(offered, 1),
+                                    "completed_before_cancel": completed_w,
+                                    "rest": "cancelled at the end of the window"}}
+
+
+def _poll_done(srv, t):
+    """True when the ticket completed, False when it was cancelled."""
+    import paper_2605_14743_gb300 as afc
+    try:
+        return srv.poll(t) is not None
+    except afc.AfcError as e:
+        if e.code == afc.AFC_ECANCELED:
+            return False
+        raise
 
 
 def run_ws20000(args):
@@ -728,54 +867,12 @@ def run_fma_peak(args):
 
 
 def run_serving(args):
-    """The serving stream through the native serving loop: a closed batch of its first queries
-    measures capacity, then the next queries arrive as a Poisson stream at a fraction of that
-    capacity; p50/p99 submit-to-result latency.  The specified 200 queries/s is reported as
-    the overload factor over the measured capacity."""
-    import numpy as np
     import torch
-    import paper_2605_14743_gb300 as afc
-    from afc_inputs import serving_stream
     torch.cuda.set_device(0)
-    stream = [wl for _, wl in serving_stream(max_queries=400, seed=105)]
-    k = args.serve_probe
-    with afc.Server() as srv:
-        t0 = time.perf_counter()
-        ts = [srv.submit(wl) for wl in stream[:k]]
-        for t in ts:
-            srv.poll(t)
-        wall = time.perf_counter() - t0
-        probe = srv.stats()
-    cap = k / wall
-    rate = args.serve_rate_frac * cap
-    rng = np.random.default_rng(5)
-    with afc.Server() as srv:
-        t0 = time.perf_counter()
-        nxt, tickets, i = 0.0, [], k
-        while len(tickets) < args.serve_queries and i < len(stream):
-            delay = t0 + nxt - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets.append(srv.submit(stream[i]))
-            i += 1
-            nxt += rng.exponential(1.0 / rate)
-        lat = [srv.poll(t).latency_ms for t in tickets]
-        st = srv.stats()
-    line = {"config": {"workload": "serving stream: Poisson arrivals, ER/WS 50/50, n log-U[100, "
-                                   "1e4], mean degree U(6,12), failure U(0.01,0.3), lengths "
-                                   "{1..100}, realizations log-U[256,8192], FP32 + recheck",
-                       "probe_queries": k, "rate_qps": rate, "rate_fraction_of_capacity":
-                       args.serve_rate_frac, "arrivals": len(tickets),
-                       "offered_as_specified_qps": 200.0,
-                       "as_specified_overload": 200.0 / cap},
-            "capacity_qps": cap, "capacity_realizations_per_s": probe["realizations_per_s"],
-            "queries": len(tickets), "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-            "mean_ms": st["mean_ms"], "wait_p50_ms": st["wait_p50_ms"],
-            "wait_p99_ms": st["wait_p99_ms"], "realizations_per_s": st["realizations_per_s"],
-            "gteps": st["edge_visits"] / max(st["wall_s"], 1e-9) / 1e9,
-            "slices": st["slices"], "shed": st["shed"], "failed": st["failed"],
-            "latency_check_ms": [float(np.percentile(lat, 50)), float(np.percentile(lat, 99))]}
-    print(json.dumps(line))
+    res = serving_leg(scale=args.serve_scale, arrivals=args.serve_queries,
+                      probe=args.serve_probe, window_s=args.serve_window,
+                      rate_frac=args.serve_rate_frac)
+    print(json.dumps({"config": {"workload": res["workload"]}, "metric": "queries/s, ms", **res}))
     return 0
 
 
@@ -802,10 +899,18 @@ def main():
     ap.add_argument("--perturb-count", type=int, default=1000)
     ap.add_argument("--perturb-n", type=int, default=20000,
                     help="nodes of the synthetic chain of --config perturb-large")
-    ap.add_argument("--serve-probe", type=int, default=6)
-    ap.add_argument("--serve-queries", type=int, default=12,
+    ap.add_argument("--mix-subset", action="store_true",
+                    help="--config mix on every 4th graph at full realization counts")
+    ap.add_argument("--serve-probe", type=int, default=16)
+    ap.add_argument("--serve-queries", type=int, default=100,
                     help="Poisson arrivals in the rate-scaled serving run")
     ap.add_argument("--serve-rate-frac", type=float, default=0.7)
+    ap.add_argument("--serve-scale", type=float, default=1.0 / 16,
+                    help="realization budgets of the rate-scaled serving run, as a fraction")
+    ap.add_argument("--serve-window", type=float, default=2.0,
+                    help="seconds of the specified 200 queries/s offered to the server")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="benchmark line without the mix comparison and serving sub-objects")
     args = ap.parse_args()
     if args.config == "mix":
         return run_mix(args)

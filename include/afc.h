@@ -39,6 +39,7 @@ extern "C" {
 #define AFC_EUNSUPPORTED 7 /* the problem exceeds an implementation limit                  */
 #define AFC_EDEVICE 8      /* a device-side consistency check failed (see message)        */
 #define AFC_EBUSY 9        /* serving: refused for now (over budget, queue full) or pending */
+#define AFC_ECANCELED 10   /* serving: the query was cancelled (afc_server_cancel)           */
 
 #define AFC_FP64 0          /* dependencies delta accumulated in FP64                        */
 #define AFC_FP32_RECHECK 1  /* delta in FP32, realizations with a near-tied top two in FP64 */
@@ -544,6 +545,7 @@ typedef struct {
 
 typedef struct {
   uint64_t submitted, admitted, completed, shed, failed;
+  uint64_t cancelled;          /* queries cancelled before they were counted                 */
   uint64_t realizations;       /* realizations of completed queries                          */
   uint64_t edge_visits;        /* Graph500 edge count of completed queries                   */
   uint64_t slices;             /* batched counting launches                                  */
@@ -572,6 +574,13 @@ int afc_server_poll(afc_server *s, uint64_t ticket, int32_t wait_ms, afc_host_re
                     double *latency_ms);
 
 int afc_server_stats(afc_server *s, afc_serving_stats *out);
+
+/* Cancels the query `ticket`, or every query not yet counted when ticket is 0.  A queued
+ * query leaves the queue at once; an admitted one leaves at the next slice boundary (the slice
+ * already on the GPU completes) and its device memory is freed; a query already counted
+ * finishes normally.  Polling a cancelled ticket returns AFC_ECANCELED.  Returns AFC_OK, or
+ * AFC_EINVAL for an unknown or already collected ticket. */
+int afc_server_cancel(afc_server *s, uint64_t ticket);
 
 /* Finishes every admitted and queued query, then stops the threads and frees everything. */
 void afc_server_destroy(afc_server *s);

@@ -31,7 +31,7 @@ __all__ = [
     "afc_run_host", "afc_absorbing_solve_noalloc", "AFC_FP64", "AFC_FP32_RECHECK",
     "AFC_PATH_AUTO", "AFC_PATH_SHARED", "AFC_PATH_GLOBAL", "AFC_EBUSY", "ServerCfg",
     "ServerStats", "afc_server_create", "afc_server_submit", "afc_server_poll",
-    "afc_server_stats", "afc_server_destroy", "Params", "PerturbStats", "afc_graph_create",
+    "afc_server_stats", "afc_server_cancel", "AFC_ECANCELED", "afc_server_destroy", "Params", "PerturbStats", "afc_graph_create",
     "afc_graph_create_csr", "afc_graph_nodes", "afc_graph_edges", "afc_graph_destroy",
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
@@ -43,6 +43,7 @@ __all__ = [
 
 AFC_OK, AFC_EINVAL, AFC_ENOMEM, AFC_EOVERFLOW, AFC_ESINGULAR = 0, 1, 2, 3, 4
 AFC_ETIMEOUT, AFC_ECUDA, AFC_EUNSUPPORTED, AFC_EDEVICE, AFC_EBUSY = 5, 6, 7, 8, 9
+AFC_ECANCELED = 10
 AFC_FP64, AFC_FP32_RECHECK = 0, 1
 AFC_PATH_AUTO, AFC_PATH_SHARED, AFC_PATH_GLOBAL = 0, 1, 2
 
@@ -117,7 +118,7 @@ class ServerCfg(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", c_u64), ("admitted", c_u64), ("completed", c_u64), ("shed", c_u64),
-                ("failed", c_u64), ("realizations", c_u64), ("edge_visits", c_u64),
+                ("failed", c_u64), ("cancelled", c_u64), ("realizations", c_u64), ("edge_visits", c_u64),
                 ("slices", c_u64), ("peak_bytes", c_u64), ("p50_ms", c_f64), ("p99_ms", c_f64),
                 ("mean_ms", c_f64), ("max_ms", c_f64), ("wait_p50_ms", c_f64),
                 ("wait_p99_ms", c_f64), ("wall_s", c_f64), ("realizations_per_s", c_f64)]
@@ -198,6 +199,7 @@ _SIGS = {
     "afc_server_poll": ([c_p, c_u64, c_i32, ctypes.POINTER(HostResult), ctypes.POINTER(c_f64)],
                         ctypes.c_int),
     "afc_server_stats": ([c_p, ctypes.POINTER(ServerStats)], ctypes.c_int),
+    "afc_server_cancel": ([c_p, c_u64], ctypes.c_int),
     "afc_server_destroy": ([c_p], None),
     "afc_graph_create": ([c_i32, c_i64, c_p, c_p, ctypes.POINTER(c_p)], ctypes.c_int),
     "afc_graph_create_csr": ([c_i32, c_p, c_p, c_p, ctypes.POINTER(c_p)], ctypes.c_int),
@@ -497,6 +499,11 @@ def afc_server_stats(server: int) -> ServerStats:
     st = ServerStats()
     _chk(lib().afc_server_stats(server, ctypes.byref(st)))
     return st
+
+
+def afc_server_cancel(server: int, ticket: int = 0) -> None:
+    """Cancels one query (ticket) or every query not yet counted (ticket 0)."""
+    _chk(lib().afc_server_cancel(server, ticket))
 
 
 def afc_server_destroy(server: int) -> None:

@@ -108,16 +108,20 @@ struct BigGroup {
   unsigned long long edges, verts;
   uint32_t *rp, *arc, *comp, *cinfo, *centre, *rank;
   uint16_t *src;
-  // betweenness: 128-bit fixed point accumulated as (bhi, bc's bits) with 64 fraction bits,
-  // converted to doubles in place (bc) before the selection
+  // betweenness: exact fixed point accumulated in (bc's bits, a1, a2), B 2^64 = bc 2^64 +
+  // a1 2^32 + a2, converted to doubles in place (bc) before the selection
   double *bc;
-  unsigned long long *bhi;
+  unsigned long long *a1, *a2;
   unsigned long long *best;
+  uint16_t *mw;           // smallest alive incident length per node
 };
 
 // bytes of one group's arrays and of one source slot (global path)
 size_t big_group_bytes(uint32_t n, uint64_t arcs);
 uint32_t big_slot_bytes(uint32_t n);
+// bytes of one warp's region of the arena on the settle-step global path (path counts, settle
+// order, pending list, and the distances when they are not kept on chip)
+size_t big_step_slot_bytes(uint32_t n, bool dist_in_arena);
 void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs);
 bool big_config_supported(int block, int team);
 // Runs realizations [0, r_count) of the problem *Pd (device copy) through the global path in

@@ -220,20 +220,23 @@ __device__ __forceinline__ void warp_arcs(uint32_t deg, uint32_t e0, uint8_t *ta
   __syncwarp();
 }
 
-// Betweenness accumulators: B_v = sum over sources of delta_s(v), kept exactly as a 128-bit
-// fixed-point number with 64 fraction bits in two 64-bit words (hi: integer part and carries,
-// lo: fraction).  Every addend x (0 <= x < 2^64) is split exactly, from its bits, into the
-// integer part and the fraction scaled by 2^64 (truncated below 2^-64, i.e. exact whenever
-// x >= 2^-12); integer additions are associative, so the sum does not depend on the order in
-// which sources finish, and B is the same bit for bit whatever the launch shape.  Unique-path
-// dependencies (exact integers) go straight to hi.  Integer operations only: no FP64 work.
-__device__ __forceinline__ void fx_add(unsigned long long *lo, unsigned long long *hi, uint32_t v,
-                                       double x) {
+// Betweenness accumulators of a realization: B_v 2^64 = a0 2^64 + a1 2^32 + a2 (see fx_red).
+struct BcAcc {
+  unsigned long long *a0, *a1, *a2;
+};
+
+// Betweenness accumulation without return values (device-memory reductions): the addend x
+// (0 <= x < 2^64) is split exactly, from its bits, into x 2^64 = xi 2^64 + xf (xf < 2^64,
+// truncated below 2^-64, i.e. exact whenever x >= 2^-12), and xi, the top and the bottom 32 bits of xf go to three
+// 64-bit sums (each far from overflow for fewer than 2^31 addends).  Integer additions are
+// associative, so the total is exact and independent of the order.
+__device__ __forceinline__ void fx_red(unsigned long long *a0, unsigned long long *a1,
+                                       unsigned long long *a2, uint32_t v, double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FFu);
-  if (ex == 0 || (b >> 63)) return;   // zero (or a subnormal far below 2^-64); never negative
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // x = m 2^(ex - 1075)
-  const int sh = ex - 1075 + 64;   // x 2^64 = m 2^sh
+  if (ex == 0 || (b >> 63)) return;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1075 + 64;
   unsigned long long xi, xf;
   if (sh >= 64) {
     xi = m << (sh - 64);
@@ -247,11 +250,20 @@ __device__ __forceinline__ void fx_add(unsigned long long *lo, unsigned long lon
   } else {
     return;
   }
-  if (xf) {
-    const unsigned long long old = atomicAdd(&lo[v], xf);
-    if (old + xf < old) ++xi;   // carry out of the fraction word
+  if (xi) atomicAdd(&a0[v], xi);
+  if (xf >> 32) atomicAdd(&a1[v], xf >> 32);
+  if (xf & 0xFFFFFFFFull) atomicAdd(&a2[v], xf & 0xFFFFFFFFull);
+}
+
+// B_v as a double, written over a0 (each thread converts its own entries).
+__device__ __forceinline__ void fx_finalize3(unsigned long long *a0, const unsigned long long *a1,
+                                             const unsigned long long *a2, uint32_t n) {
+  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const unsigned long long t = a1[v];
+    const unsigned long long lo = a2[v] + (t << 32);
+    const unsigned long long hi = a0[v] + (t >> 32) + (lo < (t << 32) ? 1ull : 0ull);
+    reinterpret_cast<double *>(a0)[v] = (double)hi + __ull2double_rn(lo) * 0x1p-64;
   }
-  if (xi) atomicAdd(&hi[v], xi);
 }
 
 // Correctly rounded reciprocal in the dependency precision.
@@ -272,28 +284,17 @@ __device__ __forceinline__ void dependency(uint64_t sg, DT acc, DT &dep, DT &rho
   }
 }
 
-// The accumulated value as a double, in the storage of the fraction word (B = hi + lo 2^-64;
-// each thread converts its own entries).
-__device__ __forceinline__ void fx_finalize(unsigned long long *lo, const unsigned long long *hi,
-                                            uint32_t n) {
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const double b = (double)hi[v] + __ull2double_rn(lo[v]) * 0x1p-64;
-    reinterpret_cast<double *>(lo)[v] = b;
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 // Bucketed Brandes for graphs whose per-source state does not fit on chip (the global-memory
 // path).  A batch of S sources (srcs[0..S)) in the slots [slot0, slot0 + S) is advanced in
 // lockstep by one team, bucket by bucket (integer Delta-stepping), every pass warp-cooperative
-// over the members' arcs.  Adds delta_s(v) for v != s to the fixed-point accumulators
-// (blo, bhi) of fx_add.  Every thread of the team must call it.
+// over the members' arcs.  Adds delta_s(v) for v != s to the exact accumulators (fx_red).
+// Every thread of the team must call it.
 // ---------------------------------------------------------------------------------------
 template <int TS, int BLOCK, typename DT>
 __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const Realized &H,
                                               const SlotSpace &sp, uint32_t slot0, uint32_t S,
-                                              const uint16_t *srcs, uint32_t dsh,
-                                              unsigned long long *blo, unsigned long long *bhi,
+                                              const uint16_t *srcs, uint32_t dsh, const BcAcc &acc,
                                               CtaCtl *ctl, uint32_t *err_out, uint32_t *ovf_out) {
   const uint32_t n = H.n, W = sp.words;
   constexpr uint32_t kRingMask = kRing - 1u;
@@ -687,14 +688,14 @@ __device__ __forceinline__ bool brandes_batch(const Team<TS, BLOCK> &team, const
             if (sg == 1ull && !any_f) {
               // delta(v) = sum of the successors' subtree sizes: exact in integers
               a.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-              if (!is_src && acc_i) atomicAdd(&bhi[v], (unsigned long long)acc_i);
+              if (!is_src && acc_i) atomicAdd(&acc.a0[v], (unsigned long long)acc_i);
             } else {
               DT dep, rho;
               dependency<DT>(sg, (DT)acc_i + acc_f, dep, rho);
               uint64_t bits = 0;
               *reinterpret_cast<DT *>(&bits) = rho;
               a.sig[v] = bits;
-              if (!is_src) fx_add(blo, bhi, v, (double)dep);
+              if (!is_src) fx_red(acc.a0, acc.a1, acc.a2, v, (double)dep);
             }
             __threadfence_block();
             st_volatile(&a.dist[v], dvm);

@@ -15,9 +15,11 @@
 //            cleared, and a second brandes + select pair redoes exactly the flagged groups in
 //            FP64 (A7)
 // All launches are stream ordered; nothing waits on the host.
-#include "mc_common.cuh"
+#include "mc_steps.cuh"
 
 namespace afc {
+
+__host__ __device__ inline size_t al256(size_t x) { return (x + 255u) & ~size_t(255); }
 
 namespace {
 
@@ -48,9 +50,11 @@ big_prep_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t r0, uin
   components(P, H, G.comp, G.cinfo);
   if (P.per_row) keep_anchor_component(n, anchor, G.comp, G.cinfo);
   bucket_setup(ctl, P.delta);
+  min_lengths(H, G.mw);
   uint32_t *cedges = G.centre;   // scratch until selection
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    cedges[v] = 0; reinterpret_cast<unsigned long long *>(G.bc)[v] = 0ull; G.bhi[v] = 0ull;
+    cedges[v] = 0; reinterpret_cast<unsigned long long *>(G.bc)[v] = 0ull;
+    G.a1[v] = 0ull; G.a2[v] = 0ull;
   }
   __syncthreads();
   for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -134,13 +138,64 @@ big_brandes_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngro
       team.sync();
       if (k0 >= nsrc) break;
       const uint32_t S = min(spt, nsrc - k0);
-      unsigned long long *blo = reinterpret_cast<unsigned long long *>(G.bc);
+      const BcAcc acc{reinterpret_cast<unsigned long long *>(G.bc), G.a1, G.a2};
       if (mode == 1)
-        brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, G.src + k0, dsh, blo,
-                                        G.bhi, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, float>(team, H, sp, team.id * spt, S, G.src + k0, dsh, acc,
+                                        ctl, &G.err, &G.ovf);
       else
-        brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, G.src + k0, dsh, blo,
-                                         G.bhi, ctl, &G.err, &G.ovf);
+        brandes_batch<TS, BLOCK, double>(team, H, sp, team.id * spt, S, G.src + k0, dsh, acc,
+                                         ctl, &G.err, &G.ovf);
+    }
+  }
+}
+
+// Settle-step Brandes (mc_steps.cuh) for the realizations in flight: a persistent grid whose
+// warps each own one source slot -- its distance array in shared memory where it fits (every
+// arc reads it and the relaxations update it atomically), its path counts, settle order and
+// pending list in the warp's region of the device arena -- and claim the sources of the
+// groups one at a time, group by group, so the realized graph being worked on stays hot in L2.
+// mode as for big_brandes_kernel.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1)
+big_steps_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngroups,
+                 unsigned char *arena, size_t slot_stride, uint32_t nsw, int mode,
+                 int dist_on_chip) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  if (warp >= nsw) return;   // the warps are independent: no CTA barrier below
+  const uint32_t n = (uint32_t)Pd->n;
+  unsigned char *mine = arena + ((size_t)blockIdx.x * nsw + warp) * slot_stride;
+  StepSlot sl;
+  sl.sig = reinterpret_cast<uint64_t *>(mine);
+  mine += al256(8ull * n);
+  sl.ord = reinterpret_cast<uint16_t *>(mine);
+  mine += al256(2ull * n);
+  sl.plist = reinterpret_cast<uint16_t *>(mine);
+  mine += al256(2ull * n);
+  sl.dist = dist_on_chip ? reinterpret_cast<uint32_t *>(smem + (size_t)warp * al16(4u * n))
+                         : reinterpret_cast<uint32_t *>(mine);
+  for (uint32_t g = 0; g < ngroups; ++g) {
+    BigGroup &G = groups[g];
+    if (!G.active || (mode == 2 && !G.redo)) continue;
+    const Realized H{n, G.rp, G.arc};
+    const BcAcc acc{reinterpret_cast<unsigned long long *>(G.bc), G.a1, G.a2};
+    const uint32_t nsrc = G.nsrc;
+    uint32_t err = 0, ovf = 0;
+    for (;;) {
+      uint32_t k = 0;
+      if (lane == 0) k = atomicAdd(&G.cursor, 1u);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= nsrc) break;
+      const uint32_t s = G.src[k];
+      const bool ok = mode == 1 ? source_steps<float>(H, G.mw, sl, s, true, acc, err, ovf)
+                                : source_steps<double>(H, G.mw, sl, s, true, acc, err, ovf);
+      if (!ok) break;
+    }
+    err = __reduce_or_sync(kFull, err);
+    ovf = __reduce_or_sync(kFull, ovf);
+    if (lane == 0) {
+      if (err) atomicOr(&G.err, err);
+      if (ovf) atomicOr(&G.ovf, 1u);
     }
   }
 }
@@ -153,7 +208,7 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
   BigGroup &G = groups[blockIdx.x];
   if (!G.active || (redo_only && !G.redo)) return;
   const uint32_t n = (uint32_t)P.n;
-  fx_finalize(reinterpret_cast<unsigned long long *>(G.bc), G.bhi, n);   // doubles in place
+  fx_finalize3(reinterpret_cast<unsigned long long *>(G.bc), G.a1, G.a2, n);   // doubles in place
   __syncthreads();
   SlotArrays s0{};
   s0.sig = reinterpret_cast<uint64_t *>(G.best);
@@ -165,7 +220,8 @@ big_select_kernel(const McDev *__restrict__ Pd, BigGroup *groups, int gap_test, 
   if (recheck) {
     for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
       reinterpret_cast<unsigned long long *>(G.bc)[v] = 0ull;
-      G.bhi[v] = 0ull;
+      G.a1[v] = 0ull;
+      G.a2[v] = 0ull;
     }
     if (threadIdx.x == 0) {
       G.redo = 1;
@@ -206,10 +262,38 @@ cudaError_t launch_brandes_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups
   X(256, 64) X(256, 128) X(256, 256) X(512, 128) X(512, 256) X(512, 512) \
   X(1024, 128) X(1024, 256) X(1024, 512) X(1024, 1024)
 
+template <int BLOCK>
+cudaError_t launch_steps_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups,
+                           unsigned char *arena, size_t stride, uint32_t nsw, int mode,
+                           uint32_t smem_bytes, int dist_on_chip, uint32_t grid,
+                           cudaStream_t stream) {
+  if (smem_bytes > 48u * 1024u)
+    cudaFuncSetAttribute(big_steps_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_bytes);
+  big_steps_kernel<BLOCK><<<grid, BLOCK, smem_bytes, stream>>>(Pd, groups, ngroups, arena, stride,
+                                                               nsw, mode, dist_on_chip);
+  return cudaGetLastError();
+}
+
+// team 0: the settle-step kernel with spt source warps per CTA (slots_on_chip: their distance
+// arrays in shared memory); otherwise the bucketed kernel with teams of `team` threads
 cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *groups,
                            uint32_t ngroups, unsigned char *arena, size_t stride, uint32_t spt,
                            int mode, uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
                            cudaStream_t stream) {
+  if (team == 0) {
+    if (spt < 1 || spt > (uint32_t)block / 32u) return cudaErrorInvalidValue;
+    if (block == 256)
+      return launch_steps_t<256>(Pd, groups, ngroups, arena, stride, spt, mode, smem_bytes,
+                                 slots_on_chip, grid, stream);
+    if (block == 512)
+      return launch_steps_t<512>(Pd, groups, ngroups, arena, stride, spt, mode, smem_bytes,
+                                 slots_on_chip, grid, stream);
+    if (block == 1024)
+      return launch_steps_t<1024>(Pd, groups, ngroups, arena, stride, spt, mode, smem_bytes,
+                                  slots_on_chip, grid, stream);
+    return cudaErrorInvalidValue;
+  }
 #define AFC_X(B, T)                                                                   \
   if (block == B && team == T)                                                        \
     return launch_brandes_t<B, T>(Pd, groups, ngroups, arena, stride, spt, mode,      \
@@ -228,14 +312,17 @@ bool big_config_supported(int block, int team) {
   return false;
 }
 
-static size_t al256(size_t x) { return (x + 255u) & ~size_t(255); }
 
 size_t big_group_bytes(uint32_t n, uint64_t arcs) {
   return al256(4ull * (n + 1)) + al256(4ull * (arcs > 0 ? arcs : 1)) + 4 * al256(4ull * n) +
-         al256(2ull * n) + 3 * al256(8ull * n);
+         2 * al256(2ull * n) + 4 * al256(8ull * n);
 }
 
 uint32_t big_slot_bytes(uint32_t n) { return (slot_bytes_for(n) + 255u) & ~255u; }
+
+size_t big_step_slot_bytes(uint32_t n, bool dist_in_arena) {
+  return al256(8ull * n) + 2 * al256(2ull * n) + (dist_in_arena ? al256(4ull * n) : 0);
+}
 
 void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs) {
   unsigned char *p = base;
@@ -249,7 +336,9 @@ void big_group_carve(BigGroup &G, unsigned char *base, uint32_t n, uint64_t arcs
   G.rank = reinterpret_cast<uint32_t *>(take(4ull * n));
   G.src = reinterpret_cast<uint16_t *>(take(2ull * n));
   G.bc = reinterpret_cast<double *>(take(8ull * n));
-  G.bhi = reinterpret_cast<unsigned long long *>(take(8ull * n));
+  G.a1 = reinterpret_cast<unsigned long long *>(take(8ull * n));
+  G.a2 = reinterpret_cast<unsigned long long *>(take(8ull * n));
+  G.mw = reinterpret_cast<uint16_t *>(take(2ull * n));
   G.best = reinterpret_cast<unsigned long long *>(take(8ull * n));
 }
 
@@ -266,7 +355,7 @@ cudaError_t launch_mc_global(int block, int team, const McDev *Pd, int precision
                              unsigned char *arena, size_t slot_stride, uint32_t spt,
                              uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
                              cudaStream_t stream) {
-  if (!big_config_supported(block, team)) return cudaErrorInvalidValue;
+  if (team != 0 && !big_config_supported(block, team)) return cudaErrorInvalidValue;
   const bool fp32 = (precision == 1);
   for (uint32_t r0 = 0; r0 < r_count; r0 += ngroups) {
     big_prep_kernel<<<ngroups, kPrepThreads, sizeof(CtaCtl), stream>>>(Pd, groups_d, r0, r_count);

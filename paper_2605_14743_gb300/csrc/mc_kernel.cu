@@ -5,36 +5,20 @@
 //   A1  Philox4x32-10 edge draws -> alive-compacted CSR with packed (neighbour, length) arcs,
 //       and the smallest alive length at every node
 //   A2  components by lock-free union-find (root = smallest id), sizes, candidate flags
-//   A3  one warp per source: Dijkstra by settle steps.  Every step settles, at once, all
-//       pending nodes v whose tentative distance d(v) is below d_min + mw(v) (mw: v's smallest
-//       incident length; the "IN" criterion) or below the smallest d(u) + mw(u) over the
-//       pending nodes u (the "OUT" criterion).  Such a distance is final, and no pending node
-//       can precede v on a shortest path, so every predecessor of a step's nodes was settled
-//       in an earlier step.
-//   A4  path counts sigma (exact 64-bit) pulled from those predecessors in the same arc scan
-//       that relaxes the step's outgoing arcs: one scan per arc in the forward direction
-//   A5  dependencies delta step by step in reverse (a successor is always settled in a later
-//       step), one scan per arc; betweenness accumulated exactly in 128-bit fixed point
+//   A3  one warp per source: Dijkstra by settle steps (mc_steps.cuh), source slots on chip
+//   A4  path counts sigma (exact 64-bit) pulled from the settled predecessors in the same arc
+//       scan that relaxes the step's outgoing arcs: one scan per arc in the forward direction
+//   A5  dependencies delta step by step in reverse, one scan per arc; betweenness accumulated
+//       exactly in 128-bit fixed point
 //   A6  tie-ruled argmax per valid component (Sec. 3.2 eq. local-center, Sec. 7.1 Sel_W)
 //       and the transition-count update of every anchor (Alg. 1 / Alg. 2)
 //   A7  FP32 mode: a realization whose top-two gap is under the margin is redone in FP64
 // Per-source results do not depend on which warp or CTA runs the source, and the exact
 // betweenness sum does not depend on the order in which sources finish, so B and every count
 // are the same bit for bit for any launch shape.
-#include "mc_common.cuh"
+#include "mc_steps.cuh"
 
 namespace afc {
-
-// One source slot: dist[n] (u32 | kFlag once settled), sig[n] (sigma, then rho in place),
-// ord[n] (settle order; bit 15 marks the first node of a step) and plist[n] (the pending nodes:
-// discovered, not yet settled, each once).
-struct StepSlot {
-  uint32_t *dist;
-  uint64_t *sig;
-  uint16_t *ord, *plist;
-};
-
-constexpr uint16_t kStepStart = 0x8000u;   // ord entry opens a step (node ids stay below 2^15)
 
 // Shared-memory layout of a counting CTA: control head, the realization (rp, arcs, smallest
 // incident length) and one slot per source warp.  What the source warps do not touch while
@@ -85,298 +69,6 @@ struct CtaScratch {
     a2 = reinterpret_cast<unsigned long long *>(p);
   }
 };
-
-// Betweenness accumulation without return values (device-memory reductions): the addend x
-// (0 <= x < 2^64) is split exactly, from its bits, into x 2^64 = xi 2^64 + xf (xf < 2^64,
-// truncated below 2^-64 as in fx_add), and xi, the top and the bottom 32 bits of xf go to three
-// 64-bit sums (each far from overflow for fewer than 2^31 addends).  Integer additions are
-// associative, so the total is exact and independent of the order.
-__device__ __forceinline__ void fx_red(unsigned long long *a0, unsigned long long *a1,
-                                       unsigned long long *a2, uint32_t v, double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FFu);
-  if (ex == 0 || (b >> 63)) return;
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = ex - 1075 + 64;
-  unsigned long long xi, xf;
-  if (sh >= 64) {
-    xi = m << (sh - 64);
-    xf = 0ull;
-  } else if (sh > 0) {
-    xi = m >> (64 - sh);
-    xf = m << sh;
-  } else if (sh > -53) {
-    xi = 0ull;
-    xf = m >> (-sh);
-  } else {
-    return;
-  }
-  if (xi) atomicAdd(&a0[v], xi);
-  if (xf >> 32) atomicAdd(&a1[v], xf >> 32);
-  if (xf & 0xFFFFFFFFull) atomicAdd(&a2[v], xf & 0xFFFFFFFFull);
-}
-
-// B_v as a double, written over a0 (each thread converts its own entries).
-__device__ __forceinline__ void fx_finalize3(unsigned long long *a0, const unsigned long long *a1,
-                                             const unsigned long long *a2, uint32_t n) {
-  for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
-    const unsigned long long t = a1[v];
-    const unsigned long long lo = a2[v] + (t << 32);
-    const unsigned long long hi = a0[v] + (t >> 32) + (lo < (t << 32) ? 1ull : 0ull);
-    reinterpret_cast<double *>(a0)[v] = (double)hi + __ull2double_rn(lo) * 0x1p-64;
-  }
-}
-
-// Smallest alive incident length of every node (0xFFFF for a node without alive arcs).
-__device__ inline void min_lengths(const Realized &H, uint16_t *mw) {
-  for (uint32_t v = threadIdx.x; v < H.n; v += blockDim.x) {
-    uint32_t m = 0xFFFFu;
-    for (uint32_t e = H.rp[v]; e < H.rp[v + 1]; ++e) m = min(m, H.arc[e] >> 16);
-    mw[v] = (uint16_t)m;
-  }
-}
-
-// Exclusive prefix of x over the warp's lanes; total = the sum over all lanes.
-__device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
-  const uint32_t lane = lane_id();
-  uint32_t incl = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
-  }
-  total = __shfl_sync(kFull, incl, 31);
-  return incl - x;
-}
-
-// Pending-list windows (32 nodes each) loaded together at the start of a step's selection.
-constexpr int kPendCache = 8;
-
-// ---------------------------------------------------------------------------------------
-// Brandes from source s by one warp (Sec. 3.1 definitions: d_H, sigma_st, ordered-pair
-// betweenness).  Forward: settle steps (see the file comment), sigma pulled from the
-// predecessors while the step's arcs are relaxed; the next step's bounds d_min and
-// min (d + mw) come from the pending nodes that stay and from the relaxations (every pending
-// node's current distance is one of those values, and no recorded value is below the node's
-// current distance), so no separate pass over the pending list is needed.  Backward (want_delta): the steps in
-// reverse; rho(v) = (1 + delta(v)) / sigma(v) replaces sigma in place, delta(v) =
-// sigma(v) * sum over successors w of rho(w) in arc order; unique-path subtrees (sigma = 1
-// throughout) stay exact integers.  delta_s(v) for v != s goes to the exact accumulators of
-// the CTA scratch (fx_red).  Every lane of the warp must call it; err / ovf collect
-// device-error bits and path-count overflow per lane.
-// ---------------------------------------------------------------------------------------
-template <typename DT>
-__device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSlot &sl,
-                             uint32_t s, bool want_delta, const CtaScratch &cs, uint32_t &err,
-                             uint32_t &ovf) {
-  const uint32_t n = H.n, lane = lane_id();
-  for (uint32_t v = lane; v < n; v += 32) sl.dist[v] = kInf;
-  __syncwarp();
-  if (lane == 0) {
-    sl.dist[s] = 0u;
-    sl.sig[s] = 1ull;
-    sl.plist[0] = (uint16_t)s;
-  }
-  __syncwarp();
-
-  // ---- forward
-  uint32_t nord = 0, pc = 1;                   // settled nodes, pending nodes (warp-uniform)
-  uint32_t dmin = 0u, lout = (uint32_t)mw[s];   // d_min and min (d + mw) over the pending nodes
-  for (uint32_t step = 0;; ++step) {
-    if (step > n) { err |= kErrPassLimit; return false; }
-    if (pc == 0) break;   // nothing pending: the source's component is done
-    // (1) settle every pending v with d(v) < d_min + mw(v) (IN) or d(v) < lout (OUT; the node
-    // at d_min always qualifies): append it to ord, flag it settled; the others stay,
-    // compacted in order, and give the next step's bounds together with the relaxations below
-    const uint32_t g0 = nord;
-    const uint32_t below = lanemask_lt();
-    uint32_t kept = 0, ndmin = kInf, nlout = 0xFFFFFFFFu;
-    auto place = [&](bool sel, bool keep, uint32_t sm, uint32_t km, uint32_t v, uint32_t d,
-                     uint32_t m) {
-      if (sel) {
-        const uint32_t pos = nord + (uint32_t)__popc(sm & below);
-        if (pos < n) {
-          sl.ord[pos] = (uint16_t)(v | (pos == g0 ? kStepStart : 0u));
-          sl.dist[v] = d | kFlag;
-        } else {
-          err |= kErrCapacity;
-        }
-      } else if (keep) {
-        sl.plist[kept + (uint32_t)__popc(km & below)] = (uint16_t)v;
-        ndmin = min(ndmin, d);
-        nlout = min(nlout, d + m);
-      }
-      nord += (uint32_t)__popc(sm);
-      kept += (uint32_t)__popc(km);
-    };
-    {
-      // the first kPendCache windows: every load first, then the decisions, then the stores
-      uint32_t cv[kPendCache], cm[kPendCache], cd[kPendCache];
-#pragma unroll
-      for (int c = 0; c < kPendCache; ++c) {
-        const uint32_t j = (uint32_t)c * 32u + lane;
-        cv[c] = j < pc ? (uint32_t)sl.plist[j] : 0u;
-      }
-#pragma unroll
-      for (int c = 0; c < kPendCache; ++c) {
-        const bool valid = (uint32_t)c * 32u + lane < pc;
-        cm[c] = valid ? (uint32_t)mw[cv[c]] : 0u;
-        cd[c] = valid ? (uint32_t)sl.dist[cv[c]] : 0u;
-      }
-#pragma unroll
-      for (int c = 0; c < kPendCache; ++c) {
-        if ((uint32_t)c * 32u >= pc) break;   // warp-uniform
-        const bool valid = (uint32_t)c * 32u + lane < pc;
-        const bool sel = valid && (cd[c] < dmin + cm[c] || cd[c] < lout);
-        const uint32_t sm = __ballot_sync(kFull, sel), km = __ballot_sync(kFull, valid && !sel);
-        place(sel, valid && !sel, sm, km, cv[c], cd[c], cm[c]);
-      }
-    }
-    // the other windows: each is read before its kept nodes move down (to lower positions)
-    for (uint32_t j0 = kPendCache * 32u; j0 < pc; j0 += 32u) {
-      const uint32_t j = j0 + lane;
-      uint32_t v = 0, d = 0, m = 0;
-      if (j < pc) {
-        v = sl.plist[j];
-        d = sl.dist[v];
-        m = mw[v];
-      }
-      const bool sel = j < pc && (d < dmin + m || d < lout);
-      const uint32_t smw = __ballot_sync(kFull, sel);
-      const uint32_t kmw = __ballot_sync(kFull, j < pc && !sel);
-      place(sel, j < pc && !sel, smw, kmw, v, d, m);
-    }
-    pc = kept;
-    __syncwarp();
-    // (3) the step's arcs, one member per lane: sigma from the (settled) predecessors and
-    // relaxation of the rest; each group of four arcs issues its loads and atomics together
-    const uint32_t g1 = min(nord, n);
-    for (uint32_t c0 = g0; c0 < g1; c0 += 32) {
-      const uint32_t k = c0 + lane;
-      const bool mine = k < g1;
-      uint32_t v = 0, dv = 0, e = 0, e1 = 0;
-      if (mine) {
-        v = sl.ord[k] & 0x7FFFu;
-        dv = sl.dist[v] & kMask;
-        e = H.rp[v];
-        e1 = H.rp[v + 1];
-      }
-      unsigned long long sg = 0;
-      while (__any_sync(kFull, e < e1)) {
-        uint32_t pk[4], du[4], old[4];
-        unsigned long long x[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) du[t] = e + t < e1 ? sl.dist[pk[t] & 0xFFFFu] : kFlag;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const uint32_t u = pk[t] & 0xFFFFu, len = pk[t] >> 16;
-          // a predecessor: settled in an earlier step
-          const bool pred = (du[t] & kFlag) && (du[t] & kMask) + len == dv && e + t < e1;
-          x[t] = pred ? sl.sig[u] : 0ull;
-          const uint32_t nd = dv + len;
-          const bool relax = !(du[t] & kFlag) && nd < du[t];
-          old[t] = relax ? atomicMin(&sl.dist[u], nd) : 0u;
-          if (relax) {   // a pending node's new distance: the next step's bounds
-            ndmin = min(ndmin, nd);
-            nlout = min(nlout, nd + (uint32_t)mw[u]);
-          }
-        }
-        // discovered now (each node once): onto the pending list
-        uint32_t dm[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) dm[t] = __ballot_sync(kFull, old[t] == kInf);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const unsigned long long nx = sg + x[t];
-          if (nx < sg) ovf = 1u;
-          sg = nx;
-          if ((dm[t] >> lane) & 1u)
-            sl.plist[pc + (uint32_t)__popc(dm[t] & lanemask_lt())] = (uint16_t)(pk[t] & 0xFFFFu);
-          pc += (uint32_t)__popc(dm[t]);
-        }
-        e += 4;
-      }
-      if (mine && v != s) sl.sig[v] = sg;
-    }
-    dmin = __reduce_min_sync(kFull, ndmin);
-    lout = __reduce_min_sync(kFull, nlout);
-    __syncwarp();
-  }
-  if (!want_delta) return true;
-
-  // ---- backward: the steps in reverse order of settlement, one member per lane
-  uint32_t hi = min(nord, n);
-  while (hi > 0) {
-    // the step holding position hi - 1 starts at the nearest step mark at or below it
-    uint32_t lo = 0;
-    for (int32_t top = (int32_t)hi - 1; top >= 0; top -= 32) {
-      const int32_t p = top - (int32_t)lane;
-      const bool mark = p >= 0 && (sl.ord[p] & kStepStart);
-      const uint32_t mm = __ballot_sync(kFull, mark);
-      if (mm) {
-        lo = (uint32_t)(top - (__ffs(mm) - 1));
-        break;
-      }
-    }
-    for (uint32_t c0 = lo; c0 < hi; c0 += 32) {
-      const uint32_t k = c0 + lane;
-      const bool mine = k < hi;
-      uint32_t v = 0, dv = 0, e = 0, e1 = 0;
-      uint64_t sg = 0;
-      if (mine) {
-        v = sl.ord[k] & 0x7FFFu;
-        dv = sl.dist[v] & kMask;
-        e = H.rp[v];
-        e1 = H.rp[v + 1];
-        sg = sl.sig[v];
-      }
-      // the successors' rho in arc order: integral ones exactly, the others in DT
-      uint32_t acc_i = 0;
-      DT acc_f = 0;
-      bool any_f = false;
-      while (__any_sync(kFull, e < e1)) {
-        uint32_t pk[4];
-        uint64_t rw[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const bool suc = e + t < e1 && (sl.dist[pk[t] & 0xFFFFu] & kMask) == dv + (pk[t] >> 16);
-          rw[t] = suc ? sl.sig[pk[t] & 0xFFFFu] : kIntTag;   // kIntTag alone adds 0
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          if (rw[t] & kIntTag) {
-            acc_i += (uint32_t)rw[t];
-          } else {
-            acc_f += *reinterpret_cast<const DT *>(&rw[t]);
-            any_f = true;
-          }
-        }
-        e += 4;
-      }
-      if (mine) {
-        if (sg == 1ull && !any_f) {
-          // delta(v) = sum of the successors' subtree sizes: exact in integers
-          sl.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
-          if (v != s && acc_i) atomicAdd(&cs.a0[v], (unsigned long long)acc_i);
-        } else {
-          DT dep, rho;
-          dependency<DT>(sg, (DT)acc_i + acc_f, dep, rho);
-          uint64_t bits = 0;
-          *reinterpret_cast<DT *>(&bits) = rho;
-          sl.sig[v] = bits;
-          if (v != s) fx_red(cs.a0, cs.a1, cs.a2, v, (double)dep);
-        }
-      }
-    }
-    __syncwarp();
-    hi = lo;
-  }
-  return true;
-}
 
 // ---------------------------------------------------------------------------------------
 // The persistent kernel.  Work item w enumerates (problem, realization) pairs of all
@@ -484,8 +176,9 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
           k = __shfl_sync(kFull, k, 0);
           if (k >= nsrc) break;
           const uint32_t s = src[k];
-          const bool ok = use32 ? source_steps<float>(H, mw, sl, s, true, cs, err, ovf)
-                                : source_steps<double>(H, mw, sl, s, true, cs, err, ovf);
+          const BcAcc acc{cs.a0, cs.a1, cs.a2};
+          const bool ok = use32 ? source_steps<float>(H, mw, sl, s, true, acc, err, ovf)
+                                : source_steps<double>(H, mw, sl, s, true, acc, err, ovf);
           if (!ok) break;
         }
         err = __reduce_or_sync(kFull, err);
@@ -588,7 +281,7 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
     const uint32_t s = (sv >= 0 && (uint32_t)sv < n) ? (uint32_t)sv : 0u;
     const StepSlot sl = L.slot(smem, warp, n);
     uint32_t err = 0, ovf = 0;
-    source_steps<double>(H, mw, sl, s, false, CtaScratch{}, err, ovf);
+    source_steps<double>(H, mw, sl, s, false, BcAcc{}, err, ovf);
     err = __reduce_or_sync(kFull, err);
     ovf = __reduce_or_sync(kFull, ovf);
     if (lane == 0) {

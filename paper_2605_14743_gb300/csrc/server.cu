@@ -69,6 +69,7 @@ struct Job {
   std::string err;
   int state = kWaiting;
   bool want_counts = false;   // submitted through afc_submit: the result carries the counts
+  bool cancel = false;        // cancelled while admitted: leaves at the next slice boundary
 };
 
 using JobP = std::shared_ptr<Job>;
@@ -212,11 +213,20 @@ void scheduler_main(afc_server *S) {
         failed.push_back(j);
       }
     }
+    std::vector<JobP> done;
     {
       std::lock_guard<std::mutex> lk(S->mu);
       for (JobP &j : admit)
         if (j->status == AFC_OK) S->active.push_back(j);
-      batch = S->active;
+      // cancelled queries leave here (their slices so far are already on the stream)
+      for (JobP &j : S->active)
+        if (j->cancel) {
+          j->status = AFC_ECANCELED;
+          j->err = "query cancelled";
+          done.push_back(j);
+        } else {
+          batch.push_back(j);
+        }
     }
     // The next slice: the admitted queries with the least remaining work first (at most
     // slice_queries of them), each advanced by a chunk of realizations sized so that the slice
@@ -227,7 +237,6 @@ void scheduler_main(afc_server *S) {
       return ca < cb || (ca == cb && a->ticket < b->ticket);
     });
     if (batch.size() > S->cfg.slice_queries) batch.resize(S->cfg.slice_queries);
-    std::vector<JobP> done;
     if (!batch.empty()) {
       const double share = 4.0 * (double)S->sms * kUnitWork / (double)batch.size();
       std::vector<afc_mc_problem> probs;
@@ -421,6 +430,8 @@ void finisher_main(afc_server *S) {
         S->st.realizations += j->q.realizations;
         S->st.edge_visits += j->res.stats.edge_visits;
         S->lat_ms.push_back(1e3 * (j->t_done - j->t_submit));
+      } else if (j->status == AFC_ECANCELED) {
+        S->st.cancelled++;
       } else {
         S->st.failed++;
       }
@@ -626,6 +637,37 @@ int afc_server_stats(afc_server *S, afc_serving_stats *out) {
   out->wait_p99_ms = percentile(S->wait_ms, 0.99);
   out->wall_s = S->t_first < 0 ? 0.0 : std::max(0.0, S->t_last - S->t_first);
   out->realizations_per_s = out->wall_s > 0 ? (double)out->realizations / out->wall_s : 0.0;
+  return AFC_OK;
+}
+
+int afc_server_cancel(afc_server *S, uint64_t ticket) {
+  if (!S) return afc::report_error(AFC_EINVAL, "null server");
+  std::vector<JobP> targets;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (ticket) {
+      auto it = S->jobs.find(ticket);
+      if (it == S->jobs.end()) return afc::report_error(AFC_EINVAL, "unknown or collected ticket");
+      targets.push_back(it->second);
+    } else {
+      for (auto &kv : S->jobs) targets.push_back(kv.second);
+    }
+    const double t = now_s();
+    for (JobP &j : targets) {
+      if (j->state == kWaiting) {
+        S->waiting.erase(std::find(S->waiting.begin(), S->waiting.end(), j));
+        j->status = AFC_ECANCELED;
+        j->err = "query cancelled";
+        j->state = kDone;
+        j->t_done = t;
+        S->st.cancelled++;
+      } else if (j->state == kActive) {
+        j->cancel = true;
+      }
+    }
+  }
+  S->cv_done.notify_all();
+  S->cv_sched.notify_one();
   return AFC_OK;
 }
 

@@ -610,6 +610,11 @@ class Server:
         return ServedResult(ticket, b, mu, counts, r.expected_T, r.b_f, r.c, st,
                             np.array(list(r.perturb_counters), np.uint64), lat)
 
+    def cancel(self, ticket: int = 0) -> None:
+        """Cancels one query, or every query not yet counted (ticket 0)."""
+        from . import afc_server_cancel
+        afc_server_cancel(self.handle, ticket)
+
     def stats(self) -> dict:
         from . import afc_server_stats
         st = afc_server_stats(self.handle)

@@ -107,3 +107,32 @@ def test_bounded_wait_runs_out_with_timeout():
         res = srv.poll(t)
     assert res is not None and res.stats["realizations"] == wl.realizations
     assert abs(res.b.sum() - 1.0) < 1e-9
+
+
+def test_cancel_drops_queued_and_admitted_queries():
+    """Cancelling: queued queries leave at once, admitted ones at the next slice boundary; their
+    tickets poll as AFC_ECANCELED, a query counted before the cancel finishes normally, and the
+    server can then be closed without running the cancelled work."""
+    import time
+    big = workload("ws1000")                     # ~2 s of counting each
+    small = variant(workload("small_er"), realizations=200)
+    with afc.Server(max_active=2) as srv:
+        first = srv.submit(small)
+        assert srv.poll(first) is not None       # counted before the cancel
+        ts = [srv.submit(big) for _ in range(6)]  # two admitted, four queued
+        time.sleep(0.3)
+        srv.cancel()
+        for t in ts:
+            with pytest.raises(afc.AfcError) as e:
+                srv.poll(t)
+            assert e.value.code == afc.AFC_ECANCELED
+        st = srv.stats()
+        t0 = time.perf_counter()
+    assert time.perf_counter() - t0 < 10.0
+    assert st["cancelled"] == 6 and st["completed"] == 1 and st["failed"] == 0
+    with afc.Server() as srv:
+        t = srv.submit(small)
+        with pytest.raises(afc.AfcError) as e:
+            srv.cancel(t + 1000)                 # unknown ticket
+        assert e.value.code == afc.AFC_EINVAL
+        assert srv.poll(t) is not None
