@@ -546,11 +546,17 @@ def bootstrap(next_states, alpha, B, seed, level=0.95, s=None, eta=1e-6):
     return b_rep, T_rep, lo, hi
 
 
+# HiGHS feasibility tolerances for the oracle's LPs (its smallest accepted values; the default
+# 1e-7 lets bounds be missed by that much)
+_HIGHS_TIGHT = {"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10}
+
+
 def robust_inner(Q0, eps, r_min, v, v_bot, support_only=True):
     """Row-wise robust inner problem (Sec. 8, post-processing on the estimated AMC):
     T_i(v) = inf over q_i in U_i of sum_j q_ij v_j + (1 - sum_j q_ij) v_bot, with U_i the box
     [(Q0_ij - eps)_+, min(Q0_ij + eps, 1)] of Sec. 5.1 (on the support {j : Q0_ij > 0} when
-    support_only, else on every j) and sum_j q_ij <= 1 - r_min.  One LP per row (scipy HiGHS).
+    support_only, else on every j) and sum_j q_ij <= 1 - r_min.  One LP per row (scipy HiGHS,
+    feasibility tolerances 1e-10).
     Returns (T [n], Qstar [n, n] a minimiser)."""
     from scipy.optimize import linprog
     Q0 = np.asarray(Q0, np.float64)
@@ -566,7 +572,7 @@ def robust_inner(Q0, eps, r_min, v, v_bot, support_only=True):
         lo = np.maximum(Q0[i, cols] - eps, 0.0)
         hi = np.minimum(Q0[i, cols] + eps, 1.0)
         res = linprog(v[cols] - v_bot, A_ub=np.ones((1, cols.size)), b_ub=[1.0 - r_min],
-                      bounds=list(zip(lo, hi)), method="highs")
+                      bounds=list(zip(lo, hi)), method="highs", options=_HIGHS_TIGHT)
         if not res.success:
             raise RuntimeError("robust_inner: row %d: %s" % (i, res.message))
         T[i] = v_bot + res.fun
@@ -730,11 +736,15 @@ def perturb_sweep(Q0, r0, s, p_begin, p_count, radius, r_min, seed, top_k=5, K2=
                         None if kl is None else kl[:p_count])
 
 
-def w1_graph(n, eu, ev, x, y):
+def w1_graph(n, eu, ev, x, y, certificate=False):
     """Wasserstein-1 distance between distributions x and y on the nodes with the base
     graph's shortest-path (hop) metric (Sec. 9 robust experiment): the transshipment LP
     min sum_e (f+_e + f-_e) with net outflow x - y at every node (Beckmann's formulation),
-    solved by scipy's HiGHS.  Assumes sum x = sum y and a connected support."""
+    solved by scipy's HiGHS with feasibility tolerances of 1e-10 (its default 1e-7 admits flows
+    slightly below zero, whose cost undercuts the optimum).  Assumes sum x = sum y and a
+    connected support.  certificate=True also returns the flow [2m] (f+ then f-) and HiGHS's
+    node potentials phi [n] (the dual: |phi_u - phi_v| <= 1 on every edge, and at the optimum
+    phi . (x - y) equals the flow's cost)."""
     from scipy.optimize import linprog
     from scipy.sparse import coo_matrix
     eu = np.asarray(eu, np.int64)
@@ -745,8 +755,13 @@ def w1_graph(n, eu, ev, x, y):
     cols = np.concatenate([e, e, m + e, m + e])
     vals = np.concatenate([np.ones(m), -np.ones(m), np.ones(m), -np.ones(m)])
     A = coo_matrix((vals, (rows, cols)), shape=(n, 2 * m)).tocsr()
-    res = linprog(np.ones(2 * m), A_eq=A, b_eq=np.asarray(x, np.float64) - np.asarray(y, np.float64),
-                  bounds=(0, None), method="highs")
+    b = np.asarray(x, np.float64) - np.asarray(y, np.float64)
+    res = linprog(np.ones(2 * m), A_eq=A, b_eq=b, bounds=(0, None), method="highs",
+                  options=_HIGHS_TIGHT)
     if not res.success:
         raise RuntimeError("w1_graph: " + res.message)
+    if m and res.x.min() < -1e-12:
+        raise RuntimeError("w1_graph: the LP returned a flow below zero (%g)" % res.x.min())
+    if certificate:
+        return float(res.fun), res.x, np.asarray(res.eqlin.marginals, np.float64)
     return float(res.fun)

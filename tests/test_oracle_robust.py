@@ -43,6 +43,33 @@ def test_w1_closed_form_on_a_path_and_transport_lp():
         assert abs(O.w1_graph(n, eu, ev, x, y) - O.w1_graph(n, eu, ev, y, x)) <= 1e-9
 
 
+@pytest.mark.parametrize("n,seed", [(300, 5), (120, 8)])
+def test_w1_optimality_certificate(n, seed):
+    """Weak duality certifies the oracle's value whatever solver produced it: a flow that meets
+    the node balances with no negative entry costs at least W1, potentials that differ by at
+    most 1 across every edge give phi . (x - y) <= W1, so equal values pin the optimum.  The
+    300-node case is one where HiGHS at its default tolerances returned an entry of -7e-8 and a
+    value 7e-8 below the optimum."""
+    from afc_inputs import ws_edges
+    eu, ev = ws_edges(n, 6, 0.1, seed)
+    rng = np.random.default_rng(2)
+    x = rng.random((5, n))
+    x /= x.sum(axis=1, keepdims=True)
+    y = rng.random(n)
+    y /= y.sum()
+    for k in range(5):
+        val, f, phi = O.w1_graph(n, eu, ev, x[k], y, certificate=True)
+        m = len(eu)
+        fp, fm = f[:m], f[m:]
+        assert f.min() >= -1e-15 and abs(val - f.sum()) <= 1e-12
+        out = np.zeros(n)
+        np.add.at(out, eu, fp - fm)
+        np.add.at(out, ev, fm - fp)
+        assert np.abs(out - (x[k] - y)).max() <= 1e-14
+        assert np.abs(phi[eu] - phi[ev]).max() <= 1 + 1e-9
+        assert abs(val - phi @ (x[k] - y)) <= 1e-9 * max(val, 1.0)
+
+
 def test_multiplicative_row_model():
     rng = np.random.default_rng(5)
     n, rel, r_min = 40, 0.5, 0.05
