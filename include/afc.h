@@ -366,6 +366,41 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out);
 
+/* The same distances on the device (Sec. 9 robust experiment): out[k] = W1(x_k, y) for the
+ * `count` DEVICE rows x_k = x + k n against DEVICE y [n], over the graph's DEVICE symmetric CSR
+ * (row_ptr [n+1], col [2m], eid [2m], afc_csr_from_edges layout).  Exact: the min-cost flow of
+ * unit edge costs, solved per row by one warp with the primal-dual method (Dijkstra phases on
+ * reduced costs, then a blocking flow on the zero-reduced-cost arcs); masses settled to a
+ * relative 1e-14 of max_v |x_kv - y_v|; out[k] = sum over edges of |flow| in a fixed order.
+ * DEVICE out [count].  Workspace: afc_w1_batch_workspace(n, m, count) bytes (256 when a row's
+ * state fits in shared memory).  SYNCHRONISES `stream`.  Errors: AFC_EINVAL for bad arguments
+ * or when more than 1e-9 of some row's excess mass reaches no deficit (x_k and y differ in total
+ * on a connected component), AFC_EDEVICE when an iteration bound or a flow invariant fails. */
+size_t afc_w1_batch_workspace(int32_t n, int64_t m, int32_t count);
+int afc_w1_batch(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                 const int32_t *eid, const double *x, const double *y, int32_t count, double *out,
+                 void *workspace, size_t workspace_bytes, void *stream);
+
+/* Ranking under the tie band (the ordering the sweep and the centre rule use, Sec. 5.5 and
+ * Sec. 2.3): rank[v] = #{u != v : b_u - b_v > tie_rel max b, or |b_u - b_v| <= tie_rel max b and
+ * u < v}; the band is not transitive, so equal counts are ordered by node id: topk[p] = the node
+ * at position p < k of the order (rank[v], v).  The Top-k of the rank-stability check (Sec. 8:
+ * estimates from M and from 2M realizations) compares two such lists.  DEVICE in b [n]; DEVICE
+ * out rank [n], topk [k] (may be NULL when k = 0).  O(n^2) work.  Asynchronous on `stream`. */
+int afc_rank_order(int32_t n, const double *b, double tie_rel, int32_t k, int32_t *rank,
+                   int32_t *topk, void *stream);
+
+/* Reductions of the sampled robust search (Sec. 9; Remark on the robust optimisation viewpoint
+ * in Sec. 5): arg[0] / arg[1] = the sample maximising d1 / d2 (DEVICE [count] each, e.g. the KL
+ * values of afc_perturb_params.kl_out and the afc_w1_batch distances; NULL gives -1), ties to
+ * the smaller index and NaN above every number (numpy's argmax); b_low / b_high [n] = per node
+ * the smallest / largest of b0 and the sampled rows b_rows [count][n] (the sampled envelopes,
+ * an inner approximation of the inf / sup over the whole uncertainty set).  All DEVICE; any
+ * output may be NULL.  Asynchronous on `stream`. */
+int afc_robust_summary(int32_t n, int32_t count, const double *b_rows, const double *b0,
+                       const double *d1, const double *d2, int32_t *arg, double *b_low,
+                       double *b_high, void *stream);
+
 /* Set-constrained kernels (Sec. 7).  Counts of the hard-filtered kernel P^W come from
  * afc_transition_counts with in_w / top_k; of the fallback kernel P^{W,fb} with use_fallback,
  * which also fills fallback_count.  b^W, b^{W,fb} and b^W . f come from afc_absorbing_solve on

@@ -36,7 +36,8 @@ __all__ = [
     "afc_params_default", "afc_run", "afc_result_counts", "afc_result_afc", "afc_result_diag",
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
-    "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_robust_inner",
+    "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_w1_batch_workspace",
+    "afc_w1_batch", "afc_rank_order", "afc_robust_summary", "afc_robust_inner",
     "afc_robust_value_workspace", "afc_robust_value", "afc_weight_table_normal",
     "afc_measure_fma_rate",
 ]
@@ -157,6 +158,11 @@ _SIGS = {
     "afc_feasibility": ([ctypes.POINTER(Chain), c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_bootstrap_workspace": ([c_i32, c_i32, c_u32, c_u32], c_sz),
     "afc_w1_graph": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_i32, c_p], ctypes.c_int),
+    "afc_w1_batch_workspace": ([c_i32, c_i64, c_i32], c_sz),
+    "afc_w1_batch": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_p, c_i32, c_p, c_p, c_sz, c_p],
+                     ctypes.c_int),
+    "afc_rank_order": ([c_i32, c_p, c_f64, c_i32, c_p, c_p, c_p], ctypes.c_int),
+    "afc_robust_summary": ([c_i32, c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_measure_fma_rate": ([c_i32, c_p, c_p], ctypes.c_int),
     "afc_weight_table_normal": ([c_i64, c_p, c_u32, c_f64, c_f64, c_p, c_p, c_sz, c_p],
                                 ctypes.c_int),
@@ -365,6 +371,25 @@ def afc_w1_graph(n, eu, ev, x, y):
     _chk(lib().afc_w1_graph(int(n), int(eu.shape[0]), _ptr(eu), _ptr(ev), _ptr(x), _ptr(y),
                             int(x.shape[0]), _ptr(out)))
     return out
+
+
+def afc_w1_batch_workspace(n, m, count) -> int:
+    return int(lib().afc_w1_batch_workspace(int(n), int(m), int(count)))
+
+
+def afc_w1_batch(n, m, row_ptr, col, eid, x, y, count, out, workspace, workspace_bytes, stream):
+    _chk(lib().afc_w1_batch(int(n), int(m), _ptr(row_ptr), _ptr(col), _ptr(eid), _ptr(x), _ptr(y),
+                            int(count), _ptr(out), _ptr(workspace), int(workspace_bytes), stream))
+
+
+def afc_rank_order(n, b, tie_rel, k, rank, topk, stream):
+    _chk(lib().afc_rank_order(int(n), _ptr(b), float(tie_rel), int(k), _ptr(rank), _ptr(topk),
+                              stream))
+
+
+def afc_robust_summary(n, count, b_rows, b0, d1, d2, arg, b_low, b_high, stream):
+    _chk(lib().afc_robust_summary(int(n), int(count), _ptr(b_rows), _ptr(b0), _ptr(d1), _ptr(d2),
+                                  _ptr(arg), _ptr(b_low), _ptr(b_high), stream))
 
 
 def afc_pool_summaries(n, b, in_w, fallback_set, b_pool, b_censored, mass, stream):

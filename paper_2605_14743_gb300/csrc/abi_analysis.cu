@@ -32,6 +32,29 @@ int robust_checks(const afc_chain *chain, const uint32_t *counts, double eps, do
 
 size_t al256h(size_t x) { return (x + 255u) & ~size_t(255); }
 
+// Rows of afc_w1_batch in flight: one 32-thread CTA each.  Its state and a copy of the graph
+// in shared memory when both fit, else its state alone, else both in device memory (a slab
+// per CTA); as many CTAs per SM as shared memory holds (at most 16), 8 per SM on the slab.
+struct W1Plan {
+  int mode = 0, grid = 1;
+  size_t slot = 0, slab = 0;
+};
+
+W1Plan w1_plan(int32_t n, int64_t m, int32_t count) {
+  const DevInfo d = dev_info();
+  W1Plan p;
+  p.slot = w1_slot_bytes(n, m);
+  const size_t cap = (size_t)std::max(0, d.smem_optin - 1024);
+  const size_t both = p.slot + w1_graph_bytes(n, m);
+  p.mode = both <= cap ? 2 : p.slot <= cap ? 1 : 0;
+  const size_t dyn = p.mode == 2 ? both : p.slot;
+  const size_t per_sm = p.mode ? std::min<size_t>(16, (228u * 1024u) / (dyn + 1024u)) : 8;
+  p.grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(count, (int64_t)std::max(1, d.sms) * (int64_t)std::max<size_t>(1, per_sm)));
+  p.slab = p.mode ? 0 : p.slot * (size_t)p.grid;
+  return p;
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,6 +302,61 @@ int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, con
     if (failed) return fail(AFC_ENOMEM, "afc_w1_graph: host allocation failed");
     return AFC_OK;
   });
+}
+
+size_t afc_w1_batch_workspace(int32_t n, int64_t m, int32_t count) {
+  if (n < 1 || m < 0 || count < 0) return 0;
+  return 256 + w1_plan(n, m, count).slab;
+}
+
+int afc_w1_batch(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col,
+                 const int32_t *eid, const double *x, const double *y, int32_t count, double *out,
+                 void *workspace, size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.w1_batch");
+  if (n < 1 || m < 0 || count < 0 || !row_ptr || !y || (count > 0 && (!x || !out)) ||
+      (m > 0 && (!col || !eid)))
+    return fail(AFC_EINVAL, "bad arguments");
+  if (m > 0x7FFFFFFFll / 2) return fail(AFC_EUNSUPPORTED, "more than 2^30 edges");
+  const W1Plan p = w1_plan(n, m, count);
+  if (!workspace || workspace_bytes < 256 + p.slab)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes,
+                256 + p.slab);
+  if (count == 0) return AFC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  cudaError_t e = launch_w1(n, m, row_ptr, col, eid, x, y, count, out, ws + 256, p.mode,
+                            p.grid, status, s);
+  if (e != cudaSuccess) return cuda_fail(e, "w1 launch");
+  uint32_t h = 0;
+  AFC_CUDA(cudaMemcpyAsync(&h, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  AFC_CUDA(cudaStreamSynchronize(s));
+  if (h & 1u)
+    return fail(AFC_EINVAL, "mass that reaches no deficit: x_k and y differ in total on some "
+                            "connected component");
+  if (h & 2u) return fail(AFC_EDEVICE, "w1: an iteration bound was hit");
+  if (h & 4u) return fail(AFC_EDEVICE, "w1: a flow invariant failed");
+  return AFC_OK;
+}
+
+int afc_rank_order(int32_t n, const double *b, double tie_rel, int32_t k, int32_t *rank,
+                   int32_t *topk, void *stream) {
+  if (n < 1 || !b || !rank || k < 0 || k > n || (k > 0 && !topk) || !(tie_rel >= 0.0))
+    return fail(AFC_EINVAL, "bad arguments");
+  cudaError_t e = launch_rank(n, b, tie_rel, k, rank, topk, (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "rank launch");
+}
+
+int afc_robust_summary(int32_t n, int32_t count, const double *b_rows, const double *b0,
+                       const double *d1, const double *d2, int32_t *arg, double *b_low,
+                       double *b_high, void *stream) {
+  if (n < 1 || count < 0 || !b0 || (count > 0 && !b_rows && (b_low || b_high)) ||
+      (arg && count > 0 && !d1 && !d2))
+    return fail(AFC_EINVAL, "bad arguments");
+  cudaError_t e = launch_robust_summary(n, count, b_rows, b0, d1, d2, arg, b_low, b_high,
+                                        (cudaStream_t)stream);
+  return e == cudaSuccess ? AFC_OK : cuda_fail(e, "robust summary launch");
 }
 
 }  // extern "C"

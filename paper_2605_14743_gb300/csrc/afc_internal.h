@@ -231,6 +231,23 @@ cudaError_t launch_robust_star(int32_t n, const double *A, const int32_t *piv, c
 double w1_graph_host(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *eid,
                      const double *x, const double *y);
 
+// w1.cu: the same distances on the device, one warp per row; status bits 1 = excess left that
+// reaches no deficit, 2 = an iteration bound, 4 = a broken invariant
+// (mode 2: row state and graph in shared memory, 1: row state only, 0: both in the slab)
+size_t w1_slot_bytes(int32_t n, int64_t m);
+size_t w1_graph_bytes(int32_t n, int64_t m);
+cudaError_t launch_w1(int32_t n, int64_t m, const int32_t *rp, const int32_t *col,
+                      const int32_t *eid, const double *x, const double *y, int32_t count,
+                      double *out, unsigned char *slab, int mode, int grid, uint32_t *status,
+                      cudaStream_t stream);
+// perturb.cu: ranking under the tie band (rank [n]) and the first k nodes in rank order
+cudaError_t launch_rank(int32_t n, const double *b, double tie_rel, int32_t k, int32_t *rank,
+                        int32_t *topk, cudaStream_t stream);
+// robust.cu: maximisers of two discrepancies and the sampled envelopes of a robust search
+cudaError_t launch_robust_summary(int32_t n, int32_t count, const double *rows, const double *b0,
+                                  const double *d1, const double *d2, int32_t *arg, double *lo,
+                                  double *hi, cudaStream_t stream);
+
 // constrained.cu: feasibility xi per row, pool mass / censoring summaries, 3-clique pools
 cudaError_t launch_feasibility(int32_t n, uint32_t R, double alpha, double eta,
                                const uint32_t *counts, const uint32_t *fb_count, double *xi,

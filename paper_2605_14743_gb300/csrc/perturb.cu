@@ -569,6 +569,28 @@ size_t perturb_slab_bytes(int32_t n, int32_t c) {
   return (arena_bytes(c) + mixed_bytes(c) + 255) & ~size_t(255);
 }
 
+// Position of every node in the order (rank, id) -- rank counts of a tie-band ranking need
+// not be distinct, the band is not transitive -- and topk[pos] = v for positions below k.
+__global__ void rank_order_kernel(int32_t n, const int32_t *rank, int32_t k, int32_t *topk) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t rv = rank[v];
+    int32_t pos = 0;
+    for (int32_t u = 0; u < n; ++u) {
+      const int32_t ru = rank[u];
+      pos += (ru < rv || (ru == rv && u < v)) ? 1 : 0;
+    }
+    if (pos < k) topk[pos] = v;
+  }
+}
+
+cudaError_t launch_rank(int32_t n, const double *b, double tie_rel, int32_t k, int32_t *rank,
+                        int32_t *topk, cudaStream_t stream) {
+  const int grid = (n + 255) / 256;
+  nominal_rank_kernel<<<grid, 256, 0, stream>>>(n, b, tie_rel, 0, rank, nullptr);
+  if (topk && k > 0) rank_order_kernel<<<grid, 256, 0, stream>>>(n, rank, k, topk);
+  return cudaGetLastError();
+}
+
 uint32_t perturb_smem_bytes(int32_t n, int32_t c) {
   (void)n;
   return (uint32_t)arena_bytes(c);

@@ -214,6 +214,80 @@ cudaError_t launch_robust_star(int32_t n, const double *A, const int32_t *piv, c
   return cudaGetLastError();
 }
 
+namespace {
+
+// Order of numpy's argmax: a larger value first (NaN above every number), then a smaller index.
+__device__ __forceinline__ bool beats(double a, int32_t ia, double b, int32_t ib) {
+  const bool na = isnan(a), nb = isnan(b);
+  if (na != nb) return na;
+  if (!na && a != b) return a > b;
+  return ia < ib;
+}
+
+// arg[0] = argmax of d1, arg[1] = argmax of d2 (-1 for a NULL array or count 0).
+__global__ void __launch_bounds__(256) argmax2_kernel(int32_t count, const double *d1,
+                                                      const double *d2, int32_t *arg) {
+  __shared__ double sv[256];
+  __shared__ int32_t si[256];
+  const int t = threadIdx.x;
+  for (int w = 0; w < 2; ++w) {
+    const double *d = w ? d2 : d1;
+    if (!d) {
+      if (t == 0) arg[w] = -1;
+      continue;
+    }
+    double bv = 0.0;
+    int32_t bi = -1;
+    for (int32_t k = t; k < count; k += blockDim.x) {
+      const double x = d[k];
+      if (bi < 0 || beats(x, k, bv, bi)) {
+        bv = x;
+        bi = k;
+      }
+    }
+    sv[t] = bv;
+    si[t] = bi;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (t < s && si[t + s] >= 0 && (si[t] < 0 || beats(sv[t + s], si[t + s], sv[t], si[t]))) {
+        sv[t] = sv[t + s];
+        si[t] = si[t + s];
+      }
+      __syncthreads();
+    }
+    if (t == 0) arg[w] = si[0];
+    __syncthreads();
+  }
+}
+
+// Sampled envelopes: lo[v] / hi[v] = the smallest / largest of b0[v] and rows[k][v].
+__global__ void envelope_kernel(int32_t n, int32_t count, const double *rows, const double *b0,
+                                double *lo, double *hi) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    double a = b0[v], z = a;
+    for (int32_t k = 0; k < count; ++k) {
+      const double x = rows[(size_t)k * (size_t)n + v];
+      a = fmin(a, x);
+      z = fmax(z, x);
+    }
+    if (lo) lo[v] = a;
+    if (hi) hi[v] = z;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_robust_summary(int32_t n, int32_t count, const double *rows, const double *b0,
+                                  const double *d1, const double *d2, int32_t *arg, double *lo,
+                                  double *hi, cudaStream_t stream) {
+  if (arg) argmax2_kernel<<<1, 256, 0, stream>>>(count, d1, d2, arg);
+  if (lo || hi) {
+    const int grid = std::max(1, std::min((n + 255) / 256, 1024));
+    envelope_kernel<<<grid, 256, 0, stream>>>(n, count, rows, b0, lo, hi);
+  }
+  return cudaGetLastError();
+}
+
 // W1 on a graph metric is an uncapacitated transshipment problem on the graph itself (each
 // unit of mass moved across an edge costs 1).  It is solved exactly by successive shortest
 // paths: node potentials keep the reduced arc costs non-negative, each round runs a

@@ -16,7 +16,8 @@ import numpy as np
 from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
-               afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility, afc_w1_graph,
+               afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility,
+               afc_rank_order, afc_robust_summary, afc_w1_batch, afc_w1_batch_workspace,
                afc_robust_value, afc_robust_value_workspace,
                afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
@@ -358,16 +359,15 @@ class Query:
                           self.b, self.lu, self.piv, self.p_counters, self.p_pairs, self.p_hist,
                           self.p_max, b_out, self.ws_solve, self.ws_solve.numel(), self._stream())
 
-    def _topk(self, k):
-        """Nominal Top-k under the ranking rule of the sweep (u ahead of v when b_u - b_v >
-        tie_rel max b, or within that band and u < v)."""
-        b = self.b.cpu().numpy()
-        tau = float(self.wl.tie_rel) * float(b.max())
-        d = b[None, :] - b[:, None]                       # d[v, u] = b_u - b_v
-        ids = np.arange(self.n)
-        ahead = (d > tau) | ((np.abs(d) <= tau) & (ids[None, :] < ids[:, None]))
-        rank = ahead.sum(axis=1)
-        return [int(v) for v in np.argsort(rank, kind="stable")[:k]]
+    def topk(self, k):
+        """Top-k under the ranking rule of the sweep (u ahead of v when b_u - b_v > tie_rel max b,
+        or within that band and u < v; equal counts ordered by id), ranked on the device."""
+        torch = self.torch
+        k = min(int(k), self.n)
+        rank = torch.empty(self.n, dtype=torch.int32, device=self.b.device)
+        top = torch.empty(max(k, 1), dtype=torch.int32, device=self.b.device)
+        afc_rank_order(self.n, self.b, float(self.wl.tie_rel), k, rank, top, self._stream())
+        return [int(v) for v in top[:k].cpu().numpy()]
 
     def rank_stability(self, M=None, k=5):
         """The rank-stability check the paper recommends with the bootstrap (Sec. 8): the chain
@@ -377,11 +377,11 @@ class Query:
         self.run_counts(0, M)
         self.wl.realizations = M
         self.run_solve()
-        top_m = self._topk(k)
+        top_m = self.topk(k)
         self.run_counts(M, M, zero=False)
         self.wl.realizations = 2 * M
         self.run_solve()
-        top_2m = self._topk(k)
+        top_2m = self.topk(k)
         return {"stable": set(top_m) == set(top_2m), "top_M": top_m, "top_2M": top_2m}
 
     def robust_value(self, eps=0.05, r_min=0.05, support_only=True, sense=-1):
@@ -403,13 +403,25 @@ class Query:
         return {"V": V, "Qstar": Qs, "b_star": b, "expected_T": float(sc[0]), "b_f": float(sc[1]),
                 "iterations": it}
 
+    def w1(self, x, y, count=None):
+        """W1 distances under the base graph's hop metric between the rows of the device array
+        x ([count, n]) and y ([n]), on the device (`afc_w1_batch`); returns a device tensor."""
+        torch = self.torch
+        count = int(x.shape[0]) if count is None else int(count)
+        out = torch.empty(max(count, 1), dtype=torch.float64, device=self.b.device)
+        wsb = afc_w1_batch_workspace(self.n, self.graph.m, count)
+        ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=self.b.device)
+        afc_w1_batch(self.n, self.graph.m, self.graph.row_ptr, self.graph.col, self.graph.eid, x,
+                     y, count, out, ws, ws.numel(), self._stream())
+        return out[:count]
+
     def robust_search(self, samples=100, rel_radius=0.5, r_min=0.05, seed=None):
         """Sampled robust search of the paper's robust experiment (Sec. 9; Remark on the robust
         optimisation viewpoint in Sec. 5): `samples` multiplicative row perturbations of the
         estimated kernel (relative radius, leak r_min), the perturbed AFC b' of each, and the
-        maximisers of KL(b' || b) and of W1(b', b) on the base graph's hop metric.  Needs
-        run_solve first.  Returns a dict with b_kl, b_w1, the index and value of each maximiser,
-        and the per-sample kl and w1 arrays."""
+        maximisers of KL(b' || b) and of W1(b', b) on the base graph's hop metric, all on the
+        device.  Needs run_solve first.  Returns a dict with b_kl, b_w1, the index and value of
+        each maximiser, the per-sample kl and w1 arrays and the sampled envelopes."""
         torch = self.torch
         dev = self.counts.device
         pp = self.perturb_params(0, samples)
@@ -426,16 +438,19 @@ class Query:
         afc_perturb_sweep(self.chain(), pp, self.counts, self.c_index, self.c_list, self.c,
                           self.mu, self.b, self.lu, self.piv, cnt, pairs, hist, mx, b_out,
                           self.ws_solve, self.ws_solve.numel(), self._stream())
-        bs = b_out.cpu().numpy()
-        b0 = self.b.cpu().numpy()
-        kl = kl.cpu().numpy()
-        w1 = afc_w1_graph(self.n, self.wl.eu, self.wl.ev, bs, b0)
-        k_kl, k_w1 = int(np.argmax(kl)), int(np.argmax(w1))
+        w1 = self.w1(b_out, self.b, samples)
+        arg = torch.empty(2, dtype=torch.int32, device=dev)
+        lo = torch.empty(self.n, dtype=torch.float64, device=dev)
+        hi = torch.empty(self.n, dtype=torch.float64, device=dev)
         # sampled envelopes of each b_v: the range over the sampled admissible kernels (and the
         # nominal one), an inner approximation of inf / sup over the whole set
-        return {"b_kl": bs[k_kl], "b_w1": bs[k_w1], "k_kl": k_kl, "k_w1": k_w1,
-                "kl_max": float(kl[k_kl]), "w1_max": float(w1[k_w1]), "kl": kl, "w1": w1,
-                "b_low": np.minimum(bs.min(axis=0), b0), "b_high": np.maximum(bs.max(axis=0), b0),
+        afc_robust_summary(self.n, samples, b_out, self.b, kl, w1, arg, lo, hi, self._stream())
+        k_kl, k_w1 = (int(v) for v in arg.cpu().numpy())
+        kl_h, w1_h = kl.cpu().numpy(), w1.cpu().numpy()
+        return {"b_kl": b_out[k_kl].cpu().numpy(), "b_w1": b_out[k_w1].cpu().numpy(),
+                "k_kl": k_kl, "k_w1": k_w1, "kl_max": float(kl_h[k_kl]),
+                "w1_max": float(w1_h[k_w1]), "kl": kl_h, "w1": w1_h,
+                "b_low": lo.cpu().numpy(), "b_high": hi.cpu().numpy(),
                 "counters": cnt.cpu().numpy()}
 
     def step(self, perturb=True):

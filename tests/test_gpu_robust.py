@@ -1,6 +1,7 @@
 """The sampled robust search on the GPU (Sec. 9 robust experiment): multiplicative kernels,
 their perturbed AFC vectors and KL discrepancies from the sweep kernel, W1 on the base graph's
-hop metric from the host solver, and the two maximisers, against the oracle on the same
+hop metric (afc_w1_batch), the two maximisers and the sampled envelopes (afc_robust_summary),
+the Top-k ranking of the M vs 2M check (afc_rank_order), against the oracle on the same
 estimated kernel."""
 import numpy as np
 import pytest
@@ -29,7 +30,9 @@ def test_robust_search_maximisers(name, R):
     assert close(res["kl"], ref.kl, rel=1e-7, abs_floor=1e-14)
     _, b0, _, _ = O.afc_from_q(Q)
     w1 = np.array([O.w1_graph(wl.n, wl.eu, wl.ev, ref.b[k], b0) for k in range(40)])
-    assert np.allclose(res["w1"], w1, rtol=1e-8, atol=1e-12)
+    # W1 is 1-Lipschitz in l1 times the diameter: the inputs' own 1e-13 differences stay far
+    # below the 1e-9 bar
+    assert close(res["w1"], w1, rel=1e-9, abs_floor=1e-12)
     # the maximisers (unique here: the runner-up is clearly below)
     for key, vals in (("k_kl", ref.kl), ("k_w1", w1)):
         srt = np.sort(vals)
@@ -41,6 +44,47 @@ def test_robust_search_maximisers(name, R):
     assert close(res["b_low"], np.minimum(ref.b.min(axis=0), b0))
     assert close(res["b_high"], np.maximum(ref.b.max(axis=0), b0))
     assert np.all(res["b_low"] <= res["b_high"])
+
+
+def test_rank_order_matches_oracle():
+    rng = np.random.default_rng(4)
+    tie = 1e-3
+    # clusters inside the tie band and chains of 0.6 x band steps (a non-transitive band)
+    b = np.concatenate([rng.random(300), np.full(20, 0.5), 0.9 + 0.6 * tie * np.arange(12),
+                        0.7 + rng.random(40) * tie])
+    b = b[rng.permutation(b.shape[0])]
+    n = b.shape[0]
+    rank = torch.empty(n, dtype=torch.int32, device="cuda")
+    top = torch.empty(n, dtype=torch.int32, device="cuda")
+    afc.afc_rank_order(n, torch.from_numpy(b).cuda(), tie, n, rank, top,
+                       torch.cuda.current_stream().cuda_stream)
+    ref = O.rank(b, tie)
+    assert (rank.cpu().numpy() == ref).all()
+    assert len(np.unique(ref)) < n                      # equal counts do occur
+    assert (top.cpu().numpy() == np.argsort(ref, kind="stable")).all()
+
+
+def test_robust_summary_argmax_and_envelopes():
+    rng = np.random.default_rng(6)
+    count, n = 300, 77
+    rows = rng.random((count, n))
+    b0 = rng.random(n)
+    d1 = np.round(rng.random(count), 2)                 # ties: the first maximiser wins
+    d2 = rng.random(count)
+    d2[[40, 200]] = np.nan                              # NaN above every number, first one
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    arg = torch.empty(2, dtype=torch.int32, device="cuda")
+    lo = torch.empty(n, dtype=torch.float64, device="cuda")
+    hi = torch.empty(n, dtype=torch.float64, device="cuda")
+    afc.afc_robust_summary(n, count, dev(rows), dev(b0), dev(d1), dev(d2), arg, lo, hi,
+                           torch.cuda.current_stream().cuda_stream)
+    assert arg.cpu().numpy().tolist() == [int(np.argmax(d1)), int(np.argmax(d2))] == \
+        [int(np.argmax(d1)), 40]
+    assert (lo.cpu().numpy() == np.minimum(rows.min(axis=0), b0)).all()
+    assert (hi.cpu().numpy() == np.maximum(rows.max(axis=0), b0)).all()
+    afc.afc_robust_summary(n, count, None, dev(b0), None, dev(d2), arg, None, None,
+                           torch.cuda.current_stream().cuda_stream)
+    assert arg.cpu().numpy().tolist() == [-1, 40]
 
 
 def test_rank_stability_m_and_2m():
@@ -92,7 +136,7 @@ def test_robust_value_vs_oracle(sense, support_only):
     V, Qs, b, T, bf = O.robust_value(Q, 0.05, 0.05, wl.reward, sense=sense,
                                      support_only=bool(support_only))
     assert close(res["V"].cpu().numpy(), V, rel=1e-9)
-    assert close(res["b_star"].cpu().numpy(), b, rel=1e-8)
+    assert close(res["b_star"].cpu().numpy(), b, rel=1e-9)
     assert abs(res["expected_T"] - T) <= 1e-9 * T and abs(res["b_f"] - bf) <= 1e-9 * abs(bf)
     assert np.allclose(res["Qstar"].cpu().numpy(), Qs, rtol=0, atol=1e-9)
     assert 2 <= res["iterations"] <= 100
