@@ -137,6 +137,24 @@ def clique_bridge_edges():
     return _canon(c1 + c2 + [(0, 4), (4, 5)])
 
 
+def large_c_counts(n: int = 20000, c: int = 1251, R: int = 2048, seed: int = 2048) -> np.ndarray:
+    """Transition counts [n][n+1] of the 20,000-node workload's shape with c observed states:
+    per row 100-400 targets drawn from a popularity-skewed (Zipf 0.8) support, multinomial
+    counts over R draws with 10% of the mass on absorption (column n)."""
+    rng = np.random.default_rng(seed)
+    C = rng.choice(n, c, replace=False)
+    pop = 1.0 / np.arange(1, c + 1) ** 0.8
+    pop /= pop.sum()
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        k = int(rng.integers(100, 401))
+        cols = rng.choice(c, k, replace=False, p=pop)
+        d = rng.multinomial(R, np.append(rng.dirichlet(np.ones(k)) * 0.9, 0.1))
+        counts[i, C[cols]] = d[:-1].astype(np.uint32)
+        counts[i, n] = d[-1]
+    return counts
+
+
 def path_edges(n):
     return _canon([(i, i + 1) for i in range(n - 1)])
 

@@ -812,20 +812,10 @@ def run_perturb_large(args):
     import numpy as np
     import torch
     import paper_2605_14743_gb300 as afc
-    from afc_inputs import Workload
+    from afc_inputs import Workload, large_c_counts
     torch.cuda.set_device(0)
-    n, c, R = args.perturb_n, 1251, 2048
-    rng = np.random.default_rng(2048)
-    C = rng.choice(n, c, replace=False)
-    pop = 1.0 / np.arange(1, c + 1) ** 0.8
-    pop /= pop.sum()
-    counts = np.zeros((n, n + 1), np.uint32)
-    for i in range(n):
-        k = int(rng.integers(100, 401))
-        cols = rng.choice(c, k, replace=False, p=pop)
-        d = rng.multinomial(R, np.append(rng.dirichlet(np.ones(k)) * 0.9, 0.1))
-        counts[i, C[cols]] = d[:-1].astype(np.uint32)
-        counts[i, n] = d[-1]
+    n, R = args.perturb_n, 2048
+    counts = large_c_counts(n, 1251, R, 2048)
     eu = np.arange(n - 1, dtype=np.int32)
     wl = Workload("perturb_large", n, eu, eu + 1, 1.0, 1, 1, R, seed=1,
                   n_perturb=args.perturb_count)
@@ -835,6 +825,9 @@ def run_perturb_large(args):
     q.run_solve()
     q.run_perturb(0, 16)                          # warm-up
     torch.cuda.synchronize()
+    q.p_counters.zero_()
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    q.solve_stats = stats
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -849,7 +842,9 @@ def run_perturb_large(args):
             "metric": "perturbations/s", "value": args.perturb_count / (ms / 1e3), "ms": ms,
             "c": q.c, "lu_fp64_tflops": lu_flop * args.perturb_count / (ms / 1e3) / 1e12,
             "extrapolated_10000_s": 10000 * ms / args.perturb_count / 1e3,
-            "counters": q.p_counters.cpu().numpy().tolist()}
+            "counters": q.p_counters.cpu().numpy().tolist(),
+            "solved_by": dict(zip(("defect_correction", "factorisation"),
+                                  stats.cpu().numpy().tolist()))}
     print(json.dumps(line))
     return 0
 

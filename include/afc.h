@@ -482,6 +482,11 @@ typedef struct {
   double *kl_out;            /* [p_count] DEVICE or NULL: KL(b' || b0) = sum_v b'_v          */
                              /* log(b'_v / b0_v) per perturbation (the robust search's       */
                              /* discrepancy; pair it with b_out to pick the maximiser)        */
+  uint64_t *solve_stats;     /* [2] DEVICE or NULL, accumulated: perturbations whose reduced  */
+                             /* systems were solved by defect correction on the nominal     */
+                             /* factors, and by factoring I - Q'_CC (large c only: c x c     */
+                             /* matrices that do not fit in shared memory; small c always   */
+                             /* factors in shared memory and counts neither)                 */
 } afc_perturb_params;
 
 /* DEVICE outputs (accumulated, caller zeroes): counters [3] = {top-1 changes, top-k set

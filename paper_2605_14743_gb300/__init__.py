@@ -90,7 +90,8 @@ class Chain(ctypes.Structure):
 class PerturbParams(ctypes.Structure):
     _fields_ = [("p_begin", c_u32), ("p_count", c_u32), ("l1_radius", c_f64), ("r_min", c_f64),
                 ("seed", c_u64), ("top_k", c_i32), ("k2", c_i32), ("hist_bins", c_i32),
-                ("tie_rel", c_f64), ("model", c_i32), ("rel_radius", c_f64), ("kl_out", c_p)]
+                ("tie_rel", c_f64), ("model", c_i32), ("rel_radius", c_f64), ("kl_out", c_p),
+                ("solve_stats", c_p)]
 
 
 class HostQuery(ctypes.Structure):

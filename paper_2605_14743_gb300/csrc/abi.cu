@@ -781,7 +781,9 @@ static SolveWs ws_layout_for(int32_t n, int32_t c) {
   // nonzeros of the kernel: at most the transient columns in C plus the absorbing column
   const size_t nnz_cap = (size_t)n * ((size_t)std::min<int32_t>(c, n) + 1);
   const size_t slab = std::max<size_t>(perturb_slab_bytes(n, c) + nnz_cap * 8, 8 * (size_t)(c + 1) * 64 / (size_t)std::max(1, d.sms) + 256);
-  return solve_ws_layout(n, c, nnz_cap, perturb_slabs(d, slab), slab);
+  // the large-c sweep's column-wise pattern of Q_CC (at most c entries per column)
+  const size_t csc = perturb_on_chip(c, d.smem_optin) ? 0 : (size_t)c * (size_t)c;
+  return solve_ws_layout(n, c, nnz_cap, perturb_slabs(d, slab), slab, csc);
 }
 
 static size_t solve_ws_bytes(int32_t n, int32_t c) { return ws_layout_for(n, c).total; }

@@ -187,12 +187,13 @@ struct ChainDev {
 
 // Workspace carve-up of the solve path (byte offsets), shared by solve and perturb.
 struct SolveWs {
-  size_t off_y, off_t, off_rowscale, off_nzptr, off_nzcol, off_nzval, off_flags, off_tmp, off_slab,
-      total;
+  size_t off_y, off_t, off_rowscale, off_nzptr, off_nzcol, off_nzval, off_flags, off_tmp, off_csc,
+      off_slab, total;
   size_t nnz_cap;
+  size_t csc_cap;   // entries of the column-wise pattern of Q_CC the large-c sweep builds (0: none)
 };
 SolveWs solve_ws_layout(int32_t n, int32_t c, size_t nnz_cap, uint32_t perturb_slabs,
-                        size_t slab_bytes);
+                        size_t slab_bytes, size_t csc_cap);
 
 cudaError_t launch_observed_states(int32_t n, const uint32_t *counts, int32_t *c_index,
                                    int32_t *c_list, int32_t *c_dev, cudaStream_t stream);
@@ -209,6 +210,8 @@ cudaError_t launch_certificates(const ChainDev &C, const double *mu0, const doub
                                 const int32_t *pu, const int32_t *pv, double *gap, double *sharp,
                                 unsigned char *ws, const SolveWs &L, cudaStream_t stream);
 size_t perturb_slab_bytes(int32_t n, int32_t c);
+// true when the sweep keeps a perturbation's c x c matrix in shared memory (else: device slabs)
+bool perturb_on_chip(int32_t c, int smem_optin);
 // bootstrap.cu: realization-level bootstrap replicates of b and their percentile intervals
 size_t bootstrap_slab_bytes(int32_t n, int32_t c, uint32_t R);
 cudaError_t launch_bootstrap(const ChainDev &C, const int32_t *rec, uint32_t R, uint32_t B,

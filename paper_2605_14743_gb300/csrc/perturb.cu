@@ -142,6 +142,145 @@ __device__ bool refine(const double *A, const float *Af, const int32_t *piv, int
   return false;
 }
 
+// Column-wise pattern of Q_CC for the large-c sweep: column j of the C rows' entries as
+// ptr[j] .. ptr[j+1]-1, each giving the entry's index in the sparse rows (e) and its row's
+// position in C (a), rows ascending.  Built once per launch: every perturbed kernel keeps the
+// nominal support.
+struct CscPattern {
+  const int32_t *ptr, *e, *a;
+};
+
+// Position of column j in the sparse-row entries [lo, hi) (columns ascending), or -1.
+__device__ __forceinline__ int32_t find_col(const int32_t *nzcol, int32_t lo, int32_t hi,
+                                            int32_t j) {
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t v = nzcol[mid];
+    if (v == j) return mid;
+    if (v < j) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+// One warp per column; fill = 0 counts its entries into cnt[j], fill = 1 writes them at ptr[j].
+__global__ void csc_kernel(ChainDev C, const int32_t *nzptr, const int32_t *nzcol, int fill,
+                           int32_t *cnt, const int32_t *ptr, int32_t *ce, int32_t *ca) {
+  const int32_t c = C.c;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t j = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < c;
+       j += (int32_t)nwarps) {
+    int32_t at = fill ? ptr[j] : 0;
+    for (int32_t a0 = 0; a0 < c; a0 += 32) {
+      const int32_t a = a0 + (int32_t)lane;
+      int32_t e = -1;
+      if (a < c) {
+        const int32_t i = C.c_list[a];
+        e = find_col(nzcol, nzptr[i], nzptr[i + 1] - 1, j);   // the last entry is absorption
+      }
+      const uint32_t hit = __ballot_sync(0xFFFFFFFFu, e >= 0);
+      if (fill && e >= 0) {
+        const int32_t pos = at + __popc(hit & ((1u << lane) - 1u));
+        ce[pos] = e;
+        ca[pos] = a;
+      }
+      at += __popc(hit);
+    }
+    if (!fill && lane == 0) cnt[j] = at;
+  }
+}
+
+// ptr[j] = cnt[0] + ... + cnt[j-1] for j <= c (one CTA of whole warps).
+__global__ void csc_scan_kernel(int32_t c, const int32_t *cnt, int32_t *ptr) {
+  __shared__ int32_t wt[32];
+  __shared__ int32_t base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  for (int32_t s0 = 0; s0 < c; s0 += blockDim.x) {
+    const int32_t j = s0 + threadIdx.x;
+    const int32_t x = j < c ? cnt[j] : 0;
+    int32_t inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    int32_t off = base;
+    for (uint32_t w = 0; w < warp; ++w) off += wt[w];
+    if (j < c) ptr[j] = off + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (uint32_t w = 0; w < blockDim.x / 32u; ++w) base += wt[w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ptr[c] = base;
+}
+
+// Defect correction on the nominal factors (large c): solves op(I - Q'_CC) x = b (op = the
+// transpose when TRANS; b NULL = all ones) by x <- x + op(M)^-1 (b - op(I - Q'_CC) x), with
+// M = I - Q_CC the nominal matrix the solve factored once.  The residual is sparse (the
+// perturbed C rows, qp) and summed in a fixed order; the correction is two triangular solves
+// with M's factors, which every CTA of the launch reads (they stay in L2).  The error shrinks
+// by the spectral radius of M^-1 (Q' - Q)_CC each round -- about 0.004 for l1 moves of 0.05 on
+// a chain whose rows absorb 10%, two to three digits a round.  Starts from x = op(M)^-1 b;
+// returns false (the caller then factors I - Q'_CC) when an update shrinks by less than 5x
+// from the third round on, or 40 rounds do not bring it below 1e-15 of x.
+template <bool TRANS>
+__device__ bool defect_solve(const ChainDev &Cd, const double *lu0, const int32_t *piv0,
+                             const int32_t *nzptr, const int32_t *nzcol, const double *qp,
+                             const CscPattern &P, const double *b, double *x, double *r,
+                             double *red) {
+  const int32_t c = Cd.c;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int32_t k = threadIdx.x; k < c; k += blockDim.x) x[k] = b ? b[k] : 1.0;
+  __syncthreads();
+  if (TRANS) lu_solve_transposed_blocked_t(lu0, c, c, piv0, x);
+  else lu_solve_blocked_t(lu0, c, c, piv0, x);
+  double prev = 0.0;
+  for (int it = 0; it < 40; ++it) {
+    if (TRANS) {
+      // r_j = b_j - x_j + sum_a Q'_aj x_a, gathered down column j
+      for (int32_t j = (int32_t)warp; j < c; j += (int32_t)nw) {
+        double acc = 0.0;
+        for (int32_t k = P.ptr[j] + (int32_t)lane; k < P.ptr[j + 1]; k += 32)
+          acc = fma(qp[P.e[k]], x[P.a[k]], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) r[j] = (b ? b[j] : 1.0) - x[j] + acc;
+      }
+    } else {
+      // r_a = b_a - x_a + sum_j Q'_aj x_j along row a
+      for (int32_t a = (int32_t)warp; a < c; a += (int32_t)nw) {
+        const int32_t i = Cd.c_list[a];
+        double acc = 0.0;
+        for (int32_t e = nzptr[i] + (int32_t)lane; e < nzptr[i + 1]; e += 32) {
+          const int32_t pj = nzcol[e];
+          if (pj < c) acc = fma(qp[e], x[pj], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) r[a] = (b ? b[a] : 1.0) - x[a] + acc;
+      }
+    }
+    __syncthreads();
+    if (TRANS) lu_solve_transposed_blocked_t(lu0, c, c, piv0, r);
+    else lu_solve_blocked_t(lu0, c, c, piv0, r);
+    double dm = 0.0, xm = 0.0;
+    for (int32_t k = threadIdx.x; k < c; k += blockDim.x) {
+      x[k] += r[k];
+      dm = fmax(dm, fabs(r[k]));
+      xm = fmax(xm, fabs(x[k]));
+    }
+    dm = block_max(dm, red);
+    xm = block_max(xm, red);
+    if (dm <= 1e-15 * xm) return true;
+    if (it >= 2 && !(dm < 0.2 * prev)) return false;
+    prev = dm;
+  }
+  return false;
+}
+
 // Entries per lane a perturbed row keeps in registers (rows of up to 32 * kRowRegs entries).
 constexpr int kRowRegs = 4;
 
@@ -155,7 +294,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
                const double *nzval, const int32_t *byrank0, uint64_t *counters,
                uint64_t *pair_flips, uint64_t *shift_hist, double *maxima, double *b_out,
                unsigned char *slabs, size_t slab_bytes, int use_smem, int use_priv,
-               uint32_t *status) {
+               CscPattern csc, unsigned long long *solve_stats, uint32_t *status) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sval[33];
   __shared__ int32_t sidx[32];
@@ -195,11 +334,17 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
   const double T0 = block_sum(part, red);
   double loc_db = 0.0, loc_lin = 0.0, loc_t = 0.0;
 
+  // large c: defect correction on the nominal factors; I - Q'_CC is assembled only where it
+  // is factored (small c, or a perturbation the correction does not settle)
+  const bool defect = !use_smem && csc.ptr != nullptr;
+  const bool dense = !defect;
+  uint32_t loc_defect = 0, loc_factored = 0;
   const uint32_t p_end = pp.p_begin + pp.p_count;
   for (uint32_t p = pp.p_begin + blockIdx.x; p < p_end; p += gridDim.x) {
-    // (1) A' = I, y' = 0, x = 0
-    for (size_t k = threadIdx.x; k < (size_t)c * c; k += blockDim.x)
-      ar.A[k] = (k / c == k % c) ? 1.0 : 0.0;
+    // (1) A' = I (where factored), y' = 0, x = 0
+    if (dense)
+      for (size_t k = threadIdx.x; k < (size_t)c * c; k += blockDim.x)
+        ar.A[k] = (k / c == k % c) ? 1.0 : 0.0;
     for (int32_t k = threadIdx.x; k < c; k += blockDim.x) { ar.y[k] = 0.0; ar.x[k] = 0.0; }
     if (use_priv)
       for (int32_t k = threadIdx.x; k < 2 * (int32_t)nw * c; k += blockDim.x) wy[k] = 0.0;
@@ -319,7 +464,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
           if (pj < c) {
             const double v = qv[t];
             qp[e] = v;
-            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= v;
+            if (pi >= 0) { if (dense) ar.A[(size_t)pi * c + pj] -= v; }
             else add_y(pj, si * v);
             add_x(pj, mi * (v - q0[t]));
           } else {
@@ -348,7 +493,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
           const int32_t pj = nzcol[e];
           if (pj < c) {
             const double q = qp[e];
-            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
+            if (pi >= 0) { if (dense) ar.A[(size_t)pi * c + pj] -= q; }
             else add_y(pj, si * q);
             add_x(pj, mi * (q - nzval[e]));
           } else {
@@ -394,7 +539,7 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
           if (pj < c) {
             if (ra < pp.r_min) q *= f;
             qp[e] = q;
-            if (pi >= 0) ar.A[(size_t)pi * c + pj] -= q;
+            if (pi >= 0) { if (dense) ar.A[(size_t)pi * c + pj] -= q; }
             else add_y(pj, si * q);
             add_x(pj, mi * (q - nzval[e]));
           } else {
@@ -426,7 +571,32 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
         __syncthreads();
         lu_solve(ar.A, c, c, ar.piv, ar.t, ls);
       }
+    } else if (c > 0 && defect &&
+               [&] {
+                 for (int32_t k = threadIdx.x; k < c; k += blockDim.x) by[k] = ar.y[k];
+                 __syncthreads();
+                 return defect_solve<true>(C, lu0, piv0, nzptr, nzcol, qp, csc, by, ar.y, rv, red) &&
+                        defect_solve<false>(C, lu0, piv0, nzptr, nzcol, qp, csc, nullptr, ar.t, rv,
+                                            red);
+               }()) {
+      ++loc_defect;
     } else if (c > 0) {
+      ++loc_factored;
+      if (defect) {
+        // the correction did not settle: assemble I - Q'_CC from the perturbed C rows
+        for (size_t k = threadIdx.x; k < (size_t)c * c; k += blockDim.x)
+          ar.A[k] = (k / c == k % c) ? 1.0 : 0.0;
+        for (int32_t k = threadIdx.x; k < c; k += blockDim.x) ar.y[k] = by[k];
+        __syncthreads();
+        for (int32_t a = (int32_t)warp; a < c; a += (int32_t)nw) {
+          const int32_t i = C.c_list[a];
+          for (int32_t e = nzptr[i] + (int32_t)lane; e < nzptr[i + 1]; e += 32) {
+            const int32_t pj = nzcol[e];
+            if (pj < c) ar.A[(size_t)a * c + pj] -= qp[e];
+          }
+        }
+        __syncthreads();
+      }
       // A in the device slab (large c): blocked LU of an FP32 copy (GB300's FP32 rate is many
       // times its FP64 rate), then FP64 iterative refinement against the FP64 matrix; if the
       // refinement stalls, the FP64 blocked LU of A itself
@@ -548,6 +718,10 @@ perturb_kernel(ChainDev C, afc_perturb_params pp, const double *mu0, const doubl
   loc_db = block_max(loc_db, red);
   loc_lin = block_max(loc_lin, red);
   loc_t = block_max(loc_t, red);
+  if (threadIdx.x == 0 && solve_stats && !use_smem) {
+    if (loc_defect) atomicAdd(&solve_stats[0], (unsigned long long)loc_defect);
+    if (loc_factored) atomicAdd(&solve_stats[1], (unsigned long long)loc_factored);
+  }
   if (threadIdx.x == 0) {
     atomic_max_pos(&maxima[0], loc_db);
     atomic_max_pos(&maxima[1], loc_lin);
@@ -591,6 +765,10 @@ cudaError_t launch_rank(int32_t n, const double *b, double tie_rel, int32_t k, i
   return cudaGetLastError();
 }
 
+bool perturb_on_chip(int32_t c, int smem_optin) {
+  return (int)arena_bytes(c) + 16 * 1024 <= smem_optin;
+}
+
 uint32_t perturb_smem_bytes(int32_t n, int32_t c) {
   (void)n;
   return (uint32_t)arena_bytes(c);
@@ -616,7 +794,7 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   int max_optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const int use_smem = (int)smem + 16 * 1024 <= max_optin ? 1 : 0;
+  const int use_smem = perturb_on_chip(c, max_optin) ? 1 : 0;
   const uint32_t priv = 2u * (kPerturbThreads / 32) * (uint32_t)(c > 0 ? c : 1) * 8u;
   const int use_priv = (use_smem && (int)(smem + priv) + 16 * 1024 <= max_optin) ? 1 : 0;
   // the slab path takes the blocked LU's tiles as dynamic shared memory
@@ -631,12 +809,25 @@ cudaError_t launch_perturb(const ChainDev &C, const afc_perturb_params &pp, cons
   if (fit > (size_t)pp.p_count) fit = (size_t)pp.p_count;
   const int grid = (int)fit;
   if (grid <= 0) return cudaErrorMemoryAllocation;
+  // large c: the column-wise pattern of Q_CC for the defect correction (none: always factor)
+  CscPattern csc{nullptr, nullptr, nullptr};
+  if (!use_smem && c > 0 && L.csc_cap >= (size_t)c * (size_t)c) {
+    int32_t *ptr = reinterpret_cast<int32_t *>(ws + L.off_csc);
+    int32_t *ce = ptr + (((size_t)c + 1 + 63) & ~size_t(63));
+    int32_t *ca = ce + L.csc_cap;
+    const int cgrid = (int)(((size_t)c * 32 + 255) / 256);
+    csc_kernel<<<cgrid, 256, 0, stream>>>(C, nzptr, nzcol, 0, ptr, nullptr, nullptr, nullptr);
+    csc_scan_kernel<<<1, 1024, 0, stream>>>(c, ptr, ptr);
+    csc_kernel<<<cgrid, 256, 0, stream>>>(C, nzptr, nzcol, 1, nullptr, ptr, ce, ca);
+    csc = CscPattern{ptr, ce, ca};
+  }
   // set on every launch: the attribute is the kernel's limit, and an earlier launch may have
   // left it below what this one needs
   cudaFuncSetAttribute(perturb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
   perturb_kernel<<<grid, kPerturbThreads, dyn, stream>>>(
       C, pp, mu0, b0, lu0, piv0, nzptr, nzcol, nzval, byrank0, counters, pair_flips, shift_hist,
-      maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, use_priv, status_dev);
+      maxima, b_out, ws + L.off_slab, slab_bytes, use_smem, use_priv, csc,
+      reinterpret_cast<unsigned long long *>(pp.solve_stats), status_dev);
   return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ cudaError_t launch_observed_states(int32_t n, const uint32_t *counts, int32_t *c
 
 // ---- workspace ----------------------------------------------------------------------------
 SolveWs solve_ws_layout(int32_t n, int32_t c, size_t nnz_cap, uint32_t perturb_slabs,
-                        size_t slab_bytes) {
+                        size_t slab_bytes, size_t csc_cap) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   SolveWs L{};
   size_t o = 0;
@@ -83,6 +83,8 @@ SolveWs solve_ws_layout(int32_t n, int32_t c, size_t nnz_cap, uint32_t perturb_s
   L.off_nzval = o;    o = al(o + 8 * nnz_cap);
   L.off_flags = o;    o = al(o + 4 * (size_t)n + 64);
   L.off_tmp = o;      o = al(o + 8 * (4 * (size_t)n + 4 * cc + 64));
+  L.off_csc = o;      o = al(o + (csc_cap ? 4 * ((cc + 1 + 63) & ~size_t(63)) + 8 * csc_cap : 0));
+  L.csc_cap = csc_cap;
   L.off_slab = o;     o = al(o + (size_t)perturb_slabs * slab_bytes);
   L.total = o;
   L.nnz_cap = nnz_cap;

@@ -128,6 +128,7 @@ class Query:
         self.wl = wl
         self.n = n = int(wl.n)
         self.device = device
+        self.solve_stats = None
         self.graph = DeviceGraph.from_edges(n, wl.eu, wl.ev, device)
         m = self.graph.m
         self.thresh = None
@@ -344,6 +345,8 @@ class Query:
         pp.seed = int(self.wl.perturb_seed)
         pp.top_k, pp.k2, pp.hist_bins = top_k, k2, hist
         pp.tie_rel = float(self.wl.tie_rel)
+        # optional device int64 [2]: perturbations solved by defect correction / factorisation
+        pp.solve_stats = None if self.solve_stats is None else self.solve_stats.data_ptr()
         return pp
 
     def run_perturb(self, p_begin=0, p_count=None, b_out=None, zero=True):

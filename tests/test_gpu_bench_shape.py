@@ -9,6 +9,9 @@
   register path up to its 128-entry limit, for both row models.
 * The batched mix: the first four realizations of all 64 graphs in one batched FP32 + recheck
   call and four further realizations of each graph drawn at random, counts against the oracle.
+* The large-c sweep: the synthetic chain of the 20,000-node workload's shape (c = 1,251 observed
+  states, rows of 100-400 entries) on 4,000 nodes, solved by defect correction on the nominal
+  factors as in the timed run; perturbations on both sides of the first wave of CTAs.
 """
 import os
 from concurrent.futures import ThreadPoolExecutor
@@ -17,7 +20,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from afc_inputs import mixed_batch, workload
+from afc_inputs import large_c_counts, mixed_batch, workload
 from tests._util import close, max_rel, oracle_counts, oracle_graph
 
 pytestmark = pytest.mark.gpu
@@ -165,3 +168,24 @@ def test_mix_subsample_counts_vs_oracle():
     for g, w in enumerate(batch):
         assert (first[g] == ref_first[g]).all(), f"batched counts differ on {w.name}"
         assert (single[g] == ref_single[g]).all(), f"single-call counts differ on {w.name}"
+
+
+def test_large_c_sweep_sampled():
+    n, R, alpha = 4000, 2048, 0.15
+    counts = large_c_counts(n, 1251, R, 2048)
+    ch = Chain(counts, R, alpha)
+    assert ch.c == 1251
+    Q, r = O.assemble_q(counts, R, alpha)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # a whole first wave (two CTAs per SM) and a few beyond; the oracle checks a sample
+    P = 2 * sms + 4
+    cnt, pairs, hst, mx, bo = ch.sweep(0, P, 0.05, 0.05, 7, stats=stats)
+    assert stats.cpu().numpy().tolist() == [P, 0]
+    for p in (0, 2 * sms, P - 1):   # about 15 s of oracle each
+        ref = O.perturb_sweep(Q, r, None, p, 1, 0.05, 0.05, 7, keep=True)
+        assert close(bo[p], ref.b[0]), p
+        one = ch.sweep(p, 1, 0.05, 0.05, 7)
+        assert one[0].tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+        assert (one[1] == ref.pair_flips).all() and (one[2] == ref.shift_hist).all()
+        assert max_rel(one[3], [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7

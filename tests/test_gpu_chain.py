@@ -52,13 +52,14 @@ class Chain:
         torch.cuda.synchronize()
 
     def sweep(self, p_begin, p_count, radius, r_min, seed, keep=True, top_k=5, k2=10, hist=16,
-              tie_rel=1e-9, model=0, kl=None):
+              tie_rel=1e-9, model=0, kl=None, stats=None):
         pp = afc.PerturbParams()
         pp.p_begin, pp.p_count, pp.l1_radius, pp.r_min, pp.seed = p_begin, p_count, radius, r_min, seed
         pp.top_k, pp.k2, pp.hist_bins, pp.tie_rel = top_k, k2, hist, tie_rel
         if model == 1:   # radius is the relative radius of the multiplicative model
             pp.model, pp.rel_radius, pp.l1_radius = 1, radius, 0.0
         pp.kl_out = None if kl is None else kl.data_ptr()
+        pp.solve_stats = None if stats is None else stats.data_ptr()
         cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
         pairs = torch.zeros(k2 * k2, dtype=torch.int64, device="cuda")
         hst = torch.zeros(hist, dtype=torch.int64, device="cuda")
@@ -282,10 +283,43 @@ def test_perturb_large_support_global_slab(parity):
     ch = Chain(counts, 300, 0.15)
     assert ch.c > 170 and ch.c % 2 == parity
     Q, r = O.assemble_q(counts, 300, 0.15)
-    cnt, pairs, hst, mx, bo = ch.sweep(5, 3, 0.05, 0.05, 11)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    cnt, pairs, hst, mx, bo = ch.sweep(5, 3, 0.05, 0.05, 11, stats=stats)
     ref = O.perturb_sweep(Q, r, None, 5, 3, 0.05, 0.05, 11, keep=True)
     assert close(bo, ref.b)
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+    assert (pairs == ref.pair_flips).all() and (hst == ref.shift_hist).all()
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    # solved by defect correction on the nominal factors, none factored
+    assert stats.cpu().numpy().tolist() == [3, 0]
+
+
+def test_large_c_factorisation_fallback():
+    """Perturbations too large for the defect correction on the nominal factors (multiplicative
+    moves of 90% on rows that keep 97% of their mass in transient states): the sweep factors
+    I - Q'_CC instead, with the same results."""
+    n, R = 400, 3000
+    rng = np.random.default_rng(12)
+    C = rng.choice(n, size=240, replace=False)
+    counts = np.zeros((n, n + 1), np.uint32)
+    for i in range(n):
+        k = int(rng.integers(2, 8))
+        p = np.append(rng.dirichlet(np.ones(k)) * 0.97, 0.03)
+        d = rng.multinomial(R, p)
+        counts[i, rng.choice(C, size=k, replace=False)] = d[:-1].astype(np.uint32)
+        counts[i, n] = d[-1]
+    ch = Chain(counts, R, 0.0)
+    assert ch.c > 170
+    Q, r = O.assemble_q(counts, R, 0.0)
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    kl = torch.empty(4, dtype=torch.float64, device="cuda")
+    cnt, pairs, hst, mx, bo = ch.sweep(0, 4, 0.9, 0.01, 5, model=1, kl=kl, stats=stats)
+    ref = O.perturb_sweep(Q, r, None, 0, 4, 0.9, 0.01, 5, keep=True, model=1)
+    assert close(bo, ref.b)
+    assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    st = stats.cpu().numpy().tolist()
+    assert sum(st) == 4 and st[1] >= 1
 
 
 # ------------------------------------------------ multiplicative model (robust search) ----
