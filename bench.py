@@ -46,7 +46,7 @@ def _env_rank():
 # DRAM bytes of one counting launch of the benchmark, from ncu (profiles/counts_traffic.txt); valid
 # only for the kernel sources it was taken on, so the file records their hash.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "counts_traffic.txt")
-KERNEL_SOURCES = ["mc_common.cuh", "mc_steps.cuh", "mc_kernel.cu", "afc_internal.h",
+KERNEL_SOURCES = ["mc_common.cuh", "mc_steps.cuh", "mc_kernel.cu", "mc_types.h",
                   "afc_device.cuh"]
 
 

@@ -12,7 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "afc_device.cuh"
-#include "afc_internal.h"
+#include "mc_types.h"
 
 namespace afc {
 

@@ -15,6 +15,7 @@
 //            cleared, and a second brandes + select pair redoes exactly the flagged groups in
 //            FP64 (A7)
 // All launches are stream ordered; nothing waits on the host.
+#include "afc_internal.h"
 #include "mc_steps.cuh"
 
 namespace afc {

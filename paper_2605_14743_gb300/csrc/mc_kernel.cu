@@ -16,6 +16,7 @@
 // Per-source results do not depend on which warp or CTA runs the source, and the exact
 // betweenness sum does not depend on the order in which sources finish, so B and every count
 // are the same bit for bit for any launch shape.
+#include "afc_internal.h"
 #include "mc_steps.cuh"
 
 namespace afc {

@@ -70,13 +70,12 @@ def _sweep_check(counts, R, alpha, P, seed, model):
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
     assert (pairs == ref.pair_flips).all()
     assert (hst == ref.shift_hist).all()
-    # largest |b' - b0| and largest ||N'||_inf at 1e-9; the first-order error is a difference
-    # of nearly equal vectors (b' against b0 + the linear term), so its relative rounding is
-    # amplified by the cancellation and it is compared at 1e-7
-    assert max_rel(mx[[0, 2]], [ref.max_db, ref.max_rowsum_N]) < 1e-9
-    assert max_rel(mx[1:2], [ref.max_lin_err]) < 1e-7
+    # largest |b' - b0|, the largest first-order error and largest ||N'||_inf at 1e-9: the
+    # first-order error is a difference of nearly equal vectors (b' against b0 + the linear
+    # term), which amplifies FP64 rounding by at most about 1e4 here (3e-11 measured)
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9
     if model == 1:
-        assert close(kl.cpu().numpy(), ref.kl, rel=1e-7, abs_floor=1e-14)
+        assert close(kl.cpu().numpy(), ref.kl, rel=1e-9, abs_floor=1e-14)
     return ch
 
 
@@ -188,4 +187,4 @@ def test_large_c_sweep_sampled():
         one = ch.sweep(p, 1, 0.05, 0.05, 7)
         assert one[0].tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
         assert (one[1] == ref.pair_flips).all() and (one[2] == ref.shift_hist).all()
-        assert max_rel(one[3], [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+        assert max_rel(one[3], [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9

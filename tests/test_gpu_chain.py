@@ -233,7 +233,7 @@ def test_perturb_sweep_vs_oracle(er_counts):
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
     assert (pairs == ref.pair_flips).all()
     assert (hst == ref.shift_hist).all()
-    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9
     assert mx[2] <= 1 / 0.05 + 1e-9
 
 
@@ -289,7 +289,7 @@ def test_perturb_large_support_global_slab(parity):
     assert close(bo, ref.b)
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
     assert (pairs == ref.pair_flips).all() and (hst == ref.shift_hist).all()
-    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9
     # solved by defect correction on the nominal factors, none factored
     assert stats.cpu().numpy().tolist() == [3, 0]
 
@@ -317,7 +317,7 @@ def test_large_c_factorisation_fallback():
     ref = O.perturb_sweep(Q, r, None, 0, 4, 0.9, 0.01, 5, keep=True, model=1)
     assert close(bo, ref.b)
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
-    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9
     st = stats.cpu().numpy().tolist()
     assert sum(st) == 4 and st[1] >= 1
 
@@ -331,10 +331,10 @@ def _mult_check(counts, R, alpha, p_begin, P, seed, rel=0.5):
     cnt, pairs, hst, mx, bo = ch.sweep(p_begin, P, rel, 0.05, seed, model=1, kl=kl)
     ref = O.perturb_sweep(Q, r, None, p_begin, P, rel, 0.05, seed, keep=True, model=1)
     assert close(bo, ref.b)
-    assert close(kl.cpu().numpy(), ref.kl, rel=1e-7, abs_floor=1e-14)
+    assert close(kl.cpu().numpy(), ref.kl, rel=1e-9, abs_floor=1e-14)
     assert cnt.tolist() == [ref.top1_changes, ref.topk_set_changes, ref.topk_order_changes]
     assert (pairs == ref.pair_flips).all() and (hst == ref.shift_hist).all()
-    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-7
+    assert max_rel(mx, [ref.max_db, ref.max_lin_err, ref.max_rowsum_N]) < 1e-9
     return ch
 
 
