@@ -580,6 +580,61 @@ def robust_inner(Q0, eps, r_min, v, v_bot, support_only=True):
     return T, Qs
 
 
+def robust_envelope(Q0, eps, r_min, v, sense=1, support_only=True, s=None, kernel=False):
+    """Envelope of the AFC coordinate b_v over the row-wise uncertainty set (Remark on the
+    robust optimisation viewpoint in Sec. 5: inf / sup over P in U of b_v(s; P)), with U the set
+    of robust_inner: every row q_i in the box [(Q0_ij - eps)_+, min(Q0_ij + eps, 1)] (on the
+    support {j : Q0_ij > 0} when support_only, else on every j) with sum_j q_ij <= 1 - r_min.
+
+    Solved as one LP over occupancy measures: a kernel in U has visits mu = s (I - Q)^-1 and
+    flows x_ij = mu_i q_ij with mu_j = s_j + sum_i x_ij, mu_i lo_ij <= x_ij <= mu_i hi_ij and
+    sum_j x_ij <= (1 - r_min) mu_i; conversely such (mu, x) give q_ij = x_ij / mu_i in U (rows
+    with mu_i = 0 are never visited).  b_v = mu_v / sum mu is linear-fractional, so the
+    Charnes-Cooper substitution y = mu / sum mu, z = x / sum mu, t = 1 / sum mu makes it linear:
+    optimise y_v subject to y_j = t s_j + sum_i z_ij, sum y = 1, y_i lo_ij <= z_ij <= y_i hi_ij,
+    sum_j z_ij <= (1 - r_min) y_i, z, t >= 0.  scipy's HiGHS at 1e-10 feasibility tolerances.
+    sense +1: the supremum, -1: the infimum.  kernel=True also returns the optimal Q."""
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    Q0 = np.asarray(Q0, np.float64)
+    n = Q0.shape[0]
+    s_ = np.full(n, 1.0 / n) if s is None else np.asarray(s, np.float64)
+    rows, cols = np.nonzero(Q0 > 0) if support_only else np.nonzero(np.ones((n, n), bool))
+    q = Q0[rows, cols]
+    lo = np.maximum(q - eps, 0.0)
+    hi = np.minimum(q + eps, 1.0)
+    nz = rows.shape[0]
+    # variables: y [n] | z [nz] | t
+    ny, iz, it = n, n, n + nz
+    nv = n + nz + 1
+    k = np.arange(nz)
+    # equalities: y_j - sum_i z_ij - t s_j = 0 (n rows), sum_j y_j = 1 (one row)
+    er = np.concatenate([np.arange(n), cols, np.arange(n), np.full(n, n)])
+    ec = np.concatenate([np.arange(n), iz + k, np.full(n, it), np.arange(n)])
+    ev = np.concatenate([np.ones(n), -np.ones(nz), -s_, np.ones(n)])
+    A_eq = coo_matrix((ev, (er, ec)), shape=(n + 1, nv)).tocsr()
+    b_eq = np.concatenate([np.zeros(n), [1.0]])
+    # inequalities: lo_ij y_i - z_ij <= 0, z_ij - hi_ij y_i <= 0, sum_j z_ij - (1 - r_min) y_i <= 0
+    ur = np.concatenate([k, k, nz + k, nz + k, 2 * nz + rows, 2 * nz + np.arange(n)])
+    uc = np.concatenate([rows, iz + k, iz + k, rows, iz + k, np.arange(n)])
+    uv = np.concatenate([lo, -np.ones(nz), np.ones(nz), -hi, np.ones(nz),
+                         -np.full(n, 1.0 - r_min)])
+    A_ub = coo_matrix((uv, (ur, uc)), shape=(2 * nz + n, nv)).tocsr()
+    c = np.zeros(nv)
+    c[v] = -1.0 if sense > 0 else 1.0
+    res = linprog(c, A_ub=A_ub, b_ub=np.zeros(2 * nz + n), A_eq=A_eq, b_eq=b_eq,
+                  bounds=(0, None), method="highs", options=_HIGHS_TIGHT)
+    if not res.success:
+        raise RuntimeError("robust_envelope: " + res.message)
+    val = float(res.x[v])
+    if not kernel:
+        return val
+    y, z, t = res.x[:n], res.x[iz:iz + nz], res.x[it]
+    Q = np.zeros((n, n))
+    Q[rows, cols] = np.where(y[rows] > 0, z / np.where(y[rows] > 0, y[rows], 1.0), lo)
+    return val, Q
+
+
 def robust_value(Q0, eps, r_min, f, sense=-1, support_only=True, s=None, max_iter=100):
     """Robust expected accumulated reward under the rectangular set U (Sec. 8: a scenario
     kernel P* chosen by a robust Bellman operator): V = f + T(V) with v_bot = 0, T the inner

@@ -109,3 +109,82 @@ def test_multiplicative_sweep_kl():
     assert (st.kl >= 0).all() and st.kl.max() > 0      # Gibbs' inequality, strict somewhere
     k = int(st.kl.argmax())
     assert st.kl[k] == pytest.approx(float(np.sum(st.b[k] * np.log(st.b[k] / b0))), rel=1e-12)
+
+
+# ---- envelopes of b_v over the row-wise set (Remark on the robust optimisation viewpoint) ----
+
+def _afc_np(Q, s):
+    mu = np.linalg.solve((np.eye(Q.shape[0]) - Q).T, s)
+    return mu / mu.sum()
+
+
+def _row_vertices(lo, hi, budget):
+    """Vertices of {q : lo <= q <= hi, sum q <= budget}: box corners within the budget and the
+    points where a box edge meets the budget plane."""
+    import itertools
+    k = lo.shape[0]
+    out = []
+    for corner in itertools.product(*[(0, 1)] * k):
+        q = np.where(np.array(corner) == 1, hi, lo)
+        if q.sum() <= budget + 1e-15:
+            out.append(q)
+        for j in range(k):   # the edge along coordinate j through this corner
+            rest = q.sum() - q[j]
+            x = budget - rest
+            if lo[j] < x < hi[j]:
+                e = q.copy()
+                e[j] = x
+                out.append(e)
+    return np.unique(np.round(np.array(out), 15), axis=0)
+
+
+def _tiny_chain(seed):
+    rng = np.random.default_rng(seed)
+    n = 3
+    Q0 = rng.random((n, n))
+    Q0 *= (0.55 + 0.4 * rng.random((n, 1))) / Q0.sum(axis=1, keepdims=True)
+    return Q0, rng.dirichlet(np.ones(n))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_envelope_brute_force_over_vertex_kernels(seed):
+    """b_v is a ratio of affine functions of any one row (the others fixed), so its extrema over
+    a product of polytopes sit at products of vertices: enumerate them all."""
+    import itertools
+    Q0, s = _tiny_chain(seed)
+    n, eps, r_min = 3, 0.12, 0.05
+    verts = [_row_vertices(np.maximum(Q0[i] - eps, 0), np.minimum(Q0[i] + eps, 1), 1 - r_min)
+             for i in range(n)]
+    vals = []
+    for combo in itertools.product(*verts):
+        vals.append(_afc_np(np.array(combo), s))
+    vals = np.array(vals)
+    for v in range(n):
+        hi = O.robust_envelope(Q0, eps, r_min, v, +1, support_only=False, s=s)
+        lo = O.robust_envelope(Q0, eps, r_min, v, -1, support_only=False, s=s)
+        assert abs(hi - vals[:, v].max()) <= 1e-9 and abs(lo - vals[:, v].min()) <= 1e-9
+        assert lo < _afc_np(Q0, s)[v] < hi
+
+
+def test_envelope_degenerate_and_interior_kernels():
+    Q0, s = _tiny_chain(7)
+    b0 = _afc_np(Q0, s)
+    for v in range(3):   # eps = 0: the set is the nominal kernel alone
+        for sense in (1, -1):
+            assert abs(O.robust_envelope(Q0, 0.0, 0.05, v, sense, False, s) - b0[v]) <= 1e-9
+    # random kernels of the set land inside; the LP's own kernel attains its value
+    rng = np.random.default_rng(8)
+    eps, r_min = 0.1, 0.05
+    verts = [_row_vertices(np.maximum(Q0[i] - eps, 0), np.minimum(Q0[i] + eps, 1), 1 - r_min)
+             for i in range(3)]
+    env = {(v, sn): O.robust_envelope(Q0, eps, r_min, v, sn, False, s, kernel=True)
+           for v in range(3) for sn in (1, -1)}
+    for _ in range(200):
+        Q = np.array([rng.dirichlet(np.ones(len(vt))) @ vt for vt in verts])
+        b = _afc_np(Q, s)
+        for v in range(3):
+            assert env[(v, -1)][0] - 1e-12 <= b[v] <= env[(v, 1)][0] + 1e-12
+    for (v, sn), (val, Qs) in env.items():
+        assert abs(_afc_np(Qs, s)[v] - val) <= 1e-9
+        assert (Qs.sum(axis=1) <= 1 - r_min + 1e-9).all()
+        assert (np.abs(Qs - Q0) <= eps + 1e-9).all()
