@@ -742,9 +742,17 @@ def run_robust(args):
         t0 = _time.perf_counter()
         rv = q.robust_value(eps=0.05, r_min=0.05, support_only=False, sense=+1)
         t_rv = _time.perf_counter() - t0
+        # exact envelopes of the nominal Top-5 over the same set (10 problems in one batch)
+        t0 = _time.perf_counter()
+        env = q.robust_envelope(top(b), eps=0.05, r_min=0.05, support_only=False)
+        t_env = _time.perf_counter() - t0
         out["runs"][name] = {"seconds": wall, "samples_per_s": 100 / wall, "c": q.c,
                              "robust_value_s": t_rv, "robust_value_rounds": rv["iterations"],
                              "robust_max_expected_T": rv["expected_T"],
+                             "envelope_top5": {"b_lo": env["b_lo"].tolist(),
+                                               "b_hi": env["b_hi"].tolist(),
+                                               "dinkelbach_steps": env["iterations"].tolist(),
+                                               "seconds": t_env},
                              "top5_nominal": top(b), "top5_kl": top(res["b_kl"]),
                              "top5_w1": top(res["b_w1"]), "kl_max": res["kl_max"],
                              "w1_max": res["w1_max"]}

@@ -357,6 +357,25 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
                      double *scalars, int32_t *iterations, void *workspace, size_t workspace_bytes,
                      void *stream);
 
+/* Envelopes of AFC coordinates over the row-wise uncertainty set (Remark on the robust
+ * optimisation viewpoint in Sec. 5: inf / sup over P in U of b_v(s; P)), with U the set of
+ * afc_robust_inner (box of radius eps around the kernel assembled from `counts`, transient row
+ * sums at most 1 - r_min, support_only as there).  b_v = (s N)_v / (s N 1) is linear-fractional
+ * in the visits, so its extremes are the roots of F(lambda) = opt over U of s N (e_v - lambda 1),
+ * a robust value that policy iteration computes exactly on a rectangular set (afc_robust_value
+ * with that reward); Dinkelbach's iteration lambda <- b_v(argopt) from lambda = 0 reaches the
+ * root (until lambda moves by at most 1e-13 relative, at most 60 steps).  The 2k problems (the
+ * supremum and the infimum for each of the k HOST nodes) run as one batch: one CTA each for the
+ * dense FP64 LU of I - Q*.  HOST out: b_lo [k], b_hi [k], iterations [2k] (or NULL: Dinkelbach
+ * steps of the supremum, then the infimum, per node).  n <= 4096.  Workspace:
+ * afc_robust_envelope_workspace(n, k) (2 n^2 + O(n) doubles per problem).  SYNCHRONISES
+ * `stream`.  Errors as afc_robust_value; AFC_EDEVICE when Dinkelbach does not settle. */
+size_t afc_robust_envelope_workspace(int32_t n, int32_t k);
+int afc_robust_envelope(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                        int32_t support_only, int32_t k, const int32_t *nodes, double *b_lo,
+                        double *b_hi, int32_t *iterations, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
 /* Wasserstein-1 distances under the base graph's shortest-path (hop) metric, the second
  * discrepancy of the paper's robust search (Sec. 9): out[k] = W1(x_k, y) for the `count` HOST
  * rows x_k = x + k n (each summing to sum y), over the HOST edge lists eu, ev (as

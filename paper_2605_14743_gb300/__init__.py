@@ -37,7 +37,8 @@ __all__ = [
     "afc_result_destroy", "afc_perturb", "afc_submit", "afc_poll", "afc_debug_realization",
     "TuneResult", "afc_autotune", "afc_feasibility", "afc_pool_summaries", "afc_clique_pool",
     "afc_bootstrap_workspace", "afc_bootstrap", "afc_w1_graph", "afc_w1_batch_workspace",
-    "afc_w1_batch", "afc_rank_order", "afc_robust_summary", "afc_robust_inner",
+    "afc_w1_batch", "afc_rank_order", "afc_robust_summary", "afc_robust_envelope_workspace",
+    "afc_robust_envelope", "afc_robust_inner",
     "afc_robust_value_workspace", "afc_robust_value", "afc_weight_table_normal",
     "afc_measure_fma_rate",
 ]
@@ -163,6 +164,9 @@ _SIGS = {
     "afc_w1_batch": ([c_i32, c_i64, c_p, c_p, c_p, c_p, c_p, c_i32, c_p, c_p, c_sz, c_p],
                      ctypes.c_int),
     "afc_rank_order": ([c_i32, c_p, c_f64, c_i32, c_p, c_p, c_p], ctypes.c_int),
+    "afc_robust_envelope_workspace": ([c_i32, c_i32], c_sz),
+    "afc_robust_envelope": ([ctypes.POINTER(Chain), c_p, c_f64, c_f64, c_i32, c_i32, c_p, c_p, c_p,
+                             c_p, c_p, c_sz, c_p], ctypes.c_int),
     "afc_robust_summary": ([c_i32, c_i32, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p], ctypes.c_int),
     "afc_measure_fma_rate": ([c_i32, c_p, c_p], ctypes.c_int),
     "afc_weight_table_normal": ([c_i64, c_p, c_u32, c_f64, c_f64, c_p, c_p, c_sz, c_p],
@@ -386,6 +390,23 @@ def afc_w1_batch(n, m, row_ptr, col, eid, x, y, count, out, workspace, workspace
 def afc_rank_order(n, b, tie_rel, k, rank, topk, stream):
     _chk(lib().afc_rank_order(int(n), _ptr(b), float(tie_rel), int(k), _ptr(rank), _ptr(topk),
                               stream))
+
+
+def afc_robust_envelope_workspace(n, k) -> int:
+    return int(lib().afc_robust_envelope_workspace(int(n), int(k)))
+
+
+def afc_robust_envelope(chain, counts, eps, r_min, support_only, nodes, workspace,
+                        workspace_bytes, stream):
+    """(b_lo [k], b_hi [k], iterations [k, 2]) for the HOST node list `nodes`."""
+    nodes = np.ascontiguousarray(nodes, np.int32)
+    k = int(nodes.shape[0])
+    lo, hi = np.zeros(k), np.zeros(k)
+    its = np.zeros(2 * k, np.int32)
+    _chk(lib().afc_robust_envelope(ctypes.byref(chain), _ptr(counts), float(eps), float(r_min),
+                                   int(support_only), k, _ptr(nodes), _ptr(lo), _ptr(hi),
+                                   _ptr(its), _ptr(workspace), int(workspace_bytes), stream))
+    return lo, hi, its.reshape(k, 2)
 
 
 def afc_robust_summary(n, count, b_rows, b0, d1, d2, arg, b_low, b_high, stream):

@@ -268,6 +268,131 @@ int afc_robust_value(const afc_chain *chain, const uint32_t *counts, double eps,
   return AFC_OK;
 }
 
+// Envelope workspace: [status | per-problem scalars | per-problem slabs (Q*, A, V, x, T, f, piv)].
+static size_t env_head_bytes(size_t P) { return 256 + al256h(P * 48); }
+static size_t env_problem_bytes(size_t n) {
+  return 2 * al256h(8 * n * n) + 4 * al256h(8 * n) + al256h(4 * n);
+}
+
+size_t afc_robust_envelope_workspace(int32_t n, int32_t k) {
+  if (n < 1 || n > 4096 || k < 1) return 0;
+  const size_t P = 2 * (size_t)k;
+  return env_head_bytes(P) + P * env_problem_bytes((size_t)n);
+}
+
+int afc_robust_envelope(const afc_chain *chain, const uint32_t *counts, double eps, double r_min,
+                        int32_t support_only, int32_t k, const int32_t *nodes, double *b_lo,
+                        double *b_hi, int32_t *iterations, void *workspace,
+                        size_t workspace_bytes, void *stream) {
+  NvtxRange nvtx_range("afc.robust_envelope");
+  int st = robust_checks(chain, counts, eps, r_min);
+  if (st) return st;
+  const int32_t n = chain->n;
+  if (k < 1 || !nodes || !b_lo || !b_hi) return fail(AFC_EINVAL, "bad arguments");
+  for (int32_t q = 0; q < k; ++q)
+    if (nodes[q] < 0 || nodes[q] >= n) return fail(AFC_EINVAL, "node %d out of range", nodes[q]);
+  if (n > 4096) return fail(AFC_EUNSUPPORTED, "the envelopes take n <= 4096 (dense LU)");
+  const size_t need = afc_robust_envelope_workspace(n, k);
+  if (!workspace || workspace_bytes < need)
+    return fail(AFC_ENOMEM, "workspace of %zu bytes given, %zu needed", workspace_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t P = 2u * (uint32_t)k;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws);
+  unsigned char *h = ws + 256;
+  uint32_t *d_active = reinterpret_cast<uint32_t *>(h);
+  double *d_vsign = reinterpret_cast<double *>(h + 8 * (size_t)P);
+  double *d_lambda = d_vsign + P;
+  int32_t *d_node = reinterpret_cast<int32_t *>(d_lambda + P);
+  double *d_diff = reinterpret_cast<double *>(d_node + 2 * (size_t)P);
+  double *d_ratio = d_diff + P;
+  const size_t nn = (size_t)n * n, vs = (al256h(8 * (size_t)n)) / 8;
+  unsigned char *slab = ws + env_head_bytes(P);
+  EnvBatch B{};
+  B.Qs = reinterpret_cast<double *>(slab);
+  B.A = B.Qs + P * (al256h(8 * nn) / 8);
+  double *vec = B.A + P * (al256h(8 * nn) / 8);
+  B.vstride = vs;
+  B.V = vec;
+  B.x = B.V + P * vs;
+  B.T = B.x + P * vs;
+  B.f = B.T + P * vs;
+  B.piv = reinterpret_cast<int32_t *>(B.f + P * vs);
+  B.active = d_active;
+  B.vsign = d_vsign;
+  B.lambda = d_lambda;
+  B.node = d_node;
+  B.diff = d_diff;
+  B.ratio = d_ratio;
+  // problem 2q: the supremum of b_v (the adversary maximises: vsign -1), 2q + 1: the infimum
+  std::vector<uint32_t> dk(P, 1u), pi(P, 0u);
+  std::vector<double> vsign(P), lambda(P, 0.0), diff(P), ratio(P), result(P, 0.0);
+  std::vector<int32_t> node(2 * (size_t)P, 0), its(P, 0);
+  for (uint32_t p = 0; p < P; ++p) {
+    node[p] = nodes[p / 2];
+    vsign[p] = (p % 2 == 0) ? -1.0 : 1.0;
+  }
+  AFC_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), s));
+  AFC_CUDA(cudaMemcpyAsync(d_vsign, vsign.data(), 8 * (size_t)P, cudaMemcpyHostToDevice, s));
+  AFC_CUDA(cudaMemcpyAsync(d_node, node.data(), 4 * (size_t)P, cudaMemcpyHostToDevice, s));
+  auto check_status = [&]() -> int {
+    uint32_t hs = 0;
+    AFC_CUDA(cudaMemcpyAsync(&hs, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    AFC_CUDA(cudaStreamSynchronize(s));
+    if (hs & kErrInput) return fail(AFC_EINVAL, "empty uncertainty set: a row's lower bounds exceed 1 - r_min");
+    if (hs & kErrSolve) return fail(AFC_ESINGULAR, "zero pivot in I - Q*");
+    return AFC_OK;
+  };
+  // Dinkelbach: lambda <- b_v of the kernel optimising s N (e_v - lambda 1) over the set, until
+  // it stops moving (that optimum is then 0 and lambda the envelope)
+  for (int outer = 0; outer < 60; ++outer) {
+    if (std::find(dk.begin(), dk.end(), 1u) == dk.end()) break;
+    AFC_CUDA(cudaMemcpyAsync(d_lambda, lambda.data(), 8 * (size_t)P, cudaMemcpyHostToDevice, s));
+    AFC_CUDA(cudaMemcpyAsync(d_active, dk.data(), 4 * (size_t)P, cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_env_reward(n, P, B, s);
+    if (e != cudaSuccess) return cuda_fail(e, "envelope reward");
+    // policy iteration of every problem still moving, in lockstep
+    pi = dk;
+    for (int it = 0; it < 100; ++it) {
+      AFC_CUDA(cudaMemcpyAsync(d_active, pi.data(), 4 * (size_t)P, cudaMemcpyHostToDevice, s));
+      e = launch_env_round(n, chain->realizations, chain->alpha, chain->absorb_floor, counts, eps,
+                           r_min, support_only ? 1 : 0, P, B, status, s);
+      if (e != cudaSuccess) return cuda_fail(e, "envelope round");
+      AFC_CUDA(cudaMemcpyAsync(diff.data(), d_diff, 8 * (size_t)P, cudaMemcpyDeviceToHost, s));
+      if (int rc = check_status()) return rc;
+      bool any = false;
+      for (uint32_t p = 0; p < P; ++p) {
+        if (pi[p] && it > 0 && diff[p] <= 1e-13) pi[p] = 0;
+        any = any || pi[p];
+      }
+      if (!any) break;
+    }
+    AFC_CUDA(cudaMemcpyAsync(d_active, dk.data(), 4 * (size_t)P, cudaMemcpyHostToDevice, s));
+    e = launch_env_ratio(n, chain->s_init, P, B, s);
+    if (e != cudaSuccess) return cuda_fail(e, "envelope ratio");
+    AFC_CUDA(cudaMemcpyAsync(ratio.data(), d_ratio, 8 * (size_t)P, cudaMemcpyDeviceToHost, s));
+    if (int rc = check_status()) return rc;
+    for (uint32_t p = 0; p < P; ++p) {
+      if (!dk[p]) continue;
+      ++its[p];
+      result[p] = ratio[p];
+      if (std::fabs(ratio[p] - lambda[p]) <= 1e-13 * std::fabs(ratio[p])) dk[p] = 0;
+      else lambda[p] = ratio[p];
+    }
+  }
+  if (std::find(dk.begin(), dk.end(), 1u) != dk.end())
+    return fail(AFC_EDEVICE, "envelope: the Dinkelbach iteration did not settle in 60 steps");
+  for (int32_t q = 0; q < k; ++q) {
+    b_hi[q] = result[2 * q];
+    b_lo[q] = result[2 * q + 1];
+    if (iterations) {
+      iterations[2 * q] = its[2 * q];
+      iterations[2 * q + 1] = its[2 * q + 1];
+    }
+  }
+  return AFC_OK;
+}
+
 int afc_w1_graph(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const double *x,
                  const double *y, int32_t count, double *out) {
   NvtxRange nvtx_range("afc.w1_graph");

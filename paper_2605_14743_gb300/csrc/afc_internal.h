@@ -140,6 +140,27 @@ cudaError_t launch_w1(int32_t n, int64_t m, const int32_t *rp, const int32_t *co
 // perturb.cu: ranking under the tie band (rank [n]) and the first k nodes in rank order
 cudaError_t launch_rank(int32_t n, const double *b, double tie_rel, int32_t k, int32_t *rank,
                         int32_t *topk, cudaStream_t stream);
+// robust.cu: a batch of robust problems on one estimated kernel, each with its own node v,
+// sense and Dinkelbach parameter lambda (the envelopes of b_v over the row-wise set); problem
+// p's n-vectors at p * vstride, its n x n matrices at p * n * n
+struct EnvBatch {
+  double *Qs, *A;                 // [P][n][n] the inner problem's kernel; I - Q* then its LU
+  double *V, *x, *T, *f;          // [P][vstride]
+  int32_t *piv;                   // [P][vstride]
+  size_t vstride;
+  const uint32_t *active;         // [P] 1 while the problem iterates
+  const double *vsign;            // [P] 1: the adversary minimises, -1: it maximises
+  const double *lambda;           // [P]
+  const int32_t *node;            // [P]
+  double *diff, *ratio;           // [P] policy-evaluation change; b_v of the current kernel
+};
+cudaError_t launch_env_reward(int32_t n, uint32_t P, const EnvBatch &B, cudaStream_t stream);
+cudaError_t launch_env_round(int32_t n, uint32_t R, double alpha, double eta,
+                             const uint32_t *counts, double eps, double r_min, int support_only,
+                             uint32_t P, const EnvBatch &B, uint32_t *status,
+                             cudaStream_t stream);
+cudaError_t launch_env_ratio(int32_t n, const double *s, uint32_t P, const EnvBatch &B,
+                             cudaStream_t stream);
 // robust.cu: maximisers of two discrepancies and the sampled envelopes of a robust search
 cudaError_t launch_robust_summary(int32_t n, int32_t count, const double *rows, const double *b0,
                                   const double *d1, const double *d2, int32_t *arg, double *lo,

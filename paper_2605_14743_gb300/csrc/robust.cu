@@ -53,14 +53,13 @@ __device__ __forceinline__ double warp_sum_d(double x) {
   return x;
 }
 
-// Row-wise inner problem (warp per row) at the continuation value vsign * (v, v_bot).
-__global__ void robust_inner_kernel(int32_t n, uint32_t R, double alpha, double eta,
-                                    const uint32_t *counts, double eps, double r_min,
-                                    int support_only, const double *v, double v_bot, double vsign,
-                                    double *T, double *Qstar, uint32_t *status) {
+// Row-wise inner problem (warp per row, rows warp, warp + nwarps, ...) at the continuation
+// value vsign * (v, v_bot).
+__device__ void inner_rows(int32_t n, uint32_t R, double alpha, double eta,
+                           const uint32_t *counts, double eps, double r_min, int support_only,
+                           const double *v, double v_bot, double vsign, double *T, double *Qstar,
+                           uint32_t *status, uint32_t warp, uint32_t nwarps) {
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const size_t stride = (size_t)n + 1;
   const double vb = vsign * v_bot;
   for (uint32_t i = warp; i < (uint32_t)n; i += nwarps) {
@@ -123,6 +122,15 @@ __global__ void robust_inner_kernel(int32_t n, uint32_t R, double alpha, double 
   }
 }
 
+__global__ void robust_inner_kernel(int32_t n, uint32_t R, double alpha, double eta,
+                                    const uint32_t *counts, double eps, double r_min,
+                                    int support_only, const double *v, double v_bot, double vsign,
+                                    double *T, double *Qstar, uint32_t *status) {
+  inner_rows(n, R, alpha, eta, counts, eps, r_min, support_only, v, v_bot, vsign, T, Qstar,
+             status, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5);
+}
+
 __global__ void build_a_kernel(int32_t n, const double *Qstar, double *A) {
   const size_t nn = (size_t)n * n;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nn;
@@ -132,17 +140,10 @@ __global__ void build_a_kernel(int32_t n, const double *Qstar, double *A) {
 
 // One CTA of 256 threads: factor A (the blocked LU: the matrix is in device memory), V_new =
 // A^-1 f (f = 1 when null), diff = max |V_new - V|, V <- V_new.
-__global__ void __launch_bounds__(256, 1)
-eval_kernel(int32_t n, double *A, int32_t *piv, const double *f, double *V, double *x,
-            double *diff, uint32_t *status) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double sval[33];
-  __shared__ int32_t sidx[32];
-  __shared__ double sb[2];
-  __shared__ int32_t sflag[1];
-  __shared__ double red[33];
-  LinScratch ls{sval, sidx, sb, sflag};
-  if (!lu_factor_blocked(A, n, n, piv, ls, reinterpret_cast<double *>(smem))) {
+__device__ void eval_body(int32_t n, double *A, int32_t *piv, const double *f, double *V,
+                          double *x, double *diff, uint32_t *status, LinScratch ls, double *red,
+                          double *tiles) {
+  if (!lu_factor_blocked(A, n, n, piv, ls, tiles)) {
     if (threadIdx.x == 0) { atomicOr(status, kErrSolve); *diff = 0.0; }
     return;
   }
@@ -158,6 +159,19 @@ eval_kernel(int32_t n, double *A, int32_t *piv, const double *f, double *V, doub
   scale = block_max(scale, red);
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) V[i] = x[i];
   if (threadIdx.x == 0) *diff = m / scale;
+}
+
+__global__ void __launch_bounds__(256, 1)
+eval_kernel(int32_t n, double *A, int32_t *piv, const double *f, double *V, double *x,
+            double *diff, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  LinScratch ls{sval, sidx, sb, sflag};
+  eval_body(n, A, piv, f, V, x, diff, status, ls, red, reinterpret_cast<double *>(smem));
 }
 
 // The AFC of the scenario kernel from the factors of the last evaluation: A^T mu = s,
@@ -185,7 +199,103 @@ star_kernel(int32_t n, const double *A, const int32_t *piv, const double *s, con
   if (threadIdx.x == 0) { out[0] = T; out[1] = TF / T; }
 }
 
+// ---- batched robust problems (the envelopes): problem p's arrays at p times the stride ----
+
+// inner problem of every active problem (blockIdx.y = problem)
+__global__ void inner_batched_kernel(int32_t n, uint32_t R, double alpha, double eta,
+                                     const uint32_t *counts, double eps, double r_min,
+                                     int support_only, const EnvBatch B, uint32_t *status) {
+  const uint32_t p = blockIdx.y;
+  if (!B.active[p]) return;
+  const size_t nn = (size_t)n * n;
+  inner_rows(n, R, alpha, eta, counts, eps, r_min, support_only, B.V + p * B.vstride, 0.0,
+             B.vsign[p], B.T + p * B.vstride, B.Qs + p * nn, status,
+             (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
+}
+
+// one CTA per active problem: A = I - Q*, its LU, V <- A^-1 f, diff
+__global__ void __launch_bounds__(256, 1)
+eval_batched_kernel(int32_t n, const EnvBatch B, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  const uint32_t p = blockIdx.x;
+  if (!B.active[p]) return;
+  LinScratch ls{sval, sidx, sb, sflag};
+  const size_t nn = (size_t)n * n;
+  const double *Qs = B.Qs + p * nn;
+  double *A = B.A + p * nn;
+  for (size_t k = threadIdx.x; k < nn; k += blockDim.x)
+    A[k] = ((k / n) == (k % n) ? 1.0 : 0.0) - Qs[k];
+  __syncthreads();
+  eval_body(n, A, B.piv + p * B.vstride, B.f + p * B.vstride, B.V + p * B.vstride,
+            B.x + p * B.vstride, B.diff + p, status, ls, red, reinterpret_cast<double *>(smem));
+}
+
+// one CTA per active problem: the visits mu of its kernel (A^T mu = s from the last factors),
+// ratio[p] = mu_v / sum mu = b_v for the problem's node v
+__global__ void __launch_bounds__(1024, 1)
+star_batched_kernel(int32_t n, const double *s, const EnvBatch B) {
+  __shared__ double sval[33];
+  __shared__ int32_t sidx[32];
+  __shared__ double sb[2];
+  __shared__ int32_t sflag[1];
+  __shared__ double red[33];
+  const uint32_t p = blockIdx.x;
+  if (!B.active[p]) return;
+  LinScratch ls{sval, sidx, sb, sflag};
+  double *mu = B.x + p * B.vstride;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) mu[i] = s ? s[i] : 1.0 / (double)n;
+  __syncthreads();
+  lu_solve_transposed(B.A + p * (size_t)n * n, n, n, B.piv + p * B.vstride, mu, ls);
+  double t = 0.0;
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) t += mu[i];
+  const double T = block_sum(t, red);
+  if (threadIdx.x == 0) B.ratio[p] = mu[B.node[p]] / T;
+}
+
+// f_p = e_v - lambda_p for every active problem
+__global__ void env_reward_kernel(int32_t n, uint32_t P, const EnvBatch B) {
+  const size_t total = (size_t)P * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t p = (uint32_t)(k / n);
+    const int32_t j = (int32_t)(k % n);
+    if (!B.active[p]) continue;
+    B.f[p * B.vstride + j] = (j == B.node[p] ? 1.0 : 0.0) - B.lambda[p];
+    B.V[p * B.vstride + j] = 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_env_reward(int32_t n, uint32_t P, const EnvBatch &B, cudaStream_t stream) {
+  const size_t total = (size_t)P * n;
+  const int grid = (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 4096));
+  env_reward_kernel<<<grid, 256, 0, stream>>>(n, P, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_round(int32_t n, uint32_t R, double alpha, double eta,
+                             const uint32_t *counts, double eps, double r_min, int support_only,
+                             uint32_t P, const EnvBatch &B, uint32_t *status,
+                             cudaStream_t stream) {
+  const dim3 grid((unsigned)std::min<int64_t>(((int64_t)n + 7) / 8, 1024), P);
+  inner_batched_kernel<<<grid, 256, 0, stream>>>(n, R, alpha, eta, counts, eps, r_min,
+                                                 support_only, B, status);
+  eval_batched_kernel<<<P, 256, sizeof(double) * lu_blocked_smem_doubles(), stream>>>(n, B,
+                                                                                     status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_ratio(int32_t n, const double *s, uint32_t P, const EnvBatch &B,
+                             cudaStream_t stream) {
+  star_batched_kernel<<<P, 1024, 0, stream>>>(n, s, B);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_robust_inner(int32_t n, uint32_t R, double alpha, double eta,
                                 const uint32_t *counts, double eps, double r_min,

@@ -17,7 +17,8 @@ from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProbl
                PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
                afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility,
-               afc_rank_order, afc_robust_summary, afc_w1_batch, afc_w1_batch_workspace,
+               afc_rank_order, afc_robust_envelope, afc_robust_envelope_workspace,
+               afc_robust_summary, afc_w1_batch, afc_w1_batch_workspace,
                afc_robust_value, afc_robust_value_workspace,
                afc_pool_summaries, afc_transition_counts,
                afc_transition_counts_workspace)
@@ -405,6 +406,19 @@ class Query:
         sc = sc.cpu().numpy()
         return {"V": V, "Qstar": Qs, "b_star": b, "expected_T": float(sc[0]), "b_f": float(sc[1]),
                 "iterations": it}
+
+    def robust_envelope(self, nodes, eps=0.05, r_min=0.05, support_only=True):
+        """inf / sup of b_v over the row-wise set of robust_value (Remark on the robust
+        optimisation viewpoint in Sec. 5) for the given nodes, exactly (Dinkelbach over robust
+        policy iteration, all nodes and both senses in one batch).  Needs the counts.  Returns
+        a dict with b_lo, b_hi (numpy, one entry per node) and the Dinkelbach steps [k, 2]."""
+        torch = self.torch
+        nodes = np.asarray(nodes, np.int32).reshape(-1)
+        wsb = afc_robust_envelope_workspace(self.n, len(nodes))
+        ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=self.counts.device)
+        lo, hi, its = afc_robust_envelope(self.chain(), self.counts, eps, r_min, support_only,
+                                          nodes, ws, ws.numel(), self._stream())
+        return {"nodes": nodes, "b_lo": lo, "b_hi": hi, "iterations": its}
 
     def w1(self, x, y, count=None):
         """W1 distances under the base graph's hop metric between the rows of the device array

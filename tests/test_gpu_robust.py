@@ -140,3 +140,32 @@ def test_robust_value_vs_oracle(sense, support_only):
     assert abs(res["expected_T"] - T) <= 1e-9 * T and abs(res["b_f"] - bf) <= 1e-9 * abs(bf)
     assert np.allclose(res["Qstar"].cpu().numpy(), Qs, rtol=0, atol=1e-9)
     assert 2 <= res["iterations"] <= 100
+
+
+@pytest.mark.parametrize("support_only", [1, 0])
+def test_robust_envelope_vs_occupancy_lp(support_only):
+    """inf / sup of b_v over the row-wise set (Remark on the robust optimisation viewpoint,
+    Sec. 5): Dinkelbach over robust policy iteration on the device against the oracle's LP over
+    occupancy measures, for the nominal top three, a middle node and a node never visited
+    after the start."""
+    wl = variant(workload("small_er"), realizations=400)
+    counts, _ = oracle_counts(wl, 0, 400)
+    Q, _ = O.assemble_q(counts, 400, wl.alpha)
+    q = _device_chain(wl, counts)
+    q.run_solve()
+    b = q.b.cpu().numpy()
+    order = np.argsort(-b, kind="stable")
+    cold = [v for v in range(wl.n) if counts[:, v].sum() == 0]
+    nodes = [int(order[0]), int(order[1]), int(order[2]), int(order[wl.n // 2])] + cold[:1]
+    eps, r_min = 0.05, 0.05
+    res = q.robust_envelope(nodes, eps=eps, r_min=r_min, support_only=bool(support_only))
+    for i, v in enumerate(nodes):
+        hi = O.robust_envelope(Q, eps, r_min, v, +1, support_only=bool(support_only))
+        lo = O.robust_envelope(Q, eps, r_min, v, -1, support_only=bool(support_only))
+        assert abs(res["b_hi"][i] - hi) <= 1e-9 * max(hi, 1e-12), (v, res["b_hi"][i], hi)
+        assert abs(res["b_lo"][i] - lo) <= 1e-9 * max(lo, 1e-12), (v, res["b_lo"][i], lo)
+        assert res["b_lo"][i] <= b[v] + 1e-15 <= res["b_hi"][i] + 2e-15
+    assert (res["iterations"] >= 1).all() and (res["iterations"] <= 60).all()
+    # a set of radius 0 holds the nominal kernel alone
+    res0 = q.robust_envelope(nodes[:2], eps=0.0, r_min=r_min, support_only=bool(support_only))
+    assert close(res0["b_lo"], b[nodes[:2]]) and close(res0["b_hi"], b[nodes[:2]])
