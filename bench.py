@@ -408,8 +408,8 @@ def mix_compare(batch, label, clock_gpu=0):
     probs = (afc.McProblem * len(batch))(*[q.prob for q in q32])
     rc = np.array([w.realizations for w in batch], np.uint32)
     ptrs = np.array([q.counts.data_ptr() for q in q32], np.uint64)
-    stats32 = torch.zeros((len(batch), 7), dtype=torch.int64, device="cuda")
-    stats64 = [torch.zeros(7, dtype=torch.int64, device="cuda") for _ in batch]
+    stats32 = torch.zeros((len(batch), afc.MC_STATS_WORDS), dtype=torch.int64, device="cuda")
+    stats64 = [torch.zeros(afc.MC_STATS_WORDS, dtype=torch.int64, device="cuda") for _ in batch]
     wsb = afc.afc_transition_counts_batched_workspace(len(batch), probs, rc)
     ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
 

@@ -168,6 +168,8 @@ typedef struct {
   uint64_t rechecked;        /* FP32 mode: realizations recomputed in FP64                */
   uint64_t device_error;     /* bit mask of device consistency failures (0 = none)         */
   uint64_t vertex_visits;    /* sum over solved sources of the size of the source's component */
+  uint64_t wide_redone;      /* shared-memory path: realizations redone with 64-bit path-count */
+                             /* slots because a count exceeded 2^32 - 1 (results unchanged)   */
 } afc_mc_stats;
 
 /* AFC_PATH_SHARED or AFC_PATH_GLOBAL: where afc_transition_counts runs this problem (the

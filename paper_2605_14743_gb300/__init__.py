@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "AfcError", "lib", "McProblem", "McStats", "Chain", "PerturbParams", "HostQuery", "HostResult",
+    "AfcError", "lib", "McProblem", "McStats", "MC_STATS_WORDS", "Chain", "PerturbParams", "HostQuery", "HostResult",
     "afc_last_error", "afc_version", "afc_csr_from_edges", "afc_survival_threshold",
     "afc_transition_counts_workspace", "afc_transition_counts", "afc_counts_path",
     "afc_reward_afc",
@@ -80,7 +80,10 @@ class McProblem(ctypes.Structure):
 class McStats(ctypes.Structure):
     _fields_ = [("realizations", c_u64), ("sources", c_u64), ("edge_visits", c_u64),
                 ("overflow", c_u64), ("rechecked", c_u64), ("device_error", c_u64),
-                ("vertex_visits", c_u64)]
+                ("vertex_visits", c_u64), ("wide_redone", c_u64)]
+
+
+MC_STATS_WORDS = ctypes.sizeof(McStats) // 8   # afc_mc_stats as a uint64 device array
 
 
 class Chain(ctypes.Structure):

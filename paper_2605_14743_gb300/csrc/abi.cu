@@ -182,12 +182,10 @@ struct McPlan {
   bool fits = true;
 };
 
-// Source slots that fit next to the realization of an (n, arcs) graph within `bytes` of
-// shared memory.
+// Source slots (narrow: 32-bit path counts) that fit next to the realization of an (n, arcs)
+// graph within `bytes` of shared memory, with room for at least one wide slot.
 uint32_t slots_within(uint32_t n, uint64_t arcs, uint32_t bytes) {
-  const uint32_t base = mc_layout_bytes(n, arcs, 0);
-  const uint32_t one = mc_layout_bytes(n, arcs, 1) - base;
-  return base <= bytes ? (bytes - base) / one : 0u;
+  return mc_slots_within(n, arcs, bytes);
 }
 
 // want_warps: source warps the launch should offer (0: as many as fit for the largest graph;

@@ -22,12 +22,16 @@
 namespace afc {
 
 // Shared-memory layout of a counting CTA: control head, the realization (rp, arcs, smallest
-// incident length) and one slot per source warp.  What the source warps do not touch while
-// they run (components, the source list, selection scratch, betweenness accumulators) lives
-// in the CTA's region of device memory (CtaScratch), so that more source slots fit on chip.
+// incident length) and the source slots.  What the source warps do not touch while they run
+// (components, the source list, selection scratch, betweenness accumulators) lives in the
+// CTA's region of device memory (CtaScratch), so that more source slots fit on chip.  The slot
+// region holds nsw narrow slots (14 bytes per node: 32-bit path counts, the pending list in
+// their words' high halves) and, reusing the same bytes, wide_slots() 16-byte slots (64-bit
+// path counts, separate pending list) for a realization whose path counts need them; it is
+// never smaller than one wide slot.
 struct StepLayout {
   uint32_t off_rp, off_arc, off_mw, off_slots;
-  uint32_t slot_bytes, total;
+  uint32_t slot_bytes, wide_bytes, total;
   __host__ __device__ static uint32_t al(uint32_t x) { return al16(x); }
   __host__ __device__ void make(uint32_t n, uint32_t arcs, uint32_t nsw) {
     uint32_t o = al(sizeof(CtaHead));
@@ -35,16 +39,23 @@ struct StepLayout {
     off_arc = o;    o = al(o + 4u * (arcs > 0 ? arcs : 1));
     off_mw = o;     o = al(o + 2u * n);
     off_slots = o;
-    slot_bytes = al(4u * n) + al(8u * n) + 2u * al(2u * n);
-    total = o + nsw * slot_bytes;
+    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n);
+    wide_bytes = slot_bytes + al(2u * n);
+    const uint32_t region = nsw * slot_bytes;
+    total = o + (nsw == 0 ? 0u : (region > wide_bytes ? region : wide_bytes));
   }
-  __device__ StepSlot slot(unsigned char *smem, uint32_t i, uint32_t n) const {
-    unsigned char *p = smem + off_slots + i * slot_bytes;
+  // wide slots in the region of nsw narrow ones (at least one)
+  __host__ __device__ uint32_t wide_slots(uint32_t nsw) const {
+    const uint32_t k = nsw * slot_bytes / wide_bytes;
+    return k > 0 ? k : 1u;
+  }
+  __device__ StepSlot slot(unsigned char *smem, uint32_t i, uint32_t n, bool wide) const {
+    unsigned char *p = smem + off_slots + i * (wide ? wide_bytes : slot_bytes);
     StepSlot s;
     s.dist = reinterpret_cast<uint32_t *>(p);  p += al(4u * n);
     s.sig = reinterpret_cast<uint64_t *>(p);   p += al(8u * n);
     s.ord = reinterpret_cast<uint16_t *>(p);   p += al(2u * n);
-    s.plist = reinterpret_cast<uint16_t *>(p);
+    s.plist = wide ? reinterpret_cast<uint16_t *>(p) : nullptr;
     return s;
   }
 };
@@ -106,7 +117,7 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     uint32_t *comp = cs.comp, *cinfo = cs.cinfo, *sel = cs.sel;
     uint16_t *src = cs.src;
     if (threadIdx.x == 0) {
-      ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->cursor = 0;
+      ctl->err = 0; ctl->ovf = 0; ctl->nsrc = 0; ctl->cursor = 0; ctl->wide_redo = 0;
       ctl->edges = 0; ctl->verts = 0; ctl->wmax = 1;
     }
     __syncthreads();
@@ -157,39 +168,57 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     __syncthreads();
     const uint32_t nsrc = ctl->nsrc;
 
-    const bool fp32 = (P.precision == 1);
-    const StepSlot s0 = L.slot(smem, 0, n);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      const bool use32 = fp32 && attempt == 0;
-      if (attempt == 1) {
+    // Attempts: narrow slots first; a path count above 2^32 - 1 redoes the realization with
+    // wide slots (fewer sources at a time), and in FP32 mode a top-two gap under the margin
+    // redoes it with FP64 dependencies.  Each can happen once: at most three attempts.
+    bool use32 = (P.precision == 1), wide = false;
+    const StepSlot s0 = L.slot(smem, 0, n, false);
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      if (attempt > 0) {
         for (uint32_t v = threadIdx.x; v < n; v += blockDim.x) {
           cs.a0[v] = 0ull; cs.a1[v] = 0ull; cs.a2[v] = 0ull;
         }
-        if (threadIdx.x == 0) ctl->cursor = 0;
+        if (threadIdx.x == 0) { ctl->cursor = 0; ctl->wide_redo = 0; }
         __syncthreads();
       }
-      if (warp < nsw) {
-        const StepSlot sl = L.slot(smem, warp, n);
+      if (warp < (wide ? L.wide_slots(nsw) : nsw)) {
+        const StepSlot sl = L.slot(smem, warp, n, wide);
         uint32_t err = 0, ovf = 0;
         for (;;) {
           uint32_t k = 0;
-          if (lane == 0) k = atomicAdd(&ctl->cursor, 1u);
+          if (lane == 0)
+            k = *reinterpret_cast<volatile uint32_t *>(&ctl->wide_redo) ? nsrc
+                                                                         : atomicAdd(&ctl->cursor, 1u);
           k = __shfl_sync(kFull, k, 0);
           if (k >= nsrc) break;
           const uint32_t s = src[k];
           const BcAcc acc{cs.a0, cs.a1, cs.a2};
-          const bool ok = use32 ? source_steps<float>(H, mw, sl, s, true, acc, err, ovf)
-                                : source_steps<double>(H, mw, sl, s, true, acc, err, ovf);
+          bool ok;
+          if (wide)
+            ok = use32 ? source_steps<float, false>(H, mw, sl, s, true, acc, err, ovf)
+                       : source_steps<double, false>(H, mw, sl, s, true, acc, err, ovf);
+          else
+            ok = use32 ? source_steps<float, true>(H, mw, sl, s, true, acc, err, ovf)
+                       : source_steps<double, true>(H, mw, sl, s, true, acc, err, ovf);
           if (!ok) break;
+          if (__any_sync(kFull, ovf & kOvfWide)) {
+            if (lane == 0) atomicOr(&ctl->wide_redo, 1u);
+            break;
+          }
         }
         err = __reduce_or_sync(kFull, err);
         ovf = __reduce_or_sync(kFull, ovf);
         if (lane == 0) {
           if (err) atomicOr(&ctl->err, err);
-          if (ovf) atomicOr(&ctl->ovf, 1u);
+          if (ovf & 1u) atomicOr(&ctl->ovf, 1u);
         }
       }
       __syncthreads();
+      if (ctl->wide_redo) {
+        wide = true;
+        if (threadIdx.x == 0 && P.stats) atomicAdd(u64p(&P.stats->wide_redone), 1ull);
+        continue;
+      }
       fx_finalize3(cs.a0, cs.a1, cs.a2, n);   // betweenness as doubles, in a0's storage
       __syncthreads();
       SlotArrays scratch{};
@@ -200,6 +229,7 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
                                             src, use32, ctl);
       __syncthreads();
       if (!recheck) break;
+      use32 = false;
       if (threadIdx.x == 0 && P.stats) atomicAdd(u64p(&P.stats->rechecked), 1ull);
     }
     if (threadIdx.x == 0 && P.stats) {
@@ -256,17 +286,19 @@ __global__ void debug_components_kernel(McDev P, int32_t *comp_out, int32_t *csi
   }
 }
 
-// Distances and path counts of given sources from the production forward routine: warp w of
-// CTA b handles source b * nsw + w of the list on realization r.
+// Distances and path counts of given sources from the production forward routine, on the
+// wide slots (64-bit path counts) of a layout of nsw narrow slots: warp w of CTA b handles
+// source b * W + w of the list on realization r, W = the layout's wide slots.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1)
-debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t nsw,
+debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uint32_t nsw_layout,
                   uint32_t *dist_out, uint64_t *sigma_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   CtaHead *ctl = reinterpret_cast<CtaHead *>(smem);
   const uint32_t n = P.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   StepLayout L;
-  L.make(n, (uint32_t)(2 * P.m), nsw);
+  L.make(n, (uint32_t)(2 * P.m), nsw_layout);
+  const uint32_t nsw = L.wide_slots(nsw_layout);
   uint32_t *rp = reinterpret_cast<uint32_t *>(smem + L.off_rp);
   uint32_t *arc = reinterpret_cast<uint32_t *>(smem + L.off_arc);
   uint16_t *mw = reinterpret_cast<uint16_t *>(smem + L.off_mw);
@@ -280,9 +312,9 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
   if (warp < nsw && k < (uint32_t)nsrc) {
     const int32_t sv = sources[k];
     const uint32_t s = (sv >= 0 && (uint32_t)sv < n) ? (uint32_t)sv : 0u;
-    const StepSlot sl = L.slot(smem, warp, n);
+    const StepSlot sl = L.slot(smem, warp, n, true);   // wide slots: 64-bit path counts
     uint32_t err = 0, ovf = 0;
-    source_steps<double>(H, mw, sl, s, false, BcAcc{}, err, ovf);
+    source_steps<double, false>(H, mw, sl, s, false, BcAcc{}, err, ovf);
     err = __reduce_or_sync(kFull, err);
     ovf = __reduce_or_sync(kFull, ovf);
     if (lane == 0) {
@@ -310,6 +342,14 @@ uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nsw) {
   StepLayout L;
   L.make(n, (uint32_t)arcs, nsw);
   return L.total;
+}
+
+uint32_t mc_slots_within(uint32_t n, uint64_t arcs, uint32_t bytes) {
+  StepLayout L;
+  L.make(n, (uint32_t)arcs, 0);
+  if (L.off_slots > bytes) return 0u;
+  const uint32_t room = bytes - L.off_slots;
+  return room >= L.wide_bytes ? room / L.slot_bytes : 0u;
 }
 
 size_t mc_cta_scratch_bytes(uint32_t n) { return CtaScratch::bytes(n); }
@@ -363,7 +403,10 @@ template <int BLOCK>
 static cudaError_t launch_sssp_t(const McDev &P, uint32_t r, const int32_t *sources, int32_t nsrc,
                                  uint32_t nsw, uint32_t smem, uint32_t *dist, uint64_t *sigma,
                                  cudaStream_t stream) {
-  const uint32_t grid = (uint32_t)((nsrc + (int32_t)nsw - 1) / (int32_t)nsw);
+  StepLayout L;
+  L.make((uint32_t)P.n, (uint32_t)(2 * P.m), nsw);
+  const int32_t nw = (int32_t)L.wide_slots(nsw);
+  const uint32_t grid = (uint32_t)((nsrc + nw - 1) / nw);
   cudaFuncSetAttribute(debug_sssp_kernel<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   debug_sssp_kernel<BLOCK><<<grid, BLOCK, smem, stream>>>(P, r, sources, nsrc, nsw, dist, sigma);
   return cudaGetLastError();

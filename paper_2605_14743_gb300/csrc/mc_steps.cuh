@@ -18,11 +18,44 @@ namespace afc {
 // One source slot: dist[n] (u32 | kFlag once settled), sig[n] (sigma, then rho in place),
 // ord[n] (settle order; bit 15 marks the first node of a step) and plist[n] (the pending nodes:
 // discovered, not yet settled, each once).
+//
+// Narrow slots (NARROW = true, 14 bytes per node instead of 16) keep sigma in the low 32 bits
+// of v's 8-byte word and the pending list in the high halves (entries 2k and 2k + 1 in word k;
+// plist is unused): the forward pass needs sigma and the pending list, the backward pass only
+// rho, which then takes the whole word.  A path count above 2^32 - 1 cannot be stored there:
+// the routine reports it (ovf bit 1) and the caller redoes the realization with 64-bit slots.
 struct StepSlot {
   uint32_t *dist;
   uint64_t *sig;
   uint16_t *ord, *plist;
 };
+
+constexpr uint32_t kOvfWide = 2u;   // ovf bit: a path count does not fit a narrow slot
+
+template <bool NARROW>
+__device__ __forceinline__ uint16_t *pend_at(const StepSlot &sl, uint32_t j) {
+  if constexpr (NARROW)
+    return reinterpret_cast<uint16_t *>(sl.sig) + 4u * (j >> 1) + 2u + (j & 1u);
+  else
+    return sl.plist + j;
+}
+
+// sigma(v) during the forward pass (and of a node not yet given its rho in the backward pass)
+template <bool NARROW>
+__device__ __forceinline__ uint64_t sig_get(const StepSlot &sl, uint32_t v) {
+  if constexpr (NARROW)
+    return (uint64_t)reinterpret_cast<const uint32_t *>(sl.sig)[2u * v];
+  else
+    return sl.sig[v];
+}
+
+template <bool NARROW>
+__device__ __forceinline__ void sig_put(const StepSlot &sl, uint32_t v, uint64_t x) {
+  if constexpr (NARROW)
+    reinterpret_cast<uint32_t *>(sl.sig)[2u * v] = (uint32_t)x;
+  else
+    sl.sig[v] = x;
+}
 
 constexpr uint16_t kStepStart = 0x8000u;   // ord entry opens a step (node ids stay below 2^15)
 
@@ -62,9 +95,10 @@ constexpr int kPendCache = 8;
 // sigma(v) * sum over successors w of rho(w) in arc order; unique-path subtrees (sigma = 1
 // throughout) stay exact integers.  delta_s(v) for v != s goes to the exact accumulators of
 // the CTA scratch (fx_red).  Every lane of the warp must call it; err / ovf collect
-// device-error bits and path-count overflow per lane.
+// device-error bits and path-count overflow per lane (bit 0: above 2^64 - 1; bit 1, narrow
+// slots only: above 2^32 - 1, after which the backward pass is skipped).
 // ---------------------------------------------------------------------------------------
-template <typename DT>
+template <typename DT, bool NARROW = false>
 __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSlot &sl,
                              uint32_t s, bool want_delta, const BcAcc &cs, uint32_t &err,
                              uint32_t &ovf) {
@@ -73,8 +107,8 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
   __syncwarp();
   if (lane == 0) {
     sl.dist[s] = 0u;
-    sl.sig[s] = 1ull;
-    sl.plist[0] = (uint16_t)s;
+    sig_put<NARROW>(sl, s, 1ull);
+    *pend_at<NARROW>(sl, 0) = (uint16_t)s;
   }
   __syncwarp();
 
@@ -101,7 +135,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
           err |= kErrCapacity;
         }
       } else if (keep) {
-        sl.plist[kept + (uint32_t)__popc(km & below)] = (uint16_t)v;
+        *pend_at<NARROW>(sl, kept + (uint32_t)__popc(km & below)) = (uint16_t)v;
         ndmin = min(ndmin, d);
         nlout = min(nlout, d + m);
       }
@@ -114,7 +148,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
         const uint32_t j = (uint32_t)c * 32u + lane;
-        cv[c] = j < pc ? (uint32_t)sl.plist[j] : 0u;
+        cv[c] = j < pc ? (uint32_t)*pend_at<NARROW>(sl, j) : 0u;
       }
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
@@ -136,7 +170,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       const uint32_t j = j0 + lane;
       uint32_t v = 0, d = 0, m = 0;
       if (j < pc) {
-        v = sl.plist[j];
+        v = *pend_at<NARROW>(sl, j);
         d = sl.dist[v];
         m = mw[v];
       }
@@ -173,7 +207,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
           const uint32_t u = pk[t] & 0xFFFFu, len = pk[t] >> 16;
           // a predecessor: settled in an earlier step
           const bool pred = (du[t] & kFlag) && (du[t] & kMask) + len == dv && e + t < e1;
-          x[t] = pred ? sl.sig[u] : 0ull;
+          x[t] = pred ? sig_get<NARROW>(sl, u) : 0ull;
           const uint32_t nd = dv + len;
           const bool relax = !(du[t] & kFlag) && nd < du[t];
           old[t] = relax ? atomicMin(&sl.dist[u], nd) : 0u;
@@ -189,21 +223,25 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const unsigned long long nx = sg + x[t];
-          if (nx < sg) ovf = 1u;
+          if (!NARROW && nx < sg) ovf |= 1u;   // narrow addends are below 2^32: no wrap
           sg = nx;
           if ((dm[t] >> lane) & 1u)
-            sl.plist[pc + (uint32_t)__popc(dm[t] & lanemask_lt())] = (uint16_t)(pk[t] & 0xFFFFu);
+            *pend_at<NARROW>(sl, pc + (uint32_t)__popc(dm[t] & lanemask_lt())) =
+                (uint16_t)(pk[t] & 0xFFFFu);
           pc += (uint32_t)__popc(dm[t]);
         }
         e += 4;
       }
-      if (mine && v != s) sl.sig[v] = sg;
+      if (NARROW && (sg >> 32)) ovf |= kOvfWide;
+      if (mine && v != s) sig_put<NARROW>(sl, v, sg);
     }
     dmin = __reduce_min_sync(kFull, ndmin);
     lout = __reduce_min_sync(kFull, nlout);
     __syncwarp();
   }
   if (!want_delta) return true;
+  // a path count that a narrow slot cannot hold: the caller redoes the realization
+  if (NARROW && __any_sync(kFull, ovf & kOvfWide)) return true;
 
   // ---- backward: the steps in reverse order of settlement, one member per lane
   uint32_t hi = min(nord, n);
@@ -229,7 +267,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
         dv = sl.dist[v] & kMask;
         e = H.rp[v];
         e1 = H.rp[v + 1];
-        sg = sl.sig[v];
+        sg = sig_get<NARROW>(sl, v);
       }
       // the successors' rho in arc order: integral ones exactly, the others in DT
       uint32_t acc_i = 0;

@@ -89,7 +89,7 @@ struct CtaHead {
   unsigned long long edges, verts;
   uint32_t need_recheck, delta, dsh, wmax;
   uint32_t scan[32];
-  uint32_t scan_total, pad1, pad2, pad3;
+  uint32_t scan_total, wide_redo, pad2, pad3;   // wide_redo: a path count needs 64-bit slots
 };
 
 // The bucketed kernel's control block: the head plus its slot, team and warp tables.

@@ -13,8 +13,8 @@ from typing import Optional
 
 import numpy as np
 
-from . import (AFC_FP32_RECHECK, AFC_FP64, Chain, HostQuery, HostResult, McProblem, McStats,
-               PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
+from . import (AFC_FP32_RECHECK, AFC_FP64, MC_STATS_WORDS, Chain, HostQuery, HostResult,
+               McProblem, McStats, PerturbParams, afc_absorbing_solve, afc_csr_from_edges, afc_observed_states,
                afc_perturb_sweep, afc_run_host, afc_solve_workspace, afc_survival_threshold,
                afc_autotune, afc_bootstrap, afc_bootstrap_workspace, afc_feasibility,
                afc_rank_order, afc_robust_envelope, afc_robust_envelope_workspace,
@@ -180,7 +180,7 @@ class Query:
             self.prob.fallback_node = int(fallback_node)
             self.prob.fallback_count = self.fb_count.data_ptr()
         self.counts = torch.zeros((n, n + 1), dtype=torch.int32, device=device)
-        self.stats = torch.zeros(7, dtype=torch.int64, device=device)
+        self.stats = torch.zeros(MC_STATS_WORDS, dtype=torch.int64, device=device)
         wsb = afc_transition_counts_workspace(self.prob)
         self.ws_counts = torch.empty(max(wsb, 256), dtype=torch.uint8, device=device)
         self.c_index = torch.empty(n, dtype=torch.int32, device=device)

@@ -125,7 +125,7 @@ def test_mix_subsample_counts_vs_oracle():
     probs = (afc.McProblem * len(batch))(*[q.prob for q in qs])
     rc = np.full(len(batch), 4, np.uint32)
     ptrs = np.array([q.counts.data_ptr() for q in qs], np.uint64)
-    stats = torch.zeros((len(batch), 7), dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(batch), afc.MC_STATS_WORDS), dtype=torch.int64, device="cuda")
     wsb = afc.afc_transition_counts_batched_workspace(len(batch), probs, rc)
     ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
     afc.afc_transition_counts_batched(len(batch), probs, rc, ptrs, stats, ws, ws.numel(),

@@ -155,7 +155,7 @@ def test_batched_mix_across_paths():
     probs = (afc.McProblem * len(wls))(*[q.prob for q in qs])
     rc = np.array([w.realizations for w in wls], np.uint32)
     ptrs = np.array([q.counts.data_ptr() for q in qs], np.uint64)
-    stats = torch.zeros((len(wls), 7), dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(wls), afc.MC_STATS_WORDS), dtype=torch.int64, device="cuda")
     wsb = afc.afc_transition_counts_batched_workspace(len(wls), probs, rc)
     ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
     for q in qs:

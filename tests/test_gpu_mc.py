@@ -193,6 +193,46 @@ def test_sigma_overflow_reported():
     assert ovf and dev_ovf >= 1
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
+def test_path_counts_above_32_bits_redo_with_wide_slots(precision):
+    """The shared path's source slots hold 32-bit path counts.  On a 30 x 30 grid of unit
+    lengths the counts between far corners reach C(58, 29) ~ 3e16 > 2^32, so every realization
+    is redone with 64-bit slots (FP32 mode: then again in FP64 when the top-two gap is under the
+    margin): betweenness, next states and counts still match the oracle."""
+    eu, ev = grid_edges(30, 30)
+    R = 3
+    wl = Workload("grid", 900, eu, ev, 0.98, 1, 1, R, seed=3, precision=precision)
+    q = _dev(wl, memory_path=afc.AFC_PATH_SHARED)
+    assert afc.afc_counts_path(q.prob) == afc.AFC_PATH_SHARED
+    bc = torch.empty((R, wl.n), dtype=torch.float64, device="cuda")
+    nx = torch.empty((R, wl.n), dtype=torch.int32, device="cuda")
+    q.run_counts(0, R, dump_bc=bc, dump_next=nx)
+    torch.cuda.synchronize()
+    # FP64: betweenness within 1e-9; FP32 dependencies (no gap under the margin here): within
+    # the FP32 error, the reported nodes exact either way
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    for k in range(R):
+        _, _, _, _, obc, onx = oracle_realization(wl, k)
+        assert max_rel(bc[k].cpu().numpy(), obc) <= tol
+        assert (nx[k].cpu().numpy() == onx).all()
+    st = dict(zip([f[0] for f in afc.McStats._fields_], q.stats.cpu().numpy().tolist()))
+    assert st["wide_redone"] == R and st["overflow"] == 0 and st["device_error"] == 0
+    assert st["realizations"] == R
+    oc, _ = oracle_counts(wl, 0, R)
+    assert (q.counts.cpu().numpy().view(np.uint32) == oc).all()
+
+
+def test_path_counts_within_32_bits_keep_narrow_slots():
+    """The 1000-node Watts-Strogatz workload never needs 64-bit path counts: no realization is
+    redone."""
+    wl = variant(_ws1000(), realizations=8)
+    q = _dev(wl)
+    q.run_counts(0, 8)
+    torch.cuda.synchronize()
+    st = dict(zip([f[0] for f in afc.McStats._fields_], q.stats.cpu().numpy().tolist()))
+    assert st["realizations"] == 8 and st["wide_redone"] == 0
+
+
 # ------------------------------------------------------------------ A5 / A6 ----
 
 def _mc_check(wl, r_begin, r_count, **kw):
