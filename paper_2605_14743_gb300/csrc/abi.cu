@@ -182,7 +182,7 @@ struct McPlan {
   bool fits = true;
 };
 
-// Source slots (narrow: 32-bit path counts) that fit next to the realization of an (n, arcs)
+// Source slots (compact: 12 bytes per node) that fit next to the realization of an (n, arcs)
 // graph within `bytes` of shared memory, with room for at least one wide slot.
 uint32_t slots_within(uint32_t n, uint64_t arcs, uint32_t bytes) {
   return mc_slots_within(n, arcs, bytes);

@@ -52,7 +52,7 @@ afc_host_query host_query_of(const afc_graph *g, const afc_params *p, uint32_t n
 // Shared memory of a counting CTA of the shared-memory path: a graph of n nodes and `arcs`
 // arcs, and `nsw` warps that each own one source slot.
 uint32_t mc_layout_bytes(uint32_t n, uint64_t arcs, uint32_t nsw);
-// Narrow source slots that fit next to the realization within `bytes` (0 unless at least one
+// Compact source slots that fit next to the realization within `bytes` (0 unless at least one
 // wide slot fits).
 uint32_t mc_slots_within(uint32_t n, uint64_t arcs, uint32_t bytes);
 // Device memory of one counting CTA of the shared-memory path (graphs of up to n nodes):

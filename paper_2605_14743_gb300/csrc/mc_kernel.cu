@@ -25,10 +25,9 @@ namespace afc {
 // incident length) and the source slots.  What the source warps do not touch while they run
 // (components, the source list, selection scratch, betweenness accumulators) lives in the
 // CTA's region of device memory (CtaScratch), so that more source slots fit on chip.  The slot
-// region holds nsw narrow slots (14 bytes per node: 32-bit path counts, the pending list in
-// their words' high halves) and, reusing the same bytes, wide_slots() 16-byte slots (64-bit
-// path counts, separate pending list) for a realization whose path counts need them; it is
-// never smaller than one wide slot.
+// region holds nsw compact slots (12 bytes per node, see StepSlot) and, reusing the same bytes,
+// wide_slots() 16-byte slots for a realization with a length above kCompactMaxLen or a path
+// count above 2^32 - 1; it is never smaller than one wide slot.
 struct StepLayout {
   uint32_t off_rp, off_arc, off_mw, off_slots;
   uint32_t slot_bytes, wide_bytes, total;
@@ -39,12 +38,12 @@ struct StepLayout {
     off_arc = o;    o = al(o + 4u * (arcs > 0 ? arcs : 1));
     off_mw = o;     o = al(o + 2u * n);
     off_slots = o;
-    slot_bytes = al(4u * n) + al(8u * n) + al(2u * n);
-    wide_bytes = slot_bytes + al(2u * n);
+    slot_bytes = al(4u * n) + al(8u * n);
+    wide_bytes = slot_bytes + 2u * al(2u * n);
     const uint32_t region = nsw * slot_bytes;
     total = o + (nsw == 0 ? 0u : (region > wide_bytes ? region : wide_bytes));
   }
-  // wide slots in the region of nsw narrow ones (at least one)
+  // wide slots in the region of nsw compact ones (at least one)
   __host__ __device__ uint32_t wide_slots(uint32_t nsw) const {
     const uint32_t k = nsw * slot_bytes / wide_bytes;
     return k > 0 ? k : 1u;
@@ -54,7 +53,7 @@ struct StepLayout {
     StepSlot s;
     s.dist = reinterpret_cast<uint32_t *>(p);  p += al(4u * n);
     s.sig = reinterpret_cast<uint64_t *>(p);   p += al(8u * n);
-    s.ord = reinterpret_cast<uint16_t *>(p);   p += al(2u * n);
+    s.ord = wide ? reinterpret_cast<uint16_t *>(p) : nullptr;   p += al(2u * n);
     s.plist = wide ? reinterpret_cast<uint16_t *>(p) : nullptr;
     return s;
   }
@@ -168,10 +167,11 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
     __syncthreads();
     const uint32_t nsrc = ctl->nsrc;
 
-    // Attempts: narrow slots first; a path count above 2^32 - 1 redoes the realization with
-    // wide slots (fewer sources at a time), and in FP32 mode a top-two gap under the margin
-    // redoes it with FP64 dependencies.  Each can happen once: at most three attempts.
-    bool use32 = (P.precision == 1), wide = false;
+    // Attempts: compact slots first (wide ones from the start for a length above
+    // kCompactMaxLen); a path count above 2^32 - 1 redoes the realization with wide slots
+    // (fewer sources at a time), and in FP32 mode a top-two gap under the margin redoes it with
+    // FP64 dependencies.  Each can happen once: at most three attempts.
+    bool use32 = (P.precision == 1), wide = ctl->wmax > kCompactMaxLen;
     const StepSlot s0 = L.slot(smem, 0, n, false);
     for (int attempt = 0; attempt < 3; ++attempt) {
       if (attempt > 0) {
@@ -287,7 +287,7 @@ __global__ void debug_components_kernel(McDev P, int32_t *comp_out, int32_t *csi
 }
 
 // Distances and path counts of given sources from the production forward routine, on the
-// wide slots (64-bit path counts) of a layout of nsw narrow slots: warp w of CTA b handles
+// wide slots (64-bit path counts) of a layout of nsw compact slots: warp w of CTA b handles
 // source b * W + w of the list on realization r, W = the layout's wide slots.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1)

@@ -15,46 +15,88 @@
 
 namespace afc {
 
-// One source slot: dist[n] (u32 | kFlag once settled), sig[n] (sigma, then rho in place),
-// ord[n] (settle order; bit 15 marks the first node of a step) and plist[n] (the pending nodes:
-// discovered, not yet settled, each once).
+// One source slot, wide form (16 bytes per node): dist[n] (u32 | kFlag once settled), sig[n]
+// (sigma, then rho in place), ord[n] (settle order; bit 15 marks the first node of a step) and
+// plist[n] (the pending nodes: discovered, not yet settled, each once).
 //
-// Narrow slots (NARROW = true, 14 bytes per node instead of 16) keep sigma in the low 32 bits
-// of v's 8-byte word and the pending list in the high halves (entries 2k and 2k + 1 in word k;
-// plist is unused): the forward pass needs sigma and the pending list, the backward pass only
-// rho, which then takes the whole word.  A path count above 2^32 - 1 cannot be stored there:
-// the routine reports it (ovf bit 1) and the caller redoes the realization with 64-bit slots.
+// Compact form (COMPACT = true, 12 bytes per node): dist[n] and one 8-byte word per node,
+// word[v] = sigma(v) (32 bits) | plist entry v (16 bits) | ord entry v (16 bits); ord and plist
+// are not used.  The backward pass no longer needs sigma of a node once its rho is known, nor
+// the pending list, nor 32-bit distances: when the forward pass ends, each node's distance
+// mod 2^16 moves into its plist half, and rho(v) (64 bits) takes dist[v] (high half) and the
+// sigma half of word[v] (low half).  Distances mod 2^16 identify successors exactly when every
+// length is below 2^15 (adjacent nodes' distances differ by at most the arc's length), and
+// sigma must stay below 2^32: a realization outside either limit runs on wide slots (the
+// routine reports a path count above 2^32 - 1 as ovf bit 1 and the caller redoes the
+// realization).
 struct StepSlot {
   uint32_t *dist;
   uint64_t *sig;
   uint16_t *ord, *plist;
 };
 
-constexpr uint32_t kOvfWide = 2u;   // ovf bit: a path count does not fit a narrow slot
+constexpr uint32_t kOvfWide = 2u;          // ovf bit: a path count does not fit a compact slot
+constexpr uint32_t kCompactMaxLen = 32767;  // longest length a compact slot supports
 
-template <bool NARROW>
+template <bool COMPACT>
 __device__ __forceinline__ uint16_t *pend_at(const StepSlot &sl, uint32_t j) {
-  if constexpr (NARROW)
-    return reinterpret_cast<uint16_t *>(sl.sig) + 4u * (j >> 1) + 2u + (j & 1u);
+  if constexpr (COMPACT)
+    return reinterpret_cast<uint16_t *>(sl.sig) + 4u * j + 2u;
   else
     return sl.plist + j;
 }
 
+template <bool COMPACT>
+__device__ __forceinline__ uint16_t *ord_at(const StepSlot &sl, uint32_t k) {
+  if constexpr (COMPACT)
+    return reinterpret_cast<uint16_t *>(sl.sig) + 4u * k + 3u;
+  else
+    return sl.ord + k;
+}
+
 // sigma(v) during the forward pass (and of a node not yet given its rho in the backward pass)
-template <bool NARROW>
+template <bool COMPACT>
 __device__ __forceinline__ uint64_t sig_get(const StepSlot &sl, uint32_t v) {
-  if constexpr (NARROW)
+  if constexpr (COMPACT)
     return (uint64_t)reinterpret_cast<const uint32_t *>(sl.sig)[2u * v];
   else
     return sl.sig[v];
 }
 
-template <bool NARROW>
+template <bool COMPACT>
 __device__ __forceinline__ void sig_put(const StepSlot &sl, uint32_t v, uint64_t x) {
-  if constexpr (NARROW)
+  if constexpr (COMPACT)
     reinterpret_cast<uint32_t *>(sl.sig)[2u * v] = (uint32_t)x;
   else
     sl.sig[v] = x;
+}
+
+// rho(v) in the backward pass (kIntTag | integer, or the bits of a DT)
+template <bool COMPACT>
+__device__ __forceinline__ uint64_t rho_get(const StepSlot &sl, uint32_t v) {
+  if constexpr (COMPACT)
+    return ((uint64_t)sl.dist[v] << 32) | reinterpret_cast<const uint32_t *>(sl.sig)[2u * v];
+  else
+    return sl.sig[v];
+}
+
+template <bool COMPACT>
+__device__ __forceinline__ void rho_put(const StepSlot &sl, uint32_t v, uint64_t x) {
+  if constexpr (COMPACT) {
+    sl.dist[v] = (uint32_t)(x >> 32);
+    reinterpret_cast<uint32_t *>(sl.sig)[2u * v] = (uint32_t)x;
+  } else {
+    sl.sig[v] = x;
+  }
+}
+
+// Distance of a settled node in the backward pass: exact (wide) or mod 2^16 (compact).
+template <bool COMPACT>
+__device__ __forceinline__ uint32_t bdist(const StepSlot &sl, uint32_t v) {
+  if constexpr (COMPACT)
+    return reinterpret_cast<const uint16_t *>(sl.sig)[4u * v + 2u];
+  else
+    return sl.dist[v] & kMask;
 }
 
 constexpr uint16_t kStepStart = 0x8000u;   // ord entry opens a step (node ids stay below 2^15)
@@ -83,6 +125,8 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
 
 // Pending-list windows (32 nodes each) loaded together at the start of a step's selection.
 constexpr int kPendCache = 8;
+// Arcs of a lane's node whose loads (and relaxations) are issued together, forward and backward.
+constexpr int kArcsFwd = 4, kArcsBwd = 4;
 
 // ---------------------------------------------------------------------------------------
 // Brandes from source s by one warp (Sec. 3.1 definitions: d_H, sigma_st, ordered-pair
@@ -95,10 +139,11 @@ constexpr int kPendCache = 8;
 // sigma(v) * sum over successors w of rho(w) in arc order; unique-path subtrees (sigma = 1
 // throughout) stay exact integers.  delta_s(v) for v != s goes to the exact accumulators of
 // the CTA scratch (fx_red).  Every lane of the warp must call it; err / ovf collect
-// device-error bits and path-count overflow per lane (bit 0: above 2^64 - 1; bit 1, narrow
-// slots only: above 2^32 - 1, after which the backward pass is skipped).
+// device-error bits and path-count overflow per lane (bit 0: above 2^64 - 1; bit 1, compact
+// slots only: above 2^32 - 1, after which the backward pass is skipped).  Compact slots need
+// every length below 2^15 (kCompactMaxLen).
 // ---------------------------------------------------------------------------------------
-template <typename DT, bool NARROW = false>
+template <typename DT, bool COMPACT = false>
 __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSlot &sl,
                              uint32_t s, bool want_delta, const BcAcc &cs, uint32_t &err,
                              uint32_t &ovf) {
@@ -107,8 +152,8 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
   __syncwarp();
   if (lane == 0) {
     sl.dist[s] = 0u;
-    sig_put<NARROW>(sl, s, 1ull);
-    *pend_at<NARROW>(sl, 0) = (uint16_t)s;
+    sig_put<COMPACT>(sl, s, 1ull);
+    *pend_at<COMPACT>(sl, 0) = (uint16_t)s;
   }
   __syncwarp();
 
@@ -129,13 +174,13 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       if (sel) {
         const uint32_t pos = nord + (uint32_t)__popc(sm & below);
         if (pos < n) {
-          sl.ord[pos] = (uint16_t)(v | (pos == g0 ? kStepStart : 0u));
+          *ord_at<COMPACT>(sl, pos) = (uint16_t)(v | (pos == g0 ? kStepStart : 0u));
           sl.dist[v] = d | kFlag;
         } else {
           err |= kErrCapacity;
         }
       } else if (keep) {
-        *pend_at<NARROW>(sl, kept + (uint32_t)__popc(km & below)) = (uint16_t)v;
+        *pend_at<COMPACT>(sl, kept + (uint32_t)__popc(km & below)) = (uint16_t)v;
         ndmin = min(ndmin, d);
         nlout = min(nlout, d + m);
       }
@@ -148,7 +193,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
         const uint32_t j = (uint32_t)c * 32u + lane;
-        cv[c] = j < pc ? (uint32_t)*pend_at<NARROW>(sl, j) : 0u;
+        cv[c] = j < pc ? (uint32_t)*pend_at<COMPACT>(sl, j) : 0u;
       }
 #pragma unroll
       for (int c = 0; c < kPendCache; ++c) {
@@ -170,7 +215,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       const uint32_t j = j0 + lane;
       uint32_t v = 0, d = 0, m = 0;
       if (j < pc) {
-        v = *pend_at<NARROW>(sl, j);
+        v = *pend_at<COMPACT>(sl, j);
         d = sl.dist[v];
         m = mw[v];
       }
@@ -182,32 +227,32 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
     pc = kept;
     __syncwarp();
     // (3) the step's arcs, one member per lane: sigma from the (settled) predecessors and
-    // relaxation of the rest; each group of four arcs issues its loads and atomics together
+    // relaxation of the rest; each group of kArcsFwd arcs issues its loads and atomics together
     const uint32_t g1 = min(nord, n);
     for (uint32_t c0 = g0; c0 < g1; c0 += 32) {
       const uint32_t k = c0 + lane;
       const bool mine = k < g1;
       uint32_t v = 0, dv = 0, e = 0, e1 = 0;
       if (mine) {
-        v = sl.ord[k] & 0x7FFFu;
+        v = *ord_at<COMPACT>(sl, k) & 0x7FFFu;
         dv = sl.dist[v] & kMask;
         e = H.rp[v];
         e1 = H.rp[v + 1];
       }
       unsigned long long sg = 0;
       while (__any_sync(kFull, e < e1)) {
-        uint32_t pk[4], du[4], old[4];
-        unsigned long long x[4];
+        uint32_t pk[kArcsFwd], du[kArcsFwd], old[kArcsFwd];
+        unsigned long long x[kArcsFwd];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
+        for (int t = 0; t < kArcsFwd; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) du[t] = e + t < e1 ? sl.dist[pk[t] & 0xFFFFu] : kFlag;
+        for (int t = 0; t < kArcsFwd; ++t) du[t] = e + t < e1 ? sl.dist[pk[t] & 0xFFFFu] : kFlag;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kArcsFwd; ++t) {
           const uint32_t u = pk[t] & 0xFFFFu, len = pk[t] >> 16;
           // a predecessor: settled in an earlier step
           const bool pred = (du[t] & kFlag) && (du[t] & kMask) + len == dv && e + t < e1;
-          x[t] = pred ? sig_get<NARROW>(sl, u) : 0ull;
+          x[t] = pred ? sig_get<COMPACT>(sl, u) : 0ull;
           const uint32_t nd = dv + len;
           const bool relax = !(du[t] & kFlag) && nd < du[t];
           old[t] = relax ? atomicMin(&sl.dist[u], nd) : 0u;
@@ -217,31 +262,38 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
           }
         }
         // discovered now (each node once): onto the pending list
-        uint32_t dm[4];
+        uint32_t dm[kArcsFwd];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) dm[t] = __ballot_sync(kFull, old[t] == kInf);
+        for (int t = 0; t < kArcsFwd; ++t) dm[t] = __ballot_sync(kFull, old[t] == kInf);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kArcsFwd; ++t) {
           const unsigned long long nx = sg + x[t];
-          if (!NARROW && nx < sg) ovf |= 1u;   // narrow addends are below 2^32: no wrap
+          if (!COMPACT && nx < sg) ovf |= 1u;   // compact addends are below 2^32: no wrap
           sg = nx;
           if ((dm[t] >> lane) & 1u)
-            *pend_at<NARROW>(sl, pc + (uint32_t)__popc(dm[t] & lanemask_lt())) =
+            *pend_at<COMPACT>(sl, pc + (uint32_t)__popc(dm[t] & lanemask_lt())) =
                 (uint16_t)(pk[t] & 0xFFFFu);
           pc += (uint32_t)__popc(dm[t]);
         }
-        e += 4;
+        e += kArcsFwd;
       }
-      if (NARROW && (sg >> 32)) ovf |= kOvfWide;
-      if (mine && v != s) sig_put<NARROW>(sl, v, sg);
+      if (COMPACT && (sg >> 32)) ovf |= kOvfWide;
+      if (mine && v != s) sig_put<COMPACT>(sl, v, sg);
     }
     dmin = __reduce_min_sync(kFull, ndmin);
     lout = __reduce_min_sync(kFull, nlout);
     __syncwarp();
   }
   if (!want_delta) return true;
-  // a path count that a narrow slot cannot hold: the caller redoes the realization
-  if (NARROW && __any_sync(kFull, ovf & kOvfWide)) return true;
+  if constexpr (COMPACT) {
+    // a path count that a compact slot cannot hold: the caller redoes the realization
+    if (__any_sync(kFull, ovf & kOvfWide)) return true;
+    // distances mod 2^16 into the (now empty) pending-list halves; every node the backward
+    // pass reads was reached (settled nodes and their neighbours)
+    uint16_t *w16 = reinterpret_cast<uint16_t *>(sl.sig);
+    for (uint32_t v = lane; v < n; v += 32) w16[4u * v + 2u] = (uint16_t)sl.dist[v];
+    __syncwarp();
+  }
 
   // ---- backward: the steps in reverse order of settlement, one member per lane
   uint32_t hi = min(nord, n);
@@ -250,7 +302,7 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
     uint32_t lo = 0;
     for (int32_t top = (int32_t)hi - 1; top >= 0; top -= 32) {
       const int32_t p = top - (int32_t)lane;
-      const bool mark = p >= 0 && (sl.ord[p] & kStepStart);
+      const bool mark = p >= 0 && (*ord_at<COMPACT>(sl, (uint32_t)p) & kStepStart);
       const uint32_t mm = __ballot_sync(kFull, mark);
       if (mm) {
         lo = (uint32_t)(top - (__ffs(mm) - 1));
@@ -263,28 +315,29 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
       uint32_t v = 0, dv = 0, e = 0, e1 = 0;
       uint64_t sg = 0;
       if (mine) {
-        v = sl.ord[k] & 0x7FFFu;
-        dv = sl.dist[v] & kMask;
+        v = *ord_at<COMPACT>(sl, k) & 0x7FFFu;
+        dv = bdist<COMPACT>(sl, v);
         e = H.rp[v];
         e1 = H.rp[v + 1];
-        sg = sig_get<NARROW>(sl, v);
+        sg = sig_get<COMPACT>(sl, v);
       }
       // the successors' rho in arc order: integral ones exactly, the others in DT
       uint32_t acc_i = 0;
       DT acc_f = 0;
       bool any_f = false;
       while (__any_sync(kFull, e < e1)) {
-        uint32_t pk[4];
-        uint64_t rw[4];
+        uint32_t pk[kArcsBwd];
+        uint64_t rw[kArcsBwd];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
+        for (int t = 0; t < kArcsBwd; ++t) pk[t] = e + t < e1 ? H.arc[e + t] : 0u;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const bool suc = e + t < e1 && (sl.dist[pk[t] & 0xFFFFu] & kMask) == dv + (pk[t] >> 16);
-          rw[t] = suc ? sl.sig[pk[t] & 0xFFFFu] : kIntTag;   // kIntTag alone adds 0
+        for (int t = 0; t < kArcsBwd; ++t) {
+          const uint32_t w = pk[t] & 0xFFFFu, want = dv + (pk[t] >> 16);
+          const bool suc = e + t < e1 && bdist<COMPACT>(sl, w) == (COMPACT ? want & 0xFFFFu : want);
+          rw[t] = suc ? rho_get<COMPACT>(sl, w) : kIntTag;   // kIntTag alone adds 0
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int t = 0; t < kArcsBwd; ++t) {
           if (rw[t] & kIntTag) {
             acc_i += (uint32_t)rw[t];
           } else {
@@ -292,19 +345,19 @@ __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSl
             any_f = true;
           }
         }
-        e += 4;
+        e += kArcsBwd;
       }
       if (mine) {
         if (sg == 1ull && !any_f) {
           // delta(v) = sum of the successors' subtree sizes: exact in integers
-          sl.sig[v] = kIntTag | (uint64_t)(1u + acc_i);
+          rho_put<COMPACT>(sl, v, kIntTag | (uint64_t)(1u + acc_i));
           if (v != s && acc_i) atomicAdd(&cs.a0[v], (unsigned long long)acc_i);
         } else {
           DT dep, rho;
           dependency<DT>(sg, (DT)acc_i + acc_f, dep, rho);
           uint64_t bits = 0;
           *reinterpret_cast<DT *>(&bits) = rho;
-          sl.sig[v] = bits;
+          rho_put<COMPACT>(sl, v, bits);
           if (v != s) fx_red(cs.a0, cs.a1, cs.a2, v, (double)dep);
         }
       }

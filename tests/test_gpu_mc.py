@@ -222,7 +222,7 @@ def test_path_counts_above_32_bits_redo_with_wide_slots(precision):
     assert (q.counts.cpu().numpy().view(np.uint32) == oc).all()
 
 
-def test_path_counts_within_32_bits_keep_narrow_slots():
+def test_path_counts_within_32_bits_keep_compact_slots():
     """The 1000-node Watts-Strogatz workload never needs 64-bit path counts: no realization is
     redone."""
     wl = variant(_ws1000(), realizations=8)
@@ -231,6 +231,17 @@ def test_path_counts_within_32_bits_keep_narrow_slots():
     torch.cuda.synchronize()
     st = dict(zip([f[0] for f in afc.McStats._fields_], q.stats.cpu().numpy().tolist()))
     assert st["realizations"] == 8 and st["wide_redone"] == 0
+
+
+@pytest.mark.parametrize("w_hi", [32767, 65535])
+def test_lengths_at_and_above_the_compact_slot_limit(w_hi):
+    """Compact source slots identify successors by distances mod 2^16, exact for lengths below
+    2^15: lengths up to 32767 run on them (distances far above 2^16, differences at the limit),
+    a realization with a longer length runs on wide slots from the start.  Both match the
+    oracle."""
+    eu, ev = er_edges(60, 0.1, 5)
+    wl = Workload("er60_long", 60, eu, ev, 0.95, 1, w_hi, 12, seed=9, k_min=3)
+    _mc_check(wl, 0, 12, memory_path=afc.AFC_PATH_SHARED)
 
 
 # ------------------------------------------------------------------ A5 / A6 ----
