@@ -45,7 +45,7 @@ extern "C" {
 #define AFC_FP32_RECHECK 1  /* delta in FP32, realizations with a near-tied top two in FP64 */
 
 #define AFC_PATH_AUTO 0     /* counting path chosen by what fits in shared memory            */
-                            /* (and, with automatic teams, holds at least four of them)      */
+                            /* (a CTA must hold at least six source slots)                   */
 #define AFC_PATH_SHARED 1   /* realization and source state in shared memory (small graphs)  */
 #define AFC_PATH_GLOBAL 2   /* realized graph and source state in device memory (any size)   */
 
@@ -110,11 +110,11 @@ typedef struct {
                              /* each team advances its own batch of sources; 0 = auto      */
   int32_t slots_per_team;    /* sources a team advances in lockstep (1..16); 0 = as many   */
                              /* as shared memory holds                                     */
-  int32_t memory_path;       /* AFC_PATH_AUTO: realizations of graphs whose per-CTA state  */
-                             /* fits in shared memory run there (with team_threads 0: only */
-                             /* if it holds at least four teams per CTA), others on the    */
-                             /* global-memory path; AFC_PATH_SHARED / AFC_PATH_GLOBAL force */
-                             /* one (AFC_EUNSUPPORTED if the shared path does not fit)      */
+  int32_t memory_path;       /* AFC_PATH_AUTO: realizations of graphs whose CTA holds the  */
+                             /* realization and at least six source slots in shared memory */
+                             /* run there, others on the global-memory path;               */
+                             /* AFC_PATH_SHARED / AFC_PATH_GLOBAL force one                 */
+                             /* (AFC_EUNSUPPORTED if the shared path does not fit)          */
   /* Simulator-level rewards (Sec. 6) and rank-r reports.  The ordering pi of a valid        */
   /* component K repeats the centre rule on the nodes of K not yet listed (B* over the rest, */
   /* the tie_rel band, smallest id), so pi(1) is the centre (Sec. 2.3 eq. topk-comp).        */

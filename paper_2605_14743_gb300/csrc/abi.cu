@@ -329,10 +329,11 @@ bool smem_fits(const afc_mc_problem &p) {
   return plan_for(p, (uint32_t)p.n, 2ull * (uint64_t)p.m, 1).fits;
 }
 
-// AFC_PATH_AUTO: the shared-memory path when shared memory holds at least this many source
-// slots.  Measured on the mix (mean degree 8): with 10 slots (1,132 nodes) it is 7% faster
-// than the global path's settle-step kernel, with 5 slots (1,771 nodes) 1.5x slower.
-constexpr uint32_t kMinSharedSlots = 8;
+// AFC_PATH_AUTO: the shared-memory path when shared memory holds at least this many compact
+// source slots.  Measured on mix graphs (mean degree 8, FP64): with 7 slots (1,771 nodes) it
+// is 7% faster than the global path's settle-step kernel, with 6 slots (2,014 nodes) 3%
+// faster, with 5 slots (2,161-2,340 nodes) 7-8% slower.
+constexpr uint32_t kMinSharedSlots = 6;
 
 bool wants_global(const afc_mc_problem &p) {
   if (p.memory_path == AFC_PATH_GLOBAL) return true;

@@ -188,8 +188,9 @@ big_steps_kernel(const McDev *__restrict__ Pd, BigGroup *groups, uint32_t ngroup
       k = __shfl_sync(kFull, k, 0);
       if (k >= nsrc) break;
       const uint32_t s = G.src[k];
-      const bool ok = mode == 1 ? source_steps<float>(H, G.mw, sl, s, true, acc, err, ovf)
-                                : source_steps<double>(H, G.mw, sl, s, true, acc, err, ovf);
+      const bool ok =
+          mode == 1 ? source_steps<float, false, false>(H, G.mw, sl, s, true, acc, err, ovf)
+                    : source_steps<double, false, false>(H, G.mw, sl, s, true, acc, err, ovf);
       if (!ok) break;
     }
     err = __reduce_or_sync(kFull, err);
@@ -277,7 +278,8 @@ cudaError_t launch_steps_t(const McDev *Pd, BigGroup *groups, uint32_t ngroups,
 }
 
 // team 0: the settle-step kernel with spt source warps per CTA (slots_on_chip: their distance
-// arrays in shared memory); otherwise the bucketed kernel with teams of `team` threads
+// arrays in shared memory) in CTAs of 256 or 512 threads (1024 would cap the registers below
+// what the routine needs); otherwise the bucketed kernel with teams of `team` threads
 cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *groups,
                            uint32_t ngroups, unsigned char *arena, size_t stride, uint32_t spt,
                            int mode, uint32_t smem_bytes, int slots_on_chip, uint32_t grid,
@@ -290,9 +292,6 @@ cudaError_t launch_brandes(int block, int team, const McDev *Pd, BigGroup *group
     if (block == 512)
       return launch_steps_t<512>(Pd, groups, ngroups, arena, stride, spt, mode, smem_bytes,
                                  slots_on_chip, grid, stream);
-    if (block == 1024)
-      return launch_steps_t<1024>(Pd, groups, ngroups, arena, stride, spt, mode, smem_bytes,
-                                  slots_on_chip, grid, stream);
     return cudaErrorInvalidValue;
   }
 #define AFC_X(B, T)                                                                   \

@@ -195,11 +195,11 @@ mc_counts_kernel(const McDev *__restrict__ probs, int nprob, const uint64_t *ite
           const BcAcc acc{cs.a0, cs.a1, cs.a2};
           bool ok;
           if (wide)
-            ok = use32 ? source_steps<float, false>(H, mw, sl, s, true, acc, err, ovf)
-                       : source_steps<double, false>(H, mw, sl, s, true, acc, err, ovf);
+            ok = use32 ? source_steps<float, false, true>(H, mw, sl, s, true, acc, err, ovf)
+                       : source_steps<double, false, true>(H, mw, sl, s, true, acc, err, ovf);
           else
-            ok = use32 ? source_steps<float, true>(H, mw, sl, s, true, acc, err, ovf)
-                       : source_steps<double, true>(H, mw, sl, s, true, acc, err, ovf);
+            ok = use32 ? source_steps<float, true, true>(H, mw, sl, s, true, acc, err, ovf)
+                       : source_steps<double, true, true>(H, mw, sl, s, true, acc, err, ovf);
           if (!ok) break;
           if (__any_sync(kFull, ovf & kOvfWide)) {
             if (lane == 0) atomicOr(&ctl->wide_redo, 1u);
@@ -314,7 +314,7 @@ debug_sssp_kernel(McDev P, uint32_t r, const int32_t *sources, int32_t nsrc, uin
     const uint32_t s = (sv >= 0 && (uint32_t)sv < n) ? (uint32_t)sv : 0u;
     const StepSlot sl = L.slot(smem, warp, n, true);   // wide slots: 64-bit path counts
     uint32_t err = 0, ovf = 0;
-    source_steps<double, false>(H, mw, sl, s, false, BcAcc{}, err, ovf);
+    source_steps<double, false, true>(H, mw, sl, s, false, BcAcc{}, err, ovf);
     err = __reduce_or_sync(kFull, err);
     ovf = __reduce_or_sync(kFull, ovf);
     if (lane == 0) {

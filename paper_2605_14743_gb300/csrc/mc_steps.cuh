@@ -123,10 +123,14 @@ __device__ __forceinline__ uint32_t warp_excl(uint32_t x, uint32_t &total) {
   return incl - x;
 }
 
-// Pending-list windows (32 nodes each) loaded together at the start of a step's selection.
-constexpr int kPendCache = 8;
-// Arcs of a lane's node whose loads (and relaxations) are issued together, forward and backward.
-constexpr int kArcsFwd = 4, kArcsBwd = 4;
+// Issue widths of the routine, by where the source slot lives (measured on ws1000 for slots in
+// shared memory, on the batched mix's 2,300-3,800-node graphs for slots in the device arena):
+// pend: pending-list windows (32 nodes each) loaded together at the start of a step's
+// selection; fwd / bwd: arcs of a lane's node whose loads (and relaxations) are issued
+// together in the forward / backward pass.
+template <bool ONCHIP> struct StepTune;
+template <> struct StepTune<true> { static constexpr int pend = 6, fwd = 4, bwd = 2; };
+template <> struct StepTune<false> { static constexpr int pend = 16, fwd = 4, bwd = 8; };
 
 // ---------------------------------------------------------------------------------------
 // Brandes from source s by one warp (Sec. 3.1 definitions: d_H, sigma_st, ordered-pair
@@ -143,10 +147,13 @@ constexpr int kArcsFwd = 4, kArcsBwd = 4;
 // slots only: above 2^32 - 1, after which the backward pass is skipped).  Compact slots need
 // every length below 2^15 (kCompactMaxLen).
 // ---------------------------------------------------------------------------------------
-template <typename DT, bool COMPACT = false>
+template <typename DT, bool COMPACT, bool ONCHIP>
 __device__ bool source_steps(const Realized &H, const uint16_t *mw, const StepSlot &sl,
                              uint32_t s, bool want_delta, const BcAcc &cs, uint32_t &err,
                              uint32_t &ovf) {
+  constexpr int kPendCache = StepTune<ONCHIP>::pend, kArcsFwd = StepTune<ONCHIP>::fwd,
+                kArcsBwd = StepTune<ONCHIP>::bwd;
+  static_assert(!COMPACT || ONCHIP, "compact slots live in shared memory");
   const uint32_t n = H.n, lane = lane_id();
   for (uint32_t v = lane; v < n; v += 32) sl.dist[v] = kInf;
   __syncwarp();

@@ -138,7 +138,7 @@ def test_shared_path_rejects_graph_that_does_not_fit():
 
 
 def test_auto_path_3000_nodes():
-    """A graph whose shared-memory CTA would hold fewer than four source slots runs on the
+    """A graph whose shared-memory CTA would hold fewer than six source slots runs on the
     global path by itself."""
     q = afc.Query(_ws3000())
     assert afc.afc_counts_path(q.prob) == GLOBAL
