@@ -252,9 +252,14 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
     const uint32_t per_sm = std::max<uint32_t>(
         1u, std::min<uint32_t>(2048u / (uint32_t)b.block, (228u * 1024u) / (b.smem + 1024u)));
     b.grid = (uint32_t)std::max(1, d.sms) * per_sm;
-    const uint64_t want = ((uint64_t)4 * b.grid * b.spt + n - 1) / n;
+    // realizations in flight: enough for about 64 sources per warp of the grid (at most 128),
+    // since warps that run out of sources idle until the batch ends; measured on the mix's
+    // 2,306 / 3,164 / 3,818-node graphs (realizations/s): about 4 sources per warp 863 / 394 /
+    // 252, 8: 894 / 423 / 271, 16: 928 / 439 / 282, 32: 947 / 448 / 289, 64: 954 / 452 / 293,
+    // 128 (at most 256 groups): 960 / 456 / 294
+    const uint64_t want = ((uint64_t)64 * b.grid * b.spt + n - 1) / n;
     b.ngroups = (uint32_t)std::max<uint64_t>(
-        1, std::min<uint64_t>({std::max<uint64_t>(want, 2), 64, std::max<uint64_t>(r_count, 1)}));
+        1, std::min<uint64_t>({std::max<uint64_t>(want, 2), 128, std::max<uint64_t>(r_count, 1)}));
     b.group_bytes = big_group_bytes(n, arcs);
     size_t o = 0;
     b.off_groups = o; o += (sizeof(BigGroup) * b.ngroups + 255) & ~size_t(255);
