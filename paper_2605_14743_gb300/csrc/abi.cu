@@ -219,8 +219,24 @@ McPlan plan_for(const afc_mc_problem &p0, uint32_t nmax, uint64_t amax, uint64_t
 }
 
 // The global path's settle-step kernel when shared memory holds the distance arrays of at
-// least this many warps (about 14,000 nodes); beyond, the bucketed kernel with large teams.
+// least this many warps (about 14,000 nodes) and steps_beat_buckets; otherwise the bucketed
+// kernel.
 constexpr uint32_t kMinStepWarps = 4;
+
+// Whether the settle-step kernel outruns the bucketed one on this graph.  Its cost grows with
+// the range of lengths (a wider range settles fewer nodes per step against a pending list of
+// about the same length), the bucketed kernel's does not.  Measured on WS graphs of mean
+// degree 8 (k = 8, beta = 0.2, survival 0.9), lengths uniform in 1..W, realizations/s of the
+// settle-step kernel over the better bucketed team size: n = 2,500: W = 25 2.43x, 50 1.91x,
+// 100 1.51x, 400 1.29x; n = 3,200: 2.07x, 1.59x, 1.19x, 0.98x; n = 3,818: 1.89x, 1.45x, 1.07x,
+// 0.85x; n = 4,000: 1.73x, 1.31x, 0.96x, 0.75x; W = 100: n = 5,000 0.75x, 7,000 0.53x, 10,000
+// 0.30x.  The ratio goes about as n^-1.17 and min(W, 200)^-0.35, which puts the crossover at
+// n min(W, 200)^0.35 = 19,500 (n = 6,400 for W = 25, 5,000 for W = 50, 3,900 for W = 100,
+// 3,050 for W >= 200).  Per-edge length ranges and length laws count as W = 65,535.
+bool steps_beat_buckets(const afc_mc_problem &p) {
+  const double w = (p.w_hi || p.wtab_ptr) ? 65535.0 : (double)std::max<uint32_t>(p.w_hi_all, 1u);
+  return (double)p.n * std::pow(std::min(w, 200.0), 0.35) <= 19500.0;
+}
 
 // Launch plan of the global-memory path for one problem.
 struct BigPlan {
@@ -239,7 +255,7 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   const uint64_t arcs = 2ull * (uint64_t)p.m;
   const uint32_t per_warp = (4u * n + 15u) & ~15u;   // one distance array
   const uint32_t fit = (uint32_t)std::max(0, d.smem_optin - 1024) / per_warp;
-  if (p.team_threads == 0 && fit >= kMinStepWarps) {
+  if (p.team_threads == 0 && fit >= kMinStepWarps && steps_beat_buckets(p)) {
     // settle-step kernel: one source per warp, its distances on chip (16 warps per CTA at most:
     // 1024-thread CTAs would cap the registers below what the routine needs)
     b.team = 0;
@@ -273,21 +289,26 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   if (p.team_threads) {
     b.team = p.team_threads;
   } else {
-    // measured on ER and WS graphs of mean degree 8 (n = 1,000 .. 6,000) and on the
+    // measured on ER and WS graphs of mean degree 8 (n = 1,000 .. 10,000) and on the
     // 20,000-node workload: up to about 4,000 nodes, teams of 128 threads (8 sources in flight
     // per CTA), except where only four whole slots fit in shared memory: then four teams of 256
     // with their slots on chip (+7% at n = 1,800, +10-14% at n = 3,200 over teams of 128 with
-    // only their distances on chip); beyond, teams of 512 whose two slots keep at least their
-    // distance arrays in shared memory (7.1 realizations/s on the 20,000-node workload, against
-    // 6.2 with four teams of 256 and distances in device memory), or 256 when two such arrays
-    // do not fit
+    // only their distances on chip); teams of 128 up to 6,000 nodes (realizations/s, 128 / 256
+    // threads: n = 4,600 156 / 143, n = 5,000 132 / 124); then teams of 256 while four distance
+    // arrays fit on chip (n = 7,000: 67 against 58 with 128 and 58 with 512; n = 10,000: 36
+    // against 28 and 30); beyond, teams of 512 whose two slots keep at least their distance
+    // arrays in shared memory (7.1 realizations/s on the 20,000-node workload, against 6.2 with
+    // four teams of 256 and distances in device memory), or 256 when two such arrays do not fit
     if (n <= 4096) {
       const bool eight = (int)big_slots_smem_bytes(n, 8u) + 1024 <= d.smem_optin;
       const bool four = (int)big_slots_smem_bytes(n, 4u) + 1024 <= d.smem_optin;
       b.team = (b.block == 1024 && !eight && four) ? 256 : 128;
+    } else if (n <= 6000) {
+      b.team = 128;
     } else {
+      const bool four_fit = (int)big_dist_smem_bytes(n, 4u) + 1024 <= d.smem_optin;
       const bool two_fit = (int)big_dist_smem_bytes(n, 2u) + 1024 <= d.smem_optin;
-      b.team = (b.block >= 1024 && two_fit) ? 512 : 256;
+      b.team = (b.block >= 1024 && !four_fit && two_fit) ? 512 : 256;
     }
     b.team = std::min(b.block, b.team);
     if (!big_config_supported(b.block, b.team)) b.team = b.block;
