@@ -332,8 +332,11 @@ BigPlan plan_big(const afc_mc_problem &p, uint64_t r_count) {
   const uint32_t per_sm = std::max<uint32_t>(
       1u, std::min<uint32_t>((uint32_t)std::max(1, 1024 / b.block), (228u * 1024u) / (smem_cta + 1024u)));
   b.grid = (uint32_t)std::max(1, d.sms) * per_sm;
-  // realizations in flight: enough sources for every team a few times over
-  const uint64_t want = ((uint64_t)4 * b.grid * nt * b.spt + n - 1) / n;
+  // realizations in flight: about 64 sources for every team (at most 64 realizations), since
+  // teams that run out of sources idle until the batch ends; measured with lengths 1..100
+  // (realizations/s, about 4 / 16 / 64 sources per team): n = 5,000 131 / 141 / 148, n = 7,000
+  // 67 / 67 / 69, n = 10,000 35.9 / 35.9 / 36.6
+  const uint64_t want = ((uint64_t)64 * b.grid * nt * b.spt + n - 1) / n;
   b.ngroups = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>({std::max<uint64_t>(want, 2), 64,
                                                                    std::max<uint64_t>(r_count, 1)}));
   b.group_bytes = big_group_bytes(n, arcs);
