@@ -50,12 +50,44 @@ KERNEL_SOURCES = ["mc_common.cuh", "mc_steps.cuh", "mc_kernel.cu", "mc_types.h",
                   "afc_device.cuh"]
 
 
-def kernel_source_hash() -> str:
+def _code_only(text: str) -> str:
+    """A CUDA/C++ source without its // and /* */ comments and with blank space collapsed, so
+    that rewording a comment does not separate a kernel from the counters taken on it."""
+    import re
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":   # literals are copied whole (a // inside them is not a comment)
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
+def kernel_source_hash(read=None) -> str:
+    """sha256 over the counting kernel's sources, code only (`_code_only`).  `read(name)` gives
+    a source's text (default: the file in the package's csrc)."""
     import hashlib
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2605_14743_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2605_14743_gb300", "csrc", name)) as f:
+                text = f.read()
+        else:
+            text = read(name)
+        h.update(_code_only(text).encode())
     return h.hexdigest()
 
 

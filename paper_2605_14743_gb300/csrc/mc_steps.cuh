@@ -19,16 +19,16 @@ namespace afc {
 // (sigma, then rho in place), ord[n] (settle order; bit 15 marks the first node of a step) and
 // plist[n] (the pending nodes: discovered, not yet settled, each once).
 //
-// Compact form (COMPACT = true, 12 bytes per node): dist[n] and one 8-byte word per node,
-// word[v] = sigma(v) (32 bits) | plist entry v (16 bits) | ord entry v (16 bits); ord and plist
-// are not used.  The backward pass no longer needs sigma of a node once its rho is known, nor
-// the pending list, nor 32-bit distances: when the forward pass ends, each node's distance
-// mod 2^16 moves into its plist half, and rho(v) (64 bits) takes dist[v] (high half) and the
-// sigma half of word[v] (low half).  Distances mod 2^16 identify successors exactly when every
-// length is below 2^15 (adjacent nodes' distances differ by at most the arc's length), and
-// sigma must stay below 2^32: a realization outside either limit runs on wide slots (the
-// routine reports a path count above 2^32 - 1 as ovf bit 1 and the caller redoes the
-// realization).
+// Compact form (COMPACT = true, 12 bytes per node): dist[n] and n 8-byte words, word[k] =
+// sigma of node k (low 32 bits) | pending-list entry k (16 bits) | settle-order entry k (top
+// 16 bits); the separate ord and plist arrays are not used.  The backward pass no longer needs
+// sigma of a node once its rho is known, nor the pending list, nor 32-bit distances: when the
+// forward pass ends, node v's distance mod 2^16 moves into the pending-list half of word[v],
+// and rho(v) (64 bits) takes dist[v] (high half) and the sigma half of word[v] (low half).
+// Distances mod 2^16 identify successors exactly when every length is below 2^15 (adjacent
+// nodes' distances differ by at most the arc's length), and sigma must stay below 2^32: a
+// realization outside either limit runs on wide slots (the routine reports a path count above
+// 2^32 - 1 as ovf bit 1 and the caller redoes the realization).
 struct StepSlot {
   uint32_t *dist;
   uint64_t *sig;
@@ -138,8 +138,9 @@ template <> struct StepTune<false> { static constexpr int pend = 16, fwd = 4, bw
 // predecessors while the step's arcs are relaxed; the next step's bounds d_min and
 // min (d + mw) come from the pending nodes that stay and from the relaxations (every pending
 // node's current distance is one of those values, and no recorded value is below the node's
-// current distance), so no separate pass over the pending list is needed.  Backward (want_delta): the steps in
-// reverse; rho(v) = (1 + delta(v)) / sigma(v) replaces sigma in place, delta(v) =
+// current distance), so no separate pass over the pending list is needed.  Backward
+// (want_delta): the steps in reverse; rho(v) = (1 + delta(v)) / sigma(v) replaces sigma in
+// place, delta(v) =
 // sigma(v) * sum over successors w of rho(w) in arc order; unique-path subtrees (sigma = 1
 // throughout) stay exact integers.  delta_s(v) for v != s goes to the exact accumulators of
 // the CTA scratch (fx_red).  Every lane of the warp must call it; err / ovf collect
